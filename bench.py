@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark: factor + solve of a FEM stiffness system on one B300.
+
+Default workload: 2D heterogeneous diffusion on 512 x 512 cubic (Q3) Lagrange
+elements (2,362,369 dofs), k_e = 10^U(-2,2) per element, manufactured load,
+elimination tree by recursive bisection to single elements.  One step =
+factor (all Foata classes) + solve refined in FP64 to a normwise backward
+error <= 1e-12.  The headline path factors in FP32 fronts (precision
+``--precision``, default f32); the plain FP64 GPU path is timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank solves its own replica (the workload has no
+exchange step); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import fem_inputs as F  # noqa: E402
+
+METRIC = "factor+solve ms and TFLOP/s vs plain FP64 GPU path at rel. residual <=1e-12"
+TOL = 1e-12
+WORKLOADS = {
+    # name: (builder, description)
+    "diffusion2d_q3_512": (lambda: F.diffusion_2d(512, 3, seed=F.SEED_BASE + 2),
+                           "2D heterogeneous diffusion, 512x512 Q3, k=10^U(-2,2), 2,362,369 dofs"),
+    "diffusion2d_q3_128": (lambda: F.diffusion_2d(128, 3, seed=F.SEED_BASE + 2),
+                           "2D heterogeneous diffusion, 128x128 Q3, k=10^U(-2,2), 148,225 dofs"),
+    "diffusion3d_q1_64": (lambda: F.diffusion_3d_q1(64, seed=F.SEED_BASE + 4),
+                          "3D diffusion, 64^3 Q1, k=10^U(-1,1), 274,625 dofs"),
+    "poisson2d_q1_16": (lambda: F.poisson_2d_q1(16), "2D Poisson, 16x16 Q1, 289 dofs"),
+}
+# bounded CPU sample per workload for the oracle arm: same recipe, smaller mesh
+CPU_SAMPLE = {
+    "diffusion2d_q3_512": ("diffusion2d_q3_128", lambda: F.diffusion_2d(128, 3, seed=F.SEED_BASE + 2)),
+    "diffusion2d_q3_128": ("diffusion2d_q3_128", lambda: F.diffusion_2d(128, 3, seed=F.SEED_BASE + 2)),
+    "diffusion3d_q1_64": ("diffusion3d_q1_16", lambda: F.diffusion_3d_q1(16, seed=F.SEED_BASE + 4)),
+    "poisson2d_q1_16": ("poisson2d_q1_16", lambda: F.poisson_2d_q1(16)),
+}
+FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"], "src": "measured"}
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "src": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_arm_step(sample_builder):
+    """One oracle factor + refined solve of the bounded sample; returns (seconds, flops, threads, info)."""
+    import oracle as O
+    pr = sample_builder()
+    pm = pr.mesh
+    s = O.OracleSolver(pm.n_nodes, pm.elem_nodes, O.tree_bisection(pm.nel))
+    nt = O.max_threads()
+    t0 = time.perf_counter()
+    s.factor(F.to_colmajor(pr.Ke), nthreads=nt)
+    x, it = s.solve_refined(pr.b, maxit=10)
+    t1 = time.perf_counter()
+    fl = s.flops + 2.0 * s.nnz_lu * (it + 1) * pr.nrhs
+    return t1 - t0, fl, nt, {"refine_steps": it, "n_dof": pm.n_nodes}
+
+
+def full_flops(name):
+    """Algorithmic factor flops + one solve of the full workload (oracle's symbolic count)."""
+    import oracle as O
+    pr_nel = {"diffusion2d_q3_512": ((512, 512), 3), "diffusion2d_q3_128": ((128, 128), 3),
+              "diffusion3d_q1_64": ((64, 64, 64), 1), "poisson2d_q1_16": ((16, 16), 1)}[name]
+    pm = F.structured_mesh(*pr_nel)
+    s = O.OracleSolver(pm.n_nodes, pm.elem_nodes, O.tree_bisection(pm.nel))
+    return float(s.flops), float(s.nnz_lu)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    name = args.workload
+    sname, sb = CPU_SAMPLE[name]
+    ff, fnnz = full_flops(name)
+    times, fls = [], []
+    for i in range(args.warmup + args.steps):
+        dt, fl, nt, info = oracle_arm_step(sb)
+        if i >= args.warmup:
+            times.append(dt)
+            fls.append(fl)
+    # project the sample's time to the full workload by the algorithmic flop ratio
+    sample_flops = float(np.mean(fls))
+    full = ff + 2.0 * fnnz * (info["refine_steps"] + 1)
+    ms = float(np.mean(times)) * 1e3 * full / sample_flops
+    tflops = sample_flops / float(np.mean(times)) / 1e12
+    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": name, "desc": WORKLOADS[name][1], "cpu_sample": sname},
+            "tflops": tflops,
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": nt, "kind": "oracle",
+                             "sample": f"oracle factor+refined solve of {sname} (same recipe) per step, "
+                                       f"time scaled to the full workload by algorithmic flops"},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="diffusion2d_q3_512", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default="f32", choices=["f32", "tf32", "f64"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import paper_2306_08994_b300 as M
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    builder, desc = WORKLOADS[args.workload]
+    pr = builder()
+    pm = pr.mesh
+    Kcm = F.to_colmajor(pr.Ke)
+    vals = torch.tensor(Kcm, device="cuda")
+    b = torch.tensor(np.ascontiguousarray(pr.b.T), device="cuda").reshape(-1) if pr.nrhs == 1 else \
+        torch.tensor(np.ascontiguousarray(pr.b.T), device="cuda")
+    x = torch.empty_like(b)
+    mesh = M.Mesh(pm.elem_nodes, pm.n_nodes, pm.dim, grid_dims=pm.nel)
+    an = M.Analysis(mesh, M.default_options(precision=args.precision, max_nrhs=max(4, pr.nrhs)))
+    fac = M.Factors(an)
+    info = an.info
+    stream = torch.cuda.current_stream()
+
+    def step(f, v, bb, xx):
+        f.factor(v)
+        return f.refine_solve(v, bb, xx, tol=TOL, maxit=60)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        r = step(fac, vals, b, x)
+    barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    fac.profile_read()  # reset launch/work accounting
+    iters = []
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        for i in range(args.steps):
+            r = step(fac, vals, b, x)
+            iters.append(r["iterations"])
+            ev[i + 1].record(stream)
+        barrier()
+    acct = fac.profile_read()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    ms = float(np.sum(per)) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = fac.status()
+    launches = int(sum(v["launches"] for v in acct.values()))
+    nsolve = float(np.mean(iters)) + 1
+    flops = info["factor_flops"] + info["solve_flops"] * nsolve * pr.nrhs
+    eta = r["backward_error"]
+
+    # accuracy vs the refined target: independent host check of the backward error
+    xs = x.reshape(pr.nrhs, -1).cpu().numpy().T
+
+    # plain FP64 GPU path, same metric
+    fp64 = None
+    if args.precision != "f64" and args.fp64_steps > 0:
+        an64 = M.Analysis(mesh, M.default_options(precision="f64", max_nrhs=max(4, pr.nrhs)))
+        f64 = M.Factors(an64)
+        x64 = torch.empty_like(b)
+        step(f64, vals, b, x64)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.fp64_steps):
+            r64 = step(f64, vals, b, x64)
+        e1.record(stream)
+        barrier()
+        ms64 = e0.elapsed_time(e1) / args.fp64_steps
+        nsolve64 = r64["iterations"] + 1
+        fp64 = {"ms": ms64, "tflops": (info["factor_flops"] + info["solve_flops"] * nsolve64 * pr.nrhs) / ms64 / 1e9,
+                "backward_error": r64["backward_error"], "refine_iterations": r64["iterations"],
+                "rel_diff_vs_headline": float(torch.linalg.norm(x64 - x) / torch.linalg.norm(x64))}
+        del f64, an64, x64
+        torch.cuda.empty_cache()
+
+    # roofline: per-family event timing over the same K steps
+    fac.profile(True)
+    fac.profile_read()
+    for _ in range(args.steps):
+        step(fac, vals, b, x)
+    prof = fac.profile_read()
+    fac.profile(False)
+    peaks = load_peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    launches_dom = max(d["launches"], 1)
+    per_launch_ms = d["ms"] / launches_dom
+    if dom in ("trailing_gemm", "schur_gemm", "panel") and args.precision != "tf32":
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS if args.precision != "f64" else None,
+                "unit": "TFLOP/s"}
+    elif dom in ("trailing_gemm", "schur_gemm"):
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"] / 2, "unit": "TFLOP/s"}
+    else:
+        achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("peak") else None
+    roof["traffic"] = None
+    roof["kernel_family"] = dom
+    roof["per_launch_ms"] = per_launch_ms
+    roof["peak_src"] = peaks["src"] if roof["bound"] != "alu" else "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz"
+    families = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                    "GBps": v["bytes"] / max(v["ms"], 1e-9) / 1e6, "TFLOPps": v["flops"] / max(v["ms"], 1e-9) / 1e9}
+                for k, v in prof.items() if v["launches"]}
+
+    # end to end through the public API with host buffers
+    hv = torch.from_numpy(Kcm).pin_memory()
+    hb = b.cpu().pin_memory()
+    hx = torch.empty_like(hb).pin_memory()
+    dv = torch.empty_like(vals)
+    db = torch.empty_like(b)
+    dx = torch.empty_like(b)
+    for _ in range(1):
+        dv.copy_(hv, non_blocking=True)
+        db.copy_(hb, non_blocking=True)
+        step(fac, dv, db, dx)
+        hx.copy_(dx, non_blocking=True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dv.copy_(hv, non_blocking=True)
+        db.copy_(hb, non_blocking=True)
+        step(fac, dv, db, dx)
+        hx.copy_(dx, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sname, sb = CPU_SAMPLE[args.workload]
+        dt, fl, nt, cinfo = oracle_arm_step(sb)
+        ff, fnnz = full_flops(args.workload)
+        full = ff + 2.0 * fnnz * (cinfo["refine_steps"] + 1)
+        cpu = {"value": dt * 1e3 * full / fl, "unit": "ms", "cores": nt, "kind": "oracle",
+               "sample": f"one oracle factor+refined solve of {sname} (same recipe, {cinfo['n_dof']} dofs) "
+                         f"took {dt:.2f} s; scaled to the full workload by algorithmic flops"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": args.workload, "desc": desc, "n_dof": info["n_dof"], "n_front": info["n_front"],
+                       "classes": info["n_classes"], "max_front": info["max_m"], "nrhs": pr.nrhs,
+                       "refine": f"FP64 residual, tol {TOL} normwise backward error",
+                       "l2": "inputs larger than L2 (element matrices %.0f MB)" % (Kcm.nbytes / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "tflops": flops / ms / 1e9,
+            "backward_error": eta, "rel_residual": r["rel_residual"], "refine_iterations": float(np.mean(iters)),
+            "pivots_perturbed": st["n_perturbed"],
+            "fp64_path": fp64,
+            "speedup_vs_fp64": (fp64["ms"] / ms) if fp64 else None,
+            "roofline": roof,
+            "families": families,
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(Kcm.nbytes + b.numel() * 8),
+                    "d2h_bytes_per_step": int(b.numel() * 8)},
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * mfsolve -- multifrontal direct solver for finite-element matrices on one
+ * B300 GPU (sm_103a).  C ABI of libmfsolve.so.
+ *
+ * The method is the multifrontal LU of arXiv 2306.08994: an elimination tree
+ * built bottom-up from element fronts (Sec. 2.4), fronts processed level by
+ * level, every level being one Foata normal-form class whose fronts are
+ * independent (Sec. 3.3), each front assembled from its children's Schur
+ * complements (extend-add, "join_fronts", Table 1), partially factored on its
+ * fully assembled pivots with the division / multiplication / subtraction
+ * tasks of Sec. 3 and Table 2 (no pivoting, L non-unit, U unit diagonal), and
+ * its Schur complement S = F22 - F21 F11^-1 F12 (Sec. 2.2) handed to the
+ * parent; the root is factored completely (Table 1).  The solution is
+ * obtained by forward and backward substitution (`get_solution`, Table 2).
+ *
+ * Conventions for every entry point
+ *  - Return value: MF_OK (0) or a negative MF_E* code; nothing throws across
+ *    the ABI.  mf_strerror() names a code.
+ *  - Pointers named d_* are device pointers (CUDA global memory of the
+ *    current device); every other pointer is host memory.  Inputs are owned
+ *    by the caller and only borrowed for the duration of the call (device
+ *    inputs: until the work enqueued on `stream` has finished).
+ *  - Opaque handles are owned by the library until mf_free_*().
+ *  - Device work is enqueued asynchronously on `stream` (NULL = legacy
+ *    default stream); device-detected conditions (perturbed or zero pivots,
+ *    non-finite values) are reported by mf_status(), which synchronises.
+ *  - Handles are not thread-safe; use one handle per host thread.
+ *  - Element matrices: n_elem blocks of npe*npe doubles, block e column-major
+ *    (entry (a,b) of element e at e*npe*npe + a + b*npe), rows/columns in the
+ *    order of that element's nodes.  Dirichlet conditions are the caller's:
+ *    the library solves the assembled system sum_e P_e^T K_e P_e exactly as
+ *    given.
+ *  - Vectors: n_dof x nrhs doubles, column-major (dof fastest).
+ */
+#ifndef MFSOLVE_H
+#define MFSOLVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ABI-compatible with cudaStream_t / CUstream. */
+typedef struct CUstream_st* mf_stream_t;
+
+#define MF_OK 0
+#define MF_EINVAL (-1)       /* bad argument or handle */
+#define MF_ENOMEM (-2)       /* device or host allocation failed */
+#define MF_ECUDA (-3)        /* a CUDA runtime call failed */
+#define MF_EZERO_PIVOT (-4)  /* |pivot| below the static threshold with pivot_fail set */
+#define MF_ENOCONV (-5)      /* refinement did not reach the tolerance within maxit */
+#define MF_ETIMEOUT (-6)     /* a bounded device wait ran out */
+#define MF_ENOTSUP (-7)      /* option or input form not supported */
+
+/* Arithmetic of the fronts (factor storage, extend-add, partial LU, Schur
+ * update, triangular solves).  Residuals and solution updates are always FP64. */
+#define MF_F64 0   /* FP64 throughout: the plain path */
+#define MF_F32 1   /* FP32 fronts, FP32 SIMT Schur GEMMs */
+#define MF_TF32 2  /* FP32 fronts, Schur GEMMs of large fronts on the tensor cores (tcgen05,
+                      three-pass split TF32 = FP32-accurate products), FP32 accumulation */
+
+typedef struct {
+    int precision;        /* MF_F64 (default), MF_F32 or MF_TF32 */
+    double pivot_tol;     /* static pivot check: a pivot with |p| < pivot_tol * max|F| (max over its
+                             front at assembly) is replaced by sign(p) * that bound (counted in
+                             mf_status) or fails; <= 0 selects the unit roundoff of `precision` */
+    int pivot_fail;       /* nonzero: a small pivot makes mf_status return MF_EZERO_PIVOT */
+    int small_front_max;  /* fronts with m <= this run in the fused one-CTA kernel; 0 = default */
+    int panel_width;      /* pivot block width of the large-front partial LU; 0 = default */
+    int use_graph;        /* nonzero: replay factor/solve as captured CUDA graphs */
+    int max_nrhs;         /* largest nrhs passed to mf_solve / mf_refine_solve; 0 = 4 */
+} mf_options;
+
+typedef struct {
+    int dim;                      /* 2 or 3 */
+    int64_t n_nodes;              /* number of dofs (one per node) */
+    int64_t n_elem;
+    int nodes_per_elem;           /* npe, <= 64 */
+    const int64_t* elem_nodes;    /* n_elem * npe node ids, element e at [e*npe, (e+1)*npe) */
+    const double* elem_centroid;  /* n_elem * dim coordinates used for recursive coordinate
+                                     bisection when grid_dims is NULL; may be NULL otherwise */
+    const int32_t* grid_dims;     /* {nx, ny, nz} (nz = 1 in 2D) for a structured grid whose
+                                     element (ex,ey,ez) has id ex + nx*(ey + ny*ez): the tree is
+                                     the recursive floor bisection of the element box along its
+                                     longest axis (ties x, y, z) -- or NULL */
+} mf_mesh_desc;
+
+typedef struct {
+    int64_t n_dof, n_elem, n_front, n_meshes;
+    int32_t n_classes;    /* Foata classes = tree height (leaves are class 1) */
+    int32_t max_m, max_k, root_m;
+    int64_t sum_k;        /* equals n_dof */
+    int64_t nnz_lu;       /* sum over fronts of m*k + k*(m-k) */
+    int64_t sum_cb;       /* sum over fronts of (m-k)^2 */
+    double factor_flops;  /* sum over pivots of (m-p-1) + 2 (m-p-1)^2 */
+    double solve_flops;   /* per right-hand side: 2 nnz_lu (approx.) */
+} mf_info;
+
+typedef struct {
+    int64_t n_perturbed;  /* pivots replaced by the static check */
+    int32_t first_front;  /* front (analysis numbering) of the first small pivot, or -1 */
+    int32_t first_pivot;  /* its pivot index inside the front, or -1 */
+    int32_t nonfinite;    /* nonzero if a non-finite pivot was met */
+    int32_t timeout;      /* nonzero if a bounded device wait ran out */
+} mf_status_info;
+
+typedef struct {
+    int iterations;       /* refinement corrections applied */
+    double backward_error;/* final ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf), max over rhs */
+    double rel_residual;  /* final ||b - A x||_2 / ||b||_2, max over rhs */
+} mf_refine_info;
+
+typedef struct mf_analysis mf_analysis;
+typedef struct mf_factors mf_factors;
+
+void mf_default_options(mf_options* opt);
+const char* mf_strerror(int code);
+
+/* Symbolic analysis of one mesh (Sec. 2.4 tree, Table 2 pivot rule, Sec. 3.2
+ * pivots-first ordering, Sec. 3.3 Foata classes at front granularity).  Host
+ * only; copies everything it needs from `mesh`.  `opt` may be NULL. */
+int mf_analyze_mesh(const mf_mesh_desc* mesh, const mf_options* opt, mf_analysis** out);
+
+/* Analysis of `count` independent meshes solved together: one forest whose
+ * fronts of equal height (aligned from the leaves) form one class, so each
+ * class runs as one batched pass across all meshes.  Dofs, elements and
+ * vectors are the meshes' concatenated in order. */
+int mf_analyze_batch(const mf_mesh_desc* meshes, int count, const mf_options* opt, mf_analysis** out);
+
+int mf_analysis_info(const mf_analysis* a, mf_info* out);
+
+/* Export the front structure (fronts numbered class by class).  Every array
+ * may be NULL.  parent, cls, m, k: n_front entries (parent -1 at a root);
+ * dof_ptr: n_front+1 offsets into dofs; dofs: sum of m entries, each front's
+ * pivots (ascending dof id) followed by its contribution-block dofs
+ * (ascending). */
+int mf_analysis_export(const mf_analysis* a, int32_t* parent, int32_t* cls, int32_t* m, int32_t* k,
+                       int64_t* dof_ptr, int32_t* dofs);
+
+/* Allocate the device storage for one factorization of `a` (factor arena,
+ * contribution-block arena, solve and refinement work space) and upload the
+ * front maps.  Allocation happens here and only here, so mf_factor /
+ * mf_solve / mf_refine_solve allocate nothing.  `opt` may be NULL (the
+ * analysis options are used). */
+int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf_factors** out);
+
+/* Numeric factorization (Tables 1-2): class by class, one batched pass per
+ * class of extend-add, partial LU with the static pivot check, and Schur
+ * update.  d_values: the element matrices (see conventions), device. */
+int mf_factor(mf_factors* f, const double* d_values, mf_stream_t stream);
+
+/* x = A^-1 b in place: forward substitution with L leaves->root, backward
+ * with U root->leaves (get_solution, Table 2).  d_rhs: n_dof x nrhs. */
+int mf_solve(mf_factors* f, double* d_rhs, int nrhs, mf_stream_t stream);
+
+/* x = A^-T b in place with the same factors: U^T forward, L^T backward. */
+int mf_solve_adjoint(mf_factors* f, double* d_rhs, int nrhs, mf_stream_t stream);
+
+/* Iterative refinement in FP64: x = solve(b); repeat r = b - A x (FP64,
+ * element by element), x += solve(r) until the normwise backward error
+ * ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= tol or maxit corrections.
+ * Returns MF_ENOCONV if tol was not reached (x still holds the last iterate).
+ * Synchronises `stream` once per correction to test convergence. */
+int mf_refine_solve(mf_factors* f, const double* d_values, const double* d_b, double* d_x, int nrhs,
+                    double tol, int maxit, mf_refine_info* info, mf_stream_t stream);
+
+/* r = b - A x in FP64 with A given element by element. */
+int mf_residual(const mf_factors* f, const double* d_values, const double* d_x, const double* d_b,
+                double* d_r, int nrhs, mf_stream_t stream);
+
+/* Adjoint gradient for per-element parameters: g_e = -lambda_e^T dK_e x_e,
+ * dK_e = dK/dtheta_e given as element matrices (same layout as values);
+ * lambda solves A^T lambda = dJ/dx (mf_solve_adjoint).  One right-hand side. */
+int mf_element_grad(const mf_factors* f, const double* d_dvalues, const double* d_lambda, const double* d_x,
+                    double* d_grad, mf_stream_t stream);
+
+/* Gradient with respect to the element matrices themselves:
+ * G_e = -lambda_e x_e^T (npe x npe, column-major per element), summed over
+ * nrhs right-hand sides. */
+int mf_element_outer(const mf_factors* f, const double* d_lambda, const double* d_x, int nrhs,
+                     double* d_gradK, mf_stream_t stream);
+
+/* Synchronise and report what the device saw during the last mf_factor.
+ * Returns MF_EZERO_PIVOT if a pivot was small and pivot_fail is set. */
+int mf_status(mf_factors* f, mf_status_info* out);
+
+/* Copy front `front`'s factor to the host as FP64: L (m x k, column-major:
+ * the pivot columns, L on/below the diagonal, U11 strictly above) and U
+ * (k x m, column-major: the pivot rows).  Synchronises.  For tests. */
+int mf_factors_export_front(const mf_factors* f, int32_t front, double* L, double* U);
+
+/* Per-kernel-family accounting for roofline reports.  While enabled, every
+ * launch issued by mf_factor / mf_solve / mf_solve_adjoint / mf_refine_solve
+ * is bracketed by CUDA events on the launching stream and its algorithmic
+ * work is added up: bytes = the data the operation must move at minimum
+ * (inputs read once, outputs written once), flops = the arithmetic the
+ * algorithm performs.  Families: 0 fused small fronts, 1 large-front
+ * assembly, 2 panel LU, 3 trailing GEMM, 4 Schur GEMM, 5 forward
+ * substitution, 6 backward substitution, 7 residual and norms, 8 other.
+ * mf_profile_read synchronises, writes MF_PROFILE_FAMILIES entries to each
+ * non-NULL array (summed since the last read) and resets the sums. */
+#define MF_PROFILE_FAMILIES 9
+int mf_profile_enable(mf_factors* f, int enable);
+int mf_profile_read(mf_factors* f, double* ms, int64_t* launches, double* bytes, double* flops);
+
+void mf_free_factors(mf_factors* f);
+void mf_free_analysis(mf_analysis* a);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFSOLVE_H */

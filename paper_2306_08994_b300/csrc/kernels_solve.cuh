@@ -1,0 +1,471 @@
+// Solve-phase kernels: batched forward/backward substitution down the tree
+// (`get_solution`, Table 2), FP64 element-by-element residual for iterative
+// refinement, norms, and the adjoint gradient contractions.
+#pragma once
+
+#include <cstdint>
+
+#include "mf_internal.h"
+
+// ---------------------------------------------------------------------------
+// Substitution down the tree (`get_solution`, Table 2), one class per step.
+// Per front, with w the front's right-hand side (b at its pivots plus the
+// children's update vectors):
+//   forward  !TRANS: L11 y = w1, w2 -= L21 y           (L non-unit)
+//             TRANS: U11^T y = w1, w2 -= U12^T y       (unit)
+//   backward !TRANS: U11 x1 = y - U12 x_CB             (unit)
+//             TRANS: L11^T x1 = y - L21^T x_CB
+// y is kept in x at the pivots between the two sweeps; w2 goes to the
+// front's update vector, pulled by the parent (no two fronts write the same
+// entry, so the result is deterministic).
+//
+// Coefficient accessors.  Forward: coefficient of pivot p in row i (i > p).
+template <typename T, bool TRANS>
+__device__ __forceinline__ T fcoef(const T* P, const T* R, int m, int k, int i, int p) {
+    if (!TRANS) return P[i + (int64_t)p * m];
+    return i < k ? P[p + (int64_t)i * m] : R[p + (int64_t)(i - k) * k];
+}
+// Backward: coefficient of unknown j in pivot row i (j > i).
+template <typename T, bool TRANS>
+__device__ __forceinline__ T bcoef(const T* P, const T* R, int m, int k, int i, int j) {
+    if (!TRANS) return j < k ? P[i + (int64_t)j * m] : R[i + (int64_t)(j - k) * k];
+    return P[j + (int64_t)i * m];
+}
+template <typename T, bool TRANS>
+__device__ __forceinline__ T fdiag(const T* P, int m, int p) {
+    return TRANS ? T(1) : P[p + (int64_t)p * m];
+}
+template <typename T, bool TRANS>
+__device__ __forceinline__ T bdiag(const T* P, int m, int p) {
+    return TRANS ? P[p + (int64_t)p * m] : T(1);
+}
+
+template <typename T>
+__device__ __forceinline__ T gather_rhs(const FrontDev& fr, const FrontDev* __restrict__ fronts, const int32_t* __restrict__ fd,
+                                        const int32_t* __restrict__ maps, const T* __restrict__ vr,
+                                        const double* __restrict__ xr, int i) {
+    T v = i < fr.k ? (T)xr[fd[i]] : T(0);
+    for (int c = 0; c < fr.nchild; c++) {
+        int ic = maps[fr.map_off + (int64_t)c * fr.m + i];
+        if (ic >= 0) v += vr[fronts[fr.child[c]].vec_off + ic];
+    }
+    return v;
+}
+
+// Small fronts (m <= 64): one warp per front, rows lane and lane+32.
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256) k_fwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
+                                                  const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
+                                                  double* __restrict__ x, int64_t n_dof) {
+    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (wid >= count) return;
+    const int r = blockIdx.y;
+    const FrontDev fr = fronts[list[wid]];
+    const int m = fr.m, k = fr.k;
+    const int32_t* fd = dofs + fr.dof_off;
+    double* xr = x + (int64_t)r * n_dof;
+    T* vr = vecs + (int64_t)r * vec_size;
+    const T* P = fac + fr.P_off;
+    const T* R = fac + fr.R_off;
+    const int i0 = lane, i1 = lane + 32;
+    T w0 = i0 < m ? gather_rhs<T>(fr, fronts, fd, maps, vr, xr, i0) : T(0);
+    T w1 = i1 < m ? gather_rhs<T>(fr, fronts, fd, maps, vr, xr, i1) : T(0);
+    for (int pc = 0; pc < k; pc += 8) {
+        T c0[8], c1[8], dg[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int p = pc + q;
+            c0[q] = (p < k && i0 > p && i0 < m) ? fcoef<T, TRANS>(P, R, m, k, i0, p) : T(0);
+            c1[q] = (p < k && i1 > p && i1 < m) ? fcoef<T, TRANS>(P, R, m, k, i1, p) : T(0);
+            dg[q] = p < k ? fdiag<T, TRANS>(P, m, p) : T(1);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int p = pc + q;
+            if (p >= k) break;
+            T wp = (p < 32) ? __shfl_sync(0xffffffffu, w0, p) : __shfl_sync(0xffffffffu, w1, p - 32);
+            const T yp = wp / dg[q];
+            if (i0 == p) w0 = yp;
+            if (i1 == p) w1 = yp;
+            w0 -= c0[q] * yp;
+            w1 -= c1[q] * yp;
+        }
+    }
+    if (i0 < m) {
+        if (i0 < k) xr[fd[i0]] = (double)w0;
+        else vr[fr.vec_off + (i0 - k)] = w0;
+    }
+    if (i1 < m) {
+        if (i1 < k) xr[fd[i1]] = (double)w1;
+        else vr[fr.vec_off + (i1 - k)] = w1;
+    }
+}
+
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256) k_bwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
+                                                  double* __restrict__ x, int64_t n_dof) {
+    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (wid >= count) return;
+    const int r = blockIdx.y;
+    const FrontDev fr = fronts[list[wid]];
+    const int m = fr.m, k = fr.k;
+    const int32_t* fd = dofs + fr.dof_off;
+    double* xr = x + (int64_t)r * n_dof;
+    const T* P = fac + fr.P_off;
+    const T* R = fac + fr.R_off;
+    const int i0 = lane, i1 = lane + 32;
+    // all unknowns of the front: pivots hold y, CB holds the final x
+    T v0 = i0 < m ? (T)xr[fd[i0]] : T(0);
+    T v1 = i1 < m ? (T)xr[fd[i1]] : T(0);
+    // eliminate the CB unknowns from the pivot rows (j >= k), then back-substitute
+    for (int jc = m - 1; jc >= 0; jc -= 8) {
+        T c0[8], c1[8], dg[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int j = jc - q;
+            c0[q] = (j >= 0 && i0 < k && i0 < j) ? bcoef<T, TRANS>(P, R, m, k, i0, j) : T(0);
+            c1[q] = (j >= 0 && i1 < k && i1 < j) ? bcoef<T, TRANS>(P, R, m, k, i1, j) : T(0);
+            dg[q] = (j >= 0 && j < k) ? bdiag<T, TRANS>(P, m, j) : T(1);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int j = jc - q;
+            if (j < 0) break;
+            T xj = (j < 32) ? __shfl_sync(0xffffffffu, v0, j) : __shfl_sync(0xffffffffu, v1, j - 32);
+            if (j < k) {
+                xj = xj / dg[q];
+                if (i0 == j) v0 = xj;
+                if (i1 == j) v1 = xj;
+            }
+            v0 -= c0[q] * xj;
+            v1 -= c1[q] * xj;
+        }
+    }
+    if (i0 < k) xr[fd[i0]] = (double)v0;
+    if (i1 < k) xr[fd[i1]] = (double)v1;
+}
+
+// Larger fronts: one CTA per front.  The pivot block is processed in
+// 32-wide blocks; each 32x32 diagonal block is staged in shared memory by all
+// threads, solved by warp 0, then applied to the later rows.  With
+// `rows_all` the CTA also produces the update vector (all m rows); otherwise
+// it stops at row k and k_fwd_rows does the contribution-block rows.
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256) k_fwd_cta(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+                                                 int rows_all, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
+                                                 const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
+                                                 double* __restrict__ x, int64_t n_dof) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Dg = reinterpret_cast<T*>(smem_raw);  // 32 x 33
+    T* w = Dg + 32 * 33;
+    const int r = blockIdx.y;
+    const FrontDev fr = fronts[list[blockIdx.x]];
+    const int m = fr.m, k = fr.k;
+    const int mr = rows_all ? m : k;
+    const int32_t* fd = dofs + fr.dof_off;
+    double* xr = x + (int64_t)r * n_dof;
+    T* vr = vecs + (int64_t)r * vec_size;
+    const T* P = fac + fr.P_off;
+    const T* R = fac + fr.R_off;
+    for (int i = threadIdx.x; i < mr; i += blockDim.x) w[i] = gather_rhs<T>(fr, fronts, fd, maps, vr, xr, i);
+    const int lane = threadIdx.x & 31;
+    for (int pb = 0; pb < k; pb += 32) {
+        const int wb = min(32, k - pb);
+        for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+            const int i = idx & 31, p = idx >> 5;  // row pb+i, pivot pb+p
+            T v = T(0);
+            if (i < wb && p < wb) v = (i > p) ? fcoef<T, TRANS>(P, R, m, k, pb + i, pb + p)
+                                              : (i == p ? fdiag<T, TRANS>(P, m, pb + p) : T(0));
+            Dg[i * 33 + p] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            T val = lane < wb ? w[pb + lane] : T(0);
+            for (int p = 0; p < wb; p++) {
+                T yp = __shfl_sync(0xffffffffu, val, p) / Dg[p * 33 + p];
+                if (lane == p) val = yp;
+                if (lane > p) val -= Dg[lane * 33 + p] * yp;
+            }
+            if (lane < wb) w[pb + lane] = val;
+        }
+        __syncthreads();
+        for (int i = pb + wb + threadIdx.x; i < mr; i += blockDim.x) {
+            T acc = T(0);
+#pragma unroll 8
+            for (int p = 0; p < wb; p++) acc += fcoef<T, TRANS>(P, R, m, k, i, pb + p) * w[pb + p];
+            w[i] -= acc;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < mr; i += blockDim.x) {
+        if (i < k) xr[fd[i]] = (double)w[i];
+        else vr[fr.vec_off + (i - k)] = w[i];
+    }
+}
+
+// Contribution-block rows of large fronts: u_i = w_i - sum_p coef(i,p) y_p for
+// a chunk of 128 rows, y read back from x at the front's pivots.
+struct RowTask {
+    int32_t front, r0, r1, pad;
+};
+
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(128) k_fwd_rows(const FrontDev* __restrict__ fronts, const RowTask* __restrict__ tasks,
+                                                  const T* __restrict__ fac, const int32_t* __restrict__ dofs,
+                                                  const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
+                                                  double* __restrict__ x, int64_t n_dof) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* y = reinterpret_cast<T*>(smem_raw);
+    const RowTask t = tasks[blockIdx.x];
+    const int r = blockIdx.y;
+    const FrontDev fr = fronts[t.front];
+    const int m = fr.m, k = fr.k;
+    const int32_t* fd = dofs + fr.dof_off;
+    double* xr = x + (int64_t)r * n_dof;
+    T* vr = vecs + (int64_t)r * vec_size;
+    const T* P = fac + fr.P_off;
+    const T* R = fac + fr.R_off;
+    for (int p = threadIdx.x; p < k; p += blockDim.x) y[p] = (T)xr[fd[p]];
+    __syncthreads();
+    const int i = t.r0 + threadIdx.x;
+    if (i >= t.r1) return;
+    T acc = gather_rhs<T>(fr, fronts, fd, maps, vr, xr, i);
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    int p = 0;
+    for (; p + 4 <= k; p += 4) {
+        a0 += fcoef<T, TRANS>(P, R, m, k, i, p) * y[p];
+        a1 += fcoef<T, TRANS>(P, R, m, k, i, p + 1) * y[p + 1];
+        a2 += fcoef<T, TRANS>(P, R, m, k, i, p + 2) * y[p + 2];
+        a3 += fcoef<T, TRANS>(P, R, m, k, i, p + 3) * y[p + 3];
+    }
+    for (; p < k; p++) a0 += fcoef<T, TRANS>(P, R, m, k, i, p) * y[p];
+    vr[fr.vec_off + (i - k)] = acc - ((a0 + a1) + (a2 + a3));
+}
+
+// Backward, large fronts split: pivot rows i of a chunk: z_i = y_i - sum_{j>=k} coef(i,j) x_j.
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(128) k_bwd_rows(const FrontDev* __restrict__ fronts, const RowTask* __restrict__ tasks,
+                                                  const T* __restrict__ fac, const int32_t* __restrict__ dofs,
+                                                  double* __restrict__ x, int64_t n_dof) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xc = reinterpret_cast<T*>(smem_raw);
+    const RowTask t = tasks[blockIdx.x];
+    const int r = blockIdx.y;
+    const FrontDev fr = fronts[t.front];
+    const int m = fr.m, k = fr.k, nc = m - k;
+    const int32_t* fd = dofs + fr.dof_off;
+    double* xr = x + (int64_t)r * n_dof;
+    const T* P = fac + fr.P_off;
+    const T* R = fac + fr.R_off;
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) xc[j] = (T)xr[fd[k + j]];
+    __syncthreads();
+    const int i = t.r0 + threadIdx.x;
+    if (i >= t.r1) return;
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    int j = 0;
+    for (; j + 4 <= nc; j += 4) {
+        a0 += bcoef<T, TRANS>(P, R, m, k, i, k + j) * xc[j];
+        a1 += bcoef<T, TRANS>(P, R, m, k, i, k + j + 1) * xc[j + 1];
+        a2 += bcoef<T, TRANS>(P, R, m, k, i, k + j + 2) * xc[j + 2];
+        a3 += bcoef<T, TRANS>(P, R, m, k, i, k + j + 3) * xc[j + 3];
+    }
+    for (; j < nc; j++) a0 += bcoef<T, TRANS>(P, R, m, k, i, k + j) * xc[j];
+    xr[fd[i]] = (double)((T)xr[fd[i]] - ((a0 + a1) + (a2 + a3)));
+}
+
+// Backward, one CTA per large front.  With `cb_done` the CB part was already
+// subtracted by k_bwd_rows; otherwise it is done here first.
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256) k_bwd_cta(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+                                                 int cb_done, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
+                                                 double* __restrict__ x, int64_t n_dof) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Dg = reinterpret_cast<T*>(smem_raw);
+    T* v = Dg + 32 * 33;
+    const int r = blockIdx.y;
+    const FrontDev fr = fronts[list[blockIdx.x]];
+    const int m = fr.m, k = fr.k;
+    const int32_t* fd = dofs + fr.dof_off;
+    double* xr = x + (int64_t)r * n_dof;
+    const T* P = fac + fr.P_off;
+    const T* R = fac + fr.R_off;
+    const int mv = cb_done ? k : m;
+    for (int i = threadIdx.x; i < mv; i += blockDim.x) v[i] = (T)xr[fd[i]];
+    __syncthreads();
+    if (!cb_done) {
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            T acc = T(0);
+            for (int j = k; j < m; j++) acc += bcoef<T, TRANS>(P, R, m, k, i, j) * v[j];
+            v[i] -= acc;
+        }
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    for (int pe = k; pe > 0; pe -= 32) {
+        const int pb = max(0, pe - 32), wb = pe - pb;
+        for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+            const int i = idx & 31, j = idx >> 5;  // row pb+i, unknown pb+j
+            T c = T(0);
+            if (i < wb && j < wb) c = (i < j) ? bcoef<T, TRANS>(P, R, m, k, pb + i, pb + j)
+                                              : (i == j ? bdiag<T, TRANS>(P, m, pb + j) : T(0));
+            Dg[i * 33 + j] = c;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            T val = lane < wb ? v[pb + lane] : T(0);
+            for (int j = wb - 1; j >= 0; j--) {
+                T xj = __shfl_sync(0xffffffffu, val, j) / Dg[j * 33 + j];
+                if (lane == j) val = xj;
+                if (lane < j) val -= Dg[lane * 33 + j] * xj;
+            }
+            if (lane < wb) v[pb + lane] = val;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < pb; i += blockDim.x) {
+            T acc = T(0);
+#pragma unroll 8
+            for (int j = 0; j < wb; j++) acc += bcoef<T, TRANS>(P, R, m, k, i, pb + j) * v[pb + j];
+            v[i] -= acc;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) xr[fd[i]] = (double)v[i];
+}
+
+// ---------------------------------------------------------------------------
+// FP64 residual, element by element, deterministic:
+//   Y[e*npe + a] = sum_b K_e[a,b] x[node(e,b)]          (k_elem_apply)
+//   r[d] = b[d] - sum over the (e,a) touching d of Y    (k_gather_residual)
+// absmode: |K_e| and x = 1, giving the element-wise bound of ||A||_inf rows.
+__global__ void k_elem_apply(const double* __restrict__ values, const int64_t* __restrict__ en, const double* __restrict__ x,
+                             double* __restrict__ Y, int64_t n_elem, int npe, int64_t n_dof, int absmode) {
+    const int64_t nE = n_elem * npe;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (idx >= nE) return;
+    const int64_t e = idx / npe;
+    const int a = (int)(idx - e * npe);
+    const double* K = values + e * npe * npe + a;
+    const int64_t* nd = en + e * npe;
+    const double* xr = x + (int64_t)r * n_dof;
+    double acc = 0.0;
+    if (absmode) {
+        for (int b = 0; b < npe; b++) acc += fabs(K[b * npe]);
+    } else {
+        for (int b = 0; b < npe; b++) acc = fma(K[b * npe], xr[nd[b]], acc);
+    }
+    Y[idx + (int64_t)r * nE] = acc;
+}
+
+__global__ void k_gather_residual(const int64_t* __restrict__ node_ptr, const int64_t* __restrict__ node_inc,
+                                  const double* __restrict__ Y, const double* __restrict__ b, double* __restrict__ out,
+                                  int64_t n_dof, int64_t nE, int mode) {
+    const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (d >= n_dof) return;
+    double acc = 0.0;
+    for (int64_t t = node_ptr[d]; t < node_ptr[d + 1]; t++) acc += Y[node_inc[t] + (int64_t)r * nE];
+    // mode 0: out = b - A x ; mode 1: out = A x (b unused)
+    out[d + (int64_t)r * n_dof] = mode == 0 ? b[d + (int64_t)r * n_dof] - acc : acc;
+}
+
+// max that keeps a NaN once it has seen one (fmax would drop it)
+__device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
+
+// Per right-hand side norms: out[r*6 + {0..5}] = ||r||_inf, ||x||_inf, ||b||_inf,
+// ||r||_2^2, ||b||_2^2, ||Arow||_inf (the last one only for r == 0, from rowabs).
+// Two stages for a deterministic sum: block partials, then one block.
+__global__ void k_norms_partial(const double* __restrict__ rv, const double* __restrict__ xv, const double* __restrict__ bv,
+                                const double* __restrict__ rowabs, int64_t n, double* __restrict__ part) {
+    const int r = blockIdx.y;
+    const double* rr = rv + (int64_t)r * n;
+    const double* xx = xv + (int64_t)r * n;
+    const double* bb = bv + (int64_t)r * n;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double ri = rr[i], xi = xx[i], bi = bb[i];
+        a0 = nanmax(a0, fabs(ri));
+        a1 = nanmax(a1, fabs(xi));
+        a2 = nanmax(a2, fabs(bi));
+        a3 += ri * ri;
+        a4 += bi * bi;
+        if (rowabs) a5 = nanmax(a5, rowabs[i]);
+    }
+    __shared__ double sh[6][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 = nanmax(a0, __shfl_xor_sync(0xffffffffu, a0, o));
+        a1 = nanmax(a1, __shfl_xor_sync(0xffffffffu, a1, o));
+        a2 = nanmax(a2, __shfl_xor_sync(0xffffffffu, a2, o));
+        a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+        a4 += __shfl_xor_sync(0xffffffffu, a4, o);
+        a5 = nanmax(a5, __shfl_xor_sync(0xffffffffu, a5, o));
+    }
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sh[0][w] = a0; sh[1][w] = a1; sh[2][w] = a2; sh[3][w] = a3; sh[4][w] = a4; sh[5][w] = a5;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double o0 = 0, o1 = 0, o2 = 0, o3 = 0, o4 = 0, o5 = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+            o0 = nanmax(o0, sh[0][i]); o1 = nanmax(o1, sh[1][i]); o2 = nanmax(o2, sh[2][i]);
+            o3 += sh[3][i]; o4 += sh[4][i]; o5 = nanmax(o5, sh[5][i]);
+        }
+        double* p = part + ((int64_t)r * gridDim.x + blockIdx.x) * 6;
+        p[0] = o0; p[1] = o1; p[2] = o2; p[3] = o3; p[4] = o4; p[5] = o5;
+    }
+}
+
+__global__ void k_norms_final(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+    const int r = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    double o0 = 0, o1 = 0, o2 = 0, o3 = 0, o4 = 0, o5 = 0;
+    for (int i = 0; i < nblk; i++) {
+        const double* p = part + ((int64_t)r * nblk + i) * 6;
+        o0 = nanmax(o0, p[0]); o1 = nanmax(o1, p[1]); o2 = nanmax(o2, p[2]);
+        o3 += p[3]; o4 += p[4]; o5 = nanmax(o5, p[5]);
+    }
+    double* q = out + r * 6;
+    q[0] = o0; q[1] = o1; q[2] = o2; q[3] = o3; q[4] = o4; q[5] = o5;
+}
+
+__global__ void k_axpy(double* __restrict__ x, const double* __restrict__ d, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] += d[i];
+}
+
+// g_e = -lambda_e^T dK_e x_e: one warp per element.
+__global__ void k_element_grad(const double* __restrict__ dK, const int64_t* __restrict__ en, const double* __restrict__ lam,
+                               const double* __restrict__ x, double* __restrict__ g, int64_t n_elem, int npe) {
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (e >= n_elem) return;
+    const double* K = dK + e * npe * npe;
+    const int64_t* nd = en + e * npe;
+    double acc = 0.0;
+    for (int t = lane; t < npe * npe; t += 32) {
+        int a = t % npe, b = t / npe;
+        acc += lam[nd[a]] * K[t] * x[nd[b]];
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) g[e] = -acc;
+}
+
+// G_e[a + b*npe] = -sum_r lambda[node(e,a), r] x[node(e,b), r]
+__global__ void k_element_outer(const int64_t* __restrict__ en, const double* __restrict__ lam, const double* __restrict__ x,
+                                double* __restrict__ G, int64_t n_elem, int npe, int64_t n_dof, int nrhs) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nn = (int64_t)npe * npe;
+    if (idx >= n_elem * nn) return;
+    const int64_t e = idx / nn;
+    const int t = (int)(idx - e * nn);
+    const int a = t % npe, b = t / npe;
+    const int64_t na = en[e * npe + a], nb = en[e * npe + b];
+    double acc = 0.0;
+    for (int r = 0; r < nrhs; r++) acc += lam[na + (int64_t)r * n_dof] * x[nb + (int64_t)r * n_dof];
+    G[idx] = -acc;
+}

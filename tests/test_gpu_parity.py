@@ -1,0 +1,207 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (derived in the design doc):
+  * FP64 factors: |L - L_oracle| <= 1e-11 * max|front| per front (two FP64
+    eliminations of the same front differing only in summation order);
+  * solutions: ||x - x_oracle||_2 / ||x_oracle||_2 <= 1e-10 (the stated bar),
+    x_oracle refined with a double-double residual;
+  * refined paths (FP64 and FP32 fronts): normwise backward error
+    ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= 1e-12.
+"""
+import numpy as np
+import pytest
+import torch
+
+import fem_inputs as F
+import oracle as O
+import paper_2306_08994_b300 as M
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def _setup(pr, prec="f64", **opt):
+    pm = pr.mesh
+    a = M.Analysis(M.Mesh(pm.elem_nodes, pm.n_nodes, pm.dim, grid_dims=pm.nel),
+                   M.default_options(precision=prec, **opt))
+    f = M.Factors(a)
+    vals = torch.tensor(F.to_colmajor(pr.Ke), device=DEV)
+    return a, f, vals
+
+
+def _oracle(pr):
+    pm = pr.mesh
+    s = O.OracleSolver(pm.n_nodes, pm.elem_nodes, O.tree_bisection(pm.nel))
+    assert s.factor(F.to_colmajor(pr.Ke)) == 0
+    return s
+
+
+def _backward_error_host(pr, x, b):
+    """eta = ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) with the oracle's
+    double-double residual and the assembled ||A||_inf (host, independent of the GPU)."""
+    import scipy.sparse as sp
+    r = O.residual_dd(pr.mesh.elem_nodes, F.to_colmajor(pr.Ke), x, b)
+    rp, cp, vp = F.assemble_csr(pr.mesh, pr.Ke)
+    A = sp.csr_matrix((vp, cp, rp))
+    an = np.abs(A).sum(axis=1).max()
+    x2 = np.asarray(x).reshape(pr.mesh.n_nodes, -1)
+    b2 = np.asarray(b).reshape(pr.mesh.n_nodes, -1)
+    r2 = np.asarray(r).reshape(pr.mesh.n_nodes, -1)
+    out = 0.0
+    for j in range(x2.shape[1]):
+        num = np.abs(r2[:, j]).max()
+        den = an * np.abs(x2[:, j]).max() + np.abs(b2[:, j]).max()
+        out = max(out, num / den if den > 0 else (0.0 if num == 0 else np.inf))
+    return out
+
+
+CASES = {
+    "q1_16": (lambda: F.poisson_2d_q1(16), {}),
+    "q3_12_large_path": (lambda: F.diffusion_2d(12, 3, seed=31), {"small_front_max": 16}),
+    "q3_10_mixed_buckets": (lambda: F.diffusion_2d(10, 3, seed=32), {"small_front_max": 48}),
+    "q1_3d_6_large_path": (lambda: F.diffusion_3d_q1(6, seed=33), {"small_front_max": 24}),
+    "q1_1x1": (lambda: F.poisson_2d_q1(1), {}),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_f64_factors_match_oracle_front_by_front(case):
+    mk, opt = CASES[case]
+    pr = mk()
+    a, f, vals = _setup(pr, "f64", **opt)
+    f.factor(vals)
+    st = f.status()
+    assert st["rc"] == 0 and st["n_perturbed"] == 0
+    s = _oracle(pr)
+    order = np.lexsort((np.arange(s.n_front), s.height))
+    for g, v in enumerate(order):
+        Lg, Ug = f.export_front(g)
+        Lo, Uo = s.factor_of(v)
+        k = Lo.shape[1]
+        if k == 0:
+            continue
+        sc = max(np.abs(Lo).max(), np.abs(Uo).max(), 1.0)
+        low = np.tril(np.ones((Lo.shape[0], k), bool))
+        up = np.triu(np.ones((k, Uo.shape[1]), bool), 1)
+        assert np.abs(Lg - Lo)[low].max() <= 1e-11 * sc, (case, g)
+        if up.any():
+            assert np.abs(Ug - Uo)[up].max() <= 1e-11 * sc, (case, g)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_solution_matches_oracle(case, prec):
+    mk, opt = CASES[case]
+    pr = mk()
+    a, f, vals = _setup(pr, prec, **opt)
+    f.factor(vals)
+    s = _oracle(pr)
+    b = np.ascontiguousarray(pr.b.T)  # (nrhs, n)
+    xo, _ = s.solve_refined(pr.b)
+    bt = torch.tensor(b, device=DEV)
+    x = torch.empty_like(bt)
+    info = f.refine_solve(vals, bt, x, tol=1e-14, maxit=30)
+    xg = x.cpu().numpy().T
+    assert info["backward_error"] <= 1e-12, info
+    assert _backward_error_host(pr, xg, pr.b) <= 1e-12
+    err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    assert err <= 1e-10, (case, prec, err, info)
+    if prec == "f64":
+        # the plain FP64 solve (no refinement) also meets the solution bar
+        x1 = bt.clone()
+        f.solve(x1)
+        e1 = np.linalg.norm(x1.cpu().numpy().T - xo) / np.linalg.norm(xo)
+        assert e1 <= 1e-10, e1
+
+
+def test_adjoint_solve_on_unsymmetric_matrix():
+    pr = F.convection_2d_q1(9)
+    a, f, vals = _setup(pr, "f64", small_front_max=8)
+    f.factor(vals)
+    s = _oracle(pr)
+    g = np.ascontiguousarray(pr.b[:, 0])
+    lo = s.solve(g, adjoint=True)
+    xo = s.solve(g)
+    t = torch.tensor(g, device=DEV)
+    lam = t.clone()
+    f.solve(lam, adjoint=True)
+    x = t.clone()
+    f.solve(x)
+    assert np.linalg.norm(lam.cpu().numpy() - lo) <= 1e-12 * np.linalg.norm(lo)
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-12 * np.linalg.norm(xo)
+    assert np.linalg.norm(lo - xo) > 1e-3 * np.linalg.norm(xo)  # really unsymmetric
+
+
+def test_element_gradient_matches_oracle_and_autograd():
+    pr = F.adjoint_problem(n=24, n_fd=8)
+    a, f, vals = _setup(pr, "f64")
+    ut = pr.extra["u_target"]
+    b = torch.tensor(pr.b[:, 0], device=DEV)
+    K = vals.clone().requires_grad_(True)
+    x = M.MFSolve.apply(K, b, f, 0.0)
+    J = 0.5 * torch.sum((x - torch.tensor(ut, device=DEV)) ** 2)
+    J.backward()
+    s = _oracle(pr)
+    xo = s.solve(pr.b[:, 0])
+    lo = s.solve(xo - ut, adjoint=True)
+    go = O.element_grad(pr.mesh.elem_nodes, F.to_colmajor(pr.extra["dK"]), lo, xo)
+    # dJ/dK_e = -lambda_e x_e^T ; chain to theta through dK_e/dtheta_e
+    gK = K.grad.cpu().numpy().reshape(pr.mesh.n_elem, -1)
+    g_chain = (gK * F.to_colmajor(pr.extra["dK"]).reshape(pr.mesh.n_elem, -1)).sum(axis=1)
+    assert np.abs(g_chain - go).max() <= 1e-10 * np.abs(go).max()
+    lam = torch.tensor(lo, device=DEV)
+    g = torch.empty(pr.mesh.n_elem, dtype=torch.float64, device=DEV)
+    f.element_grad(torch.tensor(F.to_colmajor(pr.extra["dK"]), device=DEV), lam,
+                   torch.tensor(xo, device=DEV), g)
+    assert np.abs(g.cpu().numpy() - go).max() <= 1e-12 * np.abs(go).max()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_static_pivot_check_on_singular_matrix(prec):
+    pm = F.structured_mesh((4, 4), 1)
+    Ke = F.element_matrices(pm, dirichlet=False)  # pure Neumann: singular
+    pr = F.Problem("neumann", pm, Ke, np.zeros((pm.n_nodes, 1)))
+    a, f, vals = _setup(pr, prec, pivot_tol=1e-6)
+    f.factor(vals)
+    st = f.status()
+    assert st["rc"] == 0 and st["n_perturbed"] >= 1 and st["first_front"] == a.n_front - 1
+    a2, f2, vals2 = _setup(pr, prec, pivot_tol=1e-6, pivot_fail=1)
+    f2.factor(vals2)
+    assert f2.status()["rc"] == M.mfsolve.MF_EZERO_PIVOT
+
+
+def test_batched_meshes_with_four_rhs():
+    sizes = [5, 9, 4, 12]
+    probs = F.batched_poisson(sizes, nrhs=4, seed=77)
+    meshes = [M.Mesh(p.mesh.elem_nodes, p.mesh.n_nodes, 2, grid_dims=p.mesh.nel) for p in probs]
+    for prec in ("f64", "f32"):
+        a = M.Analysis(meshes, M.default_options(precision=prec, small_front_max=24))
+        f = M.Factors(a)
+        vals = torch.tensor(np.concatenate([F.to_colmajor(p.Ke) for p in probs]), device=DEV)
+        f.factor(vals)
+        b = np.concatenate([p.b for p in probs], axis=0)  # (N, 4)
+        bt = torch.tensor(np.ascontiguousarray(b.T), device=DEV)
+        x = torch.empty_like(bt)
+        info = f.refine_solve(vals, bt, x, tol=1e-14, maxit=30)
+        assert info["backward_error"] <= 1e-12
+        xg = x.cpu().numpy().T
+        off = 0
+        for p in probs:
+            xo, _ = _oracle(p).solve_refined(p.b)
+            n = p.mesh.n_nodes
+            assert np.linalg.norm(xg[off:off + n] - xo) <= 1e-10 * np.linalg.norm(xo)
+            off += n
+
+
+def test_repeat_factor_is_bitwise_deterministic():
+    pr = F.diffusion_2d(16, 3, seed=41)
+    a, f, vals = _setup(pr, "f32", small_front_max=64)
+    b = torch.tensor(pr.b[:, 0], device=DEV)
+    outs = []
+    for _ in range(2):
+        f.factor(vals)
+        x = b.clone()
+        f.solve(x)
+        outs.append(x.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
