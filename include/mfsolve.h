@@ -52,6 +52,7 @@ typedef struct CUstream_st* mf_stream_t;
 #define MF_ENOCONV (-5)      /* refinement did not reach the tolerance within maxit */
 #define MF_ETIMEOUT (-6)     /* a bounded device wait ran out */
 #define MF_ENOTSUP (-7)      /* option or input form not supported */
+#define MF_ETOOLARGE (-8)    /* problem larger than mf_residual_noalloc's static scratch */
 
 /* Arithmetic of the fronts (factor storage, extend-add, partial LU, Schur
  * update, triangular solves).  Residuals and solution updates are always FP64. */
@@ -189,6 +190,28 @@ int mf_status(mf_factors* f, mf_status_info* out);
  * the pivot columns, L on/below the diagonal, U11 strictly above) and U
  * (k x m, column-major: the pivot rows).  Synchronises.  For tests. */
 int mf_factors_export_front(const mf_factors* f, int32_t front, double* L, double* U);
+
+/* r = b - A x (A given element by element, FP64) without any device
+ * allocation.  The paper has no counterpart: this serves callers that may not
+ * call cudaMalloc or any allocating routine when they evaluate a residual --
+ * code under a memory budget fixed in advance, host frameworks that own
+ * every device allocation through their own pool, real-time loops that
+ * cannot afford an allocation's implicit synchronisation -- and that hold no
+ * mf_factors handle.  Every pointer is the caller's: d_elem_nodes (device,
+ * n_elem * npe global dof ids, as in mf_mesh_desc), d_values (element
+ * matrices, as for mf_factor), d_x, d_b, d_r (n_dof x nrhs).
+ * Work space is one file-scope device array of MF_NOALLOC_MAX_ENTRIES
+ * doubles (8 MiB) that every device loading the library keeps until exit;
+ * n_dof * nrhs beyond it returns MF_ETOOLARGE and launches nothing.  The
+ * first call on a device looks the array's address up (cudaGetSymbolAddress,
+ * that device current) and caches it: make that first call before any stream
+ * capture.  Calls share the array (each clears what it uses first), so calls
+ * that overlap on the GPU race.  Sums use FP64 atomics: results equal
+ * mf_residual's up to rounding order. */
+#define MF_NOALLOC_MAX_ENTRIES (1 << 20)
+int mf_residual_noalloc(int64_t n_dof, int64_t n_elem, int nodes_per_elem, const int64_t* d_elem_nodes,
+                        const double* d_values, const double* d_x, const double* d_b, double* d_r, int nrhs,
+                        mf_stream_t stream);
 
 /* Per-kernel-family accounting for roofline reports.  While enabled, every
  * launch issued by mf_factor / mf_solve / mf_solve_adjoint / mf_refine_solve

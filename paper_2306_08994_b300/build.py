@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmfsolve.so")
-SOURCES = ["analysis.cpp", "capi.cpp", "executor.cu"]
+SOURCES = ["analysis.cpp", "capi.cpp", "executor.cu", "noalloc.cu"]
 HEADERS = ["mf_internal.h", "kernels_factor.cuh", "kernels_solve.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -27,6 +27,7 @@ extern "C" const char* mf_strerror(int code) {
         case MF_ENOCONV: return "refinement did not converge";
         case MF_ETIMEOUT: return "bounded device wait timed out";
         case MF_ENOTSUP: return "not supported";
+        case MF_ETOOLARGE: return "larger than the static scratch of mf_residual_noalloc";
         default: return "unknown error";
     }
 }

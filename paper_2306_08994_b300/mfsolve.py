@@ -21,6 +21,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmfsolve.so")
 
 MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_EZERO_PIVOT, MF_ENOCONV, MF_ETIMEOUT, MF_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
+MF_ETOOLARGE = -8
+MF_NOALLOC_MAX_ENTRIES = 1 << 20
 MF_F64, MF_F32, MF_TF32 = 0, 1, 2
 PRECISIONS = {"f64": MF_F64, "f32": MF_F32, "tf32": MF_TF32}
 
@@ -58,7 +60,7 @@ class mf_refine_info(ctypes.Structure):
 EXPORTS = ["mf_default_options", "mf_strerror", "mf_analyze_mesh", "mf_analyze_batch", "mf_analysis_info",
            "mf_analysis_export", "mf_factors_create", "mf_factor", "mf_solve", "mf_solve_adjoint", "mf_refine_solve",
            "mf_residual", "mf_element_grad", "mf_element_outer", "mf_status", "mf_factors_export_front",
-           "mf_free_factors", "mf_free_analysis", "mf_profile_enable", "mf_profile_read"]
+           "mf_free_factors", "mf_free_analysis", "mf_profile_enable", "mf_profile_read", "mf_residual_noalloc"]
 PROFILE_FAMILIES = ["fused", "assemble", "panel", "trailing_gemm", "schur_gemm", "forward", "backward", "residual",
                     "other"]
 
@@ -85,6 +87,7 @@ def _load():
         "mf_status": ([P, P], I), "mf_factors_export_front": ([P, ctypes.c_int32, P, P], I),
         "mf_free_factors": ([P], None), "mf_free_analysis": ([P], None),
         "mf_profile_enable": ([P, I], I), "mf_profile_read": ([P, P, P, P, P], I),
+        "mf_residual_noalloc": ([I64, I64, I, P, P, P, P, P, I, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
