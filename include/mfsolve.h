@@ -71,6 +71,9 @@ typedef struct {
     int panel_width;      /* pivot block width of the large-front partial LU; 0 = default */
     int use_graph;        /* nonzero: replay factor/solve as captured CUDA graphs */
     int max_nrhs;         /* largest nrhs passed to mf_solve / mf_refine_solve; 0 = 4 */
+    int subtree_levels;   /* bottom classes fused per subtree (one CTA walks classes 1..n of a
+                             subtree with a block barrier between them): n > 0 = at most n
+                             (fewer if a subtree would not fit shared memory); <= 0 = off */
 } mf_options;
 
 typedef struct {

@@ -299,7 +299,7 @@ int mf_symbolic(const mf_mesh_desc* meshes, int count, const mf_options* opt, mf
     a->parent.assign(nt, -1);
     a->dofs.clear();
     a->maps.clear();
-    int64_t fac = 0, cbo = 0, vec = 0;
+    int64_t fac = 0, cbo = 0, vec = 0, inv = 0, ysz = 0;
     std::vector<int32_t> where(n_dof, -1), stamp(n_dof, -1);
     double flops = 0;
     int64_t nnz = 0, scb = 0;
@@ -330,6 +330,16 @@ int mf_symbolic(const mf_mesh_desc* meshes, int count, const mf_options* opt, mf
         cbo += (m - k) * (m - k);
         F.vec_off = vec;
         vec += m - k;
+        if (k >= kInvMinK) {
+            inv = align_up(inv, 32);
+            F.q_off = inv;
+            inv += k * k;
+            F.y_off = ysz;
+            ysz += k;
+        } else {
+            F.q_off = -1;
+            F.y_off = -1;
+        }
         F.dof_off = (int64_t)a->dofs.size();
         const std::vector<int32_t>& fd = fdofs[v];
         a->dofs.insert(a->dofs.end(), fd.begin(), fd.end());
@@ -364,6 +374,8 @@ int mf_symbolic(const mf_mesh_desc* meshes, int count, const mf_options* opt, mf
     a->factor_size = align_up(fac, 32);
     a->cb_size = align_up(std::max<int64_t>(cbo, 1), 32);
     a->vec_size = std::max<int64_t>(vec, 1);
+    a->inv_size = std::max<int64_t>(align_up(inv, 32), 32);
+    a->ys_size = std::max<int64_t>(ysz, 1);
 
     // dof -> (element, local) incidence for the element-by-element residual
     a->node_ptr.assign(n_dof + 1, 0);

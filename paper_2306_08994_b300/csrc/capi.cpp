@@ -15,6 +15,7 @@ extern "C" void mf_default_options(mf_options* o) {
     o->panel_width = 0;
     o->use_graph = 0;
     o->max_nrhs = 4;
+    o->subtree_levels = 0;
 }
 
 extern "C" const char* mf_strerror(int code) {

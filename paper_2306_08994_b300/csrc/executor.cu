@@ -11,11 +11,12 @@
 
 #include "kernels_factor.cuh"
 #include "kernels_solve.cuh"
+#include "kernels_subtree.cuh"
 #include "mf_internal.h"
 
 namespace {
 
-enum LaunchKind { K_FUSED = 0, K_ASM = 1, K_PANEL = 2, K_GEMM = 3 };
+enum LaunchKind { K_FUSED = 0, K_ASM = 1, K_PDIAG = 2, K_GEMM = 3, K_INVDIAG = 4, K_SUBTREE = 5 };
 
 struct Launch {
     int kind;
@@ -27,13 +28,12 @@ struct Launch {
 
 // Solve plan of one class: fronts split by size (see kernels_solve.cuh).
 struct ClassList {
-    int n_small, n_cta, n_split, n_frows, n_brows;
-    int maxm_cta, maxk_split, maxnc_split, maxk_all;
-    int64_t off_small, off_cta, off_split;  // into the solve front list
-    int64_t off_frows, off_brows;           // into the row-task list
+    int n_small, n_cta, n_piv, n_all;
+    int maxm_cta, maxin_inv;
+    int64_t off_small, off_cta;   // into the solve front list
+    int64_t off_piv, off_all;     // into the row-block list (inverse fronts)
 };
 constexpr int kSolveWarpMax = 64;   // m <= this: one warp per front
-constexpr int kSolveSplitCB = 256;  // m - k > this: CB rows in a separate row-parallel launch
 
 #define CUDA_TRY(x)                          \
     do {                                     \
@@ -65,14 +65,125 @@ int upload(T** p, const std::vector<T>& v) {
     return MF_OK;
 }
 
-constexpr int kPanelNB64 = 32;  // FP64 panel width
-constexpr int kPanelNB32 = 64;  // FP32 panel width
+constexpr int kPanelNB64 = 32;  // panel width (pivot block of a step), FP64
+constexpr int kPanelNB32 = 64;  // FP32
 
 __global__ void k_init_status(DevStatus* st) {
     st->n_perturbed = 0ull;
     st->first = ~0ull;
     st->nonfinite = 0;
     st->timeout = 0;
+}
+
+// Subtree fusion plan: disjoint subtrees covering every front of height <= h.
+struct SubtreePlan {
+    int h = 0;
+    std::vector<SubtreeTask> tasks;
+    std::vector<SubtreeEntry> ecb, euv;  // factor (CB pool) and solve (update-vector pool) entries
+    SubtreeLayout lay_f{0, 0}, lay_s{0, 0};
+    size_t smem_f = 0, smem_s = 0;
+    double bytes = 0, flops = 0;
+};
+
+// first-fit offset for `size` elements among live [off, off+size) ranges
+int32_t first_fit(std::vector<std::pair<int32_t, int32_t>> live, int32_t size) {
+    std::sort(live.begin(), live.end());
+    int32_t off = 0;
+    for (const auto& r : live) {
+        if (off + size <= r.first) break;
+        off = std::max(off, r.first + r.second);
+    }
+    return off;
+}
+
+bool subtree_try(const mf_analysis* a, int h, size_t tsize, size_t budget, SubtreePlan& SP) {
+    SP = SubtreePlan{};
+    SP.h = h;
+    const std::vector<FrontDev>& Fr = a->fronts;
+    std::vector<int32_t> roots;
+    for (int32_t f = 0; f < a->n_front; f++)
+        if (Fr[f].cls < h && (a->parent[f] < 0 || Fr[a->parent[f]].cls >= h)) roots.push_back(f);
+    std::stable_sort(roots.begin(), roots.end(), [&](int32_t x, int32_t y) { return Fr[x].cls > Fr[y].cls; });
+    int32_t work_max = 1, pcb_max = 1, puv_max = 1;
+    const double T = (double)tsize;
+    std::vector<int32_t> cboff(a->n_front, -1), uvoff(a->n_front, -1);
+    for (int32_t root : roots) {
+        const int nl = Fr[root].cls + 1;
+        if (nl > kSubMaxLevels) return false;
+        std::vector<std::vector<int32_t>> lev(nl);
+        std::vector<int32_t> stack{root};
+        while (!stack.empty()) {
+            int32_t f = stack.back();
+            stack.pop_back();
+            lev[Fr[f].cls].push_back(f);
+            for (int c = 0; c < Fr[f].nchild; c++) stack.push_back(Fr[f].child[c]);
+        }
+        SubtreeTask t{};
+        t.first = (int32_t)SP.ecb.size();
+        t.n_levels = nl;
+        // live allocations: (off, size) with the level at which they are freed
+        std::vector<std::pair<int32_t, int32_t>> live_cb, live_uv;
+        std::vector<int> free_cb, free_uv;
+        for (int L = 0; L < nl; L++) {
+            std::sort(lev[L].begin(), lev[L].end());
+            for (size_t i = live_cb.size(); i-- > 0;)
+                if (free_cb[i] <= L) {
+                    live_cb.erase(live_cb.begin() + i);
+                    free_cb.erase(free_cb.begin() + i);
+                }
+            for (size_t i = live_uv.size(); i-- > 0;)
+                if (free_uv[i] <= L) {
+                    live_uv.erase(live_uv.begin() + i);
+                    free_uv.erase(free_uv.begin() + i);
+                }
+            t.level_ptr[L] = (int32_t)SP.ecb.size() - t.first;
+            int mmax = 1;
+            for (int32_t f : lev[L]) {
+                const FrontDev& fr = Fr[f];
+                if (fr.m > kSubMaxM) return false;
+                mmax = std::max(mmax, fr.m);
+                SubtreeEntry ec{f, -1, {-1, -1}}, eu{f, -1, {-1, -1}};
+                for (int c = 0; c < fr.nchild; c++) {
+                    ec.child_off[c] = cboff[fr.child[c]];
+                    eu.child_off[c] = uvoff[fr.child[c]];
+                }
+                const int32_t nc = fr.m - fr.k;
+                if (f != root) {
+                    const int fl = Fr[a->parent[f]].cls + 1;
+                    ec.cb_off = first_fit(live_cb, nc * nc);
+                    live_cb.push_back({ec.cb_off, nc * nc});
+                    free_cb.push_back(fl);
+                    pcb_max = std::max(pcb_max, ec.cb_off + nc * nc);
+                    eu.cb_off = first_fit(live_uv, nc);
+                    live_uv.push_back({eu.cb_off, nc});
+                    free_uv.push_back(fl);
+                    puv_max = std::max(puv_max, eu.cb_off + nc);
+                }
+                cboff[f] = ec.cb_off;
+                uvoff[f] = eu.cb_off;
+                SP.ecb.push_back(ec);
+                SP.euv.push_back(eu);
+                // algorithmic work: inputs once, outputs once
+                if (fr.nchild == 0) SP.bytes += 8.0 * a->npe * a->npe;
+                SP.bytes += T * ((double)fr.m * fr.k + (double)fr.k * nc) + (f == root ? T * nc * nc : 0.0);
+                double am = fr.m - fr.k, bm = fr.m - 1;
+                if (fr.k > 0)
+                    SP.flops += (am + bm) * (bm - am + 1) / 2.0 +
+                                2.0 * (bm * (bm + 1) * (2 * bm + 1) / 6.0 - (am - 1) * am * (2 * am - 1) / 6.0);
+            }
+            t.level_mmax[L] = mmax;
+            const int nlf = (int)lev[L].size();
+            const int slots = nlf >= 4 ? std::min(nlf, 8) : 1;
+            work_max = std::max(work_max, slots * (mmax | 1) * mmax);
+        }
+        t.level_ptr[nl] = (int32_t)SP.ecb.size() - t.first;
+        SP.tasks.push_back(t);
+    }
+    SP.lay_f = {work_max, pcb_max};
+    SP.lay_s = {0, puv_max};
+    SP.smem_f = (size_t)(work_max + pcb_max) * tsize + 8 * 2 * kSubMaxM * sizeof(int32_t) + 64;
+    SP.smem_s = (size_t)puv_max * tsize + 16;
+    return SP.smem_f <= budget && SP.smem_s <= budget;
 }
 
 }  // namespace
@@ -98,9 +209,16 @@ struct mf_factors {
     void* d_vec = nullptr;
     int32_t* d_flist = nullptr;
     int32_t* d_slist = nullptr;
-    RowTask* d_rows = nullptr;
+    RowBlock* d_rows = nullptr;
+    InvTask* d_invt = nullptr;
+    void* d_inv = nullptr;
+    void* d_scr = nullptr;
+    void* d_ys = nullptr;
+    int64_t scr_size = 1;
     AsmTile* d_asm = nullptr;
-    PanelTask* d_panel = nullptr;
+    DiagTask* d_panel = nullptr;
+    void* d_pnl = nullptr;
+    int64_t pnl_size = 64 * 64;
     GemmTile* d_gemm = nullptr;
     unsigned int* d_famax = nullptr;
     DevStatus* d_status = nullptr;
@@ -108,6 +226,11 @@ struct mf_factors {
     int norm_blocks = 296;
     bool rowabs_valid = false;
     const double* rowabs_values = nullptr;
+    // subtree fusion of the bottom classes
+    SubtreePlan sub;
+    SubtreeTask* d_sub_tasks = nullptr;
+    SubtreeEntry* d_sub_ecb = nullptr;
+    SubtreeEntry* d_sub_euv = nullptr;
     // plan
     std::vector<Launch> plan;
     std::vector<ClassList> classes;
@@ -128,7 +251,7 @@ struct mf_factors {
 };
 
 enum Family { FAM_FUSED = 0, FAM_ASM = 1, FAM_PANEL = 2, FAM_TRAIL = 3, FAM_SCHUR = 4, FAM_FWD = 5, FAM_BWD = 6,
-              FAM_RESID = 7, FAM_OTHER = 8 };
+              FAM_RESID = 7, FAM_OTHER = 8, FAM_INV = 2 /* accounted with the panel LU */ };
 
 // Bracket one launch: returns a slot index (or -1 when profiling is off).
 static int prof_begin(mf_factors* F, cudaStream_t s, int fam, double bytes, double flops, int kernels = 1) {
@@ -158,7 +281,7 @@ static void free_factors(mf_factors* f) {
     if (!f) return;
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
-                    f->d_vec, f->d_flist, f->d_slist, f->d_rows, f->d_asm, f->d_panel, f->d_gemm, f->d_famax, f->d_status,
+                    f->d_vec, f->d_flist, f->d_slist, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_famax, f->d_status,
                     f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -174,9 +297,10 @@ static size_t fused_smem(int maxm) {
 static int build_plan(mf_factors* F) {
     const mf_analysis* a = F->a;
     std::vector<int32_t> flist, slist;
-    std::vector<RowTask> rows;
+    std::vector<RowBlock> rows;
+    std::vector<InvTask> invt;
     std::vector<AsmTile> asmt;
-    std::vector<PanelTask> pan;
+    std::vector<DiagTask> pan;
     std::vector<GemmTile> gem;
     const int bounds64[] = {16, 32, 48, 64, 96, 128, 160};
     const int bounds32[] = {16, 32, 48, 64, 96, 128, 160, 192, 224};
@@ -205,12 +329,29 @@ static int build_plan(mf_factors* F) {
                 GemmTile t{};
                 t.a_off = a_off; t.b_off = b_off; t.c_off = c_off;
                 t.lda = lda; t.ldb = ldb; t.ldc = ldc;
-                t.M = M; t.N = N; t.K = K; t.i0 = i0; t.j0 = j0; t.c_in_cb = c_in_cb;
+                t.M = M; t.N = N; t.K = K; t.i0 = i0; t.j0 = j0;
+                t.a_ar = AR_FAC; t.b_ar = AR_FAC; t.c_ar = c_in_cb ? AR_CB : AR_FAC; t.op = 0;
                 gem.push_back(t);
             }
     };
+    // subtree fusion of the bottom classes
+    {
+        int want = F->opt.subtree_levels;
+        int hmax = want <= 0 ? 0 : std::min(a->n_cls, want);
+        hmax = std::min(hmax, kSubMaxLevels);
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const size_t budget = (size_t)std::min(optin > 0 ? optin : 100000, 200 * 1024);
+        F->sub = SubtreePlan{};
+        for (int h = hmax; h >= 2; h--)
+            if (subtree_try(a, h, F->tsize, budget, F->sub)) break;
+        if (F->sub.tasks.empty() || F->sub.h < 2) F->sub = SubtreePlan{};
+        if (F->sub.h >= 2) push({K_SUBTREE, 0, (int)F->sub.tasks.size(), 0, 0}, FAM_FUSED, F->sub.bytes, F->sub.flops);
+    }
     for (int c = 0; c < a->n_cls; c++) {
         const int32_t f0 = a->cls_ptr[c], f1 = a->cls_ptr[c + 1];
+        const bool fused_by_subtree = c < F->sub.h;
         // solve list: all fronts of the class, largest first
         std::vector<int32_t> all;
         int maxm_all = 1;
@@ -221,13 +362,13 @@ static int build_plan(mf_factors* F) {
         std::stable_sort(all.begin(), all.end(), [&](int32_t x, int32_t y) { return a->fronts[x].m > a->fronts[y].m; });
         {
             ClassList C{};
-            std::vector<int32_t> sm, ct, sp;
+            std::vector<int32_t> sm, ct, iv;
             for (int32_t f : all) {
+                if (fused_by_subtree) break;
                 const FrontDev& fr = a->fronts[f];
-                if (fr.m <= kSolveWarpMax) sm.push_back(f);
-                else if (fr.m - fr.k <= kSolveSplitCB) ct.push_back(f);
-                else sp.push_back(f);
-                C.maxk_all = std::max(C.maxk_all, fr.k);
+                if (fr.q_off >= 0) iv.push_back(f);
+                else if (fr.m <= kSolveWarpMax) sm.push_back(f);
+                else ct.push_back(f);
             }
             C.n_small = (int)sm.size();
             C.off_small = (int64_t)slist.size();
@@ -236,23 +377,20 @@ static int build_plan(mf_factors* F) {
             C.off_cta = (int64_t)slist.size();
             slist.insert(slist.end(), ct.begin(), ct.end());
             for (int32_t f : ct) C.maxm_cta = std::max(C.maxm_cta, a->fronts[f].m);
-            C.n_split = (int)sp.size();
-            C.off_split = (int64_t)slist.size();
-            slist.insert(slist.end(), sp.begin(), sp.end());
-            C.off_frows = (int64_t)rows.size();
-            for (int32_t f : sp) {
+            C.off_piv = (int64_t)rows.size();
+            for (int32_t f : iv) {
                 const FrontDev& fr = a->fronts[f];
-                C.maxk_split = std::max(C.maxk_split, fr.k);
-                C.maxnc_split = std::max(C.maxnc_split, fr.m - fr.k);
-                for (int i = fr.k; i < fr.m; i += 128) rows.push_back({f, i, std::min(fr.m, i + 128), 0});
+                C.maxin_inv = std::max(C.maxin_inv, std::max(fr.k, fr.m - fr.k));
+                for (int i = 0; i < fr.k; i += 32) rows.push_back({f, i, std::min(fr.k, i + 32), 0});
             }
-            C.n_frows = (int)(rows.size() - C.off_frows);
-            C.off_brows = (int64_t)rows.size();
-            for (int32_t f : sp) {
+            C.n_piv = (int)(rows.size() - C.off_piv);
+            C.off_all = (int64_t)rows.size();
+            for (int32_t f : iv) {
                 const FrontDev& fr = a->fronts[f];
-                for (int i = 0; i < fr.k; i += 128) rows.push_back({f, i, std::min(fr.k, i + 128), 0});
+                for (int i = 0; i < fr.k; i += 32) rows.push_back({f, i, std::min(fr.k, i + 32), 0});
+                for (int i = fr.k; i < fr.m; i += 32) rows.push_back({f, i, std::min(fr.m, i + 32), 0});
             }
-            C.n_brows = (int)(rows.size() - C.off_brows);
+            C.n_all = (int)(rows.size() - C.off_all);
             F->classes.push_back(C);
         }
         {
@@ -278,6 +416,7 @@ static int build_plan(mf_factors* F) {
         }
         slist.insert(slist.end(), all.begin(), all.end());
 
+        if (fused_by_subtree) continue;
         // fused buckets (largest first inside each launch)
         int lo = 0;
         for (int bi = 0; bi < nbounds && lo < F->small_max; bi++) {
@@ -326,29 +465,69 @@ static int build_plan(mf_factors* F) {
         }
         int maxk = 0;
         for (int32_t f : big) maxk = std::max(maxk, a->fronts[f].k);
-        std::vector<PanelTask> diag;
+        F->pnl_size = std::max<int64_t>(F->pnl_size, (int64_t)big.size() * 64 * 64);
+        auto tile_raw = [&](int8_t aar, int64_t ao, int lda, int8_t am, int8_t bar, int64_t bo, int ldb, int8_t bm,
+                            int8_t car, int64_t co, int ldc, int M, int N, int K, int8_t op) {
+            for (int j0 = 0; j0 < N; j0 += 64)
+                for (int i0 = 0; i0 < M; i0 += 64) {
+                    GemmTile t{};
+                    t.a_off = ao; t.b_off = bo; t.c_off = co;
+                    t.lda = lda; t.ldb = ldb; t.ldc = ldc;
+                    t.M = M; t.N = N; t.K = K; t.i0 = i0; t.j0 = j0;
+                    t.a_ar = aar; t.b_ar = bar; t.c_ar = car; t.op = op; t.a_mask = am; t.b_mask = bm;
+                    gem.push_back(t);
+                }
+            gf += 2.0 * M * N * K;
+            gb += T * ((double)M * K + (double)K * N + 2.0 * M * N);
+        };
         for (int kb = 0; kb < maxk; kb += nb) {
+            // (A) diagonal blocks: factor + invert, one warp per front
             int64_t poff = (int64_t)pan.size();
-            int64_t goff = (int64_t)gem.size();
             double pb = 0, pf = 0;
+            for (size_t bi = 0; bi < big.size(); bi++) {
+                const FrontDev& fr = a->fronts[big[bi]];
+                if (kb >= fr.k) continue;
+                const int w = std::min(nb, fr.k - kb);
+                pan.push_back({big[bi], kb, w, 0, (int64_t)bi * 64 * 64});
+                pb += 3.0 * T * w * w;
+                pf += 2.0 * w * w * w;
+            }
+            push({K_PDIAG, c, (int)(pan.size() - poff), 0, poff}, FAM_PANEL, pb, pf);
+            // (B) panel products in place: L21 = A21 U_D^-1, U12 = L_D^-1 A12
+            int64_t goff = (int64_t)gem.size();
+            gb = gf = 0;
+            for (size_t bi = 0; bi < big.size(); bi++) {
+                const FrontDev& fr = a->fronts[big[bi]];
+                if (kb >= fr.k) continue;
+                const int m = fr.m, k = fr.k, w = std::min(nb, k - kb), r0 = kb + w;
+                const int64_t slot = (int64_t)bi * 64 * 64;
+                if (m - r0 > 0) {
+                    const int64_t ab = fr.P_off + r0 + (int64_t)kb * m;
+                    tile_raw(AR_FAC, ab, m, 0, AR_PNL, slot, 64, 2, AR_FAC, ab, m, m - r0, w, w, 1);
+                }
+                if (k - r0 > 0) {
+                    const int64_t bb = fr.P_off + kb + (int64_t)r0 * m;
+                    tile_raw(AR_PNL, slot, 64, 1, AR_FAC, bb, m, 0, AR_FAC, bb, m, w, k - r0, w, 1);
+                }
+                if (m - k > 0) {
+                    const int64_t bb = fr.R_off + kb;
+                    tile_raw(AR_PNL, slot, 64, 1, AR_FAC, bb, k, 0, AR_FAC, bb, k, w, m - k, w, 1);
+                }
+            }
+            if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_PANEL, gb, gf);
+            // (C) trailing updates restricted to the pivot rows/columns
+            goff = (int64_t)gem.size();
             gb = gf = 0;
             for (int32_t f : big) {
                 const FrontDev& fr = a->fronts[f];
                 if (kb >= fr.k) continue;
                 const int m = fr.m, k = fr.k, w = std::min(nb, k - kb), r0 = kb + w;
-                pb += 2.0 * T * ((double)w * w + 2.0 * (double)(m - r0) * w);
-                pf += 2.0 * w * w * w / 3.0 + 2.0 * (double)(m - r0) * w * w;
-                diag.push_back({f, kb, w, 2, 0, 0, 0, 0});
-                for (int i = r0; i < m; i += 256) pan.push_back({f, kb, w, 0, i, std::min(m, i + 256), 0, 0});
-                for (int j = r0; j < m; j += 256) pan.push_back({f, kb, w, 1, j, std::min(m, j + 256), 0, 0});
-                // trailing updates restricted to the pivot rows/columns
                 if (m - r0 > 0 && k - r0 > 0)
                     gemm_tiles(fr.P_off + r0 + (int64_t)kb * m, m, fr.P_off + kb + (int64_t)r0 * m, m,
                                fr.P_off + r0 + (int64_t)r0 * m, m, m - r0, k - r0, w, 0);
                 if (k - r0 > 0 && m - k > 0)
                     gemm_tiles(fr.P_off + r0 + (int64_t)kb * m, m, fr.R_off + kb, k, fr.R_off + r0, k, k - r0, m - k, w, 0);
             }
-            if (pan.size() > (size_t)poff) push({K_PANEL, c, (int)(pan.size() - poff), 0, poff}, FAM_PANEL, pb, pf);
             if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_TRAIL, gb, gf);
         }
         // Schur update S -= L21 U12 (Sec. 2.2)
@@ -360,12 +539,77 @@ static int build_plan(mf_factors* F) {
             if (m - k > 0 && k > 0) gemm_tiles(fr.P_off + k, m, fr.R_off, k, fr.S_off, m - k, m - k, m - k, k, 1);
         }
         if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_SCHUR, gb, gf);
-        if (!diag.empty()) {
-            int64_t doff = (int64_t)pan.size();
-            double db = 0;
-            for (const PanelTask& t : diag) db += 2.0 * T * t.w * t.w;
-            pan.insert(pan.end(), diag.begin(), diag.end());
-            push({K_PANEL, c, (int)diag.size(), 0, doff}, FAM_PANEL, db, 0.0);
+    }
+    // explicit pivot-block inverses of the large fronts, after the last class
+    {
+        std::vector<int32_t> ivf;
+        int maxk = 0;
+        for (int32_t f = 0; f < a->n_front; f++)
+            if (a->fronts[f].q_off >= 0) {
+                ivf.push_back(f);
+                maxk = std::max(maxk, a->fronts[f].k);
+            }
+        if (!ivf.empty()) {
+            int64_t off = (int64_t)invt.size();
+            double by = 0, fl = 0;
+            for (int32_t f : ivf) {
+                const FrontDev& fr = a->fronts[f];
+                for (int kb = 0; kb < fr.k; kb += 64) {
+                    int w = std::min(64, fr.k - kb);
+                    invt.push_back({f, kb, w, 0, fr.q_off});
+                    by += 2.0 * T * w * w;
+                    fl += 2.0 * w * w * w / 3.0;
+                }
+            }
+            push({K_INVDIAG, a->n_cls - 1, (int)(invt.size() - off), 0, off}, FAM_INV, by, fl);
+            for (int S = 64; S < maxk; S *= 2) {
+                int64_t scr = 0;
+                int64_t g1 = (int64_t)gem.size();
+                gb = gf = 0;
+                std::vector<GemmTile> ph2;
+                for (int32_t f : ivf) {
+                    const FrontDev& fr = a->fronts[f];
+                    const int m = fr.m, k = fr.k;
+                    for (int a0 = 0; a0 + S < k; a0 += 2 * S) {
+                        const int n2 = std::min(a0 + 2 * S, k) - (a0 + S);
+                        const int64_t t1 = scr, t2 = scr + (int64_t)n2 * S;
+                        scr += 2 * (int64_t)n2 * S;
+                        auto tiles = [&](std::vector<GemmTile>& out, int8_t aar, int64_t ao, int lda, int8_t am, int8_t bar,
+                                         int64_t bo, int ldb, int8_t bm, int64_t co, int ldc, int M, int N, int K, int8_t op) {
+                            for (int j0 = 0; j0 < N; j0 += 64)
+                                for (int i0 = 0; i0 < M; i0 += 64) {
+                                    GemmTile t{};
+                                    t.a_off = ao; t.b_off = bo; t.c_off = co;
+                                    t.lda = lda; t.ldb = ldb; t.ldc = ldc;
+                                    t.M = M; t.N = N; t.K = K; t.i0 = i0; t.j0 = j0;
+                                    t.a_ar = aar; t.b_ar = bar; t.c_ar = op == 2 ? AR_INV : AR_SCR; t.op = op;
+                                    t.a_mask = am; t.b_mask = bm;
+                                    out.push_back(t);
+                                }
+                            gf += 2.0 * M * N * K;
+                            gb += T * ((double)M * K + (double)K * N + (double)M * N);
+                        };
+                        const int64_t q = fr.q_off;
+                        // T1 = L21 X1 ; T2 = U12 Y2
+                        tiles(gem, AR_FAC, fr.P_off + (a0 + S) + (int64_t)a0 * m, m, 0, AR_INV, q + a0 + (int64_t)a0 * k, k, 1,
+                              t1, n2, n2, S, S, 1);
+                        tiles(gem, AR_FAC, fr.P_off + a0 + (int64_t)(a0 + S) * m, m, 0, AR_INV,
+                              q + (a0 + S) + (int64_t)(a0 + S) * k, k, 2, t2, S, S, n2, n2, 1);
+                        // Q21 = -X2 T1 ; Q12 = -Y1 T2
+                        tiles(ph2, AR_INV, q + (a0 + S) + (int64_t)(a0 + S) * k, k, 1, AR_SCR, t1, n2, 0,
+                              q + (a0 + S) + (int64_t)a0 * k, k, n2, S, n2, 2);
+                        tiles(ph2, AR_INV, q + a0 + (int64_t)a0 * k, k, 2, AR_SCR, t2, S, 0, q + a0 + (int64_t)(a0 + S) * k, k,
+                              S, n2, S, 2);
+                    }
+                }
+                F->scr_size = std::max(F->scr_size, scr);
+                if (gem.size() > (size_t)g1) {
+                    push({K_GEMM, a->n_cls - 1, (int)(gem.size() - g1), 0, g1}, FAM_INV, gb / 2, gf / 2);
+                    int64_t g2 = (int64_t)gem.size();
+                    gem.insert(gem.end(), ph2.begin(), ph2.end());
+                    push({K_GEMM, a->n_cls - 1, (int)(gem.size() - g2), 0, g2}, FAM_INV, gb / 2, gf / 2);
+                }
+            }
         }
     }
     {
@@ -377,6 +621,10 @@ static int build_plan(mf_factors* F) {
     if ((rc = upload(&F->d_flist, flist))) return rc;
     if ((rc = upload(&F->d_slist, slist))) return rc;
     if ((rc = upload(&F->d_rows, rows))) return rc;
+    if ((rc = upload(&F->d_invt, invt))) return rc;
+    if ((rc = upload(&F->d_sub_tasks, F->sub.tasks))) return rc;
+    if ((rc = upload(&F->d_sub_ecb, F->sub.ecb))) return rc;
+    if ((rc = upload(&F->d_sub_euv, F->sub.euv))) return rc;
     if ((rc = upload(&F->d_asm, asmt))) return rc;
     if ((rc = upload(&F->d_panel, pan))) return rc;
     if ((rc = upload(&F->d_gemm, gem))) return rc;
@@ -394,10 +642,18 @@ static int set_smem_limits() {
     CUDA_TRY(cudaFuncSetAttribute(k_fwd_cta<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_bwd_cta<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_bwd_cta<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_fwd_rows<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_fwd_rows<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_bwd_rows<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_bwd_rows<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_inv_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_subtree_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_subtree_fwd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_subtree_fwd<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, false, PH_FWD1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, false, PH_FWD2>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, false, PH_BWD1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, false, PH_BWD2>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, true, PH_FWD1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, true, PH_FWD2>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, true, PH_BWD1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, true, PH_BWD2>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     return MF_OK;
 }
 
@@ -452,6 +708,10 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     TRY(dev_alloc(&F->d_part, (size_t)F->norm_blocks * 6 * F->max_nrhs));
     TRY(dev_alloc(&F->d_norms, (size_t)6 * F->max_nrhs));
     TRY(build_plan(F));
+    TRY(dev_alloc((char**)&F->d_inv, (size_t)a->inv_size * F->tsize));
+    TRY(dev_alloc((char**)&F->d_scr, (size_t)F->scr_size * F->tsize));
+    TRY(dev_alloc((char**)&F->d_pnl, (size_t)F->pnl_size * F->tsize));
+    TRY(dev_alloc((char**)&F->d_ys, (size_t)a->ys_size * F->max_nrhs * F->tsize));
 #undef TRY
     *out = F;
     return MF_OK;
@@ -483,16 +743,24 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
             case K_ASM:
                 k_assemble_large<T><<<L.count, 256, 0, s>>>(F->d_fronts, F->d_asm + L.off, F->d_maps, fac, cb, F->d_famax);
                 break;
-            case K_PANEL:
-                if constexpr (sizeof(T) == 8)
-                    k_panel<T, kPanelNB64><<<L.count, 256, 0, s>>>(F->d_fronts, F->d_panel + L.off, fac, F->d_famax,
-                                                                   F->tol_rel, F->d_status);
-                else
-                    k_panel<T, kPanelNB32><<<L.count, 256, 0, s>>>(F->d_fronts, F->d_panel + L.off, fac, F->d_famax,
-                                                                   F->tol_rel, F->d_status);
+            case K_PDIAG: {
+                constexpr int NB = sizeof(T) == 8 ? kPanelNB64 : kPanelNB32;
+                k_panel_diag<T, NB><<<L.count, (NB / 4) * (NB / 4), 0, s>>>(F->d_fronts, F->d_panel + L.off, fac,
+                                                                            (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
                 break;
-            case K_GEMM:
-                k_gemm_sub<T, sizeof(T) == 8 ? 8 : 16><<<L.count, 256, 0, s>>>(F->d_gemm + L.off, fac, fac, cb);
+            }
+            case K_GEMM: {
+                Arenas<T> ar{{fac, cb, (T*)F->d_inv, (T*)F->d_scr, (T*)F->d_pnl}};
+                k_gemm<T, sizeof(T) == 8 ? 8 : 16><<<L.count, 256, 0, s>>>(F->d_gemm + L.off, ar);
+                break;
+            }
+            case K_SUBTREE:
+                k_subtree_factor<T><<<L.count, 256, F->sub.smem_f, s>>>(F->d_fronts, F->d_sub_tasks, F->d_sub_ecb, F->d_maps,
+                                                                       d_values, a->npe, fac, cb, F->sub.lay_f, F->tol_rel,
+                                                                       F->d_status);
+                break;
+            case K_INVDIAG:
+                k_inv_diag<T><<<L.count, 128, 2 * 64 * 65 * sizeof(T), s>>>(F->d_fronts, F->d_invt + L.off, fac, (T*)F->d_inv);
                 break;
         }
         prof_end(F, s, slot);
@@ -516,14 +784,31 @@ template <typename T>
 static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStream_t s) {
     const mf_analysis* a = F->a;
     const T* fac = (const T*)F->d_fac;
+    const T* inv = (const T*)F->d_inv;
     T* vec = (T*)F->d_vec;
+    T* ys = (T*)F->d_ys;
     const FrontDev* fr = F->d_fronts;
     const int32_t* L = F->d_slist;
-    const int64_t n = a->n_dof, vs = a->vec_size;
+    const int64_t n = a->n_dof, vs = a->vec_size, yss = a->ys_size;
     const size_t dgs = 32 * 33 * sizeof(T);
+    if (F->sub.h >= 2) {
+        int slot = prof_begin(F, s, FAM_FWD, 0, 0);
+        dim3 g((unsigned)F->sub.tasks.size(), nrhs);
+        if (!trans)
+            k_subtree_fwd<T, false><<<g, 256, F->sub.smem_s, s>>>(fr, F->d_sub_tasks, F->d_sub_euv, fac, F->d_dofs, F->d_maps,
+                                                               vec, vs, F->sub.lay_s, d_x, n);
+        else
+            k_subtree_fwd<T, true><<<g, 256, F->sub.smem_s, s>>>(fr, F->d_sub_tasks, F->d_sub_euv, fac, F->d_dofs, F->d_maps,
+                                                              vec, vs, F->sub.lay_s, d_x, n);
+        prof_end(F, s, slot);
+        CUDA_TRY(cudaGetLastError());
+    }
+#define INV_LAUNCH(TR, PH, CNT, OFF)                                                                               \
+    k_inv_gemv<T, TR, PH><<<dim3(CNT, nrhs), 256, (8 * 32 + C.maxin_inv) * sizeof(T), s>>>(                      \
+        fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_maps, vec, vs, ys, yss, d_x, n)
     for (int c = 0; c < a->n_cls; c++) {
         const ClassList& C = F->classes[c];
-        int nk = (C.n_small > 0) + (C.n_cta > 0) + (C.n_split > 0) + (C.n_frows > 0);
+        int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0);
         int slot = prof_begin(F, s, FAM_FWD, F->fwd_bytes[c] * nrhs, F->fwd_flops[c] * nrhs, nk);
         if (C.n_small) {
             dim3 g((C.n_small + 7) / 8, nrhs);
@@ -536,36 +821,30 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
             if (!trans) k_fwd_cta<T, false><<<g, 256, sm, s>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n);
             else k_fwd_cta<T, true><<<g, 256, sm, s>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n);
         }
-        if (C.n_split) {
-            dim3 g(C.n_split, nrhs);
-            size_t sm = dgs + (size_t)C.maxk_split * sizeof(T);
-            if (!trans) k_fwd_cta<T, false><<<g, 256, sm, s>>>(fr, L + C.off_split, 0, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n);
-            else k_fwd_cta<T, true><<<g, 256, sm, s>>>(fr, L + C.off_split, 0, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n);
-        }
-        if (C.n_frows) {
-            dim3 g(C.n_frows, nrhs);
-            size_t sm = (size_t)C.maxk_split * sizeof(T);
-            if (!trans) k_fwd_rows<T, false><<<g, 128, sm, s>>>(fr, F->d_rows + C.off_frows, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n);
-            else k_fwd_rows<T, true><<<g, 128, sm, s>>>(fr, F->d_rows + C.off_frows, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n);
+        if (C.n_piv) {
+            if (!trans) {
+                INV_LAUNCH(false, PH_FWD1, C.n_piv, C.off_piv);
+                INV_LAUNCH(false, PH_FWD2, C.n_all, C.off_all);
+            } else {
+                INV_LAUNCH(true, PH_FWD1, C.n_piv, C.off_piv);
+                INV_LAUNCH(true, PH_FWD2, C.n_all, C.off_all);
+            }
         }
         prof_end(F, s, slot);
         CUDA_TRY(cudaGetLastError());
     }
     for (int c = a->n_cls - 1; c >= 0; c--) {
         const ClassList& C = F->classes[c];
-        int nk = (C.n_small > 0) + (C.n_cta > 0) + (C.n_split > 0) + (C.n_brows > 0);
+        int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0);
         int slot = prof_begin(F, s, FAM_BWD, F->bwd_bytes[c] * nrhs, F->bwd_flops[c] * nrhs, nk);
-        if (C.n_brows) {
-            dim3 g(C.n_brows, nrhs);
-            size_t sm = (size_t)C.maxnc_split * sizeof(T);
-            if (!trans) k_bwd_rows<T, false><<<g, 128, sm, s>>>(fr, F->d_rows + C.off_brows, fac, F->d_dofs, d_x, n);
-            else k_bwd_rows<T, true><<<g, 128, sm, s>>>(fr, F->d_rows + C.off_brows, fac, F->d_dofs, d_x, n);
-        }
-        if (C.n_split) {
-            dim3 g(C.n_split, nrhs);
-            size_t sm = dgs + (size_t)C.maxk_split * sizeof(T);
-            if (!trans) k_bwd_cta<T, false><<<g, 256, sm, s>>>(fr, L + C.off_split, 1, fac, F->d_dofs, d_x, n);
-            else k_bwd_cta<T, true><<<g, 256, sm, s>>>(fr, L + C.off_split, 1, fac, F->d_dofs, d_x, n);
+        if (C.n_piv) {
+            if (!trans) {
+                INV_LAUNCH(false, PH_BWD1, C.n_piv, C.off_piv);
+                INV_LAUNCH(false, PH_BWD2, C.n_piv, C.off_piv);
+            } else {
+                INV_LAUNCH(true, PH_BWD1, C.n_piv, C.off_piv);
+                INV_LAUNCH(true, PH_BWD2, C.n_piv, C.off_piv);
+            }
         }
         if (C.n_cta) {
             dim3 g(C.n_cta, nrhs);
@@ -578,6 +857,17 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
             if (!trans) k_bwd_warp<T, false><<<g, 256, 0, s>>>(fr, L + C.off_small, C.n_small, fac, F->d_dofs, d_x, n);
             else k_bwd_warp<T, true><<<g, 256, 0, s>>>(fr, L + C.off_small, C.n_small, fac, F->d_dofs, d_x, n);
         }
+        prof_end(F, s, slot);
+        CUDA_TRY(cudaGetLastError());
+    }
+#undef INV_LAUNCH
+    if (F->sub.h >= 2) {
+        int slot = prof_begin(F, s, FAM_BWD, 0, 0);
+        dim3 g((unsigned)F->sub.tasks.size(), nrhs);
+        if (!trans)
+            k_subtree_bwd<T, false><<<g, 256, 0, s>>>(fr, F->d_sub_tasks, F->d_sub_euv, fac, F->d_dofs, d_x, n);
+        else
+            k_subtree_bwd<T, true><<<g, 256, 0, s>>>(fr, F->d_sub_tasks, F->d_sub_euv, fac, F->d_dofs, d_x, n);
         prof_end(F, s, slot);
         CUDA_TRY(cudaGetLastError());
     }

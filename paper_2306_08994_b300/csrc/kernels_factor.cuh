@@ -16,6 +16,19 @@ struct DevStatus {
     int timeout;
 };
 
+// Asynchronous global -> shared copies of single elements (cp.async): many
+// copies stay in flight per thread, unlike a load-then-store loop whose every
+// shared store waits for its own global load.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gmem_src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if constexpr (sizeof(T) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename T>
 __device__ __forceinline__ T tiny_pivot() { return sizeof(T) == 8 ? (T)1e-300 : (T)1e-37f; }
 
@@ -212,129 +225,205 @@ __global__ void __launch_bounds__(256) k_assemble_large(const FrontDev* __restri
     }
 }
 
-// Panel step of the blocked partial LU (large fronts).  With the pivot block
-// [kb, kb+w):
-//   D = F[kb:kb+w, kb:kb+w] = L11 U11     (unblocked Table 2 tasks, in smem)
-//   L21 = F[kb+w:m, kb:kb+w] U11^-1       (role 0: a chunk of rows)
-//   U12 = L11^-1 F[kb:kb+w, kb+w:m]       (role 1: a chunk of columns, in P or R)
-// Every CTA factors D itself from P (w^3/3 flops) instead of waiting for
-// another CTA, so D must stay unfactored in P while the step runs: the
-// factored diagonal blocks are written back by role 2 tasks in one launch
-// after the class's panel loop (nothing else reads or writes them in
-// between: the trailing updates start at row/column kb+w).
-struct PanelTask {
-    int32_t front, kb, w, role, r0, r1, pad0, pad1;
+// Panel step of the blocked partial LU (large fronts), pivot block
+// [kb, kb+w), w <= 64:
+//   k_panel_diag: D = F[kb:kb+w, kb:kb+w] = L_D U_D by the Table 2 tasks
+//     (division of the pivot row, then multiplication/subtraction on the
+//     trailing block) with the static pivot check, written back to P; and
+//     the inverses L_D^-1, U_D^-1 packed into the front's panel slot.
+//   then one batched k_gemm launch, in place:
+//     L21 = F[kb+w:m, kb:kb+w] U_D^-1,   U12 = L_D^-1 F[kb:kb+w, kb+w:m]
+//   (each output tile spans the whole w-wide side, so it reads all of its
+//   input before writing), then the trailing update k_gemm.
+// One CTA per front.
+struct DiagTask {
+    int32_t front, kb, w, pad;
+    int64_t slot;  // panel-slot offset (64 x 64, column-major, ld 64)
 };
 
+// One CTA per pivot block, NB/4 x NB/4 threads, each owning a 4x4 register
+// tile (rows 4*tr.., columns 4*tc..).  Per pivot the owners of the pivot
+// column and row publish them to double-buffered shared memory, one barrier,
+// then every thread applies the rank-1 update to its own tile (masked to
+// the trailing block).  The block is padded with the identity beyond w.
+// The two inverse sweeps run the same way, interleaved: L_D^-1 top-down
+// (row p of the inverse scaled by 1/L_pp, rows below lose L_ip * row p) and
+// U_D^-1 bottom-up (rows above lose U_iq * row q).
 template <typename T, int NB>
-__device__ __forceinline__ void factor_diag_block(T (*D)[NB + 1], int w, T thr, bool record, int32_t front, int kb,
-                                                  DevStatus* st) {
-    for (int p = 0; p < w; p++) {
-        const T piv = checked_pivot(D[p][p], thr, record && threadIdx.x == 0, front, kb + p, st);
-        __syncthreads();
-        const int n = w - p - 1;
-        if (threadIdx.x == 0) D[p][p] = piv;
-        for (int j = p + 1 + (int)threadIdx.x; j < w; j += blockDim.x) D[p][j] = D[p][j] / piv;
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-            const int i = p + 1 + idx % n, j = p + 1 + idx / n;
-            D[i][j] -= D[i][p] * D[p][j];
-        }
-        __syncthreads();
-    }
-}
-
-template <typename T, int NB>
-__global__ void __launch_bounds__(256) k_panel(const FrontDev* __restrict__ fronts, const PanelTask* __restrict__ tasks,
-                                               T* __restrict__ fac, const unsigned int* __restrict__ famax, double tol_rel,
-                                               DevStatus* st) {
-    __shared__ T D[NB][NB + 1];
-    const PanelTask t = tasks[blockIdx.x];
+__global__ void __launch_bounds__((NB / 4) * (NB / 4)) k_panel_diag(const FrontDev* __restrict__ fronts,
+                                                                    const DiagTask* __restrict__ tasks, T* __restrict__ fac,
+                                                                    T* __restrict__ slots, const unsigned int* __restrict__ famax,
+                                                                    double tol_rel, DevStatus* st) {
+    constexpr int TPD = NB / 4;
+    __shared__ T Ds[NB][NB + 1];
+    __shared__ T colb[2][NB], rowb[2][NB], colc[2][NB], rowc[2][NB];
+    const DiagTask t = tasks[blockIdx.x];
     const FrontDev fr = fronts[t.front];
-    const int m = fr.m, k = fr.k, kb = t.kb, w = t.w;
+    const int m = fr.m, kb = t.kb, w = t.w;
+    const int tid = threadIdx.x, tr = tid / TPD, tc = tid % TPD;
     T* P = fac + fr.P_off;
-    T* R = fac + fr.R_off;
-    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-        int i = idx % w, j = idx / w;
-        D[i][j] = P[(kb + i) + (int64_t)(kb + j) * m];
-    }
+    for (int j = tid / 32; j < NB; j += TPD * TPD / 32)
+        for (int i = tid % 32; i < NB; i += 32) {
+            if (i < w && j < w) cp_async_elem(&Ds[i][j], P + (kb + i) + (int64_t)(kb + j) * m);
+            else Ds[i][j] = (i == j) ? T(1) : T(0);
+        }
+    cp_async_wait_all();
     __syncthreads();
+    T a[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) a[r][c] = Ds[4 * tr + r][4 * tc + c];
     const T amax = (T)__uint_as_float(famax[t.front]);
     const T thr = (T)tol_rel * amax > T(0) ? (T)tol_rel * amax : tiny_pivot<T>();
-    factor_diag_block<T, NB>(D, w, thr, t.role == 2, t.front, kb, st);
-    if (t.role == 2) {
-        for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-            int i = idx % w, j = idx / w;
-            P[(kb + i) + (int64_t)(kb + j) * m] = D[i][j];
-        }
-        return;
-    }
-    if (t.role == 0) {
-        const int i = t.r0 + threadIdx.x;
-        if (i >= t.r1) return;
-        T l[NB];
+    // ---- LU (Table 2 tasks: divide the pivot row, update the trailing block)
+    for (int pb = 0; pb < NB; pb += 4) {
 #pragma unroll
-        for (int p = 0; p < NB; p++)
-            if (p < w) l[p] = P[i + (int64_t)(kb + p) * m];
+        for (int pp = 0; pp < 4; pp++) {
+            const int p = pb + pp, par = p & 1;
+            if (tc == pb / 4) {
 #pragma unroll
-        for (int p = 0; p < NB; p++) {
-            if (p < w) {
-                T a = l[p];
+                for (int r = 0; r < 4; r++) colb[par][4 * tr + r] = a[r][pp];
+            }
+            if (tr == pb / 4) {
 #pragma unroll
-                for (int q = 0; q < NB; q++)
-                    if (q < p) a -= l[q] * D[q][p];
-                l[p] = a;
+                for (int c = 0; c < 4; c++) rowb[par][4 * tc + c] = a[pp][c];
+            }
+            __syncthreads();
+            T piv = rowb[par][p];
+            if (p < w) piv = checked_pivot(piv, thr, tid == 0, t.front, kb + p, st);
+            const T rinv = T(1) / piv;
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const int i = 4 * tr + r;
+                const T li = colb[par][i];
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const int j = 4 * tc + c;
+                    const T uj = rowb[par][j] * rinv;
+                    if (i > p && j > p) a[r][c] -= li * uj;
+                    else if (i == p && j > p) a[r][c] = uj;
+                    else if (i == p && j == p) a[r][c] = piv;
+                }
             }
         }
+    }
+    // factored block back to P (through shared memory, coalesced)
+    __syncthreads();
 #pragma unroll
-        for (int p = 0; p < NB; p++)
-            if (p < w) P[i + (int64_t)(kb + p) * m] = l[p];
-    } else {
-        const int j = t.r0 + threadIdx.x;
-        if (j >= t.r1) return;
-        T* col = (j < k) ? (P + kb + (int64_t)j * m) : (R + kb + (int64_t)(j - k) * k);
-        T u[NB];
+    for (int r = 0; r < 4; r++)
 #pragma unroll
-        for (int p = 0; p < NB; p++)
-            if (p < w) u[p] = col[p];
+        for (int c = 0; c < 4; c++) Ds[4 * tr + r][4 * tc + c] = a[r][c];
+    __syncthreads();
+    for (int j = tid / 32; j < w; j += TPD * TPD / 32)
+        for (int i = tid % 32; i < w; i += 32) P[(kb + i) + (int64_t)(kb + j) * m] = Ds[i][j];
+    // ---- inverses: x = L_D^-1 (lower incl. diagonal), y = U_D^-1 (strict upper)
+    T x[4][4], y[4][4];
 #pragma unroll
-        for (int p = 0; p < NB; p++) {
-            if (p < w) {
-                T a = u[p];
+    for (int r = 0; r < 4; r++)
 #pragma unroll
-                for (int q = 0; q < NB; q++)
-                    if (q < p) a -= D[p][q] * u[q];
-                u[p] = a / D[p][p];
+        for (int c = 0; c < 4; c++) {
+            const bool d = (4 * tr + r) == (4 * tc + c);
+            x[r][c] = d ? T(1) : T(0);
+            y[r][c] = d ? T(1) : T(0);
+        }
+    for (int sb = 0; sb < NB; sb += 4) {
+#pragma unroll
+        for (int ss = 0; ss < 4; ss++) {
+            const int p = sb + ss, par = p & 1;
+            const int q = NB - 1 - p;  // q's tile column/row index: (NB-1-sb-ss)/4 = TPD-1-sb/4, offset 3-ss
+            const int qb = TPD - 1 - sb / 4, qq = 3 - ss;
+            if (tc == sb / 4) {
+#pragma unroll
+                for (int r = 0; r < 4; r++) colb[par][4 * tr + r] = a[r][ss];  // L column p
+            }
+            if (tr == sb / 4) {
+#pragma unroll
+                for (int c = 0; c < 4; c++) rowb[par][4 * tc + c] = x[ss][c];  // inverse row p (unscaled)
+            }
+            if (tc == qb) {
+#pragma unroll
+                for (int r = 0; r < 4; r++) colc[par][4 * tr + r] = a[r][qq];  // U column q
+            }
+            if (tr == qb) {
+#pragma unroll
+                for (int c = 0; c < 4; c++) rowc[par][4 * tc + c] = y[qq][c];  // U^-1 row q (final)
+            }
+            __syncthreads();
+            const T rinv = T(1) / colb[par][p];
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const int i = 4 * tr + r;
+                const T li = colb[par][i], ui = colc[par][i];
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const int j = 4 * tc + c;
+                    const T xp = rowb[par][j] * rinv;
+                    if (j <= p) {
+                        if (i > p) x[r][c] -= li * xp;
+                        else if (i == p) x[r][c] = xp;
+                    }
+                    if (i < q && j >= q) y[r][c] -= ui * (j == q ? T(1) : rowc[par][j]);
+                }
             }
         }
-#pragma unroll
-        for (int p = 0; p < NB; p++)
-            if (p < w) col[p] = u[p];
     }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const int i = 4 * tr + r, j = 4 * tc + c;
+            Ds[i][j] = j <= i ? x[r][c] : y[r][c];
+        }
+    __syncthreads();
+    T* Z = slots + t.slot;
+    for (int j = tid / 32; j < w; j += TPD * TPD / 32)
+        for (int i = tid % 32; i < w; i += 32) Z[i + j * 64] = Ds[i][j];
 }
 
 // ---------------------------------------------------------------------------
-// Batched SIMT GEMM C -= A B (column-major, explicit leading dimensions),
-// 64x64 tiles, 256 threads, 4x4 outputs per thread.  Used for the trailing
-// updates of the panel loop and for the Schur update S -= L21 U12 (Sec. 2.2).
+// Batched SIMT GEMM over column-major operands with explicit leading
+// dimensions, 64x64 tiles, 256 threads, 4x4 outputs per thread.
+//   op 0: C -= A B      (trailing updates, Schur update S -= L21 U12, Sec. 2.2)
+//   op 1: C  = A B      op 2: C = -A B   (triangular inversion levels)
+// Operands live in one of the arenas (factor, CB, inverse, scratch, panel
+// slots).  A tile may write the operand it reads (panel step) when it spans
+// that operand's whole K extent: all loads precede the epilogue's stores.  A
+// triangular operand is read through a mask: 1 = lower (entries above the
+// diagonal read as 0), 2 = unit upper (below the diagonal 0, diagonal 1),
+// relative to the operand's own origin.
+enum { AR_FAC = 0, AR_CB = 1, AR_INV = 2, AR_SCR = 3, AR_PNL = 4 };
+
 struct GemmTile {
-    int64_t a_off, b_off, c_off;  // element offsets: A, B in the factor arena; C in factor or CB arena
+    int64_t a_off, b_off, c_off;  // element offsets into the arenas named below
     int32_t lda, ldb, ldc;
     int32_t M, N, K;
     int32_t i0, j0;
-    int32_t c_in_cb;
-    int32_t pad;
+    int8_t a_ar, b_ar, c_ar, op;
+    int8_t a_mask, b_mask, pad0, pad1;
 };
 
+template <typename T>
+struct Arenas {
+    T* a[5];
+};
+
+template <typename T>
+__device__ __forceinline__ T masked(T v, int mask, int r, int c) {
+    if (mask == 1) return r >= c ? v : T(0);
+    if (mask == 2) return r < c ? v : (r == c ? T(1) : T(0));
+    return v;
+}
+
 template <typename T, int BK>
-__global__ void __launch_bounds__(256) k_gemm_sub(const GemmTile* __restrict__ tiles, const T* __restrict__ fac,
-                                                  T* __restrict__ facw, T* __restrict__ cbs) {
+__global__ void __launch_bounds__(256) k_gemm(const GemmTile* __restrict__ tiles, Arenas<T> ar) {
     __shared__ T As[2][BK][64 + 1];
     __shared__ T Bs[2][BK][64 + 1];
     const GemmTile t = tiles[blockIdx.x];
-    const T* A = fac + t.a_off;
-    const T* B = fac + t.b_off;
-    T* C = (t.c_in_cb ? cbs : facw) + t.c_off;
+    const T* A = ar.a[t.a_ar] + t.a_off;
+    const T* B = ar.a[t.b_ar] + t.b_off;
+    T* C = ar.a[t.c_ar] + t.c_off;
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     T acc[4][4];
@@ -343,23 +432,25 @@ __global__ void __launch_bounds__(256) k_gemm_sub(const GemmTile* __restrict__ t
 #pragma unroll
         for (int c = 0; c < 4; c++) acc[r][c] = T(0);
 
-    constexpr int ALOADS = 64 * BK / 256;  // A tile elements per thread
-    T ra[ALOADS], rb[ALOADS];
+    constexpr int LOADS = 64 * BK / 256;
+    T ra[LOADS], rb[LOADS];
     auto load = [&](int kk0) {
 #pragma unroll
-        for (int r = 0; r < ALOADS; r++) {
+        for (int r = 0; r < LOADS; r++) {
             int idx = tid + 256 * r;
             int i = idx & 63, kk = idx >> 6;
             int gi = t.i0 + i, gk = kk0 + kk;
-            ra[r] = (gi < t.M && gk < t.K) ? A[gi + (int64_t)gk * t.lda] : T(0);
+            T va = (gi < t.M && gk < t.K) ? A[gi + (int64_t)gk * t.lda] : T(0);
+            ra[r] = (gi < t.M && gk < t.K) ? masked(va, t.a_mask, gi, gk) : T(0);
             int kb = idx % BK, j = idx / BK;
             int gj = t.j0 + j, gk2 = kk0 + kb;
-            rb[r] = (gj < t.N && gk2 < t.K) ? B[gk2 + (int64_t)gj * t.ldb] : T(0);
+            T vb = (gj < t.N && gk2 < t.K) ? B[gk2 + (int64_t)gj * t.ldb] : T(0);
+            rb[r] = (gj < t.N && gk2 < t.K) ? masked(vb, t.b_mask, gk2, gj) : T(0);
         }
     };
     auto store = [&](int buf) {
 #pragma unroll
-        for (int r = 0; r < ALOADS; r++) {
+        for (int r = 0; r < LOADS; r++) {
             int idx = tid + 256 * r;
             As[buf][idx >> 6][idx & 63] = ra[r];
             Bs[buf][idx % BK][idx / BK] = rb[r];
@@ -394,7 +485,65 @@ __global__ void __launch_bounds__(256) k_gemm_sub(const GemmTile* __restrict__ t
 #pragma unroll
         for (int r = 0; r < 4; r++) {
             int gi = t.i0 + tx + 16 * r;
-            if (gi < t.M) C[gi + (int64_t)gj * t.ldc] -= acc[r][c];
+            if (gi >= t.M) continue;
+            T* dst = C + gi + (int64_t)gj * t.ldc;
+            if (t.op == 0) *dst -= acc[r][c];
+            else if (t.op == 1) *dst = acc[r][c];
+            else *dst = -acc[r][c];
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Explicit inverses of the pivot blocks of large fronts, used by the solve
+// (the triangular solves become wide products).  The inverse block Q (k x k,
+// column-major, in the inverse arena) holds L11^-1 on and below the diagonal
+// and the strictly upper part of U11^-1 (unit diagonal implied), packed like
+// P's own L11\U11 block.  k_inv_diag inverts the 64x64 diagonal blocks; the
+// off-diagonal blocks follow by block doubling,
+//   [L1 0; L21 L2]^-1 = [X1 0; -X2 L21 X1  X2],
+//   [U1 U12; 0 U2]^-1 = [Y1 -Y1 U12 Y2; 0 Y2],
+// with two k_gemm launches per doubling level.
+struct InvTask {
+    int32_t front, kb, w, pad;
+    int64_t q_off;  // inverse-arena offset of the front's Q
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_inv_diag(const FrontDev* __restrict__ fronts, const InvTask* __restrict__ tasks,
+                                                  const T* __restrict__ fac, T* __restrict__ inv) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T(*A)[65] = reinterpret_cast<T(*)[65]>(smem_raw);       // 64 x 65
+    T(*X)[65] = reinterpret_cast<T(*)[65]>(smem_raw) + 64;  // 64 x 65
+    const InvTask t = tasks[blockIdx.x];
+    const FrontDev fr = fronts[t.front];
+    const int m = fr.m, k = fr.k, kb = t.kb, w = t.w;
+    const T* P = fac + fr.P_off;
+    for (int j = threadIdx.x >> 5; j < w; j += 4)
+        for (int i = threadIdx.x & 31; i < w; i += 32) cp_async_elem(&A[i][j], P + (kb + i) + (int64_t)(kb + j) * m);
+    cp_async_wait_all();
+    __syncthreads();
+    const int c = threadIdx.x & 63;
+    if (c < w) {
+        if (threadIdx.x < 64) {
+            // column c of L^-1: forward substitution on L x = e_c
+            X[c][c] = T(1) / A[c][c];
+            for (int i = c + 1; i < w; i++) {
+                T sacc = T(0);
+                for (int q = c; q < i; q++) sacc += A[i][q] * X[q][c];
+                X[i][c] = -sacc / A[i][i];
+            }
+        } else {
+            // column c of U^-1 (unit upper): back substitution on U y = e_c
+            for (int i = c - 1; i >= 0; i--) {
+                T sacc = A[i][c];
+                for (int q = i + 1; q < c; q++) sacc += A[i][q] * X[q][c];
+                X[i][c] = -sacc;
+            }
+        }
+    }
+    __syncthreads();
+    T* Q = inv + t.q_off;
+    for (int j = threadIdx.x >> 5; j < w; j += 4)
+        for (int i = threadIdx.x & 31; i < w; i += 32) Q[(kb + i) + (int64_t)(kb + j) * k] = X[i][j];
 }

@@ -149,11 +149,10 @@ __global__ void __launch_bounds__(256) k_bwd_warp(const FrontDev* __restrict__ f
     if (i1 < k) xr[fd[i1]] = (double)v1;
 }
 
-// Larger fronts: one CTA per front.  The pivot block is processed in
-// 32-wide blocks; each 32x32 diagonal block is staged in shared memory by all
-// threads, solved by warp 0, then applied to the later rows.  With
-// `rows_all` the CTA also produces the update vector (all m rows); otherwise
-// it stops at row k and k_fwd_rows does the contribution-block rows.
+// Mid-size fronts (m > 64, k < kInvMinK): one CTA per front.  The pivot block
+// is processed in 32-wide blocks; each 32x32 diagonal block is staged in
+// shared memory by all threads, solved by warp 0, then applied to the later
+// rows, including the contribution-block rows (update vector).
 template <typename T, bool TRANS>
 __global__ void __launch_bounds__(256) k_fwd_cta(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                  int rows_all, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
@@ -175,12 +174,20 @@ __global__ void __launch_bounds__(256) k_fwd_cta(const FrontDev* __restrict__ fr
     const int lane = threadIdx.x & 31;
     for (int pb = 0; pb < k; pb += 32) {
         const int wb = min(32, k - pb);
-        for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-            const int i = idx & 31, p = idx >> 5;  // row pb+i, pivot pb+p
-            T v = T(0);
-            if (i < wb && p < wb) v = (i > p) ? fcoef<T, TRANS>(P, R, m, k, pb + i, pb + p)
-                                              : (i == p ? fdiag<T, TRANS>(P, m, pb + p) : T(0));
-            Dg[i * 33 + p] = v;
+        {
+            T v[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int idx = threadIdx.x + 256 * q, i = idx & 31, p = idx >> 5;  // row pb+i, pivot pb+p
+                v[q] = T(0);
+                if (i < wb && p < wb) v[q] = (i > p) ? fcoef<T, TRANS>(P, R, m, k, pb + i, pb + p)
+                                                     : (i == p ? fdiag<T, TRANS>(P, m, pb + p) : T(0));
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int idx = threadIdx.x + 256 * q;
+                Dg[(idx & 31) * 33 + (idx >> 5)] = v[q];
+            }
         }
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -207,78 +214,8 @@ __global__ void __launch_bounds__(256) k_fwd_cta(const FrontDev* __restrict__ fr
     }
 }
 
-// Contribution-block rows of large fronts: u_i = w_i - sum_p coef(i,p) y_p for
-// a chunk of 128 rows, y read back from x at the front's pivots.
-struct RowTask {
-    int32_t front, r0, r1, pad;
-};
-
-template <typename T, bool TRANS>
-__global__ void __launch_bounds__(128) k_fwd_rows(const FrontDev* __restrict__ fronts, const RowTask* __restrict__ tasks,
-                                                  const T* __restrict__ fac, const int32_t* __restrict__ dofs,
-                                                  const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
-                                                  double* __restrict__ x, int64_t n_dof) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* y = reinterpret_cast<T*>(smem_raw);
-    const RowTask t = tasks[blockIdx.x];
-    const int r = blockIdx.y;
-    const FrontDev fr = fronts[t.front];
-    const int m = fr.m, k = fr.k;
-    const int32_t* fd = dofs + fr.dof_off;
-    double* xr = x + (int64_t)r * n_dof;
-    T* vr = vecs + (int64_t)r * vec_size;
-    const T* P = fac + fr.P_off;
-    const T* R = fac + fr.R_off;
-    for (int p = threadIdx.x; p < k; p += blockDim.x) y[p] = (T)xr[fd[p]];
-    __syncthreads();
-    const int i = t.r0 + threadIdx.x;
-    if (i >= t.r1) return;
-    T acc = gather_rhs<T>(fr, fronts, fd, maps, vr, xr, i);
-    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-    int p = 0;
-    for (; p + 4 <= k; p += 4) {
-        a0 += fcoef<T, TRANS>(P, R, m, k, i, p) * y[p];
-        a1 += fcoef<T, TRANS>(P, R, m, k, i, p + 1) * y[p + 1];
-        a2 += fcoef<T, TRANS>(P, R, m, k, i, p + 2) * y[p + 2];
-        a3 += fcoef<T, TRANS>(P, R, m, k, i, p + 3) * y[p + 3];
-    }
-    for (; p < k; p++) a0 += fcoef<T, TRANS>(P, R, m, k, i, p) * y[p];
-    vr[fr.vec_off + (i - k)] = acc - ((a0 + a1) + (a2 + a3));
-}
-
-// Backward, large fronts split: pivot rows i of a chunk: z_i = y_i - sum_{j>=k} coef(i,j) x_j.
-template <typename T, bool TRANS>
-__global__ void __launch_bounds__(128) k_bwd_rows(const FrontDev* __restrict__ fronts, const RowTask* __restrict__ tasks,
-                                                  const T* __restrict__ fac, const int32_t* __restrict__ dofs,
-                                                  double* __restrict__ x, int64_t n_dof) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* xc = reinterpret_cast<T*>(smem_raw);
-    const RowTask t = tasks[blockIdx.x];
-    const int r = blockIdx.y;
-    const FrontDev fr = fronts[t.front];
-    const int m = fr.m, k = fr.k, nc = m - k;
-    const int32_t* fd = dofs + fr.dof_off;
-    double* xr = x + (int64_t)r * n_dof;
-    const T* P = fac + fr.P_off;
-    const T* R = fac + fr.R_off;
-    for (int j = threadIdx.x; j < nc; j += blockDim.x) xc[j] = (T)xr[fd[k + j]];
-    __syncthreads();
-    const int i = t.r0 + threadIdx.x;
-    if (i >= t.r1) return;
-    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-    int j = 0;
-    for (; j + 4 <= nc; j += 4) {
-        a0 += bcoef<T, TRANS>(P, R, m, k, i, k + j) * xc[j];
-        a1 += bcoef<T, TRANS>(P, R, m, k, i, k + j + 1) * xc[j + 1];
-        a2 += bcoef<T, TRANS>(P, R, m, k, i, k + j + 2) * xc[j + 2];
-        a3 += bcoef<T, TRANS>(P, R, m, k, i, k + j + 3) * xc[j + 3];
-    }
-    for (; j < nc; j++) a0 += bcoef<T, TRANS>(P, R, m, k, i, k + j) * xc[j];
-    xr[fd[i]] = (double)((T)xr[fd[i]] - ((a0 + a1) + (a2 + a3)));
-}
-
-// Backward, one CTA per large front.  With `cb_done` the CB part was already
-// subtracted by k_bwd_rows; otherwise it is done here first.
+// Backward, one CTA per mid-size front: the CB part of the pivot rows first,
+// then the unit (or, transposed, L11^T) triangle in 32-wide blocks.
 template <typename T, bool TRANS>
 __global__ void __launch_bounds__(256) k_bwd_cta(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                  int cb_done, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
@@ -307,12 +244,20 @@ __global__ void __launch_bounds__(256) k_bwd_cta(const FrontDev* __restrict__ fr
     const int lane = threadIdx.x & 31;
     for (int pe = k; pe > 0; pe -= 32) {
         const int pb = max(0, pe - 32), wb = pe - pb;
-        for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
-            const int i = idx & 31, j = idx >> 5;  // row pb+i, unknown pb+j
-            T c = T(0);
-            if (i < wb && j < wb) c = (i < j) ? bcoef<T, TRANS>(P, R, m, k, pb + i, pb + j)
-                                              : (i == j ? bdiag<T, TRANS>(P, m, pb + j) : T(0));
-            Dg[i * 33 + j] = c;
+        {
+            T v[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int idx = threadIdx.x + 256 * q, i = idx & 31, j = idx >> 5;  // row pb+i, unknown pb+j
+                v[q] = T(0);
+                if (i < wb && j < wb) v[q] = (i < j) ? bcoef<T, TRANS>(P, R, m, k, pb + i, pb + j)
+                                                     : (i == j ? bdiag<T, TRANS>(P, m, pb + j) : T(0));
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int idx = threadIdx.x + 256 * q;
+                Dg[(idx & 31) * 33 + (idx >> 5)] = v[q];
+            }
         }
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -334,6 +279,114 @@ __global__ void __launch_bounds__(256) k_bwd_cta(const FrontDev* __restrict__ fr
         __syncthreads();
     }
     for (int i = threadIdx.x; i < k; i += blockDim.x) xr[fd[i]] = (double)v[i];
+}
+
+// ---------------------------------------------------------------------------
+// Fronts with explicit pivot-block inverses (k >= kInvMinK): each sweep is
+// two wide products per front, 32 rows per CTA.
+//   FWD1: y = L11^-1 w1            (TRANS: U11^-T w1)      -> pivot scratch
+//   FWD2: rows < k: y -> x at the pivots; rows >= k: u = w2 - L21 y (TRANS: U12^T y)
+//   BWD1: z = y - U12 x_CB         (TRANS: L21^T x_CB)     -> pivot scratch
+//   BWD2: x1 = U11^-1 z            (TRANS: L11^-T z)       -> x at the pivots
+// !TRANS operands are read column by column (lane = row, the 8 warps split the
+// columns, partial sums added in warp order); TRANS operands row by row
+// (warp = row, lanes split the columns, shuffle tree).  Both orders are fixed,
+// so results are deterministic.
+enum { PH_FWD1 = 0, PH_FWD2 = 1, PH_BWD1 = 2, PH_BWD2 = 3 };
+
+struct RowBlock {
+    int32_t front, r0, r1, pad;
+};
+
+template <typename T, bool TRANS, int PH>
+__device__ __forceinline__ T inv_coef(const T* __restrict__ P, const T* __restrict__ R, const T* __restrict__ Q, int m,
+                                      int k, int i, int j) {
+    if (PH == PH_FWD1) return TRANS ? (j == i ? T(1) : Q[j + (int64_t)i * k]) : Q[i + (int64_t)j * k];
+    if (PH == PH_FWD2) return TRANS ? R[j + (int64_t)(i - k) * k] : P[i + (int64_t)j * m];
+    if (PH == PH_BWD1) return TRANS ? P[(k + j) + (int64_t)i * m] : R[i + (int64_t)j * k];
+    return TRANS ? Q[j + (int64_t)i * k] : (j == i ? T(1) : Q[i + (int64_t)j * k]);
+}
+
+template <typename T, bool TRANS, int PH>
+__global__ void __launch_bounds__(256) k_inv_gemv(const FrontDev* __restrict__ fronts, const RowBlock* __restrict__ tasks,
+                                                  const T* __restrict__ fac, const T* __restrict__ inv,
+                                                  const int32_t* __restrict__ dofs, const int32_t* __restrict__ maps,
+                                                  T* __restrict__ vecs, int64_t vec_size, T* __restrict__ ys,
+                                                  int64_t ys_size, double* __restrict__ x, int64_t n_dof) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* red = reinterpret_cast<T*>(smem_raw);  // 8 x 32
+    T* vin = red + 8 * 32;
+    const RowBlock t = tasks[blockIdx.x];
+    const int r = blockIdx.y;
+    const FrontDev fr = fronts[t.front];
+    const int m = fr.m, k = fr.k;
+    const int32_t* fd = dofs + fr.dof_off;
+    double* xr = x + (int64_t)r * n_dof;
+    T* vr = vecs + (int64_t)r * vec_size;
+    T* yr = ys + (int64_t)r * ys_size + fr.y_off;
+    const T* P = fac + fr.P_off;
+    const T* R = fac + fr.R_off;
+    const T* Q = inv + (fr.q_off >= 0 ? fr.q_off : 0);
+    if (PH == PH_FWD2 && t.r0 < k) {
+        for (int i = t.r0 + threadIdx.x; i < t.r1; i += blockDim.x) xr[fd[i]] = (double)yr[i];
+        return;
+    }
+    const int nin = (PH == PH_BWD1) ? m - k : k;
+    for (int j = threadIdx.x; j < nin; j += blockDim.x) {
+        T v;
+        if (PH == PH_FWD1) v = gather_rhs<T>(fr, fronts, fd, maps, vr, xr, j);
+        else if (PH == PH_BWD1) v = (T)xr[fd[k + j]];
+        else v = yr[j];
+        vin[j] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // column range of row i
+    auto lo = [&](int i) { return PH == PH_BWD2 ? i : 0; };
+    auto hi = [&](int i) { return PH == PH_FWD1 ? i + 1 : nin; };
+    auto finish = [&](int i, T acc) {
+        if (PH == PH_FWD1) yr[i] = acc;
+        else if (PH == PH_FWD2) vr[fr.vec_off + (i - k)] = gather_rhs<T>(fr, fronts, fd, maps, vr, xr, i) - acc;
+        else if (PH == PH_BWD1) yr[i] = (T)xr[fd[i]] - acc;
+        else xr[fd[i]] = (double)acc;
+    };
+    if (!TRANS) {
+        const int i = t.r0 + lane;
+        const bool valid = i < t.r1;
+        const int c0 = PH == PH_BWD2 ? t.r0 : 0;
+        const int c1 = PH == PH_FWD1 ? min(t.r1, k) : nin;
+        T a0 = T(0), a1 = T(0);
+        int j = c0 + warp;
+        for (; j + 8 < c1; j += 16) {
+            if (valid && j >= lo(i) && j < hi(i)) a0 += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j) * vin[j];
+            if (valid && j + 8 >= lo(i) && j + 8 < hi(i)) a1 += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j + 8) * vin[j + 8];
+        }
+        for (; j < c1; j += 8)
+            if (valid && j >= lo(i) && j < hi(i)) a0 += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j) * vin[j];
+        red[warp * 32 + lane] = a0 + a1;
+        __syncthreads();
+        if (warp == 0 && valid) {
+            T acc = T(0);
+            for (int w = 0; w < 8; w++) acc += red[w * 32 + lane];
+            finish(i, acc);
+        }
+    } else {
+        for (int q = 0; q < 4; q++) {
+            const int i = t.r0 + warp * 4 + q;
+            if (i >= t.r1) break;
+            T a0 = T(0), a1 = T(0);
+            const int jl = lo(i), jh = hi(i);
+            int j = jl + lane;
+            for (; j + 32 < jh; j += 64) {
+                a0 += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j) * vin[j];
+                a1 += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j + 32) * vin[j + 32];
+            }
+            if (j < jh) a0 += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j) * vin[j];
+            T acc = a0 + a1;
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) finish(i, acc);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

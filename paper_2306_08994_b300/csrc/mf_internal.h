@@ -34,7 +34,14 @@ struct FrontDev {
                       // front row, -1 if the row is not in that child's CB); leaf: m int32
                       // (element-local node of each front row)
     int64_t dof_off;  // into dofs: m global dof ids (pivots ascending, then CB ascending)
+    int64_t q_off;    // fronts with k >= kInvMinK: inverse-arena offset of Q (k x k: L11^-1 on and
+                      // below the diagonal, strict upper part of U11^-1); otherwise -1
+    int64_t y_off;    // same fronts: offset of their k pivot values in the solve's pivot scratch
 };
+
+// Fronts with at least this many pivots get explicit pivot-block inverses,
+// so their triangular solves run as wide products.
+constexpr int kInvMinK = 64;
 
 struct mf_analysis {
     mf_options opt;
@@ -49,7 +56,7 @@ struct mf_analysis {
     std::vector<int64_t> elem_nodes;  // n_elem * npe (batch: global dof ids)
     std::vector<int64_t> node_ptr;    // n_dof + 1: incidence CSR (dof -> e*npe + a)
     std::vector<int64_t> node_inc;
-    int64_t factor_size = 0, cb_size = 0, vec_size = 0;
+    int64_t factor_size = 0, cb_size = 0, vec_size = 0, inv_size = 0, ys_size = 0;
     mf_info info{};
 };
 

@@ -30,7 +30,7 @@ PRECISIONS = {"f64": MF_F64, "f32": MF_F32, "tf32": MF_TF32}
 class mf_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("pivot_tol", ctypes.c_double), ("pivot_fail", ctypes.c_int),
                 ("small_front_max", ctypes.c_int), ("panel_width", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("max_nrhs", ctypes.c_int)]
+                ("max_nrhs", ctypes.c_int), ("subtree_levels", ctypes.c_int)]
 
 
 class mf_mesh_desc(ctypes.Structure):

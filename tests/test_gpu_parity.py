@@ -62,6 +62,9 @@ CASES = {
     "q3_10_mixed_buckets": (lambda: F.diffusion_2d(10, 3, seed=32), {"small_front_max": 48}),
     "q1_3d_6_large_path": (lambda: F.diffusion_3d_q1(6, seed=33), {"small_front_max": 24}),
     "q1_1x1": (lambda: F.poisson_2d_q1(1), {}),
+    "q3_12_no_subtree": (lambda: F.diffusion_2d(12, 3, seed=34), {"subtree_levels": -1, "small_front_max": 32}),
+    "q1_9_subtree3_unbalanced": (lambda: F.poisson_2d_q1(9), {"subtree_levels": 3}),
+    "q1_3d_5_subtree": (lambda: F.diffusion_3d_q1(5, seed=35), {"subtree_levels": 4, "small_front_max": 24}),
 }
 
 
