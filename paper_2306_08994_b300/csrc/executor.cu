@@ -12,11 +12,12 @@
 #include "kernels_factor.cuh"
 #include "kernels_solve.cuh"
 #include "kernels_subtree.cuh"
+#include "kernels_tc.cuh"
 #include "mf_internal.h"
 
 namespace {
 
-enum LaunchKind { K_FUSED = 0, K_ASM = 1, K_PDIAG = 2, K_GEMM = 3, K_INVDIAG = 4, K_SUBTREE = 5 };
+enum LaunchKind { K_FUSED = 0, K_ASM = 1, K_PDIAG = 2, K_GEMM = 3, K_INVDIAG = 4, K_SUBTREE = 5, K_GEMMTC = 6 };
 
 struct Launch {
     int kind;
@@ -220,6 +221,7 @@ struct mf_factors {
     void* d_pnl = nullptr;
     int64_t pnl_size = 64 * 64;
     GemmTile* d_gemm = nullptr;
+    GemmTile* d_gtc = nullptr;  // tensor-core (128 x 128) Schur tiles
     unsigned int* d_famax = nullptr;
     DevStatus* d_status = nullptr;
     double *d_r = nullptr, *d_d = nullptr, *d_Y = nullptr, *d_rowabs = nullptr, *d_part = nullptr, *d_norms = nullptr;
@@ -281,7 +283,7 @@ static void free_factors(mf_factors* f) {
     if (!f) return;
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
-                    f->d_vec, f->d_flist, f->d_slist, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_famax, f->d_status,
+                    f->d_vec, f->d_flist, f->d_slist, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_famax, f->d_status,
                     f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -301,7 +303,7 @@ static int build_plan(mf_factors* F) {
     std::vector<InvTask> invt;
     std::vector<AsmTile> asmt;
     std::vector<DiagTask> pan;
-    std::vector<GemmTile> gem;
+    std::vector<GemmTile> gem, gtc;
     const int bounds64[] = {16, 32, 48, 64, 96, 128, 160};
     const int bounds32[] = {16, 32, 48, 64, 96, 128, 160, 192, 224};
     const int* bounds = F->prec == MF_F64 ? bounds64 : bounds32;
@@ -530,15 +532,33 @@ static int build_plan(mf_factors* F) {
             }
             if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_TRAIL, gb, gf);
         }
-        // Schur update S -= L21 U12 (Sec. 2.2)
+        // Schur update S -= L21 U12 (Sec. 2.2): tensor cores (MF_TF32) for large blocks, SIMT otherwise
         int64_t goff = (int64_t)gem.size();
+        int64_t toff = (int64_t)gtc.size();
+        double tb = 0, tf = 0;
         gb = gf = 0;
         for (int32_t f : big) {
             const FrontDev& fr = a->fronts[f];
-            const int m = fr.m, k = fr.k;
-            if (m - k > 0 && k > 0) gemm_tiles(fr.P_off + k, m, fr.R_off, k, fr.S_off, m - k, m - k, m - k, k, 1);
+            const int m = fr.m, k = fr.k, nc = m - k;
+            if (nc <= 0 || k <= 0) continue;
+            if (F->prec == MF_TF32 && nc >= 96 && k >= 16) {
+                for (int j0 = 0; j0 < nc; j0 += tc::kTileN)
+                    for (int i0 = 0; i0 < nc; i0 += tc::kTileM) {
+                        GemmTile t{};
+                        t.a_off = fr.P_off + k; t.b_off = fr.R_off; t.c_off = fr.S_off;
+                        t.lda = m; t.ldb = k; t.ldc = nc;
+                        t.M = nc; t.N = nc; t.K = k; t.i0 = i0; t.j0 = j0;
+                        t.a_ar = AR_FAC; t.b_ar = AR_FAC; t.c_ar = AR_CB; t.op = 0;
+                        gtc.push_back(t);
+                    }
+                tf += 2.0 * nc * nc * k;
+                tb += T * (2.0 * nc * k + 2.0 * nc * nc);
+            } else {
+                gemm_tiles(fr.P_off + k, m, fr.R_off, k, fr.S_off, nc, nc, nc, k, 1);
+            }
         }
         if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_SCHUR, gb, gf);
+        if (gtc.size() > (size_t)toff) push({K_GEMMTC, c, (int)(gtc.size() - toff), 0, toff}, FAM_SCHUR, tb, tf);
     }
     // explicit pivot-block inverses of the large fronts, after the last class
     {
@@ -628,6 +648,7 @@ static int build_plan(mf_factors* F) {
     if ((rc = upload(&F->d_asm, asmt))) return rc;
     if ((rc = upload(&F->d_panel, pan))) return rc;
     if ((rc = upload(&F->d_gemm, gem))) return rc;
+    if ((rc = upload(&F->d_gtc, gtc))) return rc;
     return MF_OK;
 }
 
@@ -644,6 +665,7 @@ static int set_smem_limits() {
     CUDA_TRY(cudaFuncSetAttribute(k_bwd_cta<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_inv_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_subtree_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
     CUDA_TRY(cudaFuncSetAttribute(k_subtree_fwd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_subtree_fwd<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, false, PH_FWD1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
@@ -758,6 +780,12 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
                 k_subtree_factor<T><<<L.count, 256, F->sub.smem_f, s>>>(F->d_fronts, F->d_sub_tasks, F->d_sub_ecb, F->d_maps,
                                                                        d_values, a->npe, fac, cb, F->sub.lay_f, F->tol_rel,
                                                                        F->d_status);
+                break;
+            case K_GEMMTC:
+                if constexpr (sizeof(T) == 4) {
+                    Arenas<float> ar{{fac, cb, (float*)F->d_inv, (float*)F->d_scr, (float*)F->d_pnl}};
+                    k_gemm_tc<<<L.count, 128, tc::kSmemBytes, s>>>(F->d_gtc + L.off, ar, F->d_status);
+                }
                 break;
             case K_INVDIAG:
                 k_inv_diag<T><<<L.count, 128, 2 * 64 * 65 * sizeof(T), s>>>(F->d_fronts, F->d_invt + L.off, fac, (T*)F->d_inv);

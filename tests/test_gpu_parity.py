@@ -118,6 +118,33 @@ def test_solution_matches_oracle(case, prec):
         assert e1 <= 1e-10, e1
 
 
+@pytest.mark.parametrize("n", [40, 56])
+def test_tensor_core_schur_path(n):
+    """MF_TF32: Schur updates of large fronts on tcgen05 (3-pass TF32).  Factors agree
+    with the FP32 SIMT path to within the FP32 path's own distance from FP64, and the
+    refined solution meets the same bars."""
+    pr = F.diffusion_2d(n, 3, seed=36)
+    factors = {}
+    for prec in ("f64", "f32", "tf32"):
+        a, f, vals = _setup(pr, prec, small_front_max=64)
+        f.factor(vals)
+        assert f.status()["rc"] == 0
+        g = a.n_front - 2  # a front just below the root: its front matrix came through Schur updates
+        factors[prec] = f.export_front(g)[0]
+        if prec == "tf32":
+            s = _oracle(pr)
+            xo, _ = s.solve_refined(pr.b)
+            bt = torch.tensor(np.ascontiguousarray(pr.b.T), device=DEV)
+            x = torch.empty_like(bt)
+            info = f.refine_solve(vals, bt, x, tol=1e-14, maxit=40)
+            xg = x.cpu().numpy().T
+            assert info["backward_error"] <= 1e-12, info
+            assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-10
+    d32 = np.abs(factors["f32"] - factors["f64"]).max()
+    dtc = np.abs(factors["tf32"] - factors["f64"]).max()
+    assert dtc <= 10 * d32 + 1e-12, (dtc, d32)
+
+
 def test_adjoint_solve_on_unsymmetric_matrix():
     pr = F.convection_2d_q1(9)
     a, f, vals = _setup(pr, "f64", small_front_max=8)
