@@ -30,8 +30,10 @@ struct Launch {
 // Solve plan of one class: fronts split by size (see kernels_solve.cuh).
 struct ClassList {
     int n_small, n_cta, n_piv, n_all;
-    int maxm_cta, maxin_inv;
+    int n_grp[4];                 // fronts with m <= 4, 8, 16, 32 (lane groups of 4, 8, 16, 32)
+    int maxm_cta, maxin_inv, maxk_inv, maxnc_inv;
     int64_t off_small, off_cta;   // into the solve front list
+    int64_t off_grp[4];
     int64_t off_piv, off_all;     // into the row-block list (inverse fronts)
 };
 constexpr int kSolveWarpMax = 64;   // m <= this: one warp per front
@@ -364,13 +366,22 @@ static int build_plan(mf_factors* F) {
         std::stable_sort(all.begin(), all.end(), [&](int32_t x, int32_t y) { return a->fronts[x].m > a->fronts[y].m; });
         {
             ClassList C{};
-            std::vector<int32_t> sm, ct, iv;
+            std::vector<int32_t> sm, ct, iv, gp[4];
             for (int32_t f : all) {
                 if (fused_by_subtree) break;
                 const FrontDev& fr = a->fronts[f];
                 if (fr.q_off >= 0) iv.push_back(f);
+                else if (fr.m <= 4) gp[0].push_back(f);
+                else if (fr.m <= 8) gp[1].push_back(f);
+                else if (fr.m <= 16) gp[2].push_back(f);
+                else if (fr.m <= 32) gp[3].push_back(f);
                 else if (fr.m <= kSolveWarpMax) sm.push_back(f);
                 else ct.push_back(f);
+            }
+            for (int q = 0; q < 4; q++) {
+                C.n_grp[q] = (int)gp[q].size();
+                C.off_grp[q] = (int64_t)slist.size();
+                slist.insert(slist.end(), gp[q].begin(), gp[q].end());
             }
             C.n_small = (int)sm.size();
             C.off_small = (int64_t)slist.size();
@@ -383,6 +394,8 @@ static int build_plan(mf_factors* F) {
             for (int32_t f : iv) {
                 const FrontDev& fr = a->fronts[f];
                 C.maxin_inv = std::max(C.maxin_inv, std::max(fr.k, fr.m - fr.k));
+                C.maxk_inv = std::max(C.maxk_inv, fr.k);
+                C.maxnc_inv = std::max(C.maxnc_inv, fr.m - fr.k);
                 for (int i = 0; i < fr.k; i += 32) rows.push_back({f, i, std::min(fr.k, i + 32), 0});
             }
             C.n_piv = (int)(rows.size() - C.off_piv);
@@ -668,14 +681,12 @@ static int set_smem_limits() {
     CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
     CUDA_TRY(cudaFuncSetAttribute(k_subtree_fwd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_subtree_fwd<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, false, PH_FWD1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, false, PH_FWD2>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, false, PH_BWD1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, false, PH_BWD2>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, true, PH_FWD1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, true, PH_FWD2>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, true, PH_BWD1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, true, PH_BWD2>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+#define SET_INV(TR, PH)                                                                                            \
+    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, TR, PH, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));    \
+    CUDA_TRY(cudaFuncSetAttribute(k_inv_gemv<T, TR, PH, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    SET_INV(false, PH_FWD1) SET_INV(false, PH_FWD2) SET_INV(false, PH_BWD1) SET_INV(false, PH_BWD2)
+    SET_INV(true, PH_FWD1) SET_INV(true, PH_FWD2) SET_INV(true, PH_BWD1) SET_INV(true, PH_BWD2)
+#undef SET_INV
     return MF_OK;
 }
 
@@ -832,12 +843,33 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         CUDA_TRY(cudaGetLastError());
     }
 #define INV_LAUNCH(TR, PH, CNT, OFF)                                                                               \
-    k_inv_gemv<T, TR, PH><<<dim3(CNT, nrhs), 256, (8 * 32 + C.maxin_inv) * sizeof(T), s>>>(                      \
-        fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_maps, vec, vs, ys, yss, d_x, n)
+    if ((PH == PH_BWD1 ? C.maxnc_inv : C.maxk_inv) > 512)                                                          \
+        k_inv_gemv<T, TR, PH, 32><<<dim3(CNT, nrhs), 1024, (32 * 32 + C.maxin_inv) * sizeof(T), s>>>(            \
+            fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_maps, vec, vs, ys, yss, d_x, n);                      \
+    else                                                                                                           \
+        k_inv_gemv<T, TR, PH, 8><<<dim3(CNT, nrhs), 256, (8 * 32 + C.maxin_inv) * sizeof(T), s>>>(               \
+            fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_maps, vec, vs, ys, yss, d_x, n)
     for (int c = 0; c < a->n_cls; c++) {
         const ClassList& C = F->classes[c];
-        int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0);
+        int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0) + (C.n_grp[0] > 0) + (C.n_grp[1] > 0) + (C.n_grp[2] > 0) + (C.n_grp[3] > 0);
         int slot = prof_begin(F, s, FAM_FWD, F->fwd_bytes[c] * nrhs, F->fwd_flops[c] * nrhs, nk);
+#define GRP_FWD(Q, GS)                                                                                             \
+        if (C.n_grp[Q]) {                                                                                          \
+            dim3 g((C.n_grp[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)), nrhs);                                       \
+            if (!trans) k_fwd_grp<T, false, GS><<<g, 256, 0, s>>>(fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, \
+                                                                 F->d_maps, vec, vs, d_x, n);                       \
+            else k_fwd_grp<T, true, GS><<<g, 256, 0, s>>>(fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs,        \
+                                                          F->d_maps, vec, vs, d_x, n);                              \
+        }
+        GRP_FWD(0, 4)
+        GRP_FWD(1, 8)
+        GRP_FWD(2, 16)
+#undef GRP_FWD
+        if (C.n_grp[3]) {  // 16 < m <= 32: the one-front-per-warp kernel is faster forward
+            dim3 g((C.n_grp[3] + 7) / 8, nrhs);
+            if (!trans) k_fwd_warp<T, false><<<g, 256, 0, s>>>(fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_maps, vec, vs, d_x, n);
+            else k_fwd_warp<T, true><<<g, 256, 0, s>>>(fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_maps, vec, vs, d_x, n);
+        }
         if (C.n_small) {
             dim3 g((C.n_small + 7) / 8, nrhs);
             if (!trans) k_fwd_warp<T, false><<<g, 256, 0, s>>>(fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n);
@@ -863,8 +895,20 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
     }
     for (int c = a->n_cls - 1; c >= 0; c--) {
         const ClassList& C = F->classes[c];
-        int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0);
+        int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0) + (C.n_grp[0] > 0) + (C.n_grp[1] > 0) + (C.n_grp[2] > 0) + (C.n_grp[3] > 0);
         int slot = prof_begin(F, s, FAM_BWD, F->bwd_bytes[c] * nrhs, F->bwd_flops[c] * nrhs, nk);
+#define GRP_BWD(Q, GS)                                                                                             \
+        if (C.n_grp[Q]) {                                                                                          \
+            dim3 g((C.n_grp[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)), nrhs);                                       \
+            if (!trans) k_bwd_grp<T, false, GS><<<g, 256, 0, s>>>(fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, \
+                                                                 d_x, n);                                           \
+            else k_bwd_grp<T, true, GS><<<g, 256, 0, s>>>(fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, d_x, n); \
+        }
+        GRP_BWD(0, 4)
+        GRP_BWD(1, 8)
+        GRP_BWD(2, 16)
+        GRP_BWD(3, 32)
+#undef GRP_BWD
         if (C.n_piv) {
             if (!trans) {
                 INV_LAUNCH(false, PH_BWD1, C.n_piv, C.off_piv);

@@ -54,7 +54,7 @@ __device__ __forceinline__ T gather_rhs(const FrontDev& fr, const FrontDev* __re
 
 // Small fronts (m <= 64): one warp per front, rows lane and lane+32.
 template <typename T, bool TRANS>
-__global__ void __launch_bounds__(256) k_fwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(256, 4) k_fwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                   int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                   const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
                                                   double* __restrict__ x, int64_t n_dof) {
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256) k_fwd_warp(const FrontDev* __restrict__ f
 }
 
 template <typename T, bool TRANS>
-__global__ void __launch_bounds__(256) k_bwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(256, 4) k_bwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                   int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                   double* __restrict__ x, int64_t n_dof) {
     const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -147,6 +147,96 @@ __global__ void __launch_bounds__(256) k_bwd_warp(const FrontDev* __restrict__ f
     }
     if (i0 < k) xr[fd[i0]] = (double)v0;
     if (i1 < k) xr[fd[i1]] = (double)v1;
+}
+
+// Tiny fronts (m <= G, G in {4, 8, 16}): 32/G fronts per warp, one lane per
+// row, shuffles of width G; all coefficients are loaded before the short
+// sequential pivot loop.
+template <typename T, bool TRANS, int G>
+__global__ void __launch_bounds__(256) k_fwd_grp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+                                                 int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
+                                                 const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
+                                                 double* __restrict__ x, int64_t n_dof) {
+    const int lane = threadIdx.x & 31;
+    const int fidx = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
+    const bool active = fidx < count;
+    const int r = blockIdx.y;
+    const int i = lane % G;
+    FrontDev fr{};
+    int m = 0, k = 0;
+    if (active) {
+        fr = fronts[list[fidx]];
+        m = fr.m;
+        k = fr.k;
+    }
+    const int32_t* fd = dofs + fr.dof_off;
+    double* xr = x + (int64_t)r * n_dof;
+    T* vr = vecs + (int64_t)r * vec_size;
+    const T* P = fac + fr.P_off;
+    const T* R = fac + fr.R_off;
+    T c[G], dg[G];
+#pragma unroll
+    for (int p = 0; p < G; p++) {
+        c[p] = (p < k && i > p && i < m) ? fcoef<T, TRANS>(P, R, m, k, i, p) : T(0);
+        dg[p] = p < k ? fdiag<T, TRANS>(P, m, p) : T(1);
+    }
+    T w = (active && i < m) ? gather_rhs<T>(fr, fronts, fd, maps, vr, xr, i) : T(0);
+    const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)k);  // warp-uniform pivot count
+#pragma unroll
+    for (int p = 0; p < G; p++) {
+        if (p < kmax) {
+            const T yp = __shfl_sync(0xffffffffu, w, p, G) / dg[p];
+            if (p < k) {
+                if (i == p) w = yp;
+                w -= c[p] * yp;
+            }
+        }
+    }
+    if (active && i < m) {
+        if (i < k) xr[fd[i]] = (double)w;
+        else vr[fr.vec_off + (i - k)] = w;
+    }
+}
+
+template <typename T, bool TRANS, int G>
+__global__ void __launch_bounds__(256) k_bwd_grp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+                                                 int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
+                                                 double* __restrict__ x, int64_t n_dof) {
+    const int lane = threadIdx.x & 31;
+    const int fidx = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
+    const bool active = fidx < count;
+    const int r = blockIdx.y;
+    const int i = lane % G;
+    FrontDev fr{};
+    int m = 0, k = 0;
+    if (active) {
+        fr = fronts[list[fidx]];
+        m = fr.m;
+        k = fr.k;
+    }
+    const int32_t* fd = dofs + fr.dof_off;
+    double* xr = x + (int64_t)r * n_dof;
+    const T* P = fac + fr.P_off;
+    const T* R = fac + fr.R_off;
+    T c[G], dg[G];
+#pragma unroll
+    for (int j = 0; j < G; j++) {
+        c[j] = (j < m && i < k && i < j) ? bcoef<T, TRANS>(P, R, m, k, i, j) : T(0);
+        dg[j] = j < k ? bdiag<T, TRANS>(P, m, j) : T(1);
+    }
+    T v = (active && i < m) ? (T)xr[fd[i]] : T(0);
+    const int mmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);  // warp-uniform front size
+#pragma unroll
+    for (int j = G - 1; j >= 0; j--) {
+        if (j >= mmax) continue;
+        T xj = __shfl_sync(0xffffffffu, v, j, G);
+        if (j < k) {
+            xj = xj / dg[j];
+            if (i == j) v = xj;
+        }
+        v -= c[j] * xj;
+    }
+    if (active && i < k) xr[fd[i]] = (double)v;
 }
 
 // Mid-size fronts (m > 64, k < kInvMinK): one CTA per front.  The pivot block
@@ -234,9 +324,27 @@ __global__ void __launch_bounds__(256) k_bwd_cta(const FrontDev* __restrict__ fr
     for (int i = threadIdx.x; i < mv; i += blockDim.x) v[i] = (T)xr[fd[i]];
     __syncthreads();
     if (!cb_done) {
+        // pivot rows (lane, lane + 32; k < 64) minus their CB part; the 8 warps split the columns
+        T* red = Dg;  // reused: 8 x 64 partial sums fit the 32 x 33 staging area
+        const int lane0 = threadIdx.x & 31, w0 = threadIdx.x >> 5;
+        T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
+        const int i0 = lane0, i1 = lane0 + 32;
+        int j = k + w0;
+        for (; j + 8 < m; j += 16) {
+            const T x0 = v[j], x1 = v[j + 8];
+            if (i0 < k) { a0 += bcoef<T, TRANS>(P, R, m, k, i0, j) * x0; b0 += bcoef<T, TRANS>(P, R, m, k, i0, j + 8) * x1; }
+            if (i1 < k) { a1 += bcoef<T, TRANS>(P, R, m, k, i1, j) * x0; b1 += bcoef<T, TRANS>(P, R, m, k, i1, j + 8) * x1; }
+        }
+        for (; j < m; j += 8) {
+            if (i0 < k) a0 += bcoef<T, TRANS>(P, R, m, k, i0, j) * v[j];
+            if (i1 < k) a1 += bcoef<T, TRANS>(P, R, m, k, i1, j) * v[j];
+        }
+        red[w0 * 64 + i0] = a0 + b0;
+        red[w0 * 64 + i1] = a1 + b1;
+        __syncthreads();
         for (int i = threadIdx.x; i < k; i += blockDim.x) {
             T acc = T(0);
-            for (int j = k; j < m; j++) acc += bcoef<T, TRANS>(P, R, m, k, i, j) * v[j];
+            for (int w = 0; w < 8; w++) acc += red[w * 64 + i];
             v[i] -= acc;
         }
         __syncthreads();
@@ -307,15 +415,15 @@ __device__ __forceinline__ T inv_coef(const T* __restrict__ P, const T* __restri
     return TRANS ? Q[j + (int64_t)i * k] : (j == i ? T(1) : Q[i + (int64_t)j * k]);
 }
 
-template <typename T, bool TRANS, int PH>
-__global__ void __launch_bounds__(256) k_inv_gemv(const FrontDev* __restrict__ fronts, const RowBlock* __restrict__ tasks,
+template <typename T, bool TRANS, int PH, int NW>
+__global__ void __launch_bounds__(NW * 32) k_inv_gemv(const FrontDev* __restrict__ fronts, const RowBlock* __restrict__ tasks,
                                                   const T* __restrict__ fac, const T* __restrict__ inv,
                                                   const int32_t* __restrict__ dofs, const int32_t* __restrict__ maps,
                                                   T* __restrict__ vecs, int64_t vec_size, T* __restrict__ ys,
                                                   int64_t ys_size, double* __restrict__ x, int64_t n_dof) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* red = reinterpret_cast<T*>(smem_raw);  // 8 x 32
-    T* vin = red + 8 * 32;
+    T* red = reinterpret_cast<T*>(smem_raw);  // NW x 32
+    T* vin = red + NW * 32;
     const RowBlock t = tasks[blockIdx.x];
     const int r = blockIdx.y;
     const FrontDev fr = fronts[t.front];
@@ -351,40 +459,51 @@ __global__ void __launch_bounds__(256) k_inv_gemv(const FrontDev* __restrict__ f
         else xr[fd[i]] = (double)acc;
     };
     if (!TRANS) {
+        // lane = row, the NW warps split the columns; the rectangle part of the
+        // column range needs no per-element test, only the triangle edge does
         const int i = t.r0 + lane;
         const bool valid = i < t.r1;
-        const int c0 = PH == PH_BWD2 ? t.r0 : 0;
-        const int c1 = PH == PH_FWD1 ? min(t.r1, k) : nin;
-        T a0 = T(0), a1 = T(0);
-        int j = c0 + warp;
-        for (; j + 8 < c1; j += 16) {
-            if (valid && j >= lo(i) && j < hi(i)) a0 += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j) * vin[j];
-            if (valid && j + 8 >= lo(i) && j + 8 < hi(i)) a1 += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j + 8) * vin[j + 8];
+        // full columns for every row of the block: FWD1 [0, r0); BWD2 [r1, k); else [0, nin)
+        const int f0 = PH == PH_BWD2 ? t.r1 : 0;
+        const int f1 = PH == PH_FWD1 ? t.r0 : nin;
+        T acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) acc[u] = T(0);
+        if (valid) {
+            int j = f0 + warp;
+            for (; j + 7 * NW < f1; j += 8 * NW) {
+#pragma unroll
+                for (int u = 0; u < 8; u++) acc[u] += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j + NW * u) * vin[j + NW * u];
+            }
+            for (; j < f1; j += NW) acc[0] += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j) * vin[j];
+            // triangle edge: columns of the block's own diagonal band
+            if (PH == PH_FWD1 || PH == PH_BWD2) {
+                for (int jj = t.r0 + warp; jj < t.r1; jj += NW)
+                    if (jj >= lo(i) && jj < hi(i)) acc[1] += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, jj) * vin[jj];
+            }
         }
-        for (; j < c1; j += 8)
-            if (valid && j >= lo(i) && j < hi(i)) a0 += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j) * vin[j];
-        red[warp * 32 + lane] = a0 + a1;
+        red[warp * 32 + lane] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
         __syncthreads();
         if (warp == 0 && valid) {
-            T acc = T(0);
-            for (int w = 0; w < 8; w++) acc += red[w * 32 + lane];
-            finish(i, acc);
+            T sum = T(0);
+            for (int w = 0; w < NW; w++) sum += red[w * 32 + lane];
+            finish(i, sum);
         }
     } else {
-        for (int q = 0; q < 4; q++) {
-            const int i = t.r0 + warp * 4 + q;
-            if (i >= t.r1) break;
-            T a0 = T(0), a1 = T(0);
+        for (int i = t.r0 + warp; i < t.r1; i += NW) {  // one row per warp
+            T acc[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) acc[u] = T(0);
             const int jl = lo(i), jh = hi(i);
             int j = jl + lane;
-            for (; j + 32 < jh; j += 64) {
-                a0 += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j) * vin[j];
-                a1 += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j + 32) * vin[j + 32];
+            for (; j + 224 < jh; j += 256) {
+#pragma unroll
+                for (int u = 0; u < 8; u++) acc[u] += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j + 32 * u) * vin[j + 32 * u];
             }
-            if (j < jh) a0 += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j) * vin[j];
-            T acc = a0 + a1;
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) finish(i, acc);
+            for (; j < jh; j += 32) acc[0] += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j) * vin[j];
+            T sum = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == 0) finish(i, sum);
         }
     }
 }
