@@ -968,8 +968,18 @@ static int residual_into(const mf_factors* Fc, const double* d_values, const dou
     const mf_analysis* a = F->a;
     const int64_t nE = a->n_elem * a->npe;
     int slot = prof_begin(F, s, FAM_RESID, F->resid_bytes * nrhs, F->resid_flops * nrhs, 2);
-    dim3 g1((unsigned)((nE + 255) / 256), nrhs);
-    k_elem_apply<<<g1, 256, 0, s>>>(d_values, F->d_en, d_x, F->d_Y, a->n_elem, a->npe, a->n_dof, 0);
+    const int G = a->npe <= 4 ? 4 : a->npe <= 8 ? 8 : a->npe <= 16 ? 16 : a->npe <= 32 ? 32 : 0;
+    if (G) {
+        const int64_t nthreads = a->n_elem * G;
+        dim3 g1((unsigned)((nthreads + 255) / 256), nrhs);
+        if (G == 4) k_elem_apply_grp<4><<<g1, 256, 0, s>>>(d_values, F->d_en, d_x, F->d_Y, a->n_elem, a->npe, a->n_dof);
+        else if (G == 8) k_elem_apply_grp<8><<<g1, 256, 0, s>>>(d_values, F->d_en, d_x, F->d_Y, a->n_elem, a->npe, a->n_dof);
+        else if (G == 16) k_elem_apply_grp<16><<<g1, 256, 0, s>>>(d_values, F->d_en, d_x, F->d_Y, a->n_elem, a->npe, a->n_dof);
+        else k_elem_apply_grp<32><<<g1, 256, 0, s>>>(d_values, F->d_en, d_x, F->d_Y, a->n_elem, a->npe, a->n_dof);
+    } else {
+        dim3 g1((unsigned)((nE + 255) / 256), nrhs);
+        k_elem_apply<<<g1, 256, 0, s>>>(d_values, F->d_en, d_x, F->d_Y, a->n_elem, a->npe, a->n_dof, 0);
+    }
     CUDA_TRY(cudaGetLastError());
     dim3 g2((unsigned)((a->n_dof + 255) / 256), nrhs);
     k_gather_residual<<<g2, 256, 0, s>>>(F->d_node_ptr, F->d_node_inc, F->d_Y, d_b, d_r, a->n_dof, nE, 0);

@@ -533,6 +533,28 @@ __global__ void k_elem_apply(const double* __restrict__ values, const int64_t* _
     Y[idx + (int64_t)r * nE] = acc;
 }
 
+// Same product with one lane group of G >= npe lanes per element: each lane
+// loads its node's x once and the group shares them by shuffles.
+template <int G>
+__global__ void __launch_bounds__(256) k_elem_apply_grp(const double* __restrict__ values, const int64_t* __restrict__ en,
+                                                        const double* __restrict__ x, double* __restrict__ Y, int64_t n_elem,
+                                                        int npe, int64_t n_dof) {
+    const int lane = threadIdx.x & 31;
+    const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int a = lane % G;
+    const int r = blockIdx.y;
+    const bool act = e < n_elem && a < npe;
+    const double* xr = x + (int64_t)r * n_dof;
+    const double xa = act ? xr[en[e * npe + a]] : 0.0;
+    const double* K = values + (act ? e : 0) * npe * npe + a;
+    double acc = 0.0;
+    for (int b = 0; b < npe; b++) {
+        const double xb = __shfl_sync(0xffffffffu, xa, b, G);
+        if (act) acc = fma(K[b * npe], xb, acc);
+    }
+    if (act) Y[e * npe + a + (int64_t)r * n_elem * npe] = acc;
+}
+
 __global__ void k_gather_residual(const int64_t* __restrict__ node_ptr, const int64_t* __restrict__ node_inc,
                                   const double* __restrict__ Y, const double* __restrict__ b, double* __restrict__ out,
                                   int64_t n_dof, int64_t nE, int mode) {
@@ -593,16 +615,27 @@ __global__ void k_norms_partial(const double* __restrict__ rv, const double* __r
 }
 
 __global__ void k_norms_final(const double* __restrict__ part, int nblk, double* __restrict__ out) {
-    const int r = blockIdx.x;
-    if (threadIdx.x != 0) return;
+    // one warp per right-hand side; fixed strided order, then a fixed shuffle tree
+    const int r = blockIdx.x, lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) return;
     double o0 = 0, o1 = 0, o2 = 0, o3 = 0, o4 = 0, o5 = 0;
-    for (int i = 0; i < nblk; i++) {
+    for (int i = lane; i < nblk; i += 32) {
         const double* p = part + ((int64_t)r * nblk + i) * 6;
         o0 = nanmax(o0, p[0]); o1 = nanmax(o1, p[1]); o2 = nanmax(o2, p[2]);
         o3 += p[3]; o4 += p[4]; o5 = nanmax(o5, p[5]);
     }
-    double* q = out + r * 6;
-    q[0] = o0; q[1] = o1; q[2] = o2; q[3] = o3; q[4] = o4; q[5] = o5;
+    for (int o = 16; o > 0; o >>= 1) {
+        o0 = nanmax(o0, __shfl_xor_sync(0xffffffffu, o0, o));
+        o1 = nanmax(o1, __shfl_xor_sync(0xffffffffu, o1, o));
+        o2 = nanmax(o2, __shfl_xor_sync(0xffffffffu, o2, o));
+        o3 += __shfl_xor_sync(0xffffffffu, o3, o);
+        o4 += __shfl_xor_sync(0xffffffffu, o4, o);
+        o5 = nanmax(o5, __shfl_xor_sync(0xffffffffu, o5, o));
+    }
+    if (lane == 0) {
+        double* q = out + r * 6;
+        q[0] = o0; q[1] = o1; q[2] = o2; q[3] = o3; q[4] = o4; q[5] = o5;
+    }
 }
 
 __global__ void k_axpy(double* __restrict__ x, const double* __restrict__ d, int64_t n) {
