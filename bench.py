@@ -179,6 +179,7 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "tf32", "f64"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="direct launches instead of CUDA-graph replay")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -208,10 +209,13 @@ def main():
         torch.tensor(np.ascontiguousarray(pr.b.T), device="cuda")
     x = torch.empty_like(b)
     mesh = M.Mesh(pm.elem_nodes, pm.n_nodes, pm.dim, grid_dims=pm.nel)
-    an = M.Analysis(mesh, M.default_options(precision=args.precision, max_nrhs=max(4, pr.nrhs)))
+    use_graph = 0 if args.no_graph else 1
+    an = M.Analysis(mesh, M.default_options(precision=args.precision, max_nrhs=max(4, pr.nrhs), use_graph=use_graph))
     fac = M.Factors(an)
     info = an.info
-    stream = torch.cuda.current_stream()
+    # a non-default stream: CUDA graphs cannot capture the legacy default stream
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
 
     def step(f, v, bb, xx):
         f.factor(v)
@@ -254,7 +258,7 @@ def main():
     # plain FP64 GPU path, same metric
     fp64 = None
     if args.precision != "f64" and args.fp64_steps > 0:
-        an64 = M.Analysis(mesh, M.default_options(precision="f64", max_nrhs=max(4, pr.nrhs)))
+        an64 = M.Analysis(mesh, M.default_options(precision="f64", max_nrhs=max(4, pr.nrhs), use_graph=use_graph))
         f64 = M.Factors(an64)
         x64 = torch.empty_like(b)
         step(f64, vals, b, x64)
@@ -351,7 +355,8 @@ def main():
                        "classes": info["n_classes"], "max_front": info["max_m"], "nrhs": pr.nrhs,
                        "refine": f"FP64 residual, tol {TOL} normwise backward error",
                        "l2": "inputs larger than L2 (element matrices %.0f MB)" % (Kcm.nbytes / 1e6),
-                       "parallelism": "replicas" if world > 1 else "single"},
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "launch": "CUDA graph replay" if use_graph else "direct launches"},
             "tflops": flops / ms / 1e9,
             "backward_error": eta, "rel_residual": r["rel_residual"], "refine_iterations": float(np.mean(iters)),
             "pivots_perturbed": st["n_perturbed"],

@@ -235,6 +235,16 @@ struct mf_factors {
     SubtreeTask* d_sub_tasks = nullptr;
     SubtreeEntry* d_sub_ecb = nullptr;
     SubtreeEntry* d_sub_euv = nullptr;
+    // captured CUDA graphs, keyed by the buffers they were captured with
+    struct GraphEntry {
+        int kind;  // 0 factor, 1 refine start, 2 refine step
+        const void* p[3];
+        int nrhs;
+        cudaGraphExec_t exec;
+        int64_t launches[MF_PROFILE_FAMILIES];  // what one replay adds to the accounting
+        double bytes[MF_PROFILE_FAMILIES], flops[MF_PROFILE_FAMILIES];
+    };
+    std::vector<GraphEntry> graphs;
     // plan
     std::vector<Launch> plan;
     std::vector<ClassList> classes;
@@ -283,6 +293,7 @@ static void prof_end(mf_factors* F, cudaStream_t s, int slot) {
 
 static void free_factors(mf_factors* f) {
     if (!f) return;
+    for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
                     f->d_vec, f->d_flist, f->d_slist, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_famax, f->d_status,
@@ -290,6 +301,73 @@ static void free_factors(mf_factors* f) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete f;
+}
+
+// Replay the graph captured for (kind, p0, p1, p2, nrhs) on stream s, capturing
+// `enqueue` first if there is none.  Graphs need a capturable stream: the
+// legacy default stream (NULL) runs `enqueue` directly.
+template <typename Fn>
+static int run_graph(mf_factors* F, int kind, const void* p0, const void* p1, const void* p2, int nrhs, cudaStream_t s,
+                     Fn enqueue) {
+    if (!F->opt.use_graph || F->prof || s == nullptr) return enqueue(s);
+    for (auto& g : F->graphs)
+        if (g.kind == kind && g.p[0] == p0 && g.p[1] == p1 && g.p[2] == p2 && g.nrhs == nrhs) {
+            CUDA_TRY(cudaGraphLaunch(g.exec, s));
+            for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {
+                F->acc_launch[q] += g.launches[q];
+                F->acc_bytes[q] += g.bytes[q];
+                F->acc_flops[q] += g.flops[q];
+            }
+            return MF_OK;
+        }
+    int64_t l0[MF_PROFILE_FAMILIES];
+    double b0[MF_PROFILE_FAMILIES], f0[MF_PROFILE_FAMILIES];
+    for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {
+        l0[q] = F->acc_launch[q];
+        b0[q] = F->acc_bytes[q];
+        f0[q] = F->acc_flops[q];
+    }
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue(s);
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc != MF_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        (void)cudaGetLastError();
+        return rc != MF_OK ? rc : MF_ECUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return MF_ECUDA;
+    }
+    // keep a handful per kind
+    int same = 0;
+    for (auto& g : F->graphs) same += g.kind == kind;
+    if (same >= 4)
+        for (size_t i = 0; i < F->graphs.size(); i++)
+            if (F->graphs[i].kind == kind) {
+                cudaGraphExecDestroy(F->graphs[i].exec);
+                F->graphs.erase(F->graphs.begin() + i);
+                break;
+            }
+    mf_factors::GraphEntry ge{};
+    ge.kind = kind;
+    ge.p[0] = p0;
+    ge.p[1] = p1;
+    ge.p[2] = p2;
+    ge.nrhs = nrhs;
+    ge.exec = exec;
+    for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {  // the capture already counted this first run
+        ge.launches[q] = F->acc_launch[q] - l0[q];
+        ge.bytes[q] = F->acc_bytes[q] - b0[q];
+        ge.flops[q] = F->acc_flops[q] - f0[q];
+    }
+    F->graphs.push_back(ge);
+    CUDA_TRY(cudaGraphLaunch(exec, s));
+    return MF_OK;
 }
 
 template <typename T>
@@ -811,7 +889,9 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
 extern "C" int mf_factor(mf_factors* F, const double* d_values, mf_stream_t stream) {
     if (!F || !d_values) return MF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    int rc = F->prec == MF_F64 ? run_factor<double>(F, d_values, s) : run_factor<float>(F, d_values, s);
+    int rc = run_graph(F, 0, d_values, nullptr, nullptr, 0, s, [&](cudaStream_t st) {
+        return F->prec == MF_F64 ? run_factor<double>(F, d_values, st) : run_factor<float>(F, d_values, st);
+    });
     if (rc == MF_OK) {
         F->factored = true;
         F->rowabs_valid = false;
@@ -955,11 +1035,15 @@ static int solve_common(mf_factors* F, double* d_rhs, int nrhs, bool trans, mf_s
 }
 
 extern "C" int mf_solve(mf_factors* F, double* d_rhs, int nrhs, mf_stream_t stream) {
-    return solve_common(F, d_rhs, nrhs, false, stream);
+    if (!F || !d_rhs || nrhs < 1 || !F->factored || nrhs > F->max_nrhs) return MF_EINVAL;
+    return run_graph(F, 3, d_rhs, nullptr, nullptr, nrhs, (cudaStream_t)stream,
+                     [&](cudaStream_t st) { return solve_common(F, d_rhs, nrhs, false, (mf_stream_t)st); });
 }
 
 extern "C" int mf_solve_adjoint(mf_factors* F, double* d_rhs, int nrhs, mf_stream_t stream) {
-    return solve_common(F, d_rhs, nrhs, true, stream);
+    if (!F || !d_rhs || nrhs < 1 || !F->factored || nrhs > F->max_nrhs) return MF_EINVAL;
+    return run_graph(F, 4, d_rhs, nullptr, nullptr, nrhs, (cudaStream_t)stream,
+                     [&](cudaStream_t st) { return solve_common(F, d_rhs, nrhs, true, (mf_stream_t)st); });
 }
 
 static int residual_into(const mf_factors* Fc, const double* d_values, const double* d_x, const double* d_b, double* d_r,
@@ -1018,21 +1102,45 @@ extern "C" int mf_refine_solve(mf_factors* F, const double* d_values, const doub
     int rc;
     if (!F->rowabs_valid || F->rowabs_values != d_values)
         if ((rc = compute_rowabs(F, d_values, s))) return rc;
-    int slot = prof_begin(F, s, FAM_OTHER, 16.0 * n * nrhs, 0, 0);
-    CUDA_TRY(cudaMemcpyAsync(d_x, d_b, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
-    prof_end(F, s, slot);
-    if ((rc = mf_solve(F, d_x, nrhs, stream))) return rc;
+    // the residual and its norms after the current x (device only)
+    auto residual_norms = [&](cudaStream_t st) -> int {
+        int r2;
+        if ((r2 = residual_into(F, d_values, d_x, d_b, F->d_r, nrhs, st))) return r2;
+        dim3 gp(F->norm_blocks, nrhs);
+        int sl = prof_begin(F, st, FAM_RESID, 24.0 * n * nrhs, 5.0 * n * nrhs, 2);
+        k_norms_partial<<<gp, 256, 0, st>>>(F->d_r, d_x, d_b, F->d_rowabs, n, F->d_part);
+        k_norms_final<<<nrhs, 32, 0, st>>>(F->d_part, F->norm_blocks, F->d_norms);
+        prof_end(F, st, sl);
+        CUDA_TRY(cudaGetLastError());
+        return MF_OK;
+    };
+    // first solve: x = A^-1 b, then residual
+    auto start = [&](cudaStream_t st) -> int {
+        int sl = prof_begin(F, st, FAM_OTHER, 16.0 * n * nrhs, 0, 0);
+        CUDA_TRY(cudaMemcpyAsync(d_x, d_b, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, st));
+        prof_end(F, st, sl);
+        int r2;
+        if ((r2 = solve_common(F, d_x, nrhs, false, (mf_stream_t)st))) return r2;
+        return residual_norms(st);
+    };
+    // one correction: d = A^-1 r, x += d, then residual
+    auto step = [&](cudaStream_t st) -> int {
+        int sl = prof_begin(F, st, FAM_OTHER, 16.0 * n * nrhs, 0, 0);
+        CUDA_TRY(cudaMemcpyAsync(F->d_d, F->d_r, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, st));
+        prof_end(F, st, sl);
+        int r2;
+        if ((r2 = solve_common(F, F->d_d, nrhs, false, (mf_stream_t)st))) return r2;
+        sl = prof_begin(F, st, FAM_OTHER, 24.0 * n * nrhs, 1.0 * n * nrhs);
+        k_axpy<<<(unsigned)((n * nrhs + 255) / 256), 256, 0, st>>>(d_x, F->d_d, n * nrhs);
+        prof_end(F, st, sl);
+        CUDA_TRY(cudaGetLastError());
+        return residual_norms(st);
+    };
     std::vector<double> h(6 * nrhs);
     int it = 0;
     double eta = 0, rel = 0;
+    if ((rc = run_graph(F, 1, d_values, d_b, d_x, nrhs, s, start))) return rc;
     for (;;) {
-        if ((rc = residual_into(F, d_values, d_x, d_b, F->d_r, nrhs, s))) return rc;
-        dim3 gp(F->norm_blocks, nrhs);
-        int slot = prof_begin(F, s, FAM_RESID, 24.0 * n * nrhs, 5.0 * n * nrhs, 2);
-        k_norms_partial<<<gp, 256, 0, s>>>(F->d_r, d_x, d_b, F->d_rowabs, n, F->d_part);
-        k_norms_final<<<nrhs, 32, 0, s>>>(F->d_part, F->norm_blocks, F->d_norms);
-        prof_end(F, s, slot);
-        CUDA_TRY(cudaGetLastError());
         CUDA_TRY(cudaMemcpyAsync(h.data(), F->d_norms, sizeof(double) * 6 * nrhs, cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
         const double anorm = h[5];
@@ -1046,14 +1154,7 @@ extern "C" int mf_refine_solve(mf_factors* F, const double* d_values, const doub
             rel = std::max(rel, q[4] > 0 ? std::sqrt(q[3] / q[4]) : std::sqrt(q[3]));
         }
         if (eta <= tol || it >= maxit || !std::isfinite(eta)) break;
-        slot = prof_begin(F, s, FAM_OTHER, 16.0 * n * nrhs, 0, 0);
-        CUDA_TRY(cudaMemcpyAsync(F->d_d, F->d_r, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, s));
-        prof_end(F, s, slot);
-        if ((rc = mf_solve(F, F->d_d, nrhs, stream))) return rc;
-        slot = prof_begin(F, s, FAM_OTHER, 24.0 * n * nrhs, 1.0 * n * nrhs);
-        k_axpy<<<(unsigned)((n * nrhs + 255) / 256), 256, 0, s>>>(d_x, F->d_d, n * nrhs);
-        prof_end(F, s, slot);
-        CUDA_TRY(cudaGetLastError());
+        if ((rc = run_graph(F, 2, d_values, d_b, d_x, nrhs, s, step))) return rc;
         it++;
     }
     if (info) {

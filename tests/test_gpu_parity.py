@@ -224,6 +224,33 @@ def test_batched_meshes_with_four_rhs():
             off += n
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_graph_replay_equals_direct_launches(prec):
+    """use_graph: factor, solve and refinement replayed from captured CUDA graphs on a
+    user stream give bitwise the same results as direct launches."""
+    pr = F.diffusion_2d(20, 3, seed=42)
+    outs = []
+    for graph in (0, 1):
+        a, f, vals = _setup(pr, prec, use_graph=graph, small_front_max=32)
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            b = torch.tensor(pr.b[:, 0], device=DEV)
+            res = []
+            for rep in range(3):  # capture, then replays
+                f.factor(vals, stream=stream)
+                x = torch.empty_like(b)
+                info = f.refine_solve(vals, b, x, tol=1e-14, maxit=30, stream=stream)
+                y = b.clone()
+                f.solve(y, stream=stream)
+                stream.synchronize()
+                res.append((x.cpu().numpy(), y.cpu().numpy(), info["iterations"]))
+        for r in res[1:]:
+            assert np.array_equal(r[0], res[0][0]) and np.array_equal(r[1], res[0][1])
+        outs.append(res[0])
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
+
+
 def test_repeat_factor_is_bitwise_deterministic():
     pr = F.diffusion_2d(16, 3, seed=41)
     a, f, vals = _setup(pr, "f32", small_front_max=64)
