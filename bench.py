@@ -169,6 +169,15 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def plan_summary(o, tinfo):
+    d = o.as_dict()
+    keep = {k: d[k] for k in ("precision", "small_front_max", "subtree_levels", "tc_min_cb", "fused_threads")}
+    keep["tuned"] = None if tinfo is None else {"from_cache": bool(tinfo["from_cache"]),
+                                                  "ms_best": tinfo["ms_best"], "ms_default": tinfo["ms_default"],
+                                                  "candidates": tinfo["candidates"]}
+    return keep
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -180,6 +189,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="direct launches instead of CUDA-graph replay")
+    ap.add_argument("--tune", default="cache", choices=["off", "cache", "run"],
+                    help="plan autotuner (untimed, before warm-up): off = default plan; cache = tuned plan from "
+                         "the package's plan cache, tuning and recording it when missing; run = tune afresh")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -211,11 +223,22 @@ def main():
     mesh = M.Mesh(pm.elem_nodes, pm.n_nodes, pm.dim, grid_dims=pm.nel)
     use_graph = 0 if args.no_graph else 1
     an = M.Analysis(mesh, M.default_options(precision=args.precision, max_nrhs=max(4, pr.nrhs), use_graph=use_graph))
-    fac = M.Factors(an)
     info = an.info
     # a non-default stream: CUDA graphs cannot capture the legacy default stream
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
+
+    from paper_2306_08994_b300 import autotune as AT
+    b1 = b.reshape(pr.nrhs, -1)[0].contiguous()
+
+    def plan_for(analysis):
+        if args.tune == "off":
+            return analysis.options, None
+        return AT.tune(analysis, vals, b1, cache_path=AT.DEFAULT_CACHE if args.tune == "cache" else None,
+                       stream=stream)
+
+    opts, tinfo = plan_for(an)
+    fac = M.Factors(an, opts)
 
     def step(f, v, bb, xx):
         f.factor(v)
@@ -259,7 +282,8 @@ def main():
     fp64 = None
     if args.precision != "f64" and args.fp64_steps > 0:
         an64 = M.Analysis(mesh, M.default_options(precision="f64", max_nrhs=max(4, pr.nrhs), use_graph=use_graph))
-        f64 = M.Factors(an64)
+        opts64, tinfo64 = plan_for(an64)
+        f64 = M.Factors(an64, opts64)
         x64 = torch.empty_like(b)
         step(f64, vals, b, x64)
         barrier()
@@ -272,6 +296,7 @@ def main():
         ms64 = e0.elapsed_time(e1) / args.fp64_steps
         nsolve64 = r64["iterations"] + 1
         fp64 = {"ms": ms64, "tflops": (info["factor_flops"] + info["solve_flops"] * nsolve64 * pr.nrhs) / ms64 / 1e9,
+                "plan": plan_summary(opts64, tinfo64),
                 "backward_error": r64["backward_error"], "refine_iterations": r64["iterations"],
                 "rel_diff_vs_headline": float(torch.linalg.norm(x64 - x) / torch.linalg.norm(x64))}
         del f64, an64, x64
@@ -356,7 +381,8 @@ def main():
                        "refine": f"FP64 residual, tol {TOL} normwise backward error",
                        "l2": "inputs larger than L2 (element matrices %.0f MB)" % (Kcm.nbytes / 1e6),
                        "parallelism": "replicas" if world > 1 else "single",
-                       "launch": "CUDA graph replay" if use_graph else "direct launches"},
+                       "launch": "CUDA graph replay" if use_graph else "direct launches",
+                       "plan": plan_summary(opts, tinfo)},
             "tflops": flops / ms / 1e9,
             "backward_error": eta, "rel_residual": r["rel_residual"], "refine_iterations": float(np.mean(iters)),
             "pivots_perturbed": st["n_perturbed"],

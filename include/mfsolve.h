@@ -61,6 +61,9 @@ typedef struct CUstream_st* mf_stream_t;
 #define MF_TF32 2  /* FP32 fronts, Schur GEMMs of large fronts on the tensor cores (tcgen05,
                       three-pass split TF32 = FP32-accurate products), FP32 accumulation */
 
+/* Front-size buckets of the fused small-front kernel (upper bounds on m). */
+#define MF_FUSED_BUCKETS 9
+
 typedef struct {
     int precision;        /* MF_F64 (default), MF_F32 or MF_TF32 */
     double pivot_tol;     /* static pivot check: a pivot with |p| < pivot_tol * max|F| (max over its
@@ -74,6 +77,12 @@ typedef struct {
     int subtree_levels;   /* bottom classes fused per subtree (one CTA walks classes 1..n of a
                              subtree with a block barrier between them): n > 0 = at most n
                              (fewer if a subtree would not fit shared memory); <= 0 = off */
+    int tc_min_cb;        /* MF_TF32: smallest contribution block (m - k) whose Schur update runs
+                             on the tensor cores; smaller ones use the SIMT GEMM; 0 = 96 */
+    int fused_threads[MF_FUSED_BUCKETS];
+                          /* threads per CTA of the fused small-front kernel for each front-size
+                             bucket (m <= 16, 32, 48, 64, 96, 128, 160, 192, 224): 32, 64, 128 or
+                             256; 0 = default (64 up to m = 32, 128 up to 64, 256 above) */
 } mf_options;
 
 typedef struct {
@@ -229,6 +238,35 @@ int mf_residual_noalloc(int64_t n_dof, int64_t n_elem, int nodes_per_elem, const
 #define MF_PROFILE_FAMILIES 9
 int mf_profile_enable(mf_factors* f, int enable);
 int mf_profile_read(mf_factors* f, double* ms, int64_t* launches, double* bytes, double* flops);
+
+/* Plan autotuner.  Sec. 3.3 fixes the class order of the fronts and leaves
+ * open how the tasks of one class are cut into launches; the launch plan's
+ * free choices are timed here on the caller's problem and the fastest kept:
+ *   fused_threads[]  per front-size bucket (per-bucket times of profiled
+ *                    factorizations, all buckets in one sweep),
+ *   small_front_max  fused / blocked crossover,
+ *   subtree_levels   depth of the bottom-class subtree fusion,
+ *   precision and tc_min_cb  (FP32 family only) SIMT or tensor-core Schur GEMMs.
+ * Candidates are timed as one factorization plus one solve (CUDA events on
+ * `stream`, CUDA graph replay, median of `reps` after one untimed run).
+ * Arguments: a (analysis), d_values (device, element matrices as for
+ * mf_factor), d_b (device, n_dof values: the right-hand side of the timed
+ * solves; not modified), base (options to start from: its precision family,
+ * FP64 or FP32/TF32, is kept; NULL = defaults), reps (>= 1), cache_path (a
+ * JSON Lines file, one object per tuned problem keyed by the device and the
+ * analysis' shape; an entry with this key is returned without timing, a new
+ * result is appended; NULL = no cache), best (out: base with the tuned fields
+ * set), info (out, may be NULL).  Allocates and frees one factor set per
+ * candidate; returns MF_EINVAL, MF_ENOMEM or MF_ECUDA on failure, in which
+ * case `best` is left unchanged.  Synchronises `stream`. */
+typedef struct {
+    double ms_default;   /* factor + solve with `base` (0 when taken from the cache) */
+    double ms_best;      /* factor + solve with `best` */
+    int candidates;      /* plans timed */
+    int from_cache;      /* nonzero if `best` came from cache_path */
+} mf_tune_info;
+int mf_autotune(const mf_analysis* a, const double* d_values, const double* d_b, const mf_options* base, int reps,
+                const char* cache_path, mf_options* best, mf_tune_info* info, mf_stream_t stream);
 
 void mf_free_factors(mf_factors* f);
 void mf_free_analysis(mf_analysis* a);

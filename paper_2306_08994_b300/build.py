@@ -13,8 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmfsolve.so")
-SOURCES = ["analysis.cpp", "capi.cpp", "executor.cu", "noalloc.cu"]
-HEADERS = ["mf_internal.h", "kernels_factor.cuh", "kernels_solve.cuh"]
+SOURCES = ["analysis.cpp", "capi.cpp", "executor.cu", "noalloc.cu", "autotune.cpp"]
+HEADERS = ["mf_internal.h", "kernels_factor.cuh", "kernels_solve.cuh", "kernels_subtree.cuh", "kernels_tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

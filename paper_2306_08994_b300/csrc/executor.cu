@@ -25,6 +25,8 @@ struct Launch {
     int count;
     int maxm;     // fused: bucket bound (shared-memory size)
     int64_t off;  // offset into the list of its kind
+    int bucket = -1;  // fused: size bucket (index into kFusedBounds)
+    int threads = 0;  // fused: threads per CTA
 };
 
 // Solve plan of one class: fronts split by size (see kernels_solve.cuh).
@@ -199,6 +201,7 @@ struct mf_factors {
     double tol_rel = 0;
     int nb = 32;
     int small_max = 96;
+    int tc_min = 96;
     int max_nrhs = 4;
     // device
     FrontDev* d_fronts = nullptr;
@@ -258,6 +261,7 @@ struct mf_factors {
     bool prof = false;
     std::vector<cudaEvent_t> ev;  // pairs
     std::vector<int> ev_fam;
+    std::vector<int> ev_tag;  // fused launches: size bucket; otherwise -1
     size_t ev_used = 0;
     double acc_bytes[MF_PROFILE_FAMILIES] = {};
     double acc_flops[MF_PROFILE_FAMILIES] = {};
@@ -268,7 +272,8 @@ enum Family { FAM_FUSED = 0, FAM_ASM = 1, FAM_PANEL = 2, FAM_TRAIL = 3, FAM_SCHU
               FAM_RESID = 7, FAM_OTHER = 8, FAM_INV = 2 /* accounted with the panel LU */ };
 
 // Bracket one launch: returns a slot index (or -1 when profiling is off).
-static int prof_begin(mf_factors* F, cudaStream_t s, int fam, double bytes, double flops, int kernels = 1) {
+static int prof_begin(mf_factors* F, cudaStream_t s, int fam, double bytes, double flops, int kernels = 1,
+                      int tag = -1) {
     F->acc_launch[fam] += kernels;
     F->acc_bytes[fam] += bytes;
     F->acc_flops[fam] += flops;
@@ -280,9 +285,11 @@ static int prof_begin(mf_factors* F, cudaStream_t s, int fam, double bytes, doub
             F->ev.push_back(e);
         }
         F->ev_fam.resize(F->ev.size() / 2);
+        F->ev_tag.resize(F->ev.size() / 2);
     }
     int slot = (int)F->ev_used++;
     F->ev_fam[slot] = fam;
+    F->ev_tag[slot] = tag;
     cudaEventRecord(F->ev[2 * slot], s);
     return slot;
 }
@@ -384,10 +391,8 @@ static int build_plan(mf_factors* F) {
     std::vector<AsmTile> asmt;
     std::vector<DiagTask> pan;
     std::vector<GemmTile> gem, gtc;
-    const int bounds64[] = {16, 32, 48, 64, 96, 128, 160};
-    const int bounds32[] = {16, 32, 48, 64, 96, 128, 160, 192, 224};
-    const int* bounds = F->prec == MF_F64 ? bounds64 : bounds32;
-    const int nbounds = F->prec == MF_F64 ? 7 : 9;
+    const int* bounds = kFusedBounds;
+    const int nbounds = F->prec == MF_F64 ? kFusedBuckets64 : MF_FUSED_BUCKETS;
     const int nb = F->nb;
     const double T = (double)F->tsize;
     double gb = 0, gf = 0;  // running algorithmic counts of the GEMM launch being built
@@ -530,7 +535,9 @@ static int build_plan(mf_factors* F) {
                     by += T * (m * k + k * nc + nc * nc);
                     fl += pflops(m, k);
                 }
-                push({K_FUSED, c, (int)L.size(), hi, (int64_t)flist.size()}, FAM_FUSED, by, fl);
+                int th = F->opt.fused_threads[bi];
+                if (th <= 0) th = hi <= 32 ? 64 : (hi <= 64 ? 128 : 256);
+                push({K_FUSED, c, (int)L.size(), hi, (int64_t)flist.size(), bi, th}, FAM_FUSED, by, fl);
                 flist.insert(flist.end(), L.begin(), L.end());
             }
             lo = hi;
@@ -632,7 +639,7 @@ static int build_plan(mf_factors* F) {
             const FrontDev& fr = a->fronts[f];
             const int m = fr.m, k = fr.k, nc = m - k;
             if (nc <= 0 || k <= 0) continue;
-            if (F->prec == MF_TF32 && nc >= 96 && k >= 16) {
+            if (F->prec == MF_TF32 && nc >= F->tc_min && k >= 16) {
                 for (int j0 = 0; j0 < nc; j0 += tc::kTileN)
                     for (int i0 = 0; i0 < nc; i0 += tc::kTileM) {
                         GemmTile t{};
@@ -789,6 +796,14 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     F->small_max = F->opt.small_front_max > 0 ? F->opt.small_front_max : (F->prec == MF_F64 ? 96 : 128);
     F->small_max = std::min(F->small_max, F->prec == MF_F64 ? 160 : 224);
     F->small_max = std::max(F->small_max, a->npe);
+    F->tc_min = F->opt.tc_min_cb > 0 ? F->opt.tc_min_cb : 96;
+    for (int i = 0; i < MF_FUSED_BUCKETS; i++) {
+        const int t = F->opt.fused_threads[i];
+        if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256) {
+            delete F;
+            return MF_EINVAL;
+        }
+    }
     F->max_nrhs = F->opt.max_nrhs > 0 ? F->opt.max_nrhs : 4;
     int rc = MF_OK;
 #define TRY(x)                \
@@ -841,13 +856,13 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
     prof_end(F, s, slot);
     for (size_t li = 0; li < F->plan.size(); li++) {
         const Launch& L = F->plan[li];
-        slot = prof_begin(F, s, F->plan_fam[li], F->plan_bytes[li], F->plan_flops[li]);
+        slot = prof_begin(F, s, F->plan_fam[li], F->plan_bytes[li], F->plan_flops[li], 1,
+                          F->plan[li].kind == K_FUSED ? F->plan[li].bucket : -1);
         switch (L.kind) {
             case K_FUSED: {
                 int ldm = L.maxm | 1;
                 size_t sm = fused_smem<T>(L.maxm);
-                int threads = L.maxm <= 32 ? 64 : (L.maxm <= 64 ? 128 : 256);
-                k_front_fused<T><<<L.count, threads, sm, s>>>(F->d_fronts, F->d_flist + L.off, F->d_maps, d_values, a->npe,
+                k_front_fused<T><<<L.count, L.threads, sm, s>>>(F->d_fronts, F->d_flist + L.off, F->d_maps, d_values, a->npe,
                                                               fac, cb, L.maxm, ldm, F->tol_rel, F->d_status);
                 break;
             }
@@ -1235,6 +1250,20 @@ extern "C" int mf_factors_export_front(const mf_factors* F, int32_t front, doubl
 extern "C" int mf_profile_enable(mf_factors* F, int enable) {
     if (!F) return MF_EINVAL;
     F->prof = enable != 0;
+    return MF_OK;
+}
+
+int mf_profile_read_buckets(mf_factors* F, double* ms) {
+    if (!F || !ms) return MF_EINVAL;
+    CUDA_TRY(cudaDeviceSynchronize());
+    for (int b = 0; b < MF_FUSED_BUCKETS; b++) ms[b] = 0;
+    for (size_t i = 0; i < F->ev_used; i++) {
+        const int b = F->ev_tag[i];
+        if (b < 0 || b >= MF_FUSED_BUCKETS) continue;
+        float e = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&e, F->ev[2 * i], F->ev[2 * i + 1]));
+        ms[b] += e;
+    }
     return MF_OK;
 }
 

@@ -145,10 +145,10 @@ __device__ __forceinline__ void tc_stage(const float* __restrict__ base, int ld,
 }
 
 __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTile* __restrict__ tiles, Arenas<float> ar, DevStatus* st) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* stage[2] = {smem_raw, smem_raw + tc::kStageBytes};
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + 2 * tc::kStageBytes);
-    uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(smem_raw + 2 * tc::kStageBytes + 64);
+    extern __shared__ __align__(128) unsigned char smem_tc[];
+    unsigned char* stage[2] = {smem_tc, smem_tc + tc::kStageBytes};
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_tc + 2 * tc::kStageBytes);
+    uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(smem_tc + 2 * tc::kStageBytes + 64);
     const GemmTile t = tiles[blockIdx.x];
     const float* A = ar.a[t.a_ar] + t.a_off + t.i0;                  // rows i0.. of A (M x K, column-major)
     const float* B = ar.a[t.b_ar] + t.b_off + (int64_t)t.j0 * t.ldb;  // columns j0.. of B (K x N, column-major)

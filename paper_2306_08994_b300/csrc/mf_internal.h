@@ -60,6 +60,17 @@ struct mf_analysis {
     mf_info info{};
 };
 
+// Upper bounds on m of the fused small-front kernel's size buckets (FP64
+// fronts use the first kFusedBuckets64: a 160 x 160 FP64 front fills the
+// shared memory of one CTA).
+constexpr int kFusedBounds[MF_FUSED_BUCKETS] = {16, 32, 48, 64, 96, 128, 160, 192, 224};
+constexpr int kFusedBuckets64 = 7;
+
+struct mf_factors;
+// Fused-kernel time per size bucket (ms) over the launches profiled since the
+// last mf_profile_read; synchronises.  Used by the plan autotuner.
+int mf_profile_read_buckets(mf_factors* f, double* ms);
+
 // Bisection trees.  Nodes in postorder; child[2v], child[2v+1]; leaf_elem -1
 // for internal nodes.
 struct HostTree {

@@ -25,12 +25,18 @@ MF_ETOOLARGE = -8
 MF_NOALLOC_MAX_ENTRIES = 1 << 20
 MF_F64, MF_F32, MF_TF32 = 0, 1, 2
 PRECISIONS = {"f64": MF_F64, "f32": MF_F32, "tf32": MF_TF32}
+MF_FUSED_BUCKETS = 9
+FUSED_BOUNDS = (16, 32, 48, 64, 96, 128, 160, 192, 224)
 
 
 class mf_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("pivot_tol", ctypes.c_double), ("pivot_fail", ctypes.c_int),
                 ("small_front_max", ctypes.c_int), ("panel_width", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("max_nrhs", ctypes.c_int), ("subtree_levels", ctypes.c_int)]
+                ("max_nrhs", ctypes.c_int), ("subtree_levels", ctypes.c_int), ("tc_min_cb", ctypes.c_int),
+                ("fused_threads", ctypes.c_int * MF_FUSED_BUCKETS)]
+
+    def as_dict(self) -> dict:
+        return {f: (list(getattr(self, f)) if f == "fused_threads" else getattr(self, f)) for f, _ in self._fields_}
 
 
 class mf_mesh_desc(ctypes.Structure):
@@ -56,11 +62,17 @@ class mf_refine_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("backward_error", ctypes.c_double), ("rel_residual", ctypes.c_double)]
 
 
+class mf_tune_info(ctypes.Structure):
+    _fields_ = [("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double), ("candidates", ctypes.c_int),
+                ("from_cache", ctypes.c_int)]
+
+
 # every symbol include/mfsolve.h declares
 EXPORTS = ["mf_default_options", "mf_strerror", "mf_analyze_mesh", "mf_analyze_batch", "mf_analysis_info",
            "mf_analysis_export", "mf_factors_create", "mf_factor", "mf_solve", "mf_solve_adjoint", "mf_refine_solve",
            "mf_residual", "mf_element_grad", "mf_element_outer", "mf_status", "mf_factors_export_front",
-           "mf_free_factors", "mf_free_analysis", "mf_profile_enable", "mf_profile_read", "mf_residual_noalloc"]
+           "mf_free_factors", "mf_free_analysis", "mf_profile_enable", "mf_profile_read", "mf_residual_noalloc",
+           "mf_autotune"]
 PROFILE_FAMILIES = ["fused", "assemble", "panel", "trailing_gemm", "schur_gemm", "forward", "backward", "residual",
                     "other"]
 
@@ -88,6 +100,7 @@ def _load():
         "mf_free_factors": ([P], None), "mf_free_analysis": ([P], None),
         "mf_profile_enable": ([P, I], I), "mf_profile_read": ([P, P, P, P, P], I),
         "mf_residual_noalloc": ([I64, I64, I, P, P, P, P, P, I, P], I),
+        "mf_autotune": ([P, P, P, P, I, ctypes.c_char_p, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -114,6 +127,8 @@ def default_options(**kw) -> mf_options:
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
+        if k == "fused_threads":
+            v = (ctypes.c_int * MF_FUSED_BUCKETS)(*v)
         setattr(o, k, v)
     return o
 
@@ -283,3 +298,16 @@ class Factors:
         if h is not None and h.value:
             _lib.mf_free_factors(h)
             self._h = None
+
+
+def autotune(analysis: Analysis, values, b, base: Optional[mf_options] = None, reps: int = 3,
+             cache_path: Optional[str] = None, stream=None):
+    """mf_autotune: (tuned options, info dict).  values/b are CUDA tensors (element
+    matrices; one right-hand side of n_dof values, not modified)."""
+    best = mf_options()
+    info = mf_tune_info()
+    base = base if base is not None else analysis.options
+    path = cache_path.encode() if cache_path else None
+    _check(_lib.mf_autotune(analysis._h, _dptr(values), _dptr(b), ctypes.byref(base), int(reps), path,
+                            ctypes.byref(best), ctypes.byref(info), _stream(stream)), "mf_autotune")
+    return best, {f: getattr(info, f) for f, _ in mf_tune_info._fields_}

@@ -76,20 +76,25 @@ def test_f64_factors_match_oracle_front_by_front(case):
     f.factor(vals)
     st = f.status()
     assert st["rc"] == 0 and st["n_perturbed"] == 0
-    s = _oracle(pr)
+    _check_factors(f, _oracle(pr), case)
+
+
+def _check_factors(f, s, tag, stride=1):
+    """Front by front: the library numbers fronts class by class (stable in the
+    oracle's postorder), so sorting the oracle's fronts by height pairs them up."""
     order = np.lexsort((np.arange(s.n_front), s.height))
-    for g, v in enumerate(order):
+    for g in range(0, len(order), stride):
         Lg, Ug = f.export_front(g)
-        Lo, Uo = s.factor_of(v)
+        Lo, Uo = s.factor_of(order[g])
         k = Lo.shape[1]
         if k == 0:
             continue
         sc = max(np.abs(Lo).max(), np.abs(Uo).max(), 1.0)
         low = np.tril(np.ones((Lo.shape[0], k), bool))
         up = np.triu(np.ones((k, Uo.shape[1]), bool), 1)
-        assert np.abs(Lg - Lo)[low].max() <= 1e-11 * sc, (case, g)
+        assert np.abs(Lg - Lo)[low].max() <= 1e-11 * sc, (tag, g)
         if up.any():
-            assert np.abs(Ug - Uo)[up].max() <= 1e-11 * sc, (case, g)
+            assert np.abs(Ug - Uo)[up].max() <= 1e-11 * sc, (tag, g)
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -262,3 +267,48 @@ def test_repeat_factor_is_bitwise_deterministic():
         f.solve(x)
         outs.append(x.cpu().numpy())
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("threads", [32, 64, 128, 256])
+def test_fused_threads_per_bucket_keep_parity(threads):
+    """Every thread count the autotuner may pick for a fused size bucket gives FP64
+    factors equal to the oracle's (front by front) and the same refined solution."""
+    pr = F.diffusion_2d(14, 3, seed=43)
+    a, f, vals = _setup(pr, "f64", small_front_max=160, fused_threads=[threads] * M.mfsolve.MF_FUSED_BUCKETS)
+    f.factor(vals)
+    assert f.status()["rc"] == 0
+    s = _oracle(pr)
+    _check_factors(f, s, threads, stride=3)
+    b = torch.tensor(pr.b[:, 0], device=DEV)
+    x = torch.empty_like(b)
+    info = f.refine_solve(vals, b, x, tol=1e-14, maxit=30)
+    xo, _ = s.solve_refined(pr.b)
+    assert info["backward_error"] <= 1e-12
+    assert np.linalg.norm(x.cpu().numpy() - xo[:, 0]) <= 1e-10 * np.linalg.norm(xo[:, 0])
+
+
+def test_autotune_returns_a_correct_plan_and_caches_it(tmp_path):
+    pr = F.diffusion_2d(24, 3, seed=44)
+    pm = pr.mesh
+    a = M.Analysis(M.Mesh(pm.elem_nodes, pm.n_nodes, pm.dim, grid_dims=pm.nel), M.default_options(precision="f32"))
+    vals = torch.tensor(F.to_colmajor(pr.Ke), device=DEV)
+    b = torch.tensor(pr.b[:, 0], device=DEV)
+    b0 = b.clone()
+    cache = str(tmp_path / "plans.jsonl")
+    best, info = M.mfsolve.autotune(a, vals, b, reps=2, cache_path=cache)
+    assert torch.equal(b, b0)
+    assert info["from_cache"] == 0 and info["candidates"] >= 8
+    assert 0 < info["ms_best"] <= info["ms_default"]
+    assert best.precision in (M.mfsolve.MF_F32, M.mfsolve.MF_TF32)
+    assert all(t in (0, 32, 64, 128, 256) for t in best.fused_threads)
+    best2, info2 = M.mfsolve.autotune(a, vals, b, reps=2, cache_path=cache)
+    assert info2["from_cache"] == 1 and best2.as_dict() == best.as_dict()
+    with open(cache) as fh:
+        assert len(fh.read().strip().splitlines()) == 1
+    f = M.Factors(a, best)
+    f.factor(vals)
+    x = torch.empty_like(b)
+    info3 = f.refine_solve(vals, b, x, tol=1e-14, maxit=30)
+    xo, _ = _oracle(pr).solve_refined(pr.b)
+    assert info3["backward_error"] <= 1e-12
+    assert np.linalg.norm(x.cpu().numpy() - xo[:, 0]) <= 1e-10 * np.linalg.norm(xo[:, 0])
