@@ -239,6 +239,25 @@ int mf_residual_noalloc(int64_t n_dof, int64_t n_elem, int nodes_per_elem, const
 int mf_profile_enable(mf_factors* f, int enable);
 int mf_profile_read(mf_factors* f, double* ms, int64_t* launches, double* bytes, double* flops);
 
+/* Launch trace of the profiled region: one record per event-bracketed launch
+ * (a factorization launch, or all kernels of one class of a substitution),
+ * in issue order.  kind: 0 fused small fronts, 1 large-front assembly,
+ * 2 panel diagonal block, 3 SIMT GEMM, 4 pivot-block inverses, 5 subtree
+ * factorization, 6 tensor-core GEMM, or one of the MF_TRACE_* codes below;
+ * cls: 0-based Foata class or -1; tasks: fronts, tiles or tasks in the launch.
+ * Call before mf_profile_read (which clears the trace).  Writes at most `cap`
+ * records and stores the number recorded in *n; synchronises. */
+#define MF_TRACE_FWD_CLASS 100
+#define MF_TRACE_BWD_CLASS 101
+#define MF_TRACE_SUBTREE_FWD 102
+#define MF_TRACE_SUBTREE_BWD 103
+#define MF_TRACE_OTHER 199
+typedef struct {
+    int family, kind, cls, tasks;
+    double ms;
+} mf_trace_rec;
+int mf_profile_trace(mf_factors* f, mf_trace_rec* out, int cap, int* n);
+
 /* Plan autotuner.  Sec. 3.3 fixes the class order of the fronts and leaves
  * open how the tasks of one class are cut into launches; the launch plan's
  * free choices are timed here on the caller's problem and the fastest kept:

@@ -260,8 +260,8 @@ struct mf_factors {
     // profiling
     bool prof = false;
     std::vector<cudaEvent_t> ev;  // pairs
-    std::vector<int> ev_fam;
-    std::vector<int> ev_tag;  // fused launches: size bucket; otherwise -1
+    std::vector<mf_trace_rec> ev_rec;  // per event pair: family, kind, class, tasks (ms filled on read)
+    std::vector<int> ev_tag;           // fused launches: size bucket; otherwise -1
     size_t ev_used = 0;
     double acc_bytes[MF_PROFILE_FAMILIES] = {};
     double acc_flops[MF_PROFILE_FAMILIES] = {};
@@ -273,7 +273,7 @@ enum Family { FAM_FUSED = 0, FAM_ASM = 1, FAM_PANEL = 2, FAM_TRAIL = 3, FAM_SCHU
 
 // Bracket one launch: returns a slot index (or -1 when profiling is off).
 static int prof_begin(mf_factors* F, cudaStream_t s, int fam, double bytes, double flops, int kernels = 1,
-                      int tag = -1) {
+                      int tag = -1, int kind = MF_TRACE_OTHER, int cls = -1, int tasks = 0) {
     F->acc_launch[fam] += kernels;
     F->acc_bytes[fam] += bytes;
     F->acc_flops[fam] += flops;
@@ -284,11 +284,11 @@ static int prof_begin(mf_factors* F, cudaStream_t s, int fam, double bytes, doub
             if (cudaEventCreate(&e) != cudaSuccess) return -1;
             F->ev.push_back(e);
         }
-        F->ev_fam.resize(F->ev.size() / 2);
+        F->ev_rec.resize(F->ev.size() / 2);
         F->ev_tag.resize(F->ev.size() / 2);
     }
     int slot = (int)F->ev_used++;
-    F->ev_fam[slot] = fam;
+    F->ev_rec[slot] = mf_trace_rec{fam, kind, cls, tasks, 0.0};
     F->ev_tag[slot] = tag;
     cudaEventRecord(F->ev[2 * slot], s);
     return slot;
@@ -857,7 +857,8 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
     for (size_t li = 0; li < F->plan.size(); li++) {
         const Launch& L = F->plan[li];
         slot = prof_begin(F, s, F->plan_fam[li], F->plan_bytes[li], F->plan_flops[li], 1,
-                          F->plan[li].kind == K_FUSED ? F->plan[li].bucket : -1);
+                          F->plan[li].kind == K_FUSED ? F->plan[li].bucket : -1, F->plan[li].kind, F->plan[li].cls,
+                          F->plan[li].count);
         switch (L.kind) {
             case K_FUSED: {
                 int ldm = L.maxm | 1;
@@ -871,7 +872,7 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
                 break;
             case K_PDIAG: {
                 constexpr int NB = sizeof(T) == 8 ? kPanelNB64 : kPanelNB32;
-                k_panel_diag<T, NB><<<L.count, (NB / 4) * (NB / 4), 0, s>>>(F->d_fronts, F->d_panel + L.off, fac,
+                k_panel_diag_blk<T, NB><<<L.count, 256, 0, s>>>(F->d_fronts, F->d_panel + L.off, fac,
                                                                             (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
                 break;
             }
@@ -926,7 +927,7 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
     const int64_t n = a->n_dof, vs = a->vec_size, yss = a->ys_size;
     const size_t dgs = 32 * 33 * sizeof(T);
     if (F->sub.h >= 2) {
-        int slot = prof_begin(F, s, FAM_FWD, 0, 0);
+        int slot = prof_begin(F, s, FAM_FWD, 0, 0, 1, -1, MF_TRACE_SUBTREE_FWD, 0, (int)F->sub.tasks.size());
         dim3 g((unsigned)F->sub.tasks.size(), nrhs);
         if (!trans)
             k_subtree_fwd<T, false><<<g, 256, F->sub.smem_s, s>>>(fr, F->d_sub_tasks, F->d_sub_euv, fac, F->d_dofs, F->d_maps,
@@ -947,7 +948,8 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
     for (int c = 0; c < a->n_cls; c++) {
         const ClassList& C = F->classes[c];
         int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0) + (C.n_grp[0] > 0) + (C.n_grp[1] > 0) + (C.n_grp[2] > 0) + (C.n_grp[3] > 0);
-        int slot = prof_begin(F, s, FAM_FWD, F->fwd_bytes[c] * nrhs, F->fwd_flops[c] * nrhs, nk);
+        int slot = prof_begin(F, s, FAM_FWD, F->fwd_bytes[c] * nrhs, F->fwd_flops[c] * nrhs, nk, -1, MF_TRACE_FWD_CLASS,
+                              c, a->cls_ptr[c + 1] - a->cls_ptr[c]);
 #define GRP_FWD(Q, GS)                                                                                             \
         if (C.n_grp[Q]) {                                                                                          \
             dim3 g((C.n_grp[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)), nrhs);                                       \
@@ -991,7 +993,8 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
     for (int c = a->n_cls - 1; c >= 0; c--) {
         const ClassList& C = F->classes[c];
         int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0) + (C.n_grp[0] > 0) + (C.n_grp[1] > 0) + (C.n_grp[2] > 0) + (C.n_grp[3] > 0);
-        int slot = prof_begin(F, s, FAM_BWD, F->bwd_bytes[c] * nrhs, F->bwd_flops[c] * nrhs, nk);
+        int slot = prof_begin(F, s, FAM_BWD, F->bwd_bytes[c] * nrhs, F->bwd_flops[c] * nrhs, nk, -1, MF_TRACE_BWD_CLASS,
+                              c, a->cls_ptr[c + 1] - a->cls_ptr[c]);
 #define GRP_BWD(Q, GS)                                                                                             \
         if (C.n_grp[Q]) {                                                                                          \
             dim3 g((C.n_grp[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)), nrhs);                                       \
@@ -1029,7 +1032,7 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
     }
 #undef INV_LAUNCH
     if (F->sub.h >= 2) {
-        int slot = prof_begin(F, s, FAM_BWD, 0, 0);
+        int slot = prof_begin(F, s, FAM_BWD, 0, 0, 1, -1, MF_TRACE_SUBTREE_BWD, 0, (int)F->sub.tasks.size());
         dim3 g((unsigned)F->sub.tasks.size(), nrhs);
         if (!trans)
             k_subtree_bwd<T, false><<<g, 256, 0, s>>>(fr, F->d_sub_tasks, F->d_sub_euv, fac, F->d_dofs, d_x, n);
@@ -1267,6 +1270,19 @@ int mf_profile_read_buckets(mf_factors* F, double* ms) {
     return MF_OK;
 }
 
+extern "C" int mf_profile_trace(mf_factors* F, mf_trace_rec* out, int cap, int* n) {
+    if (!F || !n || cap < 0 || (cap > 0 && !out)) return MF_EINVAL;
+    CUDA_TRY(cudaDeviceSynchronize());
+    *n = (int)F->ev_used;
+    for (size_t i = 0; i < F->ev_used && (int)i < cap; i++) {
+        float e = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&e, F->ev[2 * i], F->ev[2 * i + 1]));
+        out[i] = F->ev_rec[i];
+        out[i].ms = e;
+    }
+    return MF_OK;
+}
+
 extern "C" int mf_profile_read(mf_factors* F, double* ms, int64_t* launches, double* bytes, double* flops) {
     if (!F) return MF_EINVAL;
     CUDA_TRY(cudaDeviceSynchronize());
@@ -1274,7 +1290,7 @@ extern "C" int mf_profile_read(mf_factors* F, double* ms, int64_t* launches, dou
     for (size_t i = 0; i < F->ev_used; i++) {
         float e = 0.f;
         CUDA_TRY(cudaEventElapsedTime(&e, F->ev[2 * i], F->ev[2 * i + 1]));
-        t[F->ev_fam[i]] += e;
+        t[F->ev_rec[i].family] += e;
     }
     for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {
         if (ms) ms[q] = t[q];

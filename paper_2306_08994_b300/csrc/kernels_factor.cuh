@@ -241,145 +241,248 @@ struct DiagTask {
     int64_t slot;  // panel-slot offset (64 x 64, column-major, ld 64)
 };
 
-// One CTA per pivot block, NB/4 x NB/4 threads, each owning a 4x4 register
-// tile (rows 4*tr.., columns 4*tc..).  Per pivot the owners of the pivot
-// column and row publish them to double-buffered shared memory, one barrier,
-// then every thread applies the rank-1 update to its own tile (masked to
-// the trailing block).  The block is padded with the identity beyond w.
-// The two inverse sweeps run the same way, interleaved: L_D^-1 top-down
-// (row p of the inverse scaled by 1/L_pp, rows below lose L_ip * row p) and
-// U_D^-1 bottom-up (rows above lose U_iq * row q).
+// Pivot block of a large front (NB x NB at pivot kb, padded with the
+// identity beyond w): partial LU in place (L with its diagonal, unit U) and
+// the explicit inverses L_D^-1 (on and below the diagonal) and U_D^-1 (strict
+// upper part) into the front's panel slot, for the panel products
+// L21 = A21 U_D^-1 and U12 = L_D^-1 A12 that follow.
+// Worked in 16 x 16 sub-blocks (NB/16 of them along the diagonal), 256
+// threads.  For each diagonal sub-block kk:
+//   (1) one warp factors it in registers (lane = row r and half h of the 16
+//       columns; pivot value, pivot column entry and pivot row broadcast by
+//       shuffles), with the static pivot check;
+//   (2) the sub-panels beside it are finished by triangular solves, one
+//       thread per row (L: X U_kk = A) or per column (U: L_kk Y = A);
+//   (3) the trailing sub-blocks take the rank-16 update.
+// Three block barriers per sub-block.  The inverses then come blockwise:
+// diagonal sub-blocks by one thread per column, off-diagonal ones by
+// distance from the diagonal,
+//   X_ik = -X_ii sum_{j=k}^{i-1} L_ij X_jk,   Y_kj = -Y_kk sum_{i=k+1}^{j} U_ki Y_ij,
+// one warp per sub-block and one barrier per distance.
 template <typename T, int NB>
-__global__ void __launch_bounds__((NB / 4) * (NB / 4)) k_panel_diag(const FrontDev* __restrict__ fronts,
-                                                                    const DiagTask* __restrict__ tasks, T* __restrict__ fac,
-                                                                    T* __restrict__ slots, const unsigned int* __restrict__ famax,
-                                                                    double tol_rel, DevStatus* st) {
-    constexpr int TPD = NB / 4;
-    __shared__ T Ds[NB][NB + 1];
-    __shared__ T colb[2][NB], rowb[2][NB], colc[2][NB], rowc[2][NB];
+__global__ void __launch_bounds__(256) k_panel_diag_blk(const FrontDev* __restrict__ fronts,
+                                                        const DiagTask* __restrict__ tasks, T* __restrict__ fac,
+                                                        T* __restrict__ slots, const unsigned int* __restrict__ famax,
+                                                        double tol_rel, DevStatus* st) {
+    constexpr int NBB = NB / 16;
+    static_assert(NB % 16 == 0 && NBB <= 4, "NB must be 16, 32, 48 or 64");
+    __shared__ T D[NB][NB + 1];
+    __shared__ T Z[NB][NB + 1];
+    __shared__ T Tw[8][16][17];
+    __shared__ T rdiag[NB];
     const DiagTask t = tasks[blockIdx.x];
     const FrontDev fr = fronts[t.front];
     const int m = fr.m, kb = t.kb, w = t.w;
-    const int tid = threadIdx.x, tr = tid / TPD, tc = tid % TPD;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     T* P = fac + fr.P_off;
-    for (int j = tid / 32; j < NB; j += TPD * TPD / 32)
-        for (int i = tid % 32; i < NB; i += 32) {
-            if (i < w && j < w) cp_async_elem(&Ds[i][j], P + (kb + i) + (int64_t)(kb + j) * m);
-            else Ds[i][j] = (i == j) ? T(1) : T(0);
+    for (int j = warp; j < NB; j += 8)
+        for (int i = lane; i < NB; i += 32) {
+            if (i < w && j < w) cp_async_elem(&D[i][j], P + (kb + i) + (int64_t)(kb + j) * m);
+            else D[i][j] = (i == j) ? T(1) : T(0);
         }
     cp_async_wait_all();
     __syncthreads();
-    T a[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; r++)
-#pragma unroll
-        for (int c = 0; c < 4; c++) a[r][c] = Ds[4 * tr + r][4 * tc + c];
     const T amax = (T)__uint_as_float(famax[t.front]);
     const T thr = (T)tol_rel * amax > T(0) ? (T)tol_rel * amax : tiny_pivot<T>();
-    // ---- LU (Table 2 tasks: divide the pivot row, update the trailing block)
-    for (int pb = 0; pb < NB; pb += 4) {
+
+    for (int kk = 0; kk < NBB; kk++) {
+        const int o = 16 * kk;
+        // (1) diagonal sub-block: Table 2 tasks T1 (divide the pivot row), T2/T3 (update)
+        if (warp == 0) {
+            const int r = lane & 15, h = lane >> 4;
+            T a[8];
 #pragma unroll
-        for (int pp = 0; pp < 4; pp++) {
-            const int p = pb + pp, par = p & 1;
-            if (tc == pb / 4) {
+            for (int e = 0; e < 8; e++) a[e] = D[o + r][o + 8 * h + e];
 #pragma unroll
-                for (int r = 0; r < 4; r++) colb[par][4 * tr + r] = a[r][pp];
+            for (int p = 0; p < 16; p++) {
+                const T pv = __shfl_sync(0xffffffffu, a[p & 7], p + 16 * (p >> 3));
+                T piv = pv;
+                if (o + p < w) piv = checked_pivot(pv, thr, lane == 0, t.front, kb + o + p, st);
+                const T rinv = T(1) / piv;
+                const T lr = __shfl_sync(0xffffffffu, a[p & 7], r + 16 * (p >> 3));
+#pragma unroll
+                for (int e = 0; e < 8; e++) {
+                    const int j = 8 * h + e;
+                    const T uj = __shfl_sync(0xffffffffu, a[e], p + 16 * h) * rinv;
+                    if (r > p && j > p) a[e] -= lr * uj;
+                    else if (r == p && j > p) a[e] = uj;
+                    else if (r == p && j == p) a[e] = piv;
+                }
+                if (lane == 0) rdiag[o + p] = rinv;
             }
-            if (tr == pb / 4) {
 #pragma unroll
-                for (int c = 0; c < 4; c++) rowb[par][4 * tc + c] = a[pp][c];
+            for (int e = 0; e < 8; e++) D[o + r][o + 8 * h + e] = a[e];
+        }
+        __syncthreads();
+        const int R = NB - o - 16;  // rows (columns) of the sub-panels below (right of) the block
+        if (R > 0) {
+            // (2) L sub-panel rows: x U_kk = a (unit upper);  U sub-panel columns: L_kk y = a
+            if (tid < R) {
+                const int i = o + 16 + tid;
+                T x[16];
+#pragma unroll
+                for (int c = 0; c < 16; c++) x[c] = D[i][o + c];
+#pragma unroll
+                for (int c = 1; c < 16; c++)
+#pragma unroll
+                    for (int q = 0; q < c; q++) x[c] -= x[q] * D[o + q][o + c];
+#pragma unroll
+                for (int c = 0; c < 16; c++) D[i][o + c] = x[c];
+            } else if (tid >= 128 && tid < 128 + R) {
+                const int j = o + 16 + (tid - 128);
+                T y[16];
+#pragma unroll
+                for (int q = 0; q < 16; q++) y[q] = D[o + q][j];
+#pragma unroll
+                for (int rr = 0; rr < 16; rr++) {
+#pragma unroll
+                    for (int q = 0; q < rr; q++) y[rr] -= D[o + rr][o + q] * y[q];
+                    y[rr] *= rdiag[o + rr];
+                }
+#pragma unroll
+                for (int q = 0; q < 16; q++) D[o + q][j] = y[q];
             }
             __syncthreads();
-            T piv = rowb[par][p];
-            if (p < w) piv = checked_pivot(piv, thr, tid == 0, t.front, kb + p, st);
-            const T rinv = T(1) / piv;
+            // (3) trailing sub-blocks: A_ij -= L_i,kk U_kk,j
+            const int nb = R / 16, tr = tid >> 4, tc = tid & 15;
+            T acc[3][3];
 #pragma unroll
-            for (int r = 0; r < 4; r++) {
-                const int i = 4 * tr + r;
-                const T li = colb[par][i];
+            for (int aa = 0; aa < 3; aa++)
 #pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    const int j = 4 * tc + c;
-                    const T uj = rowb[par][j] * rinv;
-                    if (i > p && j > p) a[r][c] -= li * uj;
-                    else if (i == p && j > p) a[r][c] = uj;
-                    else if (i == p && j == p) a[r][c] = piv;
+                for (int bb = 0; bb < 3; bb++) acc[aa][bb] = T(0);
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+                T lv[3], uv[3];
+#pragma unroll
+                for (int aa = 0; aa < 3; aa++) {
+                    lv[aa] = aa < nb ? D[o + 16 + tr + 16 * aa][o + q] : T(0);
+                    uv[aa] = aa < nb ? D[o + q][o + 16 + tc + 16 * aa] : T(0);
                 }
+#pragma unroll
+                for (int aa = 0; aa < 3; aa++)
+#pragma unroll
+                    for (int bb = 0; bb < 3; bb++) acc[aa][bb] += lv[aa] * uv[bb];
             }
+#pragma unroll
+            for (int aa = 0; aa < 3; aa++)
+#pragma unroll
+                for (int bb = 0; bb < 3; bb++)
+                    if (aa < nb && bb < nb) D[o + 16 + tr + 16 * aa][o + 16 + tc + 16 * bb] -= acc[aa][bb];
+            __syncthreads();
         }
     }
-    // factored block back to P (through shared memory, coalesced)
-    __syncthreads();
+    // factored block back to P (coalesced)
+    for (int j = warp; j < w; j += 8)
+        for (int i = lane; i < w; i += 32) P[(kb + i) + (int64_t)(kb + j) * m] = D[i][j];
+
+    // ---- inverses, diagonal sub-blocks: warp kk -> L_kk^-1, warp NBB + kk -> U_kk^-1 (one lane per column)
+    if (warp < 2 * NBB && lane < 16) {
+        const int kk = warp % NBB, o = 16 * kk, c = lane;
+        T x[16];
+        if (warp < NBB) {  // L_kk x = e_c
 #pragma unroll
-    for (int r = 0; r < 4; r++)
+            for (int rr = 0; rr < 16; rr++) {
+                T v = rr == c ? T(1) : T(0);
 #pragma unroll
-        for (int c = 0; c < 4; c++) Ds[4 * tr + r][4 * tc + c] = a[r][c];
-    __syncthreads();
-    for (int j = tid / 32; j < w; j += TPD * TPD / 32)
-        for (int i = tid % 32; i < w; i += 32) P[(kb + i) + (int64_t)(kb + j) * m] = Ds[i][j];
-    // ---- inverses: x = L_D^-1 (lower incl. diagonal), y = U_D^-1 (strict upper)
-    T x[4][4], y[4][4];
+                for (int q = 0; q < rr; q++) v -= D[o + rr][o + q] * x[q];
+                x[rr] = v * rdiag[o + rr];
+            }
 #pragma unroll
-    for (int r = 0; r < 4; r++)
+            for (int rr = 0; rr < 16; rr++)
+                if (rr >= c) Z[o + rr][o + c] = x[rr];
+        } else {  // U_kk y = e_c (unit upper), bottom-up
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-            const bool d = (4 * tr + r) == (4 * tc + c);
-            x[r][c] = d ? T(1) : T(0);
-            y[r][c] = d ? T(1) : T(0);
+            for (int rr = 15; rr >= 0; rr--) {
+                T v = rr == c ? T(1) : T(0);
+#pragma unroll
+                for (int q = rr + 1; q < 16; q++) v -= D[o + rr][o + q] * x[q];
+                x[rr] = v;
+            }
+#pragma unroll
+            for (int rr = 0; rr < 16; rr++)
+                if (rr < c) Z[o + rr][o + c] = x[rr];
         }
-    for (int sb = 0; sb < NB; sb += 4) {
+    }
+    __syncthreads();
+    // ---- off-diagonal sub-blocks by distance d from the diagonal
+    for (int d = 1; d < NBB; d++) {
+        const int nblk = NBB - d;
+        if (warp < 2 * nblk) {
+            const bool lower = warp < nblk;
+            const int k0 = lower ? warp : warp - nblk;  // X_{k0+d, k0} or Y_{k0, k0+d}
+            const int r = lane & 15, h = lane >> 4;
+            T acc[8];
 #pragma unroll
-        for (int ss = 0; ss < 4; ss++) {
-            const int p = sb + ss, par = p & 1;
-            const int q = NB - 1 - p;  // q's tile column/row index: (NB-1-sb-ss)/4 = TPD-1-sb/4, offset 3-ss
-            const int qb = TPD - 1 - sb / 4, qq = 3 - ss;
-            if (tc == sb / 4) {
+            for (int e = 0; e < 8; e++) acc[e] = T(0);
+            if (lower) {  // T = sum_{j=k0}^{i-1} L_ij X_j,k0,   i = k0 + d
+                const int io = 16 * (k0 + d), ko = 16 * k0;
+                for (int jb = k0; jb < k0 + d; jb++) {
+                    const int jo = 16 * jb;
 #pragma unroll
-                for (int r = 0; r < 4; r++) colb[par][4 * tr + r] = a[r][ss];  // L column p
-            }
-            if (tr == sb / 4) {
+                    for (int q = 0; q < 16; q++) {
+                        const T l = D[io + r][jo + q];
 #pragma unroll
-                for (int c = 0; c < 4; c++) rowb[par][4 * tc + c] = x[ss][c];  // inverse row p (unscaled)
-            }
-            if (tc == qb) {
-#pragma unroll
-                for (int r = 0; r < 4; r++) colc[par][4 * tr + r] = a[r][qq];  // U column q
-            }
-            if (tr == qb) {
-#pragma unroll
-                for (int c = 0; c < 4; c++) rowc[par][4 * tc + c] = y[qq][c];  // U^-1 row q (final)
-            }
-            __syncthreads();
-            const T rinv = T(1) / colb[par][p];
-#pragma unroll
-            for (int r = 0; r < 4; r++) {
-                const int i = 4 * tr + r;
-                const T li = colb[par][i], ui = colc[par][i];
-#pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    const int j = 4 * tc + c;
-                    const T xp = rowb[par][j] * rinv;
-                    if (j <= p) {
-                        if (i > p) x[r][c] -= li * xp;
-                        else if (i == p) x[r][c] = xp;
+                        for (int e = 0; e < 8; e++) {
+                            const int cc = 8 * h + e;
+                            // X_j,k0 (lower part of Z; zero above the diagonal of a diagonal sub-block)
+                            const T xv = (jb == k0 && jo + q < ko + cc) ? T(0) : Z[jo + q][ko + cc];
+                            acc[e] += l * xv;
+                        }
                     }
-                    if (i < q && j >= q) y[r][c] -= ui * (j == q ? T(1) : rowc[par][j]);
+                }
+            } else {  // T = sum_{i=k0+1}^{j} U_k0,i Y_i,j,   j = k0 + d
+                const int ko = 16 * k0, jo = 16 * (k0 + d);
+                for (int ib = k0 + 1; ib <= k0 + d; ib++) {
+                    const int io = 16 * ib;
+#pragma unroll
+                    for (int q = 0; q < 16; q++) {
+                        const T u = D[ko + r][io + q];
+#pragma unroll
+                        for (int e = 0; e < 8; e++) {
+                            const int cc = 8 * h + e;
+                            // Y_i,j: unit diagonal, zero below it, when ib is the diagonal sub-block j
+                            T yv;
+                            if (ib == k0 + d) yv = (q == cc) ? T(1) : (q < cc ? Z[io + q][jo + cc] : T(0));
+                            else yv = Z[io + q][jo + cc];
+                            acc[e] += u * yv;
+                        }
+                    }
                 }
             }
+#pragma unroll
+            for (int e = 0; e < 8; e++) Tw[warp][r][8 * h + e] = acc[e];
+            __syncwarp();
+            T out[8];
+#pragma unroll
+            for (int e = 0; e < 8; e++) out[e] = T(0);
+            if (lower) {  // X_ik = -X_ii T
+                const int io = 16 * (k0 + d);
+#pragma unroll
+                for (int q = 0; q < 16; q++) {
+                    const T xv = q <= r ? Z[io + r][io + q] : T(0);
+#pragma unroll
+                    for (int e = 0; e < 8; e++) out[e] -= xv * Tw[warp][q][8 * h + e];
+                }
+                const int ko = 16 * k0;
+#pragma unroll
+                for (int e = 0; e < 8; e++) Z[io + r][ko + 8 * h + e] = out[e];
+            } else {  // Y_kj = -Y_kk T
+                const int ko = 16 * k0, jo = 16 * (k0 + d);
+#pragma unroll
+                for (int q = 0; q < 16; q++) {
+                    const T yv = q == r ? T(1) : (q > r ? Z[ko + r][ko + q] : T(0));
+#pragma unroll
+                    for (int e = 0; e < 8; e++) out[e] -= yv * Tw[warp][q][8 * h + e];
+                }
+#pragma unroll
+                for (int e = 0; e < 8; e++) Z[ko + r][jo + 8 * h + e] = out[e];
+            }
         }
+        __syncthreads();
     }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 4; r++)
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-            const int i = 4 * tr + r, j = 4 * tc + c;
-            Ds[i][j] = j <= i ? x[r][c] : y[r][c];
-        }
-    __syncthreads();
-    T* Z = slots + t.slot;
-    for (int j = tid / 32; j < w; j += TPD * TPD / 32)
-        for (int i = tid % 32; i < w; i += 32) Z[i + j * 64] = Ds[i][j];
+    T* Zg = slots + t.slot;
+    for (int j = warp; j < w; j += 8)
+        for (int i = lane; i < w; i += 32) Zg[i + j * 64] = Z[i][j];
 }
 
 // ---------------------------------------------------------------------------

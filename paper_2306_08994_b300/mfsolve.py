@@ -62,6 +62,15 @@ class mf_refine_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("backward_error", ctypes.c_double), ("rel_residual", ctypes.c_double)]
 
 
+class mf_trace_rec(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_int), ("kind", ctypes.c_int), ("cls", ctypes.c_int), ("tasks", ctypes.c_int),
+                ("ms", ctypes.c_double)]
+
+
+TRACE_KINDS = {0: "fused", 1: "assemble", 2: "panel_diag", 3: "gemm", 4: "inv_diag", 5: "subtree", 6: "gemm_tc",
+               100: "fwd_class", 101: "bwd_class", 102: "subtree_fwd", 103: "subtree_bwd", 199: "other"}
+
+
 class mf_tune_info(ctypes.Structure):
     _fields_ = [("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double), ("candidates", ctypes.c_int),
                 ("from_cache", ctypes.c_int)]
@@ -72,7 +81,7 @@ EXPORTS = ["mf_default_options", "mf_strerror", "mf_analyze_mesh", "mf_analyze_b
            "mf_analysis_export", "mf_factors_create", "mf_factor", "mf_solve", "mf_solve_adjoint", "mf_refine_solve",
            "mf_residual", "mf_element_grad", "mf_element_outer", "mf_status", "mf_factors_export_front",
            "mf_free_factors", "mf_free_analysis", "mf_profile_enable", "mf_profile_read", "mf_residual_noalloc",
-           "mf_autotune"]
+           "mf_autotune", "mf_profile_trace"]
 PROFILE_FAMILIES = ["fused", "assemble", "panel", "trailing_gemm", "schur_gemm", "forward", "backward", "residual",
                     "other"]
 
@@ -101,6 +110,7 @@ def _load():
         "mf_profile_enable": ([P, I], I), "mf_profile_read": ([P, P, P, P, P], I),
         "mf_residual_noalloc": ([I64, I64, I, P, P, P, P, P, I, P], I),
         "mf_autotune": ([P, P, P, P, I, ctypes.c_char_p, P, P, P], I),
+        "mf_profile_trace": ([P, P, I, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -284,6 +294,15 @@ class Factors:
         _check(_lib.mf_profile_read(self._h, _ptr(ms), _ptr(ln), _ptr(by), _ptr(fl)), "mf_profile_read")
         return {fam: {"ms": float(ms[i]), "launches": int(ln[i]), "bytes": float(by[i]), "flops": float(fl[i])}
                 for i, fam in enumerate(PROFILE_FAMILIES)}
+
+    def trace(self) -> list:
+        """Per-launch records of the profiled region (call before profile_read)."""
+        n = ctypes.c_int(0)
+        _check(_lib.mf_profile_trace(self._h, None, 0, ctypes.byref(n)), "mf_profile_trace")
+        recs = (mf_trace_rec * max(n.value, 1))()
+        _check(_lib.mf_profile_trace(self._h, recs, n.value, ctypes.byref(n)), "mf_profile_trace")
+        return [{"family": PROFILE_FAMILIES[r.family], "kind": TRACE_KINDS.get(r.kind, str(r.kind)), "cls": r.cls,
+                 "tasks": r.tasks, "ms": r.ms} for r in recs[:n.value]]
 
     def export_front(self, front: int):
         ex = self.analysis.export()

@@ -7,6 +7,10 @@ Tolerances (derived in DESIGN.md):
     x_oracle refined with a double-double residual;
   * refined paths (FP64 and FP32 fronts): normwise backward error
     ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= 1e-12.
+Refinement in these tests stops at a backward error of 1e-15: the forward
+error of a refined solution is about cond * eta, and with cond near 1e4 on the
+larger heterogeneous cases a stop at 1e-14 can leave it just above the 1e-10
+solution bar although the next correction would bring it to ~1e-13.
 """
 import numpy as np
 import pytest
@@ -109,7 +113,7 @@ def test_solution_matches_oracle(case, prec):
     xo, _ = s.solve_refined(pr.b)
     bt = torch.tensor(b, device=DEV)
     x = torch.empty_like(bt)
-    info = f.refine_solve(vals, bt, x, tol=1e-14, maxit=30)
+    info = f.refine_solve(vals, bt, x, tol=1e-15, maxit=30)
     xg = x.cpu().numpy().T
     assert info["backward_error"] <= 1e-12, info
     assert _backward_error_host(pr, xg, pr.b) <= 1e-12
@@ -141,7 +145,7 @@ def test_tensor_core_schur_path(n):
             xo, _ = s.solve_refined(pr.b)
             bt = torch.tensor(np.ascontiguousarray(pr.b.T), device=DEV)
             x = torch.empty_like(bt)
-            info = f.refine_solve(vals, bt, x, tol=1e-14, maxit=40)
+            info = f.refine_solve(vals, bt, x, tol=1e-15, maxit=40)
             xg = x.cpu().numpy().T
             assert info["backward_error"] <= 1e-12, info
             assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-10
@@ -218,7 +222,7 @@ def test_batched_meshes_with_four_rhs():
         b = np.concatenate([p.b for p in probs], axis=0)  # (N, 4)
         bt = torch.tensor(np.ascontiguousarray(b.T), device=DEV)
         x = torch.empty_like(bt)
-        info = f.refine_solve(vals, bt, x, tol=1e-14, maxit=30)
+        info = f.refine_solve(vals, bt, x, tol=1e-15, maxit=30)
         assert info["backward_error"] <= 1e-12
         xg = x.cpu().numpy().T
         off = 0
@@ -244,7 +248,7 @@ def test_graph_replay_equals_direct_launches(prec):
             for rep in range(3):  # capture, then replays
                 f.factor(vals, stream=stream)
                 x = torch.empty_like(b)
-                info = f.refine_solve(vals, b, x, tol=1e-14, maxit=30, stream=stream)
+                info = f.refine_solve(vals, b, x, tol=1e-15, maxit=30, stream=stream)
                 y = b.clone()
                 f.solve(y, stream=stream)
                 stream.synchronize()
@@ -281,7 +285,7 @@ def test_fused_threads_per_bucket_keep_parity(threads):
     _check_factors(f, s, threads, stride=3)
     b = torch.tensor(pr.b[:, 0], device=DEV)
     x = torch.empty_like(b)
-    info = f.refine_solve(vals, b, x, tol=1e-14, maxit=30)
+    info = f.refine_solve(vals, b, x, tol=1e-15, maxit=30)
     xo, _ = s.solve_refined(pr.b)
     assert info["backward_error"] <= 1e-12
     assert np.linalg.norm(x.cpu().numpy() - xo[:, 0]) <= 1e-10 * np.linalg.norm(xo[:, 0])
@@ -308,7 +312,7 @@ def test_autotune_returns_a_correct_plan_and_caches_it(tmp_path):
     f = M.Factors(a, best)
     f.factor(vals)
     x = torch.empty_like(b)
-    info3 = f.refine_solve(vals, b, x, tol=1e-14, maxit=30)
+    info3 = f.refine_solve(vals, b, x, tol=1e-15, maxit=30)
     xo, _ = _oracle(pr).solve_refined(pr.b)
     assert info3["backward_error"] <= 1e-12
     assert np.linalg.norm(x.cpu().numpy() - xo[:, 0]) <= 1e-10 * np.linalg.norm(xo[:, 0])
