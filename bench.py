@@ -32,24 +32,48 @@ import fem_inputs as F  # noqa: E402
 
 METRIC = "factor+solve ms and TFLOP/s vs plain FP64 GPU path at rel. residual <=1e-12"
 TOL = 1e-12
+
+
+def _batched_sizes():
+    return F.batched_poisson_sizes()
+
+
+# name: (problems builder, meshes-only builder (for flop counts), kind, default precision, description)
+#   kind "solve":   step = factor + FP64-refined solve of every right-hand side
+#   kind "adjoint": step = factor + solve + adjoint solve (lambda = A^-T (x - u_target)) + element gradient
 WORKLOADS = {
-    # name: (builder, description)
-    "diffusion2d_q3_512": (lambda: F.diffusion_2d(512, 3, seed=F.SEED_BASE + 2),
+    "diffusion2d_q3_512": (lambda: [F.diffusion_2d(512, 3, seed=F.SEED_BASE + 2)],
+                           lambda: [F.structured_mesh((512, 512), 3)], "solve", "f32",
                            "2D heterogeneous diffusion, 512x512 Q3, k=10^U(-2,2), 2,362,369 dofs"),
-    "diffusion2d_q3_128": (lambda: F.diffusion_2d(128, 3, seed=F.SEED_BASE + 2),
+    "diffusion2d_q3_128": (lambda: [F.diffusion_2d(128, 3, seed=F.SEED_BASE + 2)],
+                           lambda: [F.structured_mesh((128, 128), 3)], "solve", "f32",
                            "2D heterogeneous diffusion, 128x128 Q3, k=10^U(-2,2), 148,225 dofs"),
-    "diffusion3d_q1_64": (lambda: F.diffusion_3d_q1(64, seed=F.SEED_BASE + 4),
+    "batched_q1_256meshes": (lambda: F.batched_poisson(_batched_sizes(), nrhs=4),
+                             lambda: [F.structured_mesh((int(n), int(n)), 1) for n in _batched_sizes()], "solve",
+                             "f32", "256 independent 2D Q1 Poisson meshes, n ~ U{32..256} (seeded), 4 RHS each, "
+                                    "one batched analysis"),
+    "diffusion3d_q1_64": (lambda: [F.diffusion_3d_q1(64, seed=F.SEED_BASE + 4)],
+                          lambda: [F.structured_mesh((64, 64, 64), 1)], "solve", "f32",
                           "3D diffusion, 64^3 Q1, k=10^U(-1,1), 274,625 dofs"),
-    "poisson2d_q1_16": (lambda: F.poisson_2d_q1(16), "2D Poisson, 16x16 Q1, 289 dofs"),
+    "adjoint2d_q1_1024": (lambda: [F.adjoint_problem(1024)], lambda: [F.structured_mesh((1024, 1024), 1)],
+                          "adjoint", "f64",
+                          "adjoint: 2D Q1 diffusion 1024x1024, theta = log k ~ N(0,1), J = 1/2|u - u_target|^2, "
+                          "factor + solve + adjoint solve + dJ/dtheta, FP64"),
+    "poisson2d_q1_16": (lambda: [F.poisson_2d_q1(16)], lambda: [F.structured_mesh((16, 16), 1)], "solve", "f64",
+                        "2D Poisson, 16x16 Q1, 289 dofs"),
 }
-# bounded CPU sample per workload for the oracle arm: same recipe, smaller mesh
+# bounded CPU sample per workload for the oracle arm: same recipe, smaller
 CPU_SAMPLE = {
-    "diffusion2d_q3_512": ("diffusion2d_q3_128", lambda: F.diffusion_2d(128, 3, seed=F.SEED_BASE + 2)),
-    "diffusion2d_q3_128": ("diffusion2d_q3_128", lambda: F.diffusion_2d(128, 3, seed=F.SEED_BASE + 2)),
-    "diffusion3d_q1_64": ("diffusion3d_q1_16", lambda: F.diffusion_3d_q1(16, seed=F.SEED_BASE + 4)),
-    "poisson2d_q1_16": ("poisson2d_q1_16", lambda: F.poisson_2d_q1(16)),
+    "diffusion2d_q3_512": ("diffusion2d_q3_128", lambda: [F.diffusion_2d(128, 3, seed=F.SEED_BASE + 2)]),
+    "diffusion2d_q3_128": ("diffusion2d_q3_128", lambda: [F.diffusion_2d(128, 3, seed=F.SEED_BASE + 2)]),
+    "batched_q1_256meshes": ("the first 8 meshes of the batch",
+                             lambda: F.batched_poisson(_batched_sizes(), nrhs=4)[:8]),
+    "diffusion3d_q1_64": ("diffusion3d_q1_16", lambda: [F.diffusion_3d_q1(16, seed=F.SEED_BASE + 4)]),
+    "adjoint2d_q1_1024": ("adjoint2d_q1_256", lambda: [F.adjoint_problem(256)]),
+    "poisson2d_q1_16": ("poisson2d_q1_16", lambda: [F.poisson_2d_q1(16)]),
 }
 FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
+FP64_DFMA_TFLOPS = 1.201  # measured DFMA throughput of this B300 (register-resident FMA loop, all SMs)
 
 
 def load_peaks():
@@ -115,40 +139,53 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_arm_step(sample_builder):
-    """One oracle factor + refined solve of the bounded sample; returns (seconds, flops, threads, info)."""
+def oracle_arm_step(probs, kind):
+    """One oracle pass over the bounded sample (factor + refined solve, or factor + solve + adjoint
+    solve + element gradient); returns (seconds, flops, threads, info)."""
     import oracle as O
-    pr = sample_builder()
-    pm = pr.mesh
-    s = O.OracleSolver(pm.n_nodes, pm.elem_nodes, O.tree_bisection(pm.nel))
     nt = O.max_threads()
-    t0 = time.perf_counter()
-    s.factor(F.to_colmajor(pr.Ke), nthreads=nt)
-    x, it = s.solve_refined(pr.b, maxit=10)
-    t1 = time.perf_counter()
-    fl = s.flops + 2.0 * s.nnz_lu * (it + 1) * pr.nrhs
-    return t1 - t0, fl, nt, {"refine_steps": it, "n_dof": pm.n_nodes}
+    dt, fl, steps, ndof = 0.0, 0.0, 0, 0
+    for pr in probs:
+        pm = pr.mesh
+        s = O.OracleSolver(pm.n_nodes, pm.elem_nodes, O.tree_bisection(pm.nel))
+        t0 = time.perf_counter()
+        s.factor(F.to_colmajor(pr.Ke), nthreads=nt)
+        if kind == "adjoint":
+            x = s.solve(pr.b[:, 0])
+            lam = s.solve(x - pr.extra["u_target"], adjoint=True)
+            O.element_grad(pm.elem_nodes, F.to_colmajor(pr.extra["dK"]), lam, x)
+            it = 1  # two substitutions
+        else:
+            x, it = s.solve_refined(pr.b, maxit=10)
+        dt += time.perf_counter() - t0
+        fl += s.flops + 2.0 * s.nnz_lu * (it + 1) * pr.nrhs
+        steps = max(steps, it)
+        ndof += pm.n_nodes
+    return dt, fl, nt, {"refine_steps": steps, "n_dof": ndof}
 
 
-def full_flops(name):
-    """Algorithmic factor flops + one solve of the full workload (oracle's symbolic count)."""
+def full_flops(name, nrhs_of_problem):
+    """Algorithmic factor flops and nnz(L+U) of the full workload (oracle's symbolic count)."""
     import oracle as O
-    pr_nel = {"diffusion2d_q3_512": ((512, 512), 3), "diffusion2d_q3_128": ((128, 128), 3),
-              "diffusion3d_q1_64": ((64, 64, 64), 1), "poisson2d_q1_16": ((16, 16), 1)}[name]
-    pm = F.structured_mesh(*pr_nel)
-    s = O.OracleSolver(pm.n_nodes, pm.elem_nodes, O.tree_bisection(pm.nel))
-    return float(s.flops), float(s.nnz_lu)
+    ff, fnnz = 0.0, 0.0
+    for pm in WORKLOADS[name][1]():
+        s = O.OracleSolver(pm.n_nodes, pm.elem_nodes, O.tree_bisection(pm.nel))
+        ff += float(s.flops)
+        fnnz += float(s.nnz_lu) * nrhs_of_problem
+    return ff, fnnz
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
     name = args.workload
+    kind = WORKLOADS[name][2]
     sname, sb = CPU_SAMPLE[name]
-    ff, fnnz = full_flops(name)
+    probs = sb()
+    ff, fnnz = full_flops(name, probs[0].nrhs)
     times, fls = [], []
     for i in range(args.warmup + args.steps):
-        dt, fl, nt, info = oracle_arm_step(sb)
+        dt, fl, nt, info = oracle_arm_step(probs, kind)
         if i >= args.warmup:
             times.append(dt)
             fls.append(fl)
@@ -160,10 +197,11 @@ def run_reference(args, rank):
     line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": name, "desc": WORKLOADS[name][1], "cpu_sample": sname},
+            "config": {"workload": name, "desc": WORKLOADS[name][4], "cpu_sample": sname},
             "tflops": tflops,
             "cpu_baseline": {"value": ms, "unit": "ms", "cores": nt, "kind": "oracle",
-                             "sample": f"oracle factor+refined solve of {sname} (same recipe) per step, "
+                             "sample": f"oracle {'factor+solve+adjoint+gradient' if kind == 'adjoint' else 'factor+refined solve'}"
+                                       f" of {sname} (same recipe) per step, "
                                        f"time scaled to the full workload by algorithmic flops"},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -185,7 +223,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="diffusion2d_q3_512", choices=list(WORKLOADS))
-    ap.add_argument("--precision", default="f32", choices=["f32", "tf32", "f64"])
+    ap.add_argument("--precision", default=None, choices=["f32", "tf32", "f64"],
+                    help="front arithmetic; default: the workload's (FP32 fronts + FP64 refinement, or FP64)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="direct launches instead of CUDA-graph replay")
@@ -212,24 +251,33 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    builder, desc = WORKLOADS[args.workload]
-    pr = builder()
-    pm = pr.mesh
-    Kcm = F.to_colmajor(pr.Ke)
+    builder, _, kind, prec_default, desc = WORKLOADS[args.workload]
+    precision = args.precision or prec_default
+    probs = builder()
+    nrhs = probs[0].nrhs
+    Kcm = np.concatenate([F.to_colmajor(p.Ke) for p in probs]) if len(probs) > 1 else F.to_colmajor(probs[0].Ke)
     vals = torch.tensor(Kcm, device="cuda")
-    b = torch.tensor(np.ascontiguousarray(pr.b.T), device="cuda").reshape(-1) if pr.nrhs == 1 else \
-        torch.tensor(np.ascontiguousarray(pr.b.T), device="cuda")
+    bh = np.concatenate([p.b for p in probs], axis=0)  # (N, nrhs)
+    b = torch.tensor(np.ascontiguousarray(bh.T), device="cuda")
+    b = b.reshape(-1) if nrhs == 1 else b
     x = torch.empty_like(b)
-    mesh = M.Mesh(pm.elem_nodes, pm.n_nodes, pm.dim, grid_dims=pm.nel)
+    meshes = [M.Mesh(p.mesh.elem_nodes, p.mesh.n_nodes, p.mesh.dim, grid_dims=p.mesh.nel) for p in probs]
     use_graph = 0 if args.no_graph else 1
-    an = M.Analysis(mesh, M.default_options(precision=args.precision, max_nrhs=max(4, pr.nrhs), use_graph=use_graph))
+    an = M.Analysis(meshes if len(meshes) > 1 else meshes[0],
+                    M.default_options(precision=precision, max_nrhs=max(4, nrhs), use_graph=use_graph))
     info = an.info
     # a non-default stream: CUDA graphs cannot capture the legacy default stream
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
+    if kind == "adjoint":
+        dKcm = F.to_colmajor(probs[0].extra["dK"])
+        dK = torch.tensor(dKcm, device="cuda")
+        ut = torch.tensor(probs[0].extra["u_target"], device="cuda")
+        lam = torch.empty_like(b)
+        grad = torch.empty(info["n_elem"], dtype=torch.float64, device="cuda")
 
     from paper_2306_08994_b300 import autotune as AT
-    b1 = b.reshape(pr.nrhs, -1)[0].contiguous()
+    b1 = b.reshape(nrhs, -1)[0].contiguous()
 
     def plan_for(analysis):
         if args.tune == "off":
@@ -240,8 +288,16 @@ def main():
     opts, tinfo = plan_for(an)
     fac = M.Factors(an, opts)
 
-    def step(f, v, bb, xx):
+    def step(f, v, bb, xx, kv=None, kut=None):
         f.factor(v)
+        if kind == "adjoint":
+            # forward solve, adjoint solve with the loss gradient x - u_target, dJ/dtheta_e
+            xx.copy_(bb)
+            f.solve(xx)
+            torch.sub(xx, ut if kut is None else kut, out=lam)
+            f.solve(lam, adjoint=True)
+            f.element_grad(dK if kv is None else kv, lam, xx, grad)
+            return {"iterations": 0, "backward_error": None, "rel_residual": None}
         return f.refine_solve(v, bb, xx, tol=TOL, maxit=60)
 
     def barrier():
@@ -271,17 +327,19 @@ def main():
         ms = float(t.item())
     st = fac.status()
     launches = int(sum(v["launches"] for v in acct.values()))
-    nsolve = float(np.mean(iters)) + 1
-    flops = info["factor_flops"] + info["solve_flops"] * nsolve * pr.nrhs
+    nsolve = 2.0 if kind == "adjoint" else float(np.mean(iters)) + 1
+    flops = info["factor_flops"] + info["solve_flops"] * nsolve * nrhs
+    if kind == "adjoint":
+        # backward error of the plain FP64 solve: mf_refine_solve with no correction step
+        chk = fac.refine_solve(vals, b, torch.empty_like(b), tol=TOL, maxit=0)
+        r = {"iterations": 0, "backward_error": chk["backward_error"], "rel_residual": chk["rel_residual"]}
     eta = r["backward_error"]
-
-    # accuracy vs the refined target: independent host check of the backward error
-    xs = x.reshape(pr.nrhs, -1).cpu().numpy().T
 
     # plain FP64 GPU path, same metric
     fp64 = None
-    if args.precision != "f64" and args.fp64_steps > 0:
-        an64 = M.Analysis(mesh, M.default_options(precision="f64", max_nrhs=max(4, pr.nrhs), use_graph=use_graph))
+    if precision != "f64" and args.fp64_steps > 0:
+        an64 = M.Analysis(meshes if len(meshes) > 1 else meshes[0],
+                          M.default_options(precision="f64", max_nrhs=max(4, nrhs), use_graph=use_graph))
         opts64, tinfo64 = plan_for(an64)
         f64 = M.Factors(an64, opts64)
         x64 = torch.empty_like(b)
@@ -295,7 +353,7 @@ def main():
         barrier()
         ms64 = e0.elapsed_time(e1) / args.fp64_steps
         nsolve64 = r64["iterations"] + 1
-        fp64 = {"ms": ms64, "tflops": (info["factor_flops"] + info["solve_flops"] * nsolve64 * pr.nrhs) / ms64 / 1e9,
+        fp64 = {"ms": ms64, "tflops": (info["factor_flops"] + info["solve_flops"] * nsolve64 * nrhs) / ms64 / 1e9,
                 "plan": plan_summary(opts64, tinfo64),
                 "backward_error": r64["backward_error"], "refine_iterations": r64["iterations"],
                 "rel_diff_vs_headline": float(torch.linalg.norm(x64 - x) / torch.linalg.norm(x64))}
@@ -314,10 +372,10 @@ def main():
     d = prof[dom]
     launches_dom = max(d["launches"], 1)
     per_launch_ms = d["ms"] / launches_dom
-    if dom in ("trailing_gemm", "schur_gemm", "panel") and args.precision != "tf32":
+    if dom in ("trailing_gemm", "schur_gemm", "panel") and precision != "tf32":
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS if args.precision != "f64" else None,
-                "unit": "TFLOP/s"}
+        roof = {"bound": "alu", "achieved": achieved, "unit": "TFLOP/s",
+                "peak": FP32_SIMT_PEAK_TFLOPS if precision != "f64" else FP64_DFMA_TFLOPS}
     elif dom in ("trailing_gemm", "schur_gemm"):
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"] / 2, "unit": "TFLOP/s"}
@@ -328,31 +386,48 @@ def main():
     roof["traffic"] = None
     roof["kernel_family"] = dom
     roof["per_launch_ms"] = per_launch_ms
-    roof["peak_src"] = peaks["src"] if roof["bound"] != "alu" else "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz"
+    roof["peak_src"] = peaks["src"] if roof["bound"] != "alu" else (
+        "derived: 148 SM x 128 FP32 lanes x 2 x 2032 MHz" if precision != "f64" else
+        "measured: DFMA loop on this B300 (1.201 TFLOP/s)")
     families = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                     "GBps": v["bytes"] / max(v["ms"], 1e-9) / 1e6, "TFLOPps": v["flops"] / max(v["ms"], 1e-9) / 1e9}
                 for k, v in prof.items() if v["launches"]}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: inputs H2D, result D2H every step
     hv = torch.from_numpy(Kcm).pin_memory()
     hb = b.cpu().pin_memory()
-    hx = torch.empty_like(hb).pin_memory()
     dv = torch.empty_like(vals)
     db = torch.empty_like(b)
     dx = torch.empty_like(b)
-    for _ in range(1):
+    h2d = Kcm.nbytes + b.numel() * 8
+    if kind == "adjoint":
+        hk = torch.from_numpy(dKcm).pin_memory()
+        hu = ut.cpu().pin_memory()
+        dk = torch.empty_like(dK)
+        du = torch.empty_like(ut)
+        hx = torch.empty(grad.shape, dtype=grad.dtype).pin_memory()
+        h2d += dKcm.nbytes + ut.numel() * 8
+    else:
+        hx = torch.empty_like(hb).pin_memory()
+
+    def e2e_step():
         dv.copy_(hv, non_blocking=True)
         db.copy_(hb, non_blocking=True)
-        step(fac, dv, db, dx)
-        hx.copy_(dx, non_blocking=True)
+        if kind == "adjoint":
+            dk.copy_(hk, non_blocking=True)
+            du.copy_(hu, non_blocking=True)
+            step(fac, dv, db, dx, dk, du)
+            hx.copy_(grad, non_blocking=True)
+        else:
+            step(fac, dv, db, dx)
+            hx.copy_(dx, non_blocking=True)
+
+    e2e_step()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        dv.copy_(hv, non_blocking=True)
-        db.copy_(hb, non_blocking=True)
-        step(fac, dv, db, dx)
-        hx.copy_(dx, non_blocking=True)
+        e2e_step()
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1) / args.steps
@@ -364,21 +439,24 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         sname, sb = CPU_SAMPLE[args.workload]
-        dt, fl, nt, cinfo = oracle_arm_step(sb)
-        ff, fnnz = full_flops(args.workload)
+        dt, fl, nt, cinfo = oracle_arm_step(sb(), kind)
+        ff, fnnz = full_flops(args.workload, nrhs)
         full = ff + 2.0 * fnnz * (cinfo["refine_steps"] + 1)
+        what = "factor+solve+adjoint solve+gradient" if kind == "adjoint" else "factor+refined solve"
         cpu = {"value": dt * 1e3 * full / fl, "unit": "ms", "cores": nt, "kind": "oracle",
-               "sample": f"one oracle factor+refined solve of {sname} (same recipe, {cinfo['n_dof']} dofs) "
+               "sample": f"one oracle {what} of {sname} (same recipe, {cinfo['n_dof']} dofs) "
                          f"took {dt:.2f} s; scaled to the full workload by algorithmic flops"}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if precision == "f64" else "f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc, "n_dof": info["n_dof"], "n_front": info["n_front"],
-                       "classes": info["n_classes"], "max_front": info["max_m"], "nrhs": pr.nrhs,
-                       "refine": f"FP64 residual, tol {TOL} normwise backward error",
+                       "classes": info["n_classes"], "max_front": info["max_m"], "nrhs": nrhs,
+                       "meshes": info["n_meshes"], "precision": precision,
+                       "refine": (f"FP64 residual, tol {TOL} normwise backward error" if kind == "solve" else
+                                  "none (FP64 path; backward error of the plain solve reported)"),
                        "l2": "inputs larger than L2 (element matrices %.0f MB)" % (Kcm.nbytes / 1e6),
                        "parallelism": "replicas" if world > 1 else "single",
                        "launch": "CUDA graph replay" if use_graph else "direct launches",
@@ -391,8 +469,8 @@ def main():
             "roofline": roof,
             "families": families,
             "gpu_launches": launches,
-            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(Kcm.nbytes + b.numel() * 8),
-                    "d2h_bytes_per_step": int(b.numel() * 8)},
+            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(hx.numel() * 8)},
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
         }

@@ -1,0 +1,160 @@
+"""The full-size workloads, through the C ABI on the GPU, against the oracle.
+
+* 256 independent 2D Q1 Poisson meshes (n ~ U{32..256}), 4 right-hand sides,
+  one batched analysis (classes aligned from the leaves across meshes):
+  FP32 fronts + FP64 refinement and the FP64 path; a sample of meshes is
+  solved by the oracle and compared mesh by mesh; every mesh's backward error
+  is checked on the host.
+* 3D Q1 diffusion on 64^3 hexahedra: too large for the oracle's factorization
+  in a test, so the property that holds at any size is checked on the host:
+  the normwise backward error from a double-double residual.
+* Adjoint on 2D Q1 diffusion, 1024^2 elements, theta = log k: the gradient
+  dJ/dtheta_e = -lambda_e^T dK_e x_e against (a) the oracle's gradient and
+  (b) central differences of J on 32 seeded elements, where J(theta +- h e_e)
+  comes from the exact rank-4 update of the solution (Woodbury identity with
+  Z = A^-1 P_e from one 4-right-hand-side solve), so no two nearly equal
+  values of J are subtracted.
+"""
+import numpy as np
+import pytest
+import torch
+
+import fem_inputs as F
+import oracle as O
+import paper_2306_08994_b300 as M
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def _eta_host(mesh, Ke, x, b):
+    """max over right-hand sides of ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf),
+    residual in double-double (oracle), ||A||_inf from the assembled matrix."""
+    import scipy.sparse as sp
+    x2 = np.asarray(x).reshape(mesh.n_nodes, -1)
+    b2 = np.asarray(b).reshape(mesh.n_nodes, -1)
+    rp, cp, vp = F.assemble_csr(mesh, Ke)
+    an = np.abs(sp.csr_matrix((vp, cp, rp))).sum(axis=1).max()
+    out = 0.0
+    for j in range(x2.shape[1]):
+        r = O.residual_dd(mesh.elem_nodes, F.to_colmajor(Ke), np.ascontiguousarray(x2[:, j]),
+                          np.ascontiguousarray(b2[:, j]))
+        out = max(out, np.abs(r).max() / (an * np.abs(x2[:, j]).max() + np.abs(b2[:, j]).max()))
+    return out
+
+
+@pytest.fixture(scope="module")
+def batch():
+    sizes = F.batched_poisson_sizes()
+    probs = F.batched_poisson(sizes, nrhs=4)
+    meshes = [M.Mesh(p.mesh.elem_nodes, p.mesh.n_nodes, 2, grid_dims=p.mesh.nel) for p in probs]
+    return sizes, probs, meshes
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_batched_256_meshes_four_rhs(batch, prec):
+    sizes, probs, meshes = batch
+    a = M.Analysis(meshes, M.default_options(precision=prec, use_graph=1))
+    assert a.info["n_meshes"] == 256
+    vals = torch.tensor(np.concatenate([F.to_colmajor(p.Ke) for p in probs]), device=DEV)
+    b = np.concatenate([p.b for p in probs], axis=0)  # (N, 4)
+    bt = torch.tensor(np.ascontiguousarray(b.T), device=DEV)
+    x = torch.empty_like(bt)
+    f = M.Factors(a)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        f.factor(vals, stream=stream)
+        info = f.refine_solve(vals, bt, x, tol=1e-15, maxit=30, stream=stream)
+        stream.synchronize()
+    assert f.status()["rc"] == 0
+    assert info["backward_error"] <= 1e-12, info
+    xg = x.cpu().numpy().T
+    offs = np.concatenate([[0], np.cumsum([p.mesh.n_nodes for p in probs])])
+    # every mesh: host backward error; sampled meshes: the oracle's solution
+    sample = {int(np.argmin(sizes)), int(np.argmax(sizes)), 7, 100, 200}
+    for i, p in enumerate(probs):
+        xi = xg[offs[i]:offs[i + 1]]
+        if i in sample:
+            s = O.OracleSolver(p.mesh.n_nodes, p.mesh.elem_nodes, O.tree_bisection(p.mesh.nel))
+            assert s.factor(F.to_colmajor(p.Ke), nthreads=O.max_threads()) == 0
+            xo, _ = s.solve_refined(p.b)
+            assert np.linalg.norm(xi - xo) <= 1e-10 * np.linalg.norm(xo), (i, sizes[i])
+            assert _eta_host(p.mesh, p.Ke, xi, p.b) <= 1e-12
+        elif i % 32 == 0:
+            assert _eta_host(p.mesh, p.Ke, xi, p.b) <= 1e-12, (i, sizes[i])
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_3d_q1_64_backward_error(prec):
+    pr = F.diffusion_3d_q1(64, seed=F.SEED_BASE + 4)
+    pm = pr.mesh
+    a = M.Analysis(M.Mesh(pm.elem_nodes, pm.n_nodes, pm.dim, grid_dims=pm.nel), M.default_options(precision=prec))
+    assert a.info["root_m"] == 4225 and a.info["n_classes"] == 19
+    f = M.Factors(a)
+    vals = torch.tensor(F.to_colmajor(pr.Ke), device=DEV)
+    f.factor(vals)
+    assert f.status()["rc"] == 0
+    b = torch.tensor(pr.b[:, 0], device=DEV)
+    x = torch.empty_like(b)
+    info = f.refine_solve(vals, b, x, tol=1e-15, maxit=30)
+    assert info["backward_error"] <= 1e-12, info
+    assert _eta_host(pm, pr.Ke, x.cpu().numpy(), pr.b[:, 0]) <= 1e-12
+    if prec == "f64":
+        # the plain FP64 solve alone (no correction) also meets the residual bar
+        y = b.clone()
+        f.solve(y)
+        assert _eta_host(pm, pr.Ke, y.cpu().numpy(), pr.b[:, 0]) <= 1e-12
+
+
+def _woodbury_delta_J(lam_e, Ze, G, dK, xe, h):
+    """J(theta + h e_e) - J(theta) for K_e -> K_e + (e^h - 1) dK_e, exactly (Woodbury):
+    dx = -Z w, w = dKh (I + Ze dKh)^-1 x_e, dJ = -lam_e^T w + 1/2 w^T G w."""
+    dKh = np.expm1(h) * dK
+    w = dKh @ np.linalg.solve(np.eye(len(xe)) + Ze @ dKh, xe)
+    return -lam_e @ w + 0.5 * w @ G @ w
+
+
+def test_adjoint_gradient_1024_vs_finite_differences_and_oracle():
+    pr = F.adjoint_problem(1024)
+    pm = pr.mesh
+    a = M.Analysis(M.Mesh(pm.elem_nodes, pm.n_nodes, pm.dim, grid_dims=pm.nel), M.default_options(precision="f64"))
+    f = M.Factors(a)
+    vals = torch.tensor(F.to_colmajor(pr.Ke), device=DEV)
+    dK = pr.extra["dK"]
+    dKt = torch.tensor(F.to_colmajor(dK), device=DEV)
+    ut = torch.tensor(pr.extra["u_target"], device=DEV)
+    f.factor(vals)
+    x = torch.tensor(pr.b[:, 0], device=DEV)
+    f.solve(x)
+    lam = (x - ut).contiguous()
+    f.solve(lam, adjoint=True)
+    g = torch.empty(pm.n_elem, dtype=torch.float64, device=DEV)
+    f.element_grad(dKt, lam, x, g)
+    g = g.cpu().numpy()
+    xh, lh = x.cpu().numpy(), lam.cpu().numpy()
+
+    # (b) exact-difference central FD on the 32 seeded elements
+    fd_elems = pr.extra["fd_elems"]
+    h = 1e-4
+    g_fd = np.empty(len(fd_elems))
+    for q, e in enumerate(fd_elems):
+        d = pm.elem_nodes[e]
+        E = torch.zeros(4, pm.n_nodes, dtype=torch.float64, device=DEV)
+        E[torch.arange(4, device=DEV), torch.tensor(d, device=DEV)] = 1.0
+        f.solve(E)  # rows: A^-1 e_{d_i}
+        Ze = E[:, torch.tensor(d, device=DEV)].T.cpu().numpy()  # P_e^T Z
+        G = (E @ E.T).cpu().numpy()
+        dJp = _woodbury_delta_J(lh[d], Ze, G, dK[e], xh[d], h)
+        dJm = _woodbury_delta_J(lh[d], Ze, G, dK[e], xh[d], -h)
+        g_fd[q] = (dJp - dJm) / (2 * h)
+    rel = np.linalg.norm(g_fd - g[fd_elems]) / np.linalg.norm(g_fd)
+    assert rel <= 1e-6, (rel, np.abs(g_fd - g[fd_elems]).max())
+
+    # (a) the oracle's gradient (FP64 CPU multifrontal, same seeded inputs)
+    s = O.OracleSolver(pm.n_nodes, pm.elem_nodes, O.tree_bisection(pm.nel))
+    assert s.factor(F.to_colmajor(pr.Ke), nthreads=O.max_threads()) == 0
+    xo = s.solve(pr.b[:, 0])
+    lo = s.solve(xo - pr.extra["u_target"], adjoint=True)
+    go = O.element_grad(pm.elem_nodes, F.to_colmajor(dK), lo, xo)
+    assert np.linalg.norm(xh - xo) <= 1e-10 * np.linalg.norm(xo)
+    assert np.linalg.norm(g - go) <= 1e-9 * np.linalg.norm(go)
