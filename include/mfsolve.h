@@ -82,7 +82,9 @@ typedef struct {
     int fused_threads[MF_FUSED_BUCKETS];
                           /* threads per CTA of the fused small-front kernel for each front-size
                              bucket (m <= 16, 32, 48, 64, 96, 128, 160, 192, 224): 32, 64, 128 or
-                             256; 0 = default (64 up to m = 32, 128 up to 64, 256 above) */
+                             256; 0 = default (128 up to m = 64, 256 above).  Fronts with m <= 32
+                             run in the lane-group kernel instead (one group of 4, 8, 16 or 32
+                             lanes per front), so the first two entries are not used. */
 } mf_options;
 
 typedef struct {
@@ -243,7 +245,8 @@ int mf_profile_read(mf_factors* f, double* ms, int64_t* launches, double* bytes,
  * (a factorization launch, or all kernels of one class of a substitution),
  * in issue order.  kind: 0 fused small fronts, 1 large-front assembly,
  * 2 panel diagonal block, 3 SIMT GEMM, 4 pivot-block inverses, 5 subtree
- * factorization, 6 tensor-core GEMM, or one of the MF_TRACE_* codes below;
+ * factorization, 6 tensor-core GEMM, 7 lane-group tiny fronts, or one of the
+ * MF_TRACE_* codes below;
  * cls: 0-based Foata class or -1; tasks: fronts, tiles or tasks in the launch.
  * Call before mf_profile_read (which clears the trace).  Writes at most `cap`
  * records and stores the number recorded in *n; synchronises. */

@@ -17,7 +17,7 @@
 
 namespace {
 
-enum LaunchKind { K_FUSED = 0, K_ASM = 1, K_PDIAG = 2, K_GEMM = 3, K_INVDIAG = 4, K_SUBTREE = 5, K_GEMMTC = 6 };
+enum LaunchKind { K_FUSED = 0, K_ASM = 1, K_PDIAG = 2, K_GEMM = 3, K_INVDIAG = 4, K_SUBTREE = 5, K_GEMMTC = 6, K_GRP = 7 };
 
 struct Launch {
     int kind;
@@ -515,28 +515,48 @@ static int build_plan(mf_factors* F) {
         slist.insert(slist.end(), all.begin(), all.end());
 
         if (fused_by_subtree) continue;
-        // fused buckets (largest first inside each launch)
+        // tiny fronts (m <= 32): lane-group kernel, G lanes per front
+        auto small_bytes = [&](const std::vector<int32_t>& L, double& by, double& fl) {
+            by = fl = 0;
+            for (int32_t f : L) {
+                const FrontDev& fr = a->fronts[f];
+                double m = fr.m, k = fr.k, nc = m - k;
+                if (fr.nchild == 0) by += 8.0 * a->npe * a->npe;
+                for (int q = 0; q < fr.nchild; q++) {
+                    const FrontDev& ch = a->fronts[fr.child[q]];
+                    by += T * (double)(ch.m - ch.k) * (ch.m - ch.k);
+                }
+                by += T * (m * k + k * nc + nc * nc);
+                fl += pflops(m, k);
+            }
+        };
         int lo = 0;
+        for (int G : {4, 8, 16, 32}) {
+            if (lo >= F->small_max) break;
+            const int hi = std::min(G, F->small_max);
+            std::vector<int32_t> L;
+            for (int32_t f : all)
+                if (a->fronts[f].m > lo && a->fronts[f].m <= hi) L.push_back(f);
+            if (!L.empty()) {
+                double by, fl;
+                small_bytes(L, by, fl);
+                push({K_GRP, c, (int)L.size(), G, (int64_t)flist.size()}, FAM_FUSED, by, fl);
+                flist.insert(flist.end(), L.begin(), L.end());
+            }
+            lo = hi;
+        }
+        // fused buckets (largest first inside each launch)
         for (int bi = 0; bi < nbounds && lo < F->small_max; bi++) {
+            if (bounds[bi] <= lo) continue;
             int hi = std::min(bounds[bi], F->small_max);
             std::vector<int32_t> L;
             for (int32_t f : all)
                 if (a->fronts[f].m > lo && a->fronts[f].m <= hi) L.push_back(f);
             if (!L.empty()) {
-                double by = 0, fl = 0;
-                for (int32_t f : L) {
-                    const FrontDev& fr = a->fronts[f];
-                    double m = fr.m, k = fr.k, nc = m - k;
-                    if (fr.nchild == 0) by += 8.0 * a->npe * a->npe;
-                    for (int q = 0; q < fr.nchild; q++) {
-                        const FrontDev& ch = a->fronts[fr.child[q]];
-                        by += T * (double)(ch.m - ch.k) * (ch.m - ch.k);
-                    }
-                    by += T * (m * k + k * nc + nc * nc);
-                    fl += pflops(m, k);
-                }
+                double by, fl;
+                small_bytes(L, by, fl);
                 int th = F->opt.fused_threads[bi];
-                if (th <= 0) th = hi <= 32 ? 64 : (hi <= 64 ? 128 : 256);
+                if (th <= 0) th = hi <= 64 ? 128 : 256;
                 push({K_FUSED, c, (int)L.size(), hi, (int64_t)flist.size(), bi, th}, FAM_FUSED, by, fl);
                 flist.insert(flist.end(), L.begin(), L.end());
             }
@@ -834,6 +854,19 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     TRY(dev_alloc(&F->d_part, (size_t)F->norm_blocks * 6 * F->max_nrhs));
     TRY(dev_alloc(&F->d_norms, (size_t)6 * F->max_nrhs));
     TRY(build_plan(F));
+    {
+        // the mid-size solve kernels keep kRhsChunk right-hand sides of a front in shared memory
+        int dev = 0, maxsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        for (const ClassList& C : F->classes) {
+            const size_t need = (32 * 33 + 8 * 64 * kRhsChunk + (size_t)kRhsChunk * C.maxm_cta) * F->tsize;
+            if (C.n_cta > 0 && need > (size_t)maxsm) {
+                free_factors(F);
+                return MF_ENOTSUP;
+            }
+        }
+    }
     TRY(dev_alloc((char**)&F->d_inv, (size_t)a->inv_size * F->tsize));
     TRY(dev_alloc((char**)&F->d_scr, (size_t)F->scr_size * F->tsize));
     TRY(dev_alloc((char**)&F->d_pnl, (size_t)F->pnl_size * F->tsize));
@@ -865,6 +898,23 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
                 size_t sm = fused_smem<T>(L.maxm);
                 k_front_fused<T><<<L.count, L.threads, sm, s>>>(F->d_fronts, F->d_flist + L.off, F->d_maps, d_values, a->npe,
                                                               fac, cb, L.maxm, ldm, F->tol_rel, F->d_status);
+                break;
+            }
+            case K_GRP: {
+                const unsigned per = 8 * (32 / L.maxm);  // fronts per 256-thread CTA
+                const unsigned g = (unsigned)((L.count + per - 1) / per);
+#define GRP_CASE(GS)                                                                                             \
+    case GS:                                                                                                     \
+        k_front_grp<T, GS><<<g, 256, 0, s>>>(F->d_fronts, F->d_flist + L.off, L.count, F->d_maps, d_values, a->npe, \
+                                             fac, cb, F->tol_rel, F->d_status);                                  \
+        break;
+                switch (L.maxm) {
+                    GRP_CASE(4)
+                    GRP_CASE(8)
+                    GRP_CASE(16)
+                    GRP_CASE(32)
+                }
+#undef GRP_CASE
                 break;
             }
             case K_ASM:
@@ -915,6 +965,15 @@ extern "C" int mf_factor(mf_factors* F, const double* d_values, mf_stream_t stre
     return rc;
 }
 
+// Launch a solve kernel templated on the right-hand-side chunk NR: 1 for a
+// single right-hand side, kRhsChunk otherwise.
+#define SOLVE_UNPAREN(...) __VA_ARGS__
+#define SOLVE_NR(KER, TARGS, CFG, ARGS)                                                        \
+    do {                                                                                       \
+        if (nrhs == 1) KER<SOLVE_UNPAREN TARGS, 1><<<SOLVE_UNPAREN CFG>>>(SOLVE_UNPAREN ARGS);  \
+        else KER<SOLVE_UNPAREN TARGS, kRhsChunk><<<SOLVE_UNPAREN CFG>>>(SOLVE_UNPAREN ARGS);    \
+    } while (0)
+
 template <typename T>
 static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStream_t s) {
     const mf_analysis* a = F->a;
@@ -952,31 +1011,30 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
                               c, a->cls_ptr[c + 1] - a->cls_ptr[c]);
 #define GRP_FWD(Q, GS)                                                                                             \
         if (C.n_grp[Q]) {                                                                                          \
-            dim3 g((C.n_grp[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)), nrhs);                                       \
-            if (!trans) k_fwd_grp<T, false, GS><<<g, 256, 0, s>>>(fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, \
-                                                                 F->d_maps, vec, vs, d_x, n);                       \
-            else k_fwd_grp<T, true, GS><<<g, 256, 0, s>>>(fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs,        \
-                                                          F->d_maps, vec, vs, d_x, n);                              \
+            dim3 g((C.n_grp[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)));                                             \
+            if (!trans) SOLVE_NR(k_fwd_grp, (T, false, GS), (g, 256, 0, s), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs)); \
+            else SOLVE_NR(k_fwd_grp, (T, true, GS), (g, 256, 0, s), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs)); \
         }
         GRP_FWD(0, 4)
         GRP_FWD(1, 8)
         GRP_FWD(2, 16)
 #undef GRP_FWD
         if (C.n_grp[3]) {  // 16 < m <= 32: the one-front-per-warp kernel is faster forward
-            dim3 g((C.n_grp[3] + 7) / 8, nrhs);
-            if (!trans) k_fwd_warp<T, false><<<g, 256, 0, s>>>(fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_maps, vec, vs, d_x, n);
-            else k_fwd_warp<T, true><<<g, 256, 0, s>>>(fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_maps, vec, vs, d_x, n);
+            dim3 g((C.n_grp[3] + 7) / 8);
+            if (!trans) SOLVE_NR(k_fwd_warp, (T, false), (g, 256, 0, s), (fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs));
+            else SOLVE_NR(k_fwd_warp, (T, true), (g, 256, 0, s), (fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs));
         }
         if (C.n_small) {
-            dim3 g((C.n_small + 7) / 8, nrhs);
-            if (!trans) k_fwd_warp<T, false><<<g, 256, 0, s>>>(fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n);
-            else k_fwd_warp<T, true><<<g, 256, 0, s>>>(fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n);
+            dim3 g((C.n_small + 7) / 8);
+            if (!trans) SOLVE_NR(k_fwd_warp, (T, false), (g, 256, 0, s), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs));
+            else SOLVE_NR(k_fwd_warp, (T, true), (g, 256, 0, s), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs));
         }
         if (C.n_cta) {
-            dim3 g(C.n_cta, nrhs);
-            size_t sm = dgs + (size_t)C.maxm_cta * sizeof(T);
-            if (!trans) k_fwd_cta<T, false><<<g, 256, sm, s>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n);
-            else k_fwd_cta<T, true><<<g, 256, sm, s>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n);
+            dim3 g(C.n_cta);
+            const int ldw = C.maxm_cta;
+            size_t sm = dgs + (size_t)kRhsChunk * ldw * sizeof(T);
+            if (!trans) k_fwd_cta<T, false><<<g, 256, sm, s>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs, ldw);
+            else k_fwd_cta<T, true><<<g, 256, sm, s>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs, ldw);
         }
         if (C.n_piv) {
             if (!trans) {
@@ -997,10 +1055,9 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
                               c, a->cls_ptr[c + 1] - a->cls_ptr[c]);
 #define GRP_BWD(Q, GS)                                                                                             \
         if (C.n_grp[Q]) {                                                                                          \
-            dim3 g((C.n_grp[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)), nrhs);                                       \
-            if (!trans) k_bwd_grp<T, false, GS><<<g, 256, 0, s>>>(fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, \
-                                                                 d_x, n);                                           \
-            else k_bwd_grp<T, true, GS><<<g, 256, 0, s>>>(fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, d_x, n); \
+            dim3 g((C.n_grp[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)));                                             \
+            if (!trans) SOLVE_NR(k_bwd_grp, (T, false, GS), (g, 256, 0, s), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, d_x, n, nrhs)); \
+            else SOLVE_NR(k_bwd_grp, (T, true, GS), (g, 256, 0, s), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, d_x, n, nrhs)); \
         }
         GRP_BWD(0, 4)
         GRP_BWD(1, 8)
@@ -1017,15 +1074,16 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
             }
         }
         if (C.n_cta) {
-            dim3 g(C.n_cta, nrhs);
-            size_t sm = dgs + (size_t)C.maxm_cta * sizeof(T);
-            if (!trans) k_bwd_cta<T, false><<<g, 256, sm, s>>>(fr, L + C.off_cta, 0, fac, F->d_dofs, d_x, n);
-            else k_bwd_cta<T, true><<<g, 256, sm, s>>>(fr, L + C.off_cta, 0, fac, F->d_dofs, d_x, n);
+            dim3 g(C.n_cta);
+            const int ldw = C.maxm_cta;
+            size_t sm = dgs + (size_t)(8 * 64 * kRhsChunk + kRhsChunk * ldw) * sizeof(T);
+            if (!trans) k_bwd_cta<T, false><<<g, 256, sm, s>>>(fr, L + C.off_cta, 0, fac, F->d_dofs, d_x, n, nrhs, ldw);
+            else k_bwd_cta<T, true><<<g, 256, sm, s>>>(fr, L + C.off_cta, 0, fac, F->d_dofs, d_x, n, nrhs, ldw);
         }
         if (C.n_small) {
-            dim3 g((C.n_small + 7) / 8, nrhs);
-            if (!trans) k_bwd_warp<T, false><<<g, 256, 0, s>>>(fr, L + C.off_small, C.n_small, fac, F->d_dofs, d_x, n);
-            else k_bwd_warp<T, true><<<g, 256, 0, s>>>(fr, L + C.off_small, C.n_small, fac, F->d_dofs, d_x, n);
+            dim3 g((C.n_small + 7) / 8);
+            if (!trans) SOLVE_NR(k_bwd_warp, (T, false), (g, 256, 0, s), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, d_x, n, nrhs));
+            else SOLVE_NR(k_bwd_warp, (T, true), (g, 256, 0, s), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, d_x, n, nrhs));
         }
         prof_end(F, s, slot);
         CUDA_TRY(cudaGetLastError());

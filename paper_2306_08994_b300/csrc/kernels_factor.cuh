@@ -162,6 +162,116 @@ __global__ void __launch_bounds__(256) k_front_fused(const FrontDev* __restrict_
 }
 
 // ---------------------------------------------------------------------------
+// Tiny fronts (m <= G, G in {4, 8, 16, 32}): a group of G lanes per front,
+// 32/G fronts per warp, no shared memory.  Lane i holds row i of F in
+// registers; the pivot row, the pivot and the pivot-column entry travel by
+// width-G shuffles.  Same tasks as k_front_fused: assembly (element matrix
+// at a leaf, extend-add of the children's blocks otherwise), static pivot
+// check, T1 division of the pivot row, T2/T3 update, then P, R, S written.
+template <typename T, int G>
+__global__ void __launch_bounds__(256) k_front_grp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+                                                   int count, const int32_t* __restrict__ maps,
+                                                   const double* __restrict__ values, int npe, T* __restrict__ fac,
+                                                   T* __restrict__ cbs, double tol_rel, DevStatus* st) {
+    const int lane = threadIdx.x & 31;
+    const int fidx = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
+    const bool active = fidx < count;
+    const int i = lane % G;
+    int32_t f = -1;
+    FrontDev fr{};
+    if (active) {
+        f = list[fidx];
+        fr = fronts[f];
+    }
+    const int m = active ? fr.m : 0, k = active ? fr.k : 0;
+    const bool row = i < m;
+    T a[G];
+    // ---- assembly
+    T amax = T(0);
+    if (fr.nchild == 0) {
+        const int32_t* lm = maps + fr.map_off;
+        const double* K = values + (int64_t)fr.elem * npe * npe;
+        const int li = row ? lm[i] : 0;
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            T v = T(0);
+            if (row && j < m) v = (T)K[li + lm[j] * npe];
+            a[j] = v;
+            amax = max(amax, (T)fabs(v));
+        }
+    } else {
+        const int32_t* m0 = maps + fr.map_off;
+        const int32_t* m1 = m0 + m;
+        const FrontDev c0 = fronts[fr.child[0]];
+        const int n0 = c0.m - c0.k;
+        const T* S0 = cbs + c0.S_off;
+        const T* S1 = nullptr;
+        int n1 = 0;
+        const bool two = fr.nchild > 1;
+        if (two) {
+            const FrontDev c1 = fronts[fr.child[1]];
+            n1 = c1.m - c1.k;
+            S1 = cbs + c1.S_off;
+        }
+        const int i0 = row ? m0[i] : -1, i1 = (row && two) ? m1[i] : -1;
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            T v = T(0);
+            if (j < m) {
+                const int j0 = m0[j];
+                if (i0 >= 0 && j0 >= 0) v += S0[i0 + (int64_t)j0 * n0];
+                if (i1 >= 0) {
+                    const int j1 = m1[j];
+                    if (j1 >= 0) v += S1[i1 + (int64_t)j1 * n1];
+                }
+            }
+            a[j] = v;
+            amax = max(amax, (T)fabs(v));
+        }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o, G));
+    const T thr = (T)tol_rel * amax > T(0) ? (T)tol_rel * amax : tiny_pivot<T>();
+    // ---- partial LU (Table 2): all lanes shuffle, each group applies its own pivots
+    const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)k);
+#pragma unroll
+    for (int p = 0; p < G; p++) {
+        if (p < kmax) {
+            const T pv = __shfl_sync(0xffffffffu, a[p], p, G);
+            const bool mine = p < k;
+            T piv = pv;
+            if (mine) piv = checked_pivot(pv, thr, i == 0, f, p, st);
+            const T rinv = T(1) / piv;
+            const T lp = a[p];
+#pragma unroll
+            for (int j = p + 1; j < G; j++) {
+                const T uj = __shfl_sync(0xffffffffu, a[j], p, G) * rinv;
+                if (mine) {
+                    if (i > p) a[j] -= lp * uj;
+                    else if (i == p) a[j] = uj;
+                }
+            }
+            if (mine && i == p) a[p] = piv;
+        }
+    }
+    // ---- P (m x k), R (k x nc), S (nc x nc)
+    if (row) {
+        const int nc = m - k;
+        T* P = fac + fr.P_off;
+        T* R = fac + fr.R_off;
+        T* S = cbs + fr.S_off;
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            if (j < k) P[i + (int64_t)j * m] = a[j];
+            else if (j < m) {
+                if (i < k) R[i + (int64_t)(j - k) * k] = a[j];
+                else S[(i - k) + (int64_t)(j - k) * nc] = a[j];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Large fronts.  Assembly of 64x64 tiles straight into P, R and S; the
 // per-front max |entry| (for the static pivot threshold) by atomicMax on the
 // float bit pattern (non-negative floats order like their bits).

@@ -52,115 +52,197 @@ __device__ __forceinline__ T gather_rhs(const FrontDev& fr, const FrontDev* __re
     return v;
 }
 
+// Where row i of a front's right-hand side comes from: its own dof (pivot
+// rows) and the update-vector entries of the children that hold it.  Worked
+// out once per row and reused for every right-hand side.
+struct RhsSrc {
+    int64_t xi, v0, v1;  // -1 when absent
+};
+__device__ __forceinline__ RhsSrc rhs_src(const FrontDev& fr, const FrontDev* __restrict__ fronts,
+                                          const int32_t* __restrict__ fd, const int32_t* __restrict__ maps, int i) {
+    RhsSrc q{-1, -1, -1};
+    if (i < fr.k) q.xi = fd[i];
+    if (fr.nchild > 0) {
+        const int ic = maps[fr.map_off + i];
+        if (ic >= 0) q.v0 = fronts[fr.child[0]].vec_off + ic;
+    }
+    if (fr.nchild > 1) {
+        const int ic = maps[fr.map_off + fr.m + i];
+        if (ic >= 0) q.v1 = fronts[fr.child[1]].vec_off + ic;
+    }
+    return q;
+}
+template <typename T>
+__device__ __forceinline__ T rhs_val(const RhsSrc& q, const T* __restrict__ vr, const double* __restrict__ xr) {
+    T v = q.xi >= 0 ? (T)xr[q.xi] : T(0);
+    if (q.v0 >= 0) v += vr[q.v0];
+    if (q.v1 >= 0) v += vr[q.v1];
+    return v;
+}
+
+// Right-hand sides are processed in chunks inside one launch, so a front's
+// coefficients are loaded once per chunk: NR = 1 (single right-hand side,
+// fewest registers) or kRhsChunk.
+constexpr int kRhsChunk = 4;
+
+// y = w / d for one right-hand side, w * (1/d) for several (one reciprocal
+// per pivot shared by the chunk).
+template <typename T, int NR>
+__device__ __forceinline__ T pivot_scale(T d) {
+    return NR == 1 ? d : T(1) / d;
+}
+template <typename T, int NR>
+__device__ __forceinline__ T apply_pivot(T w, T ds) {
+    return NR == 1 ? w / ds : w * ds;
+}
+
 // Small fronts (m <= 64): one warp per front, rows lane and lane+32.
-template <typename T, bool TRANS>
-__global__ void __launch_bounds__(256, 4) k_fwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+template <typename T, bool TRANS, int NR>
+__global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_fwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                   int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                   const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
-                                                  double* __restrict__ x, int64_t n_dof) {
+                                                  double* __restrict__ x, int64_t n_dof, int nrhs) {
     const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (wid >= count) return;
-    const int r = blockIdx.y;
     const FrontDev fr = fronts[list[wid]];
     const int m = fr.m, k = fr.k;
     const int32_t* fd = dofs + fr.dof_off;
-    double* xr = x + (int64_t)r * n_dof;
-    T* vr = vecs + (int64_t)r * vec_size;
     const T* P = fac + fr.P_off;
     const T* R = fac + fr.R_off;
     const int i0 = lane, i1 = lane + 32;
-    T w0 = i0 < m ? gather_rhs<T>(fr, fronts, fd, maps, vr, xr, i0) : T(0);
-    T w1 = i1 < m ? gather_rhs<T>(fr, fronts, fd, maps, vr, xr, i1) : T(0);
-    for (int pc = 0; pc < k; pc += 8) {
-        T c0[8], c1[8], dg[8];
+    const RhsSrc s0 = i0 < m ? rhs_src(fr, fronts, fd, maps, i0) : RhsSrc{-1, -1, -1};
+    const RhsSrc s1 = i1 < m ? rhs_src(fr, fronts, fd, maps, i1) : RhsSrc{-1, -1, -1};
+    for (int rb = 0; rb < nrhs; rb += NR) {
+        const int nr = min(NR, nrhs - rb);
+        T w0[NR], w1[NR];
 #pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int p = pc + q;
-            c0[q] = (p < k && i0 > p && i0 < m) ? fcoef<T, TRANS>(P, R, m, k, i0, p) : T(0);
-            c1[q] = (p < k && i1 > p && i1 < m) ? fcoef<T, TRANS>(P, R, m, k, i1, p) : T(0);
-            dg[q] = p < k ? fdiag<T, TRANS>(P, m, p) : T(1);
-        }
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int p = pc + q;
-            if (p >= k) break;
-            T wp = (p < 32) ? __shfl_sync(0xffffffffu, w0, p) : __shfl_sync(0xffffffffu, w1, p - 32);
-            const T yp = wp / dg[q];
-            if (i0 == p) w0 = yp;
-            if (i1 == p) w1 = yp;
-            w0 -= c0[q] * yp;
-            w1 -= c1[q] * yp;
-        }
-    }
-    if (i0 < m) {
-        if (i0 < k) xr[fd[i0]] = (double)w0;
-        else vr[fr.vec_off + (i0 - k)] = w0;
-    }
-    if (i1 < m) {
-        if (i1 < k) xr[fd[i1]] = (double)w1;
-        else vr[fr.vec_off + (i1 - k)] = w1;
-    }
-}
-
-template <typename T, bool TRANS>
-__global__ void __launch_bounds__(256, 4) k_bwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
-                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
-                                                  double* __restrict__ x, int64_t n_dof) {
-    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (wid >= count) return;
-    const int r = blockIdx.y;
-    const FrontDev fr = fronts[list[wid]];
-    const int m = fr.m, k = fr.k;
-    const int32_t* fd = dofs + fr.dof_off;
-    double* xr = x + (int64_t)r * n_dof;
-    const T* P = fac + fr.P_off;
-    const T* R = fac + fr.R_off;
-    const int i0 = lane, i1 = lane + 32;
-    // all unknowns of the front: pivots hold y, CB holds the final x
-    T v0 = i0 < m ? (T)xr[fd[i0]] : T(0);
-    T v1 = i1 < m ? (T)xr[fd[i1]] : T(0);
-    // eliminate the CB unknowns from the pivot rows (j >= k), then back-substitute
-    for (int jc = m - 1; jc >= 0; jc -= 8) {
-        T c0[8], c1[8], dg[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int j = jc - q;
-            c0[q] = (j >= 0 && i0 < k && i0 < j) ? bcoef<T, TRANS>(P, R, m, k, i0, j) : T(0);
-            c1[q] = (j >= 0 && i1 < k && i1 < j) ? bcoef<T, TRANS>(P, R, m, k, i1, j) : T(0);
-            dg[q] = (j >= 0 && j < k) ? bdiag<T, TRANS>(P, m, j) : T(1);
-        }
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int j = jc - q;
-            if (j < 0) break;
-            T xj = (j < 32) ? __shfl_sync(0xffffffffu, v0, j) : __shfl_sync(0xffffffffu, v1, j - 32);
-            if (j < k) {
-                xj = xj / dg[q];
-                if (i0 == j) v0 = xj;
-                if (i1 == j) v1 = xj;
+        for (int rr = 0; rr < NR; rr++) {
+            w0[rr] = w1[rr] = T(0);
+            if (rr < nr) {
+                const double* xr = x + (int64_t)(rb + rr) * n_dof;
+                const T* vr = vecs + (int64_t)(rb + rr) * vec_size;
+                w0[rr] = rhs_val<T>(s0, vr, xr);
+                w1[rr] = rhs_val<T>(s1, vr, xr);
             }
-            v0 -= c0[q] * xj;
-            v1 -= c1[q] * xj;
+        }
+        for (int pc = 0; pc < k; pc += 8) {
+            T c0[8], c1[8], dg[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int p = pc + q;
+                c0[q] = (p < k && i0 > p && i0 < m) ? fcoef<T, TRANS>(P, R, m, k, i0, p) : T(0);
+                c1[q] = (p < k && i1 > p && i1 < m) ? fcoef<T, TRANS>(P, R, m, k, i1, p) : T(0);
+                dg[q] = p < k ? fdiag<T, TRANS>(P, m, p) : T(1);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int p = pc + q;
+                if (p >= k) break;
+                const T ds = pivot_scale<T, NR>(dg[q]);
+#pragma unroll
+                for (int rr = 0; rr < NR; rr++) {
+                    if (rr >= nr) break;
+                    T wp = (p < 32) ? __shfl_sync(0xffffffffu, w0[rr], p) : __shfl_sync(0xffffffffu, w1[rr], p - 32);
+                    const T yp = apply_pivot<T, NR>(wp, ds);
+                    if (i0 == p) w0[rr] = yp;
+                    if (i1 == p) w1[rr] = yp;
+                    w0[rr] -= c0[q] * yp;
+                    w1[rr] -= c1[q] * yp;
+                }
+            }
+        }
+#pragma unroll
+        for (int rr = 0; rr < NR; rr++) {
+            if (rr >= nr) break;
+            double* xr = x + (int64_t)(rb + rr) * n_dof;
+            T* vr = vecs + (int64_t)(rb + rr) * vec_size;
+            if (i0 < m) {
+                if (i0 < k) xr[fd[i0]] = (double)w0[rr];
+                else vr[fr.vec_off + (i0 - k)] = w0[rr];
+            }
+            if (i1 < m) {
+                if (i1 < k) xr[fd[i1]] = (double)w1[rr];
+                else vr[fr.vec_off + (i1 - k)] = w1[rr];
+            }
         }
     }
-    if (i0 < k) xr[fd[i0]] = (double)v0;
-    if (i1 < k) xr[fd[i1]] = (double)v1;
 }
 
-// Tiny fronts (m <= G, G in {4, 8, 16}): 32/G fronts per warp, one lane per
-// row, shuffles of width G; all coefficients are loaded before the short
-// sequential pivot loop.
-template <typename T, bool TRANS, int G>
+template <typename T, bool TRANS, int NR>
+__global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_bwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
+                                                  double* __restrict__ x, int64_t n_dof, int nrhs) {
+    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (wid >= count) return;
+    const FrontDev fr = fronts[list[wid]];
+    const int m = fr.m, k = fr.k;
+    const int32_t* fd = dofs + fr.dof_off;
+    const T* P = fac + fr.P_off;
+    const T* R = fac + fr.R_off;
+    const int i0 = lane, i1 = lane + 32;
+    const int d0 = i0 < m ? fd[i0] : 0, d1 = i1 < m ? fd[i1] : 0;
+    for (int rb = 0; rb < nrhs; rb += NR) {
+        const int nr = min(NR, nrhs - rb);
+        // all unknowns of the front: pivots hold y, CB holds the final x
+        T v0[NR], v1[NR];
+#pragma unroll
+        for (int rr = 0; rr < NR; rr++) {
+            const double* xr = x + (int64_t)(rb + rr) * n_dof;
+            v0[rr] = (rr < nr && i0 < m) ? (T)xr[d0] : T(0);
+            v1[rr] = (rr < nr && i1 < m) ? (T)xr[d1] : T(0);
+        }
+        // eliminate the CB unknowns from the pivot rows (j >= k), then back-substitute
+        for (int jc = m - 1; jc >= 0; jc -= 8) {
+            T c0[8], c1[8], dg[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int j = jc - q;
+                c0[q] = (j >= 0 && i0 < k && i0 < j) ? bcoef<T, TRANS>(P, R, m, k, i0, j) : T(0);
+                c1[q] = (j >= 0 && i1 < k && i1 < j) ? bcoef<T, TRANS>(P, R, m, k, i1, j) : T(0);
+                dg[q] = (j >= 0 && j < k) ? bdiag<T, TRANS>(P, m, j) : T(1);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int j = jc - q;
+                if (j < 0) break;
+                const T ds = pivot_scale<T, NR>(dg[q]);
+#pragma unroll
+                for (int rr = 0; rr < NR; rr++) {
+                    if (rr >= nr) break;
+                    T xj = (j < 32) ? __shfl_sync(0xffffffffu, v0[rr], j) : __shfl_sync(0xffffffffu, v1[rr], j - 32);
+                    if (j < k) {
+                        xj = apply_pivot<T, NR>(xj, ds);
+                        if (i0 == j) v0[rr] = xj;
+                        if (i1 == j) v1[rr] = xj;
+                    }
+                    v0[rr] -= c0[q] * xj;
+                    v1[rr] -= c1[q] * xj;
+                }
+            }
+        }
+#pragma unroll
+        for (int rr = 0; rr < NR; rr++) {
+            if (rr >= nr) break;
+            double* xr = x + (int64_t)(rb + rr) * n_dof;
+            if (i0 < k) xr[d0] = (double)v0[rr];
+            if (i1 < k) xr[d1] = (double)v1[rr];
+        }
+    }
+}
+
+// Tiny fronts (m <= G, G in {4, 8, 16, 32}): 32/G fronts per warp, one lane
+// per row, shuffles of width G; all coefficients are loaded once, before the
+// short sequential pivot loop.
+template <typename T, bool TRANS, int G, int NR>
 __global__ void __launch_bounds__(256) k_fwd_grp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
-                                                 double* __restrict__ x, int64_t n_dof) {
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs) {
     const int lane = threadIdx.x & 31;
     const int fidx = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
     const bool active = fidx < count;
-    const int r = blockIdx.y;
     const int i = lane % G;
     FrontDev fr{};
     int m = 0, k = 0;
@@ -170,8 +252,6 @@ __global__ void __launch_bounds__(256) k_fwd_grp(const FrontDev* __restrict__ fr
         k = fr.k;
     }
     const int32_t* fd = dofs + fr.dof_off;
-    double* xr = x + (int64_t)r * n_dof;
-    T* vr = vecs + (int64_t)r * vec_size;
     const T* P = fac + fr.P_off;
     const T* R = fac + fr.R_off;
     T c[G], dg[G];
@@ -180,32 +260,46 @@ __global__ void __launch_bounds__(256) k_fwd_grp(const FrontDev* __restrict__ fr
         c[p] = (p < k && i > p && i < m) ? fcoef<T, TRANS>(P, R, m, k, i, p) : T(0);
         dg[p] = p < k ? fdiag<T, TRANS>(P, m, p) : T(1);
     }
-    T w = (active && i < m) ? gather_rhs<T>(fr, fronts, fd, maps, vr, xr, i) : T(0);
+    const RhsSrc src = (active && i < m) ? rhs_src(fr, fronts, fd, maps, i) : RhsSrc{-1, -1, -1};
     const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)k);  // warp-uniform pivot count
+    for (int rb = 0; rb < nrhs; rb += NR) {
+        const int nr = min(NR, nrhs - rb);
+        T w[NR];
 #pragma unroll
-    for (int p = 0; p < G; p++) {
-        if (p < kmax) {
-            const T yp = __shfl_sync(0xffffffffu, w, p, G) / dg[p];
-            if (p < k) {
-                if (i == p) w = yp;
-                w -= c[p] * yp;
+        for (int rr = 0; rr < NR; rr++)
+            w[rr] = rr < nr ? rhs_val<T>(src, vecs + (int64_t)(rb + rr) * vec_size, x + (int64_t)(rb + rr) * n_dof) : T(0);
+#pragma unroll
+        for (int p = 0; p < G; p++) {
+            if (p < kmax) {
+                const T ds = pivot_scale<T, NR>(dg[p]);
+#pragma unroll
+                for (int rr = 0; rr < NR; rr++) {
+                    const T yp = apply_pivot<T, NR>(__shfl_sync(0xffffffffu, w[rr], p, G), ds);
+                    if (p < k) {
+                        if (i == p) w[rr] = yp;
+                        w[rr] -= c[p] * yp;
+                    }
+                }
+            }
+        }
+        if (active && i < m) {
+#pragma unroll
+            for (int rr = 0; rr < NR; rr++) {
+                if (rr >= nr) break;
+                if (i < k) x[(int64_t)(rb + rr) * n_dof + src.xi] = (double)w[rr];
+                else vecs[(int64_t)(rb + rr) * vec_size + fr.vec_off + (i - k)] = w[rr];
             }
         }
     }
-    if (active && i < m) {
-        if (i < k) xr[fd[i]] = (double)w;
-        else vr[fr.vec_off + (i - k)] = w;
-    }
 }
 
-template <typename T, bool TRANS, int G>
+template <typename T, bool TRANS, int G, int NR>
 __global__ void __launch_bounds__(256) k_bwd_grp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
-                                                 double* __restrict__ x, int64_t n_dof) {
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs) {
     const int lane = threadIdx.x & 31;
     const int fidx = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
     const bool active = fidx < count;
-    const int r = blockIdx.y;
     const int i = lane % G;
     FrontDev fr{};
     int m = 0, k = 0;
@@ -215,7 +309,6 @@ __global__ void __launch_bounds__(256) k_bwd_grp(const FrontDev* __restrict__ fr
         k = fr.k;
     }
     const int32_t* fd = dofs + fr.dof_off;
-    double* xr = x + (int64_t)r * n_dof;
     const T* P = fac + fr.P_off;
     const T* R = fac + fr.R_off;
     T c[G], dg[G];
@@ -224,169 +317,226 @@ __global__ void __launch_bounds__(256) k_bwd_grp(const FrontDev* __restrict__ fr
         c[j] = (j < m && i < k && i < j) ? bcoef<T, TRANS>(P, R, m, k, i, j) : T(0);
         dg[j] = j < k ? bdiag<T, TRANS>(P, m, j) : T(1);
     }
-    T v = (active && i < m) ? (T)xr[fd[i]] : T(0);
+    const int di = (active && i < m) ? fd[i] : 0;
     const int mmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);  // warp-uniform front size
+    for (int rb = 0; rb < nrhs; rb += NR) {
+        const int nr = min(NR, nrhs - rb);
+        T v[NR];
 #pragma unroll
-    for (int j = G - 1; j >= 0; j--) {
-        if (j >= mmax) continue;
-        T xj = __shfl_sync(0xffffffffu, v, j, G);
-        if (j < k) {
-            xj = xj / dg[j];
-            if (i == j) v = xj;
+        for (int rr = 0; rr < NR; rr++) v[rr] = (rr < nr && active && i < m) ? (T)x[(int64_t)(rb + rr) * n_dof + di] : T(0);
+#pragma unroll
+        for (int j = G - 1; j >= 0; j--) {
+            if (j >= mmax) continue;
+            const T ds = pivot_scale<T, NR>(dg[j]);
+#pragma unroll
+            for (int rr = 0; rr < NR; rr++) {
+                T xj = __shfl_sync(0xffffffffu, v[rr], j, G);
+                if (j < k) {
+                    xj = apply_pivot<T, NR>(xj, ds);
+                    if (i == j) v[rr] = xj;
+                }
+                v[rr] -= c[j] * xj;
+            }
         }
-        v -= c[j] * xj;
+        if (active && i < k) {
+#pragma unroll
+            for (int rr = 0; rr < NR; rr++)
+                if (rr < nr) x[(int64_t)(rb + rr) * n_dof + di] = (double)v[rr];
+        }
     }
-    if (active && i < k) xr[fd[i]] = (double)v;
 }
 
 // Mid-size fronts (m > 64, k < kInvMinK): one CTA per front.  The pivot block
 // is processed in 32-wide blocks; each 32x32 diagonal block is staged in
-// shared memory by all threads, solved by warp 0, then applied to the later
-// rows, including the contribution-block rows (update vector).
+// shared memory by all threads, solved by one warp per right-hand side, then
+// applied to the later rows, including the contribution-block rows (update
+// vector).  Shared memory: 32 x 33 T + kRhsChunk x ldw T (ldw >= m).
 template <typename T, bool TRANS>
 __global__ void __launch_bounds__(256) k_fwd_cta(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                  int rows_all, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
-                                                 double* __restrict__ x, int64_t n_dof) {
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int ldw) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* Dg = reinterpret_cast<T*>(smem_raw);  // 32 x 33
-    T* w = Dg + 32 * 33;
-    const int r = blockIdx.y;
+    T* w = Dg + 32 * 33;                     // kRhsChunk x ldw
     const FrontDev fr = fronts[list[blockIdx.x]];
     const int m = fr.m, k = fr.k;
     const int mr = rows_all ? m : k;
     const int32_t* fd = dofs + fr.dof_off;
-    double* xr = x + (int64_t)r * n_dof;
-    T* vr = vecs + (int64_t)r * vec_size;
     const T* P = fac + fr.P_off;
     const T* R = fac + fr.R_off;
-    for (int i = threadIdx.x; i < mr; i += blockDim.x) w[i] = gather_rhs<T>(fr, fronts, fd, maps, vr, xr, i);
-    const int lane = threadIdx.x & 31;
-    for (int pb = 0; pb < k; pb += 32) {
-        const int wb = min(32, k - pb);
-        {
-            T v[4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int rb = 0; rb < nrhs; rb += kRhsChunk) {
+        const int nr = min(kRhsChunk, nrhs - rb);
+        for (int i = threadIdx.x; i < mr; i += blockDim.x) {
+            const RhsSrc src = rhs_src(fr, fronts, fd, maps, i);
+            for (int rr = 0; rr < nr; rr++)
+                w[rr * ldw + i] = rhs_val<T>(src, vecs + (int64_t)(rb + rr) * vec_size, x + (int64_t)(rb + rr) * n_dof);
+        }
+        for (int pb = 0; pb < k; pb += 32) {
+            const int wb = min(32, k - pb);
+            {
+                T v[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int idx = threadIdx.x + 256 * q, i = idx & 31, p = idx >> 5;  // row pb+i, pivot pb+p
-                v[q] = T(0);
-                if (i < wb && p < wb) v[q] = (i > p) ? fcoef<T, TRANS>(P, R, m, k, pb + i, pb + p)
-                                                     : (i == p ? fdiag<T, TRANS>(P, m, pb + p) : T(0));
-            }
+                for (int q = 0; q < 4; q++) {
+                    const int idx = threadIdx.x + 256 * q, i = idx & 31, p = idx >> 5;  // row pb+i, pivot pb+p
+                    v[q] = T(0);
+                    if (i < wb && p < wb) v[q] = (i > p) ? fcoef<T, TRANS>(P, R, m, k, pb + i, pb + p)
+                                                         : (i == p ? fdiag<T, TRANS>(P, m, pb + p) : T(0));
+                }
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int idx = threadIdx.x + 256 * q;
-                Dg[(idx & 31) * 33 + (idx >> 5)] = v[q];
+                for (int q = 0; q < 4; q++) {
+                    const int idx = threadIdx.x + 256 * q;
+                    Dg[(idx & 31) * 33 + (idx >> 5)] = v[q];
+                }
             }
-        }
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            T val = lane < wb ? w[pb + lane] : T(0);
-            for (int p = 0; p < wb; p++) {
-                T yp = __shfl_sync(0xffffffffu, val, p) / Dg[p * 33 + p];
-                if (lane == p) val = yp;
-                if (lane > p) val -= Dg[lane * 33 + p] * yp;
+            __syncthreads();
+            if (warp < nr) {  // warp rr solves right-hand side rr
+                T* wr = w + warp * ldw;
+                T val = lane < wb ? wr[pb + lane] : T(0);
+                for (int p = 0; p < wb; p++) {
+                    T yp = __shfl_sync(0xffffffffu, val, p) / Dg[p * 33 + p];
+                    if (lane == p) val = yp;
+                    if (lane > p) val -= Dg[lane * 33 + p] * yp;
+                }
+                if (lane < wb) wr[pb + lane] = val;
             }
-            if (lane < wb) w[pb + lane] = val;
+            __syncthreads();
+            for (int i = pb + wb + threadIdx.x; i < mr; i += blockDim.x) {
+                T acc[kRhsChunk];
+#pragma unroll
+                for (int rr = 0; rr < kRhsChunk; rr++) acc[rr] = T(0);
+#pragma unroll 4
+                for (int p = 0; p < wb; p++) {
+                    const T cf = fcoef<T, TRANS>(P, R, m, k, i, pb + p);
+#pragma unroll
+                    for (int rr = 0; rr < kRhsChunk; rr++)
+                        if (rr < nr) acc[rr] += cf * w[rr * ldw + pb + p];
+                }
+#pragma unroll
+                for (int rr = 0; rr < kRhsChunk; rr++)
+                    if (rr < nr) w[rr * ldw + i] -= acc[rr];
+            }
+            __syncthreads();
         }
+        for (int i = threadIdx.x; i < mr; i += blockDim.x)
+            for (int rr = 0; rr < nr; rr++) {
+                if (i < k) x[(int64_t)(rb + rr) * n_dof + fd[i]] = (double)w[rr * ldw + i];
+                else vecs[(int64_t)(rb + rr) * vec_size + fr.vec_off + (i - k)] = w[rr * ldw + i];
+            }
         __syncthreads();
-        for (int i = pb + wb + threadIdx.x; i < mr; i += blockDim.x) {
-            T acc = T(0);
-#pragma unroll 8
-            for (int p = 0; p < wb; p++) acc += fcoef<T, TRANS>(P, R, m, k, i, pb + p) * w[pb + p];
-            w[i] -= acc;
-        }
-        __syncthreads();
-    }
-    for (int i = threadIdx.x; i < mr; i += blockDim.x) {
-        if (i < k) xr[fd[i]] = (double)w[i];
-        else vr[fr.vec_off + (i - k)] = w[i];
     }
 }
 
 // Backward, one CTA per mid-size front: the CB part of the pivot rows first,
 // then the unit (or, transposed, L11^T) triangle in 32-wide blocks.
+// Shared memory: 32 x 33 T + 8 x 64 x kRhsChunk T + kRhsChunk x ldw T.
 template <typename T, bool TRANS>
 __global__ void __launch_bounds__(256) k_bwd_cta(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                  int cb_done, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
-                                                 double* __restrict__ x, int64_t n_dof) {
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int ldw) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* Dg = reinterpret_cast<T*>(smem_raw);
-    T* v = Dg + 32 * 33;
-    const int r = blockIdx.y;
+    T* red = Dg + 32 * 33;                // 8 warps x 64 rows x kRhsChunk
+    T* v = red + 8 * 64 * kRhsChunk;      // kRhsChunk x ldw
     const FrontDev fr = fronts[list[blockIdx.x]];
     const int m = fr.m, k = fr.k;
     const int32_t* fd = dofs + fr.dof_off;
-    double* xr = x + (int64_t)r * n_dof;
     const T* P = fac + fr.P_off;
     const T* R = fac + fr.R_off;
     const int mv = cb_done ? k : m;
-    for (int i = threadIdx.x; i < mv; i += blockDim.x) v[i] = (T)xr[fd[i]];
-    __syncthreads();
-    if (!cb_done) {
-        // pivot rows (lane, lane + 32; k < 64) minus their CB part; the 8 warps split the columns
-        T* red = Dg;  // reused: 8 x 64 partial sums fit the 32 x 33 staging area
-        const int lane0 = threadIdx.x & 31, w0 = threadIdx.x >> 5;
-        T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
-        const int i0 = lane0, i1 = lane0 + 32;
-        int j = k + w0;
-        for (; j + 8 < m; j += 16) {
-            const T x0 = v[j], x1 = v[j + 8];
-            if (i0 < k) { a0 += bcoef<T, TRANS>(P, R, m, k, i0, j) * x0; b0 += bcoef<T, TRANS>(P, R, m, k, i0, j + 8) * x1; }
-            if (i1 < k) { a1 += bcoef<T, TRANS>(P, R, m, k, i1, j) * x0; b1 += bcoef<T, TRANS>(P, R, m, k, i1, j + 8) * x1; }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int rb = 0; rb < nrhs; rb += kRhsChunk) {
+        const int nr = min(kRhsChunk, nrhs - rb);
+        for (int i = threadIdx.x; i < mv; i += blockDim.x) {
+            const int d = fd[i];
+            for (int rr = 0; rr < nr; rr++) v[rr * ldw + i] = (T)x[(int64_t)(rb + rr) * n_dof + d];
         }
-        for (; j < m; j += 8) {
-            if (i0 < k) a0 += bcoef<T, TRANS>(P, R, m, k, i0, j) * v[j];
-            if (i1 < k) a1 += bcoef<T, TRANS>(P, R, m, k, i1, j) * v[j];
-        }
-        red[w0 * 64 + i0] = a0 + b0;
-        red[w0 * 64 + i1] = a1 + b1;
         __syncthreads();
+        if (!cb_done) {
+            // pivot rows (lane, lane + 32; k < 64) minus their CB part; the 8 warps split the columns
+            const int i0 = lane, i1 = lane + 32;
+            T a0[kRhsChunk], a1[kRhsChunk];
+#pragma unroll
+            for (int rr = 0; rr < kRhsChunk; rr++) a0[rr] = a1[rr] = T(0);
+            for (int j = k + warp; j < m; j += 8) {
+                const T c0 = i0 < k ? bcoef<T, TRANS>(P, R, m, k, i0, j) : T(0);
+                const T c1 = i1 < k ? bcoef<T, TRANS>(P, R, m, k, i1, j) : T(0);
+#pragma unroll
+                for (int rr = 0; rr < kRhsChunk; rr++) {
+                    if (rr < nr) {
+                        const T xj = v[rr * ldw + j];
+                        a0[rr] += c0 * xj;
+                        a1[rr] += c1 * xj;
+                    }
+                }
+            }
+#pragma unroll
+            for (int rr = 0; rr < kRhsChunk; rr++) {
+                red[(rr * 8 + warp) * 64 + i0] = a0[rr];
+                red[(rr * 8 + warp) * 64 + i1] = a1[rr];
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < k; i += blockDim.x)
+                for (int rr = 0; rr < nr; rr++) {
+                    T acc = T(0);
+                    for (int w = 0; w < 8; w++) acc += red[(rr * 8 + w) * 64 + i];
+                    v[rr * ldw + i] -= acc;
+                }
+            __syncthreads();
+        }
+        for (int pe = k; pe > 0; pe -= 32) {
+            const int pb = max(0, pe - 32), wb = pe - pb;
+            {
+                T t[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int idx = threadIdx.x + 256 * q, i = idx & 31, j = idx >> 5;  // row pb+i, unknown pb+j
+                    t[q] = T(0);
+                    if (i < wb && j < wb) t[q] = (i < j) ? bcoef<T, TRANS>(P, R, m, k, pb + i, pb + j)
+                                                         : (i == j ? bdiag<T, TRANS>(P, m, pb + j) : T(0));
+                }
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int idx = threadIdx.x + 256 * q;
+                    Dg[(idx & 31) * 33 + (idx >> 5)] = t[q];
+                }
+            }
+            __syncthreads();
+            if (warp < nr) {
+                T* vr = v + warp * ldw;
+                T val = lane < wb ? vr[pb + lane] : T(0);
+                for (int j = wb - 1; j >= 0; j--) {
+                    T xj = __shfl_sync(0xffffffffu, val, j) / Dg[j * 33 + j];
+                    if (lane == j) val = xj;
+                    if (lane < j) val -= Dg[lane * 33 + j] * xj;
+                }
+                if (lane < wb) vr[pb + lane] = val;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < pb; i += blockDim.x) {
+                T acc[kRhsChunk];
+#pragma unroll
+                for (int rr = 0; rr < kRhsChunk; rr++) acc[rr] = T(0);
+#pragma unroll 4
+                for (int j = 0; j < wb; j++) {
+                    const T cf = bcoef<T, TRANS>(P, R, m, k, i, pb + j);
+#pragma unroll
+                    for (int rr = 0; rr < kRhsChunk; rr++)
+                        if (rr < nr) acc[rr] += cf * v[rr * ldw + pb + j];
+                }
+#pragma unroll
+                for (int rr = 0; rr < kRhsChunk; rr++)
+                    if (rr < nr) v[rr * ldw + i] -= acc[rr];
+            }
+            __syncthreads();
+        }
         for (int i = threadIdx.x; i < k; i += blockDim.x) {
-            T acc = T(0);
-            for (int w = 0; w < 8; w++) acc += red[w * 64 + i];
-            v[i] -= acc;
+            const int d = fd[i];
+            for (int rr = 0; rr < nr; rr++) x[(int64_t)(rb + rr) * n_dof + d] = (double)v[rr * ldw + i];
         }
         __syncthreads();
     }
-    const int lane = threadIdx.x & 31;
-    for (int pe = k; pe > 0; pe -= 32) {
-        const int pb = max(0, pe - 32), wb = pe - pb;
-        {
-            T v[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int idx = threadIdx.x + 256 * q, i = idx & 31, j = idx >> 5;  // row pb+i, unknown pb+j
-                v[q] = T(0);
-                if (i < wb && j < wb) v[q] = (i < j) ? bcoef<T, TRANS>(P, R, m, k, pb + i, pb + j)
-                                                     : (i == j ? bdiag<T, TRANS>(P, m, pb + j) : T(0));
-            }
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int idx = threadIdx.x + 256 * q;
-                Dg[(idx & 31) * 33 + (idx >> 5)] = v[q];
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            T val = lane < wb ? v[pb + lane] : T(0);
-            for (int j = wb - 1; j >= 0; j--) {
-                T xj = __shfl_sync(0xffffffffu, val, j) / Dg[j * 33 + j];
-                if (lane == j) val = xj;
-                if (lane < j) val -= Dg[lane * 33 + j] * xj;
-            }
-            if (lane < wb) v[pb + lane] = val;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < pb; i += blockDim.x) {
-            T acc = T(0);
-#pragma unroll 8
-            for (int j = 0; j < wb; j++) acc += bcoef<T, TRANS>(P, R, m, k, i, pb + j) * v[pb + j];
-            v[i] -= acc;
-        }
-        __syncthreads();
-    }
-    for (int i = threadIdx.x; i < k; i += blockDim.x) xr[fd[i]] = (double)v[i];
 }
 
 // ---------------------------------------------------------------------------
