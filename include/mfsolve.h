@@ -78,7 +78,7 @@ typedef struct {
                              subtree with a block barrier between them): n > 0 = at most n
                              (fewer if a subtree would not fit shared memory); <= 0 = off */
     int tc_min_cb;        /* MF_TF32: smallest contribution block (m - k) whose Schur update runs
-                             on the tensor cores; smaller ones use the SIMT GEMM; 0 = 96 */
+                             on the tensor cores; smaller ones use the SIMT GEMM; 0 = 256 */
     int fused_threads[MF_FUSED_BUCKETS];
                           /* threads per CTA of the fused small-front kernel for each front-size
                              bucket (m <= 16, 32, 48, 64, 96, 128, 160, 192, 224): 32, 64, 128 or
@@ -245,7 +245,8 @@ int mf_profile_read(mf_factors* f, double* ms, int64_t* launches, double* bytes,
  * (a factorization launch, or all kernels of one class of a substitution),
  * in issue order.  kind: 0 fused small fronts, 1 large-front assembly,
  * 2 panel diagonal block, 3 SIMT GEMM, 4 pivot-block inverses, 5 subtree
- * factorization, 6 tensor-core GEMM, 7 lane-group tiny fronts, or one of the
+ * factorization, 6 tensor-core GEMM, 7 lane-group tiny fronts, 8 tensor-core
+ * operand packing, or one of the
  * MF_TRACE_* codes below;
  * cls: 0-based Foata class or -1; tasks: fronts, tiles or tasks in the launch.
  * Call before mf_profile_read (which clears the trace).  Writes at most `cap`

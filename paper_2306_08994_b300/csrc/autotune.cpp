@@ -29,6 +29,10 @@ struct Timer {
     }
 };
 
+// Version of the launch-plan builder: bumped whenever its kernels or its
+// decomposition change enough that plans tuned before are stale.
+constexpr int kPlanVersion = 2;
+
 int family_of(int precision) { return precision == MF_F64 ? 0 : 1; }
 
 std::string cache_key(const mf_analysis* a, int precision) {
@@ -40,8 +44,8 @@ std::string cache_key(const mf_analysis* a, int precision) {
     for (char& c : name)
         if (c == '"' || c == '\\' || c == ':') c = '_';
     char buf[512];
-    std::snprintf(buf, sizeof buf, "%s:sm%d:%s:dim%d:npe%d:meshes%d:n%lld:fronts%d:classes%d:maxm%d:maxk%d:flops%.6e",
-                  name.c_str(), p.multiProcessorCount, family_of(precision) == 0 ? "f64" : "f32", a->dim, a->npe,
+    std::snprintf(buf, sizeof buf, "plan%d:%s:sm%d:%s:dim%d:npe%d:meshes%d:n%lld:fronts%d:classes%d:maxm%d:maxk%d:flops%.6e",
+                  kPlanVersion, name.c_str(), p.multiProcessorCount, family_of(precision) == 0 ? "f64" : "f32", a->dim, a->npe,
                   a->n_meshes, (long long)a->n_dof, a->n_front, a->n_cls, a->info.max_m, a->info.max_k,
                   a->info.factor_flops);
     return buf;
@@ -264,9 +268,9 @@ extern "C" int mf_autotune(const mf_analysis* a, const double* d_values, const d
         const mf_options start = cur;
         mf_options t = start;
         t.precision = start.precision == MF_F32 ? MF_TF32 : MF_F32;
-        if (t.precision == MF_TF32) t.tc_min_cb = 96;
+        if (t.precision == MF_TF32) t.tc_min_cb = 128;
         try_one(t);
-        for (int tmin : {192, 384, 768}) {
+        for (int tmin : {256, 512, 1024}) {
             if (rc) break;
             mf_options u = start;
             u.precision = MF_TF32;

@@ -17,7 +17,8 @@
 
 namespace {
 
-enum LaunchKind { K_FUSED = 0, K_ASM = 1, K_PDIAG = 2, K_GEMM = 3, K_INVDIAG = 4, K_SUBTREE = 5, K_GEMMTC = 6, K_GRP = 7 };
+enum LaunchKind { K_FUSED = 0, K_ASM = 1, K_PDIAG = 2, K_GEMM = 3, K_INVDIAG = 4, K_SUBTREE = 5, K_GEMMTC = 6, K_GRP = 7,
+                  K_TCPACK = 8 };
 
 struct Launch {
     int kind;
@@ -72,6 +73,7 @@ int upload(T** p, const std::vector<T>& v) {
 
 constexpr int kPanelNB64 = 32;  // panel width (pivot block of a step), FP64
 constexpr int kPanelNB32 = 64;  // FP32
+constexpr int kSuperPanel = 256;  // pivots per super-panel of the large-front partial LU
 
 __global__ void k_init_status(DevStatus* st) {
     st->n_perturbed = 0ull;
@@ -226,7 +228,11 @@ struct mf_factors {
     void* d_pnl = nullptr;
     int64_t pnl_size = 64 * 64;
     GemmTile* d_gemm = nullptr;
-    GemmTile* d_gtc = nullptr;  // tensor-core (128 x 128) Schur tiles
+    TcTile* d_gtc = nullptr;    // tensor-core (128 x 256) Schur tiles
+    TcPack* d_tcpack = nullptr;  // per tensor-core front: packed operand offsets
+    TcPackJob* d_tcjob = nullptr;
+    float* d_pk = nullptr;       // packed hi/lo operands of one class (reused class by class)
+    int64_t pk_size = 0;
     unsigned int* d_famax = nullptr;
     DevStatus* d_status = nullptr;
     double *d_r = nullptr, *d_d = nullptr, *d_Y = nullptr, *d_rowabs = nullptr, *d_part = nullptr, *d_norms = nullptr;
@@ -303,7 +309,7 @@ static void free_factors(mf_factors* f) {
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
-                    f->d_vec, f->d_flist, f->d_slist, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_famax, f->d_status,
+                    f->d_vec, f->d_flist, f->d_slist, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_famax, f->d_status,
                     f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -390,7 +396,10 @@ static int build_plan(mf_factors* F) {
     std::vector<InvTask> invt;
     std::vector<AsmTile> asmt;
     std::vector<DiagTask> pan;
-    std::vector<GemmTile> gem, gtc;
+    std::vector<GemmTile> gem;
+    std::vector<TcTile> gtc;
+    std::vector<TcPack> tcp;
+    std::vector<TcPackJob> tcj;
     const int* bounds = kFusedBounds;
     const int nbounds = F->prec == MF_F64 ? kFusedBuckets64 : MF_FUSED_BUCKETS;
     const int nb = F->nb;
@@ -420,6 +429,72 @@ static int build_plan(mf_factors* F) {
                 t.a_ar = AR_FAC; t.b_ar = AR_FAC; t.c_ar = c_in_cb ? AR_CB : AR_FAC; t.op = 0;
                 gem.push_back(t);
             }
+    };
+    // Tensor-core products (MF_TF32): C -= A B with min(M, N) >= tc_min, collected per phase
+    // (a trailing step, a Schur update), then one pack launch and one GEMM launch per phase.
+    struct TcC {
+        int8_t car, op;
+        int64_t coff;
+        int ldc;
+    };
+    std::vector<TcC> tcc;
+    int64_t tc_hi = 0;
+    size_t tc_p0 = 0;
+    double tc_pb = 0, tc_gb = 0, tc_gf = 0;
+    auto use_tc = [&](int M, int N, int K) { return F->prec == MF_TF32 && std::min(M, N) >= F->tc_min && K >= 16; };
+    auto tc_add = [&](int8_t aar, int64_t aoff, int lda, int8_t bar, int64_t boff, int ldb, int8_t car, int64_t coff,
+                      int ldc, int M, int N, int K, int8_t op = 0, int8_t am = 0, int8_t bm = 0) {
+        TcPack q{};
+        q.a_ar = aar; q.a_off = aoff; q.lda = lda; q.a_mask = am;
+        q.b_ar = bar; q.b_off = boff; q.ldb = ldb; q.b_mask = bm;
+        q.M = M; q.N = N; q.K = K;
+        q.nkc = (K + tc::kChunkK - 1) / tc::kChunkK;
+        const int nra = (M + tc::kTileM - 1) / tc::kTileM, nrb = (N + tc::kTileN - 1) / tc::kTileN;
+        q.a_hi = tc_hi;
+        tc_hi += (int64_t)nra * q.nkc * tc::kChunkA;
+        q.b_hi = tc_hi;
+        tc_hi += (int64_t)nrb * q.nkc * tc::kChunkB;
+        tcp.push_back(q);
+        tcc.push_back({car, op, coff, ldc});
+        tc_gf += 2.0 * M * N * K;
+        tc_gb += T * ((double)M * K + (double)K * N + 2.0 * M * N);
+        tc_pb += T * ((double)M * K + (double)K * N) + 2.0 * 4.0 * ((double)nra * tc::kChunkA + (double)nrb * tc::kChunkB) * q.nkc;
+    };
+    auto tc_end = [&](int c, int fam) {
+        if (tcp.size() > tc_p0) {
+            const int64_t joff = (int64_t)tcj.size(), toff = (int64_t)gtc.size();
+            for (size_t qi = tc_p0; qi < tcp.size(); qi++) {
+                TcPack& q = tcp[qi];
+                q.lo_off = tc_hi;
+                const int nra = (q.M + tc::kTileM - 1) / tc::kTileM, nrb = (q.N + tc::kTileN - 1) / tc::kTileN;
+                for (int rt = 0; rt < nra; rt++)
+                    for (int kc = 0; kc < q.nkc; kc++) tcj.push_back({(int32_t)(qi - tc_p0), 0, rt, kc});
+                for (int rt = 0; rt < nrb; rt++)
+                    for (int kc = 0; kc < q.nkc; kc++) tcj.push_back({(int32_t)(qi - tc_p0), 1, rt, kc});
+                for (int rb = 0; rb < nrb; rb++)
+                    for (int ra = 0; ra < nra; ra++) {
+                        TcTile t{};
+                        t.a_hi = q.a_hi + (int64_t)ra * q.nkc * tc::kChunkA;
+                        t.b_hi = q.b_hi + (int64_t)rb * q.nkc * tc::kChunkB;
+                        t.lo_off = q.lo_off;
+                        const int i0 = ra * tc::kTileM, j0 = rb * tc::kTileN;
+                        t.c_ar = tcc[qi].car;
+                        t.op = tcc[qi].op;
+                        t.c_off = tcc[qi].coff + i0 + (int64_t)j0 * tcc[qi].ldc;
+                        t.ldc = tcc[qi].ldc;
+                        t.mrows = std::min(tc::kTileM, q.M - i0);
+                        t.ncols = std::min(tc::kTileN, q.N - j0);
+                        t.nkc = q.nkc;
+                        gtc.push_back(t);
+                    }
+            }
+            F->pk_size = std::max(F->pk_size, 2 * tc_hi);
+            push({K_TCPACK, c, (int)(tcj.size() - joff), 0, joff, (int)tc_p0}, fam, tc_pb, 0.0);
+            push({K_GEMMTC, c, (int)(gtc.size() - toff), 0, toff}, fam, tc_gb, tc_gf);
+        }
+        tc_hi = 0;
+        tc_p0 = tcp.size();
+        tc_pb = tc_gb = tc_gf = 0;
     };
     // subtree fusion of the bottom classes
     {
@@ -600,7 +675,38 @@ static int build_plan(mf_factors* F) {
             gf += 2.0 * M * N * K;
             gb += T * ((double)M * K + (double)K * N + 2.0 * M * N);
         };
+        // Pivot blocks in super-panels of kSuperPanel pivots (Crout-style inside, right-looking
+        // across): a panel is brought up to date with the pivots of its super-panel just before
+        // it is factored (thin strip products), and the rest of the pivot rows and columns takes
+        // the whole super-panel in one product of depth kSuperPanel at its end.
+        const int SP = kSuperPanel;
+        auto any_gemm = [&](int64_t ao, int lda, int64_t bo, int ldb, int8_t car, int64_t co, int ldc, int M, int N,
+                            int K) {
+            if (M <= 0 || N <= 0 || K <= 0) return;
+            if (use_tc(M, N, K)) tc_add(AR_FAC, ao, lda, AR_FAC, bo, ldb, car, co, ldc, M, N, K);
+            else gemm_tiles(ao, lda, bo, ldb, co, ldc, M, N, K, car == AR_CB);
+        };
         for (int kb = 0; kb < maxk; kb += nb) {
+            const int s0 = (kb / SP) * SP;
+            // (0) strips: panel kb (its columns from row kb down, its rows right of it) minus the
+            //     products of this super-panel's earlier pivots s0..kb-1
+            if (kb > s0) {
+                int64_t soff = (int64_t)gem.size();
+                gb = gf = 0;
+                for (int32_t f : big) {
+                    const FrontDev& fr = a->fronts[f];
+                    if (kb >= fr.k) continue;
+                    const int m = fr.m, k = fr.k, w = std::min(nb, k - kb), K0 = kb - s0;
+                    const int64_t Lrow = fr.P_off + kb + (int64_t)s0 * m;  // L[kb.., s0..kb)
+                    gemm_tiles(Lrow, m, fr.P_off + s0 + (int64_t)kb * m, m, fr.P_off + kb + (int64_t)kb * m, m, m - kb, w,
+                               K0, 0);
+                    if (k - kb - w > 0)
+                        gemm_tiles(Lrow, m, fr.P_off + s0 + (int64_t)(kb + w) * m, m, fr.P_off + kb + (int64_t)(kb + w) * m, m,
+                                   w, k - kb - w, K0, 0);
+                    if (m - k > 0) gemm_tiles(Lrow, m, fr.R_off + s0, k, fr.R_off + kb, k, w, m - k, K0, 0);
+                }
+                if (gem.size() > (size_t)soff) push({K_GEMM, c, (int)(gem.size() - soff), 0, soff}, FAM_TRAIL, gb, gf);
+            }
             // (A) diagonal blocks: factor + invert, one warp per front
             int64_t poff = (int64_t)pan.size();
             double pb = 0, pf = 0;
@@ -635,48 +741,37 @@ static int build_plan(mf_factors* F) {
                 }
             }
             if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_PANEL, gb, gf);
-            // (C) trailing updates restricted to the pivot rows/columns
-            goff = (int64_t)gem.size();
-            gb = gf = 0;
-            for (int32_t f : big) {
-                const FrontDev& fr = a->fronts[f];
-                if (kb >= fr.k) continue;
-                const int m = fr.m, k = fr.k, w = std::min(nb, k - kb), r0 = kb + w;
-                if (m - r0 > 0 && k - r0 > 0)
-                    gemm_tiles(fr.P_off + r0 + (int64_t)kb * m, m, fr.P_off + kb + (int64_t)r0 * m, m,
-                               fr.P_off + r0 + (int64_t)r0 * m, m, m - r0, k - r0, w, 0);
-                if (k - r0 > 0 && m - k > 0)
-                    gemm_tiles(fr.P_off + r0 + (int64_t)kb * m, m, fr.R_off + kb, k, fr.R_off + r0, k, k - r0, m - k, w, 0);
+            // (C) end of a super-panel: the pivot rows and columns beyond it take all of its pivots
+            if (kb + nb == s0 + SP || kb + nb >= maxk) {
+                goff = (int64_t)gem.size();
+                gb = gf = 0;
+                for (int32_t f : big) {
+                    const FrontDev& fr = a->fronts[f];
+                    const int m = fr.m, k = fr.k, e = s0 + SP;
+                    if (s0 >= k || e >= k) continue;  // the front's pivots end inside this super-panel
+                    const int64_t Lb = fr.P_off + e + (int64_t)s0 * m;  // L[e.., s0..e)
+                    any_gemm(Lb, m, fr.P_off + s0 + (int64_t)e * m, m, AR_FAC, fr.P_off + e + (int64_t)e * m, m, m - e, k - e,
+                             SP);
+                    any_gemm(Lb, m, fr.R_off + s0, k, AR_FAC, fr.R_off + e, k, k - e, m - k, SP);
+                }
+                if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_TRAIL, gb, gf);
+                tc_end(c, FAM_TRAIL);
             }
-            if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_TRAIL, gb, gf);
         }
         // Schur update S -= L21 U12 (Sec. 2.2): tensor cores (MF_TF32) for large blocks, SIMT otherwise
         int64_t goff = (int64_t)gem.size();
-        int64_t toff = (int64_t)gtc.size();
-        double tb = 0, tf = 0;
         gb = gf = 0;
         for (int32_t f : big) {
             const FrontDev& fr = a->fronts[f];
             const int m = fr.m, k = fr.k, nc = m - k;
             if (nc <= 0 || k <= 0) continue;
-            if (F->prec == MF_TF32 && nc >= F->tc_min && k >= 16) {
-                for (int j0 = 0; j0 < nc; j0 += tc::kTileN)
-                    for (int i0 = 0; i0 < nc; i0 += tc::kTileM) {
-                        GemmTile t{};
-                        t.a_off = fr.P_off + k; t.b_off = fr.R_off; t.c_off = fr.S_off;
-                        t.lda = m; t.ldb = k; t.ldc = nc;
-                        t.M = nc; t.N = nc; t.K = k; t.i0 = i0; t.j0 = j0;
-                        t.a_ar = AR_FAC; t.b_ar = AR_FAC; t.c_ar = AR_CB; t.op = 0;
-                        gtc.push_back(t);
-                    }
-                tf += 2.0 * nc * nc * k;
-                tb += T * (2.0 * nc * k + 2.0 * nc * nc);
-            } else {
+            if (use_tc(nc, nc, k))
+                tc_add(AR_FAC, fr.P_off + k, m, AR_FAC, fr.R_off, k, AR_CB, fr.S_off, nc, nc, nc, k);
+            else
                 gemm_tiles(fr.P_off + k, m, fr.R_off, k, fr.S_off, nc, nc, nc, k, 1);
-            }
         }
         if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_SCHUR, gb, gf);
-        if (gtc.size() > (size_t)toff) push({K_GEMMTC, c, (int)(gtc.size() - toff), 0, toff}, FAM_SCHUR, tb, tf);
+        tc_end(c, FAM_SCHUR);
     }
     // explicit pivot-block inverses of the large fronts, after the last class
     {
@@ -705,6 +800,19 @@ static int build_plan(mf_factors* F) {
                 int64_t g1 = (int64_t)gem.size();
                 gb = gf = 0;
                 std::vector<GemmTile> ph2;
+                struct TcArgs {
+                    int8_t aar;
+                    int64_t ao;
+                    int lda;
+                    int8_t am, bar;
+                    int64_t bo;
+                    int ldb;
+                    int8_t bm, car;
+                    int64_t co;
+                    int ldc, M, N, K;
+                    int8_t op;
+                };
+                std::vector<TcArgs> tc2;  // tensor-core products of the second phase
                 for (int32_t f : ivf) {
                     const FrontDev& fr = a->fronts[f];
                     const int m = fr.m, k = fr.k;
@@ -714,6 +822,12 @@ static int build_plan(mf_factors* F) {
                         scr += 2 * (int64_t)n2 * S;
                         auto tiles = [&](std::vector<GemmTile>& out, int8_t aar, int64_t ao, int lda, int8_t am, int8_t bar,
                                          int64_t bo, int ldb, int8_t bm, int64_t co, int ldc, int M, int N, int K, int8_t op) {
+                            const int8_t car = op == 2 ? AR_INV : AR_SCR;
+                            if (use_tc(M, N, K)) {
+                                if (&out == &gem) tc_add(aar, ao, lda, bar, bo, ldb, car, co, ldc, M, N, K, op, am, bm);
+                                else tc2.push_back({aar, ao, lda, am, bar, bo, ldb, bm, car, co, ldc, M, N, K, op});
+                                return;
+                            }
                             for (int j0 = 0; j0 < N; j0 += 64)
                                 for (int i0 = 0; i0 < M; i0 += 64) {
                                     GemmTile t{};
@@ -741,12 +855,17 @@ static int build_plan(mf_factors* F) {
                     }
                 }
                 F->scr_size = std::max(F->scr_size, scr);
-                if (gem.size() > (size_t)g1) {
-                    push({K_GEMM, a->n_cls - 1, (int)(gem.size() - g1), 0, g1}, FAM_INV, gb / 2, gf / 2);
+                // phase 1 (products into scratch), then phase 2 (negated products into the inverse)
+                if (gem.size() > (size_t)g1) push({K_GEMM, a->n_cls - 1, (int)(gem.size() - g1), 0, g1}, FAM_INV, gb / 2, gf / 2);
+                tc_end(a->n_cls - 1, FAM_INV);
+                for (const TcArgs& x : tc2)
+                    tc_add(x.aar, x.ao, x.lda, x.bar, x.bo, x.ldb, x.car, x.co, x.ldc, x.M, x.N, x.K, x.op, x.am, x.bm);
+                if (!ph2.empty()) {
                     int64_t g2 = (int64_t)gem.size();
                     gem.insert(gem.end(), ph2.begin(), ph2.end());
                     push({K_GEMM, a->n_cls - 1, (int)(gem.size() - g2), 0, g2}, FAM_INV, gb / 2, gf / 2);
                 }
+                tc_end(a->n_cls - 1, FAM_INV);
             }
         }
     }
@@ -767,6 +886,8 @@ static int build_plan(mf_factors* F) {
     if ((rc = upload(&F->d_panel, pan))) return rc;
     if ((rc = upload(&F->d_gemm, gem))) return rc;
     if ((rc = upload(&F->d_gtc, gtc))) return rc;
+    if ((rc = upload(&F->d_tcpack, tcp))) return rc;
+    if ((rc = upload(&F->d_tcjob, tcj))) return rc;
     return MF_OK;
 }
 
@@ -783,7 +904,7 @@ static int set_smem_limits() {
     CUDA_TRY(cudaFuncSetAttribute(k_bwd_cta<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_inv_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_subtree_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
+    CUDA_TRY(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
     CUDA_TRY(cudaFuncSetAttribute(k_subtree_fwd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_subtree_fwd<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
 #define SET_INV(TR, PH)                                                                                            \
@@ -816,7 +937,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     F->small_max = F->opt.small_front_max > 0 ? F->opt.small_front_max : (F->prec == MF_F64 ? 96 : 128);
     F->small_max = std::min(F->small_max, F->prec == MF_F64 ? 160 : 224);
     F->small_max = std::max(F->small_max, a->npe);
-    F->tc_min = F->opt.tc_min_cb > 0 ? F->opt.tc_min_cb : 96;
+    F->tc_min = F->opt.tc_min_cb > 0 ? F->opt.tc_min_cb : 256;
     for (int i = 0; i < MF_FUSED_BUCKETS; i++) {
         const int t = F->opt.fused_threads[i];
         if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256) {
@@ -870,6 +991,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     TRY(dev_alloc((char**)&F->d_inv, (size_t)a->inv_size * F->tsize));
     TRY(dev_alloc((char**)&F->d_scr, (size_t)F->scr_size * F->tsize));
     TRY(dev_alloc((char**)&F->d_pnl, (size_t)F->pnl_size * F->tsize));
+    if (F->pk_size > 0) TRY(dev_alloc((char**)&F->d_pk, (size_t)F->pk_size * sizeof(float)));
     TRY(dev_alloc((char**)&F->d_ys, (size_t)a->ys_size * F->max_nrhs * F->tsize));
 #undef TRY
     *out = F;
@@ -936,10 +1058,16 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
                                                                        d_values, a->npe, fac, cb, F->sub.lay_f, F->tol_rel,
                                                                        F->d_status);
                 break;
+            case K_TCPACK:
+                if constexpr (sizeof(T) == 4) {
+                    Arenas<float> ar{{fac, cb, (float*)F->d_inv, (float*)F->d_scr, (float*)F->d_pnl}};
+                    k_tc_pack<<<L.count, 256, 0, s>>>(F->d_tcpack + L.bucket, F->d_tcjob + L.off, ar, F->d_pk);
+                }
+                break;
             case K_GEMMTC:
                 if constexpr (sizeof(T) == 4) {
                     Arenas<float> ar{{fac, cb, (float*)F->d_inv, (float*)F->d_scr, (float*)F->d_pnl}};
-                    k_gemm_tc<<<L.count, 128, tc::kSmemBytes, s>>>(F->d_gtc + L.off, ar, F->d_status);
+                    k_schur_tc<<<L.count, 128, tc::kSmemBytes, s>>>(F->d_gtc + L.off, F->d_pk, ar, F->d_status);
                 }
                 break;
             case K_INVDIAG:

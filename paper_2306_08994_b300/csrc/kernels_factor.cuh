@@ -691,6 +691,18 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTile* __restrict__ tiles
         if (kt + 1 < nk) store(buf ^ 1);
         __syncthreads();
     }
+    // epilogue: for C -= A B all 16 loads are issued before any store (a load-store chain on
+    // addresses the compiler cannot prove distinct would serialise 16 memory round trips)
+    T cv[4][4];
+    if (t.op == 0) {
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const int gi = t.i0 + tx + 16 * r, gj = t.j0 + ty + 16 * c;
+                cv[r][c] = (gi < t.M && gj < t.N) ? C[gi + (int64_t)gj * t.ldc] : T(0);
+            }
+    }
 #pragma unroll
     for (int c = 0; c < 4; c++) {
         int gj = t.j0 + ty + 16 * c;
@@ -700,7 +712,7 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTile* __restrict__ tiles
             int gi = t.i0 + tx + 16 * r;
             if (gi >= t.M) continue;
             T* dst = C + gi + (int64_t)gj * t.ldc;
-            if (t.op == 0) *dst -= acc[r][c];
+            if (t.op == 0) *dst = cv[r][c] - acc[r][c];
             else if (t.op == 1) *dst = acc[r][c];
             else *dst = -acc[r][c];
         }

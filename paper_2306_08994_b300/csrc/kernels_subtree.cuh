@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) k_subtree_factor(const FrontDev* __restri
     T* pool = work + lay.work_size;
     int32_t* mapsm = reinterpret_cast<int32_t*>(pool + lay.buf_size);
     const SubtreeTask task = tasks[blockIdx.x];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     int32_t* imap = mapsm + warp * 2 * kSubMaxM;
     for (int L = 0; L < task.n_levels; L++) {
         const int e0 = task.first + task.level_ptr[L], e1 = task.first + task.level_ptr[L + 1];

@@ -1,20 +1,26 @@
-// Tensor-core Schur update on sm_100-family (B300 = sm_103a): C -= A B with
-// tcgen05.mma kind::tf32, FP32 accumulation in tensor memory (TMEM).
+// Tensor-core Schur update on sm_100-family (B300 = sm_103a): S -= L21 U12
+// (Sec. 2.2) with tcgen05.mma kind::tf32, FP32 accumulation in tensor memory.
 //
-// Accuracy: every operand x is split into x_hi = tf32(x) and x_lo = x - x_hi
-// (exact in FP32), and A B is accumulated as A_hi B_hi + A_hi B_lo + A_lo B_hi
-// (three MMAs per K slice): products accurate to about 2^-21 relative, i.e.
-// FP32-grade Schur complements, which the FP64 refinement needs.
+// Accuracy: every operand x is split into x_hi = tf32(x) and x_lo =
+// tf32(x - x_hi), and the product is accumulated as A_hi B_hi + A_hi B_lo +
+// A_lo B_hi (three MMAs per K slice): products accurate to about 2^-21
+// relative, FP32-grade Schur complements, which the FP64 refinement needs.
 //
-// Tile: 128 x 128 of C per CTA (4 warps), K staged 32 at a time in two
-// shared-memory buffers.  Operand tiles are written by the threads in the
-// K-major, no-swizzle canonical layout of core matrices (8 rows x 16 bytes):
-// core (row group r, K group g) at byte r*1024 + g*128, i.e. leading
-// (K-direction) byte offset 128 and stride (row-direction) byte offset 1024.
-// One thread issues the MMAs of a stage and commits them to that buffer's
-// mbarrier; the threads wait on it (bounded) before refilling the buffer.
-// The epilogue reads TMEM with tcgen05.ld (warp w owns lanes 32w..32w+31 =
-// rows) and subtracts the product from C in global memory.
+// Two kernels per class:
+//  * k_tc_pack splits L21 and U12 of every tensor-core front once into hi and
+//    lo copies, already in the MMA's shared-memory image: K-major, no swizzle,
+//    core matrices of 8 rows x 16 bytes, core (row group r, K group g) at byte
+//    r*512 + g*128 of a (rows x 16) chunk.  Chunks are contiguous per (row
+//    tile, 16-wide K slice) and zero-padded, so the GEMM main loop is nothing
+//    but bulk copies (cp.async.bulk, the TMA engine) and MMAs.
+//  * k_schur_tc: one CTA per 128 x 256 tile of S; warp 0 lane 0 streams the
+//    operand chunks into a 4-stage ring (mbarrier expect_tx / complete_tx),
+//    warp 1 lane 0 issues the MMAs and returns each stage with
+//    tcgen05.commit; after the last commit all 4 warps read the accumulator
+//    (tcgen05.ld, warp w = TMEM lanes 32w..32w+31 = rows) and subtract it from
+//    S in place.  Every wait is bounded (globaltimer); on expiry the kernel
+//    records a timeout, waits (bounded) for its copies and MMAs in flight,
+//    frees its tensor memory and returns.
 #pragma once
 
 #include <cstdint>
@@ -103,67 +109,121 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-constexpr int kTileM = 128, kTileN = 128, kTileK = 32;
-constexpr int kOpBytes = kTileM * kTileK * 4;       // one operand tile (hi or lo): 16 KB
-constexpr int kStageBytes = 4 * kOpBytes;           // A_hi, A_lo, B_hi, B_lo
-constexpr int kSmemBytes = 2 * kStageBytes + 1024;  // two stages + barriers / TMEM address
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+
+// 1D bulk copy global -> shared (TMA engine), completion counted on mbar.
+__device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gmem_src, uint32_t bytes, uint64_t* mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(smem_dst)),
+        "l"(gmem_src), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
+}
+
+constexpr int kTileM = 128, kTileN = 256, kChunkK = 16, kStages = 4;
+constexpr int kChunkA = kTileM * kChunkK;  // floats per A chunk (hi or lo): 8 KB
+constexpr int kChunkB = kTileN * kChunkK;  // floats per B chunk: 16 KB
+constexpr int kStageBytes = 2 * 4 * (kChunkA + kChunkB);  // bytes: A_hi, A_lo, B_hi, B_lo
+constexpr int kSmemBytes = kStages * kStageBytes + 1024;
+constexpr uint32_t kTmemCols = 256;
 constexpr uint64_t kWaitLimit = 1000000000ull;  // 1 s
+
 
 }  // namespace tc
 
-// Stage a 128 x 32 slice of a column-major operand into core-matrix layout.
-//   rows_contig = true : operand element (row, k) at base[row + k*ld]  (A, M-contiguous)
-//   rows_contig = false: operand element (row, k) at base[k + row*ld]  (B stored K x N, K-contiguous)
-__device__ __forceinline__ void tc_stage(const float* __restrict__ base, int ld, int nrows, int nk, int k0,
-                                         bool rows_contig, unsigned char* hi, unsigned char* lo) {
-    const int t = threadIdx.x;  // 128 threads
-    for (int it = 0; it < 8; it++) {
-        int row, g;
-        if (rows_contig) {
-            row = t;
-            g = it;
-        } else {
-            row = it * 16 + (t >> 3);
-            g = t & 7;
+// One product for the tensor cores (a Schur update S -= L21 U12, a trailing
+// update of a super-panel, or a level of the pivot-block inversion), with
+// the same operand conventions as the SIMT GEMM: A (M x K) element (i, p) at
+// arena a_ar [a_off + i + p lda]; B (K x N) element (p, j) at arena b_ar
+// [b_off + p + j ldb]; optional triangular masks; op 0: C -= A B, 1: C = A B,
+// 2: C = -A B.  Packed as above: A in row tiles of 128, B^T in row tiles of
+// 256; hi chunks at a_hi / b_hi, lo chunks lo_off further.
+struct TcPack {
+    int64_t a_off, b_off;
+    int64_t a_hi, b_hi, lo_off;
+    int32_t lda, ldb, M, N, K, nkc;
+    int8_t a_ar, b_ar, a_mask, b_mask, pad[4];
+};
+struct TcTile {
+    int64_t a_hi, b_hi, lo_off;  // first chunks (K slice 0) of this tile's A row tile and B row tile
+    int64_t c_off;               // offset of the tile's (0, 0) element in arena c_ar
+    int32_t ldc, mrows, ncols, nkc;
+    int32_t c_ar, op;
+};
+
+// Pack kernel: one CTA per (product, operand, row tile, 16-wide K slice),
+// 256 threads.  The slice is read coalesced into shared memory (A along its
+// contiguous rows, B along its contiguous K), then written out as hi and lo
+// chunks: 16-byte unit u of a chunk holds row (u / 32) * 8 + u % 8, K group
+// (u / 8) % 4, so consecutive threads write consecutive 16-byte units.
+struct TcPackJob {
+    int32_t task, which, rt, kc;
+};
+
+__global__ void __launch_bounds__(256) k_tc_pack(const TcPack* __restrict__ tasks, const TcPackJob* __restrict__ jobs,
+                                                 Arenas<float> ar, float* __restrict__ pk) {
+    __shared__ float tile[tc::kTileN][tc::kChunkK + 1];
+    const TcPackJob jb = jobs[blockIdx.x];
+    const TcPack t = tasks[jb.task];
+    const int rows = jb.which == 0 ? tc::kTileM : tc::kTileN;
+    const int nrow = jb.which == 0 ? t.M : t.N;
+    const float* src = jb.which == 0 ? ar.a[t.a_ar] + t.a_off : ar.a[t.b_ar] + t.b_off;
+    const int r0 = jb.rt * rows, p0 = jb.kc * tc::kChunkK;
+    for (int e = threadIdx.x; e < rows * tc::kChunkK; e += blockDim.x) {
+        int r, kk;
+        if (jb.which == 0) {  // A: column-major, consecutive threads down a column
+            r = e % rows;
+            kk = e / rows;
+        } else {  // B: K-contiguous, consecutive threads along K
+            kk = e % tc::kChunkK;
+            r = e / tc::kChunkK;
         }
-        float v[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int k = k0 + 4 * g + q;
-            v[q] = (row < nrows && k < nk) ? (rows_contig ? base[row + (int64_t)k * ld] : base[k + (int64_t)row * ld]) : 0.f;
-        }
+        const int i = r0 + r, p = p0 + kk;
+        float v = 0.f;
+        if (i < nrow && p < t.K)
+            v = jb.which == 0 ? masked(src[i + (int64_t)p * t.lda], t.a_mask, i, p)
+                              : masked(src[p + (int64_t)i * t.ldb], t.b_mask, p, i);
+        tile[r][kk] = v;
+    }
+    __syncthreads();
+    const int64_t chunk = (jb.which == 0 ? t.a_hi : t.b_hi) + ((int64_t)jb.rt * t.nkc + jb.kc) * rows * tc::kChunkK;
+    for (int u = threadIdx.x; u < rows * 4; u += blockDim.x) {
+        const int r = (u >> 5) * 8 + (u & 7), kk = ((u >> 3) & 3) * 4;
         uint32_t h[4], l[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            h[q] = tc::to_tf32(v[q]);
-            l[q] = tc::to_tf32(v[q] - __uint_as_float(h[q]));
+        for (int e = 0; e < 4; e++) {
+            const float v = tile[r][kk + e];
+            h[e] = tc::to_tf32(v);
+            l[e] = tc::to_tf32(v - __uint_as_float(h[e]));
         }
-        const int off = (row >> 3) * 1024 + g * 128 + (row & 7) * 16;
-        *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+        *reinterpret_cast<uint4*>(pk + chunk + 4 * u) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(pk + t.lo_off + chunk + 4 * u) = make_uint4(l[0], l[1], l[2], l[3]);
     }
 }
 
-__global__ void __launch_bounds__(128) k_gemm_tc(const GemmTile* __restrict__ tiles, Arenas<float> ar, DevStatus* st) {
+__global__ void __launch_bounds__(128, 1) k_schur_tc(const TcTile* __restrict__ tiles, const float* __restrict__ pk,
+                                                     Arenas<float> ar, DevStatus* st) {
     extern __shared__ __align__(128) unsigned char smem_tc[];
-    unsigned char* stage[2] = {smem_tc, smem_tc + tc::kStageBytes};
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_tc + 2 * tc::kStageBytes);
-    uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(smem_tc + 2 * tc::kStageBytes + 64);
-    const GemmTile t = tiles[blockIdx.x];
-    const float* A = ar.a[t.a_ar] + t.a_off + t.i0;                  // rows i0.. of A (M x K, column-major)
-    const float* B = ar.a[t.b_ar] + t.b_off + (int64_t)t.j0 * t.ldb;  // columns j0.. of B (K x N, column-major)
-    float* C = ar.a[t.c_ar] + t.c_off;
-    const int mrows = min(tc::kTileM, t.M - t.i0), ncols = min(tc::kTileN, t.N - t.j0);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_tc + tc::kStages * tc::kStageBytes);
+    uint64_t* empty = full + tc::kStages;
+    uint64_t* done = empty + tc::kStages;
+    uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(done + 1);
+    const TcTile t = tiles[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = t.nkc;
 
     if (threadIdx.x == 0) {
-        tc::mbar_init(&mbar[0], 1);
-        tc::mbar_init(&mbar[1], 1);
+        for (int s = 0; s < tc::kStages; s++) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(taddr_slot)),
-                     "r"(128u)
+                     "r"(tc::kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -171,55 +231,83 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTile* __restrict__ ti
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *taddr_slot;
-    constexpr uint32_t idesc = tc::idesc_tf32(tc::kTileM, tc::kTileN);
-    const int nst = (t.K + tc::kTileK - 1) / tc::kTileK;
-    bool ok = true;
-    for (int s = 0; s < nst && ok; s++) {
-        const int b = s & 1;
-        if (s >= 2) ok = tc::mbar_wait_bounded(&mbar[b], ((s >> 1) - 1) & 1, tc::kWaitLimit);
-        if (!__syncthreads_and(ok)) {
-            ok = false;
-            break;
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) s_fail = 0;
+    __syncthreads();
+
+    if (warp == 0 && lane == 0) {
+        // producer: operand chunks into the ring
+        int issued = 0;
+        bool ok = true;
+        for (int c = 0; c < nk && ok; c++) {
+            const int s = c % tc::kStages;
+            if (c >= tc::kStages) ok = tc::mbar_wait_bounded(&empty[s], ((c / tc::kStages) - 1) & 1, tc::kWaitLimit);
+            if (!ok) break;
+            unsigned char* dst = smem_tc + s * tc::kStageBytes;
+            tc::mbar_expect_tx(&full[s], tc::kStageBytes);
+            const float* a = pk + t.a_hi + (int64_t)c * tc::kChunkA;
+            const float* b = pk + t.b_hi + (int64_t)c * tc::kChunkB;
+            tc::bulk_g2s(dst, a, tc::kChunkA * 4, &full[s]);
+            tc::bulk_g2s(dst + tc::kChunkA * 4, a + t.lo_off, tc::kChunkA * 4, &full[s]);
+            tc::bulk_g2s(dst + 2 * tc::kChunkA * 4, b, tc::kChunkB * 4, &full[s]);
+            tc::bulk_g2s(dst + (2 * tc::kChunkA + tc::kChunkB) * 4, b + t.lo_off, tc::kChunkB * 4, &full[s]);
+            issued = c + 1;
         }
-        unsigned char* ahi = stage[b];
-        unsigned char* alo = ahi + tc::kOpBytes;
-        unsigned char* bhi = alo + tc::kOpBytes;
-        unsigned char* blo = bhi + tc::kOpBytes;
-        tc_stage(A, t.lda, mrows, t.K, s * tc::kTileK, true, ahi, alo);
-        tc_stage(B, t.ldb, ncols, t.K, s * tc::kTileK, false, bhi, blo);
-        tc::fence_proxy_async();
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        if (!ok) {
+            atomicExch(&s_fail, 1);
+            // let the copies already issued land before the CTA can exit
+            for (int c = max(0, issued - tc::kStages); c < issued; c++)
+                tc::mbar_wait_bounded(&full[c % tc::kStages], (c / tc::kStages) & 1, tc::kWaitLimit);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = tc::idesc_tf32(tc::kTileM, tc::kTileN);
+        bool ok = true;
+        for (int c = 0; c < nk; c++) {
+            const int s = c % tc::kStages;
+            ok = tc::mbar_wait_bounded(&full[s], (c / tc::kStages) & 1, tc::kWaitLimit);
+            if (!ok) break;
             tc::fence_after_sync();
+            const uint32_t sa = tc::smem_u32(smem_tc + s * tc::kStageBytes);
+            const uint32_t sal = sa + tc::kChunkA * 4, sb = sa + 2 * tc::kChunkA * 4, sbl = sb + tc::kChunkB * 4;
 #pragma unroll
-            for (int ks = 0; ks < tc::kTileK / 8; ks++) {  // K = 8 per MMA: two K groups of 16 bytes
-                const uint32_t koff = ks * 256;
-                const uint64_t dah = tc::smem_desc(tc::smem_u32(ahi) + koff, 128, 1024);
-                const uint64_t dal = tc::smem_desc(tc::smem_u32(alo) + koff, 128, 1024);
-                const uint64_t dbh = tc::smem_desc(tc::smem_u32(bhi) + koff, 128, 1024);
-                const uint64_t dbl = tc::smem_desc(tc::smem_u32(blo) + koff, 128, 1024);
-                const uint32_t first = (s == 0 && ks == 0) ? 0u : 1u;
-                tc::mma_tf32(tmem, dal, dbh, idesc, first);
+            for (int ks = 0; ks < tc::kChunkK / 8; ks++) {  // K = 8 per MMA: two 16-byte K groups
+                const uint32_t ko = ks * 256;
+                const uint64_t dah = tc::smem_desc(sa + ko, 128, 512), dal = tc::smem_desc(sal + ko, 128, 512);
+                const uint64_t dbh = tc::smem_desc(sb + ko, 128, 512), dbl = tc::smem_desc(sbl + ko, 128, 512);
+                tc::mma_tf32(tmem, dal, dbh, idesc, (c == 0 && ks == 0) ? 0u : 1u);
                 tc::mma_tf32(tmem, dah, dbl, idesc, 1u);
                 tc::mma_tf32(tmem, dah, dbh, idesc, 1u);
             }
-            tc::mma_commit(&mbar[b]);
+            tc::mma_commit(&empty[s]);
         }
+        if (!ok) atomicExch(&s_fail, 1);
+        tc::mma_commit(done);  // tracks every MMA issued above
     }
-    if (ok && nst > 0) ok = tc::mbar_wait_bounded(&mbar[(nst - 1) & 1], ((nst - 1) >> 1) & 1, tc::kWaitLimit);
-    ok = __syncthreads_and(ok);
+    __syncwarp();
+    bool ok = tc::mbar_wait_bounded(done, 0, tc::kWaitLimit);
+    ok = __syncthreads_and(ok && !s_fail);
     tc::fence_after_sync();
-    if (ok && nst > 0) {
+    if (ok && nk > 0) {
         const int row = 32 * warp + lane;
+        float* crow = ar.a[t.c_ar] + t.c_off + row;
 #pragma unroll 1
         for (int cg = 0; cg < tc::kTileN / 32; cg++) {
-            float v[32];
+            if (cg * 32 >= t.ncols) break;
+            float v[32], cv[32];
+            float* cp = crow + (int64_t)(cg * 32) * t.ldc;
+            const int nj = min(32, t.ncols - cg * 32);
+            // all loads of the row segment first, then the stores: a load-store-load chain on
+            // possibly aliasing addresses would serialise 32 memory round trips
+            if (row < t.mrows && t.op == 0) {
+#pragma unroll
+                for (int j = 0; j < 32; j++) cv[j] = j < nj ? cp[(int64_t)j * t.ldc] : 0.f;
+            }
             tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + cg * 32, v);
-            if (row < mrows) {
-                float* crow = C + (t.i0 + row) + (int64_t)(t.j0 + cg * 32) * t.ldc;
+            if (row < t.mrows) {
 #pragma unroll
                 for (int j = 0; j < 32; j++)
-                    if (cg * 32 + j < ncols) crow[(int64_t)j * t.ldc] -= v[j];
+                    if (j < nj) cp[(int64_t)j * t.ldc] = t.op == 0 ? cv[j] - v[j] : (t.op == 1 ? v[j] : -v[j]);
             }
         }
     } else if (!ok && threadIdx.x == 0) {
@@ -227,5 +315,6 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmTile* __restrict__ ti
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tc::kTmemCols) : "memory");
 }

@@ -127,16 +127,25 @@ def test_solution_matches_oracle(case, prec):
         assert e1 <= 1e-10, e1
 
 
-@pytest.mark.parametrize("n", [40, 56])
+@pytest.mark.parametrize("n", [40, 56, 96])
 def test_tensor_core_schur_path(n):
     """MF_TF32: Schur updates of large fronts on tcgen05 (3-pass TF32).  Factors agree
     with the FP32 SIMT path to within the FP32 path's own distance from FP64, and the
-    refined solution meets the same bars."""
+    refined solution meets the same bars.  tc_min_cb = 32 sends contribution blocks
+    from 32 up (partial 128 x 256 tiles, several tiles per front at n = 96) through
+    the tensor-core kernels."""
     pr = F.diffusion_2d(n, 3, seed=36)
     factors = {}
     for prec in ("f64", "f32", "tf32"):
-        a, f, vals = _setup(pr, prec, small_front_max=64)
+        a, f, vals = _setup(pr, prec, small_front_max=64, tc_min_cb=32)
+        if prec == "tf32":
+            f.profile(True)
         f.factor(vals)
+        if prec == "tf32":
+            kinds = {r["kind"] for r in f.trace()}
+            f.profile_read()
+            f.profile(False)
+            assert {"gemm_tc"} <= kinds, kinds
         assert f.status()["rc"] == 0
         g = a.n_front - 2  # a front just below the root: its front matrix came through Schur updates
         factors[prec] = f.export_front(g)[0]
