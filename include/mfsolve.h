@@ -79,6 +79,10 @@ typedef struct {
                              (fewer if a subtree would not fit shared memory); <= 0 = off */
     int tc_min_cb;        /* MF_TF32: smallest contribution block (m - k) whose Schur update runs
                              on the tensor cores; smaller ones use the SIMT GEMM; 0 = 256 */
+    int super_panel;      /* pivots per super-panel of the large-front partial LU (a multiple of the
+                             panel width): inside a super-panel each panel is updated just before
+                             it is factored, the rest of the pivot block once per super-panel;
+                             0 = default (256 for FP32 fronts, the panel width for FP64) */
     int fused_threads[MF_FUSED_BUCKETS];
                           /* threads per CTA of the fused small-front kernel for each front-size
                              bucket (m <= 16, 32, 48, 64, 96, 128, 160, 192, 224): 32, 64, 128 or
@@ -269,6 +273,7 @@ int mf_profile_trace(mf_factors* f, mf_trace_rec* out, int cap, int* n);
  *                    factorizations, all buckets in one sweep),
  *   small_front_max  fused / blocked crossover,
  *   subtree_levels   depth of the bottom-class subtree fusion,
+ *   super_panel      depth of the deferred trailing updates of large fronts,
  *   precision and tc_min_cb  (FP32 family only) SIMT or tensor-core Schur GEMMs.
  * Candidates are timed as one factorization plus one solve (CUDA events on
  * `stream`, CUDA graph replay, median of `reps` after one untimed run).

@@ -31,7 +31,7 @@ struct Timer {
 
 // Version of the launch-plan builder: bumped whenever its kernels or its
 // decomposition change enough that plans tuned before are stale.
-constexpr int kPlanVersion = 2;
+constexpr int kPlanVersion = 3;
 
 int family_of(int precision) { return precision == MF_F64 ? 0 : 1; }
 
@@ -76,6 +76,8 @@ bool cache_lookup(const char* path, const std::string& key, mf_options* o, doubl
     t.subtree_levels = std::atoi(v);
     if (!(v = field(hit, "tc_min_cb"))) return false;
     t.tc_min_cb = std::atoi(v);
+    if (!(v = field(hit, "super_panel"))) return false;
+    t.super_panel = std::atoi(v);
     if (!(v = field(hit, "fused_threads")) || *v != '[') return false;
     v++;
     for (int b = 0; b < MF_FUSED_BUCKETS; b++) {
@@ -97,8 +99,8 @@ void cache_append(const char* path, const std::string& key, const mf_options& o,
     FILE* fp = std::fopen(path, "a");
     if (!fp) return;
     std::fprintf(fp, "{\"key\":\"%s\",\"precision\":%d,\"small_front_max\":%d,\"subtree_levels\":%d,\"tc_min_cb\":%d,"
-                     "\"fused_threads\":[",
-                 key.c_str(), o.precision, o.small_front_max, o.subtree_levels, o.tc_min_cb);
+                     "\"super_panel\":%d,\"fused_threads\":[",
+                 key.c_str(), o.precision, o.small_front_max, o.subtree_levels, o.tc_min_cb, o.super_panel);
     for (int b = 0; b < MF_FUSED_BUCKETS; b++) std::fprintf(fp, "%s%d", b ? "," : "", o.fused_threads[b]);
     std::fprintf(fp, "],\"ms_best\":%.4f,\"ms_default\":%.4f,\"candidates\":%d}\n", ms_best, ms_default, candidates);
     std::fclose(fp);
@@ -262,6 +264,15 @@ extern "C" int mf_autotune(const mf_analysis* a, const double* d_values, const d
             mf_options t = start;
             t.subtree_levels = lv;
             if (lv != start.subtree_levels) try_one(t);
+        }
+    }
+    if (!rc) {
+        const mf_options start = cur;
+        for (int sp : {64, 128, 256, 512}) {
+            if (rc) break;
+            mf_options t = start;
+            t.super_panel = sp;
+            if (sp != start.super_panel) try_one(t);
         }
     }
     if (!rc && family_of(o.precision) == 1) {

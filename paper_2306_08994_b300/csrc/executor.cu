@@ -73,7 +73,6 @@ int upload(T** p, const std::vector<T>& v) {
 
 constexpr int kPanelNB64 = 32;  // panel width (pivot block of a step), FP64
 constexpr int kPanelNB32 = 64;  // FP32
-constexpr int kSuperPanel = 256;  // pivots per super-panel of the large-front partial LU
 
 __global__ void k_init_status(DevStatus* st) {
     st->n_perturbed = 0ull;
@@ -203,7 +202,8 @@ struct mf_factors {
     double tol_rel = 0;
     int nb = 32;
     int small_max = 96;
-    int tc_min = 96;
+    int tc_min = 256;
+    int sp = 256;  // super-panel depth (pivots)
     int max_nrhs = 4;
     // device
     FrontDev* d_fronts = nullptr;
@@ -679,7 +679,7 @@ static int build_plan(mf_factors* F) {
         // across): a panel is brought up to date with the pivots of its super-panel just before
         // it is factored (thin strip products), and the rest of the pivot rows and columns takes
         // the whole super-panel in one product of depth kSuperPanel at its end.
-        const int SP = kSuperPanel;
+        const int SP = F->sp;
         auto any_gemm = [&](int64_t ao, int lda, int64_t bo, int ldb, int8_t car, int64_t co, int ldc, int M, int N,
                             int K) {
             if (M <= 0 || N <= 0 || K <= 0) return;
@@ -938,6 +938,8 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     F->small_max = std::min(F->small_max, F->prec == MF_F64 ? 160 : 224);
     F->small_max = std::max(F->small_max, a->npe);
     F->tc_min = F->opt.tc_min_cb > 0 ? F->opt.tc_min_cb : 256;
+    F->sp = F->opt.super_panel > 0 ? F->opt.super_panel : (F->prec == MF_F64 ? F->nb : 256);
+    F->sp = std::max(F->nb, (F->sp + F->nb - 1) / F->nb * F->nb);
     for (int i = 0; i < MF_FUSED_BUCKETS; i++) {
         const int t = F->opt.fused_threads[i];
         if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256) {
