@@ -238,10 +238,11 @@ int mf_residual_noalloc(int64_t n_dof, int64_t n_elem, int nodes_per_elem, const
  * (inputs read once, outputs written once), flops = the arithmetic the
  * algorithm performs.  Families: 0 fused small fronts, 1 large-front
  * assembly, 2 panel LU, 3 trailing GEMM, 4 Schur GEMM, 5 forward
- * substitution, 6 backward substitution, 7 residual and norms, 8 other.
+ * substitution, 6 backward substitution, 7 residual and norms, 8 other,
+ * 9 pivot-block inverses (for the substitutions).
  * mf_profile_read synchronises, writes MF_PROFILE_FAMILIES entries to each
  * non-NULL array (summed since the last read) and resets the sums. */
-#define MF_PROFILE_FAMILIES 9
+#define MF_PROFILE_FAMILIES 10
 int mf_profile_enable(mf_factors* f, int enable);
 int mf_profile_read(mf_factors* f, double* ms, int64_t* launches, double* bytes, double* flops);
 
@@ -263,6 +264,7 @@ int mf_profile_read(mf_factors* f, double* ms, int64_t* launches, double* bytes,
 typedef struct {
     int family, kind, cls, tasks;
     double ms;
+    double bytes, flops;  /* algorithmic work of the record, as in mf_profile_read */
 } mf_trace_rec;
 int mf_profile_trace(mf_factors* f, mf_trace_rec* out, int cap, int* n);
 

@@ -275,7 +275,7 @@ struct mf_factors {
 };
 
 enum Family { FAM_FUSED = 0, FAM_ASM = 1, FAM_PANEL = 2, FAM_TRAIL = 3, FAM_SCHUR = 4, FAM_FWD = 5, FAM_BWD = 6,
-              FAM_RESID = 7, FAM_OTHER = 8, FAM_INV = 2 /* accounted with the panel LU */ };
+              FAM_RESID = 7, FAM_OTHER = 8, FAM_INV = 9 };
 
 // Bracket one launch: returns a slot index (or -1 when profiling is off).
 static int prof_begin(mf_factors* F, cudaStream_t s, int fam, double bytes, double flops, int kernels = 1,
@@ -294,7 +294,7 @@ static int prof_begin(mf_factors* F, cudaStream_t s, int fam, double bytes, doub
         F->ev_tag.resize(F->ev.size() / 2);
     }
     int slot = (int)F->ev_used++;
-    F->ev_rec[slot] = mf_trace_rec{fam, kind, cls, tasks, 0.0};
+    F->ev_rec[slot] = mf_trace_rec{fam, kind, cls, tasks, 0.0, bytes, flops};
     F->ev_tag[slot] = tag;
     cudaEventRecord(F->ev[2 * slot], s);
     return slot;

@@ -64,7 +64,7 @@ class mf_refine_info(ctypes.Structure):
 
 class mf_trace_rec(ctypes.Structure):
     _fields_ = [("family", ctypes.c_int), ("kind", ctypes.c_int), ("cls", ctypes.c_int), ("tasks", ctypes.c_int),
-                ("ms", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
 TRACE_KINDS = {0: "fused", 1: "assemble", 2: "panel_diag", 3: "gemm", 4: "inv_diag", 5: "subtree", 6: "gemm_tc",
@@ -84,7 +84,7 @@ EXPORTS = ["mf_default_options", "mf_strerror", "mf_analyze_mesh", "mf_analyze_b
            "mf_free_factors", "mf_free_analysis", "mf_profile_enable", "mf_profile_read", "mf_residual_noalloc",
            "mf_autotune", "mf_profile_trace"]
 PROFILE_FAMILIES = ["fused", "assemble", "panel", "trailing_gemm", "schur_gemm", "forward", "backward", "residual",
-                    "other"]
+                    "other", "inverse"]
 
 
 class MFError(RuntimeError):
@@ -303,7 +303,7 @@ class Factors:
         recs = (mf_trace_rec * max(n.value, 1))()
         _check(_lib.mf_profile_trace(self._h, recs, n.value, ctypes.byref(n)), "mf_profile_trace")
         return [{"family": PROFILE_FAMILIES[r.family], "kind": TRACE_KINDS.get(r.kind, str(r.kind)), "cls": r.cls,
-                 "tasks": r.tasks, "ms": r.ms} for r in recs[:n.value]]
+                 "tasks": r.tasks, "ms": r.ms, "bytes": r.bytes, "flops": r.flops} for r in recs[:n.value]]
 
     def export_front(self, front: int):
         ex = self.analysis.export()
