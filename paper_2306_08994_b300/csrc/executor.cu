@@ -204,6 +204,7 @@ struct mf_factors {
     int small_max = 96;
     int tc_min = 256;
     int sp = 256;  // super-panel depth (pivots)
+    int num_sms = 148;
     int max_nrhs = 4;
     // device
     FrontDev* d_fronts = nullptr;
@@ -938,6 +939,12 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     F->small_max = std::min(F->small_max, F->prec == MF_F64 ? 160 : 224);
     F->small_max = std::max(F->small_max, a->npe);
     F->tc_min = F->opt.tc_min_cb > 0 ? F->opt.tc_min_cb : 256;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&F->num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (F->num_sms <= 0) F->num_sms = 148;
+    }
     F->sp = F->opt.super_panel > 0 ? F->opt.super_panel : (F->prec == MF_F64 ? F->nb : 256);
     F->sp = std::max(F->nb, (F->sp + F->nb - 1) / F->nb * F->nb);
     for (int i = 0; i < MF_FUSED_BUCKETS; i++) {
@@ -1069,7 +1076,8 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
             case K_GEMMTC:
                 if constexpr (sizeof(T) == 4) {
                     Arenas<float> ar{{fac, cb, (float*)F->d_inv, (float*)F->d_scr, (float*)F->d_pnl}};
-                    k_schur_tc<<<L.count, 128, tc::kSmemBytes, s>>>(F->d_gtc + L.off, F->d_pk, ar, F->d_status);
+                    k_schur_tc<<<std::min(L.count, F->num_sms), kTcThreads, tc::kSmemBytes, s>>>(F->d_gtc + L.off, L.count,
+                                                                                                  F->d_pk, ar, F->d_status);
                 }
                 break;
             case K_INVDIAG:

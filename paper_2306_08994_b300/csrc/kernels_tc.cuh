@@ -109,6 +109,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
 }
@@ -202,28 +206,43 @@ __global__ void __launch_bounds__(256) k_tc_pack(const TcPack* __restrict__ task
     }
 }
 
-__global__ void __launch_bounds__(128, 1) k_schur_tc(const TcTile* __restrict__ tiles, const float* __restrict__ pk,
-                                                     Arenas<float> ar, DevStatus* st) {
+// Persistent product kernel: one CTA per SM walks the tile list (tile
+// b, b + gridDim.x, ...).  Warp 0 lane 0 streams operand chunks into the
+// 4-stage ring across tile boundaries; warp 1 lane 0 issues the MMAs of tile
+// i into TMEM accumulator i & 1 (2 x 256 columns) and commits it to acc_full;
+// warps 2-5 (TMEM lane quarters 2, 3, 0, 1) drain the accumulator of tile i
+// into C while tile i + 1 is being multiplied, then release it (acc_empty).
+constexpr int kTcThreads = 192;
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_schur_tc(const TcTile* __restrict__ tiles, int ntiles,
+                                                            const float* __restrict__ pk, Arenas<float> ar, DevStatus* st) {
     extern __shared__ __align__(128) unsigned char smem_tc[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_tc + tc::kStages * tc::kStageBytes);
     uint64_t* empty = full + tc::kStages;
-    uint64_t* done = empty + tc::kStages;
-    uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(done + 1);
-    const TcTile t = tiles[blockIdx.x];
+    uint64_t* acc_full = empty + tc::kStages;  // [2]
+    uint64_t* acc_empty = acc_full + 2;        // [2]
+    uint64_t* drain = acc_empty + 2;
+    uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    __shared__ int s_fail_raw;
+    volatile int& s_fail = s_fail_raw;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = t.nkc;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < tc::kStages; s++) {
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
-        tc::mbar_init(done, 1);
+        for (int b = 0; b < 2; b++) {
+            tc::mbar_init(&acc_full[b], 1);
+            tc::mbar_init(&acc_empty[b], 4);  // one arrive per epilogue warp
+        }
+        tc::mbar_init(drain, 1);
+        s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(taddr_slot)),
-                     "r"(tc::kTmemCols)
+                     "r"(2 * tc::kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -231,90 +250,125 @@ __global__ void __launch_bounds__(128, 1) k_schur_tc(const TcTile* __restrict__ 
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *taddr_slot;
-    __shared__ int s_fail;
-    if (threadIdx.x == 0) s_fail = 0;
-    __syncthreads();
 
-    if (warp == 0 && lane == 0) {
-        // producer: operand chunks into the ring
-        int issued = 0;
-        bool ok = true;
-        for (int c = 0; c < nk && ok; c++) {
-            const int s = c % tc::kStages;
-            if (c >= tc::kStages) ok = tc::mbar_wait_bounded(&empty[s], ((c / tc::kStages) - 1) & 1, tc::kWaitLimit);
-            if (!ok) break;
-            unsigned char* dst = smem_tc + s * tc::kStageBytes;
-            tc::mbar_expect_tx(&full[s], tc::kStageBytes);
-            const float* a = pk + t.a_hi + (int64_t)c * tc::kChunkA;
-            const float* b = pk + t.b_hi + (int64_t)c * tc::kChunkB;
-            tc::bulk_g2s(dst, a, tc::kChunkA * 4, &full[s]);
-            tc::bulk_g2s(dst + tc::kChunkA * 4, a + t.lo_off, tc::kChunkA * 4, &full[s]);
-            tc::bulk_g2s(dst + 2 * tc::kChunkA * 4, b, tc::kChunkB * 4, &full[s]);
-            tc::bulk_g2s(dst + (2 * tc::kChunkA + tc::kChunkB) * 4, b + t.lo_off, tc::kChunkB * 4, &full[s]);
-            issued = c + 1;
+    if (warp == 0) {
+        if (lane == 0) {  // producer
+            int g = 0;  // chunk counter across this CTA's tiles
+            bool ok = true;
+            for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+                const TcTile t = tiles[ti];
+                for (int c = 0; c < t.nkc; c++, g++) {
+                    const int s = g % tc::kStages;
+                    if (g >= tc::kStages) ok = tc::mbar_wait_bounded(&empty[s], ((g / tc::kStages) - 1) & 1, tc::kWaitLimit);
+                    if (!ok || s_fail) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char* dst = smem_tc + s * tc::kStageBytes;
+                    tc::mbar_expect_tx(&full[s], tc::kStageBytes);
+                    const float* a = pk + t.a_hi + (int64_t)c * tc::kChunkA;
+                    const float* b = pk + t.b_hi + (int64_t)c * tc::kChunkB;
+                    tc::bulk_g2s(dst, a, tc::kChunkA * 4, &full[s]);
+                    tc::bulk_g2s(dst + tc::kChunkA * 4, a + t.lo_off, tc::kChunkA * 4, &full[s]);
+                    tc::bulk_g2s(dst + 2 * tc::kChunkA * 4, b, tc::kChunkB * 4, &full[s]);
+                    tc::bulk_g2s(dst + (2 * tc::kChunkA + tc::kChunkB) * 4, b + t.lo_off, tc::kChunkB * 4, &full[s]);
+                }
+            }
+            if (!ok) {
+                s_fail = 1;
+                // let the copies already issued land before the CTA can exit
+                for (int c = max(0, g - tc::kStages); c < g; c++)
+                    tc::mbar_wait_bounded(&full[c % tc::kStages], (c / tc::kStages) & 1, tc::kWaitLimit);
+            }
         }
-        if (!ok) {
-            atomicExch(&s_fail, 1);
-            // let the copies already issued land before the CTA can exit
-            for (int c = max(0, issued - tc::kStages); c < issued; c++)
-                tc::mbar_wait_bounded(&full[c % tc::kStages], (c / tc::kStages) & 1, tc::kWaitLimit);
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            constexpr uint32_t idesc = tc::idesc_tf32(tc::kTileM, tc::kTileN);
+            int g = 0, i = 0;
+            bool ok = true;
+            for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x, i++) {
+                const TcTile t = tiles[ti];
+                const int buf = i & 1;
+                const uint32_t acc = tmem + buf * tc::kTmemCols;
+                if (i >= 2) ok = tc::mbar_wait_bounded(&acc_empty[buf], ((i >> 1) - 1) & 1, tc::kWaitLimit);
+                if (!ok) break;
+                tc::fence_after_sync();
+                for (int c = 0; c < t.nkc; c++, g++) {
+                    const int s = g % tc::kStages;
+                    ok = tc::mbar_wait_bounded(&full[s], (g / tc::kStages) & 1, tc::kWaitLimit);
+                    if (!ok || s_fail) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t sa = tc::smem_u32(smem_tc + s * tc::kStageBytes);
+                    const uint32_t sal = sa + tc::kChunkA * 4, sb = sa + 2 * tc::kChunkA * 4, sbl = sb + tc::kChunkB * 4;
+#pragma unroll
+                    for (int ks = 0; ks < tc::kChunkK / 8; ks++) {  // K = 8 per MMA: two 16-byte K groups
+                        const uint32_t ko = ks * 256;
+                        const uint64_t dah = tc::smem_desc(sa + ko, 128, 512), dal = tc::smem_desc(sal + ko, 128, 512);
+                        const uint64_t dbh = tc::smem_desc(sb + ko, 128, 512), dbl = tc::smem_desc(sbl + ko, 128, 512);
+                        tc::mma_tf32(acc, dal, dbh, idesc, (c == 0 && ks == 0) ? 0u : 1u);
+                        tc::mma_tf32(acc, dah, dbl, idesc, 1u);
+                        tc::mma_tf32(acc, dah, dbh, idesc, 1u);
+                    }
+                    tc::mma_commit(&empty[s]);
+                }
+                tc::mma_commit(&acc_full[buf]);  // the accumulator is complete when these MMAs are
+            }
+            if (!ok) {
+                s_fail = 1;
+                // no MMA may still be writing TMEM when it is freed
+                tc::mma_commit(drain);
+                tc::mbar_wait_bounded(drain, 0, tc::kWaitLimit);
+            }
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        constexpr uint32_t idesc = tc::idesc_tf32(tc::kTileM, tc::kTileN);
-        bool ok = true;
-        for (int c = 0; c < nk; c++) {
-            const int s = c % tc::kStages;
-            ok = tc::mbar_wait_bounded(&full[s], (c / tc::kStages) & 1, tc::kWaitLimit);
-            if (!ok) break;
+        __syncwarp();
+    } else {  // epilogue warps 2..5: TMEM lanes 32 (warp % 4) ..
+        const int q = warp & 3;
+        const int row = 32 * q + lane;
+        int i = 0;
+        for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, i++) {
+            const TcTile t = tiles[ti];
+            const int buf = i & 1;
+            bool ok = tc::mbar_wait_bounded(&acc_full[buf], (i >> 1) & 1, tc::kWaitLimit);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) s_fail = 1;
+                break;
+            }
             tc::fence_after_sync();
-            const uint32_t sa = tc::smem_u32(smem_tc + s * tc::kStageBytes);
-            const uint32_t sal = sa + tc::kChunkA * 4, sb = sa + 2 * tc::kChunkA * 4, sbl = sb + tc::kChunkB * 4;
-#pragma unroll
-            for (int ks = 0; ks < tc::kChunkK / 8; ks++) {  // K = 8 per MMA: two 16-byte K groups
-                const uint32_t ko = ks * 256;
-                const uint64_t dah = tc::smem_desc(sa + ko, 128, 512), dal = tc::smem_desc(sal + ko, 128, 512);
-                const uint64_t dbh = tc::smem_desc(sb + ko, 128, 512), dbl = tc::smem_desc(sbl + ko, 128, 512);
-                tc::mma_tf32(tmem, dal, dbh, idesc, (c == 0 && ks == 0) ? 0u : 1u);
-                tc::mma_tf32(tmem, dah, dbl, idesc, 1u);
-                tc::mma_tf32(tmem, dah, dbh, idesc, 1u);
-            }
-            tc::mma_commit(&empty[s]);
-        }
-        if (!ok) atomicExch(&s_fail, 1);
-        tc::mma_commit(done);  // tracks every MMA issued above
-    }
-    __syncwarp();
-    bool ok = tc::mbar_wait_bounded(done, 0, tc::kWaitLimit);
-    ok = __syncthreads_and(ok && !s_fail);
-    tc::fence_after_sync();
-    if (ok && nk > 0) {
-        const int row = 32 * warp + lane;
-        float* crow = ar.a[t.c_ar] + t.c_off + row;
+            float* crow = ar.a[t.c_ar] + t.c_off + row;
 #pragma unroll 1
-        for (int cg = 0; cg < tc::kTileN / 32; cg++) {
-            if (cg * 32 >= t.ncols) break;
-            float v[32], cv[32];
-            float* cp = crow + (int64_t)(cg * 32) * t.ldc;
-            const int nj = min(32, t.ncols - cg * 32);
-            // all loads of the row segment first, then the stores: a load-store-load chain on
-            // possibly aliasing addresses would serialise 32 memory round trips
-            if (row < t.mrows && t.op == 0) {
+            for (int cg = 0; cg < tc::kTileN / 32; cg++) {
+                if (cg * 32 >= t.ncols) break;
+                float v[32], cv[32];
+                float* cp = crow + (int64_t)(cg * 32) * t.ldc;
+                const int nj = min(32, t.ncols - cg * 32);
+                // all loads of the row segment first, then the stores: a load-store-load chain on
+                // possibly aliasing addresses would serialise 32 memory round trips
+                if (row < t.mrows && t.op == 0) {
 #pragma unroll
-                for (int j = 0; j < 32; j++) cv[j] = j < nj ? cp[(int64_t)j * t.ldc] : 0.f;
-            }
-            tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + cg * 32, v);
-            if (row < t.mrows) {
+                    for (int j = 0; j < 32; j++) cv[j] = j < nj ? cp[(int64_t)j * t.ldc] : 0.f;
+                }
+                tc::tmem_ld32(tmem + buf * tc::kTmemCols + ((uint32_t)(32 * q) << 16) + cg * 32, v);
+                if (row < t.mrows) {
 #pragma unroll
-                for (int j = 0; j < 32; j++)
-                    if (j < nj) cp[(int64_t)j * t.ldc] = t.op == 0 ? cv[j] - v[j] : (t.op == 1 ? v[j] : -v[j]);
+                    for (int j = 0; j < 32; j++)
+                        if (j < nj) cp[(int64_t)j * t.ldc] = t.op == 0 ? cv[j] - v[j] : (t.op == 1 ? v[j] : -v[j]);
+                }
             }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
         }
-    } else if (!ok && threadIdx.x == 0) {
-        atomicOr(&st->timeout, 1);
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tc::kTmemCols) : "memory");
+    if (s_fail && threadIdx.x == 0) atomicOr(&st->timeout, 1);
+    if (warp == 0) {
+        tc::fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * tc::kTmemCols) : "memory");
+    }
 }
