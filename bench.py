@@ -207,6 +207,22 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The slowest rank's time: every rank solves its own replica, the job ends with the last."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rank_info():
+    """(world, rank, local rank) of this process, from the launcher's environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
 def plan_summary(o, tinfo):
     d = o.as_dict()
     keep = {k: d[k] for k in ("precision", "small_front_max", "subtree_levels", "tc_min_cb", "super_panel", "fused_threads")}
@@ -235,9 +251,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = replica_rank_info()
 
     if args.impl == "reference":
         run_reference(args, rank)
@@ -321,10 +335,7 @@ def main():
     acct = fac.profile_read()
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     ms = float(np.sum(per)) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     st = fac.status()
     launches = int(sum(v["launches"] for v in acct.values()))
     nsolve = 2.0 if kind == "adjoint" else float(np.mean(iters)) + 1
@@ -447,10 +458,7 @@ def main():
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
