@@ -225,7 +225,8 @@ def replica_rank_info():
 
 def plan_summary(o, tinfo):
     d = o.as_dict()
-    keep = {k: d[k] for k in ("precision", "small_front_max", "subtree_levels", "tc_min_cb", "super_panel", "fused_threads")}
+    keep = {k: d[k] for k in ("precision", "small_front_max", "subtree_levels", "subtree_solve_levels", "tc_min_cb",
+                              "super_panel", "fused_threads")}
     keep["tuned"] = None if tinfo is None else {"from_cache": bool(tinfo["from_cache"]),
                                                   "ms_best": tinfo["ms_best"], "ms_default": tinfo["ms_default"],
                                                   "candidates": tinfo["candidates"]}

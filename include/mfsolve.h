@@ -77,6 +77,9 @@ typedef struct {
     int subtree_levels;   /* bottom classes fused per subtree (one CTA walks classes 1..n of a
                              subtree with a block barrier between them): n > 0 = at most n
                              (fewer if a subtree would not fit shared memory); <= 0 = off */
+    int subtree_solve_levels; /* bottom classes fused per subtree in the substitutions (one CTA
+                             walks a subtree, update vectors stay in shared memory): n > 0 = at
+                             most n, < 0 = off, 0 = as in the factorization (subtree_levels) */
     int tc_min_cb;        /* MF_TF32: smallest contribution block (m - k) whose Schur update runs
                              on the tensor cores; smaller ones use the SIMT GEMM; 0 = 256 */
     int super_panel;      /* pivots per super-panel of the large-front partial LU (a multiple of the
@@ -274,7 +277,8 @@ int mf_profile_trace(mf_factors* f, mf_trace_rec* out, int cap, int* n);
  *   fused_threads[]  per front-size bucket (per-bucket times of profiled
  *                    factorizations, all buckets in one sweep),
  *   small_front_max  fused / blocked crossover,
- *   subtree_levels   depth of the bottom-class subtree fusion,
+ *   subtree_levels, subtree_solve_levels  depth of the bottom-class subtree
+ *                    fusion of the factorization and of the substitutions,
  *   super_panel      depth of the deferred trailing updates of large fronts,
  *   precision and tc_min_cb  (FP32 family only) SIMT or tensor-core Schur GEMMs.
  * Candidates are timed as one factorization plus one solve (CUDA events on

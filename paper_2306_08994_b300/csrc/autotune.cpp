@@ -31,7 +31,7 @@ struct Timer {
 
 // Version of the launch-plan builder: bumped whenever its kernels or its
 // decomposition change enough that plans tuned before are stale.
-constexpr int kPlanVersion = 3;
+constexpr int kPlanVersion = 4;
 
 int family_of(int precision) { return precision == MF_F64 ? 0 : 1; }
 
@@ -78,6 +78,8 @@ bool cache_lookup(const char* path, const std::string& key, mf_options* o, doubl
     t.tc_min_cb = std::atoi(v);
     if (!(v = field(hit, "super_panel"))) return false;
     t.super_panel = std::atoi(v);
+    if (!(v = field(hit, "subtree_solve_levels"))) return false;
+    t.subtree_solve_levels = std::atoi(v);
     if (!(v = field(hit, "fused_threads")) || *v != '[') return false;
     v++;
     for (int b = 0; b < MF_FUSED_BUCKETS; b++) {
@@ -99,8 +101,9 @@ void cache_append(const char* path, const std::string& key, const mf_options& o,
     FILE* fp = std::fopen(path, "a");
     if (!fp) return;
     std::fprintf(fp, "{\"key\":\"%s\",\"precision\":%d,\"small_front_max\":%d,\"subtree_levels\":%d,\"tc_min_cb\":%d,"
-                     "\"super_panel\":%d,\"fused_threads\":[",
-                 key.c_str(), o.precision, o.small_front_max, o.subtree_levels, o.tc_min_cb, o.super_panel);
+                     "\"super_panel\":%d,\"subtree_solve_levels\":%d,\"fused_threads\":[",
+                 key.c_str(), o.precision, o.small_front_max, o.subtree_levels, o.tc_min_cb, o.super_panel,
+                 o.subtree_solve_levels);
     for (int b = 0; b < MF_FUSED_BUCKETS; b++) std::fprintf(fp, "%s%d", b ? "," : "", o.fused_threads[b]);
     std::fprintf(fp, "],\"ms_best\":%.4f,\"ms_default\":%.4f,\"candidates\":%d}\n", ms_best, ms_default, candidates);
     std::fclose(fp);
@@ -264,6 +267,15 @@ extern "C" int mf_autotune(const mf_analysis* a, const double* d_values, const d
             mf_options t = start;
             t.subtree_levels = lv;
             if (lv != start.subtree_levels) try_one(t);
+        }
+    }
+    if (!rc) {
+        const mf_options start = cur;
+        for (int lv : {-1, 4, 6, 8}) {
+            if (rc) break;
+            mf_options t = start;
+            t.subtree_solve_levels = lv;
+            if (lv != start.subtree_solve_levels) try_one(t);
         }
     }
     if (!rc) {

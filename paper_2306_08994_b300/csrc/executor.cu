@@ -102,7 +102,7 @@ int32_t first_fit(std::vector<std::pair<int32_t, int32_t>> live, int32_t size) {
     return off;
 }
 
-bool subtree_try(const mf_analysis* a, int h, size_t tsize, size_t budget, SubtreePlan& SP) {
+bool subtree_try(const mf_analysis* a, int h, size_t tsize, size_t budget, SubtreePlan& SP, bool factor = true) {
     SP = SubtreePlan{};
     SP.h = h;
     const std::vector<FrontDev>& Fr = a->fronts;
@@ -189,7 +189,7 @@ bool subtree_try(const mf_analysis* a, int h, size_t tsize, size_t budget, Subtr
     SP.lay_s = {0, puv_max};
     SP.smem_f = (size_t)(work_max + pcb_max) * tsize + 8 * 2 * kSubMaxM * sizeof(int32_t) + 64;
     SP.smem_s = (size_t)puv_max * tsize + 16;
-    return SP.smem_f <= budget && SP.smem_s <= budget;
+    return (!factor || SP.smem_f <= budget) && SP.smem_s <= budget;
 }
 
 }  // namespace
@@ -241,10 +241,13 @@ struct mf_factors {
     bool rowabs_valid = false;
     const double* rowabs_values = nullptr;
     // subtree fusion of the bottom classes
-    SubtreePlan sub;
+    SubtreePlan sub;   // subtree fusion of the bottom classes' factorization
+    SubtreePlan subs;  // ... and of their substitutions
     SubtreeTask* d_sub_tasks = nullptr;
     SubtreeEntry* d_sub_ecb = nullptr;
     SubtreeEntry* d_sub_euv = nullptr;
+    SubtreeTask* d_subs_tasks = nullptr;
+    SubtreeEntry* d_subs_euv = nullptr;
     // captured CUDA graphs, keyed by the buffers they were captured with
     struct GraphEntry {
         int kind;  // 0 factor, 1 refine start, 2 refine step
@@ -257,7 +260,7 @@ struct mf_factors {
     std::vector<GraphEntry> graphs;
     // plan
     std::vector<Launch> plan;
-    std::vector<ClassList> classes;
+    std::vector<ClassList> classes_f, classes_b;  // substitution lists per class (forward, backward)
     bool factored = false;
     // algorithmic work per plan entry / per class and direction (per rhs)
     std::vector<double> plan_bytes, plan_flops;
@@ -310,7 +313,7 @@ static void free_factors(mf_factors* f) {
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
-                    f->d_vec, f->d_flist, f->d_slist, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_famax, f->d_status,
+                    f->d_vec, f->d_flist, f->d_slist, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
                     f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -511,10 +514,30 @@ static int build_plan(mf_factors* F) {
             if (subtree_try(a, h, F->tsize, budget, F->sub)) break;
         if (F->sub.tasks.empty() || F->sub.h < 2) F->sub = SubtreePlan{};
         if (F->sub.h >= 2) push({K_SUBTREE, 0, (int)F->sub.tasks.size(), 0, 0}, FAM_FUSED, F->sub.bytes, F->sub.flops);
+        // the substitutions may fuse a different number of bottom classes (their update vectors are
+        // small, so deeper subtrees fit shared memory); default: as many as the factorization
+        int want_s = F->opt.subtree_solve_levels != 0 ? F->opt.subtree_solve_levels : F->sub.h;
+        int hs = want_s <= 0 ? 0 : std::min(std::min(a->n_cls, want_s), kSubMaxLevels);
+        F->subs = SubtreePlan{};
+        if (hs == F->sub.h) F->subs = F->sub;
+        else
+            for (int h = hs; h >= 2; h--)
+                if (subtree_try(a, h, F->tsize, budget, F->subs, false)) break;
+        if (F->subs.tasks.empty() || F->subs.h < 2) F->subs = SubtreePlan{};
+    }
+    // zero update vectors: no pivots in the front's whole subtree (fronts are class-ordered, so
+    // children come first)
+    std::vector<char> zvec(a->n_front, 0);
+    for (int32_t f = 0; f < a->n_front; f++) {
+        const FrontDev& fr = a->fronts[f];
+        bool z = fr.k == 0;
+        for (int q = 0; q < fr.nchild && z; q++) z = zvec[fr.child[q]] != 0;
+        zvec[f] = z ? 1 : 0;
     }
     for (int c = 0; c < a->n_cls; c++) {
         const int32_t f0 = a->cls_ptr[c], f1 = a->cls_ptr[c + 1];
         const bool fused_by_subtree = c < F->sub.h;
+        const bool solved_by_subtree = c < F->subs.h;
         // solve list: all fronts of the class, largest first
         std::vector<int32_t> all;
         int maxm_all = 1;
@@ -523,12 +546,17 @@ static int build_plan(mf_factors* F) {
             maxm_all = std::max(maxm_all, a->fronts[f].m);
         }
         std::stable_sort(all.begin(), all.end(), [&](int32_t x, int32_t y) { return a->fronts[x].m > a->fronts[y].m; });
-        {
+        // Substitution lists.  Forward: a front with no pivots whose children all carry zero update
+        // vectors has a zero update vector itself (the right-hand side enters at the pivot rows), so
+        // it is skipped and its slot of the (zeroed) update-vector arena stays zero.  Backward: a
+        // front with no pivots has nothing to solve.
+        auto make_list = [&](bool forward) {
             ClassList C{};
             std::vector<int32_t> sm, ct, iv, gp[4];
             for (int32_t f : all) {
-                if (fused_by_subtree) break;
+                if (solved_by_subtree) break;
                 const FrontDev& fr = a->fronts[f];
+                if (forward ? zvec[f] : fr.k == 0) continue;
                 if (fr.q_off >= 0) iv.push_back(f);
                 else if (fr.m <= 4) gp[0].push_back(f);
                 else if (fr.m <= 8) gp[1].push_back(f);
@@ -565,8 +593,10 @@ static int build_plan(mf_factors* F) {
                 for (int i = fr.k; i < fr.m; i += 32) rows.push_back({f, i, std::min(fr.m, i + 32), 0});
             }
             C.n_all = (int)(rows.size() - C.off_all);
-            F->classes.push_back(C);
-        }
+            return C;
+        };
+        F->classes_f.push_back(make_list(true));
+        F->classes_b.push_back(make_list(false));
         {
             double fb = 0, bb = 0, ff = 0, bf = 0;
             for (int32_t f : all) {
@@ -578,10 +608,14 @@ static int build_plan(mf_factors* F) {
                     const FrontDev& ch = a->fronts[fr.child[q]];
                     cin += ch.m - ch.k;
                 }
-                fb += T * nl + 8.0 * k * 2 + T * (cin + nc);
-                bb += T * nu + 8.0 * (m + k);
-                ff += 2.0 * nl;
-                bf += 2.0 * nu;
+                if (!zvec[f]) {  // fronts the forward sweep skips move nothing
+                    fb += T * nl + 8.0 * k * 2 + T * (cin + nc);
+                    ff += 2.0 * nl;
+                }
+                if (fr.k > 0) {
+                    bb += T * nu + 8.0 * (m + k);
+                    bf += 2.0 * nu;
+                }
             }
             F->fwd_bytes.push_back(fb);
             F->bwd_bytes.push_back(bb);
@@ -883,6 +917,8 @@ static int build_plan(mf_factors* F) {
     if ((rc = upload(&F->d_sub_tasks, F->sub.tasks))) return rc;
     if ((rc = upload(&F->d_sub_ecb, F->sub.ecb))) return rc;
     if ((rc = upload(&F->d_sub_euv, F->sub.euv))) return rc;
+    if ((rc = upload(&F->d_subs_tasks, F->subs.tasks))) return rc;
+    if ((rc = upload(&F->d_subs_euv, F->subs.euv))) return rc;
     if ((rc = upload(&F->d_asm, asmt))) return rc;
     if ((rc = upload(&F->d_panel, pan))) return rc;
     if ((rc = upload(&F->d_gemm, gem))) return rc;
@@ -974,6 +1010,11 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     TRY(dev_alloc((char**)&F->d_fac, (size_t)a->factor_size * F->tsize));
     TRY(dev_alloc((char**)&F->d_cb, (size_t)a->cb_size * F->tsize));
     TRY(dev_alloc((char**)&F->d_vec, (size_t)a->vec_size * F->max_nrhs * F->tsize));
+    // update vectors of fronts the forward sweep skips must read as zero
+    if (cudaMemset(F->d_vec, 0, (size_t)a->vec_size * F->max_nrhs * F->tsize) != cudaSuccess) {
+        free_factors(F);
+        return MF_ECUDA;
+    }
     TRY(dev_alloc(&F->d_famax, (size_t)a->n_front));
     TRY(dev_alloc(&F->d_status, 1));
     const size_t nv = (size_t)a->n_dof * F->max_nrhs;
@@ -989,7 +1030,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
         int dev = 0, maxsm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        for (const ClassList& C : F->classes) {
+        for (const ClassList& C : F->classes_b) {
             const size_t need = (32 * 33 + 8 * 64 * kRhsChunk + (size_t)kRhsChunk * C.maxm_cta) * F->tsize;
             if (C.n_cta > 0 && need > (size_t)maxsm) {
                 free_factors(F);
@@ -1123,15 +1164,15 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
     const int32_t* L = F->d_slist;
     const int64_t n = a->n_dof, vs = a->vec_size, yss = a->ys_size;
     const size_t dgs = 32 * 33 * sizeof(T);
-    if (F->sub.h >= 2) {
-        int slot = prof_begin(F, s, FAM_FWD, 0, 0, 1, -1, MF_TRACE_SUBTREE_FWD, 0, (int)F->sub.tasks.size());
-        dim3 g((unsigned)F->sub.tasks.size(), nrhs);
+    if (F->subs.h >= 2) {
+        int slot = prof_begin(F, s, FAM_FWD, 0, 0, 1, -1, MF_TRACE_SUBTREE_FWD, 0, (int)F->subs.tasks.size());
+        dim3 g((unsigned)F->subs.tasks.size(), nrhs);
         if (!trans)
-            k_subtree_fwd<T, false><<<g, 256, F->sub.smem_s, s>>>(fr, F->d_sub_tasks, F->d_sub_euv, fac, F->d_dofs, F->d_maps,
-                                                               vec, vs, F->sub.lay_s, d_x, n);
+            k_subtree_fwd<T, false><<<g, 256, F->subs.smem_s, s>>>(fr, F->d_subs_tasks, F->d_subs_euv, fac, F->d_dofs, F->d_maps,
+                                                               vec, vs, F->subs.lay_s, d_x, n);
         else
-            k_subtree_fwd<T, true><<<g, 256, F->sub.smem_s, s>>>(fr, F->d_sub_tasks, F->d_sub_euv, fac, F->d_dofs, F->d_maps,
-                                                              vec, vs, F->sub.lay_s, d_x, n);
+            k_subtree_fwd<T, true><<<g, 256, F->subs.smem_s, s>>>(fr, F->d_subs_tasks, F->d_subs_euv, fac, F->d_dofs, F->d_maps,
+                                                              vec, vs, F->subs.lay_s, d_x, n);
         prof_end(F, s, slot);
         CUDA_TRY(cudaGetLastError());
     }
@@ -1143,7 +1184,7 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         k_inv_gemv<T, TR, PH, 8><<<dim3(CNT, nrhs), 256, (8 * 32 + C.maxin_inv) * sizeof(T), s>>>(               \
             fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_maps, vec, vs, ys, yss, d_x, n)
     for (int c = 0; c < a->n_cls; c++) {
-        const ClassList& C = F->classes[c];
+        const ClassList& C = F->classes_f[c];
         int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0) + (C.n_grp[0] > 0) + (C.n_grp[1] > 0) + (C.n_grp[2] > 0) + (C.n_grp[3] > 0);
         int slot = prof_begin(F, s, FAM_FWD, F->fwd_bytes[c] * nrhs, F->fwd_flops[c] * nrhs, nk, -1, MF_TRACE_FWD_CLASS,
                               c, a->cls_ptr[c + 1] - a->cls_ptr[c]);
@@ -1187,7 +1228,7 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         CUDA_TRY(cudaGetLastError());
     }
     for (int c = a->n_cls - 1; c >= 0; c--) {
-        const ClassList& C = F->classes[c];
+        const ClassList& C = F->classes_b[c];
         int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0) + (C.n_grp[0] > 0) + (C.n_grp[1] > 0) + (C.n_grp[2] > 0) + (C.n_grp[3] > 0);
         int slot = prof_begin(F, s, FAM_BWD, F->bwd_bytes[c] * nrhs, F->bwd_flops[c] * nrhs, nk, -1, MF_TRACE_BWD_CLASS,
                               c, a->cls_ptr[c + 1] - a->cls_ptr[c]);
@@ -1227,13 +1268,13 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         CUDA_TRY(cudaGetLastError());
     }
 #undef INV_LAUNCH
-    if (F->sub.h >= 2) {
-        int slot = prof_begin(F, s, FAM_BWD, 0, 0, 1, -1, MF_TRACE_SUBTREE_BWD, 0, (int)F->sub.tasks.size());
-        dim3 g((unsigned)F->sub.tasks.size(), nrhs);
+    if (F->subs.h >= 2) {
+        int slot = prof_begin(F, s, FAM_BWD, 0, 0, 1, -1, MF_TRACE_SUBTREE_BWD, 0, (int)F->subs.tasks.size());
+        dim3 g((unsigned)F->subs.tasks.size(), nrhs);
         if (!trans)
-            k_subtree_bwd<T, false><<<g, 256, 0, s>>>(fr, F->d_sub_tasks, F->d_sub_euv, fac, F->d_dofs, d_x, n);
+            k_subtree_bwd<T, false><<<g, 256, 0, s>>>(fr, F->d_subs_tasks, F->d_subs_euv, fac, F->d_dofs, d_x, n);
         else
-            k_subtree_bwd<T, true><<<g, 256, 0, s>>>(fr, F->d_sub_tasks, F->d_sub_euv, fac, F->d_dofs, d_x, n);
+            k_subtree_bwd<T, true><<<g, 256, 0, s>>>(fr, F->d_subs_tasks, F->d_subs_euv, fac, F->d_dofs, d_x, n);
         prof_end(F, s, slot);
         CUDA_TRY(cudaGetLastError());
     }

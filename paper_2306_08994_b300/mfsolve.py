@@ -32,7 +32,8 @@ FUSED_BOUNDS = (16, 32, 48, 64, 96, 128, 160, 192, 224)
 class mf_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("pivot_tol", ctypes.c_double), ("pivot_fail", ctypes.c_int),
                 ("small_front_max", ctypes.c_int), ("panel_width", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("max_nrhs", ctypes.c_int), ("subtree_levels", ctypes.c_int), ("tc_min_cb", ctypes.c_int),
+                ("max_nrhs", ctypes.c_int), ("subtree_levels", ctypes.c_int), ("subtree_solve_levels", ctypes.c_int),
+                ("tc_min_cb", ctypes.c_int),
                 ("super_panel", ctypes.c_int), ("fused_threads", ctypes.c_int * MF_FUSED_BUCKETS)]
 
     def as_dict(self) -> dict:

@@ -69,6 +69,8 @@ CASES = {
     "q3_12_no_subtree": (lambda: F.diffusion_2d(12, 3, seed=34), {"subtree_levels": -1, "small_front_max": 32}),
     "q1_9_subtree3_unbalanced": (lambda: F.poisson_2d_q1(9), {"subtree_levels": 3}),
     "q1_3d_5_subtree": (lambda: F.diffusion_3d_q1(5, seed=35), {"subtree_levels": 4, "small_front_max": 24}),
+    "q3_12_solve_subtree_only": (lambda: F.diffusion_2d(12, 3, seed=37), {"subtree_solve_levels": 5}),
+    "q1_20_solve_subtree8": (lambda: F.poisson_2d_q1(20), {"subtree_solve_levels": 8, "small_front_max": 32}),
 }
 
 
