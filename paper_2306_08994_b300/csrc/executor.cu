@@ -18,7 +18,7 @@
 namespace {
 
 enum LaunchKind { K_FUSED = 0, K_ASM = 1, K_PDIAG = 2, K_GEMM = 3, K_INVDIAG = 4, K_SUBTREE = 5, K_GEMMTC = 6, K_GRP = 7,
-                  K_TCPACK = 8 };
+                  K_TCPACK = 8, K_FORK = 10, K_JOIN = 11 };
 
 struct Launch {
     int kind;
@@ -28,6 +28,7 @@ struct Launch {
     int64_t off;  // offset into the list of its kind
     int bucket = -1;  // fused: size bucket (index into kFusedBounds)
     int threads = 0;  // fused: threads per CTA
+    int stream = 0;   // 0: the caller's stream; 1: the side stream (pivot-block inverses)
 };
 
 // Solve plan of one class: fronts split by size (see kernels_solve.cuh).
@@ -234,6 +235,12 @@ struct mf_factors {
     TcPackJob* d_tcjob = nullptr;
     float* d_pk = nullptr;       // packed hi/lo operands of one class (reused class by class)
     int64_t pk_size = 0;
+    float* d_pk2 = nullptr;      // the same for the side stream (pivot-block inverses)
+    int64_t pk2_size = 0;
+    cudaStream_t s2 = nullptr;   // side stream: pivot-block inverses overlap the later classes
+    std::vector<cudaEvent_t> fork_ev;
+    cudaEvent_t join_ev = nullptr;
+    int n_forks = 0;
     unsigned int* d_famax = nullptr;
     DevStatus* d_status = nullptr;
     double *d_r = nullptr, *d_d = nullptr, *d_Y = nullptr, *d_rowabs = nullptr, *d_part = nullptr, *d_norms = nullptr;
@@ -310,10 +317,14 @@ static void prof_end(mf_factors* F, cudaStream_t s, int slot) {
 
 static void free_factors(mf_factors* f) {
     if (!f) return;
+    for (cudaEvent_t e : f->fork_ev)
+        if (e) cudaEventDestroy(e);
+    if (f->join_ev) cudaEventDestroy(f->join_ev);
+    if (f->s2) cudaStreamDestroy(f->s2);
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
-                    f->d_vec, f->d_flist, f->d_slist, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
+                    f->d_vec, f->d_flist, f->d_slist, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
                     f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -414,7 +425,9 @@ static int build_plan(mf_factors* F) {
         double a0 = m - k, b0 = m - 1;
         return (a0 + b0) * (b0 - a0 + 1) / 2.0 + 2.0 * (b0 * (b0 + 1) * (2 * b0 + 1) / 6.0 - (a0 - 1) * a0 * (2 * a0 - 1) / 6.0);
     };
+    int cur_stream = 0;  // stream the launches being planned go to
     auto push = [&](Launch L, int fam, double bytes, double flops) {
+        L.stream = cur_stream;
         F->plan.push_back(L);
         F->plan_fam.push_back(fam);
         F->plan_bytes.push_back(bytes);
@@ -492,7 +505,8 @@ static int build_plan(mf_factors* F) {
                         gtc.push_back(t);
                     }
             }
-            F->pk_size = std::max(F->pk_size, 2 * tc_hi);
+            int64_t& pks = cur_stream ? F->pk2_size : F->pk_size;  // one packed arena per stream
+            pks = std::max(pks, 2 * tc_hi);
             push({K_TCPACK, c, (int)(tcj.size() - joff), 0, joff, (int)tc_p0}, fam, tc_pb, 0.0);
             push({K_GEMMTC, c, (int)(gtc.size() - toff), 0, toff}, fam, tc_gb, tc_gf);
         }
@@ -534,7 +548,7 @@ static int build_plan(mf_factors* F) {
         for (int q = 0; q < fr.nchild && z; q++) z = zvec[fr.child[q]] != 0;
         zvec[f] = z ? 1 : 0;
     }
-    for (int c = 0; c < a->n_cls; c++) {
+    auto class_body = [&](int c) {
         const int32_t f0 = a->cls_ptr[c], f1 = a->cls_ptr[c + 1];
         const bool fused_by_subtree = c < F->sub.h;
         const bool solved_by_subtree = c < F->subs.h;
@@ -624,7 +638,7 @@ static int build_plan(mf_factors* F) {
         }
         slist.insert(slist.end(), all.begin(), all.end());
 
-        if (fused_by_subtree) continue;
+        if (fused_by_subtree) return;
         // tiny fronts (m <= 32): lane-group kernel, G lanes per front
         auto small_bytes = [&](const std::vector<int32_t>& L, double& by, double& fl) {
             by = fl = 0;
@@ -676,7 +690,7 @@ static int build_plan(mf_factors* F) {
         std::vector<int32_t> big;
         for (int32_t f : all)
             if (a->fronts[f].m > F->small_max) big.push_back(f);
-        if (big.empty()) continue;
+        if (big.empty()) return;
         {
             int64_t off = (int64_t)asmt.size();
             double by = 0;
@@ -807,17 +821,21 @@ static int build_plan(mf_factors* F) {
         }
         if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_SCHUR, gb, gf);
         tc_end(c, FAM_SCHUR);
-    }
-    // explicit pivot-block inverses of the large fronts, after the last class
-    {
+    };
+    // Explicit pivot-block inverses (used only by the substitutions): those of class c are computed
+    // on the side stream right after class c, overlapping the factorization of the later classes.
+    int n_forks = 0;
+    auto emit_inverses = [&](int cls) {
         std::vector<int32_t> ivf;
         int maxk = 0;
-        for (int32_t f = 0; f < a->n_front; f++)
+        for (int32_t f = a->cls_ptr[cls]; f < a->cls_ptr[cls + 1]; f++)
             if (a->fronts[f].q_off >= 0) {
                 ivf.push_back(f);
                 maxk = std::max(maxk, a->fronts[f].k);
             }
         if (!ivf.empty()) {
+            push({K_FORK, cls, 0, 0, n_forks++}, FAM_OTHER, 0.0, 0.0);
+            cur_stream = 1;
             int64_t off = (int64_t)invt.size();
             double by = 0, fl = 0;
             for (int32_t f : ivf) {
@@ -829,7 +847,7 @@ static int build_plan(mf_factors* F) {
                     fl += 2.0 * w * w * w / 3.0;
                 }
             }
-            push({K_INVDIAG, a->n_cls - 1, (int)(invt.size() - off), 0, off}, FAM_INV, by, fl);
+            push({K_INVDIAG, cls, (int)(invt.size() - off), 0, off}, FAM_INV, by, fl);
             for (int S = 64; S < maxk; S *= 2) {
                 int64_t scr = 0;
                 int64_t g1 = (int64_t)gem.size();
@@ -891,19 +909,26 @@ static int build_plan(mf_factors* F) {
                 }
                 F->scr_size = std::max(F->scr_size, scr);
                 // phase 1 (products into scratch), then phase 2 (negated products into the inverse)
-                if (gem.size() > (size_t)g1) push({K_GEMM, a->n_cls - 1, (int)(gem.size() - g1), 0, g1}, FAM_INV, gb / 2, gf / 2);
-                tc_end(a->n_cls - 1, FAM_INV);
+                if (gem.size() > (size_t)g1) push({K_GEMM, cls, (int)(gem.size() - g1), 0, g1}, FAM_INV, gb / 2, gf / 2);
+                tc_end(cls, FAM_INV);
                 for (const TcArgs& x : tc2)
                     tc_add(x.aar, x.ao, x.lda, x.bar, x.bo, x.ldb, x.car, x.co, x.ldc, x.M, x.N, x.K, x.op, x.am, x.bm);
                 if (!ph2.empty()) {
                     int64_t g2 = (int64_t)gem.size();
                     gem.insert(gem.end(), ph2.begin(), ph2.end());
-                    push({K_GEMM, a->n_cls - 1, (int)(gem.size() - g2), 0, g2}, FAM_INV, gb / 2, gf / 2);
+                    push({K_GEMM, cls, (int)(gem.size() - g2), 0, g2}, FAM_INV, gb / 2, gf / 2);
                 }
-                tc_end(a->n_cls - 1, FAM_INV);
+                tc_end(cls, FAM_INV);
             }
+            cur_stream = 0;
         }
+    };
+    for (int c = 0; c < a->n_cls; c++) {
+        class_body(c);
+        emit_inverses(c);
     }
+    if (n_forks > 0) push({K_JOIN, a->n_cls - 1, 0, 0, 0}, FAM_OTHER, 0.0, 0.0);
+    F->n_forks = n_forks;
     {
         const double nE = (double)a->n_elem * a->npe;
         F->resid_bytes = 8.0 * (nE * a->npe + nE * 2 + nE * 2 + 2.0 * a->n_dof + 3.0 * a->n_dof);
@@ -1042,6 +1067,23 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     TRY(dev_alloc((char**)&F->d_scr, (size_t)F->scr_size * F->tsize));
     TRY(dev_alloc((char**)&F->d_pnl, (size_t)F->pnl_size * F->tsize));
     if (F->pk_size > 0) TRY(dev_alloc((char**)&F->d_pk, (size_t)F->pk_size * sizeof(float)));
+    if (F->pk2_size > 0) TRY(dev_alloc((char**)&F->d_pk2, (size_t)F->pk2_size * sizeof(float)));
+    if (F->n_forks > 0) {
+        if (cudaStreamCreateWithFlags(&F->s2, cudaStreamNonBlocking) != cudaSuccess) {
+            free_factors(F);
+            return MF_ECUDA;
+        }
+        F->fork_ev.assign(F->n_forks, nullptr);
+        for (int i = 0; i < F->n_forks; i++)
+            if (cudaEventCreateWithFlags(&F->fork_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+                free_factors(F);
+                return MF_ECUDA;
+            }
+        if (cudaEventCreateWithFlags(&F->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+            free_factors(F);
+            return MF_ECUDA;
+        }
+    }
     TRY(dev_alloc((char**)&F->d_ys, (size_t)a->ys_size * F->max_nrhs * F->tsize));
 #undef TRY
     *out = F;
@@ -1059,8 +1101,21 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
     k_init_status<<<1, 1, 0, s>>>(F->d_status);
     CUDA_TRY(cudaMemsetAsync(F->d_famax, 0, sizeof(unsigned int) * a->n_front, s));
     prof_end(F, s, slot);
+    const cudaStream_t s_main = s;
     for (size_t li = 0; li < F->plan.size(); li++) {
         const Launch& L = F->plan[li];
+        if (L.kind == K_FORK) {  // the side stream continues after everything issued so far
+            CUDA_TRY(cudaEventRecord(F->fork_ev[L.off], s_main));
+            CUDA_TRY(cudaStreamWaitEvent(F->s2, F->fork_ev[L.off], 0));
+            continue;
+        }
+        if (L.kind == K_JOIN) {  // the caller's stream waits for the side stream's work
+            CUDA_TRY(cudaEventRecord(F->join_ev, F->s2));
+            CUDA_TRY(cudaStreamWaitEvent(s_main, F->join_ev, 0));
+            continue;
+        }
+        s = L.stream ? F->s2 : s_main;
+        float* pk = L.stream ? F->d_pk2 : F->d_pk;
         slot = prof_begin(F, s, F->plan_fam[li], F->plan_bytes[li], F->plan_flops[li], 1,
                           F->plan[li].kind == K_FUSED ? F->plan[li].bucket : -1, F->plan[li].kind, F->plan[li].cls,
                           F->plan[li].count);
@@ -1111,14 +1166,14 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
             case K_TCPACK:
                 if constexpr (sizeof(T) == 4) {
                     Arenas<float> ar{{fac, cb, (float*)F->d_inv, (float*)F->d_scr, (float*)F->d_pnl}};
-                    k_tc_pack<<<L.count, 256, 0, s>>>(F->d_tcpack + L.bucket, F->d_tcjob + L.off, ar, F->d_pk);
+                    k_tc_pack<<<L.count, 256, 0, s>>>(F->d_tcpack + L.bucket, F->d_tcjob + L.off, ar, pk);
                 }
                 break;
             case K_GEMMTC:
                 if constexpr (sizeof(T) == 4) {
                     Arenas<float> ar{{fac, cb, (float*)F->d_inv, (float*)F->d_scr, (float*)F->d_pnl}};
                     k_schur_tc<<<std::min(L.count, F->num_sms), kTcThreads, tc::kSmemBytes, s>>>(F->d_gtc + L.off, L.count,
-                                                                                                  F->d_pk, ar, F->d_status);
+                                                                                                  pk, ar, F->d_status);
                 }
                 break;
             case K_INVDIAG:
