@@ -77,6 +77,10 @@ typedef struct {
     int subtree_levels;   /* bottom classes fused per subtree (one CTA walks classes 1..n of a
                              subtree with a block barrier between them): n > 0 = at most n
                              (fewer if a subtree would not fit shared memory); <= 0 = off */
+    int sweep_kernel;     /* substitutions of the top classes in one persistent cooperative launch
+                             per sweep (bounded grid barriers between dependent phases) instead of
+                             one launch per class and kind: 0 = off (default), n > 0 = the top n
+                             classes, -1 = every class with at most 2048 fronts */
     int subtree_solve_levels; /* bottom classes fused per subtree in the substitutions (one CTA
                              walks a subtree, update vectors stay in shared memory): n > 0 = at
                              most n, < 0 = off, 0 = as in the factorization (subtree_levels) */
@@ -263,6 +267,8 @@ int mf_profile_read(mf_factors* f, double* ms, int64_t* launches, double* bytes,
 #define MF_TRACE_BWD_CLASS 101
 #define MF_TRACE_SUBTREE_FWD 102
 #define MF_TRACE_SUBTREE_BWD 103
+#define MF_TRACE_FWD_SWEEP 104   /* persistent forward sweep (all classes above the subtrees) */
+#define MF_TRACE_BWD_SWEEP 105
 #define MF_TRACE_OTHER 199
 typedef struct {
     int family, kind, cls, tasks;

@@ -41,6 +41,7 @@ struct ClassList {
     int64_t off_piv, off_all;     // into the row-block list (inverse fronts)
 };
 constexpr int kSolveWarpMax = 64;   // m <= this: one warp per front
+constexpr int kSweepMaxFronts = 2048;  // classes with at most this many fronts join the persistent sweep
 
 #define CUDA_TRY(x)                          \
     do {                                     \
@@ -268,6 +269,14 @@ struct mf_factors {
     // plan
     std::vector<Launch> plan;
     std::vector<ClassList> classes_f, classes_b;  // substitution lists per class (forward, backward)
+    // persistent substitution sweeps: phase tables, shared-memory size, bytes/flops per sweep
+    std::vector<SweepPhase> sweep_f, sweep_b;
+    SweepPhase* d_sweep_f = nullptr;
+    SweepPhase* d_sweep_b = nullptr;
+    size_t sweep_smem_f = 0, sweep_smem_b = 0;
+    unsigned int* d_bar = nullptr;
+    bool use_sweep = true;
+    int sweep_c0 = 0;  // classes >= sweep_c0 run in the persistent sweeps, the ones below per class
     bool factored = false;
     // algorithmic work per plan entry / per class and direction (per rhs)
     std::vector<double> plan_bytes, plan_flops;
@@ -324,7 +333,7 @@ static void free_factors(mf_factors* f) {
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
-                    f->d_vec, f->d_flist, f->d_slist, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
+                    f->d_vec, f->d_flist, f->d_slist, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
                     f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -934,7 +943,70 @@ static int build_plan(mf_factors* F) {
         F->resid_bytes = 8.0 * (nE * a->npe + nE * 2 + nE * 2 + 2.0 * a->n_dof + 3.0 * a->n_dof);
         F->resid_flops = 2.0 * nE * a->npe;
     }
+    // persistent-sweep phase tables (classes above the fused subtrees)
+    {
+        auto add = [&](std::vector<SweepPhase>& out, int kind, int count, int64_t off, int n, int ldw) {
+            if (count > 0) out.push_back({kind, count, off, n, ldw, 0, 0});
+        };
+        auto end_group = [&](std::vector<SweepPhase>& out, size_t start) {
+            if (out.size() > start) out.back().barrier = 1;
+        };
+        const size_t TS = F->tsize;
+        F->sweep_smem_f = F->sweep_smem_b = 16;
+        // the sweep takes the narrow top of the tree, where launch latency dominates; the wide bottom
+        // classes keep their own launches (full occupancy for their many small fronts)
+        int c0 = a->n_cls;
+        if (F->use_sweep) {
+            if (F->opt.sweep_kernel > 0) c0 = std::max(0, a->n_cls - F->opt.sweep_kernel);
+            else
+                while (c0 > 0 && a->cls_ptr[c0] - a->cls_ptr[c0 - 1] <= kSweepMaxFronts) c0--;
+        }
+        F->sweep_c0 = std::max(c0, F->subs.h);
+        for (int c = F->sweep_c0; c < a->n_cls; c++) {
+            const ClassList& C = F->classes_f[c];
+            size_t st = F->sweep_f.size();
+            add(F->sweep_f, SW_GRP4, (C.n_grp[0] + 63) / 64, C.off_grp[0], C.n_grp[0], 0);
+            add(F->sweep_f, SW_GRP8, (C.n_grp[1] + 31) / 32, C.off_grp[1], C.n_grp[1], 0);
+            add(F->sweep_f, SW_GRP16, (C.n_grp[2] + 15) / 16, C.off_grp[2], C.n_grp[2], 0);
+            add(F->sweep_f, SW_WARP, (C.n_grp[3] + 7) / 8, C.off_grp[3], C.n_grp[3], 0);
+            add(F->sweep_f, SW_WARP, (C.n_small + 7) / 8, C.off_small, C.n_small, 0);
+            add(F->sweep_f, SW_CTA, C.n_cta, C.off_cta, C.n_cta, C.maxm_cta);
+            add(F->sweep_f, SW_INV1, C.n_piv, C.off_piv, 0, 0);
+            if (C.n_piv > 0) {
+                end_group(F->sweep_f, st);
+                st = F->sweep_f.size();
+                add(F->sweep_f, SW_INV2, C.n_all, C.off_all, 0, 0);
+            }
+            end_group(F->sweep_f, st);
+            if (C.n_cta) F->sweep_smem_f = std::max(F->sweep_smem_f, (32 * 33 + (size_t)kRhsChunk * C.maxm_cta) * TS);
+            if (C.n_piv) F->sweep_smem_f = std::max(F->sweep_smem_f, (8 * 32 + (size_t)C.maxin_inv) * TS);
+        }
+        for (int c = a->n_cls - 1; c >= F->sweep_c0; c--) {
+            const ClassList& C = F->classes_b[c];
+            size_t st = F->sweep_b.size();
+            add(F->sweep_b, SW_GRP4, (C.n_grp[0] + 63) / 64, C.off_grp[0], C.n_grp[0], 0);
+            add(F->sweep_b, SW_GRP8, (C.n_grp[1] + 31) / 32, C.off_grp[1], C.n_grp[1], 0);
+            add(F->sweep_b, SW_GRP16, (C.n_grp[2] + 15) / 16, C.off_grp[2], C.n_grp[2], 0);
+            add(F->sweep_b, SW_GRP32, (C.n_grp[3] + 7) / 8, C.off_grp[3], C.n_grp[3], 0);
+            add(F->sweep_b, SW_WARP, (C.n_small + 7) / 8, C.off_small, C.n_small, 0);
+            add(F->sweep_b, SW_CTA, C.n_cta, C.off_cta, C.n_cta, C.maxm_cta);
+            add(F->sweep_b, SW_INV1, C.n_piv, C.off_piv, 0, 0);
+            if (C.n_piv > 0) {
+                end_group(F->sweep_b, st);
+                st = F->sweep_b.size();
+                add(F->sweep_b, SW_INV2, C.n_piv, C.off_piv, 0, 0);
+            }
+            end_group(F->sweep_b, st);
+            if (C.n_cta)
+                F->sweep_smem_b = std::max(F->sweep_smem_b, (32 * 33 + 8 * 64 * kRhsChunk + (size_t)kRhsChunk * C.maxm_cta) * TS);
+            if (C.n_piv) F->sweep_smem_b = std::max(F->sweep_smem_b, (8 * 32 + (size_t)C.maxin_inv) * TS);
+        }
+        if (!F->sweep_f.empty()) F->sweep_f.back().barrier = 0;  // the end of the launch is the last barrier
+        if (!F->sweep_b.empty()) F->sweep_b.back().barrier = 0;
+    }
     int rc;
+    if ((rc = upload(&F->d_sweep_f, F->sweep_f))) return rc;
+    if ((rc = upload(&F->d_sweep_b, F->sweep_b))) return rc;
     if ((rc = upload(&F->d_flist, flist))) return rc;
     if ((rc = upload(&F->d_slist, slist))) return rc;
     if ((rc = upload(&F->d_rows, rows))) return rc;
@@ -1000,6 +1072,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     F->small_max = std::min(F->small_max, F->prec == MF_F64 ? 160 : 224);
     F->small_max = std::max(F->small_max, a->npe);
     F->tc_min = F->opt.tc_min_cb > 0 ? F->opt.tc_min_cb : 256;
+    F->use_sweep = F->opt.sweep_kernel != 0;
     {
         int dev = 0;
         cudaGetDevice(&dev);
@@ -1042,6 +1115,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     }
     TRY(dev_alloc(&F->d_famax, (size_t)a->n_front));
     TRY(dev_alloc(&F->d_status, 1));
+    TRY(dev_alloc(&F->d_bar, 2));
     const size_t nv = (size_t)a->n_dof * F->max_nrhs;
     TRY(dev_alloc(&F->d_r, nv));
     TRY(dev_alloc(&F->d_d, nv));
@@ -1199,6 +1273,31 @@ extern "C" int mf_factor(mf_factors* F, const double* d_values, mf_stream_t stre
     return rc;
 }
 
+// One cooperative launch of a persistent substitution sweep (all CTAs resident,
+// as many per SM as fit).  Returns MF_ENOTSUP when the sweep cannot be
+// resident (the caller then uses per-class launches).
+template <typename T, bool TR, bool FWD>
+static int launch_sweep(mf_factors* F, const SweepArgs<T>& args, size_t smem, int nrhs, cudaStream_t s) {
+    void (*kern)(SweepArgs<T>) = nrhs == 1 ? k_solve_sweep<T, TR, FWD, 1> : k_solve_sweep<T, TR, FWD, kRhsChunk>;
+    if (smem > 48 * 1024) CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem));
+    if (per_sm < 1) return MF_ENOTSUP;
+    CUDA_TRY(cudaMemsetAsync(F->d_bar, 0, 2 * sizeof(unsigned int), s));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(per_sm * F->num_sms));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, args));
+    return MF_OK;
+}
+
 // Launch a solve kernel templated on the right-hand-side chunk NR: 1 for a
 // single right-hand side, kRhsChunk otherwise.
 #define SOLVE_UNPAREN(...) __VA_ARGS__
@@ -1231,6 +1330,51 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         prof_end(F, s, slot);
         CUDA_TRY(cudaGetLastError());
     }
+    // classes [c_top, n_cls) run in the persistent sweeps when they are enabled and fit
+    const bool sweep = F->use_sweep && !F->sweep_f.empty() && !F->sweep_b.empty();
+    int c_top = sweep ? F->sweep_c0 : a->n_cls;
+    auto run_sweeps = [&](bool forward) -> int {
+        double fb = 0, bb = 0, ff = 0, bf = 0;
+        for (int c = F->sweep_c0; c < a->n_cls; c++) {
+            fb += F->fwd_bytes[c];
+            bb += F->bwd_bytes[c];
+            ff += F->fwd_flops[c];
+            bf += F->bwd_flops[c];
+        }
+        SweepArgs<T> args{fr, L, F->d_rows, fac, inv, F->d_dofs, F->d_maps, vec, vs, ys, yss, d_x, n, nrhs,
+                          forward ? F->d_sweep_f : F->d_sweep_b,
+                          (int)(forward ? F->sweep_f.size() : F->sweep_b.size()), F->d_bar, F->d_status};
+        int slot = forward ? prof_begin(F, s, FAM_FWD, fb * nrhs, ff * nrhs, 1, -1, MF_TRACE_FWD_SWEEP, -1, args.n_phases)
+                           : prof_begin(F, s, FAM_BWD, bb * nrhs, bf * nrhs, 1, -1, MF_TRACE_BWD_SWEEP, -1, args.n_phases);
+        int rc;
+        if (forward)
+            rc = trans ? launch_sweep<T, true, true>(F, args, F->sweep_smem_f, nrhs, s)
+                       : launch_sweep<T, false, true>(F, args, F->sweep_smem_f, nrhs, s);
+        else
+            rc = trans ? launch_sweep<T, true, false>(F, args, F->sweep_smem_b, nrhs, s)
+                       : launch_sweep<T, false, false>(F, args, F->sweep_smem_b, nrhs, s);
+        prof_end(F, s, slot);
+        return rc;
+    };
+    if (sweep) {  // the sweep must be resident before any class relies on it
+        int per_sm = 0;
+        void (*kf)(SweepArgs<T>) = nrhs == 1 ? (trans ? k_solve_sweep<T, true, true, 1> : k_solve_sweep<T, false, true, 1>)
+                                             : (trans ? k_solve_sweep<T, true, true, kRhsChunk>
+                                                      : k_solve_sweep<T, false, true, kRhsChunk>);
+        void (*kb)(SweepArgs<T>) = nrhs == 1 ? (trans ? k_solve_sweep<T, true, false, 1> : k_solve_sweep<T, false, false, 1>)
+                                             : (trans ? k_solve_sweep<T, true, false, kRhsChunk>
+                                                      : k_solve_sweep<T, false, false, kRhsChunk>);
+        bool ok = true;
+        if (F->sweep_smem_f > 48 * 1024)
+            CUDA_TRY(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F->sweep_smem_f));
+        if (F->sweep_smem_b > 48 * 1024)
+            CUDA_TRY(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F->sweep_smem_b));
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, 256, F->sweep_smem_f));
+        ok = ok && per_sm >= 1;
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb, 256, F->sweep_smem_b));
+        ok = ok && per_sm >= 1;
+        if (!ok) c_top = a->n_cls;  // not resident: per-class launches for every class
+    }
 #define INV_LAUNCH(TR, PH, CNT, OFF)                                                                               \
     if ((PH == PH_BWD1 ? C.maxnc_inv : C.maxk_inv) > 512)                                                          \
         k_inv_gemv<T, TR, PH, 32><<<dim3(CNT, nrhs), 1024, (32 * 32 + C.maxin_inv) * sizeof(T), s>>>(            \
@@ -1238,7 +1382,7 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
     else                                                                                                           \
         k_inv_gemv<T, TR, PH, 8><<<dim3(CNT, nrhs), 256, (8 * 32 + C.maxin_inv) * sizeof(T), s>>>(               \
             fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_maps, vec, vs, ys, yss, d_x, n)
-    for (int c = 0; c < a->n_cls; c++) {
+    for (int c = 0; c < c_top; c++) {
         const ClassList& C = F->classes_f[c];
         int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0) + (C.n_grp[0] > 0) + (C.n_grp[1] > 0) + (C.n_grp[2] > 0) + (C.n_grp[3] > 0);
         int slot = prof_begin(F, s, FAM_FWD, F->fwd_bytes[c] * nrhs, F->fwd_flops[c] * nrhs, nk, -1, MF_TRACE_FWD_CLASS,
@@ -1282,7 +1426,13 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         prof_end(F, s, slot);
         CUDA_TRY(cudaGetLastError());
     }
-    for (int c = a->n_cls - 1; c >= 0; c--) {
+    if (c_top < a->n_cls) {
+        int rc = run_sweeps(true);
+        if (rc != MF_OK) return rc;
+        rc = run_sweeps(false);
+        if (rc != MF_OK) return rc;
+    }
+    for (int c = c_top - 1; c >= 0; c--) {
         const ClassList& C = F->classes_b[c];
         int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0) + (C.n_grp[0] > 0) + (C.n_grp[1] > 0) + (C.n_grp[2] > 0) + (C.n_grp[3] > 0);
         int slot = prof_begin(F, s, FAM_BWD, F->bwd_bytes[c] * nrhs, F->bwd_flops[c] * nrhs, nk, -1, MF_TRACE_BWD_CLASS,

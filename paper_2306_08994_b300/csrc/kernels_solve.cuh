@@ -44,10 +44,10 @@ template <typename T>
 __device__ __forceinline__ T gather_rhs(const FrontDev& fr, const FrontDev* __restrict__ fronts, const int32_t* __restrict__ fd,
                                         const int32_t* __restrict__ maps, const T* __restrict__ vr,
                                         const double* __restrict__ xr, int i) {
-    T v = i < fr.k ? (T)xr[fd[i]] : T(0);
+    T v = i < fr.k ? (T)__ldcg(xr + fd[i]) : T(0);
     for (int c = 0; c < fr.nchild; c++) {
         int ic = maps[fr.map_off + (int64_t)c * fr.m + i];
-        if (ic >= 0) v += vr[fronts[fr.child[c]].vec_off + ic];
+        if (ic >= 0) v += __ldcg(vr + fronts[fr.child[c]].vec_off + ic);
     }
     return v;
 }
@@ -74,9 +74,9 @@ __device__ __forceinline__ RhsSrc rhs_src(const FrontDev& fr, const FrontDev* __
 }
 template <typename T>
 __device__ __forceinline__ T rhs_val(const RhsSrc& q, const T* __restrict__ vr, const double* __restrict__ xr) {
-    T v = q.xi >= 0 ? (T)xr[q.xi] : T(0);
-    if (q.v0 >= 0) v += vr[q.v0];
-    if (q.v1 >= 0) v += vr[q.v1];
+    T v = q.xi >= 0 ? (T)__ldcg(xr + q.xi) : T(0);
+    if (q.v0 >= 0) v += __ldcg(vr + q.v0);
+    if (q.v1 >= 0) v += __ldcg(vr + q.v1);
     return v;
 }
 
@@ -98,11 +98,11 @@ __device__ __forceinline__ T apply_pivot(T w, T ds) {
 
 // Small fronts (m <= 64): one warp per front, rows lane and lane+32.
 template <typename T, bool TRANS, int NR>
-__global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_fwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__device__ __forceinline__ void k_fwd_warp_body(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                   int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                   const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
-                                                  double* __restrict__ x, int64_t n_dof, int nrhs) {
-    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int vb) {
+    const int wid = vb * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (wid >= count) return;
     const FrontDev fr = fronts[list[wid]];
@@ -168,12 +168,19 @@ __global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_fwd_warp(const FrontDe
         }
     }
 }
+template <typename T, bool TRANS, int NR>
+__global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_fwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
+                                                  const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
+                                                  double* __restrict__ x, int64_t n_dof, int nrhs) {
+    k_fwd_warp_body<T, TRANS, NR>(fronts, list, count, fac, dofs, maps, vecs, vec_size, x, n_dof, nrhs, blockIdx.x);
+}
 
 template <typename T, bool TRANS, int NR>
-__global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_bwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__device__ __forceinline__ void k_bwd_warp_body(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                   int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
-                                                  double* __restrict__ x, int64_t n_dof, int nrhs) {
-    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int vb) {
+    const int wid = vb * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (wid >= count) return;
     const FrontDev fr = fronts[list[wid]];
@@ -190,8 +197,8 @@ __global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_bwd_warp(const FrontDe
 #pragma unroll
         for (int rr = 0; rr < NR; rr++) {
             const double* xr = x + (int64_t)(rb + rr) * n_dof;
-            v0[rr] = (rr < nr && i0 < m) ? (T)xr[d0] : T(0);
-            v1[rr] = (rr < nr && i1 < m) ? (T)xr[d1] : T(0);
+            v0[rr] = (rr < nr && i0 < m) ? (T)__ldcg(xr + d0) : T(0);
+            v1[rr] = (rr < nr && i1 < m) ? (T)__ldcg(xr + d1) : T(0);
         }
         // eliminate the CB unknowns from the pivot rows (j >= k), then back-substitute
         for (int jc = m - 1; jc >= 0; jc -= 8) {
@@ -231,17 +238,23 @@ __global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_bwd_warp(const FrontDe
         }
     }
 }
+template <typename T, bool TRANS, int NR>
+__global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_bwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
+                                                  double* __restrict__ x, int64_t n_dof, int nrhs) {
+    k_bwd_warp_body<T, TRANS, NR>(fronts, list, count, fac, dofs, x, n_dof, nrhs, blockIdx.x);
+}
 
 // Tiny fronts (m <= G, G in {4, 8, 16, 32}): 32/G fronts per warp, one lane
 // per row, shuffles of width G; all coefficients are loaded once, before the
 // short sequential pivot loop.
 template <typename T, bool TRANS, int G, int NR>
-__global__ void __launch_bounds__(256) k_fwd_grp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__device__ __forceinline__ void k_fwd_grp_body(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
-                                                 double* __restrict__ x, int64_t n_dof, int nrhs) {
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int vb) {
     const int lane = threadIdx.x & 31;
-    const int fidx = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
+    const int fidx = (vb * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
     const bool active = fidx < count;
     const int i = lane % G;
     FrontDev fr{};
@@ -292,13 +305,20 @@ __global__ void __launch_bounds__(256) k_fwd_grp(const FrontDev* __restrict__ fr
         }
     }
 }
+template <typename T, bool TRANS, int G, int NR>
+__global__ void __launch_bounds__(256) k_fwd_grp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+                                                 int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
+                                                 const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs) {
+    k_fwd_grp_body<T, TRANS, G, NR>(fronts, list, count, fac, dofs, maps, vecs, vec_size, x, n_dof, nrhs, blockIdx.x);
+}
 
 template <typename T, bool TRANS, int G, int NR>
-__global__ void __launch_bounds__(256) k_bwd_grp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__device__ __forceinline__ void k_bwd_grp_body(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
-                                                 double* __restrict__ x, int64_t n_dof, int nrhs) {
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int vb) {
     const int lane = threadIdx.x & 31;
-    const int fidx = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
+    const int fidx = (vb * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
     const bool active = fidx < count;
     const int i = lane % G;
     FrontDev fr{};
@@ -323,7 +343,7 @@ __global__ void __launch_bounds__(256) k_bwd_grp(const FrontDev* __restrict__ fr
         const int nr = min(NR, nrhs - rb);
         T v[NR];
 #pragma unroll
-        for (int rr = 0; rr < NR; rr++) v[rr] = (rr < nr && active && i < m) ? (T)x[(int64_t)(rb + rr) * n_dof + di] : T(0);
+        for (int rr = 0; rr < NR; rr++) v[rr] = (rr < nr && active && i < m) ? (T)__ldcg(x + (int64_t)(rb + rr) * n_dof + di) : T(0);
 #pragma unroll
         for (int j = G - 1; j >= 0; j--) {
             if (j >= mmax) continue;
@@ -345,6 +365,12 @@ __global__ void __launch_bounds__(256) k_bwd_grp(const FrontDev* __restrict__ fr
         }
     }
 }
+template <typename T, bool TRANS, int G, int NR>
+__global__ void __launch_bounds__(256) k_bwd_grp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+                                                 int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs) {
+    k_bwd_grp_body<T, TRANS, G, NR>(fronts, list, count, fac, dofs, x, n_dof, nrhs, blockIdx.x);
+}
 
 // Mid-size fronts (m > 64, k < kInvMinK): one CTA per front.  The pivot block
 // is processed in 32-wide blocks; each 32x32 diagonal block is staged in
@@ -352,14 +378,14 @@ __global__ void __launch_bounds__(256) k_bwd_grp(const FrontDev* __restrict__ fr
 // applied to the later rows, including the contribution-block rows (update
 // vector).  Shared memory: 32 x 33 T + kRhsChunk x ldw T (ldw >= m).
 template <typename T, bool TRANS>
-__global__ void __launch_bounds__(256) k_fwd_cta(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__device__ __forceinline__ void k_fwd_cta_body(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                  int rows_all, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
-                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int ldw) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int ldw, int vb, unsigned char* smem_raw) {
+    __syncthreads();  // in a persistent sweep the previous body of this CTA may still be reading shared memory
     T* Dg = reinterpret_cast<T*>(smem_raw);  // 32 x 33
     T* w = Dg + 32 * 33;                     // kRhsChunk x ldw
-    const FrontDev fr = fronts[list[blockIdx.x]];
+    const FrontDev fr = fronts[list[vb]];
     const int m = fr.m, k = fr.k;
     const int mr = rows_all ? m : k;
     const int32_t* fd = dofs + fr.dof_off;
@@ -427,19 +453,27 @@ __global__ void __launch_bounds__(256) k_fwd_cta(const FrontDev* __restrict__ fr
         __syncthreads();
     }
 }
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256) k_fwd_cta(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+                                                 int rows_all, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
+                                                 const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int ldw) {
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    k_fwd_cta_body<T, TRANS>(fronts, list, rows_all, fac, dofs, maps, vecs, vec_size, x, n_dof, nrhs, ldw, blockIdx.x, smem_dyn);
+}
 
 // Backward, one CTA per mid-size front: the CB part of the pivot rows first,
 // then the unit (or, transposed, L11^T) triangle in 32-wide blocks.
 // Shared memory: 32 x 33 T + 8 x 64 x kRhsChunk T + kRhsChunk x ldw T.
 template <typename T, bool TRANS>
-__global__ void __launch_bounds__(256) k_bwd_cta(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                  int cb_done, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
-                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int ldw) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int ldw, int vb, unsigned char* smem_raw) {
+    __syncthreads();  // in a persistent sweep the previous body of this CTA may still be reading shared memory
     T* Dg = reinterpret_cast<T*>(smem_raw);
     T* red = Dg + 32 * 33;                // 8 warps x 64 rows x kRhsChunk
     T* v = red + 8 * 64 * kRhsChunk;      // kRhsChunk x ldw
-    const FrontDev fr = fronts[list[blockIdx.x]];
+    const FrontDev fr = fronts[list[vb]];
     const int m = fr.m, k = fr.k;
     const int32_t* fd = dofs + fr.dof_off;
     const T* P = fac + fr.P_off;
@@ -450,7 +484,7 @@ __global__ void __launch_bounds__(256) k_bwd_cta(const FrontDev* __restrict__ fr
         const int nr = min(kRhsChunk, nrhs - rb);
         for (int i = threadIdx.x; i < mv; i += blockDim.x) {
             const int d = fd[i];
-            for (int rr = 0; rr < nr; rr++) v[rr * ldw + i] = (T)x[(int64_t)(rb + rr) * n_dof + d];
+            for (int rr = 0; rr < nr; rr++) v[rr * ldw + i] = (T)__ldcg(x + (int64_t)(rb + rr) * n_dof + d);
         }
         __syncthreads();
         if (!cb_done) {
@@ -538,6 +572,13 @@ __global__ void __launch_bounds__(256) k_bwd_cta(const FrontDev* __restrict__ fr
         __syncthreads();
     }
 }
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256) k_bwd_cta(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+                                                 int cb_done, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int ldw) {
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    k_bwd_cta_body<T, TRANS>(fronts, list, cb_done, fac, dofs, x, n_dof, nrhs, ldw, blockIdx.x, smem_dyn);
+}
 
 // ---------------------------------------------------------------------------
 // Fronts with explicit pivot-block inverses (k >= kInvMinK): each sweep is
@@ -566,16 +607,16 @@ __device__ __forceinline__ T inv_coef(const T* __restrict__ P, const T* __restri
 }
 
 template <typename T, bool TRANS, int PH, int NW>
-__global__ void __launch_bounds__(NW * 32) k_inv_gemv(const FrontDev* __restrict__ fronts, const RowBlock* __restrict__ tasks,
+__device__ __forceinline__ void k_inv_gemv_body(const FrontDev* __restrict__ fronts, const RowBlock* __restrict__ tasks,
                                                   const T* __restrict__ fac, const T* __restrict__ inv,
                                                   const int32_t* __restrict__ dofs, const int32_t* __restrict__ maps,
                                                   T* __restrict__ vecs, int64_t vec_size, T* __restrict__ ys,
-                                                  int64_t ys_size, double* __restrict__ x, int64_t n_dof) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                  int64_t ys_size, double* __restrict__ x, int64_t n_dof, int vb, unsigned char* smem_raw, int rr) {
+    __syncthreads();  // in a persistent sweep the previous body of this CTA may still be reading shared memory
     T* red = reinterpret_cast<T*>(smem_raw);  // NW x 32
     T* vin = red + NW * 32;
-    const RowBlock t = tasks[blockIdx.x];
-    const int r = blockIdx.y;
+    const RowBlock t = tasks[vb];
+    const int r = rr;
     const FrontDev fr = fronts[t.front];
     const int m = fr.m, k = fr.k;
     const int32_t* fd = dofs + fr.dof_off;
@@ -586,15 +627,15 @@ __global__ void __launch_bounds__(NW * 32) k_inv_gemv(const FrontDev* __restrict
     const T* R = fac + fr.R_off;
     const T* Q = inv + (fr.q_off >= 0 ? fr.q_off : 0);
     if (PH == PH_FWD2 && t.r0 < k) {
-        for (int i = t.r0 + threadIdx.x; i < t.r1; i += blockDim.x) xr[fd[i]] = (double)yr[i];
+        for (int i = t.r0 + threadIdx.x; i < t.r1; i += blockDim.x) xr[fd[i]] = (double)__ldcg(yr + i);
         return;
     }
     const int nin = (PH == PH_BWD1) ? m - k : k;
     for (int j = threadIdx.x; j < nin; j += blockDim.x) {
         T v;
         if (PH == PH_FWD1) v = gather_rhs<T>(fr, fronts, fd, maps, vr, xr, j);
-        else if (PH == PH_BWD1) v = (T)xr[fd[k + j]];
-        else v = yr[j];
+        else if (PH == PH_BWD1) v = (T)__ldcg(xr + fd[k + j]);
+        else v = __ldcg(yr + j);
         vin[j] = v;
     }
     __syncthreads();
@@ -605,7 +646,7 @@ __global__ void __launch_bounds__(NW * 32) k_inv_gemv(const FrontDev* __restrict
     auto finish = [&](int i, T acc) {
         if (PH == PH_FWD1) yr[i] = acc;
         else if (PH == PH_FWD2) vr[fr.vec_off + (i - k)] = gather_rhs<T>(fr, fronts, fd, maps, vr, xr, i) - acc;
-        else if (PH == PH_BWD1) yr[i] = (T)xr[fd[i]] - acc;
+        else if (PH == PH_BWD1) yr[i] = (T)__ldcg(xr + fd[i]) - acc;
         else xr[fd[i]] = (double)acc;
     };
     if (!TRANS) {
@@ -655,6 +696,151 @@ __global__ void __launch_bounds__(NW * 32) k_inv_gemv(const FrontDev* __restrict
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
             if (lane == 0) finish(i, sum);
         }
+    }
+}
+template <typename T, bool TRANS, int PH, int NW>
+__global__ void __launch_bounds__(NW * 32) k_inv_gemv(const FrontDev* __restrict__ fronts, const RowBlock* __restrict__ tasks,
+                                                  const T* __restrict__ fac, const T* __restrict__ inv,
+                                                  const int32_t* __restrict__ dofs, const int32_t* __restrict__ maps,
+                                                  T* __restrict__ vecs, int64_t vec_size, T* __restrict__ ys,
+                                                  int64_t ys_size, double* __restrict__ x, int64_t n_dof) {
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    k_inv_gemv_body<T, TRANS, PH, NW>(fronts, tasks, fac, inv, dofs, maps, vecs, vec_size, ys, ys_size, x, n_dof, blockIdx.x, smem_dyn, blockIdx.y);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent substitution sweep: one cooperative launch walks every class of
+// the forward (or backward) sweep.  A phase is one kernel type of one class
+// over its task list; the CTAs take its virtual blocks as a bag of tasks
+// (vb = blockIdx.x, +gridDim.x, ...) and run the same bodies as the per-class
+// kernels.  Phases of one class touch disjoint fronts; a grid barrier
+// separates dependent phases (class c+1 after class c; the second inverse
+// product after the first).  The barrier is bounded: after 1 s of waiting
+// a CTA records a timeout and the whole sweep returns.  Data written by
+// other CTAs earlier in the sweep (x, update vectors, pivot scratch) is
+// read through L2 (__ldcg) by the bodies.
+enum { SW_GRP4 = 0, SW_GRP8, SW_GRP16, SW_GRP32, SW_WARP, SW_CTA, SW_INV1, SW_INV2 };
+
+struct SweepPhase {
+    int32_t kind;     // SW_*
+    int32_t count;    // virtual blocks
+    int64_t off;      // offset into the substitution list (fronts) or the row blocks (inverse products)
+    int32_t n;        // fronts in the list (lane-group and warp kinds)
+    int32_t ldw;      // CTA kind: leading dimension of the per-rhs vectors in shared memory
+    int32_t barrier;  // nonzero: grid barrier after this phase
+    int32_t pad;
+};
+
+template <typename T>
+struct SweepArgs {
+    const FrontDev* fronts;
+    const int32_t* list;
+    const RowBlock* rows;
+    const T* fac;
+    const T* inv;
+    const int32_t* dofs;
+    const int32_t* maps;
+    T* vecs;
+    int64_t vec_size;
+    T* ys;
+    int64_t ys_size;
+    double* x;
+    int64_t n_dof;
+    int nrhs;
+    const SweepPhase* phases;
+    int n_phases;
+    unsigned int* bar;  // [0] arrivals, [1] generation
+    DevStatus* st;
+};
+
+__device__ __forceinline__ uint64_t sweep_clock_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs resident), bounded.
+__device__ __forceinline__ bool sweep_barrier(unsigned int* bar, unsigned int nblocks, DevStatus* st) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int* gen = bar + 1;
+        const unsigned int g = *gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
+        if (arrived == nblocks) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const uint64_t t0 = sweep_clock_ns();
+            while (*gen == g) {
+                if (sweep_clock_ns() - t0 > 1000000000ull) {
+                    ok = 0;
+                    atomicOr(&st->timeout, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+template <typename T, bool TRANS, bool FWD, int NR>
+__global__ void __launch_bounds__(256) k_solve_sweep(SweepArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    for (int ph = 0; ph < a.n_phases; ph++) {
+        const SweepPhase P = a.phases[ph];
+        const int32_t* L = a.list + P.off;
+        for (int vb = blockIdx.x; vb < P.count; vb += gridDim.x) {
+            switch (P.kind) {
+#define SWEEP_GRP(K, GS)                                                                                              \
+    case K:                                                                                                           \
+        if (FWD)                                                                                                      \
+            k_fwd_grp_body<T, TRANS, GS, NR>(a.fronts, L, P.n, a.fac, a.dofs, a.maps, a.vecs, a.vec_size, a.x, a.n_dof, \
+                                             a.nrhs, vb);                                                             \
+        else                                                                                                          \
+            k_bwd_grp_body<T, TRANS, GS, NR>(a.fronts, L, P.n, a.fac, a.dofs, a.x, a.n_dof, a.nrhs, vb);             \
+        break;
+                SWEEP_GRP(SW_GRP4, 4)
+                SWEEP_GRP(SW_GRP8, 8)
+                SWEEP_GRP(SW_GRP16, 16)
+                SWEEP_GRP(SW_GRP32, 32)
+#undef SWEEP_GRP
+                case SW_WARP:
+                    if (FWD)
+                        k_fwd_warp_body<T, TRANS, NR>(a.fronts, L, P.n, a.fac, a.dofs, a.maps, a.vecs, a.vec_size, a.x, a.n_dof,
+                                                      a.nrhs, vb);
+                    else
+                        k_bwd_warp_body<T, TRANS, NR>(a.fronts, L, P.n, a.fac, a.dofs, a.x, a.n_dof, a.nrhs, vb);
+                    break;
+                case SW_CTA:
+                    if (FWD)
+                        k_fwd_cta_body<T, TRANS>(a.fronts, L, 1, a.fac, a.dofs, a.maps, a.vecs, a.vec_size, a.x, a.n_dof, a.nrhs,
+                                                 P.ldw, vb, smem_dyn);
+                    else
+                        k_bwd_cta_body<T, TRANS>(a.fronts, L, 0, a.fac, a.dofs, a.x, a.n_dof, a.nrhs, P.ldw, vb, smem_dyn);
+                    break;
+                case SW_INV1:
+                    for (int r = 0; r < a.nrhs; r++)
+                        k_inv_gemv_body<T, TRANS, FWD ? PH_FWD1 : PH_BWD1, 8>(a.fronts, a.rows + P.off, a.fac, a.inv, a.dofs,
+                                                                              a.maps, a.vecs, a.vec_size, a.ys, a.ys_size,
+                                                                              a.x, a.n_dof, vb, smem_dyn, r);
+                    break;
+                case SW_INV2:
+                    for (int r = 0; r < a.nrhs; r++)
+                        k_inv_gemv_body<T, TRANS, FWD ? PH_FWD2 : PH_BWD2, 8>(a.fronts, a.rows + P.off, a.fac, a.inv, a.dofs,
+                                                                              a.maps, a.vecs, a.vec_size, a.ys, a.ys_size,
+                                                                              a.x, a.n_dof, vb, smem_dyn, r);
+                    break;
+            }
+        }
+        if (P.barrier && !sweep_barrier(a.bar, gridDim.x, a.st)) return;
     }
 }
 

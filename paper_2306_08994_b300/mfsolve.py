@@ -32,7 +32,8 @@ FUSED_BOUNDS = (16, 32, 48, 64, 96, 128, 160, 192, 224)
 class mf_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("pivot_tol", ctypes.c_double), ("pivot_fail", ctypes.c_int),
                 ("small_front_max", ctypes.c_int), ("panel_width", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("max_nrhs", ctypes.c_int), ("subtree_levels", ctypes.c_int), ("subtree_solve_levels", ctypes.c_int),
+                ("max_nrhs", ctypes.c_int), ("subtree_levels", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
+                ("subtree_solve_levels", ctypes.c_int),
                 ("tc_min_cb", ctypes.c_int),
                 ("super_panel", ctypes.c_int), ("fused_threads", ctypes.c_int * MF_FUSED_BUCKETS)]
 
@@ -70,7 +71,8 @@ class mf_trace_rec(ctypes.Structure):
 
 TRACE_KINDS = {0: "fused", 1: "assemble", 2: "panel_diag", 3: "gemm", 4: "inv_diag", 5: "subtree", 6: "gemm_tc",
                7: "fused_grp", 8: "tc_pack",
-               100: "fwd_class", 101: "bwd_class", 102: "subtree_fwd", 103: "subtree_bwd", 199: "other"}
+               100: "fwd_class", 101: "bwd_class", 102: "subtree_fwd", 103: "subtree_bwd", 104: "fwd_sweep",
+               105: "bwd_sweep", 199: "other"}
 
 
 class mf_tune_info(ctypes.Structure):

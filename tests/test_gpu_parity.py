@@ -327,3 +327,30 @@ def test_autotune_returns_a_correct_plan_and_caches_it(tmp_path):
     xo, _ = _oracle(pr).solve_refined(pr.b)
     assert info3["backward_error"] <= 1e-12
     assert np.linalg.norm(x.cpu().numpy() - xo[:, 0]) <= 1e-10 * np.linalg.norm(xo[:, 0])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_persistent_sweep_matches_per_class_launches(prec):
+    """sweep_kernel (one cooperative launch per substitution sweep, grid barriers between
+    classes) gives the per-class path's solution, forward and transposed, 1 and 4 RHS."""
+    pr = F.diffusion_2d(40, 3, seed=45)
+    outs = {}
+    for sw in (0, 100):  # per-class launches; every class above the subtrees in the sweep
+        a, f, vals = _setup(pr, prec, sweep_kernel=sw, small_front_max=48)
+        f.factor(vals)
+        b4 = torch.tensor(np.random.default_rng(7).uniform(-1, 1, (4, pr.mesh.n_nodes)), device=DEV)
+        res = []
+        for adj in (False, True):
+            y = b4.clone()
+            f.solve(y, adjoint=adj)
+            y1 = b4[0].clone()
+            f.solve(y1, adjoint=adj)
+            res.append((y.cpu().numpy(), y1.cpu().numpy()))
+        outs[sw] = res
+    # the 1-RHS kernels divide by the pivot, the 4-RHS ones multiply by its reciprocal: the two
+    # agree to rounding (FP32 fronts: a few units of 1e-7 after amplification by the condition)
+    tol_rhs = 1e-9 if prec == "f64" else 1e-5
+    for (ya, y1a), (yb, y1b) in zip(outs[0], outs[100]):
+        assert np.linalg.norm(ya - yb) <= 1e-9 * np.linalg.norm(ya)
+        assert np.linalg.norm(y1a - y1b) <= 1e-9 * np.linalg.norm(y1a)
+        assert np.linalg.norm(y1b - yb[0]) <= tol_rhs * np.linalg.norm(y1b)
