@@ -308,21 +308,37 @@ __global__ void __launch_bounds__(256) k_assemble_large(const FrontDev* __restri
         r1[q] = (two && ri[q] < m) ? map1[ri[q]] : -1;
     }
     T amax = T(0);
-    for (int jj = warp; jj < 64; jj += 8) {
-        const int j = t.j0 + jj;
+    // the warp's 8 columns: all column maps, then all child entries, then the stores, so the
+    // map -> entry load chains of the 8 columns overlap instead of running one after another
+    int cj0[8], cj1[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+        const int j = t.j0 + warp + 8 * u;
+        cj0[u] = j < m ? map0[j] : -1;
+        cj1[u] = (two && j < m) ? map1[j] : -1;
+    }
+    T v[8][2];
+#pragma unroll
+    for (int u = 0; u < 8; u++)
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            T x = T(0);
+            if (r0[q] >= 0 && cj0[u] >= 0) x += S0[r0[q] + (int64_t)cj0[u] * n0];
+            if (r1[q] >= 0 && cj1[u] >= 0) x += S1[r1[q] + (int64_t)cj1[u] * n1];
+            v[u][q] = x;
+        }
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+        const int j = t.j0 + warp + 8 * u;
         if (j >= m) break;
-        const int cj0 = map0[j];
-        const int cj1 = two ? map1[j] : -1;
+#pragma unroll
         for (int q = 0; q < 2; q++) {
             const int i = ri[q];
             if (i >= m) continue;
-            T v = T(0);
-            if (r0[q] >= 0 && cj0 >= 0) v += S0[r0[q] + (int64_t)cj0 * n0];
-            if (r1[q] >= 0 && cj1 >= 0) v += S1[r1[q] + (int64_t)cj1 * n1];
-            amax = max(amax, (T)fabs(v));
-            if (j < k) fac[fr.P_off + i + (int64_t)j * m] = v;
-            else if (i < k) fac[fr.R_off + i + (int64_t)(j - k) * k] = v;
-            else cbs[fr.S_off + (i - k) + (int64_t)(j - k) * nc] = v;
+            amax = max(amax, (T)fabs(v[u][q]));
+            if (j < k) fac[fr.P_off + i + (int64_t)j * m] = v[u][q];
+            else if (i < k) fac[fr.R_off + i + (int64_t)(j - k) * k] = v[u][q];
+            else cbs[fr.S_off + (i - k) + (int64_t)(j - k) * nc] = v[u][q];
         }
     }
     for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
