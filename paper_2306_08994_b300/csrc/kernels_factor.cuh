@@ -88,44 +88,78 @@ __global__ void __launch_bounds__(256) k_front_fused(const FrontDev* __restrict_
     for (int i = threadIdx.x; i < nmap; i += blockDim.x) imap[i] = maps[fr.map_off + i];
     __syncthreads();
 
-    // ---- assembly
+    // ---- assembly: per warp 4 columns x 2 rows per lane in flight (loads first, then stores)
     T amax = T(0);
     if (fr.nchild == 0) {
         const double* K = values + (int64_t)fr.elem * npe * npe;
-        for (int j = warp; j < m; j += nwarp) {
-            const int b = imap[j];
-            for (int i = lane; i < m; i += 32) {
-                T v = (T)K[imap[i] + b * npe];
-                F[i + j * ldm] = v;
-                amax = max(amax, (T)fabs(v));
+        for (int jb = warp; jb < m; jb += 4 * nwarp)
+            for (int ib = lane; ib < m; ib += 64) {
+                double v[4][2];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        const int j = jb + u * nwarp, i = ib + 32 * q;
+                        v[u][q] = (j < m && i < m) ? K[imap[i] + imap[j] * npe] : 0.0;
+                    }
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        const int j = jb + u * nwarp, i = ib + 32 * q;
+                        if (j < m && i < m) {
+                            const T t = (T)v[u][q];
+                            F[i + j * ldm] = t;
+                            amax = max(amax, (T)fabs(t));
+                        }
+                    }
             }
-        }
     } else {
         const FrontDev c0 = fronts[fr.child[0]];
         const int n0 = c0.m - c0.k;
         const T* S0 = cbs + c0.S_off;
         const T* S1 = nullptr;
         int n1 = 0;
-        if (fr.nchild > 1) {
+        const bool two = fr.nchild > 1;
+        if (two) {
             const FrontDev c1 = fronts[fr.child[1]];
             n1 = c1.m - c1.k;
             S1 = cbs + c1.S_off;
         }
-        for (int j = warp; j < m; j += nwarp) {
-            const int j0 = imap[j];
-            const int j1 = fr.nchild > 1 ? imap[m + j] : -1;
-            for (int i = lane; i < m; i += 32) {
-                T v = T(0);
-                int i0 = imap[i];
-                if (i0 >= 0 && j0 >= 0) v += S0[i0 + (int64_t)j0 * n0];
-                if (j1 >= 0) {
-                    int i1 = imap[m + i];
-                    if (i1 >= 0) v += S1[i1 + (int64_t)j1 * n1];
+        for (int jb = warp; jb < m; jb += 4 * nwarp)
+            for (int ib = lane; ib < m; ib += 64) {
+                T v[4][2];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int j = jb + u * nwarp;
+                    const int j0 = j < m ? imap[j] : -1;
+                    const int j1 = (two && j < m) ? imap[m + j] : -1;
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        const int i = ib + 32 * q;
+                        T x = T(0);
+                        if (i < m) {
+                            const int i0 = imap[i];
+                            if (i0 >= 0 && j0 >= 0) x += S0[i0 + (int64_t)j0 * n0];
+                            if (j1 >= 0) {
+                                const int i1 = imap[m + i];
+                                if (i1 >= 0) x += S1[i1 + (int64_t)j1 * n1];
+                            }
+                        }
+                        v[u][q] = x;
+                    }
                 }
-                F[i + j * ldm] = v;
-                amax = max(amax, (T)fabs(v));
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        const int j = jb + u * nwarp, i = ib + 32 * q;
+                        if (j < m && i < m) {
+                            F[i + j * ldm] = v[u][q];
+                            amax = max(amax, (T)fabs(v[u][q]));
+                        }
+                    }
             }
-        }
     }
     amax = block_max_abs(amax, red);  // includes __syncthreads
     const T thr = (T)tol_rel * amax > T(0) ? (T)tol_rel * amax : tiny_pivot<T>();
