@@ -212,6 +212,7 @@ struct mf_factors {
     FrontDev* d_fronts = nullptr;
     int32_t* d_dofs = nullptr;
     int32_t* d_maps = nullptr;
+    int64_t* d_vsrc = nullptr;  // per front row and child: the child's update-vector index holding it, or -1
     int64_t* d_en = nullptr;
     int64_t* d_node_ptr = nullptr;
     int64_t* d_node_inc = nullptr;
@@ -332,7 +333,7 @@ static void free_factors(mf_factors* f) {
     if (f->s2) cudaStreamDestroy(f->s2);
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
-    void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
+    void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_vsrc, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
                     f->d_vec, f->d_flist, f->d_slist, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
                     f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms};
     for (void* p : ptrs)
@@ -1102,6 +1103,21 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     TRY(upload(&F->d_fronts, a->fronts));
     TRY(upload(&F->d_dofs, a->dofs));
     TRY(upload(&F->d_maps, a->maps));
+    {
+        // gather sources of the forward substitution, precomputed per front row
+        std::vector<int64_t> vsrc(2 * a->dofs.size(), -1);
+        for (int32_t f = 0; f < a->n_front; f++) {
+            const FrontDev& fr = a->fronts[f];
+            for (int c = 0; c < fr.nchild; c++) {
+                const int64_t voff = a->fronts[fr.child[c]].vec_off;
+                for (int32_t i = 0; i < fr.m; i++) {
+                    const int32_t ic = a->maps[fr.map_off + (int64_t)c * fr.m + i];
+                    if (ic >= 0) vsrc[2 * (fr.dof_off + i) + c] = voff + ic;
+                }
+            }
+        }
+        TRY(upload(&F->d_vsrc, vsrc));
+    }
     TRY(upload(&F->d_en, a->elem_nodes));
     TRY(upload(&F->d_node_ptr, a->node_ptr));
     TRY(upload(&F->d_node_inc, a->node_inc));
@@ -1341,7 +1357,7 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
             ff += F->fwd_flops[c];
             bf += F->bwd_flops[c];
         }
-        SweepArgs<T> args{fr, L, F->d_rows, fac, inv, F->d_dofs, F->d_maps, vec, vs, ys, yss, d_x, n, nrhs,
+        SweepArgs<T> args{fr, L, F->d_rows, fac, inv, F->d_dofs, F->d_vsrc, vec, vs, ys, yss, d_x, n, nrhs,
                           forward ? F->d_sweep_f : F->d_sweep_b,
                           (int)(forward ? F->sweep_f.size() : F->sweep_b.size()), F->d_bar, F->d_status};
         int slot = forward ? prof_begin(F, s, FAM_FWD, fb * nrhs, ff * nrhs, 1, -1, MF_TRACE_FWD_SWEEP, -1, args.n_phases)
@@ -1378,10 +1394,10 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
 #define INV_LAUNCH(TR, PH, CNT, OFF)                                                                               \
     if ((PH == PH_BWD1 ? C.maxnc_inv : C.maxk_inv) > 512)                                                          \
         k_inv_gemv<T, TR, PH, 32><<<dim3(CNT, nrhs), 1024, (32 * 32 + C.maxin_inv) * sizeof(T), s>>>(            \
-            fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_maps, vec, vs, ys, yss, d_x, n);                      \
+            fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_vsrc, vec, vs, ys, yss, d_x, n);                      \
     else                                                                                                           \
         k_inv_gemv<T, TR, PH, 8><<<dim3(CNT, nrhs), 256, (8 * 32 + C.maxin_inv) * sizeof(T), s>>>(               \
-            fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_maps, vec, vs, ys, yss, d_x, n)
+            fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_vsrc, vec, vs, ys, yss, d_x, n)
     for (int c = 0; c < c_top; c++) {
         const ClassList& C = F->classes_f[c];
         int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0) + (C.n_grp[0] > 0) + (C.n_grp[1] > 0) + (C.n_grp[2] > 0) + (C.n_grp[3] > 0);
@@ -1390,8 +1406,8 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
 #define GRP_FWD(Q, GS)                                                                                             \
         if (C.n_grp[Q]) {                                                                                          \
             dim3 g((C.n_grp[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)));                                             \
-            if (!trans) SOLVE_NR(k_fwd_grp, (T, false, GS), (g, 256, 0, s), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs)); \
-            else SOLVE_NR(k_fwd_grp, (T, true, GS), (g, 256, 0, s), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs)); \
+            if (!trans) SOLVE_NR(k_fwd_grp, (T, false, GS), (g, 256, 0, s), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+            else SOLVE_NR(k_fwd_grp, (T, true, GS), (g, 256, 0, s), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
         }
         GRP_FWD(0, 4)
         GRP_FWD(1, 8)
@@ -1399,20 +1415,20 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
 #undef GRP_FWD
         if (C.n_grp[3]) {  // 16 < m <= 32: the one-front-per-warp kernel is faster forward
             dim3 g((C.n_grp[3] + 7) / 8);
-            if (!trans) SOLVE_NR(k_fwd_warp, (T, false), (g, 256, 0, s), (fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs));
-            else SOLVE_NR(k_fwd_warp, (T, true), (g, 256, 0, s), (fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs));
+            if (!trans) SOLVE_NR(k_fwd_warp, (T, false), (g, 256, 0, s), (fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
+            else SOLVE_NR(k_fwd_warp, (T, true), (g, 256, 0, s), (fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
         }
         if (C.n_small) {
             dim3 g((C.n_small + 7) / 8);
-            if (!trans) SOLVE_NR(k_fwd_warp, (T, false), (g, 256, 0, s), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs));
-            else SOLVE_NR(k_fwd_warp, (T, true), (g, 256, 0, s), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs));
+            if (!trans) SOLVE_NR(k_fwd_warp, (T, false), (g, 256, 0, s), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
+            else SOLVE_NR(k_fwd_warp, (T, true), (g, 256, 0, s), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
         }
         if (C.n_cta) {
             dim3 g(C.n_cta);
             const int ldw = C.maxm_cta;
             size_t sm = dgs + (size_t)kRhsChunk * ldw * sizeof(T);
-            if (!trans) k_fwd_cta<T, false><<<g, 256, sm, s>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs, ldw);
-            else k_fwd_cta<T, true><<<g, 256, sm, s>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_maps, vec, vs, d_x, n, nrhs, ldw);
+            if (!trans) k_fwd_cta<T, false><<<g, 256, sm, s>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, ldw);
+            else k_fwd_cta<T, true><<<g, 256, sm, s>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, ldw);
         }
         if (C.n_piv) {
             if (!trans) {

@@ -40,35 +40,22 @@ __device__ __forceinline__ T bdiag(const T* P, int m, int p) {
     return TRANS ? P[p + (int64_t)p * m] : T(1);
 }
 
-template <typename T>
-__device__ __forceinline__ T gather_rhs(const FrontDev& fr, const FrontDev* __restrict__ fronts, const int32_t* __restrict__ fd,
-                                        const int32_t* __restrict__ maps, const T* __restrict__ vr,
-                                        const double* __restrict__ xr, int i) {
-    T v = i < fr.k ? (T)__ldcg(xr + fd[i]) : T(0);
-    for (int c = 0; c < fr.nchild; c++) {
-        int ic = maps[fr.map_off + (int64_t)c * fr.m + i];
-        if (ic >= 0) v += __ldcg(vr + fronts[fr.child[c]].vec_off + ic);
-    }
-    return v;
-}
-
 // Where row i of a front's right-hand side comes from: its own dof (pivot
-// rows) and the update-vector entries of the children that hold it.  Worked
-// out once per row and reused for every right-hand side.
+// rows) and the update-vector entries of the children that hold it.  The
+// children's entries are precomputed per front row (vsrc[2 (dof_off + i) + c],
+// -1 when child c does not hold row i), so no child map or child descriptor
+// is read on the way.
 struct RhsSrc {
     int64_t xi, v0, v1;  // -1 when absent
 };
-__device__ __forceinline__ RhsSrc rhs_src(const FrontDev& fr, const FrontDev* __restrict__ fronts,
-                                          const int32_t* __restrict__ fd, const int32_t* __restrict__ maps, int i) {
+__device__ __forceinline__ RhsSrc rhs_src(const FrontDev& fr, const int32_t* __restrict__ fd,
+                                          const int64_t* __restrict__ vsrc, int i) {
     RhsSrc q{-1, -1, -1};
     if (i < fr.k) q.xi = fd[i];
     if (fr.nchild > 0) {
-        const int ic = maps[fr.map_off + i];
-        if (ic >= 0) q.v0 = fronts[fr.child[0]].vec_off + ic;
-    }
-    if (fr.nchild > 1) {
-        const int ic = maps[fr.map_off + fr.m + i];
-        if (ic >= 0) q.v1 = fronts[fr.child[1]].vec_off + ic;
+        const int64_t* v = vsrc + 2 * (fr.dof_off + i);
+        q.v0 = v[0];
+        q.v1 = v[1];
     }
     return q;
 }
@@ -78,6 +65,12 @@ __device__ __forceinline__ T rhs_val(const RhsSrc& q, const T* __restrict__ vr, 
     if (q.v0 >= 0) v += __ldcg(vr + q.v0);
     if (q.v1 >= 0) v += __ldcg(vr + q.v1);
     return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T gather_rhs(const FrontDev& fr, const int32_t* __restrict__ fd, const int64_t* __restrict__ vsrc,
+                                        const T* __restrict__ vr, const double* __restrict__ xr, int i) {
+    return rhs_val<T>(rhs_src(fr, fd, vsrc, i), vr, xr);
 }
 
 // Right-hand sides are processed in chunks inside one launch, so a front's
@@ -100,7 +93,7 @@ __device__ __forceinline__ T apply_pivot(T w, T ds) {
 template <typename T, bool TRANS, int NR>
 __device__ __forceinline__ void k_fwd_warp_body(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                   int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
-                                                  const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
+                                                  const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
                                                   double* __restrict__ x, int64_t n_dof, int nrhs, int vb) {
     const int wid = vb * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -111,8 +104,8 @@ __device__ __forceinline__ void k_fwd_warp_body(const FrontDev* __restrict__ fro
     const T* P = fac + fr.P_off;
     const T* R = fac + fr.R_off;
     const int i0 = lane, i1 = lane + 32;
-    const RhsSrc s0 = i0 < m ? rhs_src(fr, fronts, fd, maps, i0) : RhsSrc{-1, -1, -1};
-    const RhsSrc s1 = i1 < m ? rhs_src(fr, fronts, fd, maps, i1) : RhsSrc{-1, -1, -1};
+    const RhsSrc s0 = i0 < m ? rhs_src(fr, fd, vsrc, i0) : RhsSrc{-1, -1, -1};
+    const RhsSrc s1 = i1 < m ? rhs_src(fr, fd, vsrc, i1) : RhsSrc{-1, -1, -1};
     for (int rb = 0; rb < nrhs; rb += NR) {
         const int nr = min(NR, nrhs - rb);
         T w0[NR], w1[NR];
@@ -171,9 +164,9 @@ __device__ __forceinline__ void k_fwd_warp_body(const FrontDev* __restrict__ fro
 template <typename T, bool TRANS, int NR>
 __global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_fwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                   int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
-                                                  const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
+                                                  const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
                                                   double* __restrict__ x, int64_t n_dof, int nrhs) {
-    k_fwd_warp_body<T, TRANS, NR>(fronts, list, count, fac, dofs, maps, vecs, vec_size, x, n_dof, nrhs, blockIdx.x);
+    k_fwd_warp_body<T, TRANS, NR>(fronts, list, count, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, blockIdx.x);
 }
 
 template <typename T, bool TRANS, int NR>
@@ -251,7 +244,7 @@ __global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_bwd_warp(const FrontDe
 template <typename T, bool TRANS, int G, int NR>
 __device__ __forceinline__ void k_fwd_grp_body(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
-                                                 const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
+                                                 const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int vb) {
     const int lane = threadIdx.x & 31;
     const int fidx = (vb * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
@@ -273,7 +266,7 @@ __device__ __forceinline__ void k_fwd_grp_body(const FrontDev* __restrict__ fron
         c[p] = (p < k && i > p && i < m) ? fcoef<T, TRANS>(P, R, m, k, i, p) : T(0);
         dg[p] = p < k ? fdiag<T, TRANS>(P, m, p) : T(1);
     }
-    const RhsSrc src = (active && i < m) ? rhs_src(fr, fronts, fd, maps, i) : RhsSrc{-1, -1, -1};
+    const RhsSrc src = (active && i < m) ? rhs_src(fr, fd, vsrc, i) : RhsSrc{-1, -1, -1};
     const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)k);  // warp-uniform pivot count
     for (int rb = 0; rb < nrhs; rb += NR) {
         const int nr = min(NR, nrhs - rb);
@@ -308,9 +301,9 @@ __device__ __forceinline__ void k_fwd_grp_body(const FrontDev* __restrict__ fron
 template <typename T, bool TRANS, int G, int NR>
 __global__ void __launch_bounds__(256) k_fwd_grp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
-                                                 const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
+                                                 const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs) {
-    k_fwd_grp_body<T, TRANS, G, NR>(fronts, list, count, fac, dofs, maps, vecs, vec_size, x, n_dof, nrhs, blockIdx.x);
+    k_fwd_grp_body<T, TRANS, G, NR>(fronts, list, count, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, blockIdx.x);
 }
 
 template <typename T, bool TRANS, int G, int NR>
@@ -380,7 +373,7 @@ __global__ void __launch_bounds__(256) k_bwd_grp(const FrontDev* __restrict__ fr
 template <typename T, bool TRANS>
 __device__ __forceinline__ void k_fwd_cta_body(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                  int rows_all, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
-                                                 const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
+                                                 const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int ldw, int vb, unsigned char* smem_raw) {
     __syncthreads();  // in a persistent sweep the previous body of this CTA may still be reading shared memory
     T* Dg = reinterpret_cast<T*>(smem_raw);  // 32 x 33
@@ -395,7 +388,7 @@ __device__ __forceinline__ void k_fwd_cta_body(const FrontDev* __restrict__ fron
     for (int rb = 0; rb < nrhs; rb += kRhsChunk) {
         const int nr = min(kRhsChunk, nrhs - rb);
         for (int i = threadIdx.x; i < mr; i += blockDim.x) {
-            const RhsSrc src = rhs_src(fr, fronts, fd, maps, i);
+            const RhsSrc src = rhs_src(fr, fd, vsrc, i);
             for (int rr = 0; rr < nr; rr++)
                 w[rr * ldw + i] = rhs_val<T>(src, vecs + (int64_t)(rb + rr) * vec_size, x + (int64_t)(rb + rr) * n_dof);
         }
@@ -456,10 +449,10 @@ __device__ __forceinline__ void k_fwd_cta_body(const FrontDev* __restrict__ fron
 template <typename T, bool TRANS>
 __global__ void __launch_bounds__(256) k_fwd_cta(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
                                                  int rows_all, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
-                                                 const int32_t* __restrict__ maps, T* __restrict__ vecs, int64_t vec_size,
+                                                 const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int ldw) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
-    k_fwd_cta_body<T, TRANS>(fronts, list, rows_all, fac, dofs, maps, vecs, vec_size, x, n_dof, nrhs, ldw, blockIdx.x, smem_dyn);
+    k_fwd_cta_body<T, TRANS>(fronts, list, rows_all, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, ldw, blockIdx.x, smem_dyn);
 }
 
 // Backward, one CTA per mid-size front: the CB part of the pivot rows first,
@@ -609,7 +602,7 @@ __device__ __forceinline__ T inv_coef(const T* __restrict__ P, const T* __restri
 template <typename T, bool TRANS, int PH, int NW>
 __device__ __forceinline__ void k_inv_gemv_body(const FrontDev* __restrict__ fronts, const RowBlock* __restrict__ tasks,
                                                   const T* __restrict__ fac, const T* __restrict__ inv,
-                                                  const int32_t* __restrict__ dofs, const int32_t* __restrict__ maps,
+                                                  const int32_t* __restrict__ dofs, const int64_t* __restrict__ vsrc,
                                                   T* __restrict__ vecs, int64_t vec_size, T* __restrict__ ys,
                                                   int64_t ys_size, double* __restrict__ x, int64_t n_dof, int vb, unsigned char* smem_raw, int rr) {
     __syncthreads();  // in a persistent sweep the previous body of this CTA may still be reading shared memory
@@ -633,7 +626,7 @@ __device__ __forceinline__ void k_inv_gemv_body(const FrontDev* __restrict__ fro
     const int nin = (PH == PH_BWD1) ? m - k : k;
     for (int j = threadIdx.x; j < nin; j += blockDim.x) {
         T v;
-        if (PH == PH_FWD1) v = gather_rhs<T>(fr, fronts, fd, maps, vr, xr, j);
+        if (PH == PH_FWD1) v = gather_rhs<T>(fr, fd, vsrc, vr, xr, j);
         else if (PH == PH_BWD1) v = (T)__ldcg(xr + fd[k + j]);
         else v = __ldcg(yr + j);
         vin[j] = v;
@@ -645,7 +638,7 @@ __device__ __forceinline__ void k_inv_gemv_body(const FrontDev* __restrict__ fro
     auto hi = [&](int i) { return PH == PH_FWD1 ? i + 1 : nin; };
     auto finish = [&](int i, T acc) {
         if (PH == PH_FWD1) yr[i] = acc;
-        else if (PH == PH_FWD2) vr[fr.vec_off + (i - k)] = gather_rhs<T>(fr, fronts, fd, maps, vr, xr, i) - acc;
+        else if (PH == PH_FWD2) vr[fr.vec_off + (i - k)] = gather_rhs<T>(fr, fd, vsrc, vr, xr, i) - acc;
         else if (PH == PH_BWD1) yr[i] = (T)__ldcg(xr + fd[i]) - acc;
         else xr[fd[i]] = (double)acc;
     };
@@ -701,11 +694,11 @@ __device__ __forceinline__ void k_inv_gemv_body(const FrontDev* __restrict__ fro
 template <typename T, bool TRANS, int PH, int NW>
 __global__ void __launch_bounds__(NW * 32) k_inv_gemv(const FrontDev* __restrict__ fronts, const RowBlock* __restrict__ tasks,
                                                   const T* __restrict__ fac, const T* __restrict__ inv,
-                                                  const int32_t* __restrict__ dofs, const int32_t* __restrict__ maps,
+                                                  const int32_t* __restrict__ dofs, const int64_t* __restrict__ vsrc,
                                                   T* __restrict__ vecs, int64_t vec_size, T* __restrict__ ys,
                                                   int64_t ys_size, double* __restrict__ x, int64_t n_dof) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
-    k_inv_gemv_body<T, TRANS, PH, NW>(fronts, tasks, fac, inv, dofs, maps, vecs, vec_size, ys, ys_size, x, n_dof, blockIdx.x, smem_dyn, blockIdx.y);
+    k_inv_gemv_body<T, TRANS, PH, NW>(fronts, tasks, fac, inv, dofs, vsrc, vecs, vec_size, ys, ys_size, x, n_dof, blockIdx.x, smem_dyn, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -739,7 +732,7 @@ struct SweepArgs {
     const T* fac;
     const T* inv;
     const int32_t* dofs;
-    const int32_t* maps;
+    const int64_t* vsrc;
     T* vecs;
     int64_t vec_size;
     T* ys;
@@ -802,7 +795,7 @@ __global__ void __launch_bounds__(256) k_solve_sweep(SweepArgs<T> a) {
 #define SWEEP_GRP(K, GS)                                                                                              \
     case K:                                                                                                           \
         if (FWD)                                                                                                      \
-            k_fwd_grp_body<T, TRANS, GS, NR>(a.fronts, L, P.n, a.fac, a.dofs, a.maps, a.vecs, a.vec_size, a.x, a.n_dof, \
+            k_fwd_grp_body<T, TRANS, GS, NR>(a.fronts, L, P.n, a.fac, a.dofs, a.vsrc, a.vecs, a.vec_size, a.x, a.n_dof, \
                                              a.nrhs, vb);                                                             \
         else                                                                                                          \
             k_bwd_grp_body<T, TRANS, GS, NR>(a.fronts, L, P.n, a.fac, a.dofs, a.x, a.n_dof, a.nrhs, vb);             \
@@ -814,14 +807,14 @@ __global__ void __launch_bounds__(256) k_solve_sweep(SweepArgs<T> a) {
 #undef SWEEP_GRP
                 case SW_WARP:
                     if (FWD)
-                        k_fwd_warp_body<T, TRANS, NR>(a.fronts, L, P.n, a.fac, a.dofs, a.maps, a.vecs, a.vec_size, a.x, a.n_dof,
+                        k_fwd_warp_body<T, TRANS, NR>(a.fronts, L, P.n, a.fac, a.dofs, a.vsrc, a.vecs, a.vec_size, a.x, a.n_dof,
                                                       a.nrhs, vb);
                     else
                         k_bwd_warp_body<T, TRANS, NR>(a.fronts, L, P.n, a.fac, a.dofs, a.x, a.n_dof, a.nrhs, vb);
                     break;
                 case SW_CTA:
                     if (FWD)
-                        k_fwd_cta_body<T, TRANS>(a.fronts, L, 1, a.fac, a.dofs, a.maps, a.vecs, a.vec_size, a.x, a.n_dof, a.nrhs,
+                        k_fwd_cta_body<T, TRANS>(a.fronts, L, 1, a.fac, a.dofs, a.vsrc, a.vecs, a.vec_size, a.x, a.n_dof, a.nrhs,
                                                  P.ldw, vb, smem_dyn);
                     else
                         k_bwd_cta_body<T, TRANS>(a.fronts, L, 0, a.fac, a.dofs, a.x, a.n_dof, a.nrhs, P.ldw, vb, smem_dyn);
@@ -829,13 +822,13 @@ __global__ void __launch_bounds__(256) k_solve_sweep(SweepArgs<T> a) {
                 case SW_INV1:
                     for (int r = 0; r < a.nrhs; r++)
                         k_inv_gemv_body<T, TRANS, FWD ? PH_FWD1 : PH_BWD1, 8>(a.fronts, a.rows + P.off, a.fac, a.inv, a.dofs,
-                                                                              a.maps, a.vecs, a.vec_size, a.ys, a.ys_size,
+                                                                              a.vsrc, a.vecs, a.vec_size, a.ys, a.ys_size,
                                                                               a.x, a.n_dof, vb, smem_dyn, r);
                     break;
                 case SW_INV2:
                     for (int r = 0; r < a.nrhs; r++)
                         k_inv_gemv_body<T, TRANS, FWD ? PH_FWD2 : PH_BWD2, 8>(a.fronts, a.rows + P.off, a.fac, a.inv, a.dofs,
-                                                                              a.maps, a.vecs, a.vec_size, a.ys, a.ys_size,
+                                                                              a.vsrc, a.vecs, a.vec_size, a.ys, a.ys_size,
                                                                               a.x, a.n_dof, vb, smem_dyn, r);
                     break;
             }
