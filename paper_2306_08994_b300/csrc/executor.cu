@@ -221,6 +221,7 @@ struct mf_factors {
     void* d_vec = nullptr;
     int32_t* d_flist = nullptr;
     int32_t* d_slist = nullptr;
+    SolveRec* d_srec = nullptr;  // the substitution list as compact records
     RowBlock* d_rows = nullptr;
     InvTask* d_invt = nullptr;
     void* d_inv = nullptr;
@@ -334,7 +335,7 @@ static void free_factors(mf_factors* f) {
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_vsrc, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
-                    f->d_vec, f->d_flist, f->d_slist, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
+                    f->d_vec, f->d_flist, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
                     f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1010,6 +1011,14 @@ static int build_plan(mf_factors* F) {
     if ((rc = upload(&F->d_sweep_b, F->sweep_b))) return rc;
     if ((rc = upload(&F->d_flist, flist))) return rc;
     if ((rc = upload(&F->d_slist, slist))) return rc;
+    {
+        std::vector<SolveRec> srec(slist.size());
+        for (size_t i = 0; i < slist.size(); i++) {
+            const FrontDev& fr = a->fronts[slist[i]];
+            srec[i] = SolveRec{fr.P_off, fr.R_off, fr.dof_off, fr.vec_off, fr.m, fr.k, fr.nchild, 0};
+        }
+        if ((rc = upload(&F->d_srec, srec))) return rc;
+    }
     if ((rc = upload(&F->d_rows, rows))) return rc;
     if ((rc = upload(&F->d_invt, invt))) return rc;
     if ((rc = upload(&F->d_sub_tasks, F->sub.tasks))) return rc;
@@ -1331,7 +1340,7 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
     T* vec = (T*)F->d_vec;
     T* ys = (T*)F->d_ys;
     const FrontDev* fr = F->d_fronts;
-    const int32_t* L = F->d_slist;
+    const SolveRec* L = F->d_srec;
     const int64_t n = a->n_dof, vs = a->vec_size, yss = a->ys_size;
     const size_t dgs = 32 * 33 * sizeof(T);
     if (F->subs.h >= 2) {

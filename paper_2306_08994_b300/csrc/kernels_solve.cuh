@@ -48,8 +48,17 @@ __device__ __forceinline__ T bdiag(const T* P, int m, int p) {
 struct RhsSrc {
     int64_t xi, v0, v1;  // -1 when absent
 };
-__device__ __forceinline__ RhsSrc rhs_src(const FrontDev& fr, const int32_t* __restrict__ fd,
-                                          const int64_t* __restrict__ vsrc, int i) {
+
+// What the small- and mid-front substitution kernels read of a front, stored
+// in substitution-list order (one load, no list -> descriptor indirection).
+struct SolveRec {
+    int64_t P_off, R_off, dof_off, vec_off;
+    int32_t m, k, nchild, pad;
+};
+
+template <typename FR>
+__device__ __forceinline__ RhsSrc rhs_src(const FR& fr, const int32_t* __restrict__ fd, const int64_t* __restrict__ vsrc,
+                                          int i) {
     RhsSrc q{-1, -1, -1};
     if (i < fr.k) q.xi = fd[i];
     if (fr.nchild > 0) {
@@ -67,10 +76,10 @@ __device__ __forceinline__ T rhs_val(const RhsSrc& q, const T* __restrict__ vr, 
     return v;
 }
 
-template <typename T>
-__device__ __forceinline__ T gather_rhs(const FrontDev& fr, const int32_t* __restrict__ fd, const int64_t* __restrict__ vsrc,
+template <typename T, typename FR>
+__device__ __forceinline__ T gather_rhs(const FR& fr, const int32_t* __restrict__ fd, const int64_t* __restrict__ vsrc,
                                         const T* __restrict__ vr, const double* __restrict__ xr, int i) {
-    return rhs_val<T>(rhs_src(fr, fd, vsrc, i), vr, xr);
+    return rhs_val<T>(rhs_src<FR>(fr, fd, vsrc, i), vr, xr);
 }
 
 // Right-hand sides are processed in chunks inside one launch, so a front's
@@ -91,21 +100,21 @@ __device__ __forceinline__ T apply_pivot(T w, T ds) {
 
 // Small fronts (m <= 64): one warp per front, rows lane and lane+32.
 template <typename T, bool TRANS, int NR>
-__device__ __forceinline__ void k_fwd_warp_body(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__device__ __forceinline__ void k_fwd_warp_body(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                   int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                   const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
                                                   double* __restrict__ x, int64_t n_dof, int nrhs, int vb) {
     const int wid = vb * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (wid >= count) return;
-    const FrontDev fr = fronts[list[wid]];
+    const SolveRec fr = list[wid];
     const int m = fr.m, k = fr.k;
     const int32_t* fd = dofs + fr.dof_off;
     const T* P = fac + fr.P_off;
     const T* R = fac + fr.R_off;
     const int i0 = lane, i1 = lane + 32;
-    const RhsSrc s0 = i0 < m ? rhs_src(fr, fd, vsrc, i0) : RhsSrc{-1, -1, -1};
-    const RhsSrc s1 = i1 < m ? rhs_src(fr, fd, vsrc, i1) : RhsSrc{-1, -1, -1};
+    const RhsSrc s0 = i0 < m ? rhs_src<SolveRec>(fr, fd, vsrc, i0) : RhsSrc{-1, -1, -1};
+    const RhsSrc s1 = i1 < m ? rhs_src<SolveRec>(fr, fd, vsrc, i1) : RhsSrc{-1, -1, -1};
     for (int rb = 0; rb < nrhs; rb += NR) {
         const int nr = min(NR, nrhs - rb);
         T w0[NR], w1[NR];
@@ -162,7 +171,7 @@ __device__ __forceinline__ void k_fwd_warp_body(const FrontDev* __restrict__ fro
     }
 }
 template <typename T, bool TRANS, int NR>
-__global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_fwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_fwd_warp(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                   int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                   const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
                                                   double* __restrict__ x, int64_t n_dof, int nrhs) {
@@ -170,13 +179,13 @@ __global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_fwd_warp(const FrontDe
 }
 
 template <typename T, bool TRANS, int NR>
-__device__ __forceinline__ void k_bwd_warp_body(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__device__ __forceinline__ void k_bwd_warp_body(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                   int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                   double* __restrict__ x, int64_t n_dof, int nrhs, int vb) {
     const int wid = vb * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (wid >= count) return;
-    const FrontDev fr = fronts[list[wid]];
+    const SolveRec fr = list[wid];
     const int m = fr.m, k = fr.k;
     const int32_t* fd = dofs + fr.dof_off;
     const T* P = fac + fr.P_off;
@@ -232,7 +241,7 @@ __device__ __forceinline__ void k_bwd_warp_body(const FrontDev* __restrict__ fro
     }
 }
 template <typename T, bool TRANS, int NR>
-__global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_bwd_warp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_bwd_warp(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                   int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                   double* __restrict__ x, int64_t n_dof, int nrhs) {
     k_bwd_warp_body<T, TRANS, NR>(fronts, list, count, fac, dofs, x, n_dof, nrhs, blockIdx.x);
@@ -242,7 +251,7 @@ __global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_bwd_warp(const FrontDe
 // per row, shuffles of width G; all coefficients are loaded once, before the
 // short sequential pivot loop.
 template <typename T, bool TRANS, int G, int NR>
-__device__ __forceinline__ void k_fwd_grp_body(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__device__ __forceinline__ void k_fwd_grp_body(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int vb) {
@@ -250,10 +259,10 @@ __device__ __forceinline__ void k_fwd_grp_body(const FrontDev* __restrict__ fron
     const int fidx = (vb * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
     const bool active = fidx < count;
     const int i = lane % G;
-    FrontDev fr{};
+    SolveRec fr{};
     int m = 0, k = 0;
     if (active) {
-        fr = fronts[list[fidx]];
+        fr = list[fidx];
         m = fr.m;
         k = fr.k;
     }
@@ -266,7 +275,7 @@ __device__ __forceinline__ void k_fwd_grp_body(const FrontDev* __restrict__ fron
         c[p] = (p < k && i > p && i < m) ? fcoef<T, TRANS>(P, R, m, k, i, p) : T(0);
         dg[p] = p < k ? fdiag<T, TRANS>(P, m, p) : T(1);
     }
-    const RhsSrc src = (active && i < m) ? rhs_src(fr, fd, vsrc, i) : RhsSrc{-1, -1, -1};
+    const RhsSrc src = (active && i < m) ? rhs_src<SolveRec>(fr, fd, vsrc, i) : RhsSrc{-1, -1, -1};
     const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)k);  // warp-uniform pivot count
     for (int rb = 0; rb < nrhs; rb += NR) {
         const int nr = min(NR, nrhs - rb);
@@ -299,7 +308,7 @@ __device__ __forceinline__ void k_fwd_grp_body(const FrontDev* __restrict__ fron
     }
 }
 template <typename T, bool TRANS, int G, int NR>
-__global__ void __launch_bounds__(256) k_fwd_grp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(256) k_fwd_grp(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs) {
@@ -307,17 +316,17 @@ __global__ void __launch_bounds__(256) k_fwd_grp(const FrontDev* __restrict__ fr
 }
 
 template <typename T, bool TRANS, int G, int NR>
-__device__ __forceinline__ void k_bwd_grp_body(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__device__ __forceinline__ void k_bwd_grp_body(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int vb) {
     const int lane = threadIdx.x & 31;
     const int fidx = (vb * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
     const bool active = fidx < count;
     const int i = lane % G;
-    FrontDev fr{};
+    SolveRec fr{};
     int m = 0, k = 0;
     if (active) {
-        fr = fronts[list[fidx]];
+        fr = list[fidx];
         m = fr.m;
         k = fr.k;
     }
@@ -359,7 +368,7 @@ __device__ __forceinline__ void k_bwd_grp_body(const FrontDev* __restrict__ fron
     }
 }
 template <typename T, bool TRANS, int G, int NR>
-__global__ void __launch_bounds__(256) k_bwd_grp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(256) k_bwd_grp(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs) {
     k_bwd_grp_body<T, TRANS, G, NR>(fronts, list, count, fac, dofs, x, n_dof, nrhs, blockIdx.x);
@@ -371,14 +380,14 @@ __global__ void __launch_bounds__(256) k_bwd_grp(const FrontDev* __restrict__ fr
 // applied to the later rows, including the contribution-block rows (update
 // vector).  Shared memory: 32 x 33 T + kRhsChunk x ldw T (ldw >= m).
 template <typename T, bool TRANS>
-__device__ __forceinline__ void k_fwd_cta_body(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__device__ __forceinline__ void k_fwd_cta_body(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int rows_all, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int ldw, int vb, unsigned char* smem_raw) {
     __syncthreads();  // in a persistent sweep the previous body of this CTA may still be reading shared memory
     T* Dg = reinterpret_cast<T*>(smem_raw);  // 32 x 33
     T* w = Dg + 32 * 33;                     // kRhsChunk x ldw
-    const FrontDev fr = fronts[list[vb]];
+    const SolveRec fr = list[vb];
     const int m = fr.m, k = fr.k;
     const int mr = rows_all ? m : k;
     const int32_t* fd = dofs + fr.dof_off;
@@ -388,7 +397,7 @@ __device__ __forceinline__ void k_fwd_cta_body(const FrontDev* __restrict__ fron
     for (int rb = 0; rb < nrhs; rb += kRhsChunk) {
         const int nr = min(kRhsChunk, nrhs - rb);
         for (int i = threadIdx.x; i < mr; i += blockDim.x) {
-            const RhsSrc src = rhs_src(fr, fd, vsrc, i);
+            const RhsSrc src = rhs_src<SolveRec>(fr, fd, vsrc, i);
             for (int rr = 0; rr < nr; rr++)
                 w[rr * ldw + i] = rhs_val<T>(src, vecs + (int64_t)(rb + rr) * vec_size, x + (int64_t)(rb + rr) * n_dof);
         }
@@ -447,7 +456,7 @@ __device__ __forceinline__ void k_fwd_cta_body(const FrontDev* __restrict__ fron
     }
 }
 template <typename T, bool TRANS>
-__global__ void __launch_bounds__(256) k_fwd_cta(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(256) k_fwd_cta(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int rows_all, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int ldw) {
@@ -459,14 +468,14 @@ __global__ void __launch_bounds__(256) k_fwd_cta(const FrontDev* __restrict__ fr
 // then the unit (or, transposed, L11^T) triangle in 32-wide blocks.
 // Shared memory: 32 x 33 T + 8 x 64 x kRhsChunk T + kRhsChunk x ldw T.
 template <typename T, bool TRANS>
-__device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int cb_done, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int ldw, int vb, unsigned char* smem_raw) {
     __syncthreads();  // in a persistent sweep the previous body of this CTA may still be reading shared memory
     T* Dg = reinterpret_cast<T*>(smem_raw);
     T* red = Dg + 32 * 33;                // 8 warps x 64 rows x kRhsChunk
     T* v = red + 8 * 64 * kRhsChunk;      // kRhsChunk x ldw
-    const FrontDev fr = fronts[list[vb]];
+    const SolveRec fr = list[vb];
     const int m = fr.m, k = fr.k;
     const int32_t* fd = dofs + fr.dof_off;
     const T* P = fac + fr.P_off;
@@ -566,7 +575,7 @@ __device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fron
     }
 }
 template <typename T, bool TRANS>
-__global__ void __launch_bounds__(256) k_bwd_cta(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(256) k_bwd_cta(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int cb_done, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int ldw) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
@@ -626,7 +635,7 @@ __device__ __forceinline__ void k_inv_gemv_body(const FrontDev* __restrict__ fro
     const int nin = (PH == PH_BWD1) ? m - k : k;
     for (int j = threadIdx.x; j < nin; j += blockDim.x) {
         T v;
-        if (PH == PH_FWD1) v = gather_rhs<T>(fr, fd, vsrc, vr, xr, j);
+        if (PH == PH_FWD1) v = gather_rhs<T, FrontDev>(fr, fd, vsrc, vr, xr, j);
         else if (PH == PH_BWD1) v = (T)__ldcg(xr + fd[k + j]);
         else v = __ldcg(yr + j);
         vin[j] = v;
@@ -638,7 +647,7 @@ __device__ __forceinline__ void k_inv_gemv_body(const FrontDev* __restrict__ fro
     auto hi = [&](int i) { return PH == PH_FWD1 ? i + 1 : nin; };
     auto finish = [&](int i, T acc) {
         if (PH == PH_FWD1) yr[i] = acc;
-        else if (PH == PH_FWD2) vr[fr.vec_off + (i - k)] = gather_rhs<T>(fr, fd, vsrc, vr, xr, i) - acc;
+        else if (PH == PH_FWD2) vr[fr.vec_off + (i - k)] = gather_rhs<T, FrontDev>(fr, fd, vsrc, vr, xr, i) - acc;
         else if (PH == PH_BWD1) yr[i] = (T)__ldcg(xr + fd[i]) - acc;
         else xr[fd[i]] = (double)acc;
     };
@@ -727,7 +736,7 @@ struct SweepPhase {
 template <typename T>
 struct SweepArgs {
     const FrontDev* fronts;
-    const int32_t* list;
+    const SolveRec* list;
     const RowBlock* rows;
     const T* fac;
     const T* inv;
@@ -789,7 +798,7 @@ __global__ void __launch_bounds__(256) k_solve_sweep(SweepArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     for (int ph = 0; ph < a.n_phases; ph++) {
         const SweepPhase P = a.phases[ph];
-        const int32_t* L = a.list + P.off;
+        const SolveRec* L = a.list + P.off;
         for (int vb = blockIdx.x; vb < P.count; vb += gridDim.x) {
             switch (P.kind) {
 #define SWEEP_GRP(K, GS)                                                                                              \
