@@ -220,6 +220,7 @@ struct mf_factors {
     void* d_cb = nullptr;
     void* d_vec = nullptr;
     int32_t* d_flist = nullptr;
+    FactorRec* d_frec = nullptr;  // the fused / lane-group launch lists as compact records
     int32_t* d_slist = nullptr;
     SolveRec* d_srec = nullptr;  // the substitution list as compact records
     RowBlock* d_rows = nullptr;
@@ -335,7 +336,7 @@ static void free_factors(mf_factors* f) {
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_vsrc, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
-                    f->d_vec, f->d_flist, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
+                    f->d_vec, f->d_flist, f->d_frec, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
                     f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1010,6 +1011,22 @@ static int build_plan(mf_factors* F) {
     if ((rc = upload(&F->d_sweep_f, F->sweep_f))) return rc;
     if ((rc = upload(&F->d_sweep_b, F->sweep_b))) return rc;
     if ((rc = upload(&F->d_flist, flist))) return rc;
+    {
+        std::vector<FactorRec> frec(flist.size());
+        for (size_t i = 0; i < flist.size(); i++) {
+            const FrontDev& fr = a->fronts[flist[i]];
+            FactorRec r{};
+            r.P_off = fr.P_off; r.R_off = fr.R_off; r.S_off = fr.S_off; r.map_off = fr.map_off;
+            r.m = fr.m; r.k = fr.k; r.nchild = fr.nchild; r.elem = fr.elem; r.front = flist[i];
+            for (int c = 0; c < fr.nchild; c++) {
+                const FrontDev& ch = a->fronts[fr.child[c]];
+                r.cS[c] = ch.S_off;
+                r.cn[c] = ch.m - ch.k;
+            }
+            frec[i] = r;
+        }
+        if ((rc = upload(&F->d_frec, frec))) return rc;
+    }
     if ((rc = upload(&F->d_slist, slist))) return rc;
     {
         std::vector<SolveRec> srec(slist.size());
@@ -1222,7 +1239,7 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
             case K_FUSED: {
                 int ldm = L.maxm | 1;
                 size_t sm = fused_smem<T>(L.maxm);
-                k_front_fused<T><<<L.count, L.threads, sm, s>>>(F->d_fronts, F->d_flist + L.off, F->d_maps, d_values, a->npe,
+                k_front_fused<T><<<L.count, L.threads, sm, s>>>(F->d_frec + L.off, F->d_maps, d_values, a->npe,
                                                               fac, cb, L.maxm, ldm, F->tol_rel, F->d_status);
                 break;
             }
@@ -1231,7 +1248,7 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
                 const unsigned g = (unsigned)((L.count + per - 1) / per);
 #define GRP_CASE(GS)                                                                                             \
     case GS:                                                                                                     \
-        k_front_grp<T, GS><<<g, 256, 0, s>>>(F->d_fronts, F->d_flist + L.off, L.count, F->d_maps, d_values, a->npe, \
+        k_front_grp<T, GS><<<g, 256, 0, s>>>(F->d_frec + L.off, L.count, F->d_maps, d_values, a->npe,               \
                                              fac, cb, F->tol_rel, F->d_status);                                  \
         break;
                 switch (L.maxm) {

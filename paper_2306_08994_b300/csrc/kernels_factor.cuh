@@ -62,6 +62,17 @@ __device__ __forceinline__ T block_max_abs(T v, float* red) {
     return (T)r;
 }
 
+// What the fused and lane-group factor kernels read of a front and of its
+// children, stored in launch-list order: one load, no list -> descriptor ->
+// child-descriptor chain before the children's blocks can be fetched.
+struct FactorRec {
+    int64_t P_off, R_off, S_off, map_off;
+    int64_t cS[2];     // children's contribution blocks (CB arena offsets)
+    int32_t m, k, nchild, elem;
+    int32_t cn[2];     // children's contribution-block orders (m - k)
+    int32_t front, pad;
+};
+
 // ---------------------------------------------------------------------------
 // Fused small front: one CTA per front, the whole front in shared memory.
 // Extend-add (or the element matrix at a leaf), partial LU on the k pivots
@@ -69,7 +80,7 @@ __device__ __forceinline__ T block_max_abs(T v, float* red) {
 // Sec. 3 / Table 2, then P, R and the Schur complement S written out.
 // Dynamic shared memory: ldm*maxm T + maxm T + 2*maxm int32 + 32 floats.
 template <typename T>
-__global__ void __launch_bounds__(256) k_front_fused(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(256) k_front_fused(const FactorRec* __restrict__ recs,
                                                      const int32_t* __restrict__ maps, const double* __restrict__ values,
                                                      int npe, T* __restrict__ fac, T* __restrict__ cbs, int maxm, int ldm,
                                                      double tol_rel, DevStatus* st) {
@@ -79,8 +90,8 @@ __global__ void __launch_bounds__(256) k_front_fused(const FrontDev* __restrict_
     int32_t* imap = reinterpret_cast<int32_t*>(urow + maxm);
     float* red = reinterpret_cast<float*>(imap + 2 * maxm);
 
-    const int32_t f = list[blockIdx.x];
-    const FrontDev fr = fronts[f];
+    const FactorRec fr = recs[blockIdx.x];
+    const int32_t f = fr.front;
     const int m = fr.m, k = fr.k, nc = m - k;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
 
@@ -115,17 +126,11 @@ __global__ void __launch_bounds__(256) k_front_fused(const FrontDev* __restrict_
                     }
             }
     } else {
-        const FrontDev c0 = fronts[fr.child[0]];
-        const int n0 = c0.m - c0.k;
-        const T* S0 = cbs + c0.S_off;
-        const T* S1 = nullptr;
-        int n1 = 0;
+        const int n0 = fr.cn[0];
+        const T* S0 = cbs + fr.cS[0];
         const bool two = fr.nchild > 1;
-        if (two) {
-            const FrontDev c1 = fronts[fr.child[1]];
-            n1 = c1.m - c1.k;
-            S1 = cbs + c1.S_off;
-        }
+        const T* S1 = two ? cbs + fr.cS[1] : nullptr;
+        const int n1 = two ? fr.cn[1] : 0;
         for (int jb = warp; jb < m; jb += 4 * nwarp)
             for (int ib = lane; ib < m; ib += 64) {
                 T v[4][2];
@@ -203,20 +208,16 @@ __global__ void __launch_bounds__(256) k_front_fused(const FrontDev* __restrict_
 // at a leaf, extend-add of the children's blocks otherwise), static pivot
 // check, T1 division of the pivot row, T2/T3 update, then P, R, S written.
 template <typename T, int G>
-__global__ void __launch_bounds__(256) k_front_grp(const FrontDev* __restrict__ fronts, const int32_t* __restrict__ list,
-                                                   int count, const int32_t* __restrict__ maps,
+__global__ void __launch_bounds__(256) k_front_grp(const FactorRec* __restrict__ recs, int count, const int32_t* __restrict__ maps,
                                                    const double* __restrict__ values, int npe, T* __restrict__ fac,
                                                    T* __restrict__ cbs, double tol_rel, DevStatus* st) {
     const int lane = threadIdx.x & 31;
     const int fidx = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
     const bool active = fidx < count;
     const int i = lane % G;
-    int32_t f = -1;
-    FrontDev fr{};
-    if (active) {
-        f = list[fidx];
-        fr = fronts[f];
-    }
+    FactorRec fr{};
+    if (active) fr = recs[fidx];
+    const int32_t f = active ? fr.front : -1;
     const int m = active ? fr.m : 0, k = active ? fr.k : 0;
     const bool row = i < m;
     T a[G];
@@ -236,17 +237,11 @@ __global__ void __launch_bounds__(256) k_front_grp(const FrontDev* __restrict__ 
     } else {
         const int32_t* m0 = maps + fr.map_off;
         const int32_t* m1 = m0 + m;
-        const FrontDev c0 = fronts[fr.child[0]];
-        const int n0 = c0.m - c0.k;
-        const T* S0 = cbs + c0.S_off;
-        const T* S1 = nullptr;
-        int n1 = 0;
+        const int n0 = fr.cn[0];
+        const T* S0 = cbs + fr.cS[0];
         const bool two = fr.nchild > 1;
-        if (two) {
-            const FrontDev c1 = fronts[fr.child[1]];
-            n1 = c1.m - c1.k;
-            S1 = cbs + c1.S_off;
-        }
+        const T* S1 = two ? cbs + fr.cS[1] : nullptr;
+        const int n1 = two ? fr.cn[1] : 0;
         const int i0 = row ? m0[i] : -1, i1 = (row && two) ? m1[i] : -1;
 #pragma unroll
         for (int j = 0; j < G; j++) {
