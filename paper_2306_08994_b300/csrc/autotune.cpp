@@ -31,7 +31,7 @@ struct Timer {
 
 // Version of the launch-plan builder: bumped whenever its kernels or its
 // decomposition change enough that plans tuned before are stale.
-constexpr int kPlanVersion = 5;
+constexpr int kPlanVersion = 6;
 
 int family_of(int precision) { return precision == MF_F64 ? 0 : 1; }
 
@@ -80,6 +80,8 @@ bool cache_lookup(const char* path, const std::string& key, mf_options* o, doubl
     t.super_panel = std::atoi(v);
     if (!(v = field(hit, "subtree_solve_levels"))) return false;
     t.subtree_solve_levels = std::atoi(v);
+    if (!(v = field(hit, "lookahead"))) return false;
+    t.lookahead = std::atoi(v);
     if (!(v = field(hit, "fused_threads")) || *v != '[') return false;
     v++;
     for (int b = 0; b < MF_FUSED_BUCKETS; b++) {
@@ -101,9 +103,9 @@ void cache_append(const char* path, const std::string& key, const mf_options& o,
     FILE* fp = std::fopen(path, "a");
     if (!fp) return;
     std::fprintf(fp, "{\"key\":\"%s\",\"precision\":%d,\"small_front_max\":%d,\"subtree_levels\":%d,\"tc_min_cb\":%d,"
-                     "\"super_panel\":%d,\"subtree_solve_levels\":%d,\"fused_threads\":[",
+                     "\"super_panel\":%d,\"subtree_solve_levels\":%d,\"lookahead\":%d,\"fused_threads\":[",
                  key.c_str(), o.precision, o.small_front_max, o.subtree_levels, o.tc_min_cb, o.super_panel,
-                 o.subtree_solve_levels);
+                 o.subtree_solve_levels, o.lookahead);
     for (int b = 0; b < MF_FUSED_BUCKETS; b++) std::fprintf(fp, "%s%d", b ? "," : "", o.fused_threads[b]);
     std::fprintf(fp, "],\"ms_best\":%.4f,\"ms_default\":%.4f,\"candidates\":%d}\n", ms_best, ms_default, candidates);
     std::fclose(fp);
@@ -286,6 +288,11 @@ extern "C" int mf_autotune(const mf_analysis* a, const double* d_values, const d
             t.super_panel = sp;
             if (sp != start.super_panel) try_one(t);
         }
+    }
+    if (!rc) {  // one-panel lookahead (only acts when the super-panel depth is the panel width)
+        mf_options t = cur;
+        t.lookahead = cur.lookahead >= 0 ? -1 : 0;
+        try_one(t);
     }
     if (!rc && family_of(o.precision) == 1) {
         const mf_options start = cur;

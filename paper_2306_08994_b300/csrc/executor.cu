@@ -18,7 +18,8 @@
 namespace {
 
 enum LaunchKind { K_FUSED = 0, K_ASM = 1, K_PDIAG = 2, K_GEMM = 3, K_INVDIAG = 4, K_SUBTREE = 5, K_GEMMTC = 6, K_GRP = 7,
-                  K_TCPACK = 8, K_FORK = 10, K_JOIN = 11 };
+                  K_TCPACK = 8, K_FORK = 10, K_JOIN = 11,
+                  K_SYNC = 12 };  // K_SYNC: stream `stream` waits for what stream `bucket` issued so far (event `off`)
 
 struct Launch {
     int kind;
@@ -28,7 +29,7 @@ struct Launch {
     int64_t off;  // offset into the list of its kind
     int bucket = -1;  // fused: size bucket (index into kFusedBounds)
     int threads = 0;  // fused: threads per CTA
-    int stream = 0;   // 0: the caller's stream; 1: the side stream (pivot-block inverses)
+    int stream = 0;   // 0: the caller's stream; 1: the side stream (pivot-block inverses); 2: the lookahead stream
 };
 
 // Solve plan of one class: fronts split by size (see kernels_solve.cuh).
@@ -245,6 +246,10 @@ struct mf_factors {
     std::vector<cudaEvent_t> fork_ev;
     cudaEvent_t join_ev = nullptr;
     int n_forks = 0;
+    bool la = false;             // one-panel lookahead in the large-front partial LU
+    cudaStream_t s3 = nullptr;   // lookahead stream: the next pivot block beside the trailing update
+    std::vector<cudaEvent_t> sync_ev;
+    int n_sync = 0;
     unsigned int* d_famax = nullptr;
     DevStatus* d_status = nullptr;
     double *d_r = nullptr, *d_d = nullptr, *d_Y = nullptr, *d_rowabs = nullptr, *d_part = nullptr, *d_norms = nullptr;
@@ -333,6 +338,9 @@ static void free_factors(mf_factors* f) {
         if (e) cudaEventDestroy(e);
     if (f->join_ev) cudaEventDestroy(f->join_ev);
     if (f->s2) cudaStreamDestroy(f->s2);
+    if (f->s3) cudaStreamDestroy(f->s3);
+    for (cudaEvent_t e : f->sync_ev)
+        if (e) cudaEventDestroy(e);
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_vsrc, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
@@ -768,18 +776,21 @@ static int build_plan(mf_factors* F) {
                 }
                 if (gem.size() > (size_t)soff) push({K_GEMM, c, (int)(gem.size() - soff), 0, soff}, FAM_TRAIL, gb, gf);
             }
-            // (A) diagonal blocks: factor + invert, one warp per front
-            int64_t poff = (int64_t)pan.size();
-            double pb = 0, pf = 0;
-            for (size_t bi = 0; bi < big.size(); bi++) {
-                const FrontDev& fr = a->fronts[big[bi]];
-                if (kb >= fr.k) continue;
-                const int w = std::min(nb, fr.k - kb);
-                pan.push_back({big[bi], kb, w, 0, (int64_t)bi * 64 * 64});
-                pb += 3.0 * T * w * w;
-                pf += 2.0 * w * w * w;
+            // (A) diagonal blocks: factor + invert, one CTA per front (with lookahead, the blocks
+            //     after the first were issued on the lookahead stream in the previous step)
+            if (!F->la || kb == 0) {
+                int64_t poff = (int64_t)pan.size();
+                double pb = 0, pf = 0;
+                for (size_t bi = 0; bi < big.size(); bi++) {
+                    const FrontDev& fr = a->fronts[big[bi]];
+                    if (kb >= fr.k) continue;
+                    const int w = std::min(nb, fr.k - kb);
+                    pan.push_back({big[bi], kb, w, 0, (int64_t)bi * 64 * 64});
+                    pb += 3.0 * T * w * w;
+                    pf += 2.0 * w * w * w;
+                }
+                push({K_PDIAG, c, (int)(pan.size() - poff), 0, poff}, FAM_PANEL, pb, pf);
             }
-            push({K_PDIAG, c, (int)(pan.size() - poff), 0, poff}, FAM_PANEL, pb, pf);
             // (B) panel products in place: L21 = A21 U_D^-1, U12 = L_D^-1 A12
             int64_t goff = (int64_t)gem.size();
             gb = gf = 0;
@@ -802,7 +813,31 @@ static int build_plan(mf_factors* F) {
                 }
             }
             if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_PANEL, gb, gf);
+            // (A') lookahead: the next pivot block takes this panel's update and is factored on
+            //      the lookahead stream while (C) runs on the main one
+            bool la_step = false;
+            if (F->la) {
+                int64_t poff = (int64_t)pan.size();
+                double pb = 0, pf = 0;
+                for (size_t bi = 0; bi < big.size(); bi++) {
+                    const FrontDev& fr = a->fronts[big[bi]];
+                    if (kb + nb >= fr.k) continue;
+                    const int w = std::min(nb, fr.k - kb - nb);
+                    pan.push_back({big[bi], kb + nb, w, nb, (int64_t)bi * 64 * 64});
+                    pb += T * (3.0 * w * w + 2.0 * w * nb);
+                    pf += 2.0 * w * w * w + 2.0 * w * w * nb;
+                }
+                if (pan.size() > (size_t)poff) {
+                    la_step = true;
+                    push({K_SYNC, c, 0, 0, F->n_sync++, 0}, FAM_OTHER, 0.0, 0.0);
+                    F->plan.back().stream = 2;
+                    cur_stream = 2;
+                    push({K_PDIAG, c, (int)(pan.size() - poff), 0, poff}, FAM_PANEL, pb, pf);
+                    cur_stream = 0;
+                }
+            }
             // (C) end of a super-panel: the pivot rows and columns beyond it take all of its pivots
+            //     (with lookahead: all but the next pivot block, which took its share in (A'))
             if (kb + nb == s0 + SP || kb + nb >= maxk) {
                 goff = (int64_t)gem.size();
                 gb = gf = 0;
@@ -811,13 +846,23 @@ static int build_plan(mf_factors* F) {
                     const int m = fr.m, k = fr.k, e = s0 + SP;
                     if (s0 >= k || e >= k) continue;  // the front's pivots end inside this super-panel
                     const int64_t Lb = fr.P_off + e + (int64_t)s0 * m;  // L[e.., s0..e)
-                    any_gemm(Lb, m, fr.P_off + s0 + (int64_t)e * m, m, AR_FAC, fr.P_off + e + (int64_t)e * m, m, m - e, k - e,
-                             SP);
+                    if (F->la) {
+                        const int w2 = std::min(nb, k - e);
+                        // below the next pivot block, then everything right of it
+                        any_gemm(Lb + w2, m, fr.P_off + s0 + (int64_t)e * m, m, AR_FAC, fr.P_off + e + w2 + (int64_t)e * m, m,
+                                 m - e - w2, w2, SP);
+                        any_gemm(Lb, m, fr.P_off + s0 + (int64_t)(e + w2) * m, m, AR_FAC, fr.P_off + e + (int64_t)(e + w2) * m,
+                                 m, m - e, k - e - w2, SP);
+                    } else {
+                        any_gemm(Lb, m, fr.P_off + s0 + (int64_t)e * m, m, AR_FAC, fr.P_off + e + (int64_t)e * m, m, m - e,
+                                 k - e, SP);
+                    }
                     any_gemm(Lb, m, fr.R_off + s0, k, AR_FAC, fr.R_off + e, k, k - e, m - k, SP);
                 }
                 if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_TRAIL, gb, gf);
                 tc_end(c, FAM_TRAIL);
             }
+            if (la_step) push({K_SYNC, c, 0, 0, F->n_sync++, 2}, FAM_OTHER, 0.0, 0.0);  // main waits for (A')
         }
         // Schur update S -= L21 U12 (Sec. 2.2): tensor cores (MF_TF32) for large blocks, SIMT otherwise
         int64_t goff = (int64_t)gem.size();
@@ -1108,6 +1153,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     }
     F->sp = F->opt.super_panel > 0 ? F->opt.super_panel : (F->prec == MF_F64 ? F->nb : 256);
     F->sp = std::max(F->nb, (F->sp + F->nb - 1) / F->nb * F->nb);
+    F->la = F->sp == F->nb && F->opt.lookahead >= 0;
     for (int i = 0; i < MF_FUSED_BUCKETS; i++) {
         const int t = F->opt.fused_threads[i];
         if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256) {
@@ -1200,6 +1246,32 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
             return MF_ECUDA;
         }
     }
+    if (F->n_sync > 0) {
+        if (cudaStreamCreateWithFlags(&F->s3, cudaStreamNonBlocking) != cudaSuccess) {
+            free_factors(F);
+            return MF_ECUDA;
+        }
+        F->sync_ev.assign(F->n_sync, nullptr);
+        for (int i = 0; i < F->n_sync; i++)
+            if (cudaEventCreateWithFlags(&F->sync_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+                free_factors(F);
+                return MF_ECUDA;
+            }
+    }
+    {
+        const cudaError_t e = F->prec == MF_F64
+                                  ? cudaFuncSetAttribute(k_panel_diag_blk<double, kPanelNB64>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)panel_diag_dyn_smem<double, kPanelNB64>())
+                                  : cudaFuncSetAttribute(k_panel_diag_blk<float, kPanelNB32>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)panel_diag_dyn_smem<float, kPanelNB32>());
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            free_factors(F);
+            return MF_ECUDA;
+        }
+    }
     TRY(dev_alloc((char**)&F->d_ys, (size_t)a->ys_size * F->max_nrhs * F->tsize));
 #undef TRY
     *out = F;
@@ -1230,8 +1302,15 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
             CUDA_TRY(cudaStreamWaitEvent(s_main, F->join_ev, 0));
             continue;
         }
-        s = L.stream ? F->s2 : s_main;
-        float* pk = L.stream ? F->d_pk2 : F->d_pk;
+        if (L.kind == K_SYNC) {  // stream L.stream waits for the work issued so far on stream L.bucket
+            const cudaStream_t sig = L.bucket == 0 ? s_main : L.bucket == 1 ? F->s2 : F->s3;
+            const cudaStream_t wai = L.stream == 0 ? s_main : L.stream == 1 ? F->s2 : F->s3;
+            CUDA_TRY(cudaEventRecord(F->sync_ev[L.off], sig));
+            CUDA_TRY(cudaStreamWaitEvent(wai, F->sync_ev[L.off], 0));
+            continue;
+        }
+        s = L.stream == 0 ? s_main : L.stream == 1 ? F->s2 : F->s3;
+        float* pk = L.stream == 1 ? F->d_pk2 : F->d_pk;
         slot = prof_begin(F, s, F->plan_fam[li], F->plan_bytes[li], F->plan_flops[li], 1,
                           F->plan[li].kind == K_FUSED ? F->plan[li].bucket : -1, F->plan[li].kind, F->plan[li].cls,
                           F->plan[li].count);
@@ -1265,7 +1344,7 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
                 break;
             case K_PDIAG: {
                 constexpr int NB = sizeof(T) == 8 ? kPanelNB64 : kPanelNB32;
-                k_panel_diag_blk<T, NB><<<L.count, 256, 0, s>>>(F->d_fronts, F->d_panel + L.off, fac,
+                k_panel_diag_blk<T, NB><<<L.count, 256, panel_diag_dyn_smem<T, NB>(), s>>>(F->d_fronts, F->d_panel + L.off, fac,
                                                                             (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
                 break;
             }

@@ -391,10 +391,17 @@ __global__ void __launch_bounds__(256) k_assemble_large(const FrontDev* __restri
 //   (each output tile spans the whole w-wide side, so it reads all of its
 //   input before writing), then the trailing update k_gemm.
 // One CTA per front.
+// With one-panel lookahead the block first takes the update from the panel
+// before it (pre = that panel's width, its columns kb-pre..kb):
+//   F[kb:kb+w, kb:kb+w] -= L[kb:kb+w, kb-pre:kb] U[kb-pre:kb, kb:kb+w],
+// so it can be factored while the rest of that panel's trailing update runs.
 struct DiagTask {
-    int32_t front, kb, w, pad;
+    int32_t front, kb, w, pre;
     int64_t slot;  // panel-slot offset (64 x 64, column-major, ld 64)
 };
+// dynamic shared memory of k_panel_diag_blk (the U block of the lookahead update)
+template <typename T, int NB>
+constexpr size_t panel_diag_dyn_smem() { return (size_t)NB * (NB + 1) * sizeof(T); }
 
 // Pivot block of a large front (NB x NB at pivot kb, padded with the
 // identity beyond w): partial LU in place (L with its diagonal, unit U) and
@@ -430,13 +437,50 @@ __global__ void __launch_bounds__(256) k_panel_diag_blk(const FrontDev* __restri
     const int m = fr.m, kb = t.kb, w = t.w;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     T* P = fac + fr.P_off;
+    extern __shared__ __align__(16) unsigned char pd_dyn[];
+    T* Us = reinterpret_cast<T*>(pd_dyn);  // U block of the lookahead update, NB x (NB + 1)
+    const int pre = t.pre, p0 = kb - t.pre;
     for (int j = warp; j < NB; j += 8)
         for (int i = lane; i < NB; i += 32) {
             if (i < w && j < w) cp_async_elem(&D[i][j], P + (kb + i) + (int64_t)(kb + j) * m);
             else D[i][j] = (i == j) ? T(1) : T(0);
+            if (pre > 0) {
+                // L block (rows kb.., columns p0..) into Z, U block (rows p0.., columns kb..) into Us;
+                // zero outside w x pre and pre x w, so the identity padding of D takes no update
+                if (i < w && j < pre) cp_async_elem(&Z[i][j], P + (kb + i) + (int64_t)(p0 + j) * m);
+                else Z[i][j] = T(0);
+                if (i < pre && j < w) cp_async_elem(&Us[i * (NB + 1) + j], P + (p0 + i) + (int64_t)(kb + j) * m);
+                else Us[i * (NB + 1) + j] = T(0);
+            }
         }
     cp_async_wait_all();
     __syncthreads();
+    if (pre > 0) {
+        constexpr int RPT = NB / 16;  // RPT x RPT outputs per thread
+        const int ti = tid >> 4, tj = tid & 15;
+        T acc[RPT][RPT];
+#pragma unroll
+        for (int r = 0; r < RPT; r++)
+#pragma unroll
+            for (int c = 0; c < RPT; c++) acc[r][c] = T(0);
+        for (int q = 0; q < pre; q++) {
+            T av[RPT], bv[RPT];
+#pragma unroll
+            for (int r = 0; r < RPT; r++) {
+                av[r] = Z[ti * RPT + r][q];
+                bv[r] = Us[q * (NB + 1) + tj * RPT + r];
+            }
+#pragma unroll
+            for (int r = 0; r < RPT; r++)
+#pragma unroll
+                for (int c = 0; c < RPT; c++) acc[r][c] += av[r] * bv[c];
+        }
+#pragma unroll
+        for (int r = 0; r < RPT; r++)
+#pragma unroll
+            for (int c = 0; c < RPT; c++) D[ti * RPT + r][tj * RPT + c] -= acc[r][c];
+        __syncthreads();
+    }
     const T amax = (T)__uint_as_float(famax[t.front]);
     const T thr = (T)tol_rel * amax > T(0) ? (T)tol_rel * amax : tiny_pivot<T>();
 

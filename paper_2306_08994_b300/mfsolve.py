@@ -35,7 +35,8 @@ class mf_options(ctypes.Structure):
                 ("max_nrhs", ctypes.c_int), ("subtree_levels", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
                 ("subtree_solve_levels", ctypes.c_int),
                 ("tc_min_cb", ctypes.c_int),
-                ("super_panel", ctypes.c_int), ("fused_threads", ctypes.c_int * MF_FUSED_BUCKETS)]
+                ("super_panel", ctypes.c_int), ("fused_threads", ctypes.c_int * MF_FUSED_BUCKETS),
+                ("lookahead", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {f: (list(getattr(self, f)) if f == "fused_threads" else getattr(self, f)) for f, _ in self._fields_}

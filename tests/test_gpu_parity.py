@@ -71,6 +71,11 @@ CASES = {
     "q1_3d_5_subtree": (lambda: F.diffusion_3d_q1(5, seed=35), {"subtree_levels": 4, "small_front_max": 24}),
     "q3_12_solve_subtree_only": (lambda: F.diffusion_2d(12, 3, seed=37), {"subtree_solve_levels": 5}),
     "q1_20_solve_subtree8": (lambda: F.poisson_2d_q1(20), {"subtree_solve_levels": 8, "small_front_max": 32}),
+    # large-front partial LU with one-panel lookahead (default when the super-panel is one panel:
+    # FP64 always, FP32 with super_panel = 64); the root (73 pivots) spans 3 FP64 / 2 FP32 panels
+    "q3_24_lookahead": (lambda: F.diffusion_2d(24, 3, seed=38), {"small_front_max": 16, "super_panel": 64}),
+    "q3_24_no_lookahead": (lambda: F.diffusion_2d(24, 3, seed=38), {"small_front_max": 16, "super_panel": 64,
+                                                                    "lookahead": -1}),
 }
 
 
@@ -163,6 +168,26 @@ def test_tensor_core_schur_path(n):
     d32 = np.abs(factors["f32"] - factors["f64"]).max()
     dtc = np.abs(factors["tf32"] - factors["f64"]).max()
     assert dtc <= 10 * d32 + 1e-12, (dtc, d32)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_lookahead_factors_match_plain_panel_order(prec):
+    """One-panel lookahead (the next pivot block takes its rank-w update inside the
+    pivot-block kernel, on a second stream) against the plain panel order: the same
+    factors up to rounding, front by front, on the top fronts of a 48 x 48 Q3 mesh
+    (root: 145 pivots, 3 FP32 / 5 FP64 panels)."""
+    pr = F.diffusion_2d(48, 3, seed=39)
+    out = {}
+    for la in (0, -1):
+        a, f, vals = _setup(pr, prec, small_front_max=16, super_panel=64 if prec == "f32" else 32, lookahead=la)
+        f.factor(vals)
+        assert f.status()["rc"] == 0
+        out[la] = [f.export_front(g) for g in range(a.n_front - 7, a.n_front)]
+    tol = 1e-12 if prec == "f64" else 2e-4
+    for (L0, U0), (L1, U1) in zip(out[0], out[-1]):
+        sc = max(np.abs(L1).max(), np.abs(U1).max(), 1.0)
+        assert np.abs(L0 - L1).max() <= tol * sc
+        assert np.abs(U0 - U1).max() <= tol * sc
 
 
 def test_adjoint_solve_on_unsymmetric_matrix():
