@@ -1350,7 +1350,8 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
             }
             case K_GEMM: {
                 Arenas<T> ar{{fac, cb, (T*)F->d_inv, (T*)F->d_scr, (T*)F->d_pnl}};
-                k_gemm<T, sizeof(T) == 8 ? 8 : 16><<<L.count, 256, 0, s>>>(F->d_gemm + L.off, ar);
+                if constexpr (sizeof(T) == 8) k_gemm<T, 8><<<L.count, 256, 0, s>>>(F->d_gemm + L.off, ar);
+                else k_gemm_cp<16, 3><<<L.count, 256, 0, s>>>(F->d_gemm + L.off, ar);
                 break;
             }
             case K_SUBTREE:

@@ -808,6 +808,116 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTile* __restrict__ tiles
     }
 }
 
+// 4-byte global -> shared copy that writes zero when `pred` is false (nothing is read then;
+// the source address is still kept inside the operand)
+__device__ __forceinline__ void cp_async4_zfill(float* smem_dst, const float* gmem_src, bool pred) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    const int n = pred ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem_src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// FP32 variant of k_gemm for the same 64 x 64 output tiles and 256 threads,
+// written against latency: the operand slices of depth BK stream through a
+// ring of STAGES shared buffers by cp.async (zero-filled outside the
+// operands, masks applied in place by the copying thread), so up to
+// STAGES - 1 slices are in flight while one is multiplied; the C tile of
+// C -= A B is read into registers at the start.  Each thread holds a
+// contiguous 4 x 4 block (rows 4tx.., columns 4ty..) and reads its operands
+// as two float4 shared loads per k.  Same tile semantics as k_gemm: op 0
+// C -= A B, op 1 C = A B, op 2 C = -A B, triangular operand masks.
+template <int BK, int STAGES>
+__global__ void __launch_bounds__(256, 3) k_gemm_cp(const GemmTile* __restrict__ tiles, Arenas<float> ar) {
+    constexpr int LD = 64 + 4;  // row pitch (floats): 16-byte aligned rows
+    __shared__ __align__(16) float As[STAGES][BK][LD];
+    __shared__ __align__(16) float Bs[STAGES][BK][LD];
+    const GemmTile t = tiles[blockIdx.x];
+    const float* A = ar.a[t.a_ar] + t.a_off;
+    const float* B = ar.a[t.b_ar] + t.b_off;
+    float* C = ar.a[t.c_ar] + t.c_off;
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    constexpr int PER = 64 * BK / 256;  // elements of each operand slice per thread
+    static_assert(PER * 4 == BK || BK == 16, "slice mapping assumes BK = 16");
+    const int nk = (t.K + BK - 1) / BK;
+    // thread -> slice elements: A (ai, ak + 4r) (down a column), B (bk, bj + 16r) (down a column of B)
+    const int ai = tid & 63, ak = tid >> 6, bk = tid & 15, bj = tid >> 4;
+    const bool a_row = t.i0 + ai < t.M;
+    const float* pa = a_row ? A + (t.i0 + ai) + (int64_t)ak * t.lda : A;
+    const float* pb = B + bk + (int64_t)(t.j0 + bj) * t.ldb;
+    auto issue = [&](int kt) {
+        const int buf = kt % STAGES, kk0 = kt * BK;
+#pragma unroll
+        for (int r = 0; r < PER; r++) {
+            const bool va = a_row && kk0 + ak + 4 * r < t.K;
+            cp_async4_zfill(&As[buf][ak + 4 * r][ai], va ? pa + (int64_t)(kk0 + 4 * r) * t.lda : A, va);
+            const bool vb = t.j0 + bj + 16 * r < t.N && kk0 + bk < t.K;
+            cp_async4_zfill(&Bs[buf][bk][bj + 16 * r], vb ? pb + kk0 + (int64_t)(16 * r) * t.ldb : B, vb);
+        }
+    };
+    auto fix_masks = [&](int kt) {  // the copying thread's own elements, after its wait
+        const int buf = kt % STAGES, kk0 = kt * BK;
+#pragma unroll
+        for (int r = 0; r < PER; r++) {
+            const int gi = t.i0 + ai, gk = kk0 + ak + 4 * r;
+            if (t.a_mask && gi < t.M && gk < t.K) As[buf][ak + 4 * r][ai] = masked(As[buf][ak + 4 * r][ai], t.a_mask, gi, gk);
+            const int gj = t.j0 + bj + 16 * r, gk2 = kk0 + bk;
+            if (t.b_mask && gj < t.N && gk2 < t.K) Bs[buf][bk][bj + 16 * r] = masked(Bs[buf][bk][bj + 16 * r], t.b_mask, gk2, gj);
+        }
+    };
+#pragma unroll
+    for (int st = 0; st < STAGES - 1; st++) {
+        if (st < nk) issue(st);
+        cp_async_commit();
+    }
+    // C of C -= A B: read now, used after the k loop
+    float cv[4][4];
+    const int ci = t.i0 + 4 * tx, cj = t.j0 + 4 * ty;
+    float* pc = C + ci + (int64_t)cj * t.ldc;
+#pragma unroll
+    for (int c = 0; c < 4; c++)
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+            cv[r][c] = (t.op == 0 && ci + r < t.M && cj + c < t.N) ? pc[r + (int64_t)c * t.ldc] : 0.f;
+    float acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[r][c] = 0.f;
+    const bool any_mask = t.a_mask || t.b_mask;
+    for (int kt = 0; kt < nk; kt++) {
+        cp_async_wait_group<STAGES - 2>();  // this thread's copies of slice kt have landed
+        if (any_mask) fix_masks(kt);
+        __syncthreads();                    // everyone's slice kt is visible; slice kt-1 is consumed
+        if (kt + STAGES - 1 < nk) issue(kt + STAGES - 1);
+        cp_async_commit();
+        const int buf = kt % STAGES;
+#pragma unroll
+        for (int kk = 0; kk < BK; kk++) {
+            const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][kk][4 * tx]);
+            const float4 b4 = *reinterpret_cast<const float4*>(&Bs[buf][kk][4 * ty]);
+            const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+            const float b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+        }
+    }
+    cp_async_wait_group<0>();
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        if (cj + c >= t.N) continue;
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            if (ci + r >= t.M) continue;
+            pc[r + (int64_t)c * t.ldc] = t.op == 0 ? cv[r][c] - acc[r][c] : (t.op == 1 ? acc[r][c] : -acc[r][c]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Explicit inverses of the pivot blocks of large fronts, used by the solve
 // (the triangular solves become wide products).  The inverse block Q (k x k,
