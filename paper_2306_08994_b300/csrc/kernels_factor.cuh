@@ -416,13 +416,11 @@ constexpr size_t panel_diag_dyn_smem() { return (size_t)NB * (NB + 1) * sizeof(T
 //   (2) the sub-panels beside it are finished by triangular solves, one
 //       thread per row (L: X U_kk = A) or per column (U: L_kk Y = A);
 //   (3) the trailing sub-blocks take the rank-16 update.
-// Three block barriers per sub-block.  The inverses then come blockwise:
-// diagonal sub-blocks by one thread per column, off-diagonal ones by
-// distance from the diagonal,
-//   X_ik = -X_ii sum_{j=k}^{i-1} L_ij X_jk,   Y_kj = -Y_kk sum_{i=k+1}^{j} U_ki Y_ij,
-// one warp per sub-block and one barrier per distance.
+// Three block barriers per sub-block.  The inverses then come column by
+// column, one thread per column of L_D^-1 (L_D x = e_c) and of U_D^-1
+// (U_D y = e_c), each column in registers.
 template <typename T, int NB>
-__global__ void __launch_bounds__(256) k_panel_diag_blk(const FrontDev* __restrict__ fronts,
+__global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __restrict__ fronts,
                                                         const DiagTask* __restrict__ tasks, T* __restrict__ fac,
                                                         T* __restrict__ slots, const unsigned int* __restrict__ famax,
                                                         double tol_rel, DevStatus* st) {
@@ -430,7 +428,6 @@ __global__ void __launch_bounds__(256) k_panel_diag_blk(const FrontDev* __restri
     static_assert(NB % 16 == 0 && NBB <= 4, "NB must be 16, 32, 48 or 64");
     __shared__ T D[NB][NB + 1];
     __shared__ T Z[NB][NB + 1];
-    __shared__ T Tw[8][16][17];
     __shared__ T rdiag[NB];
     const DiagTask t = tasks[blockIdx.x];
     const FrontDev fr = fronts[t.front];
@@ -574,111 +571,39 @@ __global__ void __launch_bounds__(256) k_panel_diag_blk(const FrontDev* __restri
     for (int j = warp; j < w; j += 8)
         for (int i = lane; i < w; i += 32) P[(kb + i) + (int64_t)(kb + j) * m] = D[i][j];
 
-    // ---- inverses, diagonal sub-blocks: warp kk -> L_kk^-1, warp NBB + kk -> U_kk^-1 (one lane per column)
-    if (warp < 2 * NBB && lane < 16) {
-        const int kk = warp % NBB, o = 16 * kk, c = lane;
-        T x[16];
-        if (warp < NBB) {  // L_kk x = e_c
+    // ---- inverses, one thread per column: threads 0..NB-1 column c of L_D^-1 (forward),
+    //      threads NB..2NB-1 column c of U_D^-1 (backward, unit diagonal).  Right-looking: once
+    //      entry r is final it is applied to all later entries, so every step is NB-r independent
+    //      FMAs on a column held in registers (the D reads are warp-wide broadcasts).
+    if (tid < 2 * NB) {
+        const int c = tid % NB;
+        T a[NB];
 #pragma unroll
-            for (int rr = 0; rr < 16; rr++) {
-                T v = rr == c ? T(1) : T(0);
+        for (int r = 0; r < NB; r++) a[r] = r == c ? T(1) : T(0);
+        if (tid < NB) {
 #pragma unroll
-                for (int q = 0; q < rr; q++) v -= D[o + rr][o + q] * x[q];
-                x[rr] = v * rdiag[o + rr];
+            for (int r = 0; r < NB; r++) {
+                const T xr = a[r] * rdiag[r];
+                a[r] = xr;
+#pragma unroll
+                for (int r2 = r + 1; r2 < NB; r2++) a[r2] -= D[r2][r] * xr;
             }
 #pragma unroll
-            for (int rr = 0; rr < 16; rr++)
-                if (rr >= c) Z[o + rr][o + c] = x[rr];
-        } else {  // U_kk y = e_c (unit upper), bottom-up
+            for (int r = 0; r < NB; r++)
+                if (r >= c) Z[r][c] = a[r];
+        } else {
 #pragma unroll
-            for (int rr = 15; rr >= 0; rr--) {
-                T v = rr == c ? T(1) : T(0);
+            for (int r = NB - 1; r > 0; r--) {
+                const T yr = a[r];
 #pragma unroll
-                for (int q = rr + 1; q < 16; q++) v -= D[o + rr][o + q] * x[q];
-                x[rr] = v;
+                for (int r2 = 0; r2 < r; r2++) a[r2] -= D[r2][r] * yr;
             }
 #pragma unroll
-            for (int rr = 0; rr < 16; rr++)
-                if (rr < c) Z[o + rr][o + c] = x[rr];
+            for (int r = 0; r < NB; r++)
+                if (r < c) Z[r][c] = a[r];
         }
     }
     __syncthreads();
-    // ---- off-diagonal sub-blocks by distance d from the diagonal
-    for (int d = 1; d < NBB; d++) {
-        const int nblk = NBB - d;
-        if (warp < 2 * nblk) {
-            const bool lower = warp < nblk;
-            const int k0 = lower ? warp : warp - nblk;  // X_{k0+d, k0} or Y_{k0, k0+d}
-            const int r = lane & 15, h = lane >> 4;
-            T acc[8];
-#pragma unroll
-            for (int e = 0; e < 8; e++) acc[e] = T(0);
-            if (lower) {  // T = sum_{j=k0}^{i-1} L_ij X_j,k0,   i = k0 + d
-                const int io = 16 * (k0 + d), ko = 16 * k0;
-                for (int jb = k0; jb < k0 + d; jb++) {
-                    const int jo = 16 * jb;
-#pragma unroll
-                    for (int q = 0; q < 16; q++) {
-                        const T l = D[io + r][jo + q];
-#pragma unroll
-                        for (int e = 0; e < 8; e++) {
-                            const int cc = 8 * h + e;
-                            // X_j,k0 (lower part of Z; zero above the diagonal of a diagonal sub-block)
-                            const T xv = (jb == k0 && jo + q < ko + cc) ? T(0) : Z[jo + q][ko + cc];
-                            acc[e] += l * xv;
-                        }
-                    }
-                }
-            } else {  // T = sum_{i=k0+1}^{j} U_k0,i Y_i,j,   j = k0 + d
-                const int ko = 16 * k0, jo = 16 * (k0 + d);
-                for (int ib = k0 + 1; ib <= k0 + d; ib++) {
-                    const int io = 16 * ib;
-#pragma unroll
-                    for (int q = 0; q < 16; q++) {
-                        const T u = D[ko + r][io + q];
-#pragma unroll
-                        for (int e = 0; e < 8; e++) {
-                            const int cc = 8 * h + e;
-                            // Y_i,j: unit diagonal, zero below it, when ib is the diagonal sub-block j
-                            T yv;
-                            if (ib == k0 + d) yv = (q == cc) ? T(1) : (q < cc ? Z[io + q][jo + cc] : T(0));
-                            else yv = Z[io + q][jo + cc];
-                            acc[e] += u * yv;
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int e = 0; e < 8; e++) Tw[warp][r][8 * h + e] = acc[e];
-            __syncwarp();
-            T out[8];
-#pragma unroll
-            for (int e = 0; e < 8; e++) out[e] = T(0);
-            if (lower) {  // X_ik = -X_ii T
-                const int io = 16 * (k0 + d);
-#pragma unroll
-                for (int q = 0; q < 16; q++) {
-                    const T xv = q <= r ? Z[io + r][io + q] : T(0);
-#pragma unroll
-                    for (int e = 0; e < 8; e++) out[e] -= xv * Tw[warp][q][8 * h + e];
-                }
-                const int ko = 16 * k0;
-#pragma unroll
-                for (int e = 0; e < 8; e++) Z[io + r][ko + 8 * h + e] = out[e];
-            } else {  // Y_kj = -Y_kk T
-                const int ko = 16 * k0, jo = 16 * (k0 + d);
-#pragma unroll
-                for (int q = 0; q < 16; q++) {
-                    const T yv = q == r ? T(1) : (q > r ? Z[ko + r][ko + q] : T(0));
-#pragma unroll
-                    for (int e = 0; e < 8; e++) out[e] -= yv * Tw[warp][q][8 * h + e];
-                }
-#pragma unroll
-                for (int e = 0; e < 8; e++) Z[ko + r][jo + 8 * h + e] = out[e];
-            }
-        }
-        __syncthreads();
-    }
     T* Zg = slots + t.slot;
     for (int j = warp; j < w; j += 8)
         for (int i = lane; i < w; i += 32) Zg[i + j * 64] = Z[i][j];
