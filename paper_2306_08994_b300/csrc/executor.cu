@@ -33,8 +33,24 @@ struct Launch {
 };
 
 // Solve plan of one class: fronts split by size (see kernels_solve.cuh).
+// Lane-group substitution kernels for small fronts with few pivots: (lanes per front G, rows per
+// lane R, pivot bound KM) of each list, chosen by m (G R >= m) and k (k <= KM).
+constexpr int kLgLists = 12;
+constexpr int kLgG[kLgLists] = {4, 8, 8, 16, 16, 16, 32, 32, 32, 32, 32, 32};
+constexpr int kLgR[kLgLists] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2};
+constexpr int kLgKM[kLgLists] = {4, 4, 8, 4, 8, 16, 4, 8, 16, 4, 8, 16};
+static int lg_list_of(int m, int k) {
+    const int base = m <= 4 ? 0 : m <= 8 ? 1 : m <= 16 ? 3 : m <= 32 ? 6 : m <= 64 ? 9 : -1;
+    if (base < 0) return -1;
+    const int n = base == 0 ? 1 : base == 1 ? 2 : 3;  // pivot bounds of this size group
+    for (int q = base; q < base + n; q++)
+        if (k <= kLgKM[q]) return q;
+    return -1;
+}
 struct ClassList {
     int n_small, n_cta, n_piv, n_all;
+    int n_lg[kLgLists];           // small fronts with few pivots, per lane-group list
+    int64_t off_lg[kLgLists];
     int n_grp[4];                 // fronts with m <= 4, 8, 16, 32 (lane groups of 4, 8, 16, 32)
     int maxm_cta, maxin_inv, maxk_inv, maxnc_inv;
     int64_t off_small, off_cta;   // into the solve front list
@@ -586,18 +602,25 @@ static int build_plan(mf_factors* F) {
         // front with no pivots has nothing to solve.
         auto make_list = [&](bool forward) {
             ClassList C{};
-            std::vector<int32_t> sm, ct, iv, gp[4];
+            std::vector<int32_t> sm, ct, iv, gp[4], lg[kLgLists];
             for (int32_t f : all) {
                 if (solved_by_subtree) break;
                 const FrontDev& fr = a->fronts[f];
                 if (forward ? zvec[f] : fr.k == 0) continue;
-                if (fr.q_off >= 0) iv.push_back(f);
+                const int li = F->use_sweep ? -1 : lg_list_of(fr.m, fr.k);
+                if (li >= 0 && fr.q_off < 0) lg[li].push_back(f);
+                else if (fr.q_off >= 0) iv.push_back(f);
                 else if (fr.m <= 4) gp[0].push_back(f);
                 else if (fr.m <= 8) gp[1].push_back(f);
                 else if (fr.m <= 16) gp[2].push_back(f);
                 else if (fr.m <= 32) gp[3].push_back(f);
                 else if (fr.m <= kSolveWarpMax) sm.push_back(f);
                 else ct.push_back(f);
+            }
+            for (int q = 0; q < kLgLists; q++) {
+                C.n_lg[q] = (int)lg[q].size();
+                C.off_lg[q] = (int64_t)slist.size();
+                slist.insert(slist.end(), lg[q].begin(), lg[q].end());
             }
             for (int q = 0; q < 4; q++) {
                 C.n_grp[q] = (int)gp[q].size();
@@ -1507,6 +1530,7 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
     for (int c = 0; c < c_top; c++) {
         const ClassList& C = F->classes_f[c];
         int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0) + (C.n_grp[0] > 0) + (C.n_grp[1] > 0) + (C.n_grp[2] > 0) + (C.n_grp[3] > 0);
+        for (int q = 0; q < kLgLists; q++) nk += C.n_lg[q] > 0;
         int slot = prof_begin(F, s, FAM_FWD, F->fwd_bytes[c] * nrhs, F->fwd_flops[c] * nrhs, nk, -1, MF_TRACE_FWD_CLASS,
                               c, a->cls_ptr[c + 1] - a->cls_ptr[c]);
 #define GRP_FWD(Q, GS)                                                                                             \
@@ -1519,6 +1543,25 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         GRP_FWD(1, 8)
         GRP_FWD(2, 16)
 #undef GRP_FWD
+#define LG_FWD(Q, GS, RS, KMS)                                                                                      \
+        if (C.n_lg[Q]) {                                                                                           \
+            dim3 g((C.n_lg[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)));                                              \
+            if (!trans) SOLVE_NR(k_fwd_lg, (T, false, GS, RS, KMS), (g, 256, 0, s), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+            else SOLVE_NR(k_fwd_lg, (T, true, GS, RS, KMS), (g, 256, 0, s), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+        }
+        LG_FWD(0, 4, 1, 4)
+        LG_FWD(1, 8, 1, 4)
+        LG_FWD(2, 8, 1, 8)
+        LG_FWD(3, 16, 1, 4)
+        LG_FWD(4, 16, 1, 8)
+        LG_FWD(5, 16, 1, 16)
+        LG_FWD(6, 32, 1, 4)
+        LG_FWD(7, 32, 1, 8)
+        LG_FWD(8, 32, 1, 16)
+        LG_FWD(9, 32, 2, 4)
+        LG_FWD(10, 32, 2, 8)
+        LG_FWD(11, 32, 2, 16)
+#undef LG_FWD
         if (C.n_grp[3]) {  // 16 < m <= 32: the one-front-per-warp kernel is faster forward
             dim3 g((C.n_grp[3] + 7) / 8);
             if (!trans) SOLVE_NR(k_fwd_warp, (T, false), (g, 256, 0, s), (fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
@@ -1557,6 +1600,7 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
     for (int c = c_top - 1; c >= 0; c--) {
         const ClassList& C = F->classes_b[c];
         int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0) + (C.n_grp[0] > 0) + (C.n_grp[1] > 0) + (C.n_grp[2] > 0) + (C.n_grp[3] > 0);
+        for (int q = 0; q < kLgLists; q++) nk += C.n_lg[q] > 0;
         int slot = prof_begin(F, s, FAM_BWD, F->bwd_bytes[c] * nrhs, F->bwd_flops[c] * nrhs, nk, -1, MF_TRACE_BWD_CLASS,
                               c, a->cls_ptr[c + 1] - a->cls_ptr[c]);
 #define GRP_BWD(Q, GS)                                                                                             \
@@ -1570,6 +1614,25 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         GRP_BWD(2, 16)
         GRP_BWD(3, 32)
 #undef GRP_BWD
+#define LG_BWD(Q, GS, RS, KMS)                                                                                      \
+        if (C.n_lg[Q]) {                                                                                           \
+            dim3 g((C.n_lg[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)));                                              \
+            if (!trans) SOLVE_NR(k_bwd_lg, (T, false, GS, RS, KMS), (g, 256, 0, s), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
+            else SOLVE_NR(k_bwd_lg, (T, true, GS, RS, KMS), (g, 256, 0, s), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
+        }
+        LG_BWD(0, 4, 1, 4)
+        LG_BWD(1, 8, 1, 4)
+        LG_BWD(2, 8, 1, 8)
+        LG_BWD(3, 16, 1, 4)
+        LG_BWD(4, 16, 1, 8)
+        LG_BWD(5, 16, 1, 16)
+        LG_BWD(6, 32, 1, 4)
+        LG_BWD(7, 32, 1, 8)
+        LG_BWD(8, 32, 1, 16)
+        LG_BWD(9, 32, 2, 4)
+        LG_BWD(10, 32, 2, 8)
+        LG_BWD(11, 32, 2, 16)
+#undef LG_BWD
         if (C.n_piv) {
             if (!trans) {
                 INV_LAUNCH(false, PH_BWD1, C.n_piv, C.off_piv);

@@ -247,6 +247,165 @@ __global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_bwd_warp(const FrontDe
     k_bwd_warp_body<T, TRANS, NR>(fronts, list, count, fac, dofs, x, n_dof, nrhs, blockIdx.x);
 }
 
+// Small fronts with few pivots (m <= G R, k <= KM): G lanes per front, lane i
+// holding rows i, i + G, ..., i + G (R - 1).  The coefficient arrays are sized
+// by the pivot bound KM rather than by the front, so the kernels stay small
+// enough for full occupancy, and every load a front needs is issued right
+// after its record: the chain is record -> (coefficients, row sources) ->
+// right-hand-side values -> the short pivot loop -> stores.
+//
+// Forward (L y = b restricted to the front, then the update vector): pivot p
+// is broadcast from its owner lane and every row below it subtracts its
+// coefficient times it.
+template <typename T, bool TRANS, int G, int R, int KM, int NR>
+__device__ __forceinline__ void k_fwd_lg_body(const SolveRec* __restrict__ list, int count, const T* __restrict__ fac,
+                                              const int32_t* __restrict__ dofs, const int64_t* __restrict__ vsrc,
+                                              T* __restrict__ vecs, int64_t vec_size, double* __restrict__ x,
+                                              int64_t n_dof, int nrhs, int vb) {
+    static_assert(KM <= G * R, "pivot bound beyond the rows of a group");
+    const int lane = threadIdx.x & 31;
+    const int fidx = (vb * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
+    const bool active = fidx < count;
+    const int i = lane % G;
+    SolveRec fr{};
+    if (active) fr = list[fidx];
+    const int m = fr.m, k = fr.k;
+    const int32_t* fd = dofs + fr.dof_off;
+    const T* P = fac + fr.P_off;
+    const T* Rb = fac + fr.R_off;
+    T c[R][KM], dg[KM];
+    RhsSrc src[R];
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+        const int row = i + G * q;
+#pragma unroll
+        for (int p = 0; p < KM; p++) c[q][p] = (p < k && row > p && row < m) ? fcoef<T, TRANS>(P, Rb, m, k, row, p) : T(0);
+        src[q] = (active && row < m) ? rhs_src<SolveRec>(fr, fd, vsrc, row) : RhsSrc{-1, -1, -1};
+    }
+#pragma unroll
+    for (int p = 0; p < KM; p++) dg[p] = p < k ? fdiag<T, TRANS>(P, m, p) : T(1);
+    const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)k);  // warp-uniform pivot count
+    for (int rb = 0; rb < nrhs; rb += NR) {
+        const int nr = min(NR, nrhs - rb);
+        T w[R][NR];
+#pragma unroll
+        for (int q = 0; q < R; q++)
+#pragma unroll
+            for (int rr = 0; rr < NR; rr++)
+                w[q][rr] = rr < nr ? rhs_val<T>(src[q], vecs + (int64_t)(rb + rr) * vec_size, x + (int64_t)(rb + rr) * n_dof)
+                                   : T(0);
+#pragma unroll
+        for (int p = 0; p < KM; p++) {
+            if (p >= kmax) break;
+            const T ds = pivot_scale<T, NR>(dg[p]);
+#pragma unroll
+            for (int rr = 0; rr < NR; rr++) {
+                const T yp = apply_pivot<T, NR>(__shfl_sync(0xffffffffu, w[p / G][rr], p % G, G), ds);
+                if (p < k) {
+#pragma unroll
+                    for (int q = 0; q < R; q++) {
+                        if (i + G * q == p) w[q][rr] = yp;
+                        w[q][rr] -= c[q][p] * yp;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            const int row = i + G * q;
+            if (!active || row >= m) continue;
+#pragma unroll
+            for (int rr = 0; rr < NR; rr++) {
+                if (rr >= nr) break;
+                if (row < k) x[(int64_t)(rb + rr) * n_dof + src[q].xi] = (double)w[q][rr];
+                else vecs[(int64_t)(rb + rr) * vec_size + fr.vec_off + (row - k)] = w[q][rr];
+            }
+        }
+    }
+}
+template <typename T, bool TRANS, int G, int R, int KM, int NR>
+__global__ void __launch_bounds__(256) k_fwd_lg(const SolveRec* __restrict__ list, int count, const T* __restrict__ fac,
+                                                const int32_t* __restrict__ dofs, const int64_t* __restrict__ vsrc,
+                                                T* __restrict__ vecs, int64_t vec_size, double* __restrict__ x,
+                                                int64_t n_dof, int nrhs) {
+    k_fwd_lg_body<T, TRANS, G, R, KM, NR>(list, count, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, blockIdx.x);
+}
+
+// Backward (U x = y on the front's pivot rows; rows >= k already hold their
+// final values): lane i holds the coefficients of its own rows in every pivot
+// equation, so pivot p needs only the group sum of (coefficient x value) over
+// the rows after it (a butterfly of log2 G shuffles) and no broadcast; pivots
+// go from k-1 down, each one final before the equations above it read it.
+template <typename T, bool TRANS, int G, int R, int KM, int NR>
+__device__ __forceinline__ void k_bwd_lg_body(const SolveRec* __restrict__ list, int count, const T* __restrict__ fac,
+                                              const int32_t* __restrict__ dofs, double* __restrict__ x, int64_t n_dof,
+                                              int nrhs, int vb) {
+    static_assert(KM <= G * R, "pivot bound beyond the rows of a group");
+    const int lane = threadIdx.x & 31;
+    const int fidx = (vb * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
+    const bool active = fidx < count;
+    const int i = lane % G;
+    SolveRec fr{};
+    if (active) fr = list[fidx];
+    const int m = fr.m, k = fr.k;
+    const int32_t* fd = dofs + fr.dof_off;
+    const T* P = fac + fr.P_off;
+    const T* Rb = fac + fr.R_off;
+    T u[R][KM], dg[KM];
+    int di[R];
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+        const int row = i + G * q;
+#pragma unroll
+        for (int p = 0; p < KM; p++) u[q][p] = (p < k && row > p && row < m) ? bcoef<T, TRANS>(P, Rb, m, k, p, row) : T(0);
+        di[q] = (active && row < m) ? fd[row] : 0;
+    }
+#pragma unroll
+    for (int p = 0; p < KM; p++) dg[p] = p < k ? bdiag<T, TRANS>(P, m, p) : T(1);
+    const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)k);
+    for (int rb = 0; rb < nrhs; rb += NR) {
+        const int nr = min(NR, nrhs - rb);
+        T v[R][NR];
+#pragma unroll
+        for (int q = 0; q < R; q++)
+#pragma unroll
+            for (int rr = 0; rr < NR; rr++)
+                v[q][rr] = (rr < nr && active && i + G * q < m) ? (T)__ldcg(x + (int64_t)(rb + rr) * n_dof + di[q]) : T(0);
+#pragma unroll
+        for (int p = KM - 1; p >= 0; p--) {
+            if (p >= kmax) continue;
+            const T ds = pivot_scale<T, NR>(dg[p]);
+#pragma unroll
+            for (int rr = 0; rr < NR; rr++) {
+                T sum = T(0);
+#pragma unroll
+                for (int q = 0; q < R; q++) sum += u[q][p] * v[q][rr];
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, G);
+                if (p < k) {
+#pragma unroll
+                    for (int q = 0; q < R; q++)
+                        if (i + G * q == p) v[q][rr] = apply_pivot<T, NR>(v[q][rr] - sum, ds);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            const int row = i + G * q;
+            if (!active || row >= k) continue;
+#pragma unroll
+            for (int rr = 0; rr < NR; rr++)
+                if (rr < nr) x[(int64_t)(rb + rr) * n_dof + di[q]] = (double)v[q][rr];
+        }
+    }
+}
+template <typename T, bool TRANS, int G, int R, int KM, int NR>
+__global__ void __launch_bounds__(256) k_bwd_lg(const SolveRec* __restrict__ list, int count, const T* __restrict__ fac,
+                                                const int32_t* __restrict__ dofs, double* __restrict__ x, int64_t n_dof,
+                                                int nrhs) {
+    k_bwd_lg_body<T, TRANS, G, R, KM, NR>(list, count, fac, dofs, x, n_dof, nrhs, blockIdx.x);
+}
+
 // Tiny fronts (m <= G, G in {4, 8, 16, 32}): 32/G fronts per warp, one lane
 // per row, shuffles of width G; all coefficients are loaded once, before the
 // short sequential pivot loop.

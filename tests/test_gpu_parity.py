@@ -373,9 +373,11 @@ def test_persistent_sweep_matches_per_class_launches(prec):
             res.append((y.cpu().numpy(), y1.cpu().numpy()))
         outs[sw] = res
     # the 1-RHS kernels divide by the pivot, the 4-RHS ones multiply by its reciprocal: the two
-    # agree to rounding (FP32 fronts: a few units of 1e-7 after amplification by the condition)
+    # agree to rounding (FP32 fronts: a few units of 1e-7 after amplification by the condition);
+    # the per-class path's small fronts (pivot-bounded lane groups, backward by group sums) and the
+    # sweep's bodies also order their sums differently, which shows at the same FP32 level
     tol_rhs = 1e-9 if prec == "f64" else 1e-5
     for (ya, y1a), (yb, y1b) in zip(outs[0], outs[100]):
-        assert np.linalg.norm(ya - yb) <= 1e-9 * np.linalg.norm(ya)
-        assert np.linalg.norm(y1a - y1b) <= 1e-9 * np.linalg.norm(y1a)
+        assert np.linalg.norm(ya - yb) <= tol_rhs * np.linalg.norm(ya)
+        assert np.linalg.norm(y1a - y1b) <= tol_rhs * np.linalg.norm(y1a)
         assert np.linalg.norm(y1b - yb[0]) <= tol_rhs * np.linalg.norm(y1b)
