@@ -291,8 +291,10 @@ int mf_profile_trace(mf_factors* f, mf_trace_rec* out, int cap, int* n);
  *                    fusion of the factorization and of the substitutions,
  *   super_panel      depth of the deferred trailing updates of large fronts,
  *   precision and tc_min_cb  (FP32 family only) SIMT or tensor-core Schur GEMMs.
- * Candidates are timed as one factorization plus one solve (CUDA events on
- * `stream`, CUDA graph replay, median of `reps` after one untimed run).
+ * Candidates are timed as one factorization plus one refined solve
+ * (mf_refine_solve to a normwise backward error of 1e-12, so a plan that
+ * needs more corrections pays for them; CUDA events on `stream`, CUDA graph
+ * replay, median of `reps` after one untimed run).
  * Arguments: a (analysis), d_values (device, element matrices as for
  * mf_factor), d_b (device, n_dof values: the right-hand side of the timed
  * solves; not modified), base (options to start from: its precision family,
@@ -304,8 +306,8 @@ int mf_profile_trace(mf_factors* f, mf_trace_rec* out, int cap, int* n);
  * candidate; returns MF_EINVAL, MF_ENOMEM or MF_ECUDA on failure, in which
  * case `best` is left unchanged.  Synchronises `stream`. */
 typedef struct {
-    double ms_default;   /* factor + solve with `base` (0 when taken from the cache) */
-    double ms_best;      /* factor + solve with `best` */
+    double ms_default;   /* factor + refined solve with `base` (0 when taken from the cache) */
+    double ms_best;      /* factor + refined solve with `best` */
     int candidates;      /* plans timed */
     int from_cache;      /* nonzero if `best` came from cache_path */
 } mf_tune_info;

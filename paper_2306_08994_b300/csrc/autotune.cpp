@@ -31,7 +31,8 @@ struct Timer {
 
 // Version of the launch-plan builder: bumped whenever its kernels or its
 // decomposition change enough that plans tuned before are stale.
-constexpr int kPlanVersion = 6;
+constexpr int kPlanVersion = 7;
+constexpr double kTuneTol = 1e-12;  // refinement target of the timed candidates
 
 int family_of(int precision) { return precision == MF_F64 ? 0 : 1; }
 
@@ -121,8 +122,12 @@ struct Ctx {
     int timed = 0;
 };
 
-// Median time (ms) of factor + one solve under options o; returns an error
-// code for plans that cannot be built or that fail.
+// Median time (ms) of factor + refined solve (FP64 refinement to a normwise
+// backward error of kTuneTol) under options o: the refinement's number of
+// corrections depends on the plan (front precision, where the SIMT / tensor-
+// core and fused / blocked crossovers fall), so it is part of the objective.
+// Returns an error code for plans that cannot be built, fail or do not reach
+// the tolerance.
 int time_plan(Ctx& c, const mf_options& o, double* ms) {
     mf_factors* F = nullptr;
     int rc = mf_factors_create(c.a, &o, &F);
@@ -134,7 +139,8 @@ int time_plan(Ctx& c, const mf_options& o, double* ms) {
         if (cudaMemcpyAsync(c.d_x, c.d_b, bytes, cudaMemcpyDeviceToDevice, c.s) != cudaSuccess) rc = MF_ECUDA;
         if (!rc && cudaEventRecord(t.e0, c.s) != cudaSuccess) rc = MF_ECUDA;
         if (!rc) rc = mf_factor(F, c.d_values, c.s);
-        if (!rc) rc = mf_solve(F, c.d_x, 1, c.s);
+        mf_refine_info ri{};
+        if (!rc) rc = mf_refine_solve(F, c.d_values, c.d_b, c.d_x, 1, kTuneTol, 30, &ri, c.s);
         if (!rc && cudaEventRecord(t.e1, c.s) != cudaSuccess) rc = MF_ECUDA;
         if (!rc && cudaEventSynchronize(t.e1) != cudaSuccess) rc = MF_ECUDA;
         float e = 0.f;
@@ -306,6 +312,25 @@ extern "C" int mf_autotune(const mf_analysis* a, const double* d_values, const d
             u.precision = MF_TF32;
             u.tc_min_cb = tmin;
             try_one(u);
+        }
+    }
+    if (!rc && family_of(o.precision) == 1) {
+        // the super-panel depth and the tensor-core crossover interact (the deep trailing products
+        // of a super-panel are tensor-core candidates): a joint pass over both
+        const mf_options start = cur;
+        for (int sp : {64, 128, 256, 512})
+            for (int tmin : {0, 128, 256, 512}) {  // 0: SIMT products only (MF_F32)
+                if (rc) break;
+                mf_options t = start;
+                t.super_panel = sp;
+                t.precision = tmin ? MF_TF32 : MF_F32;
+                t.tc_min_cb = tmin;
+                if (sp != start.super_panel || t.precision != start.precision || tmin != start.tc_min_cb) try_one(t);
+            }
+        if (!rc) {
+            mf_options t = cur;
+            t.lookahead = cur.lookahead >= 0 ? -1 : 0;
+            try_one(t);
         }
     }
     cudaFree(d_x);
