@@ -73,6 +73,11 @@ CPU_SAMPLE = {
     "poisson2d_q1_16": ("poisson2d_q1_16", lambda: [F.poisson_2d_q1(16)]),
 }
 FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
+# DRAM bytes (read + write) per launch of a dominant kernel, from one ncu capture of that workload
+# (dram__bytes_read.sum + dram__bytes_write.sum over all its launches / launches); the key names the
+# workload, the requested front precision (the tuned plan of the committed cache) and the trace
+# kind.  Valid while the kernel is unchanged.
+MEASURED_TRAFFIC = {("diffusion2d_q3_512", "f32", "gemm"): 19.73e6}
 FP64_DFMA_TFLOPS = 1.201  # measured DFMA throughput of this B300 (register-resident FMA loop, all SMs)
 
 
@@ -410,7 +415,9 @@ def main():
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "peak_src": peaks["src"]}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    # DRAM traffic per launch of the dominant kernel from an ncu capture of this workload
+    # (profiles/k_gemm_cp_diffusion2d_q3_512.md); null for kernels or workloads not captured
+    roof["traffic"] = MEASURED_TRAFFIC.get((args.workload, precision, dom))
     roof["kernel"] = dom
     roof["launches_per_step"] = d["launches"] / args.steps
     roof["per_launch_ms"] = per_launch_ms
