@@ -1173,6 +1173,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&F->num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (F->num_sms <= 0) F->num_sms = 148;
+        F->norm_blocks = 8 * F->num_sms;  // norm reduction: 64 warps per SM
     }
     F->sp = F->opt.super_panel > 0 ? F->opt.super_panel : (F->prec == MF_F64 ? F->nb : 256);
     F->sp = std::max(F->nb, (F->sp + F->nb - 1) / F->nb * F->nb);

@@ -1044,10 +1044,15 @@ __global__ void __launch_bounds__(256) k_elem_apply_grp(const double* __restrict
     const double* xr = x + (int64_t)r * n_dof;
     const double xa = act ? xr[en[e * npe + a]] : 0.0;
     const double* K = values + (act ? e : 0) * npe * npe + a;
+    // all npe loads of the lane's matrix row issued before the products (npe <= G)
+    double kv[G];
+#pragma unroll
+    for (int b = 0; b < G; b++) kv[b] = (act && b < npe) ? K[b * npe] : 0.0;
     double acc = 0.0;
-    for (int b = 0; b < npe; b++) {
+#pragma unroll
+    for (int b = 0; b < G; b++) {
         const double xb = __shfl_sync(0xffffffffu, xa, b, G);
-        if (act) acc = fma(K[b * npe], xb, acc);
+        if (b < npe) acc = fma(kv[b], xb, acc);
     }
     if (act) Y[e * npe + a + (int64_t)r * n_elem * npe] = acc;
 }
@@ -1077,15 +1082,37 @@ __global__ void k_norms_partial(const double* __restrict__ rv, const double* __r
     const double* xx = xv + (int64_t)r * n;
     const double* bb = bv + (int64_t)r * n;
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double ri = rr[i], xi = xx[i], bi = bb[i];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    auto take = [&](int64_t i) {
+        const double ri = rr[i], xi = xx[i], bi = bb[i];
         a0 = nanmax(a0, fabs(ri));
         a1 = nanmax(a1, fabs(xi));
         a2 = nanmax(a2, fabs(bi));
         a3 += ri * ri;
         a4 += bi * bi;
         if (rowabs) a5 = nanmax(a5, rowabs[i]);
+    };
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {  // four elements' loads in flight per thread
+        double rq[4], xq[4], bq[4], aq[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            rq[u] = rr[i + u * stride];
+            xq[u] = xx[i + u * stride];
+            bq[u] = bb[i + u * stride];
+            aq[u] = rowabs ? rowabs[i + u * stride] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            a0 = nanmax(a0, fabs(rq[u]));
+            a1 = nanmax(a1, fabs(xq[u]));
+            a2 = nanmax(a2, fabs(bq[u]));
+            a3 += rq[u] * rq[u];
+            a4 += bq[u] * bq[u];
+            a5 = nanmax(a5, aq[u]);
+        }
     }
+    for (; i < n; i += stride) take(i);
     __shared__ double sh[6][32];
     for (int o = 16; o > 0; o >>= 1) {
         a0 = nanmax(a0, __shfl_xor_sync(0xffffffffu, a0, o));
