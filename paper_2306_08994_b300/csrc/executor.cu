@@ -35,12 +35,12 @@ struct Launch {
 // Solve plan of one class: fronts split by size (see kernels_solve.cuh).
 // Lane-group substitution kernels for small fronts with few pivots: (lanes per front G, rows per
 // lane R, pivot bound KM) of each list, chosen by m (G R >= m) and k (k <= KM).
-constexpr int kLgLists = 12;
-constexpr int kLgG[kLgLists] = {4, 8, 8, 16, 16, 16, 32, 32, 32, 32, 32, 32};
-constexpr int kLgR[kLgLists] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2};
-constexpr int kLgKM[kLgLists] = {4, 4, 8, 4, 8, 16, 4, 8, 16, 4, 8, 16};
+constexpr int kLgLists = 15;
+constexpr int kLgG[kLgLists] = {4, 8, 8, 16, 16, 16, 32, 32, 32, 32, 32, 32, 32, 32, 32};
+constexpr int kLgR[kLgLists] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 3, 3, 3};
+constexpr int kLgKM[kLgLists] = {4, 4, 8, 4, 8, 16, 4, 8, 16, 4, 8, 16, 4, 8, 16};
 static int lg_list_of(int m, int k) {
-    const int base = m <= 4 ? 0 : m <= 8 ? 1 : m <= 16 ? 3 : m <= 32 ? 6 : m <= 64 ? 9 : -1;
+    const int base = m <= 4 ? 0 : m <= 8 ? 1 : m <= 16 ? 3 : m <= 32 ? 6 : m <= 64 ? 9 : m <= 96 ? 12 : -1;
     if (base < 0) return -1;
     const int n = base == 0 ? 1 : base == 1 ? 2 : 3;  // pivot bounds of this size group
     for (int q = base; q < base + n; q++)
@@ -1562,6 +1562,9 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         LG_FWD(9, 32, 2, 4)
         LG_FWD(10, 32, 2, 8)
         LG_FWD(11, 32, 2, 16)
+        LG_FWD(12, 32, 3, 4)
+        LG_FWD(13, 32, 3, 8)
+        LG_FWD(14, 32, 3, 16)
 #undef LG_FWD
         if (C.n_grp[3]) {  // 16 < m <= 32: the one-front-per-warp kernel is faster forward
             dim3 g((C.n_grp[3] + 7) / 8);
@@ -1633,6 +1636,9 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         LG_BWD(9, 32, 2, 4)
         LG_BWD(10, 32, 2, 8)
         LG_BWD(11, 32, 2, 16)
+        LG_BWD(12, 32, 3, 4)
+        LG_BWD(13, 32, 3, 8)
+        LG_BWD(14, 32, 3, 16)
 #undef LG_BWD
         if (C.n_piv) {
             if (!trans) {
