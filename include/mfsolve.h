@@ -195,6 +195,15 @@ int mf_solve_adjoint(mf_factors* f, double* d_rhs, int nrhs, mf_stream_t stream)
 int mf_refine_solve(mf_factors* f, const double* d_values, const double* d_b, double* d_x, int nrhs,
                     double tol, int maxit, mf_refine_info* info, mf_stream_t stream);
 
+/* The same refinement for the adjoint system A^T x = b (the adjoint solve of
+ * the gradient, Sec. 4): x = solve_adjoint(b); repeat r = b - A^T x (FP64,
+ * element by element with the transposed element matrices), x +=
+ * solve_adjoint(r) until ||r||_inf / (||A^T||_inf ||x||_inf + ||b||_inf) <=
+ * tol or maxit corrections.  Arguments, layout and return codes as
+ * mf_refine_solve. */
+int mf_refine_solve_adjoint(mf_factors* f, const double* d_values, const double* d_b, double* d_x, int nrhs,
+                            double tol, int maxit, mf_refine_info* info, mf_stream_t stream);
+
 /* r = b - A x in FP64 with A given element by element. */
 int mf_residual(const mf_factors* f, const double* d_values, const double* d_x, const double* d_b,
                 double* d_r, int nrhs, mf_stream_t stream);

@@ -269,6 +269,9 @@ struct mf_factors {
     unsigned int* d_famax = nullptr;
     DevStatus* d_status = nullptr;
     double *d_r = nullptr, *d_d = nullptr, *d_Y = nullptr, *d_rowabs = nullptr, *d_part = nullptr, *d_norms = nullptr;
+    double* d_colabs = nullptr;  // column sums of |A| (||A^T||_inf of the adjoint refinement)
+    bool colabs_valid = false;
+    const double* colabs_values = nullptr;
     int norm_blocks = 296;
     bool rowabs_valid = false;
     const double* rowabs_values = nullptr;
@@ -361,7 +364,7 @@ static void free_factors(mf_factors* f) {
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_vsrc, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
                     f->d_vec, f->d_flist, f->d_frec, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
-                    f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms};
+                    f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms, f->d_colabs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete f;
@@ -1233,6 +1236,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     TRY(dev_alloc(&F->d_d, nv));
     TRY(dev_alloc(&F->d_Y, (size_t)a->n_elem * a->npe * F->max_nrhs));
     TRY(dev_alloc(&F->d_rowabs, (size_t)a->n_dof));
+    TRY(dev_alloc(&F->d_colabs, (size_t)a->n_dof));
     TRY(dev_alloc(&F->d_part, (size_t)F->norm_blocks * 6 * F->max_nrhs));
     TRY(dev_alloc(&F->d_norms, (size_t)6 * F->max_nrhs));
     TRY(build_plan(F));
@@ -1415,6 +1419,7 @@ extern "C" int mf_factor(mf_factors* F, const double* d_values, mf_stream_t stre
     if (rc == MF_OK) {
         F->factored = true;
         F->rowabs_valid = false;
+        F->colabs_valid = false;
     }
     return rc;
 }
@@ -1699,7 +1704,7 @@ extern "C" int mf_solve_adjoint(mf_factors* F, double* d_rhs, int nrhs, mf_strea
 }
 
 static int residual_into(const mf_factors* Fc, const double* d_values, const double* d_x, const double* d_b, double* d_r,
-                         int nrhs, cudaStream_t s) {
+                         int nrhs, cudaStream_t s, bool trans = false) {
     mf_factors* F = const_cast<mf_factors*>(Fc);
     const mf_analysis* a = F->a;
     const int64_t nE = a->n_elem * a->npe;
@@ -1708,13 +1713,17 @@ static int residual_into(const mf_factors* Fc, const double* d_values, const dou
     if (G) {
         const int64_t nthreads = a->n_elem * G;
         dim3 g1((unsigned)((nthreads + 255) / 256), nrhs);
-        if (G == 4) k_elem_apply_grp<4><<<g1, 256, 0, s>>>(d_values, F->d_en, d_x, F->d_Y, a->n_elem, a->npe, a->n_dof);
-        else if (G == 8) k_elem_apply_grp<8><<<g1, 256, 0, s>>>(d_values, F->d_en, d_x, F->d_Y, a->n_elem, a->npe, a->n_dof);
-        else if (G == 16) k_elem_apply_grp<16><<<g1, 256, 0, s>>>(d_values, F->d_en, d_x, F->d_Y, a->n_elem, a->npe, a->n_dof);
-        else k_elem_apply_grp<32><<<g1, 256, 0, s>>>(d_values, F->d_en, d_x, F->d_Y, a->n_elem, a->npe, a->n_dof);
+#define ELEM_APPLY(GS)                                                                                        \
+    if (trans) k_elem_apply_grp<GS, true><<<g1, 256, 0, s>>>(d_values, F->d_en, d_x, F->d_Y, a->n_elem, a->npe, a->n_dof); \
+    else k_elem_apply_grp<GS, false><<<g1, 256, 0, s>>>(d_values, F->d_en, d_x, F->d_Y, a->n_elem, a->npe, a->n_dof);
+        if (G == 4) { ELEM_APPLY(4) }
+        else if (G == 8) { ELEM_APPLY(8) }
+        else if (G == 16) { ELEM_APPLY(16) }
+        else { ELEM_APPLY(32) }
+#undef ELEM_APPLY
     } else {
         dim3 g1((unsigned)((nE + 255) / 256), nrhs);
-        k_elem_apply<<<g1, 256, 0, s>>>(d_values, F->d_en, d_x, F->d_Y, a->n_elem, a->npe, a->n_dof, 0);
+        k_elem_apply<<<g1, 256, 0, s>>>(d_values, F->d_en, d_x, F->d_Y, a->n_elem, a->npe, a->n_dof, 0, trans ? 1 : 0);
     }
     CUDA_TRY(cudaGetLastError());
     dim3 g2((unsigned)((a->n_dof + 255) / 256), nrhs);
@@ -1730,37 +1739,50 @@ extern "C" int mf_residual(const mf_factors* F, const double* d_values, const do
     return residual_into(F, d_values, d_x, d_b, d_r, nrhs, (cudaStream_t)stream);
 }
 
-static int compute_rowabs(mf_factors* F, const double* d_values, cudaStream_t s) {
+// row sums of |A| (trans: column sums, the row sums of |A^T|), element by element
+static int compute_rowabs(mf_factors* F, const double* d_values, cudaStream_t s, bool trans = false) {
     const mf_analysis* a = F->a;
     const int64_t nE = a->n_elem * a->npe;
     dim3 g1((unsigned)((nE + 255) / 256), 1);
-    k_elem_apply<<<g1, 256, 0, s>>>(d_values, F->d_en, nullptr, F->d_Y, a->n_elem, a->npe, a->n_dof, 1);
+    k_elem_apply<<<g1, 256, 0, s>>>(d_values, F->d_en, nullptr, F->d_Y, a->n_elem, a->npe, a->n_dof, 1, trans ? 1 : 0);
     CUDA_TRY(cudaGetLastError());
     dim3 g2((unsigned)((a->n_dof + 255) / 256), 1);
-    k_gather_residual<<<g2, 256, 0, s>>>(F->d_node_ptr, F->d_node_inc, F->d_Y, nullptr, F->d_rowabs, a->n_dof, nE, 1);
+    k_gather_residual<<<g2, 256, 0, s>>>(F->d_node_ptr, F->d_node_inc, F->d_Y, nullptr, trans ? F->d_colabs : F->d_rowabs,
+                                         a->n_dof, nE, 1);
     CUDA_TRY(cudaGetLastError());
+    if (trans) {
+        F->colabs_valid = true;
+        F->colabs_values = d_values;
+        return MF_OK;
+    }
     F->rowabs_valid = true;
     F->rowabs_values = d_values;
     return MF_OK;
 }
 
-extern "C" int mf_refine_solve(mf_factors* F, const double* d_values, const double* d_b, double* d_x, int nrhs, double tol,
-                               int maxit, mf_refine_info* info, mf_stream_t stream) {
+// Refinement of A x = b (trans: A^T x = b with the same factors, the adjoint solve and an
+// element-by-element residual with the transposed element matrices).
+static int refine_impl(mf_factors* F, const double* d_values, const double* d_b, double* d_x, int nrhs, double tol,
+                       int maxit, mf_refine_info* info, mf_stream_t stream, bool trans) {
     if (!F || !d_values || !d_b || !d_x || nrhs < 1 || nrhs > F->max_nrhs || maxit < 0) return MF_EINVAL;
     if (!F->factored) return MF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const mf_analysis* a = F->a;
     const int64_t n = a->n_dof;
     int rc;
-    if (!F->rowabs_valid || F->rowabs_values != d_values)
+    if (!trans && (!F->rowabs_valid || F->rowabs_values != d_values))
         if ((rc = compute_rowabs(F, d_values, s))) return rc;
+    if (trans && (!F->colabs_valid || F->colabs_values != d_values))
+        if ((rc = compute_rowabs(F, d_values, s, true))) return rc;
+    const double* anorm_rows = trans ? F->d_colabs : F->d_rowabs;
+    const int kind0 = trans ? 5 : 1;  // graph kinds of the first solve and of one correction
     // the residual and its norms after the current x (device only)
     auto residual_norms = [&](cudaStream_t st) -> int {
         int r2;
-        if ((r2 = residual_into(F, d_values, d_x, d_b, F->d_r, nrhs, st))) return r2;
+        if ((r2 = residual_into(F, d_values, d_x, d_b, F->d_r, nrhs, st, trans))) return r2;
         dim3 gp(F->norm_blocks, nrhs);
         int sl = prof_begin(F, st, FAM_RESID, 24.0 * n * nrhs, 5.0 * n * nrhs, 2);
-        k_norms_partial<<<gp, 256, 0, st>>>(F->d_r, d_x, d_b, F->d_rowabs, n, F->d_part);
+        k_norms_partial<<<gp, 256, 0, st>>>(F->d_r, d_x, d_b, anorm_rows, n, F->d_part);
         k_norms_final<<<nrhs, 32, 0, st>>>(F->d_part, F->norm_blocks, F->d_norms);
         prof_end(F, st, sl);
         CUDA_TRY(cudaGetLastError());
@@ -1772,7 +1794,7 @@ extern "C" int mf_refine_solve(mf_factors* F, const double* d_values, const doub
         CUDA_TRY(cudaMemcpyAsync(d_x, d_b, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, st));
         prof_end(F, st, sl);
         int r2;
-        if ((r2 = solve_common(F, d_x, nrhs, false, (mf_stream_t)st))) return r2;
+        if ((r2 = solve_common(F, d_x, nrhs, trans, (mf_stream_t)st))) return r2;
         return residual_norms(st);
     };
     // one correction: d = A^-1 r, x += d, then residual
@@ -1781,7 +1803,7 @@ extern "C" int mf_refine_solve(mf_factors* F, const double* d_values, const doub
         CUDA_TRY(cudaMemcpyAsync(F->d_d, F->d_r, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, st));
         prof_end(F, st, sl);
         int r2;
-        if ((r2 = solve_common(F, F->d_d, nrhs, false, (mf_stream_t)st))) return r2;
+        if ((r2 = solve_common(F, F->d_d, nrhs, trans, (mf_stream_t)st))) return r2;
         sl = prof_begin(F, st, FAM_OTHER, 24.0 * n * nrhs, 1.0 * n * nrhs);
         k_axpy<<<(unsigned)((n * nrhs + 255) / 256), 256, 0, st>>>(d_x, F->d_d, n * nrhs);
         prof_end(F, st, sl);
@@ -1791,7 +1813,7 @@ extern "C" int mf_refine_solve(mf_factors* F, const double* d_values, const doub
     std::vector<double> h(6 * nrhs);
     int it = 0;
     double eta = 0, rel = 0;
-    if ((rc = run_graph(F, 1, d_values, d_b, d_x, nrhs, s, start))) return rc;
+    if ((rc = run_graph(F, kind0, d_values, d_b, d_x, nrhs, s, start))) return rc;
     for (;;) {
         CUDA_TRY(cudaMemcpyAsync(h.data(), F->d_norms, sizeof(double) * 6 * nrhs, cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
@@ -1806,7 +1828,7 @@ extern "C" int mf_refine_solve(mf_factors* F, const double* d_values, const doub
             rel = std::max(rel, q[4] > 0 ? std::sqrt(q[3] / q[4]) : std::sqrt(q[3]));
         }
         if (eta <= tol || it >= maxit || !std::isfinite(eta)) break;
-        if ((rc = run_graph(F, 2, d_values, d_b, d_x, nrhs, s, step))) return rc;
+        if ((rc = run_graph(F, kind0 + 1, d_values, d_b, d_x, nrhs, s, step))) return rc;
         it++;
     }
     if (info) {
@@ -1815,6 +1837,16 @@ extern "C" int mf_refine_solve(mf_factors* F, const double* d_values, const doub
         info->rel_residual = rel;
     }
     return eta <= tol ? MF_OK : MF_ENOCONV;
+}
+
+extern "C" int mf_refine_solve(mf_factors* F, const double* d_values, const double* d_b, double* d_x, int nrhs, double tol,
+                               int maxit, mf_refine_info* info, mf_stream_t stream) {
+    return refine_impl(F, d_values, d_b, d_x, nrhs, tol, maxit, info, stream, false);
+}
+
+extern "C" int mf_refine_solve_adjoint(mf_factors* F, const double* d_values, const double* d_b, double* d_x, int nrhs,
+                                       double tol, int maxit, mf_refine_info* info, mf_stream_t stream) {
+    return refine_impl(F, d_values, d_b, d_x, nrhs, tol, maxit, info, stream, true);
 }
 
 extern "C" int mf_element_grad(const mf_factors* F, const double* d_dvalues, const double* d_lambda, const double* d_x,

@@ -1010,29 +1010,31 @@ __global__ void __launch_bounds__(256) k_solve_sweep(SweepArgs<T> a) {
 //   Y[e*npe + a] = sum_b K_e[a,b] x[node(e,b)]          (k_elem_apply)
 //   r[d] = b[d] - sum over the (e,a) touching d of Y    (k_gather_residual)
 // absmode: |K_e| and x = 1, giving the element-wise bound of ||A||_inf rows.
+// trans: the element matrices enter transposed (K_e^T x_e; absmode: column sums), for A^T x.
 __global__ void k_elem_apply(const double* __restrict__ values, const int64_t* __restrict__ en, const double* __restrict__ x,
-                             double* __restrict__ Y, int64_t n_elem, int npe, int64_t n_dof, int absmode) {
+                             double* __restrict__ Y, int64_t n_elem, int npe, int64_t n_dof, int absmode, int trans) {
     const int64_t nE = n_elem * npe;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
     if (idx >= nE) return;
     const int64_t e = idx / npe;
     const int a = (int)(idx - e * npe);
-    const double* K = values + e * npe * npe + a;
+    const double* K = values + e * npe * npe + (trans ? (int64_t)a * npe : a);
+    const int ks = trans ? 1 : npe;  // stride between the entries of the lane's row of K_e (or of K_e^T)
     const int64_t* nd = en + e * npe;
     const double* xr = x + (int64_t)r * n_dof;
     double acc = 0.0;
     if (absmode) {
-        for (int b = 0; b < npe; b++) acc += fabs(K[b * npe]);
+        for (int b = 0; b < npe; b++) acc += fabs(K[b * ks]);
     } else {
-        for (int b = 0; b < npe; b++) acc = fma(K[b * npe], xr[nd[b]], acc);
+        for (int b = 0; b < npe; b++) acc = fma(K[b * ks], xr[nd[b]], acc);
     }
     Y[idx + (int64_t)r * nE] = acc;
 }
 
 // Same product with one lane group of G >= npe lanes per element: each lane
 // loads its node's x once and the group shares them by shuffles.
-template <int G>
+template <int G, bool TR>
 __global__ void __launch_bounds__(256) k_elem_apply_grp(const double* __restrict__ values, const int64_t* __restrict__ en,
                                                         const double* __restrict__ x, double* __restrict__ Y, int64_t n_elem,
                                                         int npe, int64_t n_dof) {
@@ -1043,11 +1045,11 @@ __global__ void __launch_bounds__(256) k_elem_apply_grp(const double* __restrict
     const bool act = e < n_elem && a < npe;
     const double* xr = x + (int64_t)r * n_dof;
     const double xa = act ? xr[en[e * npe + a]] : 0.0;
-    const double* K = values + (act ? e : 0) * npe * npe + a;
-    // all npe loads of the lane's matrix row issued before the products (npe <= G)
+    const double* K = values + (act ? e : 0) * npe * npe + (TR ? a * npe : a);
+    // all npe loads of the lane's row of K_e (TR: of K_e^T) issued before the products (npe <= G)
     double kv[G];
 #pragma unroll
-    for (int b = 0; b < G; b++) kv[b] = (act && b < npe) ? K[b * npe] : 0.0;
+    for (int b = 0; b < G; b++) kv[b] = (act && b < npe) ? K[TR ? b : b * npe] : 0.0;
     double acc = 0.0;
 #pragma unroll
     for (int b = 0; b < G; b++) {

@@ -84,7 +84,8 @@ class mf_tune_info(ctypes.Structure):
 # every symbol include/mfsolve.h declares
 EXPORTS = ["mf_default_options", "mf_strerror", "mf_analyze_mesh", "mf_analyze_batch", "mf_analysis_info",
            "mf_analysis_export", "mf_factors_create", "mf_factor", "mf_solve", "mf_solve_adjoint", "mf_refine_solve",
-           "mf_residual", "mf_element_grad", "mf_element_outer", "mf_status", "mf_factors_export_front",
+           "mf_refine_solve_adjoint", "mf_residual", "mf_element_grad", "mf_element_outer", "mf_status",
+           "mf_factors_export_front",
            "mf_free_factors", "mf_free_analysis", "mf_profile_enable", "mf_profile_read", "mf_residual_noalloc",
            "mf_autotune", "mf_profile_trace"]
 PROFILE_FAMILIES = ["fused", "assemble", "panel", "trailing_gemm", "schur_gemm", "forward", "backward", "residual",
@@ -109,6 +110,7 @@ def _load():
         "mf_factors_create": ([P, P, P], I), "mf_factor": ([P, P, P], I),
         "mf_solve": ([P, P, I, P], I), "mf_solve_adjoint": ([P, P, I, P], I),
         "mf_refine_solve": ([P, P, P, P, I, D, I, P, P], I), "mf_residual": ([P, P, P, P, P, I, P], I),
+        "mf_refine_solve_adjoint": ([P, P, P, P, I, D, I, P, P], I),
         "mf_element_grad": ([P, P, P, P, P, P], I), "mf_element_outer": ([P, P, P, I, P, P], I),
         "mf_status": ([P, P], I), "mf_factors_export_front": ([P, ctypes.c_int32, P, P], I),
         "mf_free_factors": ([P], None), "mf_free_analysis": ([P], None),
@@ -242,6 +244,11 @@ class Factors:
         self._h = h
         self.n_dof = analysis.n_dof
 
+    @property
+    def precision(self) -> str:
+        """Front arithmetic of these factors: "f64", "f32" or "tf32"."""
+        return {v: k for k, v in PRECISIONS.items()}[self.options.precision]
+
     def factor(self, values, stream=None):
         _check(_lib.mf_factor(self._h, _dptr(values), _stream(stream)), "mf_factor")
 
@@ -253,13 +260,15 @@ class Factors:
         _check(f(self._h, _dptr(rhs), nrhs, _stream(stream)), "mf_solve_adjoint" if adjoint else "mf_solve")
         return rhs
 
-    def refine_solve(self, values, b, x, tol: float = 1e-14, maxit: int = 10, stream=None, check: bool = True):
+    def refine_solve(self, values, b, x, tol: float = 1e-14, maxit: int = 10, stream=None, check: bool = True,
+                     adjoint: bool = False):
         nrhs = 1 if b.dim() == 1 else int(b.shape[0])
         info = mf_refine_info()
-        rc = _lib.mf_refine_solve(self._h, _dptr(values), _dptr(b), _dptr(x), nrhs, float(tol), int(maxit),
-                                  ctypes.byref(info), _stream(stream))
+        fn = _lib.mf_refine_solve_adjoint if adjoint else _lib.mf_refine_solve
+        rc = fn(self._h, _dptr(values), _dptr(b), _dptr(x), nrhs, float(tol), int(maxit), ctypes.byref(info),
+                _stream(stream))
         if check and rc not in (MF_OK, MF_ENOCONV):
-            _check(rc, "mf_refine_solve")
+            _check(rc, "mf_refine_solve_adjoint" if adjoint else "mf_refine_solve")
         return {"rc": rc, "iterations": info.iterations, "backward_error": info.backward_error,
                 "rel_residual": info.rel_residual}
 

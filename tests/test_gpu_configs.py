@@ -160,3 +160,35 @@ def test_adjoint_gradient_1024_vs_finite_differences_and_oracle():
     go = O.element_grad(pm.elem_nodes, F.to_colmajor(dK), lo, xo)
     assert np.linalg.norm(xh - xo) <= 1e-10 * np.linalg.norm(xo)
     assert np.linalg.norm(g - go) <= 1e-9 * np.linalg.norm(go)
+
+
+@pytest.mark.parametrize("prec", ["f32", "tf32"])
+def test_adjoint_gradient_fp32_fronts_refined(prec):
+    """The adjoint workload's FP32-family path: FP32 / 3xTF32 fronts, the forward and the
+    adjoint solve each refined in FP64 to eta <= 1e-12, then dJ/dtheta: the oracle's FP64
+    gradient to 1e-9 (256^2 Q1, 66k dofs)."""
+    pr = F.adjoint_problem(256, n_fd=8)
+    pm = pr.mesh
+    a = M.Analysis(M.Mesh(pm.elem_nodes, pm.n_nodes, pm.dim, grid_dims=pm.nel), M.default_options(precision=prec))
+    f = M.Factors(a)
+    vals = torch.tensor(F.to_colmajor(pr.Ke), device=DEV)
+    dKt = torch.tensor(F.to_colmajor(pr.extra["dK"]), device=DEV)
+    ut = torch.tensor(pr.extra["u_target"], device=DEV)
+    f.factor(vals)
+    b = torch.tensor(pr.b[:, 0], device=DEV)
+    x = torch.empty_like(b)
+    i1 = f.refine_solve(vals, b, x, tol=1e-12, maxit=40)
+    gv = (x - ut).contiguous()
+    lam = torch.empty_like(b)
+    i2 = f.refine_solve(vals, gv, lam, tol=1e-12, maxit=40, adjoint=True)
+    assert i1["backward_error"] <= 1e-12 and i2["backward_error"] <= 1e-12, (i1, i2)
+    assert i1["iterations"] >= 1 and i2["iterations"] >= 1  # FP32 fronts alone do not reach the bar
+    g = torch.empty(pm.n_elem, dtype=torch.float64, device=DEV)
+    f.element_grad(dKt, lam, x, g)
+    s = O.OracleSolver(pm.n_nodes, pm.elem_nodes, O.tree_bisection(pm.nel))
+    assert s.factor(F.to_colmajor(pr.Ke), nthreads=O.max_threads()) == 0
+    xo = s.solve(pr.b[:, 0])
+    lo = s.solve(xo - pr.extra["u_target"], adjoint=True)
+    go = O.element_grad(pm.elem_nodes, F.to_colmajor(pr.extra["dK"]), lo, xo)
+    gh = g.cpu().numpy()
+    assert np.linalg.norm(gh - go) <= 1e-9 * np.linalg.norm(go)

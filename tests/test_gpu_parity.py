@@ -208,6 +208,36 @@ def test_adjoint_solve_on_unsymmetric_matrix():
     assert np.linalg.norm(lo - xo) > 1e-3 * np.linalg.norm(xo)  # really unsymmetric
 
 
+@pytest.mark.parametrize("prec", ["f32", "tf32"])
+def test_adjoint_refinement_unsymmetric(prec):
+    """mf_refine_solve_adjoint: FP32-family factors of an unsymmetric (convection) matrix and
+    the adjoint system A^T x = g refined in FP64 (residual with the transposed element
+    matrices): the oracle's adjoint solution to 1e-10, and the backward error of A^T
+    recomputed on the host from the assembled matrix <= 1e-12."""
+    import scipy.sparse as sp
+    pr = F.convection_2d_q1(9)
+    a, f, vals = _setup(pr, prec, small_front_max=8)
+    f.factor(vals)
+    s = _oracle(pr)
+    g = np.ascontiguousarray(pr.b[:, 0])
+    lo = s.solve(g, adjoint=True)
+    gt = torch.tensor(g, device=DEV)
+    lam = torch.empty_like(gt)
+    info = f.refine_solve(vals, gt, lam, tol=1e-15, maxit=40, adjoint=True)
+    assert info["backward_error"] <= 1e-12, info
+    lh = lam.cpu().numpy()
+    assert np.linalg.norm(lh - lo) <= 1e-10 * np.linalg.norm(lo)
+    rp, cp, vp = F.assemble_csr(pr.mesh, pr.Ke)
+    A = sp.csr_matrix((vp, cp, rp))
+    r = g - A.T @ lh
+    eta = np.abs(r).max() / (abs(A.T).sum(axis=1).max() * np.abs(lh).max() + np.abs(g).max())
+    assert eta <= 1e-12, eta
+    # the forward refinement on the same factors solves the other system
+    x = torch.empty_like(gt)
+    f.refine_solve(vals, gt, x, tol=1e-15, maxit=40)
+    assert np.linalg.norm(x.cpu().numpy() - lh) > 1e-3 * np.linalg.norm(lh)
+
+
 def test_element_gradient_matches_oracle_and_autograd():
     pr = F.adjoint_problem(n=24, n_fd=8)
     a, f, vals = _setup(pr, "f64")
