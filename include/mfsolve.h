@@ -96,10 +96,10 @@ typedef struct {
                              256; 0 = default (128 up to m = 64, 256 above).  Fronts with m <= 32
                              run in the lane-group kernel instead (one group of 4, 8, 16 or 32
                              lanes per front), so the first two entries are not used. */
-    int lookahead;        /* one-panel lookahead in the large-front partial LU when the super-panel
-                             depth equals the panel width: the next pivot block takes its share of
-                             the trailing update and is factored on a second stream while the rest
-                             of the update runs; 0 = on (default), < 0 = off */
+    int lookahead;        /* one-panel lookahead in the large-front partial LU: the next pivot block
+                             takes its share of the pending update (every pivot of its super-panel
+                             so far) and is factored on a second stream while the rest of the update
+                             runs; 0 = on (default), < 0 = off */
 } mf_options;
 
 typedef struct {

@@ -295,7 +295,7 @@ extern "C" int mf_autotune(const mf_analysis* a, const double* d_values, const d
             if (sp != start.super_panel) try_one(t);
         }
     }
-    if (!rc) {  // one-panel lookahead (only acts when the super-panel depth is the panel width)
+    if (!rc) {  // one-panel lookahead on / off
         mf_options t = cur;
         t.lookahead = cur.lookahead >= 0 ? -1 : 0;
         try_one(t);

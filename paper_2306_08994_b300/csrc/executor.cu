@@ -781,10 +781,12 @@ static int build_plan(mf_factors* F) {
             if (use_tc(M, N, K)) tc_add(AR_FAC, ao, lda, AR_FAC, bo, ldb, car, co, ldc, M, N, K);
             else gemm_tiles(ao, lda, bo, ldb, co, ldc, M, N, K, car == AR_CB);
         };
+        bool la_pending = false;  // a lookahead pivot block is in flight for this step's panel
         for (int kb = 0; kb < maxk; kb += nb) {
             const int s0 = (kb / SP) * SP;
             // (0) strips: panel kb (its columns from row kb down, its rows right of it) minus the
-            //     products of this super-panel's earlier pivots s0..kb-1
+            //     products of this super-panel's earlier pivots s0..kb-1 (with lookahead the pivot
+            //     block itself took its share in (A') of the previous step)
             if (kb > s0) {
                 int64_t soff = (int64_t)gem.size();
                 gb = gf = 0;
@@ -793,8 +795,9 @@ static int build_plan(mf_factors* F) {
                     if (kb >= fr.k) continue;
                     const int m = fr.m, k = fr.k, w = std::min(nb, k - kb), K0 = kb - s0;
                     const int64_t Lrow = fr.P_off + kb + (int64_t)s0 * m;  // L[kb.., s0..kb)
-                    gemm_tiles(Lrow, m, fr.P_off + s0 + (int64_t)kb * m, m, fr.P_off + kb + (int64_t)kb * m, m, m - kb, w,
-                               K0, 0);
+                    const int r0 = F->la ? w : 0;  // first row of the column strip
+                    gemm_tiles(Lrow + r0, m, fr.P_off + s0 + (int64_t)kb * m, m, fr.P_off + kb + r0 + (int64_t)kb * m, m,
+                               m - kb - r0, w, K0, 0);
                     if (k - kb - w > 0)
                         gemm_tiles(Lrow, m, fr.P_off + s0 + (int64_t)(kb + w) * m, m, fr.P_off + kb + (int64_t)(kb + w) * m, m,
                                    w, k - kb - w, K0, 0);
@@ -816,6 +819,10 @@ static int build_plan(mf_factors* F) {
                     pf += 2.0 * w * w * w;
                 }
                 push({K_PDIAG, c, (int)(pan.size() - poff), 0, poff}, FAM_PANEL, pb, pf);
+            }
+            if (la_pending) {  // main waits for the lookahead pivot block before the panel products
+                push({K_SYNC, c, 0, 0, F->n_sync++, 2}, FAM_OTHER, 0.0, 0.0);
+                la_pending = false;
             }
             // (B) panel products in place: L21 = A21 U_D^-1, U12 = L_D^-1 A12
             int64_t goff = (int64_t)gem.size();
@@ -839,22 +846,23 @@ static int build_plan(mf_factors* F) {
                 }
             }
             if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_PANEL, gb, gf);
-            // (A') lookahead: the next pivot block takes this panel's update and is factored on
-            //      the lookahead stream while (C) runs on the main one
-            bool la_step = false;
+            // (A') lookahead: the next pivot block takes the update of every pivot of this
+            //      super-panel so far (s0..kb+nb) and is factored on the lookahead stream while (C)
+            //      and the next step's strips run on the main one
             if (F->la) {
+                const int pre = kb + nb - s0;
                 int64_t poff = (int64_t)pan.size();
                 double pb = 0, pf = 0;
                 for (size_t bi = 0; bi < big.size(); bi++) {
                     const FrontDev& fr = a->fronts[big[bi]];
                     if (kb + nb >= fr.k) continue;
                     const int w = std::min(nb, fr.k - kb - nb);
-                    pan.push_back({big[bi], kb + nb, w, nb, (int64_t)bi * 64 * 64});
-                    pb += T * (3.0 * w * w + 2.0 * w * nb);
-                    pf += 2.0 * w * w * w + 2.0 * w * w * nb;
+                    pan.push_back({big[bi], kb + nb, w, pre, (int64_t)bi * 64 * 64});
+                    pb += T * (3.0 * w * w + 2.0 * w * pre);
+                    pf += 2.0 * w * w * w + 2.0 * w * w * pre;
                 }
                 if (pan.size() > (size_t)poff) {
-                    la_step = true;
+                    la_pending = true;
                     push({K_SYNC, c, 0, 0, F->n_sync++, 0}, FAM_OTHER, 0.0, 0.0);
                     F->plan.back().stream = 2;
                     cur_stream = 2;
@@ -888,7 +896,7 @@ static int build_plan(mf_factors* F) {
                 if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_TRAIL, gb, gf);
                 tc_end(c, FAM_TRAIL);
             }
-            if (la_step) push({K_SYNC, c, 0, 0, F->n_sync++, 2}, FAM_OTHER, 0.0, 0.0);  // main waits for (A')
+
         }
         // Schur update S -= L21 U12 (Sec. 2.2): tensor cores (MF_TF32) for large blocks, SIMT otherwise
         int64_t goff = (int64_t)gem.size();
@@ -1180,7 +1188,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     }
     F->sp = F->opt.super_panel > 0 ? F->opt.super_panel : (F->prec == MF_F64 ? F->nb : 256);
     F->sp = std::max(F->nb, (F->sp + F->nb - 1) / F->nb * F->nb);
-    F->la = F->sp == F->nb && F->opt.lookahead >= 0;
+    F->la = F->opt.lookahead >= 0;
     for (int i = 0; i < MF_FUSED_BUCKETS; i++) {
         const int t = F->opt.fused_threads[i];
         if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256) {

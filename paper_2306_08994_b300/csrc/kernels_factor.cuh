@@ -391,10 +391,11 @@ __global__ void __launch_bounds__(256) k_assemble_large(const FrontDev* __restri
 //   (each output tile spans the whole w-wide side, so it reads all of its
 //   input before writing), then the trailing update k_gemm.
 // One CTA per front.
-// With one-panel lookahead the block first takes the update from the panel
-// before it (pre = that panel's width, its columns kb-pre..kb):
+// With one-panel lookahead the block first takes the update from the pivots
+// factored since the last update that reached it (pre of them, kb-pre..kb: the
+// panel before it, or every pivot of its super-panel so far):
 //   F[kb:kb+w, kb:kb+w] -= L[kb:kb+w, kb-pre:kb] U[kb-pre:kb, kb:kb+w],
-// so it can be factored while the rest of that panel's trailing update runs.
+// so it can be factored while the rest of those updates runs.
 struct DiagTask {
     int32_t front, kb, w, pre;
     int64_t slot;  // panel-slot offset (64 x 64, column-major, ld 64)
@@ -435,24 +436,30 @@ __global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __res
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     T* P = fac + fr.P_off;
     extern __shared__ __align__(16) unsigned char pd_dyn[];
-    T* Us = reinterpret_cast<T*>(pd_dyn);  // U block of the lookahead update, NB x (NB + 1)
+    T* Us = reinterpret_cast<T*>(pd_dyn);  // U slice of the lookahead update, NB x (NB + 1)
     const int pre = t.pre, p0 = kb - t.pre;
+    // L slice (rows kb.., columns p0 + c0..) into Z, U slice (rows p0 + c0.., columns kb..) into Us,
+    // zero outside w x cw and cw x w, so the identity padding of D takes no update
+    auto stage = [&](int c0) {
+        const int cw = min(NB, pre - c0);
+        for (int j = warp; j < NB; j += 8)
+            for (int i = lane; i < NB; i += 32) {
+                if (i < w && j < cw) cp_async_elem(&Z[i][j], P + (kb + i) + (int64_t)(p0 + c0 + j) * m);
+                else Z[i][j] = T(0);
+                if (i < cw && j < w) cp_async_elem(&Us[i * (NB + 1) + j], P + (p0 + c0 + i) + (int64_t)(kb + j) * m);
+                else Us[i * (NB + 1) + j] = T(0);
+            }
+    };
     for (int j = warp; j < NB; j += 8)
         for (int i = lane; i < NB; i += 32) {
             if (i < w && j < w) cp_async_elem(&D[i][j], P + (kb + i) + (int64_t)(kb + j) * m);
             else D[i][j] = (i == j) ? T(1) : T(0);
-            if (pre > 0) {
-                // L block (rows kb.., columns p0..) into Z, U block (rows p0.., columns kb..) into Us;
-                // zero outside w x pre and pre x w, so the identity padding of D takes no update
-                if (i < w && j < pre) cp_async_elem(&Z[i][j], P + (kb + i) + (int64_t)(p0 + j) * m);
-                else Z[i][j] = T(0);
-                if (i < pre && j < w) cp_async_elem(&Us[i * (NB + 1) + j], P + (p0 + i) + (int64_t)(kb + j) * m);
-                else Us[i * (NB + 1) + j] = T(0);
-            }
         }
+    if (pre > 0) stage(0);
     cp_async_wait_all();
     __syncthreads();
     if (pre > 0) {
+        // the block's share of the pending update, pre pivots deep, NB at a time
         constexpr int RPT = NB / 16;  // RPT x RPT outputs per thread
         const int ti = tid >> 4, tj = tid & 15;
         T acc[RPT][RPT];
@@ -460,17 +467,26 @@ __global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __res
         for (int r = 0; r < RPT; r++)
 #pragma unroll
             for (int c = 0; c < RPT; c++) acc[r][c] = T(0);
-        for (int q = 0; q < pre; q++) {
-            T av[RPT], bv[RPT];
-#pragma unroll
-            for (int r = 0; r < RPT; r++) {
-                av[r] = Z[ti * RPT + r][q];
-                bv[r] = Us[q * (NB + 1) + tj * RPT + r];
+        for (int c0 = 0; c0 < pre; c0 += NB) {
+            if (c0 > 0) {
+                __syncthreads();  // the previous slice is consumed
+                stage(c0);
+                cp_async_wait_all();
+                __syncthreads();
             }
+            const int cw = min(NB, pre - c0);
+            for (int q = 0; q < cw; q++) {
+                T av[RPT], bv[RPT];
 #pragma unroll
-            for (int r = 0; r < RPT; r++)
+                for (int r = 0; r < RPT; r++) {
+                    av[r] = Z[ti * RPT + r][q];
+                    bv[r] = Us[q * (NB + 1) + tj * RPT + r];
+                }
 #pragma unroll
-                for (int c = 0; c < RPT; c++) acc[r][c] += av[r] * bv[c];
+                for (int r = 0; r < RPT; r++)
+#pragma unroll
+                    for (int c = 0; c < RPT; c++) acc[r][c] += av[r] * bv[c];
+            }
         }
 #pragma unroll
         for (int r = 0; r < RPT; r++)

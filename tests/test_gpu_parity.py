@@ -170,16 +170,19 @@ def test_tensor_core_schur_path(n):
     assert dtc <= 10 * d32 + 1e-12, (dtc, d32)
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_lookahead_factors_match_plain_panel_order(prec):
-    """One-panel lookahead (the next pivot block takes its rank-w update inside the
-    pivot-block kernel, on a second stream) against the plain panel order: the same
-    factors up to rounding, front by front, on the top fronts of a 48 x 48 Q3 mesh
-    (root: 145 pivots, 3 FP32 / 5 FP64 panels)."""
+@pytest.mark.parametrize("prec,panels", [("f64", 1), ("f32", 1), ("f64", 3), ("f32", 3)])
+def test_lookahead_factors_match_plain_panel_order(prec, panels):
+    """One-panel lookahead (the next pivot block takes its pending update inside the
+    pivot-block kernel, on a second stream, while the trailing update or the Crout strips
+    run) against the plain panel order: the same factors up to rounding, front by front,
+    on the top fronts of a 48 x 48 Q3 mesh (root: 145 pivots, 3 FP32 / 5 FP64 panels).
+    Super-panels of 1 panel (the update is one panel deep) and of 3 panels (up to 3 panels
+    deep, staged in several slices)."""
     pr = F.diffusion_2d(48, 3, seed=39)
+    nb = 64 if prec == "f32" else 32
     out = {}
     for la in (0, -1):
-        a, f, vals = _setup(pr, prec, small_front_max=16, super_panel=64 if prec == "f32" else 32, lookahead=la)
+        a, f, vals = _setup(pr, prec, small_front_max=16, super_panel=panels * nb, lookahead=la)
         f.factor(vals)
         assert f.status()["rc"] == 0
         out[la] = [f.export_front(g) for g in range(a.n_front - 7, a.n_front)]
