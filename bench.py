@@ -213,6 +213,33 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def path_roofline(trace, steps, fp64, peaks, info, elem_bytes, nsolve, nrhs, ms_step):
+    """Whole-step roofline: every launch record of the traced steps costs at least the slower of its
+    algorithmic flops at the peak of its arithmetic (tensor cores for the 3xTF32 products, FP64 DFMA or
+    FP32 FFMA otherwise) and its algorithmic bytes at the measured HBM rate; T_roof is their sum per
+    step and frac = T_roof / measured step time.  Beside it the step's must-move bytes B_min (element
+    matrices once per residual and for the factorization, factors written once and read once per
+    solve, the solution vectors) and B_sched = B_min + the contribution blocks written and read once
+    (the class-per-launch round trip)."""
+    bw = peaks["hbm_gbs"] * 1e9
+    p_tc = peaks["bf16_tflops"] / 2 / 3 * 1e12
+    p_alu = (FP64_DFMA_TFLOPS if fp64 else FP32_SIMT_PEAK_TFLOPS) * 1e12
+    t = 0.0
+    for rec in trace:
+        p = p_tc if rec["kind"] == "gemm_tc" else p_alu
+        t += max(rec["flops"] / p, rec["bytes"] / bw)
+    t_roof_ms = 1e3 * t / max(steps, 1)
+    s_f = 8.0 if fp64 else 4.0
+    n = float(info["n_dof"]) * nrhs
+    b_min = (elem_bytes * (1.0 + nsolve) + s_f * info["nnz_lu"] * (1.0 + nsolve)
+             + 8.0 * n * (2.0 + 4.0 * nsolve))
+    b_sched = b_min + 2.0 * s_f * info["sum_cb"]
+    return {"t_roof_ms": t_roof_ms, "t_measured_ms": ms_step, "frac": t_roof_ms / ms_step if ms_step > 0 else None,
+            "b_min_GB": b_min / 1e9, "b_sched_GB": b_sched / 1e9, "t_hbm_floor_ms": 1e3 * b_min / bw,
+            "peaks": {"hbm_GBps": peaks["hbm_gbs"], "tensor_3xtf32_TFLOPs": p_tc / 1e12, "alu_TFLOPs": p_alu / 1e12,
+                      "src": peaks["src"]}}
+
+
 def max_over_ranks(value, dist=None, device="cpu"):
     """The slowest rank's time: every rank solves its own replica, the job ends with the last."""
     if dist is None:
@@ -432,6 +459,7 @@ def main():
     roof["kernel"] = dom
     roof["launches_per_step"] = d["launches"] / args.steps
     roof["per_launch_ms"] = per_launch_ms
+    path_roof = path_roofline(trace, args.steps, precision == "f64", peaks, info, float(Kcm.nbytes), nsolve, nrhs, ms)
     families = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                     "GBps": v["bytes"] / max(v["ms"], 1e-9) / 1e6, "TFLOPps": v["flops"] / max(v["ms"], 1e-9) / 1e9}
                 for k, v in prof.items() if v["launches"]}
@@ -509,7 +537,7 @@ def main():
             "pivots_perturbed": st["n_perturbed"],
             "fp64_path": fp64,
             "speedup_vs_fp64": (fp64["ms"] / ms) if fp64 else None,
-            "roofline": roof,
+            "roofline": roof, "path_roofline": path_roof,
             "families": families,
             "kernels": kernels,
             "gpu_launches": launches,
