@@ -151,6 +151,70 @@ def test_foata_classes_are_the_brute_force_layering(nel, rule):
                 assert any(s.height[ch] == cl - 1 for ch in tree.child[v] if ch >= 0)
 
 
+@pytest.mark.parametrize("nel", [(2, 2), (3, 3)])
+def test_front_classes_coarsen_the_scalar_task_dag(nel):
+    """Sec. 3.3 defines Foata classes over the scalar tasks of Table 2 (T1: divide an entry of
+    the pivot row; T2/T3: update a trailing entry) and the extend-add of a child's block into
+    its parent; the build schedules whole fronts by height instead.  On tiny Q1 meshes the
+    scalar task DAG is built from the data each task reads and writes (program order inside a
+    front, extend-add after the child's last write), and the front-level classes are checked to
+    be a valid coarsening of it: every dependency between tasks of different fronts goes from a
+    lower class to a higher one, no dependency path joins two fronts of the same class, and the
+    task-level Foata layering needs at least as many layers as there are front classes."""
+    mesh = F.structured_mesh(nel, 1)
+    tree = O.tree_bisection(mesh.nel)
+    s = _solver(mesh, tree)
+    tasks = []        # (front, label)
+    preds = []        # list of predecessor task ids
+    last_write = {}   # (front, i, j) -> task id of the last write of that entry
+    def add(front, label, reads, writes):
+        tid = len(tasks)
+        tasks.append((front, label))
+        preds.append(sorted({last_write[e] for e in reads + writes if e in last_write}))
+        for e in writes:
+            last_write[e] = tid
+        return tid
+    for v in range(s.n_front):  # fronts in postorder: children first
+        m, k = int(s.m[v]), int(s.k[v])
+        for c in tree.child[v]:
+            if c < 0:
+                continue
+            cd = s.front_dofs(c)
+            kc = int(s.k[c])
+            pos = {int(d): q for q, d in enumerate(s.front_dofs(v))}
+            for a in range(kc, int(s.m[c])):
+                for b in range(kc, int(s.m[c])):
+                    add(v, "extend-add", [(c, a, b)], [(v, pos[int(cd[a])], pos[int(cd[b])])])
+        for p in range(k):
+            for j in range(p + 1, m):
+                add(v, "T1", [(v, p, p), (v, p, j)], [(v, p, j)])
+            for i in range(p + 1, m):
+                for j in range(p + 1, m):
+                    add(v, "T23", [(v, i, j), (v, i, p), (v, p, j)], [(v, i, j)])
+    n = len(tasks)
+    layer = np.zeros(n, int)
+    for t in range(n):  # ids are a topological order
+        layer[t] = 1 + max((layer[q] for q in preds[t]), default=0)
+    front = np.array([f for f, _ in tasks])
+    h = np.asarray(s.height)
+    for t in range(n):
+        for q in preds[t]:
+            if front[q] != front[t]:
+                assert h[front[q]] < h[front[t]], (tasks[q], tasks[t])
+    # no path between two different fronts of one class: reachable fronts per task (bitsets)
+    reach = [0] * n
+    for t in range(n):
+        r = 1 << int(front[t])
+        for q in preds[t]:
+            r |= reach[q]
+        reach[t] = r
+    for t in range(n):
+        for f2 in range(s.n_front):
+            if f2 != front[t] and (reach[t] >> f2) & 1:
+                assert h[f2] < h[front[t]], (tasks[t], f2)
+    assert layer.max() >= s.n_classes
+
+
 # --------------------------------------------------------------- factors
 def _global_factors(s, n):
     perm = np.concatenate([s.front_dofs(v)[: s.k[v]] for v in range(s.n_front)])
