@@ -453,8 +453,8 @@ def main():
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "peak_src": peaks["src"]}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    # DRAM traffic per launch of the dominant kernel from an ncu capture of this workload
-    # (profiles/k_gemm_cp_diffusion2d_q3_512.md); null for kernels or workloads not captured
+    # DRAM traffic per launch of the dominant kernel from one ncu capture of this workload
+    # (every launch of a full bench run); null for kernels or workloads not captured
     roof["traffic"] = MEASURED_TRAFFIC.get((args.workload, precision, dom))
     roof["kernel"] = dom
     roof["launches_per_step"] = d["launches"] / args.steps

@@ -28,7 +28,7 @@
  *     factor L (non-unit diagonal, the pivot column), then backward
  *     substitution with the unit upper factor U (the divided pivot rows).
  *
- * Readings where the paper is silent or garbled (all are listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   loop bounds j, i start at p+1 (the task definitions say j > p, i > p);
  *   the division result is stored back into F[p,j]; no pivoting, with a
  *   static check |F[p,p]| < tau that replaces the pivot by sign*tau (counted)

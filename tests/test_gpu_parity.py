@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerances (derived in the design doc):
+Tolerances (derived from the arithmetic):
   * FP64 factors: |L - L_oracle| <= 1e-11 * max|front| per front (two FP64
     eliminations of the same front differing only in summation order);
   * solutions: ||x - x_oracle||_2 / ||x_oracle||_2 <= 1e-10 (the stated bar),
