@@ -78,7 +78,7 @@ FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 f
 # (dram__bytes_read.sum + dram__bytes_write.sum over all its launches / launches); the key names the
 # workload, the requested front precision (the tuned plan of the committed cache) and the trace
 # kind.  Valid while the kernel is unchanged.
-MEASURED_TRAFFIC = {("diffusion2d_q3_512", "f32", "gemm"): 19.73e6}
+MEASURED_TRAFFIC = {("diffusion2d_q3_512", "f32", "gemm"): 19.73e6, ("diffusion3d_q1_64", "f32", "gemm_tc"): 186.1e6}
 FP64_DFMA_TFLOPS = 1.201  # measured DFMA throughput of this B300 (register-resident FMA loop, all SMs)
 
 
