@@ -238,13 +238,20 @@ int mf_factors_export_front(const mf_factors* f, int32_t front, double* L, doubl
  * mf_factors handle.  Every pointer is the caller's: d_elem_nodes (device,
  * n_elem * npe global dof ids, as in mf_mesh_desc), d_values (element
  * matrices, as for mf_factor), d_x, d_b, d_r (n_dof x nrhs).
- * Work space is one file-scope device array of MF_NOALLOC_MAX_ENTRIES
- * doubles (8 MiB) that every device loading the library keeps until exit;
- * n_dof * nrhs beyond it returns MF_ETOOLARGE and launches nothing.  The
- * first call on a device looks the array's address up (cudaGetSymbolAddress,
- * that device current) and caches it: make that first call before any stream
- * capture.  Calls share the array (each clears what it uses first), so calls
- * that overlap on the GPU race.  Sums use FP64 atomics: results equal
+ * Limits: 1 <= nodes_per_elem <= 64 and 1 <= nrhs <= 65535, else MF_EINVAL
+ * with nothing launched.  Work space is one file-scope device array of
+ * MF_NOALLOC_MAX_ENTRIES doubles (8 MiB) that every device loading the
+ * library keeps until exit; n_dof * nrhs beyond it returns MF_ETOOLARGE and
+ * launches nothing.  The caller must keep every id in d_elem_nodes in
+ * [0, n_dof): the kernel checks each id before using it, never reads or
+ * writes through one outside that range, and then fills all of d_r with NaN
+ * (the call returns before the GPU runs, so the NaN output is the report).
+ * The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress, that device current) and caches it: make that first
+ * call before any stream capture.  The cached address belongs to the CUDA
+ * context of that first call; after cudaDeviceReset, load the library afresh.
+ * Calls share the array (each clears what it uses first), so calls that
+ * overlap on the GPU race.  Sums use FP64 atomics: results equal
  * mf_residual's up to rounding order. */
 #define MF_NOALLOC_MAX_ENTRIES (1 << 20)
 int mf_residual_noalloc(int64_t n_dof, int64_t n_elem, int nodes_per_elem, const int64_t* d_elem_nodes,
@@ -325,6 +332,26 @@ int mf_autotune(const mf_analysis* a, const double* d_values, const double* d_b,
 
 void mf_free_factors(mf_factors* f);
 void mf_free_analysis(mf_analysis* a);
+
+/* ---- Testing hooks.  The paper has no counterpart: they let tests drive the
+ * library's error paths from the host without faulting, trapping or hanging
+ * the GPU. */
+
+/* Host-side allocation-failure injection: the n-th device allocation the
+ * library makes from now on (0 = the next one) fails as if the device were
+ * out of memory, so the entry point that made it releases what it had
+ * allocated and returns MF_ENOMEM.  n < 0 disarms.  Process-wide, not
+ * thread-safe with respect to concurrent allocations in other threads. */
+void mf_test_fail_alloc(int64_t n);
+
+/* Enqueues on `stream` one bounded device wait that nothing will release: a
+ * single CTA waits at the grid barrier of the persistent substitution sweep
+ * for a second CTA that is never launched, gives up after limit_ms
+ * milliseconds (0 < limit_ms <= 10000, else MF_EINVAL), records a timeout in
+ * f's status word and returns; no copy is in flight in that kernel.
+ * mf_status(f) then returns MF_ETIMEOUT; the next mf_factor clears the status
+ * and the handle stays usable. */
+int mf_test_bounded_wait(mf_factors* f, double limit_ms, mf_stream_t stream);
 
 #ifdef __cplusplus
 }

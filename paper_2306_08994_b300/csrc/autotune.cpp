@@ -210,7 +210,7 @@ extern "C" int mf_autotune(const mf_analysis* a, const double* d_values, const d
     }
     cudaStream_t s = (cudaStream_t)stream;
     double* d_x = nullptr;
-    if (cudaMalloc(&d_x, sizeof(double) * (size_t)a->n_dof) != cudaSuccess) return MF_ENOMEM;
+    if (mf_alloc_should_fail() || cudaMalloc(&d_x, sizeof(double) * (size_t)a->n_dof) != cudaSuccess) return MF_ENOMEM;
     Ctx c{a, d_values, d_b, d_x, reps, s};
     int rc = MF_OK;
     o.use_graph = 1;

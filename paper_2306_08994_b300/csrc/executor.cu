@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -14,6 +15,17 @@
 #include "kernels_subtree.cuh"
 #include "kernels_tc.cuh"
 #include "mf_internal.h"
+
+// Host-side fault injection for tests (mf_test_fail_alloc): when >= 0, the
+// allocation that brings the countdown from 0 to -1 fails as if the device
+// were out of memory.
+static std::atomic<long long> g_alloc_countdown{-1};
+bool mf_alloc_should_fail() {
+    long long c = g_alloc_countdown.load();
+    while (c >= 0)
+        if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) return c == 0;
+    return false;
+}
 
 namespace {
 
@@ -73,6 +85,7 @@ template <typename T>
 int dev_alloc(T** p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 1;
+    if (mf_alloc_should_fail()) return MF_ENOMEM;
     cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -1976,5 +1989,28 @@ extern "C" int mf_profile_read(mf_factors* F, double* ms, int64_t* launches, dou
         F->acc_flops[q] = 0;
     }
     F->ev_used = 0;
+    return MF_OK;
+}
+
+// ------------------------------------------------------------- testing hooks
+extern "C" void mf_test_fail_alloc(int64_t n) { g_alloc_countdown.store(n < 0 ? -1 : (long long)n); }
+
+namespace {
+// One CTA arrives at the substitution sweep's grid barrier expecting a second
+// CTA that is never launched: the bounded wait must give up and record a
+// timeout.  No asynchronous copies are in flight in this kernel.
+__global__ void k_test_bounded_wait(unsigned int* bar, DevStatus* st, unsigned long long limit_ns) {
+    (void)sweep_barrier(bar, 2u, st, limit_ns);
+}
+}  // namespace
+
+extern "C" int mf_test_bounded_wait(mf_factors* F, double limit_ms, mf_stream_t stream) {
+    if (!F || !(limit_ms > 0.0) || limit_ms > 10000.0) return MF_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemsetAsync(F->d_bar, 0, 2 * sizeof(unsigned int), s));
+    k_test_bounded_wait<<<1, 32, 0, s>>>(F->d_bar, F->d_status, (unsigned long long)(limit_ms * 1e6));
+    CUDA_TRY(cudaGetLastError());
+    // leave the barrier as a sweep launch expects it (every sweep launch clears it again anyway)
+    CUDA_TRY(cudaMemsetAsync(F->d_bar, 0, 2 * sizeof(unsigned int), s));
     return MF_OK;
 }

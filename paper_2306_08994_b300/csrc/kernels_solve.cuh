@@ -921,7 +921,8 @@ __device__ __forceinline__ uint64_t sweep_clock_ns() {
 }
 
 // Grid-wide barrier for a cooperative launch (all CTAs resident), bounded.
-__device__ __forceinline__ bool sweep_barrier(unsigned int* bar, unsigned int nblocks, DevStatus* st) {
+__device__ __forceinline__ bool sweep_barrier(unsigned int* bar, unsigned int nblocks, DevStatus* st,
+                                              unsigned long long limit_ns = 1000000000ull) {
     __shared__ int ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -937,7 +938,7 @@ __device__ __forceinline__ bool sweep_barrier(unsigned int* bar, unsigned int nb
         } else {
             const uint64_t t0 = sweep_clock_ns();
             while (*gen == g) {
-                if (sweep_clock_ns() - t0 > 1000000000ull) {
+                if (sweep_clock_ns() - t0 > limit_ns) {
                     ok = 0;
                     atomicOr(&st->timeout, 1);
                     break;

@@ -82,3 +82,7 @@ int mf_symbolic(const mf_mesh_desc* meshes, int count, const mf_options* opt, mf
 
 // Options with defaults filled in.
 mf_options mf_resolve_options(const mf_options* opt);
+
+// Test hook (mf_test_fail_alloc): true when this device allocation is the one
+// chosen to fail.  Every device allocation of the library asks first.
+bool mf_alloc_should_fail();

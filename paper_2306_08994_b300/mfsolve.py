@@ -87,7 +87,7 @@ EXPORTS = ["mf_default_options", "mf_strerror", "mf_analyze_mesh", "mf_analyze_b
            "mf_refine_solve_adjoint", "mf_residual", "mf_element_grad", "mf_element_outer", "mf_status",
            "mf_factors_export_front",
            "mf_free_factors", "mf_free_analysis", "mf_profile_enable", "mf_profile_read", "mf_residual_noalloc",
-           "mf_autotune", "mf_profile_trace"]
+           "mf_autotune", "mf_profile_trace", "mf_test_fail_alloc", "mf_test_bounded_wait"]
 PROFILE_FAMILIES = ["fused", "assemble", "panel", "trailing_gemm", "schur_gemm", "forward", "backward", "residual",
                     "other", "inverse"]
 
@@ -118,6 +118,7 @@ def _load():
         "mf_residual_noalloc": ([I64, I64, I, P, P, P, P, P, I, P], I),
         "mf_autotune": ([P, P, P, P, I, ctypes.c_char_p, P, P, P], I),
         "mf_profile_trace": ([P, P, I, P], I),
+        "mf_test_fail_alloc": ([I64], None), "mf_test_bounded_wait": ([P, D, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

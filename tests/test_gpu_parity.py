@@ -414,3 +414,58 @@ def test_persistent_sweep_matches_per_class_launches(prec):
         assert np.linalg.norm(ya - yb) <= tol_rhs * np.linalg.norm(ya)
         assert np.linalg.norm(y1a - y1b) <= tol_rhs * np.linalg.norm(y1a)
         assert np.linalg.norm(y1b - yb[0]) <= tol_rhs * np.linalg.norm(y1b)
+
+
+FP32_CASES = {
+    "q1_32": (lambda: F.poisson_2d_q1(32), {"small_front_max": 32}),
+    "q3_16_hetero": (lambda: F.diffusion_2d(16, 3, seed=41), {"small_front_max": 48}),
+    "q3_24_large_path": (lambda: F.diffusion_2d(24, 3, seed=42), {"small_front_max": 16, "super_panel": 64}),
+    "q1_3d_8": (lambda: F.diffusion_3d_q1(8, seed=43), {"small_front_max": 24}),
+}
+
+
+@pytest.mark.parametrize("case", list(FP32_CASES))
+@pytest.mark.parametrize("prec", ["f32", "tf32"])
+def test_fp32_family_factors_match_oracle_front_by_front(case, prec):
+    """FP32 and split-TF32 fronts against the oracle's FP64 factors, front by front.
+
+    Tolerance from the arithmetic: an entry of front f is the result of at most K_f updates,
+    K_f = the pivots eliminated in f's subtree (every pivot below f can reach it once through the
+    extend-add chain, and f's own pivots once each); each update adds a product of entries no
+    larger than the front's scale and is rounded once in FP32 (unit roundoff u = 2^-24) or, with
+    three split-TF32 products, carries a product error of about 2^-21 (the dropped lo x lo term
+    and the TF32 truncation of the lo parts).  So |L - L_oracle| <= 4 K_f u_eff max|front| with
+    u_eff = 2^-24 (f32) or 2^-21 (tf32), the factor 4 covering the division by the pivot and the
+    rounding of the assembled inputs."""
+    mk, opt = FP32_CASES[case]
+    pr = mk()
+    if prec == "tf32":
+        opt = dict(opt, tc_min_cb=16)
+    a, f, vals = _setup(pr, prec, **opt)
+    f.factor(vals)
+    st = f.status()
+    assert st["rc"] == 0 and st["n_perturbed"] == 0
+    s = _oracle(pr)
+    ksub = np.asarray(s.k, dtype=np.int64).copy()
+    for v in range(s.n_front):  # postorder: children before parents
+        if s.parent[v] >= 0:
+            ksub[s.parent[v]] += ksub[v]
+    u_eff = 2.0 ** -24 if prec == "f32" else 2.0 ** -21
+    order = np.lexsort((np.arange(s.n_front), s.height))
+    worst = 0.0
+    for g in range(len(order)):
+        v = order[g]
+        Lo, Uo = s.factor_of(v)
+        k = Lo.shape[1]
+        if k == 0:
+            continue
+        Lg, Ug = f.export_front(g)
+        sc = max(np.abs(Lo).max(), np.abs(Uo).max(), 1.0)
+        tol = 4.0 * ksub[v] * u_eff * sc
+        low = np.tril(np.ones((Lo.shape[0], k), bool))
+        up = np.triu(np.ones((k, Uo.shape[1]), bool), 1)
+        eL = np.abs(Lg - Lo)[low].max()
+        eU = np.abs(Ug - Uo)[up].max() if up.any() else 0.0
+        worst = max(worst, max(eL, eU) / tol)
+        assert eL <= tol and eU <= tol, (case, prec, g, eL, eU, tol)
+    print(f"{case} {prec}: worst error / bound = {worst:.3f}")

@@ -215,6 +215,79 @@ def test_front_classes_coarsen_the_scalar_task_dag(nel):
     assert layer.max() >= s.n_classes
 
 
+# ------------------------------------------------- work counts (orc_info)
+def test_work_counts_of_a_hand_worked_two_element_mesh():
+    """2x1 Q1 mesh, 6 nodes numbered x fastest: element 0 = {0,1,3,4}, element 1 = {1,2,4,5}.
+    By hand: each leaf eliminates its two private nodes (k = 2, m = 4: pivot 0 costs 3 divisions
+    + 2*3^2 mult/sub = 21, pivot 1 costs 2 + 2*2^2 = 10, so 31) and passes the shared pair {1, 4}
+    up; the root has m = k = 2 (pivot 0: 1 + 2*1 = 3, pivot 1: 0).  Flops 31 + 31 + 3 = 65.
+    nnz(L+U): a leaf stores 4*2 + 2*2 = 12 entries, the root 2*2 = 4, so 28; CB entries 4 + 4."""
+    en = np.array([[0, 1, 3, 4], [1, 2, 4, 5]], dtype=np.int64)
+    s = O.OracleSolver(6, en, O.tree_bisection((2, 1)))
+    assert s.n_front == 3 and s.n_classes == 2
+    assert s.flops == 65 and s.nnz_lu == 28 and s.sum_cb == 8 and s.max_m == 4 and s.max_k == 2
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_work_counts_of_one_dense_element_closed_form(p):
+    """One element = one front factored completely (m = k = (p+1)^2): divisions
+    sum_{q<m} (m-q-1) = m(m-1)/2, multiplications and subtractions 2 sum_{q<m} (m-q-1)^2
+    = (m-1)m(2m-1)/3, nnz(L+U) = m^2, no contribution block."""
+    s = _solver(F.structured_mesh((1, 1), p))
+    m = (p + 1) ** 2
+    assert s.n_front == 1 and int(s.k[0]) == m
+    assert s.flops == m * (m - 1) // 2 + (m - 1) * m * (2 * m - 1) // 3
+    assert s.nnz_lu == m * m and s.sum_cb == 0
+
+
+@pytest.mark.parametrize("nel,p", [((4, 4), 1), ((3, 3), 3), ((3, 3, 3), 1), ((5, 5), 2)])
+def test_work_counts_by_task_enumeration(nel, p):
+    """orc_info's flop count equals the number of Table 2 tasks the fronts perform, enumerated one
+    by one (a division per entry right of each pivot in its row, a multiplication and a
+    subtraction per trailing entry), and nnz(L+U) equals the number of front positions a pivot row
+    or column covers (counted on a boolean mask of each front)."""
+    s = _solver(F.structured_mesh(nel, p))
+    t1 = t23 = nnz = 0
+    for v in range(s.n_front):
+        m, k = int(s.m[v]), int(s.k[v])
+        for q in range(k):
+            t1 += len(range(q + 1, m))
+            t23 += len(range(q + 1, m)) ** 2
+        mask = np.zeros((m, m), bool)
+        mask[:k, :] = True
+        mask[:, :k] = True
+        nnz += int(mask.sum())
+    assert s.flops == t1 + 2 * t23
+    assert s.nnz_lu == nnz
+
+
+@pytest.mark.parametrize("mk", [lambda: F.poisson_2d_q1(6), lambda: F.diffusion_2d(2, 3, seed=7)])
+def test_front_blocks_cover_every_nonzero_of_the_dense_factors(mk):
+    """The fronts' pivot rows and columns (the nnz(L+U) positions) contain every nonzero of the
+    dense L and U of P A P^T computed by LAPACK, so nnz_lu bounds the true factor count from above;
+    it is tight up to the structural zeros a dense front keeps."""
+    pr = mk()
+    mesh = pr.mesh
+    s = _solver(mesh)
+    n = mesh.n_nodes
+    perm = np.concatenate([s.front_dofs(v)[: s.k[v]] for v in range(s.n_front)])
+    pos = np.empty(n, int)
+    pos[perm] = np.arange(n)
+    covered = np.zeros((n, n), bool)
+    for v in range(s.n_front):
+        fd = pos[s.front_dofs(v)]
+        k = int(s.k[v])
+        covered[np.ix_(fd, fd[:k])] = True      # L: pivot columns
+        covered[np.ix_(fd[:k], fd)] = True      # U: pivot rows
+    assert int(covered.sum()) == s.nnz_lu       # fronts' pivot blocks never overlap
+    A = F.assemble_dense(mesh, pr.Ke)[np.ix_(perm, perm)]
+    C = np.linalg.cholesky(A)
+    nzL = np.abs(C) > 1e-14 * np.abs(C).max()
+    full = nzL | nzL.T
+    assert not (full & ~covered).any()
+    assert int(full.sum()) <= s.nnz_lu
+
+
 # --------------------------------------------------------------- factors
 def _global_factors(s, n):
     perm = np.concatenate([s.front_dofs(v)[: s.k[v]] for v in range(s.n_front)])

@@ -14,6 +14,7 @@ import pytest
 import torch
 
 import fem_inputs as F
+import oracle as O
 import paper_2306_08994_b300 as M
 from paper_2306_08994_b300 import mfsolve as B
 
@@ -38,18 +39,63 @@ def test_noalloc_residual_matches_mf_residual_twice_in_a_row():
     import scipy.sparse as sp
     rp, cp, vp = F.assemble_csr(pm, pr.Ke)
     rowsum = float(np.abs(sp.csr_matrix((vp, cp, rp))).sum(axis=1).max())
+    Kcm = F.to_colmajor(pr.Ke)
     for call in range(2):
         x = torch.tensor(rng.uniform(-1, 1, (nrhs, pm.n_nodes)), device="cuda")
         r_ref = torch.empty_like(b)
         fac.residual(vals, x, b, r_ref)
         r = torch.full_like(b, float("nan"))
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         rc = _noalloc(pm.n_nodes, pm.n_elem, pm.npe, en, vals, x, b, r, nrhs)
         assert rc == B.MF_OK, rc
         torch.cuda.synchronize()
+        # no device memory was taken by the call (the first call's module load happened above, in
+        # the library's first use; the static array is part of the loaded module)
+        assert torch.cuda.mem_get_info()[0] == free0
         # same tolerance as the refinement bar: rounding-order differences only
         scale = rowsum * float(x.abs().max()) + float(b.abs().max())
         err = float((r - r_ref).abs().max())
         assert err <= 1e-13 * scale, (call, err, scale)
+        # and against the oracle's double-double residual (exact to ~1 ulp of the result)
+        r_o = O.residual_dd(pm.elem_nodes, Kcm, x.cpu().numpy().T, b.cpu().numpy().T)
+        err_o = float(np.abs(r.cpu().numpy().T - r_o).max())
+        assert err_o <= 1e-13 * scale, (call, err_o, scale)
+
+
+def test_noalloc_reports_out_of_range_node_ids_as_nan():
+    """An element node id outside [0, n_dof) is never read or written through; the call's output is NaN."""
+    pr = F.poisson_2d_q1(6)
+    pm = pr.mesh
+    vals = torch.tensor(F.to_colmajor(pr.Ke), device="cuda")
+    en_h = pm.elem_nodes.copy()
+    en_h[3, 2] = pm.n_nodes + 1000  # beyond the vectors and the scratch row in use
+    en_h[7, 0] = -5
+    en = torch.tensor(en_h, device="cuda")
+    x = torch.ones(pm.n_nodes, dtype=torch.float64, device="cuda")
+    b = torch.zeros_like(x)
+    r = torch.zeros_like(x)
+    rc = _noalloc(pm.n_nodes, pm.n_elem, pm.npe, en, vals, x, b, r, 1)
+    assert rc == B.MF_OK
+    torch.cuda.synchronize()
+    assert bool(torch.isnan(r).all())
+    # the next good call clears the flag
+    en_ok = torch.tensor(pm.elem_nodes, device="cuda")
+    rc = _noalloc(pm.n_nodes, pm.n_elem, pm.npe, en_ok, vals, x, b, r, 1)
+    assert rc == B.MF_OK
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(r).all())
+
+
+def test_noalloc_rejects_too_many_right_hand_sides_before_launching():
+    t = torch.zeros(8, dtype=torch.float64, device="cuda")
+    ti = torch.zeros(8, dtype=torch.int64, device="cuda")
+    r = torch.full((8,), 7.0, dtype=torch.float64, device="cuda")
+    rc = B.lib().mf_residual_noalloc(1, 1, 4, ti.data_ptr(), t.data_ptr(), t.data_ptr(), t.data_ptr(),
+                                     r.data_ptr(), 65536, None)
+    assert rc == B.MF_EINVAL
+    torch.cuda.synchronize()
+    assert bool((r == 7.0).all())
 
 
 def test_noalloc_rejects_sizes_beyond_the_static_scratch():
