@@ -63,6 +63,13 @@ WORKLOADS = {
     "poisson2d_q1_16": (lambda: [F.poisson_2d_q1(16)], lambda: [F.structured_mesh((16, 16), 1)], "solve", "f64",
                         "2D Poisson, 16x16 Q1, 289 dofs"),
 }
+# the paper's own model problem (Sec. 2.1): L2 projection (mass matrix, no boundary condition) for
+# p = 1, 2, 3 at about 3e5 dofs, the largest size the paper measures (Sec. 4)
+for _p, _n in F.L2_SIZES.items():
+    WORKLOADS[f"l2proj_q{_p}_{_n}"] = (
+        (lambda p=_p, n=_n: [F.l2_projection(n, p)]), (lambda p=_p, n=_n: [F.structured_mesh((n, n), p)]),
+        "solve", "f32", f"L2 projection (mass matrix) of a smooth field, {_n}x{_n} Q{_p}, "
+                        f"{(_p * _n + 1) ** 2:,} dofs")
 # CPU oracle arm per workload: (sample name, builder or None = the full workload itself).  One
 # oracle step of each full 2D workload takes roughly 10-40 s on the host cores, so those are timed
 # as they are; the 3D workload (about 1e12 flops, mostly in a handful of dense fronts the oracle
@@ -75,6 +82,8 @@ CPU_SAMPLE = {
     "adjoint2d_q1_1024": ("adjoint2d_q1_1024", None),
     "poisson2d_q1_16": ("poisson2d_q1_16", None),
 }
+for _p, _n in F.L2_SIZES.items():
+    CPU_SAMPLE[f"l2proj_q{_p}_{_n}"] = (f"l2proj_q{_p}_{_n}", None)
 # warm-up steps of the oracle arm run on this small case of the default recipe (the oracle keeps no
 # state between steps; the warm-up only starts the thread pool and pages the code in)
 CPU_WARMUP = ("diffusion2d_q3_32", lambda: [F.diffusion_2d(32, 3, seed=F.SEED_BASE + 2)])

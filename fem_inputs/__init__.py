@@ -191,8 +191,10 @@ def element_matrices(mesh: StructuredMesh, coef: Optional[np.ndarray] = None,
     return Ke
 
 
-def load_vector(mesh: StructuredMesh, f: Callable, g_dirichlet: Optional[np.ndarray] = None) -> np.ndarray:
-    """Assembled b_i = int f phi_i with (p+2)^d Gauss points; Dirichlet entries = g (0 default)."""
+def load_vector(mesh: StructuredMesh, f: Callable, g_dirichlet: Optional[np.ndarray] = None,
+                dirichlet: bool = True) -> np.ndarray:
+    """Assembled b_i = int f phi_i with (p+2)^d Gauss points; Dirichlet entries = g (0 default),
+    or left as assembled when ``dirichlet`` is False."""
     nq = mesh.p + 2
     t, w = gauss_legendre_01(nq)
     V, _ = lagrange_1d(mesh.p, t)                  # (p+1, nq)
@@ -217,7 +219,8 @@ def load_vector(mesh: StructuredMesh, f: Callable, g_dirichlet: Optional[np.ndar
         fq = f(X, Y, Z)
     be = (fq * wq[None, :]) @ phi.T * h ** d          # (ne, npe)
     b = np.bincount(mesh.elem_nodes.ravel(), weights=be.ravel(), minlength=mesh.n_nodes)
-    b[mesh.boundary] = 0.0 if g_dirichlet is None else g_dirichlet[mesh.boundary]
+    if dirichlet:
+        b[mesh.boundary] = 0.0 if g_dirichlet is None else g_dirichlet[mesh.boundary]
     return b
 
 
@@ -305,6 +308,25 @@ def diffusion_3d_q1(n: int, seed: int, decades: float = 1.0) -> Problem:
     Ke = element_matrices(mesh, coef)
     b = load_vector(mesh, lambda x, y, z: np.ones_like(x))[:, None]
     return Problem(f"diffusion3d_q1_{n}", mesh, Ke, b, coef)
+
+
+def l2_field(x, y, z=None):
+    """Smooth field projected by the L2-projection workload: exp(x) sin(3 x + 2 y) + x y^2."""
+    return np.exp(x) * np.sin(3.0 * x + 2.0 * y) + x * y * y
+
+
+# sizes of the L2-projection workload, one per order, each near the paper's largest system (3e5 dofs)
+L2_SIZES = {1: 512, 2: 256, 3: 180}
+
+
+def l2_projection(n: int, p: int, f: Callable = l2_field) -> Problem:
+    """The paper's model problem (Sec. 2.1): the L2 projection of f onto the Qp space of an n x n
+    mesh of the unit square, M u = b with the mass matrix M_ij = int phi_i phi_j (SPD, no boundary
+    condition: every node is an unknown) and b_i = int f phi_i."""
+    mesh = structured_mesh((n, n), p)
+    Ke = element_matrices(mesh, dirichlet=False, kind="mass")
+    b = load_vector(mesh, f, dirichlet=False)[:, None]
+    return Problem(f"l2proj_q{p}_{n}", mesh, Ke, b)
 
 
 def batched_poisson_sizes(count: int = 256, lo: int = 32, hi: int = 256, seed: int = SEED_BASE + 3) -> np.ndarray:

@@ -158,6 +158,29 @@ int mf_analyze_mesh(const mf_mesh_desc* mesh, const mf_options* opt, mf_analysis
  * vectors are the meshes' concatenated in order. */
 int mf_analyze_batch(const mf_mesh_desc* meshes, int count, const mf_options* opt, mf_analysis** out);
 
+/* Symbolic analysis of a general sparse n x n matrix given by its CSR pattern
+ * (host arrays, copied): rowptr (n+1 int64, rowptr[0] = 0, non-decreasing)
+ * and col (rowptr[n] int32 column ids in [0, n), strictly increasing within a
+ * row; entry q of the value array sits at row i, column col[q] for
+ * rowptr[i] <= q < rowptr[i+1]).  The paper applies the method to symmetric
+ * invertible finite-element matrices (Sec. 2.1) and builds the tree from
+ * element fronts (Sec. 2.4); without elements or coordinates, the tree here
+ * cuts the graph of A + A^T in two recursively (breadth-first level structure
+ * from a pseudo-peripheral vertex, split in half) down to single vertices,
+ * and vertex w's element holds a_ww and, for each off-diagonal pair {u, w}
+ * placed on the left side of the cut that separates u and w, the entries
+ * a_wu and a_uw; the right-side boundary of every cut becomes its separator.
+ * The mesh analysis then runs on those elements.  Numeric calls on factors of
+ * this analysis (mf_factor, mf_refine_solve, mf_refine_solve_adjoint,
+ * mf_residual, mf_autotune) take d_values = the CSR values (rowptr[n]
+ * doubles, device, in the order of col); mf_element_grad and
+ * mf_element_outer return MF_ENOTSUP.  A structurally unsymmetric pattern is
+ * symmetrised (missing mirror entries are zeros).  Limits: n < 2^30, and each
+ * vertex's element may hold at most 63 pairs (else MF_ENOTSUP); bad arrays
+ * give MF_EINVAL.  The element array (n * npe^2 doubles, npe = the largest
+ * element) is allocated by mf_factors_create. */
+int mf_analyze_csr(int64_t n, const int64_t* rowptr, const int32_t* col, const mf_options* opt, mf_analysis** out);
+
 int mf_analysis_info(const mf_analysis* a, mf_info* out);
 
 /* Export the front structure (fronts numbered class by class).  Every array
@@ -240,8 +263,11 @@ int mf_factors_export_front(const mf_factors* f, int32_t front, double* L, doubl
  * matrices, as for mf_factor), d_x, d_b, d_r (n_dof x nrhs).
  * Limits: 1 <= nodes_per_elem <= 64 and 1 <= nrhs <= 65535, else MF_EINVAL
  * with nothing launched.  Work space is one file-scope device array of
- * MF_NOALLOC_MAX_ENTRIES doubles (8 MiB) that every device loading the
- * library keeps until exit; n_dof * nrhs beyond it returns MF_ETOOLARGE and
+ * MF_NOALLOC_MAX_ENTRIES doubles (8 MiB) that a device holds from the moment
+ * the library's device code is loaded there until exit; with CUDA's lazy
+ * module loading (the default) that moment is the first call of this entry
+ * point on the device, which may therefore take device memory once; later
+ * calls take none.  n_dof * nrhs beyond the array returns MF_ETOOLARGE and
  * launches nothing.  The caller must keep every id in d_elem_nodes in
  * [0, n_dof): the kernel checks each id before using it, never reads or
  * writes through one outside that range, and then fills all of d_r with NaN

@@ -151,7 +151,9 @@ mf_options mf_resolve_options(const mf_options* opt) {
 
 // Symbolic analysis of a batch of meshes (a forest).  Each mesh keeps its own
 // tree; classes are aligned from the leaves.
-int mf_symbolic(const mf_mesh_desc* meshes, int count, const mf_options* opt, mf_analysis* a) {
+int mf_symbolic(const mf_mesh_desc* meshes, int count, const mf_options* opt, mf_analysis* a,
+                const HostTree* pretree) {
+    if (pretree && count != 1) return MF_EINVAL;
     if (count < 1 || !meshes) return MF_EINVAL;
     a->opt = mf_resolve_options(opt);
     a->npe = meshes[0].nodes_per_elem;
@@ -180,8 +182,12 @@ int mf_symbolic(const mf_mesh_desc* meshes, int count, const mf_options* opt, mf
         for (int i = 0; i < count; i++) {
             const mf_mesh_desc& m = meshes[i];
             HostTree t;
-            int rc = mf_build_tree(&m, t);
-            if (rc) return rc;
+            if (pretree) {
+                t = *pretree;
+            } else {
+                int rc = mf_build_tree(&m, t);
+                if (rc) return rc;
+            }
             int32_t base = (int32_t)tparent.size();
             for (size_t v = 0; v < t.parent.size(); v++) {
                 tparent.push_back(t.parent[v] < 0 ? -1 : t.parent[v] + base);
@@ -348,9 +354,9 @@ int mf_symbolic(const mf_mesh_desc* meshes, int count, const mf_options* opt, mf
         if (F.elem >= 0) {
             // front row i holds element-local node map[i]
             std::vector<int32_t> mp(m, -1);
-            for (int j = 0; j < npe; j++) {
+            for (int j = 0; j < npe; j++) {  // first occurrence: a repeated node's later copies carry zeros
                 int32_t d = (int32_t)a->elem_nodes[(int64_t)F.elem * npe + j];
-                mp[where[d]] = j;
+                if (mp[where[d]] < 0) mp[where[d]] = j;
             }
             a->maps.insert(a->maps.end(), mp.begin(), mp.end());
         } else {

@@ -281,6 +281,9 @@ struct mf_factors {
     int n_sync = 0;
     unsigned int* d_famax = nullptr;
     DevStatus* d_status = nullptr;
+    // CSR analyses: destination of each CSR entry in the arrowhead element array, and that array
+    int64_t* d_csr_dest = nullptr;
+    double* d_elemvals = nullptr;
     double *d_r = nullptr, *d_d = nullptr, *d_Y = nullptr, *d_rowabs = nullptr, *d_part = nullptr, *d_norms = nullptr;
     double* d_colabs = nullptr;  // column sums of |A| (||A^T||_inf of the adjoint refinement)
     bool colabs_valid = false;
@@ -377,7 +380,7 @@ static void free_factors(mf_factors* f) {
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_vsrc, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
                     f->d_vec, f->d_flist, f->d_frec, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
-                    f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms, f->d_colabs};
+                    f->d_csr_dest, f->d_elemvals, f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms, f->d_colabs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete f;
@@ -1239,6 +1242,16 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
         TRY(upload(&F->d_vsrc, vsrc));
     }
     TRY(upload(&F->d_en, a->elem_nodes));
+    if (a->csr_n > 0) {
+        TRY(upload(&F->d_csr_dest, a->csr_dest));
+        const size_t ne = (size_t)a->n_elem * a->npe * a->npe;
+        TRY(dev_alloc(&F->d_elemvals, ne));
+        // positions no CSR entry maps to (the arrowheads' empty parts, the padding) stay zero
+        if (cudaMemset(F->d_elemvals, 0, ne * sizeof(double)) != cudaSuccess) {
+            free_factors(F);
+            return MF_ECUDA;
+        }
+    }
     TRY(upload(&F->d_node_ptr, a->node_ptr));
     TRY(upload(&F->d_node_inc, a->node_inc));
     TRY(dev_alloc((char**)&F->d_fac, (size_t)a->factor_size * F->tsize));
@@ -1328,6 +1341,31 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
 }
 
 extern "C" void mf_free_factors(mf_factors* f) { free_factors(f); }
+
+namespace {
+__global__ void k_csr_scatter(const double* __restrict__ v, const int64_t* __restrict__ dest, double* __restrict__ out,
+                              int64_t nnz) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nnz) out[dest[q]] = v[q];
+}
+}  // namespace
+
+// The element matrices the kernels read: the caller's array for a mesh analysis; for a CSR
+// analysis, the caller's CSR values scattered into the arrowhead elements (F->d_elemvals).
+static int element_values(mf_factors* F, const double* d_values, cudaStream_t s, const double** out) {
+    *out = d_values;
+    const mf_analysis* a = F->a;
+    if (a->csr_n == 0) return MF_OK;
+    const int64_t nnz = a->csr_nnz;
+    if (nnz > 0) {
+        int slot = prof_begin(F, s, FAM_OTHER, 24.0 * nnz, 0.0);
+        k_csr_scatter<<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(d_values, F->d_csr_dest, F->d_elemvals, nnz);
+        prof_end(F, s, slot);
+        CUDA_TRY(cudaGetLastError());
+    }
+    *out = F->d_elemvals;
+    return MF_OK;
+}
 
 template <typename T>
 static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
@@ -1433,6 +1471,10 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
 
 extern "C" int mf_factor(mf_factors* F, const double* d_values, mf_stream_t stream) {
     if (!F || !d_values) return MF_EINVAL;
+    {
+        int rc0 = element_values(F, d_values, (cudaStream_t)stream, &d_values);
+        if (rc0) return rc0;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     int rc = run_graph(F, 0, d_values, nullptr, nullptr, 0, s, [&](cudaStream_t st) {
         return F->prec == MF_F64 ? run_factor<double>(F, d_values, st) : run_factor<float>(F, d_values, st);
@@ -1757,11 +1799,13 @@ static int residual_into(const mf_factors* Fc, const double* d_values, const dou
 extern "C" int mf_residual(const mf_factors* F, const double* d_values, const double* d_x, const double* d_b, double* d_r,
                            int nrhs, mf_stream_t stream) {
     if (!F || !d_values || !d_x || !d_b || !d_r || nrhs < 1 || nrhs > F->max_nrhs) return MF_EINVAL;
+    int rc = element_values(const_cast<mf_factors*>(F), d_values, (cudaStream_t)stream, &d_values);
+    if (rc) return rc;
     return residual_into(F, d_values, d_x, d_b, d_r, nrhs, (cudaStream_t)stream);
 }
 
 // row sums of |A| (trans: column sums, the row sums of |A^T|), element by element
-static int compute_rowabs(mf_factors* F, const double* d_values, cudaStream_t s, bool trans = false) {
+static int compute_rowabs(mf_factors* F, const double* d_values, const double* key, cudaStream_t s, bool trans = false) {
     const mf_analysis* a = F->a;
     const int64_t nE = a->n_elem * a->npe;
     dim3 g1((unsigned)((nE + 255) / 256), 1);
@@ -1773,11 +1817,11 @@ static int compute_rowabs(mf_factors* F, const double* d_values, cudaStream_t s,
     CUDA_TRY(cudaGetLastError());
     if (trans) {
         F->colabs_valid = true;
-        F->colabs_values = d_values;
+        F->colabs_values = key;
         return MF_OK;
     }
     F->rowabs_valid = true;
-    F->rowabs_values = d_values;
+    F->rowabs_values = key;
     return MF_OK;
 }
 
@@ -1791,10 +1835,12 @@ static int refine_impl(mf_factors* F, const double* d_values, const double* d_b,
     const mf_analysis* a = F->a;
     const int64_t n = a->n_dof;
     int rc;
-    if (!trans && (!F->rowabs_valid || F->rowabs_values != d_values))
-        if ((rc = compute_rowabs(F, d_values, s))) return rc;
-    if (trans && (!F->colabs_valid || F->colabs_values != d_values))
-        if ((rc = compute_rowabs(F, d_values, s, true))) return rc;
+    const double* key = d_values;  // the caller's array names the cached row sums
+    if ((rc = element_values(F, d_values, s, &d_values))) return rc;
+    if (!trans && (!F->rowabs_valid || F->rowabs_values != key))
+        if ((rc = compute_rowabs(F, d_values, key, s))) return rc;
+    if (trans && (!F->colabs_valid || F->colabs_values != key))
+        if ((rc = compute_rowabs(F, d_values, key, s, true))) return rc;
     const double* anorm_rows = trans ? F->d_colabs : F->d_rowabs;
     const int kind0 = trans ? 5 : 1;  // graph kinds of the first solve and of one correction
     // the residual and its norms after the current x (device only)
@@ -1874,6 +1920,7 @@ extern "C" int mf_element_grad(const mf_factors* F, const double* d_dvalues, con
                                double* d_grad, mf_stream_t stream) {
     if (!F || !d_dvalues || !d_lambda || !d_x || !d_grad) return MF_EINVAL;
     const mf_analysis* a = F->a;
+    if (a->csr_n > 0) return MF_ENOTSUP;  // a CSR matrix has no elements to differentiate by
     int64_t threads = a->n_elem * 32;
     k_element_grad<<<(unsigned)((threads + 255) / 256), 256, 0, (cudaStream_t)stream>>>(d_dvalues, F->d_en, d_lambda, d_x,
                                                                                          d_grad, a->n_elem, a->npe);
@@ -1885,6 +1932,7 @@ extern "C" int mf_element_outer(const mf_factors* F, const double* d_lambda, con
                                 mf_stream_t stream) {
     if (!F || !d_lambda || !d_x || !d_gradK || nrhs < 1) return MF_EINVAL;
     const mf_analysis* a = F->a;
+    if (a->csr_n > 0) return MF_ENOTSUP;
     int64_t n = a->n_elem * a->npe * a->npe;
     k_element_outer<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(F->d_en, d_lambda, d_x, d_gradK,
                                                                                     a->n_elem, a->npe, a->n_dof, nrhs);

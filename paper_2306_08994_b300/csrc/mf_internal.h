@@ -58,6 +58,11 @@ struct mf_analysis {
     std::vector<int64_t> node_inc;
     int64_t factor_size = 0, cb_size = 0, vec_size = 0, inv_size = 0, ys_size = 0;
     mf_info info{};
+    // CSR input (mf_analyze_csr): the matrix is split into one arrowhead element per vertex; the
+    // numeric entry points take the caller's CSR values and scatter entry q to element-array
+    // position csr_dest[q] (n_elem * npe * npe doubles, zero elsewhere)
+    int64_t csr_n = 0, csr_nnz = 0;  // csr_n = 0: a mesh analysis
+    std::vector<int64_t> csr_dest;
 };
 
 // Upper bounds on m of the fused small-front kernel's size buckets (FP64
@@ -78,7 +83,9 @@ struct HostTree {
 };
 
 int mf_build_tree(const mf_mesh_desc* mesh, HostTree& t);
-int mf_symbolic(const mf_mesh_desc* meshes, int count, const mf_options* opt, mf_analysis* a);
+// pretree (count == 1 only): use this element tree instead of cutting one from the mesh geometry
+int mf_symbolic(const mf_mesh_desc* meshes, int count, const mf_options* opt, mf_analysis* a,
+                const HostTree* pretree = nullptr);
 
 // Options with defaults filled in.
 mf_options mf_resolve_options(const mf_options* opt);

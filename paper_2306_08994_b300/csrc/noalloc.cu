@@ -7,8 +7,10 @@
 // allocation through its own pool, or in a real-time loop where an
 // allocation's implicit synchronisation is not allowed.  Such callers pass
 // their own inputs and output; the only work space is the file-scope array
-// below, which the library's module holds on every device that loads it
-// until the process exits.
+// below, which a device holds from the moment the library's device code is
+// loaded there until the process exits.  Under CUDA's lazy module loading
+// (the default) that is the first call of this entry point on the device:
+// that set-up call may take device memory once, later calls take none.
 //
 // Contract (also stated in include/mfsolve.h):
 //  * n_dof * nrhs must not exceed MF_NOALLOC_MAX_ENTRIES (1 << 20 doubles,

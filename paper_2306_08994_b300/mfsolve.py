@@ -82,7 +82,8 @@ class mf_tune_info(ctypes.Structure):
 
 
 # every symbol include/mfsolve.h declares
-EXPORTS = ["mf_default_options", "mf_strerror", "mf_analyze_mesh", "mf_analyze_batch", "mf_analysis_info",
+EXPORTS = ["mf_default_options", "mf_strerror", "mf_analyze_mesh", "mf_analyze_batch", "mf_analyze_csr",
+           "mf_analysis_info",
            "mf_analysis_export", "mf_factors_create", "mf_factor", "mf_solve", "mf_solve_adjoint", "mf_refine_solve",
            "mf_refine_solve_adjoint", "mf_residual", "mf_element_grad", "mf_element_outer", "mf_status",
            "mf_factors_export_front",
@@ -106,6 +107,7 @@ def _load():
     sig = {
         "mf_default_options": ([P], None), "mf_strerror": ([I], ctypes.c_char_p),
         "mf_analyze_mesh": ([P, P, P], I), "mf_analyze_batch": ([P, I, P, P], I),
+        "mf_analyze_csr": ([I64, P, P, P, P], I),
         "mf_analysis_info": ([P, P], I), "mf_analysis_export": ([P, P, P, P, P, P, P], I),
         "mf_factors_create": ([P, P, P], I), "mf_factor": ([P, P, P], I),
         "mf_solve": ([P, P, I, P], I), "mf_solve_adjoint": ([P, P, I, P], I),
@@ -209,12 +211,33 @@ class Analysis:
         _check(_lib.mf_analyze_batch(descs, len(self.meshes), ctypes.byref(self.options), ctypes.byref(h)),
                "mf_analyze_batch")
         self._h = h
+        self._load_info()
+        self.npe = int(self.meshes[0].elem_nodes.shape[1])
+
+    @classmethod
+    def from_csr(cls, n: int, rowptr: np.ndarray, col: np.ndarray, options: Optional[mf_options] = None):
+        """mf_analyze_csr: analysis of a general sparse matrix from its CSR pattern (host arrays).
+        The numeric calls on its factors take the CSR values (device, rowptr[n] doubles)."""
+        self = cls.__new__(cls)
+        self.meshes = []
+        self.options = options or default_options()
+        rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+        cl = np.ascontiguousarray(col, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(_lib.mf_analyze_csr(int(n), _ptr(rp), _ptr(cl), ctypes.byref(self.options), ctypes.byref(h)),
+               "mf_analyze_csr")
+        self._h = h
+        self._load_info()
+        self.npe = None  # no mesh elements: the element-gradient calls are not available
+        self.nnz = int(rp[-1])
+        return self
+
+    def _load_info(self):
         i = mf_info()
         _check(_lib.mf_analysis_info(self._h, ctypes.byref(i)), "mf_analysis_info")
         self.info = {f: getattr(i, f) for f, _ in mf_info._fields_}
         self.n_dof = int(i.n_dof)
         self.n_front = int(i.n_front)
-        self.npe = int(self.meshes[0].elem_nodes.shape[1])
         self.n_elem = int(i.n_elem)
 
     def export(self) -> dict:

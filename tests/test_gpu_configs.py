@@ -233,3 +233,33 @@ def test_headline_512_q3_tuned_plan_against_the_oracle():
           f"{i1['iterations']} corrections; refined eta {i2['backward_error']:.2e} after {i2['iterations']}; "
           f"rel. error vs oracle {err:.2e}; rel. error at the stop {np.linalg.norm(x_stop - xo) / np.linalg.norm(xo):.2e}")
     assert err <= 1e-10, (err, i2)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_l2_projection_near_3e5_dofs_against_the_oracle(p):
+    """The paper's model problem at its largest size (about 3e5 dofs, Sec. 4) for p = 1, 2, 3:
+    FP32 fronts + FP64 refinement and the FP64 path, each against the oracle's solution."""
+    pr = F.l2_projection(F.L2_SIZES[p], p)
+    pm = pr.mesh
+    assert 2.5e5 <= pm.n_nodes <= 3.0e5
+    s = O.OracleSolver(pm.n_nodes, pm.elem_nodes, O.tree_bisection(pm.nel))
+    assert s.factor(F.to_colmajor(pr.Ke), nthreads=O.max_threads()) == 0
+    xo, _ = s.solve_refined(pr.b[:, 0])
+    vals = torch.tensor(F.to_colmajor(pr.Ke), device=DEV)
+    b = torch.tensor(pr.b[:, 0], device=DEV)
+    for prec in ("f32", "f64"):
+        an = M.Analysis(M.Mesh(pm.elem_nodes, pm.n_nodes, 2, grid_dims=pm.nel),
+                        M.default_options(precision=prec, use_graph=1))
+        f = M.Factors(an)
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            x = torch.empty_like(b)
+            f.factor(vals, stream=stream)
+            info = f.refine_solve(vals, b, x, tol=1e-15, maxit=30, stream=stream)
+            stream.synchronize()
+        assert f.status()["rc"] == 0
+        assert info["backward_error"] <= 1e-12, (prec, info)
+        xg = x.cpu().numpy()
+        assert _eta_host(pm, pr.Ke, xg, pr.b[:, 0]) <= 1e-12
+        err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+        assert err <= 1e-10, (p, prec, err, info)

@@ -76,6 +76,10 @@ CASES = {
     "q3_24_lookahead": (lambda: F.diffusion_2d(24, 3, seed=38), {"small_front_max": 16, "super_panel": 64}),
     "q3_24_no_lookahead": (lambda: F.diffusion_2d(24, 3, seed=38), {"small_front_max": 16, "super_panel": 64,
                                                                     "lookahead": -1}),
+    # the paper's own model problem: L2-projection mass matrices (no boundary condition), p = 1, 2, 3
+    "l2_q1_32": (lambda: F.l2_projection(32, 1), {}),
+    "l2_q2_16_large_path": (lambda: F.l2_projection(16, 2), {"small_front_max": 16}),
+    "l2_q3_12": (lambda: F.l2_projection(12, 3), {"small_front_max": 48}),
 }
 
 

@@ -474,3 +474,65 @@ def test_openmp_class_parallel_factor_is_bitwise_serial():
     s2 = _solver(pr.mesh)
     s2.factor(K, nthreads=4)
     assert np.array_equal(s1.solve(pr.b), s2.solve(pr.b))
+
+
+# ------------------------------------------------- L2-projection workload
+def test_q1_element_mass_closed_form():
+    """Bilinear unit-square mass matrix, lexicographic local order: (1/36)[[4,2,2,1],...]."""
+    M = F.reference_mass(2, 1)
+    ref = np.array([[4, 2, 2, 1], [2, 4, 1, 2], [2, 1, 4, 2], [1, 2, 2, 4]]) / 36.0
+    assert np.allclose(M, ref, atol=1e-16)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_mass_entries_sum_to_the_area(p):
+    """Partition of unity: sum_ab int phi_a phi_b = int 1 over the unit square = 1 (any order)."""
+    assert abs(F.reference_mass(2, p).sum() - 1.0) < 1e-14
+    pr = F.l2_projection(5, p)
+    A = F.assemble_dense(pr.mesh, pr.Ke)
+    assert abs(A.sum() - 1.0) < 1e-13
+    assert np.allclose(A, A.T) and np.linalg.eigvalsh(A).min() > 0
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_l2_projection_reproduces_the_discrete_space(p):
+    """The L2 projection onto Qp is the identity on Qp: projecting f = x^p y^(p-1) + x y (a member
+    of Qp) with the oracle returns f at every node up to rounding."""
+    f = lambda x, y, z=None: x ** p * y ** (p - 1) + x * y
+    pr = F.l2_projection(6, p, f)
+    s = _solver(pr.mesh)
+    assert s.factor(F.to_colmajor(pr.Ke)) == 0
+    u, _ = s.solve_refined(pr.b)
+    c = pr.mesh.node_coords
+    assert np.abs(u[:, 0] - f(c[:, 0], c[:, 1])).max() <= 1e-12
+
+
+def _l2_error(pr, u, f):
+    """||u_h - f||_L2 over the unit square, element by element with (p+3)^2 Gauss points."""
+    m = pr.mesh
+    t, w = F.gauss_legendre_01(m.p + 3)
+    V, _ = F.lagrange_1d(m.p, t)
+    phi = np.einsum("aq,br->barq", V, V).reshape((m.p + 1) ** 2, -1)   # x-fastest local, x-fastest points
+    qx, qy = np.meshgrid(t, t, indexing="xy")
+    wq = np.outer(w, w).ravel()
+    org = m.node_coords[m.elem_nodes[:, 0]]
+    X = org[:, 0:1] + m.h * qx.ravel()[None, :]
+    Y = org[:, 1:2] + m.h * qy.ravel()[None, :]
+    uq = u[m.elem_nodes] @ phi
+    return float(np.sqrt(((uq - f(X, Y)) ** 2 * wq[None, :]).sum() * m.h ** 2))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_l2_projection_converges_at_order_p_plus_1(p):
+    """For a smooth f the L2-projection error ||u_h - f||_L2 (quadrature of degree 2p+5 per
+    element) falls like h^(p+1): halving h divides it by about 2^(p+1)."""
+    errs = []
+    for n in (4, 8, 16):
+        pr = F.l2_projection(n, p)
+        s = _solver(pr.mesh)
+        assert s.factor(F.to_colmajor(pr.Ke)) == 0
+        u, _ = s.solve_refined(pr.b)
+        errs.append(_l2_error(pr, u[:, 0], F.l2_field))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    lo, hi = 0.8 * 2 ** (p + 1), 1.25 * 2 ** (p + 1)
+    assert lo <= r2 <= hi and r1 >= 0.6 * 2 ** (p + 1), (errs, r1, r2)
