@@ -100,6 +100,9 @@ typedef struct {
                              takes its share of the pending update (every pivot of its super-panel
                              so far) and is factored on a second stream while the rest of the update
                              runs; 0 = on (default), < 0 = off */
+    int root_f64;         /* FP32-family fronts: the pivot blocks of the large fronts in the top
+                             root_f64 Foata classes (1 = the root's class) are factored and inverted
+                             in FP64 from the FP32 front and rounded once to FP32; 0 = none (default) */
 } mf_options;
 
 typedef struct {

@@ -42,6 +42,7 @@ struct Launch {
     int bucket = -1;  // fused: size bucket (index into kFusedBounds)
     int threads = 0;  // fused: threads per CTA
     int stream = 0;   // 0: the caller's stream; 1: the side stream (pivot-block inverses); 2: the lookahead stream
+    int wide = 0;     // K_PDIAG of FP32 fronts: factor the pivot blocks in FP64 (root separator classes)
 };
 
 // Solve plan of one class: fronts split by size (see kernels_solve.cuh).
@@ -481,6 +482,8 @@ static int build_plan(mf_factors* F) {
         return (a0 + b0) * (b0 - a0 + 1) / 2.0 + 2.0 * (b0 * (b0 + 1) * (2 * b0 + 1) / 6.0 - (a0 - 1) * a0 * (2 * a0 - 1) / 6.0);
     };
     int cur_stream = 0;  // stream the launches being planned go to
+    // FP32-family fronts in the top root_f64 classes factor their pivot blocks in FP64
+    auto wide_pdiag = [&](int c) { return F->prec != MF_F64 && F->opt.root_f64 > 0 && c >= a->n_cls - F->opt.root_f64; };
     auto push = [&](Launch L, int fam, double bytes, double flops) {
         L.stream = cur_stream;
         F->plan.push_back(L);
@@ -835,6 +838,7 @@ static int build_plan(mf_factors* F) {
                     pf += 2.0 * w * w * w;
                 }
                 push({K_PDIAG, c, (int)(pan.size() - poff), 0, poff}, FAM_PANEL, pb, pf);
+                F->plan.back().wide = wide_pdiag(c);
             }
             if (la_pending) {  // main waits for the lookahead pivot block before the panel products
                 push({K_SYNC, c, 0, 0, F->n_sync++, 2}, FAM_OTHER, 0.0, 0.0);
@@ -883,6 +887,7 @@ static int build_plan(mf_factors* F) {
                     F->plan.back().stream = 2;
                     cur_stream = 2;
                     push({K_PDIAG, c, (int)(pan.size() - poff), 0, poff}, FAM_PANEL, pb, pf);
+                    F->plan.back().wide = wide_pdiag(c);
                     cur_stream = 0;
                 }
             }
@@ -1328,7 +1333,12 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
                                   : cudaFuncSetAttribute(k_panel_diag_blk<float, kPanelNB32>,
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                          (int)panel_diag_dyn_smem<float, kPanelNB32>());
-        if (e != cudaSuccess) {
+        const cudaError_t e2 = F->prec == MF_F64
+                                   ? cudaSuccess
+                                   : cudaFuncSetAttribute(k_panel_diag_blk<float, kPanelNB32, double>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)panel_diag_dyn_smem<float, kPanelNB32, double>());
+        if (e != cudaSuccess || e2 != cudaSuccess) {
             (void)cudaGetLastError();
             free_factors(F);
             return MF_ECUDA;
@@ -1431,6 +1441,13 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
                 break;
             case K_PDIAG: {
                 constexpr int NB = sizeof(T) == 8 ? kPanelNB64 : kPanelNB32;
+                if constexpr (sizeof(T) == 4) {
+                    if (L.wide) {
+                        k_panel_diag_blk<T, NB, double><<<L.count, 256, panel_diag_dyn_smem<T, NB, double>(), s>>>(
+                            F->d_fronts, F->d_panel + L.off, fac, (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
+                        break;
+                    }
+                }
                 k_panel_diag_blk<T, NB><<<L.count, 256, panel_diag_dyn_smem<T, NB>(), s>>>(F->d_fronts, F->d_panel + L.off, fac,
                                                                             (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
                 break;

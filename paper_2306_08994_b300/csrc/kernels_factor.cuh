@@ -400,9 +400,13 @@ struct DiagTask {
     int32_t front, kb, w, pre;
     int64_t slot;  // panel-slot offset (64 x 64, column-major, ld 64)
 };
-// dynamic shared memory of k_panel_diag_blk (the U block of the lookahead update)
-template <typename T, int NB>
-constexpr size_t panel_diag_dyn_smem() { return (size_t)NB * (NB + 1) * sizeof(T); }
+// dynamic shared memory of k_panel_diag_blk: the U block of the lookahead update (storage type T),
+// and with a wider compute type C also the working block D and the inverse block Z (C each)
+template <typename T, int NB, typename C = T>
+constexpr size_t panel_diag_dyn_smem() {
+    return ((size_t)NB * (NB + 1) * sizeof(T) + 15) / 16 * 16 +
+           (sizeof(C) == sizeof(T) ? 0 : 2 * (size_t)NB * (NB + 1) * sizeof(C));
+}
 
 // Pivot block of a large front (NB x NB at pivot kb, padded with the
 // identity beyond w): partial LU in place (L with its diagonal, unit U) and
@@ -420,16 +424,21 @@ constexpr size_t panel_diag_dyn_smem() { return (size_t)NB * (NB + 1) * sizeof(T
 // Three block barriers per sub-block.  The inverses then come column by
 // column, one thread per column of L_D^-1 (L_D x = e_c) and of U_D^-1
 // (U_D y = e_c), each column in registers.
-template <typename T, int NB>
-__global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __restrict__ fronts,
+// C is the arithmetic of the block (T by default).  With T = float and
+// C = double the block is factored and inverted in FP64 from the FP32 front
+// and rounded once on the way out: the FP64 pivot blocks of the root
+// separator fronts on the FP32-front path.
+template <typename T, int NB, typename C = T>
+__global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_diag_blk(const FrontDev* __restrict__ fronts,
                                                         const DiagTask* __restrict__ tasks, T* __restrict__ fac,
                                                         T* __restrict__ slots, const unsigned int* __restrict__ famax,
                                                         double tol_rel, DevStatus* st) {
     constexpr int NBB = NB / 16;
     static_assert(NB % 16 == 0 && NBB <= 4, "NB must be 16, 32, 48 or 64");
-    __shared__ T D[NB][NB + 1];
-    __shared__ T Z[NB][NB + 1];
-    __shared__ T rdiag[NB];
+    constexpr bool kWide = sizeof(C) != sizeof(T);  // D and Z in dynamic shared memory
+    __shared__ C Dst[kWide ? 1 : NB][NB + 1];
+    __shared__ C Zst[kWide ? 1 : NB][NB + 1];
+    __shared__ C rdiag[NB];
     const DiagTask t = tasks[blockIdx.x];
     const FrontDev fr = fronts[t.front];
     const int m = fr.m, kb = t.kb, w = t.w;
@@ -437,6 +446,12 @@ __global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __res
     T* P = fac + fr.P_off;
     extern __shared__ __align__(16) unsigned char pd_dyn[];
     T* Us = reinterpret_cast<T*>(pd_dyn);  // U slice of the lookahead update, NB x (NB + 1)
+    C(*D)[NB + 1] = Dst;
+    C(*Z)[NB + 1] = Zst;
+    if constexpr (kWide) {
+        D = reinterpret_cast<C(*)[NB + 1]>(pd_dyn + ((size_t)NB * (NB + 1) * sizeof(T) + 15) / 16 * 16);
+        Z = D + NB;
+    }
     const int pre = t.pre, p0 = kb - t.pre;
     // L slice (rows kb.., columns p0 + c0..) into Z, U slice (rows p0 + c0.., columns kb..) into Us,
     // zero outside w x cw and cw x w, so the identity padding of D takes no update
@@ -444,16 +459,24 @@ __global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __res
         const int cw = min(NB, pre - c0);
         for (int j = warp; j < NB; j += 8)
             for (int i = lane; i < NB; i += 32) {
-                if (i < w && j < cw) cp_async_elem(&Z[i][j], P + (kb + i) + (int64_t)(p0 + c0 + j) * m);
-                else Z[i][j] = T(0);
+                if (i < w && j < cw) {
+                    if constexpr (kWide) Z[i][j] = (C)P[(kb + i) + (int64_t)(p0 + c0 + j) * m];
+                    else cp_async_elem(&Z[i][j], P + (kb + i) + (int64_t)(p0 + c0 + j) * m);
+                } else {
+                    Z[i][j] = C(0);
+                }
                 if (i < cw && j < w) cp_async_elem(&Us[i * (NB + 1) + j], P + (p0 + c0 + i) + (int64_t)(kb + j) * m);
                 else Us[i * (NB + 1) + j] = T(0);
             }
     };
     for (int j = warp; j < NB; j += 8)
         for (int i = lane; i < NB; i += 32) {
-            if (i < w && j < w) cp_async_elem(&D[i][j], P + (kb + i) + (int64_t)(kb + j) * m);
-            else D[i][j] = (i == j) ? T(1) : T(0);
+            if (i < w && j < w) {
+                if constexpr (kWide) D[i][j] = (C)P[(kb + i) + (int64_t)(kb + j) * m];
+                else cp_async_elem(&D[i][j], P + (kb + i) + (int64_t)(kb + j) * m);
+            } else {
+                D[i][j] = (i == j) ? C(1) : C(0);
+            }
         }
     if (pre > 0) stage(0);
     cp_async_wait_all();
@@ -462,11 +485,11 @@ __global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __res
         // the block's share of the pending update, pre pivots deep, NB at a time
         constexpr int RPT = NB / 16;  // RPT x RPT outputs per thread
         const int ti = tid >> 4, tj = tid & 15;
-        T acc[RPT][RPT];
+        C acc[RPT][RPT];
 #pragma unroll
         for (int r = 0; r < RPT; r++)
 #pragma unroll
-            for (int c = 0; c < RPT; c++) acc[r][c] = T(0);
+            for (int c = 0; c < RPT; c++) acc[r][c] = C(0);
         for (int c0 = 0; c0 < pre; c0 += NB) {
             if (c0 > 0) {
                 __syncthreads();  // the previous slice is consumed
@@ -476,11 +499,11 @@ __global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __res
             }
             const int cw = min(NB, pre - c0);
             for (int q = 0; q < cw; q++) {
-                T av[RPT], bv[RPT];
+                C av[RPT], bv[RPT];
 #pragma unroll
                 for (int r = 0; r < RPT; r++) {
                     av[r] = Z[ti * RPT + r][q];
-                    bv[r] = Us[q * (NB + 1) + tj * RPT + r];
+                    bv[r] = (C)Us[q * (NB + 1) + tj * RPT + r];
                 }
 #pragma unroll
                 for (int r = 0; r < RPT; r++)
@@ -494,28 +517,28 @@ __global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __res
             for (int c = 0; c < RPT; c++) D[ti * RPT + r][tj * RPT + c] -= acc[r][c];
         __syncthreads();
     }
-    const T amax = (T)__uint_as_float(famax[t.front]);
-    const T thr = (T)tol_rel * amax > T(0) ? (T)tol_rel * amax : tiny_pivot<T>();
+    const C amax = (C)__uint_as_float(famax[t.front]);
+    const C thr = (C)tol_rel * amax > C(0) ? (C)tol_rel * amax : (C)tiny_pivot<T>();
 
     for (int kk = 0; kk < NBB; kk++) {
         const int o = 16 * kk;
         // (1) diagonal sub-block: Table 2 tasks T1 (divide the pivot row), T2/T3 (update)
         if (warp == 0) {
             const int r = lane & 15, h = lane >> 4;
-            T a[8];
+            C a[8];
 #pragma unroll
             for (int e = 0; e < 8; e++) a[e] = D[o + r][o + 8 * h + e];
 #pragma unroll
             for (int p = 0; p < 16; p++) {
-                const T pv = __shfl_sync(0xffffffffu, a[p & 7], p + 16 * (p >> 3));
-                T piv = pv;
+                const C pv = __shfl_sync(0xffffffffu, a[p & 7], p + 16 * (p >> 3));
+                C piv = pv;
                 if (o + p < w) piv = checked_pivot(pv, thr, lane == 0, t.front, kb + o + p, st);
-                const T rinv = T(1) / piv;
-                const T lr = __shfl_sync(0xffffffffu, a[p & 7], r + 16 * (p >> 3));
+                const C rinv = C(1) / piv;
+                const C lr = __shfl_sync(0xffffffffu, a[p & 7], r + 16 * (p >> 3));
 #pragma unroll
                 for (int e = 0; e < 8; e++) {
                     const int j = 8 * h + e;
-                    const T uj = __shfl_sync(0xffffffffu, a[e], p + 16 * h) * rinv;
+                    const C uj = __shfl_sync(0xffffffffu, a[e], p + 16 * h) * rinv;
                     if (r > p && j > p) a[e] -= lr * uj;
                     else if (r == p && j > p) a[e] = uj;
                     else if (r == p && j == p) a[e] = piv;
@@ -531,7 +554,7 @@ __global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __res
             // (2) L sub-panel rows: x U_kk = a (unit upper);  U sub-panel columns: L_kk y = a
             if (tid < R) {
                 const int i = o + 16 + tid;
-                T x[16];
+                C x[16];
 #pragma unroll
                 for (int c = 0; c < 16; c++) x[c] = D[i][o + c];
 #pragma unroll
@@ -542,7 +565,7 @@ __global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __res
                 for (int c = 0; c < 16; c++) D[i][o + c] = x[c];
             } else if (tid >= 128 && tid < 128 + R) {
                 const int j = o + 16 + (tid - 128);
-                T y[16];
+                C y[16];
 #pragma unroll
                 for (int q = 0; q < 16; q++) y[q] = D[o + q][j];
 #pragma unroll
@@ -557,18 +580,18 @@ __global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __res
             __syncthreads();
             // (3) trailing sub-blocks: A_ij -= L_i,kk U_kk,j
             const int nb = R / 16, tr = tid >> 4, tc = tid & 15;
-            T acc[3][3];
+            C acc[3][3];
 #pragma unroll
             for (int aa = 0; aa < 3; aa++)
 #pragma unroll
-                for (int bb = 0; bb < 3; bb++) acc[aa][bb] = T(0);
+                for (int bb = 0; bb < 3; bb++) acc[aa][bb] = C(0);
 #pragma unroll
             for (int q = 0; q < 16; q++) {
-                T lv[3], uv[3];
+                C lv[3], uv[3];
 #pragma unroll
                 for (int aa = 0; aa < 3; aa++) {
-                    lv[aa] = aa < nb ? D[o + 16 + tr + 16 * aa][o + q] : T(0);
-                    uv[aa] = aa < nb ? D[o + q][o + 16 + tc + 16 * aa] : T(0);
+                    lv[aa] = aa < nb ? D[o + 16 + tr + 16 * aa][o + q] : C(0);
+                    uv[aa] = aa < nb ? D[o + q][o + 16 + tc + 16 * aa] : C(0);
                 }
 #pragma unroll
                 for (int aa = 0; aa < 3; aa++)
@@ -585,7 +608,7 @@ __global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __res
     }
     // factored block back to P (coalesced)
     for (int j = warp; j < w; j += 8)
-        for (int i = lane; i < w; i += 32) P[(kb + i) + (int64_t)(kb + j) * m] = D[i][j];
+        for (int i = lane; i < w; i += 32) P[(kb + i) + (int64_t)(kb + j) * m] = (T)D[i][j];
 
     // ---- inverses, one thread per column: threads 0..NB-1 column c of L_D^-1 (forward),
     //      threads NB..2NB-1 column c of U_D^-1 (backward, unit diagonal).  Right-looking: once
@@ -593,13 +616,13 @@ __global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __res
     //      FMAs on a column held in registers (the D reads are warp-wide broadcasts).
     if (tid < 2 * NB) {
         const int c = tid % NB;
-        T a[NB];
+        C a[NB];
 #pragma unroll
-        for (int r = 0; r < NB; r++) a[r] = r == c ? T(1) : T(0);
+        for (int r = 0; r < NB; r++) a[r] = r == c ? C(1) : C(0);
         if (tid < NB) {
 #pragma unroll
             for (int r = 0; r < NB; r++) {
-                const T xr = a[r] * rdiag[r];
+                const C xr = a[r] * rdiag[r];
                 a[r] = xr;
 #pragma unroll
                 for (int r2 = r + 1; r2 < NB; r2++) a[r2] -= D[r2][r] * xr;
@@ -610,7 +633,7 @@ __global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __res
         } else {
 #pragma unroll
             for (int r = NB - 1; r > 0; r--) {
-                const T yr = a[r];
+                const C yr = a[r];
 #pragma unroll
                 for (int r2 = 0; r2 < r; r2++) a[r2] -= D[r2][r] * yr;
             }
@@ -622,7 +645,7 @@ __global__ void __launch_bounds__(256, 2) k_panel_diag_blk(const FrontDev* __res
     __syncthreads();
     T* Zg = slots + t.slot;
     for (int j = warp; j < w; j += 8)
-        for (int i = lane; i < w; i += 32) Zg[i + j * 64] = Z[i][j];
+        for (int i = lane; i < w; i += 32) Zg[i + j * 64] = (T)Z[i][j];
 }
 
 // ---------------------------------------------------------------------------

@@ -473,3 +473,47 @@ def test_fp32_family_factors_match_oracle_front_by_front(case, prec):
         worst = max(worst, max(eL, eU) / tol)
         assert eL <= tol and eU <= tol, (case, prec, g, eL, eU, tol)
     print(f"{case} {prec}: worst error / bound = {worst:.3f}")
+
+
+@pytest.mark.parametrize("case,root_f64", [("q3_24_large_path", 1), ("q3_24_large_path", 3), ("q1_3d_8", 2)])
+def test_fp64_root_pivot_blocks_factors_and_solution(case, root_f64):
+    """FP32 fronts whose top `root_f64` classes factor and invert their pivot blocks in FP64
+    (option root_f64): front by front within the FP32 bound of
+    test_fp32_family_factors_match_oracle_front_by_front, and the refined solution within 1e-10."""
+    mk, opt = FP32_CASES[case]
+    pr = mk()
+    a, f, vals = _setup(pr, "f32", root_f64=root_f64, **opt)
+    f.factor(vals)
+    assert f.status()["rc"] == 0
+    s = _oracle(pr)
+    ksub = np.asarray(s.k, dtype=np.int64).copy()
+    for v in range(s.n_front):
+        if s.parent[v] >= 0:
+            ksub[s.parent[v]] += ksub[v]
+    order = np.lexsort((np.arange(s.n_front), s.height))
+    top = s.n_classes - root_f64
+    checked = 0
+    for g in range(len(order)):
+        v = order[g]
+        if s.height[v] - 1 < top:
+            continue
+        Lo, Uo = s.factor_of(v)
+        k = Lo.shape[1]
+        if k == 0:
+            continue
+        Lg, Ug = f.export_front(g)
+        sc = max(np.abs(Lo).max(), np.abs(Uo).max(), 1.0)
+        tol = 4.0 * ksub[v] * 2.0 ** -24 * sc
+        low = np.tril(np.ones((Lo.shape[0], k), bool))
+        up = np.triu(np.ones((k, Uo.shape[1]), bool), 1)
+        assert np.abs(Lg - Lo)[low].max() <= tol, (g, root_f64)
+        if up.any():
+            assert np.abs(Ug - Uo)[up].max() <= tol, (g, root_f64)
+        checked += 1
+    assert checked >= 1
+    b = torch.tensor(np.ascontiguousarray(pr.b.T), device=DEV)
+    x = torch.empty_like(b)
+    info = f.refine_solve(vals, b, x, tol=1e-15, maxit=30)
+    xo, _ = s.solve_refined(pr.b)
+    err = np.linalg.norm(x.cpu().numpy().T - xo) / np.linalg.norm(xo)
+    assert info["backward_error"] <= 1e-12 and err <= 1e-10, (info, err)
