@@ -326,6 +326,11 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="direct launches instead of CUDA-graph replay")
+    ap.add_argument("--bf16-trial", action="store_true",
+                    help="also measure the tuned plan with BF16 Schur products on the largest fronts (MF_TF32_BF16, "
+                         "one and three BF16 passes): refinement contraction, corrections and step time")
+    ap.add_argument("--root-f64-trial", type=int, default=0,
+                    help="also measure the tuned plan with the pivot blocks of the top N classes in FP64")
     ap.add_argument("--tune", default="cache", choices=["off", "cache", "run"],
                     help="plan autotuner (untimed, before warm-up): off = default plan; cache = tuned plan from "
                          "the package's plan cache, tuning and recording it when missing; run = tune afresh")
@@ -497,6 +502,61 @@ def main():
         del x64_keep
         step(fac, vals, b, x)  # leave x as the headline's solution
 
+    def contraction_probe(f, maxc=12):
+        """Backward error after c = 0, 1, ... corrections (each probe restarts the refinement), and
+        the median ratio of consecutive values while they fall (the refinement's contraction)."""
+        etas = []
+        for c in range(maxc + 1):
+            pr_ = f.refine_solve(vals, b, x, tol=0.0, maxit=c, check=False)
+            etas.append(pr_["backward_error"])
+            if etas[-1] <= 1e-16 or not np.isfinite(etas[-1]):
+                break
+        ratios = [etas[i + 1] / etas[i] for i in range(len(etas) - 1) if etas[i] > 4e-16 and etas[i + 1] > 0]
+        return etas, (float(np.median(ratios)) if ratios else None)
+
+    def time_variant(opts_v):
+        """Factor time and factor + refined solve (eta <= 1e-12) time of a plan variant, K steps each."""
+        fv = M.Factors(an, opts_v)
+        fv.factor(vals)
+        etas, rho = contraction_probe(fv)
+        conv = min(etas) <= TOL
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fv.factor(vals)
+        e1.record(stream)
+        rv = None
+        if conv:
+            for _ in range(args.steps):
+                rv = step(fv, vals, b, x)
+        e2.record(stream)
+        barrier()
+        out = {"factor_ms": e0.elapsed_time(e1) / args.steps, "etas": etas, "contraction": rho, "converges": conv,
+               "step_ms": e1.elapsed_time(e2) / args.steps if conv else None,
+               "refine_iterations": rv["iterations"] if rv else None, "status": fv.status()["rc"]}
+        del fv
+        torch.cuda.empty_cache()
+        return out
+
+    trials = {}
+    if kind == "solve" and precision != "f64" and (args.bf16_trial or args.root_f64_trial):
+        import copy
+        trials["tuned"] = time_variant(opts)
+        if args.bf16_trial:
+            for passes in (1, 3):
+                o2 = copy.copy(opts)
+                o2.precision = M.MF_TF32_BF16
+                o2.bf16_passes = passes
+                if o2.tc_min_cb == 0:
+                    o2.tc_min_cb = 256
+                trials[f"bf16_{passes}pass"] = time_variant(o2)
+        if args.root_f64_trial:
+            o2 = copy.copy(opts)
+            o2.root_f64 = args.root_f64_trial
+            trials[f"root_f64_{args.root_f64_trial}"] = time_variant(o2)
+        step(fac, vals, b, x)
+
     # roofline: per-launch event timing (launch trace) over the same K steps; the dominant
     # kernel is the trace kind with the most device time
     fac.profile(True)
@@ -626,6 +686,7 @@ def main():
             "fp64_path": fp64,
             "speedup_vs_fp64": (fp64["ms"] / ms) if fp64 else None,
             "matched_accuracy": matched,
+            "trials": trials or None,
             "accuracy_note": ("value: refined path stopped at normwise backward error <= 1e-12; matched_accuracy: "
                               "the same path stopped at the FP64 path's own backward error; rel_residual = "
                               "||b - A x||_2 / ||b||_2 of the final iterate on both paths"),

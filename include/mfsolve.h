@@ -60,12 +60,16 @@ typedef struct CUstream_st* mf_stream_t;
 #define MF_F32 1   /* FP32 fronts, FP32 SIMT Schur GEMMs */
 #define MF_TF32 2  /* FP32 fronts, Schur GEMMs of large fronts on the tensor cores (tcgen05,
                       three-pass split TF32 = FP32-accurate products), FP32 accumulation */
+#define MF_TF32_BF16 3  /* as MF_TF32, but the Schur updates S -= L21 U12 (Sec. 2.2) of fronts with a
+                      contribution block of at least bf16_min_cb rows use BF16 tensor-core products
+                      (kind::f16, FP32 accumulation): one BF16 product (bf16_passes 1) or three
+                      split-BF16 products (bf16_passes 3) */
 
 /* Front-size buckets of the fused small-front kernel (upper bounds on m). */
 #define MF_FUSED_BUCKETS 9
 
 typedef struct {
-    int precision;        /* MF_F64 (default), MF_F32 or MF_TF32 */
+    int precision;        /* MF_F64 (default), MF_F32, MF_TF32 or MF_TF32_BF16 */
     double pivot_tol;     /* static pivot check: a pivot with |p| < pivot_tol * max|F| (max over its
                              front at assembly) is replaced by sign(p) * that bound (counted in
                              mf_status) or fails; <= 0 selects the unit roundoff of `precision` */
@@ -100,6 +104,9 @@ typedef struct {
                              takes its share of the pending update (every pivot of its super-panel
                              so far) and is factored on a second stream while the rest of the update
                              runs; 0 = on (default), < 0 = off */
+    int bf16_min_cb;      /* MF_TF32_BF16: smallest contribution block whose Schur update uses BF16
+                             products; 0 = 2048 */
+    int bf16_passes;      /* MF_TF32_BF16: 1 (default, also 0) = one BF16 product, 3 = hi/lo split */
     int root_f64;         /* FP32-family fronts: the pivot blocks of the large fronts in the top
                              root_f64 Foata classes (1 = the root's class) are factored and inverted
                              in FP64 from the FP32 front and rounded once to FP32; 0 = none (default) */

@@ -5,7 +5,7 @@ ABI of include/mfsolve.h); this package only binds it.  The binding is loaded
 on first use of any name below and raises ImportError if the library has not
 been built -- there is no fallback implementation.
 """
-_NAMES = {"MF_F32", "MF_F64", "MF_TF32", "Analysis", "Factors", "Mesh", "MFError", "default_options", "lib"}
+_NAMES = {"MF_F32", "MF_F64", "MF_TF32", "MF_TF32_BF16", "Analysis", "Factors", "Mesh", "MFError", "default_options", "lib"}
 
 __all__ = sorted(_NAMES | {"MFSolve"})
 

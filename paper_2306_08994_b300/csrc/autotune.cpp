@@ -191,7 +191,8 @@ extern "C" int mf_autotune(const mf_analysis* a, const double* d_values, const d
                            int reps, const char* cache_path, mf_options* best, mf_tune_info* info, mf_stream_t stream) {
     if (!a || !d_values || !d_b || !best || reps < 1) return MF_EINVAL;
     mf_options o = base ? mf_resolve_options(base) : a->opt;
-    if (o.precision != MF_F64 && o.precision != MF_F32 && o.precision != MF_TF32) return MF_EINVAL;
+    if (o.precision != MF_F64 && o.precision != MF_F32 && o.precision != MF_TF32 && o.precision != MF_TF32_BF16)
+        return MF_EINVAL;
     const int user_graph = o.use_graph;
     const std::string key = cache_key(a, o.precision);
     if (info) *info = mf_tune_info{};

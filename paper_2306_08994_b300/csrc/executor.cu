@@ -236,6 +236,7 @@ struct mf_factors {
     int nb = 32;
     int small_max = 96;
     int tc_min = 256;
+    int bf16_min = 2048;  // MF_TF32_BF16: smallest contribution block with BF16 Schur products
     int sp = 256;  // super-panel depth (pivots)
     int num_sms = 148;
     int max_nrhs = 4;
@@ -515,62 +516,75 @@ static int build_plan(mf_factors* F) {
     std::vector<TcC> tcc;
     int64_t tc_hi = 0;
     size_t tc_p0 = 0;
-    double tc_pb = 0, tc_gb = 0, tc_gf = 0;
-    auto use_tc = [&](int M, int N, int K) { return F->prec == MF_TF32 && std::min(M, N) >= F->tc_min && K >= 16; };
+    auto use_tc = [&](int M, int N, int K) {
+        return (F->prec == MF_TF32 || F->prec == MF_TF32_BF16) && std::min(M, N) >= F->tc_min && K >= 16;
+    };
+    // per product mode (tc::Mode): packing bytes, product bytes and flops of the pending products
+    double tc_pbm[3] = {0, 0, 0}, tc_gbm[3] = {0, 0, 0}, tc_gfm[3] = {0, 0, 0};
     auto tc_add = [&](int8_t aar, int64_t aoff, int lda, int8_t bar, int64_t boff, int ldb, int8_t car, int64_t coff,
-                      int ldc, int M, int N, int K, int8_t op = 0, int8_t am = 0, int8_t bm = 0) {
+                      int ldc, int M, int N, int K, int8_t op = 0, int8_t am = 0, int8_t bm = 0, int mode = tc::kTf32x3) {
         TcPack q{};
         q.a_ar = aar; q.a_off = aoff; q.lda = lda; q.a_mask = am;
         q.b_ar = bar; q.b_off = boff; q.ldb = ldb; q.b_mask = bm;
         q.M = M; q.N = N; q.K = K;
+        q.pad[0] = (int8_t)mode;
         q.nkc = (K + tc::kChunkK - 1) / tc::kChunkK;
         const int nra = (M + tc::kTileM - 1) / tc::kTileM, nrb = (N + tc::kTileN - 1) / tc::kTileN;
+        const int ca = tc::chunk_floats_a(mode), cbk = tc::chunk_floats_b(mode);
         q.a_hi = tc_hi;
-        tc_hi += (int64_t)nra * q.nkc * tc::kChunkA;
+        tc_hi += (int64_t)nra * q.nkc * ca;
         q.b_hi = tc_hi;
-        tc_hi += (int64_t)nrb * q.nkc * tc::kChunkB;
+        tc_hi += (int64_t)nrb * q.nkc * cbk;
         tcp.push_back(q);
         tcc.push_back({car, op, coff, ldc});
-        tc_gf += 2.0 * M * N * K;
-        tc_gb += T * ((double)M * K + (double)K * N + 2.0 * M * N);
-        tc_pb += T * ((double)M * K + (double)K * N) + 2.0 * 4.0 * ((double)nra * tc::kChunkA + (double)nrb * tc::kChunkB) * q.nkc;
+        tc_gfm[mode] += 2.0 * M * N * K;
+        tc_gbm[mode] += T * ((double)M * K + (double)K * N + 2.0 * M * N);
+        tc_pbm[mode] += T * ((double)M * K + (double)K * N) +
+                        (mode == tc::kBf16 ? 1.0 : 2.0) * 4.0 * ((double)nra * ca + (double)nrb * cbk) * q.nkc;
     };
     auto tc_end = [&](int c, int fam) {
         if (tcp.size() > tc_p0) {
-            const int64_t joff = (int64_t)tcj.size(), toff = (int64_t)gtc.size();
-            for (size_t qi = tc_p0; qi < tcp.size(); qi++) {
-                TcPack& q = tcp[qi];
-                q.lo_off = tc_hi;
-                const int nra = (q.M + tc::kTileM - 1) / tc::kTileM, nrb = (q.N + tc::kTileN - 1) / tc::kTileN;
-                for (int rt = 0; rt < nra; rt++)
-                    for (int kc = 0; kc < q.nkc; kc++) tcj.push_back({(int32_t)(qi - tc_p0), 0, rt, kc});
-                for (int rt = 0; rt < nrb; rt++)
-                    for (int kc = 0; kc < q.nkc; kc++) tcj.push_back({(int32_t)(qi - tc_p0), 1, rt, kc});
-                for (int rb = 0; rb < nrb; rb++)
-                    for (int ra = 0; ra < nra; ra++) {
-                        TcTile t{};
-                        t.a_hi = q.a_hi + (int64_t)ra * q.nkc * tc::kChunkA;
-                        t.b_hi = q.b_hi + (int64_t)rb * q.nkc * tc::kChunkB;
-                        t.lo_off = q.lo_off;
-                        const int i0 = ra * tc::kTileM, j0 = rb * tc::kTileN;
-                        t.c_ar = tcc[qi].car;
-                        t.op = tcc[qi].op;
-                        t.c_off = tcc[qi].coff + i0 + (int64_t)j0 * tcc[qi].ldc;
-                        t.ldc = tcc[qi].ldc;
-                        t.mrows = std::min(tc::kTileM, q.M - i0);
-                        t.ncols = std::min(tc::kTileN, q.N - j0);
-                        t.nkc = q.nkc;
-                        gtc.push_back(t);
-                    }
+            for (size_t qi = tc_p0; qi < tcp.size(); qi++) tcp[qi].lo_off = tc_hi;  // lo chunks after all hi chunks
+            for (int mode = 0; mode < 3; mode++) {  // one pack and one product launch per mode in use
+                const int64_t joff = (int64_t)tcj.size(), toff = (int64_t)gtc.size();
+                const int ca = tc::chunk_floats_a(mode), cbk = tc::chunk_floats_b(mode);
+                for (size_t qi = tc_p0; qi < tcp.size(); qi++) {
+                    TcPack& q = tcp[qi];
+                    if (q.pad[0] != mode) continue;
+                    const int nra = (q.M + tc::kTileM - 1) / tc::kTileM, nrb = (q.N + tc::kTileN - 1) / tc::kTileN;
+                    for (int rt = 0; rt < nra; rt++)
+                        for (int kc = 0; kc < q.nkc; kc++) tcj.push_back({(int32_t)(qi - tc_p0), 0, rt, kc});
+                    for (int rt = 0; rt < nrb; rt++)
+                        for (int kc = 0; kc < q.nkc; kc++) tcj.push_back({(int32_t)(qi - tc_p0), 1, rt, kc});
+                    for (int rb = 0; rb < nrb; rb++)
+                        for (int ra = 0; ra < nra; ra++) {
+                            TcTile t{};
+                            t.a_hi = q.a_hi + (int64_t)ra * q.nkc * ca;
+                            t.b_hi = q.b_hi + (int64_t)rb * q.nkc * cbk;
+                            t.lo_off = q.lo_off;
+                            const int i0 = ra * tc::kTileM, j0 = rb * tc::kTileN;
+                            t.c_ar = tcc[qi].car;
+                            t.op = tcc[qi].op;
+                            t.c_off = tcc[qi].coff + i0 + (int64_t)j0 * tcc[qi].ldc;
+                            t.ldc = tcc[qi].ldc;
+                            t.mrows = std::min(tc::kTileM, q.M - i0);
+                            t.ncols = std::min(tc::kTileN, q.N - j0);
+                            t.nkc = q.nkc;
+                            gtc.push_back(t);
+                        }
+                }
+                if (gtc.size() == (size_t)toff) continue;
+                push({K_TCPACK, c, (int)(tcj.size() - joff), 0, joff, (int)tc_p0}, fam, tc_pbm[mode], 0.0);
+                F->plan.back().wide = mode;
+                push({K_GEMMTC, c, (int)(gtc.size() - toff), 0, toff}, fam, tc_gbm[mode], tc_gfm[mode]);
+                F->plan.back().wide = mode;
             }
             int64_t& pks = cur_stream ? F->pk2_size : F->pk_size;  // one packed arena per stream
             pks = std::max(pks, 2 * tc_hi);
-            push({K_TCPACK, c, (int)(tcj.size() - joff), 0, joff, (int)tc_p0}, fam, tc_pb, 0.0);
-            push({K_GEMMTC, c, (int)(gtc.size() - toff), 0, toff}, fam, tc_gb, tc_gf);
         }
         tc_hi = 0;
         tc_p0 = tcp.size();
-        tc_pb = tc_gb = tc_gf = 0;
+        for (int mode = 0; mode < 3; mode++) tc_pbm[mode] = tc_gbm[mode] = tc_gfm[mode] = 0;
     };
     // subtree fusion of the bottom classes
     {
@@ -927,7 +941,9 @@ static int build_plan(mf_factors* F) {
             const int m = fr.m, k = fr.k, nc = m - k;
             if (nc <= 0 || k <= 0) continue;
             if (use_tc(nc, nc, k))
-                tc_add(AR_FAC, fr.P_off + k, m, AR_FAC, fr.R_off, k, AR_CB, fr.S_off, nc, nc, nc, k);
+                tc_add(AR_FAC, fr.P_off + k, m, AR_FAC, fr.R_off, k, AR_CB, fr.S_off, nc, nc, nc, k, 0, 0, 0,
+                       F->prec == MF_TF32_BF16 && nc >= F->bf16_min ? (F->opt.bf16_passes == 3 ? tc::kBf16x3 : tc::kBf16)
+                                                                    : tc::kTf32x3);
             else
                 gemm_tiles(fr.P_off + k, m, fr.R_off, k, fr.S_off, nc, nc, nc, k, 1);
         }
@@ -1165,7 +1181,9 @@ static int set_smem_limits() {
     CUDA_TRY(cudaFuncSetAttribute(k_bwd_cta<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_inv_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_subtree_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
+    CUDA_TRY(cudaFuncSetAttribute(k_schur_tc<tc::kTf32x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
+    CUDA_TRY(cudaFuncSetAttribute(k_schur_tc<tc::kBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
+    CUDA_TRY(cudaFuncSetAttribute(k_schur_tc<tc::kBf16x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
     CUDA_TRY(cudaFuncSetAttribute(k_subtree_fwd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_subtree_fwd<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
 #define SET_INV(TR, PH)                                                                                            \
@@ -1184,7 +1202,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     F->a = a;
     F->opt = opt ? mf_resolve_options(opt) : a->opt;
     F->prec = F->opt.precision;
-    if (F->prec != MF_F64 && F->prec != MF_F32 && F->prec != MF_TF32) {
+    if (F->prec != MF_F64 && F->prec != MF_F32 && F->prec != MF_TF32 && F->prec != MF_TF32_BF16) {
         delete F;
         return MF_EINVAL;
     }
@@ -1199,6 +1217,11 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     F->small_max = std::min(F->small_max, F->prec == MF_F64 ? 160 : 224);
     F->small_max = std::max(F->small_max, a->npe);
     F->tc_min = F->opt.tc_min_cb > 0 ? F->opt.tc_min_cb : 256;
+    F->bf16_min = F->opt.bf16_min_cb > 0 ? F->opt.bf16_min_cb : 2048;
+    if (F->opt.bf16_passes != 0 && F->opt.bf16_passes != 1 && F->opt.bf16_passes != 3) {
+        delete F;
+        return MF_EINVAL;
+    }
     F->use_sweep = F->opt.sweep_kernel != 0;
     {
         int dev = 0;
@@ -1466,14 +1489,24 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
             case K_TCPACK:
                 if constexpr (sizeof(T) == 4) {
                     Arenas<float> ar{{fac, cb, (float*)F->d_inv, (float*)F->d_scr, (float*)F->d_pnl}};
-                    k_tc_pack<<<L.count, 256, 0, s>>>(F->d_tcpack + L.bucket, F->d_tcjob + L.off, ar, pk);
+                    const TcPack* tp = F->d_tcpack + L.bucket;
+                    const TcPackJob* tj = F->d_tcjob + L.off;
+                    if (L.wide == tc::kBf16) k_tc_pack<tc::kBf16><<<L.count, 256, 0, s>>>(tp, tj, ar, pk);
+                    else if (L.wide == tc::kBf16x3) k_tc_pack<tc::kBf16x3><<<L.count, 256, 0, s>>>(tp, tj, ar, pk);
+                    else k_tc_pack<tc::kTf32x3><<<L.count, 256, 0, s>>>(tp, tj, ar, pk);
                 }
                 break;
             case K_GEMMTC:
                 if constexpr (sizeof(T) == 4) {
                     Arenas<float> ar{{fac, cb, (float*)F->d_inv, (float*)F->d_scr, (float*)F->d_pnl}};
-                    k_schur_tc<<<std::min(L.count, F->num_sms), kTcThreads, tc::kSmemBytes, s>>>(F->d_gtc + L.off, L.count,
-                                                                                                  pk, ar, F->d_status);
+                    const unsigned g = (unsigned)std::min(L.count, F->num_sms);
+                    const TcTile* tl = F->d_gtc + L.off;
+                    if (L.wide == tc::kBf16)
+                        k_schur_tc<tc::kBf16><<<g, kTcThreads, tc::kSmemBytes, s>>>(tl, L.count, pk, ar, F->d_status);
+                    else if (L.wide == tc::kBf16x3)
+                        k_schur_tc<tc::kBf16x3><<<g, kTcThreads, tc::kSmemBytes, s>>>(tl, L.count, pk, ar, F->d_status);
+                    else
+                        k_schur_tc<tc::kTf32x3><<<g, kTcThreads, tc::kSmemBytes, s>>>(tl, L.count, pk, ar, F->d_status);
                 }
                 break;
             case K_INVDIAG:

@@ -5,6 +5,10 @@
 // tf32(x - x_hi), and the product is accumulated as A_hi B_hi + A_hi B_lo +
 // A_lo B_hi (three MMAs per K slice): products accurate to about 2^-21
 // relative, FP32-grade Schur complements, which the FP64 refinement needs.
+// Two BF16 modes (kind::f16, BF16 operands, FP32 accumulation) serve the
+// MF_TF32_BF16 trial on the largest Schur updates: one BF16 product (x
+// rounded to BF16, about 2^-9 relative per product) or three split-BF16
+// products (hi = bf16(x), lo = bf16(x - hi): about 2^-17).
 //
 // Two kernels per class:
 //  * k_tc_pack splits L21 and U12 of every tensor-core front once into hi and
@@ -22,6 +26,8 @@
 //    records a timeout, waits (bounded) for its copies and MMAs in flight,
 //    frees its tensor memory and returns.
 #pragma once
+
+#include <cuda_bf16.h>
 
 #include <cstdint>
 
@@ -49,6 +55,19 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 // instruction descriptor: D f32, A/B tf32, both K-major, M x N
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// instruction descriptor of kind::f16: D f32, A/B bf16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
@@ -130,6 +149,27 @@ constexpr int kChunkA = kTileM * kChunkK;  // floats per A chunk (hi or lo): 8 K
 constexpr int kChunkB = kTileN * kChunkK;  // floats per B chunk: 16 KB
 constexpr int kStageBytes = 2 * 4 * (kChunkA + kChunkB);  // bytes: A_hi, A_lo, B_hi, B_lo
 constexpr int kSmemBytes = kStages * kStageBytes + 1024;
+
+// Product modes.  A chunk is one 16-wide K slice of a 128-row (A) or 256-row
+// (B) operand tile in the MMA's shared-memory image; a stage of the ring holds
+// kCps consecutive chunks of A and of B (hi, and lo where the mode has one),
+// 48 KB in every mode.  TF32 chunks: core matrix (row group r, K group g) at
+// r*512 + g*128 bytes (4 K groups of 4 values); BF16 chunks: at r*256 + g*128
+// (2 K groups of 8 values).
+enum Mode { kTf32x3 = 0, kBf16 = 1, kBf16x3 = 2 };
+template <int MODE>
+struct ModeCfg {
+    static constexpr bool kBf = MODE != kTf32x3;
+    static constexpr bool kLo = MODE != kBf16;
+    static constexpr int kCps = MODE == kTf32x3 ? 1 : MODE == kBf16 ? 4 : 2;       // chunks per stage
+    static constexpr int kFloatsA = kBf ? kChunkA / 2 : kChunkA;                    // floats per chunk
+    static constexpr int kFloatsB = kBf ? kChunkB / 2 : kChunkB;
+    static constexpr int kSbo = kBf ? 256 : 512;                                    // row-group stride
+    static constexpr int kStage = kCps * 4 * (kFloatsA + kFloatsB) * (kLo ? 2 : 1);  // bytes
+    static_assert(kStage == kStageBytes, "every mode fills the same ring");
+};
+__host__ __device__ constexpr int chunk_floats_a(int mode) { return mode == kTf32x3 ? kChunkA : kChunkA / 2; }
+__host__ __device__ constexpr int chunk_floats_b(int mode) { return mode == kTf32x3 ? kChunkB : kChunkB / 2; }
 constexpr uint32_t kTmemCols = 256;
 constexpr uint64_t kWaitLimit = 1000000000ull;  // 1 s
 
@@ -165,8 +205,10 @@ struct TcPackJob {
     int32_t task, which, rt, kc;
 };
 
+template <int MODE>
 __global__ void __launch_bounds__(256) k_tc_pack(const TcPack* __restrict__ tasks, const TcPackJob* __restrict__ jobs,
                                                  Arenas<float> ar, float* __restrict__ pk) {
+    using Cfg = tc::ModeCfg<MODE>;
     __shared__ float tile[tc::kTileN][tc::kChunkK + 1];
     const TcPackJob jb = jobs[blockIdx.x];
     const TcPack t = tasks[jb.task];
@@ -191,6 +233,27 @@ __global__ void __launch_bounds__(256) k_tc_pack(const TcPack* __restrict__ task
         tile[r][kk] = v;
     }
     __syncthreads();
+    if constexpr (Cfg::kBf) {
+        // BF16 image: 16-byte unit u = row (u / 16) * 8 + u % 8, K group (u / 8) % 2 (8 values each)
+        const int64_t chunk = (jb.which == 0 ? t.a_hi : t.b_hi) + ((int64_t)jb.rt * t.nkc + jb.kc) * rows * 8;
+        for (int u = threadIdx.x; u < rows * 2; u += blockDim.x) {
+            const int r = (u >> 4) * 8 + (u & 7), kk = ((u >> 3) & 1) * 8;
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const float v0 = tile[r][kk + 2 * e], v1 = tile[r][kk + 2 * e + 1];
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+                h[e] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                l[e] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            *reinterpret_cast<uint4*>(pk + chunk + 4 * u) = make_uint4(h[0], h[1], h[2], h[3]);
+            if constexpr (Cfg::kLo)
+                *reinterpret_cast<uint4*>(pk + t.lo_off + chunk + 4 * u) = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+        return;
+    }
     const int64_t chunk = (jb.which == 0 ? t.a_hi : t.b_hi) + ((int64_t)jb.rt * t.nkc + jb.kc) * rows * tc::kChunkK;
     for (int u = threadIdx.x; u < rows * 4; u += blockDim.x) {
         const int r = (u >> 5) * 8 + (u & 7), kk = ((u >> 3) & 3) * 4;
@@ -214,8 +277,10 @@ __global__ void __launch_bounds__(256) k_tc_pack(const TcPack* __restrict__ task
 // into C while tile i + 1 is being multiplied, then release it (acc_empty).
 constexpr int kTcThreads = 192;
 
+template <int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1) k_schur_tc(const TcTile* __restrict__ tiles, int ntiles,
                                                             const float* __restrict__ pk, Arenas<float> ar, DevStatus* st) {
+    using Cfg = tc::ModeCfg<MODE>;
     extern __shared__ __align__(128) unsigned char smem_tc[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_tc + tc::kStages * tc::kStageBytes);
     uint64_t* empty = full + tc::kStages;
@@ -253,25 +318,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_schur_tc(const TcTile* __rest
 
     if (warp == 0) {
         if (lane == 0) {  // producer
-            int g = 0;  // chunk counter across this CTA's tiles
+            int g = 0;  // stage counter across this CTA's tiles
             bool ok = true;
+            // stage layout: A_hi (kCps chunks), A_lo, B_hi, B_lo; a tile's last stage may hold fewer chunks
+            constexpr int kA = Cfg::kCps * Cfg::kFloatsA * 4, kB = Cfg::kCps * Cfg::kFloatsB * 4;
+            constexpr int kLoA = Cfg::kLo ? kA : 0;
             for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
                 const TcTile t = tiles[ti];
-                for (int c = 0; c < t.nkc; c++, g++) {
+                for (int c = 0; c < t.nkc; c += Cfg::kCps, g++) {
                     const int s = g % tc::kStages;
                     if (g >= tc::kStages) ok = tc::mbar_wait_bounded(&empty[s], ((g / tc::kStages) - 1) & 1, tc::kWaitLimit);
                     if (!ok || s_fail) {
                         ok = false;
                         break;
                     }
+                    const int nv = min(Cfg::kCps, t.nkc - c);
+                    const uint32_t ba = nv * Cfg::kFloatsA * 4, bb = nv * Cfg::kFloatsB * 4;
                     unsigned char* dst = smem_tc + s * tc::kStageBytes;
-                    tc::mbar_expect_tx(&full[s], tc::kStageBytes);
-                    const float* a = pk + t.a_hi + (int64_t)c * tc::kChunkA;
-                    const float* b = pk + t.b_hi + (int64_t)c * tc::kChunkB;
-                    tc::bulk_g2s(dst, a, tc::kChunkA * 4, &full[s]);
-                    tc::bulk_g2s(dst + tc::kChunkA * 4, a + t.lo_off, tc::kChunkA * 4, &full[s]);
-                    tc::bulk_g2s(dst + 2 * tc::kChunkA * 4, b, tc::kChunkB * 4, &full[s]);
-                    tc::bulk_g2s(dst + (2 * tc::kChunkA + tc::kChunkB) * 4, b + t.lo_off, tc::kChunkB * 4, &full[s]);
+                    tc::mbar_expect_tx(&full[s], (ba + bb) * (Cfg::kLo ? 2u : 1u));
+                    const float* a = pk + t.a_hi + (int64_t)c * Cfg::kFloatsA;
+                    const float* b = pk + t.b_hi + (int64_t)c * Cfg::kFloatsB;
+                    tc::bulk_g2s(dst, a, ba, &full[s]);
+                    if constexpr (Cfg::kLo) tc::bulk_g2s(dst + kA, a + t.lo_off, ba, &full[s]);
+                    tc::bulk_g2s(dst + kA + kLoA, b, bb, &full[s]);
+                    if constexpr (Cfg::kLo) tc::bulk_g2s(dst + kA + kLoA + kB, b + t.lo_off, bb, &full[s]);
                 }
             }
             if (!ok) {
@@ -284,7 +354,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_schur_tc(const TcTile* __rest
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
-            constexpr uint32_t idesc = tc::idesc_tf32(tc::kTileM, tc::kTileN);
+            constexpr uint32_t idesc = Cfg::kBf ? tc::idesc_bf16(tc::kTileM, tc::kTileN) : tc::idesc_tf32(tc::kTileM, tc::kTileN);
+            constexpr int kA = Cfg::kCps * Cfg::kFloatsA * 4, kB = Cfg::kCps * Cfg::kFloatsB * 4;
+            constexpr int kLoA = Cfg::kLo ? kA : 0;
             int g = 0, i = 0;
             bool ok = true;
             for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x, i++) {
@@ -294,7 +366,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_schur_tc(const TcTile* __rest
                 if (i >= 2) ok = tc::mbar_wait_bounded(&acc_empty[buf], ((i >> 1) - 1) & 1, tc::kWaitLimit);
                 if (!ok) break;
                 tc::fence_after_sync();
-                for (int c = 0; c < t.nkc; c++, g++) {
+                for (int c = 0; c < t.nkc; c += Cfg::kCps, g++) {
                     const int s = g % tc::kStages;
                     ok = tc::mbar_wait_bounded(&full[s], (g / tc::kStages) & 1, tc::kWaitLimit);
                     if (!ok || s_fail) {
@@ -302,16 +374,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_schur_tc(const TcTile* __rest
                         break;
                     }
                     tc::fence_after_sync();
-                    const uint32_t sa = tc::smem_u32(smem_tc + s * tc::kStageBytes);
-                    const uint32_t sal = sa + tc::kChunkA * 4, sb = sa + 2 * tc::kChunkA * 4, sbl = sb + tc::kChunkB * 4;
+                    const int nv = min(Cfg::kCps, t.nkc - c);
+                    const uint32_t sa0 = tc::smem_u32(smem_tc + s * tc::kStageBytes);
+                    for (int j = 0; j < nv; j++) {
+                        const uint32_t sa = sa0 + j * Cfg::kFloatsA * 4, sal = sa + kA;
+                        const uint32_t sb = sa0 + kA + kLoA + j * Cfg::kFloatsB * 4, sbl = sb + kB;
+                        if constexpr (Cfg::kBf) {  // one K = 16 MMA per chunk (bf16: two 16-byte K groups)
+                            const uint64_t dah = tc::smem_desc(sa, 128, Cfg::kSbo), dbh = tc::smem_desc(sb, 128, Cfg::kSbo);
+                            if constexpr (Cfg::kLo) {
+                                const uint64_t dal = tc::smem_desc(sal, 128, Cfg::kSbo), dbl = tc::smem_desc(sbl, 128, Cfg::kSbo);
+                                tc::mma_bf16(acc, dal, dbh, idesc, (c == 0 && j == 0) ? 0u : 1u);
+                                tc::mma_bf16(acc, dah, dbl, idesc, 1u);
+                                tc::mma_bf16(acc, dah, dbh, idesc, 1u);
+                            } else {
+                                tc::mma_bf16(acc, dah, dbh, idesc, (c == 0 && j == 0) ? 0u : 1u);
+                            }
+                        } else {
 #pragma unroll
-                    for (int ks = 0; ks < tc::kChunkK / 8; ks++) {  // K = 8 per MMA: two 16-byte K groups
-                        const uint32_t ko = ks * 256;
-                        const uint64_t dah = tc::smem_desc(sa + ko, 128, 512), dal = tc::smem_desc(sal + ko, 128, 512);
-                        const uint64_t dbh = tc::smem_desc(sb + ko, 128, 512), dbl = tc::smem_desc(sbl + ko, 128, 512);
-                        tc::mma_tf32(acc, dal, dbh, idesc, (c == 0 && ks == 0) ? 0u : 1u);
-                        tc::mma_tf32(acc, dah, dbl, idesc, 1u);
-                        tc::mma_tf32(acc, dah, dbh, idesc, 1u);
+                            for (int ks = 0; ks < tc::kChunkK / 8; ks++) {  // K = 8 per MMA: two 16-byte K groups
+                                const uint32_t ko = ks * 256;
+                                const uint64_t dah = tc::smem_desc(sa + ko, 128, 512), dal = tc::smem_desc(sal + ko, 128, 512);
+                                const uint64_t dbh = tc::smem_desc(sb + ko, 128, 512), dbl = tc::smem_desc(sbl + ko, 128, 512);
+                                tc::mma_tf32(acc, dal, dbh, idesc, (c == 0 && j == 0 && ks == 0) ? 0u : 1u);
+                                tc::mma_tf32(acc, dah, dbl, idesc, 1u);
+                                tc::mma_tf32(acc, dah, dbh, idesc, 1u);
+                            }
+                        }
                     }
                     tc::mma_commit(&empty[s]);
                 }

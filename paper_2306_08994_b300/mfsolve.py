@@ -23,8 +23,8 @@ LIB_PATH = os.path.join(_HERE, "libmfsolve.so")
 MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_EZERO_PIVOT, MF_ENOCONV, MF_ETIMEOUT, MF_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
 MF_ETOOLARGE = -8
 MF_NOALLOC_MAX_ENTRIES = 1 << 20
-MF_F64, MF_F32, MF_TF32 = 0, 1, 2
-PRECISIONS = {"f64": MF_F64, "f32": MF_F32, "tf32": MF_TF32}
+MF_F64, MF_F32, MF_TF32, MF_TF32_BF16 = 0, 1, 2, 3
+PRECISIONS = {"f64": MF_F64, "f32": MF_F32, "tf32": MF_TF32, "tf32_bf16": MF_TF32_BF16}
 MF_FUSED_BUCKETS = 9
 FUSED_BOUNDS = (16, 32, 48, 64, 96, 128, 160, 192, 224)
 
@@ -36,7 +36,8 @@ class mf_options(ctypes.Structure):
                 ("subtree_solve_levels", ctypes.c_int),
                 ("tc_min_cb", ctypes.c_int),
                 ("super_panel", ctypes.c_int), ("fused_threads", ctypes.c_int * MF_FUSED_BUCKETS),
-                ("lookahead", ctypes.c_int), ("root_f64", ctypes.c_int)]
+                ("lookahead", ctypes.c_int), ("bf16_min_cb", ctypes.c_int), ("bf16_passes", ctypes.c_int),
+                ("root_f64", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {f: (list(getattr(self, f)) if f == "fused_threads" else getattr(self, f)) for f, _ in self._fields_}

@@ -517,3 +517,41 @@ def test_fp64_root_pivot_blocks_factors_and_solution(case, root_f64):
     xo, _ = s.solve_refined(pr.b)
     err = np.linalg.norm(x.cpu().numpy().T - xo) / np.linalg.norm(xo)
     assert info["backward_error"] <= 1e-12 and err <= 1e-10, (info, err)
+
+
+@pytest.mark.parametrize("passes", [1, 3])
+def test_bf16_schur_products_refine_to_the_fp64_bar(passes):
+    """MF_TF32_BF16 with every Schur update on BF16 tensor-core products (bf16_min_cb and tc_min_cb
+    small), on the L2-projection mass matrix, whose condition number is bounded independently of h
+    (so even a single BF16 pass, about 2^-9 per product, leaves the refinement contracting):
+    (a) front by front within 4 K_f u_eff max|front| of the oracle with u_eff = 2^-8 (one pass) or
+    2^-16 (three split passes: the dropped lo x lo term); (b) the refined solution meets the
+    1e-12 backward-error and 1e-10 solution bars."""
+    pr = F.l2_projection(24, 3)
+    a, f, vals = _setup(pr, "tf32_bf16", bf16_passes=passes, bf16_min_cb=16, tc_min_cb=16, small_front_max=16)
+    f.factor(vals)
+    assert f.status()["rc"] == 0
+    s = _oracle(pr)
+    ksub = np.asarray(s.k, dtype=np.int64).copy()
+    for v in range(s.n_front):
+        if s.parent[v] >= 0:
+            ksub[s.parent[v]] += ksub[v]
+    u_eff = 2.0 ** -8 if passes == 1 else 2.0 ** -16
+    order = np.lexsort((np.arange(s.n_front), s.height))
+    for g in range(len(order)):
+        v = order[g]
+        Lo, Uo = s.factor_of(v)
+        k = Lo.shape[1]
+        if k == 0:
+            continue
+        Lg, Ug = f.export_front(g)
+        sc = max(np.abs(Lo).max(), np.abs(Uo).max())
+        tol = 4.0 * ksub[v] * u_eff * sc
+        low = np.tril(np.ones((Lo.shape[0], k), bool))
+        assert np.abs(Lg - Lo)[low].max() <= tol, (g, passes)
+    b = torch.tensor(np.ascontiguousarray(pr.b.T), device=DEV)
+    x = torch.empty_like(b)
+    info = f.refine_solve(vals, b, x, tol=1e-15, maxit=40)
+    xo, _ = s.solve_refined(pr.b)
+    err = np.linalg.norm(x.cpu().numpy().T - xo) / np.linalg.norm(xo)
+    assert info["backward_error"] <= 1e-12 and err <= 1e-10, (passes, info, err)
