@@ -331,6 +331,9 @@ def main():
                          "one and three BF16 passes): refinement contraction, corrections and step time")
     ap.add_argument("--root-f64-trial", type=int, default=0,
                     help="also measure the tuned plan with the pivot blocks of the top N classes in FP64")
+    ap.add_argument("--foata-trial", type=int, default=0,
+                    help="also measure the tuned plan with the bottom N classes on the scalar-task Foata executor "
+                         "(and, for comparison, the tuned plan without subtree fusion)")
     ap.add_argument("--tune", default="cache", choices=["off", "cache", "run"],
                     help="plan autotuner (untimed, before warm-up): off = default plan; cache = tuned plan from "
                          "the package's plan cache, tuning and recording it when missing; run = tune afresh")
@@ -540,7 +543,7 @@ def main():
         return out
 
     trials = {}
-    if kind == "solve" and precision != "f64" and (args.bf16_trial or args.root_f64_trial):
+    if kind == "solve" and (args.bf16_trial or args.root_f64_trial or args.foata_trial):
         import copy
         trials["tuned"] = time_variant(opts)
         if args.bf16_trial:
@@ -555,6 +558,12 @@ def main():
             o2 = copy.copy(opts)
             o2.root_f64 = args.root_f64_trial
             trials[f"root_f64_{args.root_f64_trial}"] = time_variant(o2)
+        if args.foata_trial:
+            o2 = copy.copy(opts)
+            o2.subtree_levels = -1
+            trials["tuned_no_subtree"] = time_variant(o2)
+            o2.foata_classes = args.foata_trial
+            trials[f"foata_{args.foata_trial}"] = time_variant(o2)
         step(fac, vals, b, x)
 
     # roofline: per-launch event timing (launch trace) over the same K steps; the dominant

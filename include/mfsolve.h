@@ -107,6 +107,11 @@ typedef struct {
     int bf16_min_cb;      /* MF_TF32_BF16: smallest contribution block whose Schur update uses BF16
                              products; 0 = 2048 */
     int bf16_passes;      /* MF_TF32_BF16: 1 (default, also 0) = one BF16 product, 3 = hi/lo split */
+    int foata_classes;    /* the bottom foata_classes classes run the paper's scalar-task schedule
+                             (Sec. 3.3): per pivot step one launch each for the assertion (static
+                             pivot check), division, multiplication and subtraction tasks of every
+                             front of the class, after an extend-add launch; 0 = off (default: the
+                             fused per-front kernels); turns off subtree fusion */
     int root_f64;         /* FP32-family fronts: the pivot blocks of the large fronts in the top
                              root_f64 Foata classes (1 = the root's class) are factored and inverted
                              in FP64 from the FP32 front and rounded once to FP32; 0 = none (default) */
@@ -314,7 +319,7 @@ int mf_profile_read(mf_factors* f, double* ms, int64_t* launches, double* bytes,
  * in issue order.  kind: 0 fused small fronts, 1 large-front assembly,
  * 2 panel diagonal block, 3 SIMT GEMM, 4 pivot-block inverses, 5 subtree
  * factorization, 6 tensor-core GEMM, 7 lane-group tiny fronts, 8 tensor-core
- * operand packing, or one of the
+ * operand packing, 9 scalar-task Foata executor, or one of the
  * MF_TRACE_* codes below;
  * cls: 0-based Foata class or -1; tasks: fronts, tiles or tasks in the launch.
  * Call before mf_profile_read (which clears the trace).  Writes at most `cap`

@@ -19,7 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmfsolve.so")
 OBJ = os.path.join(ROOT, "_build")
 SOURCES = ["analysis.cpp", "analysis_csr.cpp", "capi.cpp", "executor.cu", "noalloc.cu", "autotune.cpp"]
-HEADERS = ["mf_internal.h", "kernels_factor.cuh", "kernels_solve.cuh", "kernels_subtree.cuh", "kernels_tc.cuh"]
+HEADERS = ["mf_internal.h", "kernels_factor.cuh", "kernels_foata.cuh", "kernels_solve.cuh", "kernels_subtree.cuh",
+           "kernels_tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

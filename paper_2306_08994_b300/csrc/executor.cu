@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "kernels_factor.cuh"
+#include "kernels_foata.cuh"
 #include "kernels_solve.cuh"
 #include "kernels_subtree.cuh"
 #include "kernels_tc.cuh"
@@ -30,7 +31,7 @@ bool mf_alloc_should_fail() {
 namespace {
 
 enum LaunchKind { K_FUSED = 0, K_ASM = 1, K_PDIAG = 2, K_GEMM = 3, K_INVDIAG = 4, K_SUBTREE = 5, K_GEMMTC = 6, K_GRP = 7,
-                  K_TCPACK = 8, K_FORK = 10, K_JOIN = 11,
+                  K_TCPACK = 8, K_FOATA = 9, K_FORK = 10, K_JOIN = 11,
                   K_SYNC = 12 };  // K_SYNC: stream `stream` waits for what stream `bucket` issued so far (event `off`)
 
 struct Launch {
@@ -253,6 +254,13 @@ struct mf_factors {
     void* d_vec = nullptr;
     int32_t* d_flist = nullptr;
     FactorRec* d_frec = nullptr;  // the fused / lane-group launch lists as compact records
+    // scalar-task Foata executor of the bottom classes: fronts' workspace offsets (parallel to the
+    // factor list), the dense front workspace W and the products' workspace X
+    int foata_cls = 0;
+    int64_t* d_fwoff = nullptr;
+    void* d_fws = nullptr;
+    void* d_fxs = nullptr;
+    int64_t fws_size = 0;
     int32_t* d_slist = nullptr;
     SolveRec* d_srec = nullptr;  // the substitution list as compact records
     RowBlock* d_rows = nullptr;
@@ -381,7 +389,7 @@ static void free_factors(mf_factors* f) {
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_vsrc, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
-                    f->d_vec, f->d_flist, f->d_frec, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
+                    f->d_vec, f->d_flist, f->d_frec, f->d_fwoff, f->d_fws, f->d_fxs, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
                     f->d_csr_dest, f->d_elemvals, f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms, f->d_colabs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -464,6 +472,7 @@ static size_t fused_smem(int maxm) {
 static int build_plan(mf_factors* F) {
     const mf_analysis* a = F->a;
     std::vector<int32_t> flist, slist;
+    std::vector<int64_t> fwoff;  // parallel to flist: Foata workspace offsets (-1 for other kernels' fronts)
     std::vector<RowBlock> rows;
     std::vector<InvTask> invt;
     std::vector<AsmTile> asmt;
@@ -588,7 +597,7 @@ static int build_plan(mf_factors* F) {
     };
     // subtree fusion of the bottom classes
     {
-        int want = F->opt.subtree_levels;
+        int want = F->foata_cls > 0 ? 0 : F->opt.subtree_levels;  // the Foata executor takes the bottom classes
         int hmax = want <= 0 ? 0 : std::min(a->n_cls, want);
         hmax = std::min(hmax, kSubMaxLevels);
         int dev = 0, optin = 0;
@@ -718,6 +727,63 @@ static int build_plan(mf_factors* F) {
         slist.insert(slist.end(), all.begin(), all.end());
 
         if (fused_by_subtree) return;
+        if (c < F->foata_cls) {
+            // the Table 2 tasks of every front of the class as Foata classes of scalar tasks: extend-add,
+            // front maxima, then per pivot step T4 (check), T1 (divide), T2 (multiply), T3 (subtract),
+            // then the write-out; each launch covers the step's tasks of all fronts
+            const int64_t off = (int64_t)flist.size();
+            int maxm = 1, maxk = 0;
+            int64_t ws = 0;
+            double by_asm = 0, by_out = 0;
+            for (int32_t f : all) {
+                const FrontDev& fr = a->fronts[f];
+                flist.push_back(f);
+                fwoff.push_back(ws);
+                ws += (int64_t)fr.m * fr.m;
+                maxm = std::max(maxm, fr.m);
+                maxk = std::max(maxk, fr.k);
+                if (fr.nchild == 0) by_asm += 8.0 * a->npe * a->npe;
+                for (int q = 0; q < fr.nchild; q++) {
+                    const FrontDev& ch = a->fronts[fr.child[q]];
+                    by_asm += T * (double)(ch.m - ch.k) * (ch.m - ch.k);
+                }
+                by_asm += T * (double)fr.m * fr.m;
+                by_out += 2.0 * T * (double)fr.m * fr.m;
+            }
+            F->fws_size = std::max(F->fws_size, ws);
+            const int nf = (int)all.size();
+            auto bpf = [](int64_t n) { return (int)std::max<int64_t>(1, (n + 255) / 256); };
+            Launch L{K_FOATA, c, nf, bpf((int64_t)maxm * maxm), off, 0, 0};
+            push(L, FAM_FUSED, by_asm, 0.0);  // threads = task kind (0 extend-add)
+            L.threads = 1;
+            push(L, FAM_FUSED, T * (double)ws, (double)ws);  // front maxima
+            for (int p = 0; p < maxk; p++) {
+                double n1 = 0, n2 = 0, nk = 0;
+                for (int32_t f : all) {
+                    const FrontDev& fr = a->fronts[f];
+                    if (p >= fr.k) continue;
+                    nk += 1;
+                    n1 += fr.m - p - 1;
+                    n2 += (double)(fr.m - p - 1) * (fr.m - p - 1);
+                }
+                L.bucket = p;
+                L.threads = 2;  // T4
+                push(L, FAM_FUSED, 2.0 * T * nk, nk);
+                L.threads = 3;  // T1
+                L.maxm = bpf(maxm - p - 1);
+                push(L, FAM_FUSED, 2.0 * T * n1, n1);
+                L.threads = 4;  // T2
+                L.maxm = bpf((int64_t)(maxm - p - 1) * (maxm - p - 1));
+                push(L, FAM_FUSED, 3.0 * T * n2, n2);
+                L.threads = 5;  // T3
+                push(L, FAM_FUSED, 3.0 * T * n2, n2);
+            }
+            L.bucket = 0;
+            L.threads = 6;  // write-out
+            L.maxm = bpf((int64_t)maxm * maxm);
+            push(L, FAM_FUSED, by_out, 0.0);
+            return;
+        }
         // tiny fronts (m <= 32): lane-group kernel, G lanes per front
         auto small_bytes = [&](const std::vector<int32_t>& L, double& by, double& fl) {
             by = fl = 0;
@@ -745,6 +811,7 @@ static int build_plan(mf_factors* F) {
                 small_bytes(L, by, fl);
                 push({K_GRP, c, (int)L.size(), G, (int64_t)flist.size()}, FAM_FUSED, by, fl);
                 flist.insert(flist.end(), L.begin(), L.end());
+                fwoff.resize(flist.size(), -1);
             }
             lo = hi;
         }
@@ -762,6 +829,7 @@ static int build_plan(mf_factors* F) {
                 if (th <= 0) th = hi <= 64 ? 128 : 256;
                 push({K_FUSED, c, (int)L.size(), hi, (int64_t)flist.size(), bi, th}, FAM_FUSED, by, fl);
                 flist.insert(flist.end(), L.begin(), L.end());
+                fwoff.resize(flist.size(), -1);
             }
             lo = hi;
         }
@@ -1127,6 +1195,8 @@ static int build_plan(mf_factors* F) {
     if ((rc = upload(&F->d_sweep_f, F->sweep_f))) return rc;
     if ((rc = upload(&F->d_sweep_b, F->sweep_b))) return rc;
     if ((rc = upload(&F->d_flist, flist))) return rc;
+    fwoff.resize(flist.size(), -1);
+    if ((rc = upload(&F->d_fwoff, fwoff))) return rc;
     {
         std::vector<FactorRec> frec(flist.size());
         for (size_t i = 0; i < flist.size(); i++) {
@@ -1233,6 +1303,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     F->sp = F->opt.super_panel > 0 ? F->opt.super_panel : (F->prec == MF_F64 ? F->nb : 256);
     F->sp = std::max(F->nb, (F->sp + F->nb - 1) / F->nb * F->nb);
     F->la = F->opt.lookahead >= 0;
+    F->foata_cls = std::max(0, F->opt.foata_classes);
     for (int i = 0; i < MF_FUSED_BUCKETS; i++) {
         const int t = F->opt.fused_threads[i];
         if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256) {
@@ -1314,6 +1385,10 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
                 return MF_ENOTSUP;
             }
         }
+    }
+    if (F->fws_size > 0) {
+        TRY(dev_alloc((char**)&F->d_fws, (size_t)F->fws_size * F->tsize));
+        TRY(dev_alloc((char**)&F->d_fxs, (size_t)F->fws_size * F->tsize));
     }
     TRY(dev_alloc((char**)&F->d_inv, (size_t)a->inv_size * F->tsize));
     TRY(dev_alloc((char**)&F->d_scr, (size_t)F->scr_size * F->tsize));
@@ -1512,6 +1587,24 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
             case K_INVDIAG:
                 k_inv_diag<T><<<L.count, 128, 2 * 64 * 65 * sizeof(T), s>>>(F->d_fronts, F->d_invt + L.off, fac, (T*)F->d_inv);
                 break;
+            case K_FOATA: {
+                const FoataArgs A{F->d_frec + L.off, F->d_fwoff + L.off, L.count, L.maxm, L.bucket};
+                T* W = (T*)F->d_fws;
+                T* X = (T*)F->d_fxs;
+                const unsigned g = (unsigned)((int64_t)L.count * L.maxm);
+                switch (L.threads) {
+                    case 0: k_foata_assemble<T><<<g, 256, 0, s>>>(A, F->d_maps, d_values, a->npe, cb, W); break;
+                    case 1: k_foata_amax<T><<<L.count, 256, 0, s>>>(A, W, F->d_famax); break;
+                    case 2:
+                        k_foata_t4<T><<<(L.count + 255) / 256, 256, 0, s>>>(A, W, F->d_famax, F->tol_rel, F->d_status);
+                        break;
+                    case 3: k_foata_t1<T><<<g, 256, 0, s>>>(A, W); break;
+                    case 4: k_foata_t2<T><<<g, 256, 0, s>>>(A, W, X); break;
+                    case 5: k_foata_t3<T><<<g, 256, 0, s>>>(A, W, X); break;
+                    default: k_foata_write<T><<<g, 256, 0, s>>>(A, W, fac, cb); break;
+                }
+                break;
+            }
         }
         prof_end(F, s, slot);
         CUDA_TRY(cudaGetLastError());

@@ -555,3 +555,69 @@ def test_bf16_schur_products_refine_to_the_fp64_bar(passes):
     xo, _ = s.solve_refined(pr.b)
     err = np.linalg.norm(x.cpu().numpy().T - xo) / np.linalg.norm(xo)
     assert info["backward_error"] <= 1e-12 and err <= 1e-10, (passes, info, err)
+
+
+FOATA_CASES = {
+    "q1_16_all": (lambda: F.poisson_2d_q1(16), 99, {}),
+    "q3_6_all": (lambda: F.diffusion_2d(6, 3, seed=61), 99, {}),
+    "q1_3d_4_all": (lambda: F.diffusion_3d_q1(4, seed=62), 99, {}),
+    "q3_16_bottom4": (lambda: F.diffusion_2d(16, 3, seed=63), 4, {"small_front_max": 48}),
+    "l2_q2_12_bottom3": (lambda: F.l2_projection(12, 2), 3, {"small_front_max": 16}),
+}
+
+
+@pytest.mark.parametrize("case", list(FOATA_CASES))
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_scalar_task_foata_executor(case, prec):
+    """The bottom classes run as the paper's scalar-task Foata classes (per pivot step one launch of
+    assertion, division, multiplication and subtraction tasks over every front of the class):
+    FP64 factors front by front within 1e-11 of the oracle (the same tasks in the same order per
+    entry as the oracle's Table 2 loop, up to the reciprocal-free division); FP32 factors within the
+    FP32 bound of test_fp32_family_factors_match_oracle_front_by_front; refined solutions within
+    1e-10."""
+    mk, ncls, opt = FOATA_CASES[case]
+    pr = mk()
+    a, f, vals = _setup(pr, prec, foata_classes=ncls, **opt)
+    f.factor(vals)
+    st = f.status()
+    assert st["rc"] == 0 and st["n_perturbed"] == 0
+    s = _oracle(pr)
+    if prec == "f64":
+        _check_factors(f, s, case)
+    else:
+        ksub = np.asarray(s.k, dtype=np.int64).copy()
+        for v in range(s.n_front):
+            if s.parent[v] >= 0:
+                ksub[s.parent[v]] += ksub[v]
+        order = np.lexsort((np.arange(s.n_front), s.height))
+        for g in range(len(order)):
+            v = order[g]
+            Lo, Uo = s.factor_of(v)
+            k = Lo.shape[1]
+            if k == 0:
+                continue
+            Lg, Ug = f.export_front(g)
+            tol = 4.0 * ksub[v] * 2.0 ** -24 * max(np.abs(Lo).max(), np.abs(Uo).max(), 1.0)
+            low = np.tril(np.ones((Lo.shape[0], k), bool))
+            assert np.abs(Lg - Lo)[low].max() <= tol, (case, g)
+    b = torch.tensor(np.ascontiguousarray(pr.b.T), device=DEV)
+    x = torch.empty_like(b)
+    info = f.refine_solve(vals, b, x, tol=1e-15, maxit=30)
+    xo, _ = s.solve_refined(pr.b)
+    err = np.linalg.norm(x.cpu().numpy().T - xo) / np.linalg.norm(xo)
+    assert info["backward_error"] <= 1e-12 and err <= 1e-10, (case, prec, info, err)
+
+
+def test_scalar_task_foata_executor_static_pivot_check():
+    """A singular (pure Neumann) Q1 Laplacian through the Foata executor: the assertion tasks replace
+    the zero pivot and count it, as the fused kernels do."""
+    mesh = F.structured_mesh((4, 4), 1)
+    Ke = F.element_matrices(mesh, dirichlet=False)
+    pr = F.Problem("neumann", mesh, Ke, np.ones((mesh.n_nodes, 1)))
+    a, f, vals = _setup(pr, "f64", foata_classes=99, pivot_tol=1e-6)
+    f.factor(vals)
+    st = f.status()
+    assert st["rc"] == 0 and st["n_perturbed"] >= 1 and st["first_front"] == a.n_front - 1
+    a2, f2, vals2 = _setup(pr, "f64", foata_classes=99, pivot_tol=1e-6, pivot_fail=1)
+    f2.factor(vals2)
+    assert f2.status()["rc"] == M.mfsolve.MF_EZERO_PIVOT
