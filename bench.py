@@ -331,6 +331,9 @@ def main():
                          "one and three BF16 passes): refinement contraction, corrections and step time")
     ap.add_argument("--root-f64-trial", type=int, default=0,
                     help="also measure the tuned plan with the pivot blocks of the top N classes in FP64")
+    ap.add_argument("--sym-trial", action="store_true",
+                    help="also measure the tuned plan in symmetric mode (L only beyond the pivot blocks, lower-half "
+                         "Schur updates, x = L^-T D L^-1 b)")
     ap.add_argument("--foata-trial", type=int, default=0,
                     help="also measure the tuned plan with the bottom N classes on the scalar-task Foata executor "
                          "(and, for comparison, the tuned plan without subtree fusion)")
@@ -543,7 +546,7 @@ def main():
         return out
 
     trials = {}
-    if kind == "solve" and (args.bf16_trial or args.root_f64_trial or args.foata_trial):
+    if kind == "solve" and (args.bf16_trial or args.root_f64_trial or args.foata_trial or args.sym_trial):
         import copy
         trials["tuned"] = time_variant(opts)
         if args.bf16_trial:
@@ -558,6 +561,10 @@ def main():
             o2 = copy.copy(opts)
             o2.root_f64 = args.root_f64_trial
             trials[f"root_f64_{args.root_f64_trial}"] = time_variant(o2)
+        if args.sym_trial:
+            o2 = copy.copy(opts)
+            o2.symmetric = 1
+            trials["symmetric"] = time_variant(o2)
         if args.foata_trial:
             o2 = copy.copy(opts)
             o2.subtree_levels = -1

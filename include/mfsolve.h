@@ -112,6 +112,11 @@ typedef struct {
                              pivot check), division, multiplication and subtraction tasks of every
                              front of the class, after an extend-add launch; 0 = off (default: the
                              fused per-front kernels); turns off subtree fusion */
+    int symmetric;        /* nonzero: the caller promises A = A^T.  Then U = D^-1 L^T (D = diag L),
+                             so beyond the pivot block the large fronts factor only L, take U12 =
+                             D^-1 L21^T by a transposing copy, and compute only the lower half of
+                             their Schur update (mirrored after); solves run x = L^-T D L^-1 b and
+                             never read U; mf_solve_adjoint equals mf_solve.  0 = general LU */
     int root_f64;         /* FP32-family fronts: the pivot blocks of the large fronts in the top
                              root_f64 Foata classes (1 = the root's class) are factored and inverted
                              in FP64 from the FP32 front and rounded once to FP32; 0 = none (default) */

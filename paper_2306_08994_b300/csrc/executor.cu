@@ -31,7 +31,7 @@ bool mf_alloc_should_fail() {
 namespace {
 
 enum LaunchKind { K_FUSED = 0, K_ASM = 1, K_PDIAG = 2, K_GEMM = 3, K_INVDIAG = 4, K_SUBTREE = 5, K_GEMMTC = 6, K_GRP = 7,
-                  K_TCPACK = 8, K_FOATA = 9, K_FORK = 10, K_JOIN = 11,
+                  K_TCPACK = 8, K_FOATA = 9, K_FORK = 10, K_JOIN = 11, K_SYMR = 13, K_MIRROR = 14,
                   K_SYNC = 12 };  // K_SYNC: stream `stream` waits for what stream `bucket` issued so far (event `off`)
 
 struct Launch {
@@ -257,6 +257,9 @@ struct mf_factors {
     // scalar-task Foata executor of the bottom classes: fronts' workspace offsets (parallel to the
     // factor list), the dense front workspace W and the products' workspace X
     int foata_cls = 0;
+    bool sym = false;                 // symmetric factors and solves (option symmetric)
+    int64_t* d_pdiag = nullptr;       // symmetric solves: factor-arena offset of each dof's pivot
+    AsmTile* d_symt = nullptr;        // tiles of the symmetric-mode R copies and S mirrors
     int64_t* d_fwoff = nullptr;
     void* d_fws = nullptr;
     void* d_fxs = nullptr;
@@ -389,7 +392,7 @@ static void free_factors(mf_factors* f) {
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_vsrc, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
-                    f->d_vec, f->d_flist, f->d_frec, f->d_fwoff, f->d_fws, f->d_fxs, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
+                    f->d_vec, f->d_flist, f->d_frec, f->d_fwoff, f->d_fws, f->d_fxs, f->d_pdiag, f->d_symt, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
                     f->d_csr_dest, f->d_elemvals, f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms, f->d_colabs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -473,6 +476,7 @@ static int build_plan(mf_factors* F) {
     const mf_analysis* a = F->a;
     std::vector<int32_t> flist, slist;
     std::vector<int64_t> fwoff;  // parallel to flist: Foata workspace offsets (-1 for other kernels' fronts)
+    std::vector<AsmTile> symt;   // symmetric mode: R tiles and S mirror tiles
     std::vector<RowBlock> rows;
     std::vector<InvTask> invt;
     std::vector<AsmTile> asmt;
@@ -502,11 +506,13 @@ static int build_plan(mf_factors* F) {
         F->plan_flops.push_back(flops);
     };
     auto gemm_tiles = [&](int64_t a_off, int lda, int64_t b_off, int ldb, int64_t c_off, int ldc, int M, int N, int K,
-                          int c_in_cb) {
-        gf += 2.0 * M * N * K;
-        gb += T * ((double)M * K + (double)K * N + 2.0 * M * N);
+                          int c_in_cb, bool lower = false) {
+        // lower: only the tiles on and below the diagonal (the symmetric Schur update)
+        gf += lower ? (double)M * (M + 1) * K : 2.0 * M * N * K;
+        gb += T * ((double)M * K + (double)K * N + (lower ? (double)M * (M + 1) : 2.0 * M * N));
         for (int j0 = 0; j0 < N; j0 += 64)
             for (int i0 = 0; i0 < M; i0 += 64) {
+                if (lower && i0 + 64 <= j0) continue;
                 GemmTile t{};
                 t.a_off = a_off; t.b_off = b_off; t.c_off = c_off;
                 t.lda = lda; t.ldb = ldb; t.ldc = ldc;
@@ -531,12 +537,14 @@ static int build_plan(mf_factors* F) {
     // per product mode (tc::Mode): packing bytes, product bytes and flops of the pending products
     double tc_pbm[3] = {0, 0, 0}, tc_gbm[3] = {0, 0, 0}, tc_gfm[3] = {0, 0, 0};
     auto tc_add = [&](int8_t aar, int64_t aoff, int lda, int8_t bar, int64_t boff, int ldb, int8_t car, int64_t coff,
-                      int ldc, int M, int N, int K, int8_t op = 0, int8_t am = 0, int8_t bm = 0, int mode = tc::kTf32x3) {
+                      int ldc, int M, int N, int K, int8_t op = 0, int8_t am = 0, int8_t bm = 0, int mode = tc::kTf32x3,
+                      bool lower = false) {
         TcPack q{};
         q.a_ar = aar; q.a_off = aoff; q.lda = lda; q.a_mask = am;
         q.b_ar = bar; q.b_off = boff; q.ldb = ldb; q.b_mask = bm;
         q.M = M; q.N = N; q.K = K;
         q.pad[0] = (int8_t)mode;
+        q.pad[1] = lower ? 1 : 0;  // only the output tiles that reach the diagonal or below it
         q.nkc = (K + tc::kChunkK - 1) / tc::kChunkK;
         const int nra = (M + tc::kTileM - 1) / tc::kTileM, nrb = (N + tc::kTileN - 1) / tc::kTileN;
         const int ca = tc::chunk_floats_a(mode), cbk = tc::chunk_floats_b(mode);
@@ -546,8 +554,8 @@ static int build_plan(mf_factors* F) {
         tc_hi += (int64_t)nrb * q.nkc * cbk;
         tcp.push_back(q);
         tcc.push_back({car, op, coff, ldc});
-        tc_gfm[mode] += 2.0 * M * N * K;
-        tc_gbm[mode] += T * ((double)M * K + (double)K * N + 2.0 * M * N);
+        tc_gfm[mode] += lower ? (double)M * (M + 1) * K : 2.0 * M * N * K;
+        tc_gbm[mode] += T * ((double)M * K + (double)K * N + (lower ? (double)M * (M + 1) : 2.0 * M * N));
         tc_pbm[mode] += T * ((double)M * K + (double)K * N) +
                         (mode == tc::kBf16 ? 1.0 : 2.0) * 4.0 * ((double)nra * ca + (double)nrb * cbk) * q.nkc;
     };
@@ -567,6 +575,7 @@ static int build_plan(mf_factors* F) {
                         for (int kc = 0; kc < q.nkc; kc++) tcj.push_back({(int32_t)(qi - tc_p0), 1, rt, kc});
                     for (int rb = 0; rb < nrb; rb++)
                         for (int ra = 0; ra < nra; ra++) {
+                            if (q.pad[1] && (ra + 1) * tc::kTileM <= rb * tc::kTileN) continue;  // above the diagonal
                             TcTile t{};
                             t.a_hi = q.a_hi + (int64_t)ra * q.nkc * ca;
                             t.b_hi = q.b_hi + (int64_t)rb * q.nkc * cbk;
@@ -902,7 +911,7 @@ static int build_plan(mf_factors* F) {
                     if (k - kb - w > 0)
                         gemm_tiles(Lrow, m, fr.P_off + s0 + (int64_t)(kb + w) * m, m, fr.P_off + kb + (int64_t)(kb + w) * m, m,
                                    w, k - kb - w, K0, 0);
-                    if (m - k > 0) gemm_tiles(Lrow, m, fr.R_off + s0, k, fr.R_off + kb, k, w, m - k, K0, 0);
+                    if (m - k > 0 && !F->sym) gemm_tiles(Lrow, m, fr.R_off + s0, k, fr.R_off + kb, k, w, m - k, K0, 0);
                 }
                 if (gem.size() > (size_t)soff) push({K_GEMM, c, (int)(gem.size() - soff), 0, soff}, FAM_TRAIL, gb, gf);
             }
@@ -942,7 +951,7 @@ static int build_plan(mf_factors* F) {
                     const int64_t bb = fr.P_off + kb + (int64_t)r0 * m;
                     tile_raw(AR_PNL, slot, 64, 1, AR_FAC, bb, m, 0, AR_FAC, bb, m, w, k - r0, w, 1);
                 }
-                if (m - k > 0) {
+                if (m - k > 0 && !F->sym) {  // symmetric fronts take U12 from L21 before the Schur update
                     const int64_t bb = fr.R_off + kb;
                     tile_raw(AR_PNL, slot, 64, 1, AR_FAC, bb, k, 0, AR_FAC, bb, k, w, m - k, w, 1);
                 }
@@ -994,14 +1003,29 @@ static int build_plan(mf_factors* F) {
                         any_gemm(Lb, m, fr.P_off + s0 + (int64_t)e * m, m, AR_FAC, fr.P_off + e + (int64_t)e * m, m, m - e,
                                  k - e, SP);
                     }
-                    any_gemm(Lb, m, fr.R_off + s0, k, AR_FAC, fr.R_off + e, k, k - e, m - k, SP);
+                    if (!F->sym) any_gemm(Lb, m, fr.R_off + s0, k, AR_FAC, fr.R_off + e, k, k - e, m - k, SP);
                 }
                 if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_TRAIL, gb, gf);
                 tc_end(c, FAM_TRAIL);
             }
 
         }
-        // Schur update S -= L21 U12 (Sec. 2.2): tensor cores (MF_TF32) for large blocks, SIMT otherwise
+        // symmetric fronts: U12 = D^-1 L21^T into R (the Schur update's B operand)
+        if (F->sym) {
+            const int64_t off = (int64_t)symt.size();
+            double by = 0;
+            for (int32_t f : big) {
+                const FrontDev& fr = a->fronts[f];
+                const int k = fr.k, nc = fr.m - fr.k;
+                if (nc <= 0 || k <= 0) continue;
+                for (int j0 = 0; j0 < nc; j0 += 64)
+                    for (int i0 = 0; i0 < k; i0 += 64) symt.push_back({f, i0, j0, 0});
+                by += 2.0 * T * k * nc + T * k;
+            }
+            if (symt.size() > (size_t)off) push({K_SYMR, c, (int)(symt.size() - off), 0, off}, FAM_SCHUR, by, 0.0);
+        }
+        // Schur update S -= L21 U12 (Sec. 2.2): tensor cores (MF_TF32) for large blocks, SIMT otherwise;
+        // symmetric fronts compute only the tiles on and below the diagonal
         int64_t goff = (int64_t)gem.size();
         gb = gf = 0;
         for (int32_t f : big) {
@@ -1011,12 +1035,26 @@ static int build_plan(mf_factors* F) {
             if (use_tc(nc, nc, k))
                 tc_add(AR_FAC, fr.P_off + k, m, AR_FAC, fr.R_off, k, AR_CB, fr.S_off, nc, nc, nc, k, 0, 0, 0,
                        F->prec == MF_TF32_BF16 && nc >= F->bf16_min ? (F->opt.bf16_passes == 3 ? tc::kBf16x3 : tc::kBf16)
-                                                                    : tc::kTf32x3);
+                                                                    : tc::kTf32x3,
+                       F->sym);
             else
-                gemm_tiles(fr.P_off + k, m, fr.R_off, k, fr.S_off, nc, nc, nc, k, 1);
+                gemm_tiles(fr.P_off + k, m, fr.R_off, k, fr.S_off, nc, nc, nc, k, 1, F->sym);
         }
         if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_SCHUR, gb, gf);
         tc_end(c, FAM_SCHUR);
+        if (F->sym) {  // S[j, i] = S[i, j], i > j
+            const int64_t off = (int64_t)symt.size();
+            double by = 0;
+            for (int32_t f : big) {
+                const FrontDev& fr = a->fronts[f];
+                const int nc = fr.m - fr.k;
+                if (nc <= 1 || fr.k <= 0) continue;
+                for (int j0 = 0; j0 < nc; j0 += 64)
+                    for (int i0 = j0; i0 < nc; i0 += 64) symt.push_back({f, i0, j0, 0});
+                by += T * (double)nc * (nc - 1);
+            }
+            if (symt.size() > (size_t)off) push({K_MIRROR, c, (int)(symt.size() - off), 0, off}, FAM_SCHUR, by, 0.0);
+        }
     };
     // Explicit pivot-block inverses (used only by the substitutions): those of class c are computed
     // on the side stream right after class c, overlapping the factorization of the later classes.
@@ -1194,6 +1232,7 @@ static int build_plan(mf_factors* F) {
     int rc;
     if ((rc = upload(&F->d_sweep_f, F->sweep_f))) return rc;
     if ((rc = upload(&F->d_sweep_b, F->sweep_b))) return rc;
+    if (!symt.empty() && (rc = upload(&F->d_symt, symt))) return rc;
     if ((rc = upload(&F->d_flist, flist))) return rc;
     fwoff.resize(flist.size(), -1);
     if ((rc = upload(&F->d_fwoff, fwoff))) return rc;
@@ -1304,6 +1343,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     F->sp = std::max(F->nb, (F->sp + F->nb - 1) / F->nb * F->nb);
     F->la = F->opt.lookahead >= 0;
     F->foata_cls = std::max(0, F->opt.foata_classes);
+    F->sym = F->opt.symmetric != 0;
     for (int i = 0; i < MF_FUSED_BUCKETS; i++) {
         const int t = F->opt.fused_threads[i];
         if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256) {
@@ -1341,6 +1381,14 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
         TRY(upload(&F->d_vsrc, vsrc));
     }
     TRY(upload(&F->d_en, a->elem_nodes));
+    if (F->sym) {  // each dof's pivot (diagonal of L) in the factor arena, for the symmetric solves
+        std::vector<int64_t> pd(a->n_dof, 0);
+        for (int32_t f = 0; f < a->n_front; f++) {
+            const FrontDev& fr = a->fronts[f];
+            for (int p = 0; p < fr.k; p++) pd[a->dofs[fr.dof_off + p]] = fr.P_off + p + (int64_t)p * fr.m;
+        }
+        TRY(upload(&F->d_pdiag, pd));
+    }
     if (a->csr_n > 0) {
         TRY(upload(&F->d_csr_dest, a->csr_dest));
         const size_t ne = (size_t)a->n_elem * a->npe * a->npe;
@@ -1587,6 +1635,12 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
             case K_INVDIAG:
                 k_inv_diag<T><<<L.count, 128, 2 * 64 * 65 * sizeof(T), s>>>(F->d_fronts, F->d_invt + L.off, fac, (T*)F->d_inv);
                 break;
+            case K_SYMR:
+                k_sym_r<T><<<L.count, 256, 0, s>>>(F->d_fronts, F->d_symt + L.off, fac);
+                break;
+            case K_MIRROR:
+                k_sym_mirror<T><<<L.count, 256, 0, s>>>(F->d_fronts, F->d_symt + L.off, cb);
+                break;
             case K_FOATA: {
                 const FoataArgs A{F->d_frec + L.off, F->d_fwoff + L.off, L.count, L.maxm, L.bucket};
                 T* W = (T*)F->d_fws;
@@ -1665,7 +1719,10 @@ static int launch_sweep(mf_factors* F, const SweepArgs<T>& args, size_t smem, in
     } while (0)
 
 template <typename T>
-static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStream_t s) {
+static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStream_t s, bool trans_b, bool scale_d) {
+    // trans: the forward sweep solves with U^T instead of L; trans_b: the backward sweep with L^T
+    // instead of U; scale_d: multiply the pivot values by their pivots in between (symmetric factors:
+    // x = L^-T D L^-1 b)
     const mf_analysis* a = F->a;
     const T* fac = (const T*)F->d_fac;
     const T* inv = (const T*)F->d_inv;
@@ -1708,8 +1765,8 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
             rc = trans ? launch_sweep<T, true, true>(F, args, F->sweep_smem_f, nrhs, s)
                        : launch_sweep<T, false, true>(F, args, F->sweep_smem_f, nrhs, s);
         else
-            rc = trans ? launch_sweep<T, true, false>(F, args, F->sweep_smem_b, nrhs, s)
-                       : launch_sweep<T, false, false>(F, args, F->sweep_smem_b, nrhs, s);
+            rc = trans_b ? launch_sweep<T, true, false>(F, args, F->sweep_smem_b, nrhs, s)
+                         : launch_sweep<T, false, false>(F, args, F->sweep_smem_b, nrhs, s);
         prof_end(F, s, slot);
         return rc;
     };
@@ -1718,9 +1775,9 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         void (*kf)(SweepArgs<T>) = nrhs == 1 ? (trans ? k_solve_sweep<T, true, true, 1> : k_solve_sweep<T, false, true, 1>)
                                              : (trans ? k_solve_sweep<T, true, true, kRhsChunk>
                                                       : k_solve_sweep<T, false, true, kRhsChunk>);
-        void (*kb)(SweepArgs<T>) = nrhs == 1 ? (trans ? k_solve_sweep<T, true, false, 1> : k_solve_sweep<T, false, false, 1>)
-                                             : (trans ? k_solve_sweep<T, true, false, kRhsChunk>
-                                                      : k_solve_sweep<T, false, false, kRhsChunk>);
+        void (*kb)(SweepArgs<T>) = nrhs == 1 ? (trans_b ? k_solve_sweep<T, true, false, 1> : k_solve_sweep<T, false, false, 1>)
+                                             : (trans_b ? k_solve_sweep<T, true, false, kRhsChunk>
+                                                        : k_solve_sweep<T, false, false, kRhsChunk>);
         bool ok = true;
         if (F->sweep_smem_f > 48 * 1024)
             CUDA_TRY(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F->sweep_smem_f));
@@ -1809,7 +1866,17 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
     if (c_top < a->n_cls) {
         int rc = run_sweeps(true);
         if (rc != MF_OK) return rc;
-        rc = run_sweeps(false);
+    }
+    if (scale_d) {
+        int slot = prof_begin(F, s, FAM_OTHER, (16.0 + 8.0 + F->tsize) * n * nrhs, 1.0 * n * nrhs);
+        k_scale_pivots<T><<<(unsigned)((n * nrhs + 255) / 256), 256, 0, s>>>(F->d_pdiag, fac, d_x, n, nrhs);
+        prof_end(F, s, slot);
+        CUDA_TRY(cudaGetLastError());
+    }
+    // the backward sweep: with U (trans_b false) or L^T (trans_b true)
+    trans = trans_b;
+    if (c_top < a->n_cls) {
+        int rc = run_sweeps(false);
         if (rc != MF_OK) return rc;
     }
     for (int c = c_top - 1; c >= 0; c--) {
@@ -1894,7 +1961,10 @@ static int solve_common(mf_factors* F, double* d_rhs, int nrhs, bool trans, mf_s
     if (!F->factored) return MF_EINVAL;
     if (nrhs > F->max_nrhs) return MF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    return F->prec == MF_F64 ? run_solve<double>(F, d_rhs, nrhs, trans, s) : run_solve<float>(F, d_rhs, nrhs, trans, s);
+    // symmetric factors: A = A^T = L D^-1 L^T, the same sweeps for the solve and the adjoint solve
+    const bool tf = F->sym ? false : trans, tb = F->sym ? true : trans;
+    return F->prec == MF_F64 ? run_solve<double>(F, d_rhs, nrhs, tf, s, tb, F->sym)
+                             : run_solve<float>(F, d_rhs, nrhs, tf, s, tb, F->sym);
 }
 
 extern "C" int mf_solve(mf_factors* F, double* d_rhs, int nrhs, mf_stream_t stream) {

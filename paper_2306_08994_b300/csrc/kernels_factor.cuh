@@ -408,6 +408,59 @@ constexpr size_t panel_diag_dyn_smem() {
            (sizeof(C) == sizeof(T) ? 0 : 2 * (size_t)NB * (NB + 1) * sizeof(C));
 }
 
+// Symmetric fronts (option symmetric): for A = A^T the paper's U (unit upper)
+// is D^-1 L^T with D = diag(L), so beyond the pivot block only L is
+// factored; the Schur update's B operand U12 = D^-1 L21^T is written into R
+// by a transposing copy (one 64 x 64 tile of R per CTA through shared
+// memory, each U entry one division T1 of Table 2 by the pivot), and the
+// update itself computes only the tiles of S on and below the diagonal,
+// mirrored afterwards (k_sym_mirror).  Tile (i0, j0) of R covers pivots
+// i0.. and contribution-block columns j0..
+template <typename T>
+__global__ void __launch_bounds__(256) k_sym_r(const FrontDev* __restrict__ fronts, const AsmTile* __restrict__ tiles,
+                                               T* __restrict__ fac) {
+    __shared__ T tl[64][65];
+    const AsmTile t = tiles[blockIdx.x];
+    const FrontDev fr = fronts[t.front];
+    const int m = fr.m, k = fr.k, nc = m - k;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int pp = warp; pp < 64; pp += 8)
+        for (int jj = lane; jj < 64; jj += 32) {
+            const int p = t.i0 + pp, j = t.j0 + jj;
+            if (p < k && j < nc) tl[pp][jj] = fac[fr.P_off + (k + j) + (int64_t)p * m];
+        }
+    __syncthreads();
+    for (int jj = warp; jj < 64; jj += 8)
+        for (int pp = lane; pp < 64; pp += 32) {
+            const int p = t.i0 + pp, j = t.j0 + jj;
+            if (p < k && j < nc) fac[fr.R_off + p + (int64_t)j * k] = tl[pp][jj] / fac[fr.P_off + p + (int64_t)p * m];
+        }
+}
+
+// S[j, i] = S[i, j] for i > j: tile (i0, j0) with i0 >= j0 of the contribution block is read
+// (its entries below the diagonal) and written transposed
+template <typename T>
+__global__ void __launch_bounds__(256) k_sym_mirror(const FrontDev* __restrict__ fronts, const AsmTile* __restrict__ tiles,
+                                                    T* __restrict__ cbs) {
+    __shared__ T tl[64][65];
+    const AsmTile t = tiles[blockIdx.x];
+    const FrontDev fr = fronts[t.front];
+    const int nc = fr.m - fr.k;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T* S = cbs + fr.S_off;
+    for (int jj = warp; jj < 64; jj += 8)
+        for (int ii = lane; ii < 64; ii += 32) {
+            const int i = t.i0 + ii, j = t.j0 + jj;
+            if (i < nc && j < nc && i > j) tl[ii][jj] = S[i + (int64_t)j * nc];
+        }
+    __syncthreads();
+    for (int ii = warp; ii < 64; ii += 8)
+        for (int jj = lane; jj < 64; jj += 32) {
+            const int i = t.i0 + ii, j = t.j0 + jj;
+            if (i < nc && j < nc && i > j) S[j + (int64_t)i * nc] = tl[ii][jj];
+        }
+}
+
 // Pivot block of a large front (NB x NB at pivot kb, padded with the
 // identity beyond w): partial LU in place (L with its diagonal, unit U) and
 // the explicit inverses L_D^-1 (on and below the diagonal) and U_D^-1 (strict

@@ -1165,6 +1165,17 @@ __global__ void k_norms_final(const double* __restrict__ part, int nblk, double*
     }
 }
 
+// Symmetric factors (A = L D^-1 L^T, D = diag(L)): between the forward sweep
+// with L and the backward sweep with L^T the pivot values are multiplied by
+// their pivots, z = D y.  diag_off[d]: factor-arena offset of dof d's pivot.
+template <typename T>
+__global__ void k_scale_pivots(const int64_t* __restrict__ diag_off, const T* __restrict__ fac, double* __restrict__ x,
+                               int64_t n, int nrhs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * nrhs) return;
+    x[i] *= (double)fac[diag_off[i % n]];
+}
+
 __global__ void k_axpy(double* __restrict__ x, const double* __restrict__ d, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] += d[i];

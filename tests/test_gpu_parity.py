@@ -621,3 +621,54 @@ def test_scalar_task_foata_executor_static_pivot_check():
     a2, f2, vals2 = _setup(pr, "f64", foata_classes=99, pivot_tol=1e-6, pivot_fail=1)
     f2.factor(vals2)
     assert f2.status()["rc"] == M.mfsolve.MF_EZERO_PIVOT
+
+
+SYM_CASES = {
+    "q3_12_large_path": (lambda: F.diffusion_2d(12, 3, seed=71), {"small_front_max": 16}),
+    "q3_24_super_panel": (lambda: F.diffusion_2d(24, 3, seed=72), {"small_front_max": 16, "super_panel": 128}),
+    "q1_3d_6_large_path": (lambda: F.diffusion_3d_q1(6, seed=73), {"small_front_max": 24}),
+    "l2_q3_10": (lambda: F.l2_projection(10, 3), {"small_front_max": 32}),
+}
+
+
+@pytest.mark.parametrize("case", list(SYM_CASES))
+def test_symmetric_mode_f64_factors_match_oracle(case):
+    """Option symmetric on SPD matrices: beyond the pivot blocks the large fronts factor only L and
+    take U12 = D^-1 L21^T; the exported L and U still equal the oracle's LU factors front by front
+    within 1e-11 (U = D^-1 L^T holds exactly for a symmetric A), and solves, adjoint solves and
+    refined solves match the oracle."""
+    mk, opt = SYM_CASES[case]
+    pr = mk()
+    a, f, vals = _setup(pr, "f64", symmetric=1, **opt)
+    f.factor(vals)
+    assert f.status()["rc"] == 0
+    s = _oracle(pr)
+    _check_factors(f, s, case)
+    xo = s.solve(pr.b)
+    for adjoint in (False, True):
+        x = torch.tensor(np.ascontiguousarray(pr.b.T), device=DEV)
+        f.solve(x, adjoint=adjoint)
+        assert np.linalg.norm(x.cpu().numpy().T - xo) <= 1e-10 * np.linalg.norm(xo), (case, adjoint)
+    b = torch.tensor(np.ascontiguousarray(pr.b.T), device=DEV)
+    x = torch.empty_like(b)
+    info = f.refine_solve(vals, b, x, tol=1e-15, maxit=20)
+    xr, _ = s.solve_refined(pr.b)
+    assert info["backward_error"] <= 1e-14
+    assert np.linalg.norm(x.cpu().numpy().T - xr) <= 1e-10 * np.linalg.norm(xr)
+
+
+@pytest.mark.parametrize("case", ["q3_24_super_panel", "q1_3d_6_large_path"])
+@pytest.mark.parametrize("prec,extra", [("f32", {}), ("tf32", {"tc_min_cb": 16})])
+def test_symmetric_mode_fp32_family_refined_solution(case, prec, extra):
+    mk, opt = SYM_CASES[case]
+    pr = mk()
+    a, f, vals = _setup(pr, prec, symmetric=1, **opt, **extra)
+    f.factor(vals)
+    assert f.status()["rc"] == 0
+    s = _oracle(pr)
+    b = torch.tensor(np.ascontiguousarray(pr.b.T), device=DEV)
+    x = torch.empty_like(b)
+    info = f.refine_solve(vals, b, x, tol=1e-15, maxit=30)
+    xr, _ = s.solve_refined(pr.b)
+    err = np.linalg.norm(x.cpu().numpy().T - xr) / np.linalg.norm(xr)
+    assert info["backward_error"] <= 1e-12 and err <= 1e-10, (info, err)
