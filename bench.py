@@ -307,7 +307,7 @@ def replica_rank_info():
 def plan_summary(o, tinfo):
     d = o.as_dict()
     keep = {k: d[k] for k in ("precision", "small_front_max", "subtree_levels", "subtree_solve_levels", "tc_min_cb",
-                              "super_panel", "fused_threads")}
+                              "super_panel", "fused_threads", "symmetric")}
     keep["tuned"] = None if tinfo is None else {"from_cache": bool(tinfo["from_cache"]),
                                                   "ms_best": tinfo["ms_best"], "ms_default": tinfo["ms_default"],
                                                   "candidates": tinfo["candidates"]}
@@ -326,6 +326,14 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="direct launches instead of CUDA-graph replay")
+    ap.add_argument("--stationary", action="store_true",
+                    help="stationary FP64 refinement instead of preconditioned conjugate gradients (the default for "
+                         "these symmetric positive definite workloads)")
+    ap.add_argument("--refine-trial", action="store_true",
+                    help="also measure the tuned plan with the other refinement method (stationary vs. CG)")
+    ap.add_argument("--general", action="store_true",
+                    help="factor as a general matrix (LU with both triangles) instead of using its symmetry; every "
+                         "workload here is symmetric positive definite")
     ap.add_argument("--bf16-trial", action="store_true",
                     help="also measure the tuned plan with BF16 Schur products on the largest fronts (MF_TF32_BF16, "
                          "one and three BF16 passes): refinement contraction, corrections and step time")
@@ -370,8 +378,11 @@ def main():
     x = torch.empty_like(b)
     meshes = [M.Mesh(p.mesh.elem_nodes, p.mesh.n_nodes, p.mesh.dim, grid_dims=p.mesh.nel) for p in probs]
     use_graph = 0 if args.no_graph else 1
+    sym = 0 if args.general else 1
+    cg = 0 if (args.general or args.stationary) else 1
     an = M.Analysis(meshes if len(meshes) > 1 else meshes[0],
-                    M.default_options(precision=precision, max_nrhs=max(4, nrhs), use_graph=use_graph))
+                    M.default_options(precision=precision, max_nrhs=max(4, nrhs), use_graph=use_graph, symmetric=sym,
+                                      refine_cg=cg))
     info = an.info
     # a non-default stream: CUDA graphs cannot capture the legacy default stream
     stream = torch.cuda.Stream()
@@ -453,7 +464,8 @@ def main():
     fp64 = None
     if precision != "f64" and args.fp64_steps > 0:
         an64 = M.Analysis(meshes if len(meshes) > 1 else meshes[0],
-                          M.default_options(precision="f64", max_nrhs=max(4, nrhs), use_graph=use_graph))
+                          M.default_options(precision="f64", max_nrhs=max(4, nrhs), use_graph=use_graph,
+                                            symmetric=sym, refine_cg=cg))
         opts64, tinfo64 = plan_for(an64)
         f64 = M.Factors(an64, opts64)
         x64 = torch.empty_like(b)
@@ -546,7 +558,8 @@ def main():
         return out
 
     trials = {}
-    if kind == "solve" and (args.bf16_trial or args.root_f64_trial or args.foata_trial or args.sym_trial):
+    if kind == "solve" and (args.bf16_trial or args.root_f64_trial or args.foata_trial or args.sym_trial or
+                            args.refine_trial):
         import copy
         trials["tuned"] = time_variant(opts)
         if args.bf16_trial:
@@ -561,10 +574,14 @@ def main():
             o2 = copy.copy(opts)
             o2.root_f64 = args.root_f64_trial
             trials[f"root_f64_{args.root_f64_trial}"] = time_variant(o2)
+        if args.refine_trial and opts.symmetric:
+            o2 = copy.copy(opts)
+            o2.refine_cg = 1 - opts.refine_cg
+            trials["refine_cg" if o2.refine_cg else "refine_stationary"] = time_variant(o2)
         if args.sym_trial:
             o2 = copy.copy(opts)
-            o2.symmetric = 1
-            trials["symmetric"] = time_variant(o2)
+            o2.symmetric = 1 - opts.symmetric
+            trials["symmetric" if o2.symmetric else "general"] = time_variant(o2)
         if args.foata_trial:
             o2 = copy.copy(opts)
             o2.subtree_levels = -1
@@ -703,6 +720,8 @@ def main():
             "speedup_vs_fp64": (fp64["ms"] / ms) if fp64 else None,
             "matched_accuracy": matched,
             "trials": trials or None,
+            "refinement": ("preconditioned conjugate gradients in FP64 (M^-1 = L^-T D L^-1 from the FP32 factors)"
+                           if opts.refine_cg and opts.symmetric else "stationary FP64 refinement"),
             "accuracy_note": ("value: refined path stopped at normwise backward error <= 1e-12; matched_accuracy: "
                               "the same path stopped at the FP64 path's own backward error; rel_residual = "
                               "||b - A x||_2 / ||b||_2 of the final iterate on both paths"),

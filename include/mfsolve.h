@@ -117,6 +117,13 @@ typedef struct {
                              D^-1 L21^T by a transposing copy, and compute only the lower half of
                              their Schur update (mirrored after); solves run x = L^-T D L^-1 b and
                              never read U; mf_solve_adjoint equals mf_solve.  0 = general LU */
+    int refine_cg;        /* with symmetric (and A positive definite): mf_refine_solve runs the FP64
+                             preconditioned conjugate-gradient method with the factorization as
+                             preconditioner (M^-1 = L^-T D L^-1, symmetric positive definite)
+                             instead of stationary refinement; the stop test uses the normwise
+                             backward error of the recursively updated residual, confirmed on the
+                             true residual b - A x (restarting from x if they disagree);
+                             iterations = preconditioner applications after the first; 0 = off */
     int root_f64;         /* FP32-family fronts: the pivot blocks of the large fronts in the top
                              root_f64 Foata classes (1 = the root's class) are factored and inverted
                              in FP64 from the FP32 front and rounded once to FP32; 0 = none (default) */

@@ -299,6 +299,8 @@ struct mf_factors {
     double* d_elemvals = nullptr;
     double *d_r = nullptr, *d_d = nullptr, *d_Y = nullptr, *d_rowabs = nullptr, *d_part = nullptr, *d_norms = nullptr;
     double* d_colabs = nullptr;  // column sums of |A| (||A^T||_inf of the adjoint refinement)
+    // conjugate-gradient refinement: search direction p, s = -A p, a zero right-hand side, scalars
+    double *d_cgp = nullptr, *d_cgs = nullptr, *d_zero = nullptr, *d_cg = nullptr;
     bool colabs_valid = false;
     const double* colabs_values = nullptr;
     int norm_blocks = 296;
@@ -392,7 +394,7 @@ static void free_factors(mf_factors* f) {
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_vsrc, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
-                    f->d_vec, f->d_flist, f->d_frec, f->d_fwoff, f->d_fws, f->d_fxs, f->d_pdiag, f->d_symt, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
+                    f->d_vec, f->d_flist, f->d_frec, f->d_fwoff, f->d_fws, f->d_fxs, f->d_pdiag, f->d_symt, f->d_cgp, f->d_cgs, f->d_zero, f->d_cg, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
                     f->d_csr_dest, f->d_elemvals, f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms, f->d_colabs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1420,6 +1422,17 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     TRY(dev_alloc(&F->d_colabs, (size_t)a->n_dof));
     TRY(dev_alloc(&F->d_part, (size_t)F->norm_blocks * 6 * F->max_nrhs));
     TRY(dev_alloc(&F->d_norms, (size_t)6 * F->max_nrhs));
+    if (F->sym && F->opt.refine_cg) {
+        TRY(dev_alloc(&F->d_cgp, nv));
+        TRY(dev_alloc(&F->d_cgs, nv));
+        TRY(dev_alloc(&F->d_zero, nv));
+        TRY(dev_alloc(&F->d_cg, (size_t)4 * F->max_nrhs));
+        if (cudaMemset(F->d_zero, 0, nv * sizeof(double)) != cudaSuccess ||
+            cudaMemset(F->d_cg, 0, 4 * F->max_nrhs * sizeof(double)) != cudaSuccess) {
+            free_factors(F);
+            return MF_ECUDA;
+        }
+    }
     TRY(build_plan(F));
     {
         // the mid-size solve kernels keep kRhsChunk right-hand sides of a front in shared memory
@@ -2093,8 +2106,7 @@ static int refine_impl(mf_factors* F, const double* d_values, const double* d_b,
     std::vector<double> h(6 * nrhs);
     int it = 0;
     double eta = 0, rel = 0;
-    if ((rc = run_graph(F, kind0, d_values, d_b, d_x, nrhs, s, start))) return rc;
-    for (;;) {
+    auto read_eta = [&]() -> int {
         CUDA_TRY(cudaMemcpyAsync(h.data(), F->d_norms, sizeof(double) * 6 * nrhs, cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
         const double anorm = h[5];
@@ -2107,9 +2119,74 @@ static int refine_impl(mf_factors* F, const double* d_values, const double* d_b,
             eta = std::max(eta, e);
             rel = std::max(rel, q[4] > 0 ? std::sqrt(q[3] / q[4]) : std::sqrt(q[3]));
         }
-        if (eta <= tol || it >= maxit || !std::isfinite(eta)) break;
-        if ((rc = run_graph(F, kind0 + 1, d_values, d_b, d_x, nrhs, s, step))) return rc;
-        it++;
+        return MF_OK;
+    };
+    if ((rc = run_graph(F, kind0, d_values, d_b, d_x, nrhs, s, start))) return rc;
+    if ((rc = read_eta())) return rc;
+    if (F->sym && F->opt.refine_cg && !trans && maxit > 0 && eta > tol && std::isfinite(eta)) {
+        // Preconditioned conjugate gradients in FP64, M^-1 = L^-T D L^-1 from the FP32 factors:
+        //   cg_step(first): z = M^-1 r; rho' = r^T z; p = z (first) or z + (rho'/rho) p; rho = rho';
+        //                   s = -A p; x += alpha p, r += alpha s, alpha = -rho / p^T s; norms of r
+        // The loop stops on the recursively updated residual, then recomputes the true one (the
+        // start graph's residual step) and restarts from the current x if drift left it above tol.
+        const unsigned nb = (unsigned)F->norm_blocks;
+        const dim3 gv((unsigned)((n + 255) / 256), nrhs);
+        auto cg_step = [&](bool first) {
+            return [&, first](cudaStream_t st) -> int {
+                int sl = prof_begin(F, st, FAM_OTHER, 16.0 * n * nrhs, 0, 0);
+                CUDA_TRY(cudaMemcpyAsync(F->d_d, F->d_r, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, st));
+                prof_end(F, st, sl);
+                int r2;
+                if ((r2 = solve_common(F, F->d_d, nrhs, false, (mf_stream_t)st))) return r2;
+                sl = prof_begin(F, st, FAM_OTHER, 16.0 * n * nrhs, 2.0 * n * nrhs, 2);
+                k_dot_partial<<<dim3(nb, nrhs), 256, 0, st>>>(F->d_r, F->d_d, n, F->d_part);
+                k_dot_final<<<nrhs, 32, 0, st>>>(F->d_part, nb, F->d_cg, first ? 0 : 2);
+                prof_end(F, st, sl);
+                sl = prof_begin(F, st, FAM_OTHER, 24.0 * n * nrhs, 2.0 * n * nrhs, first ? 1 : 2);
+                k_cg_p<<<gv, 256, 0, st>>>(F->d_cgp, F->d_d, F->d_cg, n, first ? 1 : 0);
+                if (!first) k_cg_commit<<<1, 32, 0, st>>>(F->d_cg, nrhs);
+                prof_end(F, st, sl);
+                CUDA_TRY(cudaGetLastError());
+                if ((r2 = residual_into(F, d_values, F->d_cgp, F->d_zero, F->d_cgs, nrhs, st, false))) return r2;
+                sl = prof_begin(F, st, FAM_OTHER, 48.0 * n * nrhs, 6.0 * n * nrhs, 3);
+                k_dot_partial<<<dim3(nb, nrhs), 256, 0, st>>>(F->d_cgp, F->d_cgs, n, F->d_part);
+                k_dot_final<<<nrhs, 32, 0, st>>>(F->d_part, nb, F->d_cg, 1);
+                k_cg_xr<<<gv, 256, 0, st>>>(d_x, F->d_r, F->d_cgp, F->d_cgs, F->d_cg, n);
+                prof_end(F, st, sl);
+                CUDA_TRY(cudaGetLastError());
+                sl = prof_begin(F, st, FAM_RESID, 24.0 * n * nrhs, 5.0 * n * nrhs, 2);
+                k_norms_partial<<<dim3(nb, nrhs), 256, 0, st>>>(F->d_r, d_x, d_b, anorm_rows, n, F->d_part);
+                k_norms_final<<<nrhs, 32, 0, st>>>(F->d_part, nb, F->d_norms);
+                prof_end(F, st, sl);
+                CUDA_TRY(cudaGetLastError());
+                return MF_OK;
+            };
+        };
+        auto true_residual = [&](cudaStream_t st) -> int { return residual_norms(st); };
+        // graph kinds 7-9: CG restart step, CG step, true residual (forward system only)
+        if ((rc = run_graph(F, 7, d_values, d_b, d_x, nrhs, s, cg_step(true)))) return rc;
+        it = 1;
+        for (;;) {
+            if ((rc = read_eta())) return rc;
+            if (!std::isfinite(eta)) break;
+            if (eta <= tol || it >= maxit) {
+                if ((rc = run_graph(F, 9, d_values, d_b, d_x, nrhs, s, true_residual))) return rc;
+                if ((rc = read_eta())) return rc;
+                if (eta <= tol || it >= maxit || !std::isfinite(eta)) break;
+                if ((rc = run_graph(F, 7, d_values, d_b, d_x, nrhs, s, cg_step(true)))) return rc;
+                it++;
+                continue;
+            }
+            if ((rc = run_graph(F, 8, d_values, d_b, d_x, nrhs, s, cg_step(false)))) return rc;
+            it++;
+        }
+    } else {
+        for (;;) {
+            if (eta <= tol || it >= maxit || !std::isfinite(eta)) break;
+            if ((rc = run_graph(F, kind0 + 1, d_values, d_b, d_x, nrhs, s, step))) return rc;
+            it++;
+            if ((rc = read_eta())) return rc;
+        }
     }
     if (info) {
         info->iterations = it;

@@ -1165,6 +1165,75 @@ __global__ void k_norms_final(const double* __restrict__ part, int nblk, double*
     }
 }
 
+// Conjugate-gradient refinement (symmetric factors, option refine_cg): the
+// FP32 factors give M = L D^-1 L^T, symmetric positive definite for an SPD
+// A, so the FP64 correction loop can be the preconditioned conjugate
+// gradient method instead of stationary refinement.  Per right-hand side r,
+// cg[4r .. 4r+3] = {rho = r^T z, p^T s (s = -A p), rho of the next step, spare}.
+// Dot products: per block partial sums in a fixed order, then one warp per
+// right-hand side adds them in a fixed order (deterministic).
+__global__ void k_dot_partial(const double* __restrict__ a, const double* __restrict__ b, int64_t n, double* __restrict__ part) {
+    __shared__ double red[8];
+    const int r = blockIdx.y;
+    const double* aa = a + (int64_t)r * n;
+    const double* bb = b + (int64_t)r * n;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(aa[i], bb[i], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        part[(int64_t)r * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// cg[4 r + slot] = sum of the partial sums of right-hand side r
+__global__ void k_dot_final(const double* __restrict__ part, int nblk, double* __restrict__ cg, int slot) {
+    const int r = blockIdx.x, lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) return;
+    double t = 0.0;
+    for (int i = lane; i < nblk; i += 32) t += part[(int64_t)r * nblk + i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) cg[4 * r + slot] = t;
+}
+
+// x += alpha p, r += alpha s with s = -A p and alpha = rho / (p^T A p) = -rho / (p^T s)
+__global__ void k_cg_xr(double* __restrict__ x, double* __restrict__ rv, const double* __restrict__ p,
+                        const double* __restrict__ sv, const double* __restrict__ cg, int64_t n) {
+    const int r = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double den = cg[4 * r + 1];
+    const double alpha = den != 0.0 ? -cg[4 * r] / den : 0.0;
+    const int64_t q = (int64_t)r * n + i;
+    x[q] = fma(alpha, p[q], x[q]);
+    rv[q] = fma(alpha, sv[q], rv[q]);
+}
+
+// p = z + beta p with beta = rho_next / rho (first: p = z); then rho := rho_next (k_cg_commit)
+__global__ void k_cg_p(double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ cg, int64_t n,
+                       int first) {
+    const int r = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t q = (int64_t)r * n + i;
+    if (first) {
+        p[q] = z[q];
+        return;
+    }
+    const double rho = cg[4 * r];
+    const double beta = rho != 0.0 ? cg[4 * r + 2] / rho : 0.0;
+    p[q] = fma(beta, p[q], z[q]);
+}
+
+__global__ void k_cg_commit(double* __restrict__ cg, int nrhs) {
+    const int r = threadIdx.x;
+    if (r < nrhs) cg[4 * r] = cg[4 * r + 2];
+}
+
 // Symmetric factors (A = L D^-1 L^T, D = diag(L)): between the forward sweep
 // with L and the backward sweep with L^T the pivot values are multiplied by
 // their pivots, z = D y.  diag_off[d]: factor-arena offset of dof d's pivot.
