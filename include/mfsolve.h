@@ -331,7 +331,8 @@ int mf_profile_read(mf_factors* f, double* ms, int64_t* launches, double* bytes,
  * in issue order.  kind: 0 fused small fronts, 1 large-front assembly,
  * 2 panel diagonal block, 3 SIMT GEMM, 4 pivot-block inverses, 5 subtree
  * factorization, 6 tensor-core GEMM, 7 lane-group tiny fronts, 8 tensor-core
- * operand packing, 9 scalar-task Foata executor, or one of the
+ * operand packing, 9 scalar-task Foata executor, 13 symmetric-mode U12 copy,
+ * 14 symmetric-mode contribution-block mirror, or one of the
  * MF_TRACE_* codes below;
  * cls: 0-based Foata class or -1; tasks: fronts, tiles or tasks in the launch.
  * Call before mf_profile_read (which clears the trace).  Writes at most `cap`

@@ -73,7 +73,7 @@ class mf_trace_rec(ctypes.Structure):
 
 
 TRACE_KINDS = {0: "fused", 1: "assemble", 2: "panel_diag", 3: "gemm", 4: "inv_diag", 5: "subtree", 6: "gemm_tc",
-               7: "fused_grp", 8: "tc_pack", 9: "foata",
+               7: "fused_grp", 8: "tc_pack", 9: "foata", 13: "sym_r", 14: "sym_mirror",
                100: "fwd_class", 101: "bwd_class", 102: "subtree_fwd", 103: "subtree_bwd", 104: "fwd_sweep",
                105: "bwd_sweep", 199: "other"}
 

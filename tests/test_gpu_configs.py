@@ -194,24 +194,39 @@ def test_adjoint_gradient_fp32_fronts_refined(prec):
     assert np.linalg.norm(gh - go) <= 1e-9 * np.linalg.norm(go)
 
 
-def test_headline_512_q3_tuned_plan_against_the_oracle():
-    """The benchmark's own workload and plan: 2D heterogeneous diffusion on 512^2 Q3 elements
-    (2,362,369 dofs), FP32 fronts with the tuned plan from the package's plan cache, CUDA-graph
-    replay.  (a) At the benchmark's stop (device normwise backward error <= 1e-12) the host
-    recomputes the backward error with a double-double residual and the assembled ||A||_inf.
-    (b) Refined further, to the FP64 floor, the solution matches the oracle's (FP64 multifrontal
-    factorization refined with a double-double residual, i.e. accurate to a few ulps) to 1e-10."""
-    from paper_2306_08994_b300 import autotune as AT
+@pytest.fixture(scope="module")
+def headline():
+    """2D heterogeneous diffusion on 512^2 Q3 elements (2,362,369 dofs) and the oracle's solution
+    (FP64 multifrontal factorization refined with a double-double residual: a few ulps)."""
     pr = F.diffusion_2d(512, 3, seed=F.SEED_BASE + 2)
     pm = pr.mesh
+    s = O.OracleSolver(pm.n_nodes, pm.elem_nodes, O.tree_bisection(pm.nel))
+    assert s.factor(F.to_colmajor(pr.Ke), nthreads=O.max_threads()) == 0
+    xo, _ = s.solve_refined(pr.b[:, 0])
+    del s
+    return pr, xo
+
+
+@pytest.mark.parametrize("sym,cg", [(1, 1), (0, 0)])
+def test_headline_512_q3_tuned_plan_against_the_oracle(headline, sym, cg):
+    """The benchmark's own workload and plan: FP32 fronts with the tuned plan from the package's plan
+    cache, CUDA-graph replay; symmetric factors with conjugate-gradient refinement (the benchmark's
+    default) and general LU with stationary refinement.  (a) At the benchmark's stop (device normwise
+    backward error <= 1e-12) the host recomputes the backward error with a double-double residual
+    and the assembled ||A||_inf.  (b) Refined further, to the FP64 floor, the solution matches the
+    oracle's to 1e-10."""
+    from paper_2306_08994_b300 import autotune as AT
+    pr, xo = headline
+    pm = pr.mesh
     an = M.Analysis(M.Mesh(pm.elem_nodes, pm.n_nodes, 2, grid_dims=pm.nel),
-                    M.default_options(precision="f32", max_nrhs=4, use_graph=1))
+                    M.default_options(precision="f32", max_nrhs=4, use_graph=1, symmetric=sym, refine_cg=cg))
     assert an.info["n_dof"] == 2362369 and an.info["root_m"] == 1537
     vals = torch.tensor(F.to_colmajor(pr.Ke), device=DEV)
     b = torch.tensor(pr.b[:, 0], device=DEV)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         opts, tinfo = AT.tune(an, vals, b, cache_path=AT.DEFAULT_CACHE, stream=stream)
+        assert opts.symmetric == sym and opts.refine_cg == cg
         f = M.Factors(an, opts)
         x = torch.empty_like(b)
         f.factor(vals, stream=stream)
@@ -224,13 +239,10 @@ def test_headline_512_q3_tuned_plan_against_the_oracle():
     assert i1["rc"] == 0 and i1["backward_error"] <= 1e-12, i1
     eta_stop = _eta_host(pm, pr.Ke, x_stop, pr.b[:, 0])
     assert eta_stop <= 1e-12, eta_stop
-    s = O.OracleSolver(pm.n_nodes, pm.elem_nodes, O.tree_bisection(pm.nel))
-    assert s.factor(F.to_colmajor(pr.Ke), nthreads=O.max_threads()) == 0
-    xo, _ = s.solve_refined(pr.b[:, 0])
     xg = x.cpu().numpy()
     err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
-    print(f"512^2 Q3 tuned plan: stop eta {i1['backward_error']:.2e} (host {eta_stop:.2e}) after "
-          f"{i1['iterations']} corrections; refined eta {i2['backward_error']:.2e} after {i2['iterations']}; "
+    print(f"512^2 Q3 tuned plan (symmetric {sym}, CG {cg}): stop eta {i1['backward_error']:.2e} (host {eta_stop:.2e}) "
+          f"after {i1['iterations']} corrections; refined eta {i2['backward_error']:.2e} after {i2['iterations']}; "
           f"rel. error vs oracle {err:.2e}; rel. error at the stop {np.linalg.norm(x_stop - xo) / np.linalg.norm(xo):.2e}")
     assert err <= 1e-10, (err, i2)
 
