@@ -55,6 +55,9 @@ WORKLOADS = {
     "diffusion3d_q1_64": (lambda: [F.diffusion_3d_q1(64, seed=F.SEED_BASE + 4)],
                           lambda: [F.structured_mesh((64, 64, 64), 1)], "solve", "f32",
                           "3D diffusion, 64^3 Q1, k=10^U(-1,1), 274,625 dofs"),
+    "diffusion3d_q1_32": (lambda: [F.diffusion_3d_q1(32, seed=F.SEED_BASE + 4)],
+                          lambda: [F.structured_mesh((32, 32, 32), 1)], "solve", "f32",
+                          "3D diffusion, 32^3 Q1, k=10^U(-1,1), 35,937 dofs (small case of the 64^3 recipe)"),
     "adjoint2d_q1_1024": (lambda: [F.adjoint_problem(1024)], lambda: [F.structured_mesh((1024, 1024), 1)],
                           "adjoint", "f32",
                           "adjoint: 2D Q1 diffusion 1024x1024, theta = log k ~ N(0,1), J = 1/2|u - u_target|^2, "
@@ -79,6 +82,7 @@ CPU_SAMPLE = {
     "diffusion2d_q3_128": ("diffusion2d_q3_128", None),
     "batched_q1_256meshes": ("batched_q1_256meshes", None),
     "diffusion3d_q1_64": ("diffusion3d_q1_32", lambda: [F.diffusion_3d_q1(32, seed=F.SEED_BASE + 4)]),
+    "diffusion3d_q1_32": ("diffusion3d_q1_32", None),
     "adjoint2d_q1_1024": ("adjoint2d_q1_1024", None),
     "poisson2d_q1_16": ("poisson2d_q1_16", None),
 }
@@ -331,6 +335,10 @@ def main():
                          "these symmetric positive definite workloads)")
     ap.add_argument("--refine-trial", action="store_true",
                     help="also measure the tuned plan with the other refinement method (stationary vs. CG)")
+    ap.add_argument("--trace-once", action="store_true",
+                    help="one untimed factorization with the launch trace on, printed one JSON record per launch "
+                         "(kind, class, tasks, algorithmic bytes and flops) in issue order, for matching ncu "
+                         "captures to their algorithmic work; no timed steps")
     ap.add_argument("--general", action="store_true",
                     help="factor as a general matrix (LU with both triangles) instead of using its symmetry; every "
                          "workload here is symmetric positive definite")
@@ -406,6 +414,18 @@ def main():
 
     opts, tinfo = plan_for(an)
     fac = M.Factors(an, opts)
+    if args.trace_once:
+        # launches are issued directly (no graph replay) while the trace is on, so the records come
+        # in the order the GPU receives the kernels; within a record, one kernel per plan entry
+        fac.profile(True)
+        fac.profile_read()
+        fac.factor(vals)
+        if rank == 0:
+            for i, rec in enumerate(fac.trace()):
+                print(json.dumps(dict(rec, index=i)), flush=True)
+        fac.profile_read()
+        fac.profile(False)
+        return
 
     def step(f, v, bb, xx, kv=None, kut=None, tol=TOL, maxit=60):
         f.factor(v)
