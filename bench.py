@@ -347,6 +347,9 @@ def main():
                          "one and three BF16 passes): refinement contraction, corrections and step time")
     ap.add_argument("--root-f64-trial", type=int, default=0,
                     help="also measure the tuned plan with the pivot blocks of the top N classes in FP64")
+    ap.add_argument("--panel-trial", action="store_true",
+                    help="also measure the tuned plan with the other panel method of the large-front partial LU "
+                         "(triangular solves vs. products with explicit pivot-block inverses)")
     ap.add_argument("--sym-trial", action="store_true",
                     help="also measure the tuned plan in symmetric mode (L only beyond the pivot blocks, lower-half "
                          "Schur updates, x = L^-T D L^-1 b)")
@@ -579,7 +582,7 @@ def main():
 
     trials = {}
     if kind == "solve" and (args.bf16_trial or args.root_f64_trial or args.foata_trial or args.sym_trial or
-                            args.refine_trial):
+                            args.refine_trial or args.panel_trial):
         import copy
         trials["tuned"] = time_variant(opts)
         if args.bf16_trial:
@@ -594,6 +597,10 @@ def main():
             o2 = copy.copy(opts)
             o2.root_f64 = args.root_f64_trial
             trials[f"root_f64_{args.root_f64_trial}"] = time_variant(o2)
+        if args.panel_trial:
+            o2 = copy.copy(opts)
+            o2.panel_inverse = 1 - opts.panel_inverse
+            trials["panel_inverse" if o2.panel_inverse else "panel_trsm"] = time_variant(o2)
         if args.refine_trial and opts.symmetric:
             o2 = copy.copy(opts)
             o2.refine_cg = 1 - opts.refine_cg

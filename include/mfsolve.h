@@ -124,6 +124,10 @@ typedef struct {
                              backward error of the recursively updated residual, confirmed on the
                              true residual b - A x (restarting from x if they disagree);
                              iterations = preconditioner applications after the first; 0 = off */
+    int panel_inverse;    /* large-front partial LU: 0 (default) = each pivot block's panel is finished
+                             by triangular solves against the factored block (one thread per row or
+                             column); nonzero = the pivot-block kernel also inverts both triangles and
+                             the panel is finished by products with the inverses */
     int root_f64;         /* FP32-family fronts: the pivot blocks of the large fronts in the top
                              root_f64 Foata classes (1 = the root's class) are factored and inverted
                              in FP64 from the FP32 front and rounded once to FP32; 0 = none (default) */
@@ -332,7 +336,7 @@ int mf_profile_read(mf_factors* f, double* ms, int64_t* launches, double* bytes,
  * 2 panel diagonal block, 3 SIMT GEMM, 4 pivot-block inverses, 5 subtree
  * factorization, 6 tensor-core GEMM, 7 lane-group tiny fronts, 8 tensor-core
  * operand packing, 9 scalar-task Foata executor, 13 symmetric-mode U12 copy,
- * 14 symmetric-mode contribution-block mirror, or one of the
+ * 14 symmetric-mode contribution-block mirror, 15 panel triangular solves, or one of the
  * MF_TRACE_* codes below;
  * cls: 0-based Foata class or -1; tasks: fronts, tiles or tasks in the launch.
  * Call before mf_profile_read (which clears the trace).  Writes at most `cap`

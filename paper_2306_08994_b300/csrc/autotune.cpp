@@ -36,7 +36,7 @@ constexpr double kTuneTol = 1e-12;  // refinement target of the timed candidates
 
 int family_of(int precision) { return precision == MF_F64 ? 0 : 1; }
 
-std::string cache_key(const mf_analysis* a, int precision) {
+std::string cache_key(const mf_analysis* a, int precision, int symmetric, int refine_cg) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceProp p{};
@@ -49,7 +49,11 @@ std::string cache_key(const mf_analysis* a, int precision) {
                   kPlanVersion, name.c_str(), p.multiProcessorCount, family_of(precision) == 0 ? "f64" : "f32", a->dim, a->npe,
                   a->n_meshes, (long long)a->n_dof, a->n_front, a->n_cls, a->info.max_m, a->info.max_k,
                   a->info.factor_flops);
-    return buf;
+    std::string key = buf;
+    // symmetric factors and CG refinement are timed as such: their plans are cached apart (the general
+    // LU with stationary refinement keeps the key it always had)
+    if (symmetric) key += refine_cg ? ":sym:cg" : ":sym";
+    return key;
 }
 
 // Value after `"field":` in a one-line JSON object, or nullptr.
@@ -194,7 +198,7 @@ extern "C" int mf_autotune(const mf_analysis* a, const double* d_values, const d
     if (o.precision != MF_F64 && o.precision != MF_F32 && o.precision != MF_TF32 && o.precision != MF_TF32_BF16)
         return MF_EINVAL;
     const int user_graph = o.use_graph;
-    const std::string key = cache_key(a, o.precision);
+    const std::string key = cache_key(a, o.precision, o.symmetric, o.refine_cg);
     if (info) *info = mf_tune_info{};
     if (cache_path) {
         mf_options t = o;

@@ -31,7 +31,7 @@ bool mf_alloc_should_fail() {
 namespace {
 
 enum LaunchKind { K_FUSED = 0, K_ASM = 1, K_PDIAG = 2, K_GEMM = 3, K_INVDIAG = 4, K_SUBTREE = 5, K_GEMMTC = 6, K_GRP = 7,
-                  K_TCPACK = 8, K_FOATA = 9, K_FORK = 10, K_JOIN = 11, K_SYMR = 13, K_MIRROR = 14,
+                  K_TCPACK = 8, K_FOATA = 9, K_FORK = 10, K_JOIN = 11, K_SYMR = 13, K_MIRROR = 14, K_TRSM = 15,
                   K_SYNC = 12 };  // K_SYNC: stream `stream` waits for what stream `bucket` issued so far (event `off`)
 
 struct Launch {
@@ -260,6 +260,8 @@ struct mf_factors {
     bool sym = false;                 // symmetric factors and solves (option symmetric)
     int64_t* d_pdiag = nullptr;       // symmetric solves: factor-arena offset of each dof's pivot
     AsmTile* d_symt = nullptr;        // tiles of the symmetric-mode R copies and S mirrors
+    TrsmTask* d_trsm = nullptr;       // triangular-solve panel tasks
+    bool pinv = false;                // panel products through explicit pivot-block inverses (option)
     int64_t* d_fwoff = nullptr;
     void* d_fws = nullptr;
     void* d_fxs = nullptr;
@@ -394,7 +396,7 @@ static void free_factors(mf_factors* f) {
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_vsrc, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
-                    f->d_vec, f->d_flist, f->d_frec, f->d_fwoff, f->d_fws, f->d_fxs, f->d_pdiag, f->d_symt, f->d_cgp, f->d_cgs, f->d_zero, f->d_cg, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
+                    f->d_vec, f->d_flist, f->d_frec, f->d_fwoff, f->d_fws, f->d_fxs, f->d_pdiag, f->d_symt, f->d_trsm, f->d_cgp, f->d_cgs, f->d_zero, f->d_cg, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
                     f->d_csr_dest, f->d_elemvals, f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms, f->d_colabs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -479,6 +481,7 @@ static int build_plan(mf_factors* F) {
     std::vector<int32_t> flist, slist;
     std::vector<int64_t> fwoff;  // parallel to flist: Foata workspace offsets (-1 for other kernels' fronts)
     std::vector<AsmTile> symt;   // symmetric mode: R tiles and S mirror tiles
+    std::vector<TrsmTask> trs;   // triangular-solve panel tasks
     std::vector<RowBlock> rows;
     std::vector<InvTask> invt;
     std::vector<AsmTile> asmt;
@@ -937,10 +940,30 @@ static int build_plan(mf_factors* F) {
                 push({K_SYNC, c, 0, 0, F->n_sync++, 2}, FAM_OTHER, 0.0, 0.0);
                 la_pending = false;
             }
-            // (B) panel products in place: L21 = A21 U_D^-1, U12 = L_D^-1 A12
+            // (B) the panel: L21 = A21 U_D^-1, U12 = L_D^-1 A12, by triangular solves against the
+            //     factored pivot block (default) or as products with its explicit inverses
+            if (!F->pinv) {
+                const int64_t toff = (int64_t)trs.size();
+                double tb = 0, tf = 0;
+                for (size_t bi = 0; bi < big.size(); bi++) {
+                    const int32_t f = big[bi];
+                    const FrontDev& fr = a->fronts[f];
+                    if (kb >= fr.k) continue;
+                    const int m = fr.m, k = fr.k, w = std::min(nb, k - kb), r0 = kb + w;
+                    const int ns[3] = {m - r0, k - r0, F->sym ? 0 : m - k};
+                    for (int side = 0; side < 3; side++) {
+                        for (int i0 = 0; i0 < ns[side]; i0 += 128)
+                            trs.push_back({f, kb, w, side, i0, std::min(128, ns[side] - i0)});
+                        tb += T * (2.0 * w * ns[side]);
+                        tf += (double)w * w * ns[side];
+                    }
+                    tb += T * (double)w * w;
+                }
+                if (trs.size() > (size_t)toff) push({K_TRSM, c, (int)(trs.size() - toff), 0, toff}, FAM_PANEL, tb, tf);
+            }
             int64_t goff = (int64_t)gem.size();
             gb = gf = 0;
-            for (size_t bi = 0; bi < big.size(); bi++) {
+            for (size_t bi = 0; bi < big.size() && F->pinv; bi++) {
                 const FrontDev& fr = a->fronts[big[bi]];
                 if (kb >= fr.k) continue;
                 const int m = fr.m, k = fr.k, w = std::min(nb, k - kb), r0 = kb + w;
@@ -1044,16 +1067,22 @@ static int build_plan(mf_factors* F) {
         }
         if (gem.size() > (size_t)goff) push({K_GEMM, c, (int)(gem.size() - goff), 0, goff}, FAM_SCHUR, gb, gf);
         tc_end(c, FAM_SCHUR);
-        if (F->sym) {  // S[j, i] = S[i, j], i > j
+        if (F->sym) {  // S[j, i] = S[i, j] for the 64 x 64 tiles above the diagonal the update skipped
             const int64_t off = (int64_t)symt.size();
             double by = 0;
             for (int32_t f : big) {
                 const FrontDev& fr = a->fronts[f];
                 const int nc = fr.m - fr.k;
                 if (nc <= 1 || fr.k <= 0) continue;
+                const bool on_tc = use_tc(nc, nc, fr.k);
                 for (int j0 = 0; j0 < nc; j0 += 64)
-                    for (int i0 = j0; i0 < nc; i0 += 64) symt.push_back({f, i0, j0, 0});
-                by += T * (double)nc * (nc - 1);
+                    for (int i0 = j0 + 64; i0 < nc; i0 += 64) {
+                        // target tile: rows j0.., columns i0..; a tensor-core tile (128 x 256) that
+                        // reaches the diagonal computed it already
+                        if (on_tc && ((j0 / tc::kTileM) + 1) * tc::kTileM > (i0 / tc::kTileN) * tc::kTileN) continue;
+                        symt.push_back({f, i0, j0, 0});
+                        by += 2.0 * T * std::min(64, nc - i0) * std::min(64, nc - j0);
+                    }
             }
             if (symt.size() > (size_t)off) push({K_MIRROR, c, (int)(symt.size() - off), 0, off}, FAM_SCHUR, by, 0.0);
         }
@@ -1235,6 +1264,7 @@ static int build_plan(mf_factors* F) {
     if ((rc = upload(&F->d_sweep_f, F->sweep_f))) return rc;
     if ((rc = upload(&F->d_sweep_b, F->sweep_b))) return rc;
     if (!symt.empty() && (rc = upload(&F->d_symt, symt))) return rc;
+    if (!trs.empty() && (rc = upload(&F->d_trsm, trs))) return rc;
     if ((rc = upload(&F->d_flist, flist))) return rc;
     fwoff.resize(flist.size(), -1);
     if ((rc = upload(&F->d_fwoff, fwoff))) return rc;
@@ -1346,6 +1376,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     F->la = F->opt.lookahead >= 0;
     F->foata_cls = std::max(0, F->opt.foata_classes);
     F->sym = F->opt.symmetric != 0;
+    F->pinv = F->opt.panel_inverse != 0;
     for (int i = 0; i < MF_FUSED_BUCKETS; i++) {
         const int t = F->opt.fused_threads[i];
         if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256) {
@@ -1485,18 +1516,19 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
             }
     }
     {
-        const cudaError_t e = F->prec == MF_F64
-                                  ? cudaFuncSetAttribute(k_panel_diag_blk<double, kPanelNB64>,
-                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                         (int)panel_diag_dyn_smem<double, kPanelNB64>())
-                                  : cudaFuncSetAttribute(k_panel_diag_blk<float, kPanelNB32>,
-                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                         (int)panel_diag_dyn_smem<float, kPanelNB32>());
-        const cudaError_t e2 = F->prec == MF_F64
-                                   ? cudaSuccess
-                                   : cudaFuncSetAttribute(k_panel_diag_blk<float, kPanelNB32, double>,
-                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                          (int)panel_diag_dyn_smem<float, kPanelNB32, double>());
+        const int s64 = (int)panel_diag_dyn_smem<double, kPanelNB64>(), s32 = (int)panel_diag_dyn_smem<float, kPanelNB32>();
+        const int sw = (int)panel_diag_dyn_smem<float, kPanelNB32, double>();
+        constexpr cudaFuncAttribute kA = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        cudaError_t e = cudaSuccess, e2 = cudaSuccess;
+        if (F->prec == MF_F64) {
+            e = cudaFuncSetAttribute(k_panel_diag_blk<double, kPanelNB64, double, true>, kA, s64);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_diag_blk<double, kPanelNB64, double, false>, kA, s64);
+        } else {
+            e = cudaFuncSetAttribute(k_panel_diag_blk<float, kPanelNB32, float, true>, kA, s32);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_diag_blk<float, kPanelNB32, float, false>, kA, s32);
+            e2 = cudaFuncSetAttribute(k_panel_diag_blk<float, kPanelNB32, double, true>, kA, sw);
+            if (e2 == cudaSuccess) e2 = cudaFuncSetAttribute(k_panel_diag_blk<float, kPanelNB32, double, false>, kA, sw);
+        }
         if (e != cudaSuccess || e2 != cudaSuccess) {
             (void)cudaGetLastError();
             free_factors(F);
@@ -1600,15 +1632,29 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
                 break;
             case K_PDIAG: {
                 constexpr int NB = sizeof(T) == 8 ? kPanelNB64 : kPanelNB32;
+                const DiagTask* dt = F->d_panel + L.off;
                 if constexpr (sizeof(T) == 4) {
                     if (L.wide) {
-                        k_panel_diag_blk<T, NB, double><<<L.count, 256, panel_diag_dyn_smem<T, NB, double>(), s>>>(
-                            F->d_fronts, F->d_panel + L.off, fac, (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
+                        if (F->pinv)
+                            k_panel_diag_blk<T, NB, double, true><<<L.count, 256, panel_diag_dyn_smem<T, NB, double>(), s>>>(
+                                F->d_fronts, dt, fac, (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
+                        else
+                            k_panel_diag_blk<T, NB, double, false><<<L.count, 256, panel_diag_dyn_smem<T, NB, double>(), s>>>(
+                                F->d_fronts, dt, fac, (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
                         break;
                     }
                 }
-                k_panel_diag_blk<T, NB><<<L.count, 256, panel_diag_dyn_smem<T, NB>(), s>>>(F->d_fronts, F->d_panel + L.off, fac,
-                                                                            (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
+                if (F->pinv)
+                    k_panel_diag_blk<T, NB, T, true><<<L.count, 256, panel_diag_dyn_smem<T, NB>(), s>>>(
+                        F->d_fronts, dt, fac, (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
+                else
+                    k_panel_diag_blk<T, NB, T, false><<<L.count, 256, panel_diag_dyn_smem<T, NB>(), s>>>(
+                        F->d_fronts, dt, fac, (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
+                break;
+            }
+            case K_TRSM: {
+                constexpr int NB = sizeof(T) == 8 ? kPanelNB64 : kPanelNB32;
+                k_panel_trsm<T, NB><<<L.count, 128, 0, s>>>(F->d_fronts, F->d_trsm + L.off, fac);
                 break;
             }
             case K_GEMM: {

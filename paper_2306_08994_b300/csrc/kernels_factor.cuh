@@ -424,21 +424,33 @@ __global__ void __launch_bounds__(256) k_sym_r(const FrontDev* __restrict__ fron
     const FrontDev fr = fronts[t.front];
     const int m = fr.m, k = fr.k, nc = m - k;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int pp = warp; pp < 64; pp += 8)
-        for (int jj = lane; jj < 64; jj += 32) {
-            const int p = t.i0 + pp, j = t.j0 + jj;
-            if (p < k && j < nc) tl[pp][jj] = fac[fr.P_off + (k + j) + (int64_t)p * m];
-        }
+    T v[16];
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+        const int pp = warp + 8 * (u >> 1), jj = lane + 32 * (u & 1);
+        const int p = t.i0 + pp, j = t.j0 + jj;
+        v[u] = (p < k && j < nc) ? fac[fr.P_off + (k + j) + (int64_t)p * m] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 16; u++) tl[warp + 8 * (u >> 1)][lane + 32 * (u & 1)] = v[u];
     __syncthreads();
-    for (int jj = warp; jj < 64; jj += 8)
-        for (int pp = lane; pp < 64; pp += 32) {
-            const int p = t.i0 + pp, j = t.j0 + jj;
-            if (p < k && j < nc) fac[fr.R_off + p + (int64_t)j * k] = tl[pp][jj] / fac[fr.P_off + p + (int64_t)p * m];
-        }
+    T d[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int p = t.i0 + lane + 32 * h;
+        d[h] = p < k ? fac[fr.P_off + p + (int64_t)p * m] : T(1);
+    }
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+        const int jj = warp + 8 * (u >> 1), pp = lane + 32 * (u & 1);
+        const int p = t.i0 + pp, j = t.j0 + jj;
+        if (p < k && j < nc) fac[fr.R_off + p + (int64_t)j * k] = tl[pp][jj] / d[u & 1];
+    }
 }
 
-// S[j, i] = S[i, j] for i > j: tile (i0, j0) with i0 >= j0 of the contribution block is read
-// (its entries below the diagonal) and written transposed
+// S[j, i] = S[i, j]: tile (i0, j0), i0 >= j0 + 64 (strictly below the diagonal), of the
+// contribution block is read and written transposed; all 16 loads of a thread are issued before
+// any shared-memory store, all 16 shared loads before the global stores
 template <typename T>
 __global__ void __launch_bounds__(256) k_sym_mirror(const FrontDev* __restrict__ fronts, const AsmTile* __restrict__ tiles,
                                                     T* __restrict__ cbs) {
@@ -448,17 +460,24 @@ __global__ void __launch_bounds__(256) k_sym_mirror(const FrontDev* __restrict__
     const int nc = fr.m - fr.k;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T* S = cbs + fr.S_off;
-    for (int jj = warp; jj < 64; jj += 8)
-        for (int ii = lane; ii < 64; ii += 32) {
-            const int i = t.i0 + ii, j = t.j0 + jj;
-            if (i < nc && j < nc && i > j) tl[ii][jj] = S[i + (int64_t)j * nc];
-        }
+    T v[16];
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+        const int ii = lane + 32 * (u & 1), jj = warp + 8 * (u >> 1);
+        const int i = t.i0 + ii, j = t.j0 + jj;
+        v[u] = (i < nc && j < nc) ? S[i + (int64_t)j * nc] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 16; u++) tl[lane + 32 * (u & 1)][warp + 8 * (u >> 1)] = v[u];
     __syncthreads();
-    for (int ii = warp; ii < 64; ii += 8)
-        for (int jj = lane; jj < 64; jj += 32) {
-            const int i = t.i0 + ii, j = t.j0 + jj;
-            if (i < nc && j < nc && i > j) S[j + (int64_t)i * nc] = tl[ii][jj];
-        }
+#pragma unroll
+    for (int u = 0; u < 16; u++) v[u] = tl[warp + 8 * (u >> 1)][lane + 32 * (u & 1)];
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+        const int ii = warp + 8 * (u >> 1), jj = lane + 32 * (u & 1);
+        const int i = t.i0 + ii, j = t.j0 + jj;
+        if (i < nc && j < nc) S[j + (int64_t)i * nc] = v[u];
+    }
 }
 
 // Pivot block of a large front (NB x NB at pivot kb, padded with the
@@ -481,7 +500,7 @@ __global__ void __launch_bounds__(256) k_sym_mirror(const FrontDev* __restrict__
 // C = double the block is factored and inverted in FP64 from the FP32 front
 // and rounded once on the way out: the FP64 pivot blocks of the root
 // separator fronts on the FP32-front path.
-template <typename T, int NB, typename C = T>
+template <typename T, int NB, typename C = T, bool INV = true>
 __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_diag_blk(const FrontDev* __restrict__ fronts,
                                                         const DiagTask* __restrict__ tasks, T* __restrict__ fac,
                                                         T* __restrict__ slots, const unsigned int* __restrict__ famax,
@@ -662,6 +681,7 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
     // factored block back to P (coalesced)
     for (int j = warp; j < w; j += 8)
         for (int i = lane; i < w; i += 32) P[(kb + i) + (int64_t)(kb + j) * m] = (T)D[i][j];
+    if constexpr (!INV) return;  // the panel is finished by triangular solves (k_panel_trsm)
 
     // ---- inverses, one thread per column: threads 0..NB-1 column c of L_D^-1 (forward),
     //      threads NB..2NB-1 column c of U_D^-1 (backward, unit diagonal).  Right-looking: once
@@ -699,6 +719,67 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
     T* Zg = slots + t.slot;
     for (int j = warp; j < w; j += 8)
         for (int i = lane; i < w; i += 32) Zg[i + j * 64] = (T)Z[i][j];
+}
+
+// ---------------------------------------------------------------------------
+// Panel of a pivot block finished by triangular solves against the factored
+// block D = L_D U_D (Table 2's tasks carried on past the pivot block):
+//   side 0, rows below the block:      x U_D = a   (U_D unit upper)  -> L21
+//   side 1, pivot columns right of it: L_D y = a   (L_D with its diagonal) -> U12 in P
+//   side 2, contribution-block columns: the same, in R
+// 128 threads per CTA, one row (side 0) or column (sides 1, 2) per thread, the
+// row or column in registers, D in shared memory; right-looking, so every step
+// is NB - j independent FMAs.  Each task covers up to 128 rows or columns.
+struct TrsmTask {
+    int32_t front, kb, w, side, i0, n;
+};
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(128) k_panel_trsm(const FrontDev* __restrict__ fronts, const TrsmTask* __restrict__ tasks,
+                                                    T* __restrict__ fac) {
+    __shared__ T D[NB][NB + 1];
+    __shared__ T rdiv[NB];
+    const TrsmTask t = tasks[blockIdx.x];
+    const FrontDev fr = fronts[t.front];
+    const int m = fr.m, k = fr.k, kb = t.kb, w = t.w;
+    T* P = fac + fr.P_off;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = warp; j < NB; j += 4)
+        for (int i = lane; i < NB; i += 32)
+            D[i][j] = (i < w && j < w) ? P[(kb + i) + (int64_t)(kb + j) * m] : (i == j ? T(1) : T(0));
+    __syncthreads();
+    if (threadIdx.x < NB) rdiv[threadIdx.x] = D[threadIdx.x][threadIdx.x];
+    __syncthreads();
+    const int q = threadIdx.x;
+    if (q >= t.n) return;
+    T x[NB];
+    if (t.side == 0) {
+        const int64_t i = kb + w + t.i0 + q;  // row of P
+#pragma unroll
+        for (int j = 0; j < NB; j++) x[j] = j < w ? P[i + (int64_t)(kb + j) * m] : T(0);
+#pragma unroll
+        for (int j = 0; j < NB; j++)
+#pragma unroll
+            for (int j2 = j + 1; j2 < NB; j2++) x[j2] -= x[j] * D[j][j2];
+#pragma unroll
+        for (int j = 0; j < NB; j++)
+            if (j < w) P[i + (int64_t)(kb + j) * m] = x[j];
+        return;
+    }
+    // a column of P right of the block (side 1) or of R (side 2): rows kb .. kb + w
+    T* col = t.side == 1 ? P + kb + (int64_t)(kb + w + t.i0 + q) * m : fac + fr.R_off + kb + (int64_t)(t.i0 + q) * k;
+    (void)k;
+#pragma unroll
+    for (int i = 0; i < NB; i++) x[i] = i < w ? col[i] : T(0);
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+        x[i] = x[i] / rdiv[i];  // the division task T1 by the pivot
+#pragma unroll
+        for (int i2 = i + 1; i2 < NB; i2++) x[i2] -= D[i2][i] * x[i];
+    }
+#pragma unroll
+    for (int i = 0; i < NB; i++)
+        if (i < w) col[i] = x[i];
 }
 
 // ---------------------------------------------------------------------------
