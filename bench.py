@@ -599,8 +599,8 @@ def main():
             trials[f"root_f64_{args.root_f64_trial}"] = time_variant(o2)
         if args.panel_trial:
             o2 = copy.copy(opts)
-            o2.panel_inverse = 1 - opts.panel_inverse
-            trials["panel_inverse" if o2.panel_inverse else "panel_trsm"] = time_variant(o2)
+            o2.panel_trsm = 1 - opts.panel_trsm
+            trials["panel_trsm" if o2.panel_trsm else "panel_inverse"] = time_variant(o2)
         if args.refine_trial and opts.symmetric:
             o2 = copy.copy(opts)
             o2.refine_cg = 1 - opts.refine_cg

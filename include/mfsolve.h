@@ -124,10 +124,10 @@ typedef struct {
                              backward error of the recursively updated residual, confirmed on the
                              true residual b - A x (restarting from x if they disagree);
                              iterations = preconditioner applications after the first; 0 = off */
-    int panel_inverse;    /* large-front partial LU: 0 (default) = each pivot block's panel is finished
-                             by triangular solves against the factored block (one thread per row or
-                             column); nonzero = the pivot-block kernel also inverts both triangles and
-                             the panel is finished by products with the inverses */
+    int panel_trsm;       /* large-front partial LU: 0 (default) = the pivot-block kernel also inverts
+                             both triangles and the panel is finished by products with the inverses;
+                             nonzero = the panel is finished by triangular solves against the factored
+                             block (one thread per row or column; slower here, kept as an option) */
     int root_f64;         /* FP32-family fronts: the pivot blocks of the large fronts in the top
                              root_f64 Foata classes (1 = the root's class) are factored and inverted
                              in FP64 from the FP32 front and rounded once to FP32; 0 = none (default) */

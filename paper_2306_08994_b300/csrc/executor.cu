@@ -261,7 +261,7 @@ struct mf_factors {
     int64_t* d_pdiag = nullptr;       // symmetric solves: factor-arena offset of each dof's pivot
     AsmTile* d_symt = nullptr;        // tiles of the symmetric-mode R copies and S mirrors
     TrsmTask* d_trsm = nullptr;       // triangular-solve panel tasks
-    bool pinv = false;                // panel products through explicit pivot-block inverses (option)
+    bool pinv = true;                 // panel products through explicit pivot-block inverses (default)
     int64_t* d_fwoff = nullptr;
     void* d_fws = nullptr;
     void* d_fxs = nullptr;
@@ -940,8 +940,8 @@ static int build_plan(mf_factors* F) {
                 push({K_SYNC, c, 0, 0, F->n_sync++, 2}, FAM_OTHER, 0.0, 0.0);
                 la_pending = false;
             }
-            // (B) the panel: L21 = A21 U_D^-1, U12 = L_D^-1 A12, by triangular solves against the
-            //     factored pivot block (default) or as products with its explicit inverses
+            // (B) the panel: L21 = A21 U_D^-1, U12 = L_D^-1 A12, as products with the pivot block's
+            //     explicit inverses (default) or by triangular solves against the factored block
             if (!F->pinv) {
                 const int64_t toff = (int64_t)trs.size();
                 double tb = 0, tf = 0;
@@ -1376,7 +1376,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     F->la = F->opt.lookahead >= 0;
     F->foata_cls = std::max(0, F->opt.foata_classes);
     F->sym = F->opt.symmetric != 0;
-    F->pinv = F->opt.panel_inverse != 0;
+    F->pinv = F->opt.panel_trsm == 0;
     for (int i = 0; i < MF_FUSED_BUCKETS; i++) {
         const int t = F->opt.fused_threads[i];
         if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256) {

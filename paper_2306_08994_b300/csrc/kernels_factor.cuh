@@ -758,9 +758,13 @@ __global__ void __launch_bounds__(128) k_panel_trsm(const FrontDev* __restrict__
 #pragma unroll
         for (int j = 0; j < NB; j++) x[j] = j < w ? P[i + (int64_t)(kb + j) * m] : T(0);
 #pragma unroll
-        for (int j = 0; j < NB; j++)
+        for (int j = 0; j < NB; j++) {
+            // keep each step's shared-memory reads inside the step (hoisting them all ahead would
+            // need ~NB^2/2 registers)
+            asm volatile("" ::: "memory");
 #pragma unroll
             for (int j2 = j + 1; j2 < NB; j2++) x[j2] -= x[j] * D[j][j2];
+        }
 #pragma unroll
         for (int j = 0; j < NB; j++)
             if (j < w) P[i + (int64_t)(kb + j) * m] = x[j];
@@ -773,6 +777,7 @@ __global__ void __launch_bounds__(128) k_panel_trsm(const FrontDev* __restrict__
     for (int i = 0; i < NB; i++) x[i] = i < w ? col[i] : T(0);
 #pragma unroll
     for (int i = 0; i < NB; i++) {
+        asm volatile("" ::: "memory");
         x[i] = x[i] / rdiv[i];  // the division task T1 by the pivot
 #pragma unroll
         for (int i2 = i + 1; i2 < NB; i2++) x[i2] -= D[i2][i] * x[i];

@@ -701,3 +701,16 @@ def test_conjugate_gradient_refinement(case, prec):
     xr, _ = s.solve_refined(pr.b)
     err = np.linalg.norm(x.cpu().numpy().T - xr) / np.linalg.norm(xr)
     assert info["backward_error"] <= 1e-15 and err <= 1e-10, (info, err)
+
+
+@pytest.mark.parametrize("case", ["q3_24_lookahead", "q3_12_large_path", "q1_3d_6_large_path"])
+@pytest.mark.parametrize("sym", [0, 1])
+def test_panel_triangular_solves_factors_match_oracle(case, sym):
+    """Option panel_trsm: each pivot block's panel finished by triangular solves against the factored
+    block instead of products with its inverses; FP64 factors front by front within 1e-11."""
+    mk, opt = CASES[case] if case in CASES else SYM_CASES[case]
+    pr = mk()
+    a, f, vals = _setup(pr, "f64", panel_trsm=1, symmetric=sym, **opt)
+    f.factor(vals)
+    assert f.status()["rc"] == 0
+    _check_factors(f, _oracle(pr), case)
