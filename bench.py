@@ -347,6 +347,9 @@ def main():
                          "one and three BF16 passes): refinement contraction, corrections and step time")
     ap.add_argument("--root-f64-trial", type=int, default=0,
                     help="also measure the tuned plan with the pivot blocks of the top N classes in FP64")
+    ap.add_argument("--tcpack-trial", action="store_true",
+                    help="also measure the tuned plan with the other 3xTF32 operand path (tensor-core kernel that splits "
+                         "its own operands vs. a separate pack pass)")
     ap.add_argument("--panel-trial", action="store_true",
                     help="also measure the tuned plan with the other panel method of the large-front partial LU "
                          "(triangular solves vs. products with explicit pivot-block inverses)")
@@ -582,7 +585,7 @@ def main():
 
     trials = {}
     if kind == "solve" and (args.bf16_trial or args.root_f64_trial or args.foata_trial or args.sym_trial or
-                            args.refine_trial or args.panel_trial):
+                            args.refine_trial or args.panel_trial or args.tcpack_trial):
         import copy
         trials["tuned"] = time_variant(opts)
         if args.bf16_trial:
@@ -597,6 +600,15 @@ def main():
             o2 = copy.copy(opts)
             o2.root_f64 = args.root_f64_trial
             trials[f"root_f64_{args.root_f64_trial}"] = time_variant(o2)
+        if args.tcpack_trial:
+            o2 = copy.copy(opts)
+            o2.tc_pack = 1 - opts.tc_pack
+            trials["tc_pack" if o2.tc_pack else "tc_direct"] = time_variant(o2)
+            for tmin in (128, 256):  # the direct kernel at lower tensor-core thresholds
+                o3 = copy.copy(opts)
+                o3.tc_min_cb = tmin
+                o3.precision = M.MF_TF32
+                trials[f"tc_direct_min{tmin}"] = time_variant(o3)
         if args.panel_trial:
             o2 = copy.copy(opts)
             o2.panel_trsm = 1 - opts.panel_trsm

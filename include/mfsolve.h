@@ -128,6 +128,10 @@ typedef struct {
                              both triangles and the panel is finished by products with the inverses;
                              nonzero = the panel is finished by triangular solves against the factored
                              block (one thread per row or column; slower here, kept as an option) */
+    int tc_pack;          /* MF_TF32 products: 0 (default) = the tensor-core kernel loads the FP32
+                             operands and splits them into tf32 hi/lo in shared memory itself;
+                             nonzero = a separate pass packs the split operands into the MMA's image
+                             first (the BF16 products of MF_TF32_BF16 always use the pack pass) */
     int root_f64;         /* FP32-family fronts: the pivot blocks of the large fronts in the top
                              root_f64 Foata classes (1 = the root's class) are factored and inverted
                              in FP64 from the FP32 front and rounded once to FP32; 0 = none (default) */
@@ -336,7 +340,8 @@ int mf_profile_read(mf_factors* f, double* ms, int64_t* launches, double* bytes,
  * 2 panel diagonal block, 3 SIMT GEMM, 4 pivot-block inverses, 5 subtree
  * factorization, 6 tensor-core GEMM, 7 lane-group tiny fronts, 8 tensor-core
  * operand packing, 9 scalar-task Foata executor, 13 symmetric-mode U12 copy,
- * 14 symmetric-mode contribution-block mirror, 15 panel triangular solves, or one of the
+ * 14 symmetric-mode contribution-block mirror, 15 panel triangular solves,
+ * 16 tensor-core GEMM splitting its own operands, or one of the
  * MF_TRACE_* codes below;
  * cls: 0-based Foata class or -1; tasks: fronts, tiles or tasks in the launch.
  * Call before mf_profile_read (which clears the trace).  Writes at most `cap`

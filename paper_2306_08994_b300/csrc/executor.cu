@@ -32,6 +32,7 @@ namespace {
 
 enum LaunchKind { K_FUSED = 0, K_ASM = 1, K_PDIAG = 2, K_GEMM = 3, K_INVDIAG = 4, K_SUBTREE = 5, K_GEMMTC = 6, K_GRP = 7,
                   K_TCPACK = 8, K_FOATA = 9, K_FORK = 10, K_JOIN = 11, K_SYMR = 13, K_MIRROR = 14, K_TRSM = 15,
+                  K_TCD = 16,
                   K_SYNC = 12 };  // K_SYNC: stream `stream` waits for what stream `bucket` issued so far (event `off`)
 
 struct Launch {
@@ -261,6 +262,8 @@ struct mf_factors {
     int64_t* d_pdiag = nullptr;       // symmetric solves: factor-arena offset of each dof's pivot
     AsmTile* d_symt = nullptr;        // tiles of the symmetric-mode R copies and S mirrors
     TrsmTask* d_trsm = nullptr;       // triangular-solve panel tasks
+    TcTileD* d_gtcd = nullptr;        // tensor-core tiles that split their own operands
+    bool tcd = true;                  // 3xTF32 products without the pack pass (option tc_pack)
     bool pinv = true;                 // panel products through explicit pivot-block inverses (default)
     int64_t* d_fwoff = nullptr;
     void* d_fws = nullptr;
@@ -396,7 +399,7 @@ static void free_factors(mf_factors* f) {
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_vsrc, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
-                    f->d_vec, f->d_flist, f->d_frec, f->d_fwoff, f->d_fws, f->d_fxs, f->d_pdiag, f->d_symt, f->d_trsm, f->d_cgp, f->d_cgs, f->d_zero, f->d_cg, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
+                    f->d_vec, f->d_flist, f->d_frec, f->d_fwoff, f->d_fws, f->d_fxs, f->d_pdiag, f->d_symt, f->d_trsm, f->d_gtcd, f->d_cgp, f->d_cgs, f->d_zero, f->d_cg, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
                     f->d_csr_dest, f->d_elemvals, f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms, f->d_colabs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -482,6 +485,7 @@ static int build_plan(mf_factors* F) {
     std::vector<int64_t> fwoff;  // parallel to flist: Foata workspace offsets (-1 for other kernels' fronts)
     std::vector<AsmTile> symt;   // symmetric mode: R tiles and S mirror tiles
     std::vector<TrsmTask> trs;   // triangular-solve panel tasks
+    std::vector<TcTileD> gtcd;   // direct tensor-core tiles
     std::vector<RowBlock> rows;
     std::vector<InvTask> invt;
     std::vector<AsmTile> asmt;
@@ -567,7 +571,33 @@ static int build_plan(mf_factors* F) {
     auto tc_end = [&](int c, int fam) {
         if (tcp.size() > tc_p0) {
             for (size_t qi = tc_p0; qi < tcp.size(); qi++) tcp[qi].lo_off = tc_hi;  // lo chunks after all hi chunks
-            for (int mode = 0; mode < 3; mode++) {  // one pack and one product launch per mode in use
+            bool packed = false;
+            if (F->tcd) {  // 3xTF32 products: tiles that read and split their operands themselves
+                const int64_t doff = (int64_t)gtcd.size();
+                for (size_t qi = tc_p0; qi < tcp.size(); qi++) {
+                    const TcPack& q = tcp[qi];
+                    if (q.pad[0] != tc::kTf32x3) continue;
+                    const int nra = (q.M + tc::kTileM - 1) / tc::kTileM, nrb = (q.N + tc::kTileN - 1) / tc::kTileN;
+                    for (int rb = 0; rb < nrb; rb++)
+                        for (int ra = 0; ra < nra; ra++) {
+                            if (q.pad[1] && (ra + 1) * tc::kTileM <= rb * tc::kTileN) continue;  // above the diagonal
+                            TcTileD t{};
+                            t.a_ar = q.a_ar; t.a_off = q.a_off; t.lda = q.lda; t.a_mask = q.a_mask;
+                            t.b_ar = q.b_ar; t.b_off = q.b_off; t.ldb = q.ldb; t.b_mask = q.b_mask;
+                            t.M = q.M; t.N = q.N; t.K = q.K;
+                            t.i0 = ra * tc::kTileM;
+                            t.j0 = rb * tc::kTileN;
+                            t.c_ar = tcc[qi].car;
+                            t.op = tcc[qi].op;
+                            t.c_off = tcc[qi].coff + t.i0 + (int64_t)t.j0 * tcc[qi].ldc;
+                            t.ldc = tcc[qi].ldc;
+                            gtcd.push_back(t);
+                        }
+                }
+                if (gtcd.size() > (size_t)doff)
+                    push({K_TCD, c, (int)(gtcd.size() - doff), 0, doff}, fam, tc_gbm[tc::kTf32x3], tc_gfm[tc::kTf32x3]);
+            }
+            for (int mode = F->tcd ? 1 : 0; mode < 3; mode++) {  // one pack and one product launch per mode in use
                 const int64_t joff = (int64_t)tcj.size(), toff = (int64_t)gtc.size();
                 const int ca = tc::chunk_floats_a(mode), cbk = tc::chunk_floats_b(mode);
                 for (size_t qi = tc_p0; qi < tcp.size(); qi++) {
@@ -597,13 +627,14 @@ static int build_plan(mf_factors* F) {
                         }
                 }
                 if (gtc.size() == (size_t)toff) continue;
+                packed = true;
                 push({K_TCPACK, c, (int)(tcj.size() - joff), 0, joff, (int)tc_p0}, fam, tc_pbm[mode], 0.0);
                 F->plan.back().wide = mode;
                 push({K_GEMMTC, c, (int)(gtc.size() - toff), 0, toff}, fam, tc_gbm[mode], tc_gfm[mode]);
                 F->plan.back().wide = mode;
             }
             int64_t& pks = cur_stream ? F->pk2_size : F->pk_size;  // one packed arena per stream
-            pks = std::max(pks, 2 * tc_hi);
+            if (packed) pks = std::max(pks, 2 * tc_hi);
         }
         tc_hi = 0;
         tc_p0 = tcp.size();
@@ -1265,6 +1296,7 @@ static int build_plan(mf_factors* F) {
     if ((rc = upload(&F->d_sweep_b, F->sweep_b))) return rc;
     if (!symt.empty() && (rc = upload(&F->d_symt, symt))) return rc;
     if (!trs.empty() && (rc = upload(&F->d_trsm, trs))) return rc;
+    if (!gtcd.empty() && (rc = upload(&F->d_gtcd, gtcd))) return rc;
     if ((rc = upload(&F->d_flist, flist))) return rc;
     fwoff.resize(flist.size(), -1);
     if ((rc = upload(&F->d_fwoff, fwoff))) return rc;
@@ -1325,6 +1357,7 @@ static int set_smem_limits() {
     CUDA_TRY(cudaFuncSetAttribute(k_schur_tc<tc::kTf32x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
     CUDA_TRY(cudaFuncSetAttribute(k_schur_tc<tc::kBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
     CUDA_TRY(cudaFuncSetAttribute(k_schur_tc<tc::kBf16x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
+    CUDA_TRY(cudaFuncSetAttribute(k_tc_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
     CUDA_TRY(cudaFuncSetAttribute(k_subtree_fwd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_subtree_fwd<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
 #define SET_INV(TR, PH)                                                                                            \
@@ -1377,6 +1410,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     F->foata_cls = std::max(0, F->opt.foata_classes);
     F->sym = F->opt.symmetric != 0;
     F->pinv = F->opt.panel_trsm == 0;
+    F->tcd = F->opt.tc_pack == 0;
     for (int i = 0; i < MF_FUSED_BUCKETS; i++) {
         const int t = F->opt.fused_threads[i];
         if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256) {
@@ -1652,6 +1686,13 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
                         F->d_fronts, dt, fac, (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
                 break;
             }
+            case K_TCD:
+                if constexpr (sizeof(T) == 4) {
+                    Arenas<float> ar{{fac, cb, (float*)F->d_inv, (float*)F->d_scr, (float*)F->d_pnl}};
+                    k_tc_direct<<<(unsigned)std::min(L.count, F->num_sms), kTcdThreads, tc::kSmemBytes, s>>>(
+                        F->d_gtcd + L.off, L.count, ar, F->d_status);
+                }
+                break;
             case K_TRSM: {
                 constexpr int NB = sizeof(T) == 8 ? kPanelNB64 : kPanelNB32;
                 k_panel_trsm<T, NB><<<L.count, 128, 0, s>>>(F->d_fronts, F->d_trsm + L.off, fac);

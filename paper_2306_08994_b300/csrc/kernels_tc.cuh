@@ -460,3 +460,228 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_schur_tc(const TcTile* __rest
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * tc::kTmemCols) : "memory");
     }
 }
+
+// ---------------------------------------------------------------------------
+// Tensor-core product that splits its FP32 operands itself (no pack pass).
+// Same tile (128 x 256), accumulators, epilogue and bounded waits as
+// k_schur_tc<kTf32x3>; the producer is two groups of four warps instead of one
+// bulk-copy thread.  Group q fills the ring stages g with g % 2 == q: each
+// thread loads its share of the stage's 128 x 16 slice of A and 256 x 16
+// slice of B^T straight from the arenas (any leading dimension: element
+// loads, coalesced across the warp), splits every value into tf32 hi and lo
+// and stores them as 16-byte rows of the MMA's core matrices; then a proxy
+// fence makes the shared-memory writes visible to the tensor core and one
+// lane per warp arrives on the stage's barrier (4 arrivals fill a stage).
+struct TcTileD {
+    int64_t a_off, b_off, c_off;  // operand origins of the product, the tile's (0, 0) in C
+    int32_t lda, ldb, ldc;
+    int32_t M, N, K;              // the product's extents
+    int32_t i0, j0;               // the tile's first row and column within the product
+    int8_t a_ar, b_ar, c_ar, op, a_mask, b_mask, pad[2];
+};
+
+constexpr int kTcdProducerWarps = 8;
+constexpr int kTcdThreads = (kTcdProducerWarps + 1 + 4) * 32;  // producers, MMA issuer, 4 epilogue warps
+
+__global__ void __launch_bounds__(kTcdThreads, 1) k_tc_direct(const TcTileD* __restrict__ tiles, int ntiles,
+                                                              Arenas<float> ar, DevStatus* st) {
+    extern __shared__ __align__(128) unsigned char smem_tc[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_tc + tc::kStages * tc::kStageBytes);
+    uint64_t* empty = full + tc::kStages;
+    uint64_t* acc_full = empty + tc::kStages;  // [2]
+    uint64_t* acc_empty = acc_full + 2;        // [2]
+    uint64_t* drain = acc_empty + 2;
+    uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    __shared__ int s_fail_raw;
+    volatile int& s_fail = s_fail_raw;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kMmaWarp = kTcdProducerWarps;
+    constexpr int kA = tc::kChunkA * 4, kB = tc::kChunkB * 4;  // bytes of one hi (or lo) image
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < tc::kStages; s++) {
+            tc::mbar_init(&full[s], 4);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            tc::mbar_init(&acc_full[b], 1);
+            tc::mbar_init(&acc_empty[b], 4);
+        }
+        tc::mbar_init(drain, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(taddr_slot)),
+                     "r"(2 * tc::kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *taddr_slot;
+
+    if (warp < kTcdProducerWarps) {
+        const int grp = warp >> 2, t = threadIdx.x & 127;  // producer group, thread within the group
+        int g = 0;
+        bool ok = true;
+        for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+            const TcTileD tl = tiles[ti];
+            const float* A = ar.a[tl.a_ar] + tl.a_off;
+            const float* B = ar.a[tl.b_ar] + tl.b_off;
+            const int nkc = (tl.K + tc::kChunkK - 1) / tc::kChunkK;
+            for (int c = 0; c < nkc; c++, g++) {
+                if ((g & 1) != grp) continue;
+                const int s = g % tc::kStages;
+                if (g >= tc::kStages) ok = tc::mbar_wait_bounded(&empty[s], ((g / tc::kStages) - 1) & 1, tc::kWaitLimit);
+                if (!ok || s_fail) {
+                    ok = false;
+                    break;
+                }
+                const int p0 = c * tc::kChunkK;
+                // A: 512 (row, K group) units, 4 per thread; B^T: 1024 units, 8 per thread.  All loads first.
+                float va[4][4], vb[8][4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int u = t + 128 * q, r = u & 127, kg = u >> 7;
+                    const int i = tl.i0 + r;
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const int p = p0 + 4 * kg + e;
+                        va[q][e] = (i < tl.M && p < tl.K) ? masked(A[i + (int64_t)p * tl.lda], (int)tl.a_mask, i, p) : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const int u = t + 128 * q, kg = u & 3, jr = u >> 2;
+                    const int j = tl.j0 + jr;
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const int p = p0 + 4 * kg + e;
+                        vb[q][e] = (j < tl.N && p < tl.K) ? masked(B[p + (int64_t)j * tl.ldb], (int)tl.b_mask, p, j) : 0.f;
+                    }
+                }
+                unsigned char* dst = smem_tc + s * tc::kStageBytes;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int u = t + 128 * q, r = u & 127, kg = u >> 7;
+                    uint32_t h[4], l[4];
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        h[e] = tc::to_tf32(va[q][e]);
+                        l[e] = tc::to_tf32(va[q][e] - __uint_as_float(h[e]));
+                    }
+                    const int off = (r >> 3) * 512 + kg * 128 + (r & 7) * 16;
+                    *reinterpret_cast<uint4*>(dst + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4*>(dst + kA + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                }
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const int u = t + 128 * q, kg = u & 3, jr = u >> 2;
+                    uint32_t h[4], l[4];
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        h[e] = tc::to_tf32(vb[q][e]);
+                        l[e] = tc::to_tf32(vb[q][e] - __uint_as_float(h[e]));
+                    }
+                    const int off = (jr >> 3) * 512 + kg * 128 + (jr & 7) * 16;
+                    *reinterpret_cast<uint4*>(dst + 2 * kA + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<uint4*>(dst + 2 * kA + kB + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                }
+                tc::fence_proxy_async();  // generic-proxy writes -> visible to the tensor core
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&full[s]);
+            }
+        }
+        if (!ok) s_fail = 1;
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
+        if (lane == 0) {  // MMA issuer: as k_schur_tc<kTf32x3>
+            constexpr uint32_t idesc = tc::idesc_tf32(tc::kTileM, tc::kTileN);
+            int g = 0, i = 0;
+            bool ok = true;
+            for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x, i++) {
+                const TcTileD tl = tiles[ti];
+                const int nkc = (tl.K + tc::kChunkK - 1) / tc::kChunkK;
+                const int buf = i & 1;
+                const uint32_t acc = tmem + buf * tc::kTmemCols;
+                if (i >= 2) ok = tc::mbar_wait_bounded(&acc_empty[buf], ((i >> 1) - 1) & 1, tc::kWaitLimit);
+                if (!ok) break;
+                tc::fence_after_sync();
+                for (int c = 0; c < nkc; c++, g++) {
+                    const int s = g % tc::kStages;
+                    ok = tc::mbar_wait_bounded(&full[s], (g / tc::kStages) & 1, tc::kWaitLimit);
+                    if (!ok || s_fail) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t sa = tc::smem_u32(smem_tc + s * tc::kStageBytes);
+                    const uint32_t sal = sa + kA, sb = sa + 2 * kA, sbl = sb + kB;
+#pragma unroll
+                    for (int ks = 0; ks < tc::kChunkK / 8; ks++) {
+                        const uint32_t ko = ks * 256;
+                        const uint64_t dah = tc::smem_desc(sa + ko, 128, 512), dal = tc::smem_desc(sal + ko, 128, 512);
+                        const uint64_t dbh = tc::smem_desc(sb + ko, 128, 512), dbl = tc::smem_desc(sbl + ko, 128, 512);
+                        tc::mma_tf32(acc, dal, dbh, idesc, (c == 0 && ks == 0) ? 0u : 1u);
+                        tc::mma_tf32(acc, dah, dbl, idesc, 1u);
+                        tc::mma_tf32(acc, dah, dbh, idesc, 1u);
+                    }
+                    tc::mma_commit(&empty[s]);
+                }
+                tc::mma_commit(&acc_full[buf]);
+            }
+            if (!ok) {
+                s_fail = 1;
+                tc::mma_commit(drain);
+                tc::mbar_wait_bounded(drain, 0, tc::kWaitLimit);
+            }
+        }
+        __syncwarp();
+    } else {  // epilogue warps: TMEM lanes 32 (warp % 4) ..
+        const int q = warp & 3;
+        const int row = 32 * q + lane;
+        int i = 0;
+        for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, i++) {
+            const TcTileD tl = tiles[ti];
+            const int buf = i & 1;
+            bool ok = tc::mbar_wait_bounded(&acc_full[buf], (i >> 1) & 1, tc::kWaitLimit);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                if (lane == 0) s_fail = 1;
+                break;
+            }
+            tc::fence_after_sync();
+            const int mrows = min(tc::kTileM, tl.M - tl.i0), ncols = min(tc::kTileN, tl.N - tl.j0);
+            float* crow = ar.a[tl.c_ar] + tl.c_off + row;
+#pragma unroll 1
+            for (int cg = 0; cg < tc::kTileN / 32; cg++) {
+                if (cg * 32 >= ncols) break;
+                float v[32], cv[32];
+                float* cp = crow + (int64_t)(cg * 32) * tl.ldc;
+                const int nj = min(32, ncols - cg * 32);
+                if (row < mrows && tl.op == 0) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) cv[j] = j < nj ? cp[(int64_t)j * tl.ldc] : 0.f;
+                }
+                tc::tmem_ld32(tmem + buf * tc::kTmemCols + ((uint32_t)(32 * q) << 16) + cg * 32, v);
+                if (row < mrows) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++)
+                        if (j < nj) cp[(int64_t)j * tl.ldc] = tl.op == 0 ? cv[j] - v[j] : (tl.op == 1 ? v[j] : -v[j]);
+                }
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (s_fail && threadIdx.x == 0) atomicOr(&st->timeout, 1);
+    if (warp == kMmaWarp) {
+        tc::fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * tc::kTmemCols) : "memory");
+    }
+}

@@ -38,7 +38,8 @@ class mf_options(ctypes.Structure):
                 ("super_panel", ctypes.c_int), ("fused_threads", ctypes.c_int * MF_FUSED_BUCKETS),
                 ("lookahead", ctypes.c_int), ("bf16_min_cb", ctypes.c_int), ("bf16_passes", ctypes.c_int),
                 ("foata_classes", ctypes.c_int), ("symmetric", ctypes.c_int), ("refine_cg", ctypes.c_int),
-                ("panel_trsm", ctypes.c_int), ("root_f64", ctypes.c_int)]
+                ("panel_trsm", ctypes.c_int), ("tc_pack", ctypes.c_int),
+                ("root_f64", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {f: (list(getattr(self, f)) if f == "fused_threads" else getattr(self, f)) for f, _ in self._fields_}
@@ -73,7 +74,7 @@ class mf_trace_rec(ctypes.Structure):
 
 
 TRACE_KINDS = {0: "fused", 1: "assemble", 2: "panel_diag", 3: "gemm", 4: "inv_diag", 5: "subtree", 6: "gemm_tc",
-               7: "fused_grp", 8: "tc_pack", 9: "foata", 13: "sym_r", 14: "sym_mirror", 15: "panel_trsm",
+               7: "fused_grp", 8: "tc_pack", 9: "foata", 13: "sym_r", 14: "sym_mirror", 15: "panel_trsm", 16: "gemm_tcd",
                100: "fwd_class", 101: "bwd_class", 102: "subtree_fwd", 103: "subtree_bwd", 104: "fwd_sweep",
                105: "bwd_sweep", 199: "other"}
 
