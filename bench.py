@@ -97,7 +97,7 @@ FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 f
 # (dram__bytes_read.sum + dram__bytes_write.sum over all its launches / launches); the key names the
 # workload, the requested front precision (the tuned plan of the committed cache) and the trace
 # kind.  Valid while the kernel is unchanged.
-MEASURED_TRAFFIC = {("diffusion2d_q3_512", "f32", "gemm"): 19.73e6, ("diffusion3d_q1_64", "f32", "gemm_tc"): 186.1e6}
+MEASURED_TRAFFIC = {}
 FP64_DFMA_TFLOPS = 1.201  # measured DFMA throughput of this B300 (register-resident FMA loop, all SMs)
 
 
@@ -278,7 +278,7 @@ def path_roofline(trace, steps, fp64, peaks, info, elem_bytes, nsolve, nrhs, ms_
     p_alu = (FP64_DFMA_TFLOPS if fp64 else FP32_SIMT_PEAK_TFLOPS) * 1e12
     t = 0.0
     for rec in trace:
-        p = p_tc if rec["kind"] == "gemm_tc" else p_alu
+        p = p_tc if rec["kind"] in ("gemm_tc", "gemm_tcd") else p_alu
         t += max(rec["flops"] / p, rec["bytes"] / bw)
     t_roof_ms = 1e3 * t / max(steps, 1)
     s_f = 8.0 if fp64 else 4.0
@@ -649,7 +649,8 @@ def main():
     dom = max(kinds, key=lambda k: kinds[k]["ms"])
     d = kinds[dom]
     per_launch_ms = d["ms"] / max(d["launches"], 1)
-    bound = {"gemm": "alu", "panel_diag": "alu", "inv_diag": "alu", "gemm_tc": "tensor"}.get(dom, "hbm")
+    bound = {"gemm": "alu", "panel_diag": "alu", "inv_diag": "alu", "panel_trsm": "alu", "gemm_tc": "tensor",
+             "gemm_tcd": "tensor"}.get(dom, "hbm")
     if bound == "alu":
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "unit": "TFLOP/s",

@@ -156,7 +156,7 @@ def test_tensor_core_schur_path(n):
             kinds = {r["kind"] for r in f.trace()}
             f.profile_read()
             f.profile(False)
-            assert {"gemm_tc"} <= kinds, kinds
+            assert kinds & {"gemm_tc", "gemm_tcd"}, kinds
         assert f.status()["rc"] == 0
         g = a.n_front - 2  # a front just below the root: its front matrix came through Schur updates
         factors[prec] = f.export_front(g)[0]
