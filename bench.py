@@ -348,8 +348,8 @@ def main():
     ap.add_argument("--root-f64-trial", type=int, default=0,
                     help="also measure the tuned plan with the pivot blocks of the top N classes in FP64")
     ap.add_argument("--tcpack-trial", action="store_true",
-                    help="also measure the tuned plan with the other 3xTF32 operand path (tensor-core kernel that splits "
-                         "its own operands vs. a separate pack pass)")
+                    help="also measure the tuned plan with the other 3xTF32 operand path (separate pack pass vs. a "
+                         "tensor-core kernel that splits its own operands)")
     ap.add_argument("--panel-trial", action="store_true",
                     help="also measure the tuned plan with the other panel method of the large-front partial LU "
                          "(triangular solves vs. products with explicit pivot-block inverses)")
@@ -602,13 +602,8 @@ def main():
             trials[f"root_f64_{args.root_f64_trial}"] = time_variant(o2)
         if args.tcpack_trial:
             o2 = copy.copy(opts)
-            o2.tc_pack = 1 - opts.tc_pack
-            trials["tc_pack" if o2.tc_pack else "tc_direct"] = time_variant(o2)
-            for tmin in (128, 256):  # the direct kernel at lower tensor-core thresholds
-                o3 = copy.copy(opts)
-                o3.tc_min_cb = tmin
-                o3.precision = M.MF_TF32
-                trials[f"tc_direct_min{tmin}"] = time_variant(o3)
+            o2.tc_direct = 1 - opts.tc_direct
+            trials["tc_direct" if o2.tc_direct else "tc_pack"] = time_variant(o2)
         if args.panel_trial:
             o2 = copy.copy(opts)
             o2.panel_trsm = 1 - opts.panel_trsm

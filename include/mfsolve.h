@@ -128,10 +128,11 @@ typedef struct {
                              both triangles and the panel is finished by products with the inverses;
                              nonzero = the panel is finished by triangular solves against the factored
                              block (one thread per row or column; slower here, kept as an option) */
-    int tc_pack;          /* MF_TF32 products: 0 (default) = the tensor-core kernel loads the FP32
-                             operands and splits them into tf32 hi/lo in shared memory itself;
-                             nonzero = a separate pass packs the split operands into the MMA's image
-                             first (the BF16 products of MF_TF32_BF16 always use the pack pass) */
+    int tc_direct;        /* MF_TF32 products: 0 (default) = a separate pass packs the tf32 hi/lo split
+                             operands into the MMA's shared-memory image, which the product kernel
+                             streams with bulk copies; nonzero = the product kernel loads the FP32
+                             operands and splits them in shared memory itself (no pack pass; slower
+                             here: its element loads keep too few bytes in flight) */
     int root_f64;         /* FP32-family fronts: the pivot blocks of the large fronts in the top
                              root_f64 Foata classes (1 = the root's class) are factored and inverted
                              in FP64 from the FP32 front and rounded once to FP32; 0 = none (default) */

@@ -263,7 +263,7 @@ struct mf_factors {
     AsmTile* d_symt = nullptr;        // tiles of the symmetric-mode R copies and S mirrors
     TrsmTask* d_trsm = nullptr;       // triangular-solve panel tasks
     TcTileD* d_gtcd = nullptr;        // tensor-core tiles that split their own operands
-    bool tcd = true;                  // 3xTF32 products without the pack pass (option tc_pack)
+    bool tcd = false;                 // 3xTF32 products without the pack pass (option tc_direct)
     bool pinv = true;                 // panel products through explicit pivot-block inverses (default)
     int64_t* d_fwoff = nullptr;
     void* d_fws = nullptr;
@@ -1410,7 +1410,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     F->foata_cls = std::max(0, F->opt.foata_classes);
     F->sym = F->opt.symmetric != 0;
     F->pinv = F->opt.panel_trsm == 0;
-    F->tcd = F->opt.tc_pack == 0;
+    F->tcd = F->opt.tc_direct != 0;
     for (int i = 0; i < MF_FUSED_BUCKETS; i++) {
         const int t = F->opt.fused_threads[i];
         if (t != 0 && t != 32 && t != 64 && t != 128 && t != 256) {

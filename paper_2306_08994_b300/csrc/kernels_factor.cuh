@@ -683,87 +683,37 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
         for (int i = lane; i < w; i += 32) P[(kb + i) + (int64_t)(kb + j) * m] = (T)D[i][j];
     if constexpr (!INV) return;  // the panel is finished by triangular solves (k_panel_trsm)
 
-    // ---- inverses L_D^-1 (lower, into Z on and below the diagonal) and U_D^-1 (unit upper, strict
-    //      upper part of Z), by 16 x 16 blocks.  (1) The diagonal blocks: one warp per block and
-    //      triangle, one lane per column, each a 16-step triangular solve in registers.  (2) The
-    //      blocks at distance d = 1, 2, .. from the diagonal, all threads at once:
-    //        lower  X_ij = -X_ii (sum_{l=j}^{i-1} L_il X_lj),   i = j + d
-    //        upper  Y_ji = -Y_jj (sum_{l=j+1}^{i} U_jl Y_li),   i = j + d
-    //      the sums first (into the scratch W), then the products with the diagonal blocks' inverses.
-    constexpr int NBI = NB / 16;
-    if (warp < 2 * NBI && lane < 16) {
-        const int b = warp % NBI, o = 16 * b, c = lane;
-        C a[16];
+    // ---- inverses, one thread per column: threads 0..NB-1 column c of L_D^-1 (forward),
+    //      threads NB..2NB-1 column c of U_D^-1 (backward, unit diagonal).  Right-looking: once
+    //      entry r is final it is applied to all later entries, so every step is NB-r independent
+    //      FMAs on a column held in registers (the D reads are warp-wide broadcasts).
+    if (tid < 2 * NB) {
+        const int c = tid % NB;
+        C a[NB];
 #pragma unroll
-        for (int r = 0; r < 16; r++) a[r] = r == c ? C(1) : C(0);
-        if (warp < NBI) {
+        for (int r = 0; r < NB; r++) a[r] = r == c ? C(1) : C(0);
+        if (tid < NB) {
 #pragma unroll
-            for (int r = 0; r < 16; r++) {
-                const C xr = a[r] * rdiag[o + r];
+            for (int r = 0; r < NB; r++) {
+                const C xr = a[r] * rdiag[r];
                 a[r] = xr;
 #pragma unroll
-                for (int r2 = r + 1; r2 < 16; r2++) a[r2] -= D[o + r2][o + r] * xr;
+                for (int r2 = r + 1; r2 < NB; r2++) a[r2] -= D[r2][r] * xr;
             }
 #pragma unroll
-            for (int r = 0; r < 16; r++)
-                if (r >= c) Z[o + r][o + c] = a[r];
+            for (int r = 0; r < NB; r++)
+                if (r >= c) Z[r][c] = a[r];
         } else {
 #pragma unroll
-            for (int r = 15; r > 0; r--) {
+            for (int r = NB - 1; r > 0; r--) {
                 const C yr = a[r];
 #pragma unroll
-                for (int r2 = 0; r2 < r; r2++) a[r2] -= D[o + r2][o + r] * yr;
+                for (int r2 = 0; r2 < r; r2++) a[r2] -= D[r2][r] * yr;
             }
 #pragma unroll
-            for (int r = 0; r < 16; r++)
-                if (r < c) Z[o + r][o + c] = a[r];
+            for (int r = 0; r < NB; r++)
+                if (r < c) Z[r][c] = a[r];
         }
-    }
-    __syncthreads();
-    // the lookahead's U slice is consumed by now: its shared memory holds the sums W
-    C* W = reinterpret_cast<C*>(pd_dyn);
-    for (int d = 1; d < NBI; d++) {
-        const int nblk = NBI - d, ne = 2 * nblk * 256;
-        for (int e = tid; e < ne; e += 256) {
-            const int tri = e / (nblk * 256), rem = e % (nblk * 256), j = rem / 256, idx = rem % 256;
-            const int r = idx & 15, c = idx >> 4, i = j + d;
-            C acc = C(0);
-            if (tri == 0) {  // sum_{l=j}^{i-1} L_il X_lj, entry (r, c); X_jj is lower
-#pragma unroll
-                for (int q = 0; q < 16; q++)
-                    if (q >= c) acc += D[16 * i + r][16 * j + q] * Z[16 * j + q][16 * j + c];
-                for (int l = j + 1; l < i; l++)
-#pragma unroll
-                    for (int q = 0; q < 16; q++) acc += D[16 * i + r][16 * l + q] * Z[16 * l + q][16 * j + c];
-            } else {         // sum_{l=j+1}^{i} U_jl Y_li, entry (r, c); Y_ii is unit upper
-                for (int l = j + 1; l <= i; l++)
-#pragma unroll
-                    for (int q = 0; q < 16; q++) {
-                        const C y = l < i ? Z[16 * l + q][16 * i + c] : (q < c ? Z[16 * i + q][16 * i + c] : (q == c ? C(1) : C(0)));
-                        acc += D[16 * j + r][16 * l + q] * y;
-                    }
-            }
-            W[e] = acc;
-        }
-        __syncthreads();
-        for (int e = tid; e < ne; e += 256) {
-            const int tri = e / (nblk * 256), rem = e % (nblk * 256), j = rem / 256, idx = rem % 256;
-            const int r = idx & 15, c = idx >> 4, i = j + d;
-            const C* Wb = W + tri * (nblk * 256) + j * 256;
-            C acc = C(0);
-            if (tri == 0) {  // X_ij = -X_ii W, X_ii lower
-#pragma unroll
-                for (int q = 0; q < 16; q++)
-                    if (q <= r) acc += Z[16 * i + r][16 * i + q] * Wb[q + 16 * c];
-                Z[16 * i + r][16 * j + c] = -acc;
-            } else {         // Y_ji = -Y_jj W, Y_jj unit upper
-#pragma unroll
-                for (int q = 0; q < 16; q++)
-                    if (q > r) acc += Z[16 * j + r][16 * j + q] * Wb[q + 16 * c];
-                Z[16 * j + r][16 * i + c] = -(acc + Wb[r + 16 * c]);
-            }
-        }
-        __syncthreads();
     }
     __syncthreads();
     T* Zg = slots + t.slot;

@@ -216,21 +216,36 @@ __global__ void __launch_bounds__(256) k_tc_pack(const TcPack* __restrict__ task
     const int nrow = jb.which == 0 ? t.M : t.N;
     const float* src = jb.which == 0 ? ar.a[t.a_ar] + t.a_off : ar.a[t.b_ar] + t.b_off;
     const int r0 = jb.rt * rows, p0 = jb.kc * tc::kChunkK;
-    for (int e = threadIdx.x; e < rows * tc::kChunkK; e += blockDim.x) {
-        int r, kk;
-        if (jb.which == 0) {  // A: column-major, consecutive threads down a column
-            r = e % rows;
-            kk = e / rows;
-        } else {  // B: K-contiguous, consecutive threads along K
-            kk = e % tc::kChunkK;
-            r = e / tc::kChunkK;
+    // every load of the thread is issued before the first shared-memory store (8 for an A slice,
+    // 16 for a B slice)
+    if (jb.which == 0) {  // A: column-major, consecutive threads down a column
+        constexpr int NL = tc::kTileM * tc::kChunkK / 256;
+        float v[NL];
+#pragma unroll
+        for (int q = 0; q < NL; q++) {
+            const int e = threadIdx.x + 256 * q, r = e % tc::kTileM, kk = e / tc::kTileM;
+            const int i = r0 + r, p = p0 + kk;
+            v[q] = (i < nrow && p < t.K) ? masked(src[i + (int64_t)p * t.lda], t.a_mask, i, p) : 0.f;
         }
-        const int i = r0 + r, p = p0 + kk;
-        float v = 0.f;
-        if (i < nrow && p < t.K)
-            v = jb.which == 0 ? masked(src[i + (int64_t)p * t.lda], t.a_mask, i, p)
-                              : masked(src[p + (int64_t)i * t.ldb], t.b_mask, p, i);
-        tile[r][kk] = v;
+#pragma unroll
+        for (int q = 0; q < NL; q++) {
+            const int e = threadIdx.x + 256 * q;
+            tile[e % tc::kTileM][e / tc::kTileM] = v[q];
+        }
+    } else {  // B: K-contiguous, consecutive threads along K
+        constexpr int NL = tc::kTileN * tc::kChunkK / 256;
+        float v[NL];
+#pragma unroll
+        for (int q = 0; q < NL; q++) {
+            const int e = threadIdx.x + 256 * q, kk = e % tc::kChunkK, r = e / tc::kChunkK;
+            const int i = r0 + r, p = p0 + kk;
+            v[q] = (i < nrow && p < t.K) ? masked(src[p + (int64_t)i * t.ldb], t.b_mask, p, i) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < NL; q++) {
+            const int e = threadIdx.x + 256 * q;
+            tile[e / tc::kChunkK][e % tc::kChunkK] = v[q];
+        }
     }
     __syncthreads();
     if constexpr (Cfg::kBf) {

@@ -38,7 +38,7 @@ class mf_options(ctypes.Structure):
                 ("super_panel", ctypes.c_int), ("fused_threads", ctypes.c_int * MF_FUSED_BUCKETS),
                 ("lookahead", ctypes.c_int), ("bf16_min_cb", ctypes.c_int), ("bf16_passes", ctypes.c_int),
                 ("foata_classes", ctypes.c_int), ("symmetric", ctypes.c_int), ("refine_cg", ctypes.c_int),
-                ("panel_trsm", ctypes.c_int), ("tc_pack", ctypes.c_int),
+                ("panel_trsm", ctypes.c_int), ("tc_direct", ctypes.c_int),
                 ("root_f64", ctypes.c_int)]
 
     def as_dict(self) -> dict:

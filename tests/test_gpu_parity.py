@@ -717,14 +717,14 @@ def test_panel_triangular_solves_factors_match_oracle(case, sym):
 
 
 @pytest.mark.parametrize("case", ["q3_24_large_path", "q1_3d_8"])
-@pytest.mark.parametrize("tc_pack", [0, 1])
-def test_tensor_core_operand_paths_front_by_front(case, tc_pack):
-    """3xTF32 tensor-core products with the operands split inside the product kernel (tc_pack 0, the
-    default) and through the separate pack pass (tc_pack 1): every front within the split-TF32
+@pytest.mark.parametrize("tc_direct", [0, 1])
+def test_tensor_core_operand_paths_front_by_front(case, tc_direct):
+    """3xTF32 tensor-core products through the separate pack pass (tc_direct 0, the default) and with
+    the operands split inside the product kernel (tc_direct 1): every front within the split-TF32
     bound of test_fp32_family_factors_match_oracle_front_by_front, on the same inputs."""
     mk, opt = FP32_CASES[case]
     pr = mk()
-    a, f, vals = _setup(pr, "tf32", tc_min_cb=16, tc_pack=tc_pack, **opt)
+    a, f, vals = _setup(pr, "tf32", tc_min_cb=16, tc_direct=tc_direct, **opt)
     f.factor(vals)
     assert f.status()["rc"] == 0
     s = _oracle(pr)
@@ -743,7 +743,7 @@ def test_tensor_core_operand_paths_front_by_front(case, tc_pack):
         tol = 4.0 * ksub[v] * 2.0 ** -21 * max(np.abs(Lo).max(), np.abs(Uo).max(), 1.0)
         low = np.tril(np.ones((Lo.shape[0], k), bool))
         up = np.triu(np.ones((k, Uo.shape[1]), bool), 1)
-        assert np.abs(Lg - Lo)[low].max() <= tol, (case, tc_pack, g)
+        assert np.abs(Lg - Lo)[low].max() <= tol, (case, tc_direct, g)
         if up.any():
-            assert np.abs(Ug - Uo)[up].max() <= tol, (case, tc_pack, g)
+            assert np.abs(Ug - Uo)[up].max() <= tol, (case, tc_direct, g)
 
