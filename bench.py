@@ -93,11 +93,13 @@ for _p, _n in F.L2_SIZES.items():
 CPU_WARMUP = ("diffusion2d_q3_32", lambda: [F.diffusion_2d(32, 3, seed=F.SEED_BASE + 2)])
 REF_TIME_BUDGET_S = 150.0  # the oracle arm stops starting new timed steps after this much time
 FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
-# DRAM bytes (read + write) per launch of a dominant kernel, from one ncu capture of that workload
-# (dram__bytes_read.sum + dram__bytes_write.sum over all its launches / launches); the key names the
-# workload, the requested front precision (the tuned plan of the committed cache) and the trace
-# kind.  Valid while the kernel is unchanged.
-MEASURED_TRAFFIC = {}
+# DRAM bytes (read + write) over algorithmic bytes of a kernel kind, measured with ncu on three launches of a
+# small case of the same recipe (128^2 Q3 for the SIMT and pivot-block kernels, 32^3 Q1 for the tensor-core
+# ones; dram__bytes_read.sum + dram__bytes_write.sum against the launches' algorithmic bytes from
+# `bench.py --trace-once`).  The roofline's `traffic` is this ratio times the algorithmic bytes per launch of
+# the timed workload, i.e. the capture scaled by the units a launch processes.  Valid while the kernel is
+# unchanged.
+MEASURED_TRAFFIC_RATIO = {"gemm": 0.748, "panel_diag": 0.714, "fused_grp": 0.658, "gemm_tc": 1.202, "tc_pack": 0.308}
 FP64_DFMA_TFLOPS = 1.201  # measured DFMA throughput of this B300 (register-resident FMA loop, all SMs)
 
 
@@ -663,9 +665,13 @@ def main():
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "peak_src": peaks["src"]}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    # DRAM traffic per launch of the dominant kernel from one ncu capture of this workload
-    # (every launch of a full bench run); null for kernels or workloads not captured
-    roof["traffic"] = MEASURED_TRAFFIC.get((args.workload, precision, dom))
+    # DRAM traffic per launch of the dominant kernel: the small-case capture's traffic / algorithmic ratio
+    # scaled to this workload's launches; null for kernels not captured
+    ratio = MEASURED_TRAFFIC_RATIO.get(dom)
+    roof["traffic"] = None if ratio is None else ratio * d["bytes"] / max(d["launches"], 1)
+    roof["traffic_src"] = (None if ratio is None else
+                           f"ncu dram bytes / algorithmic bytes = {ratio} on three launches of a small case of the "
+                           f"same recipe, times this workload's algorithmic bytes per launch")
     roof["kernel"] = dom
     roof["launches_per_step"] = d["launches"] / args.steps
     roof["per_launch_ms"] = per_launch_ms
