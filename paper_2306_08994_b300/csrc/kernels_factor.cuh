@@ -77,7 +77,9 @@ struct FactorRec {
 // Fused small front: one CTA per front, the whole front in shared memory.
 // Extend-add (or the element matrix at a leaf), partial LU on the k pivots
 // with the division (T1), multiplication (T2) and subtraction (T3) tasks of
-// Sec. 3 / Table 2, then P, R and the Schur complement S written out.
+// Sec. 3 / Table 2 on the pivot rows and columns, then P and R written out
+// and the Schur complement S = F22 - L21 U12 formed from registers straight
+// into the contribution-block arena.
 // Dynamic shared memory: ldm*maxm T + maxm T + 2*maxm int32 + 32 floats.
 template <typename T>
 __global__ void __launch_bounds__(256) k_front_fused(const FactorRec* __restrict__ recs,
@@ -169,35 +171,84 @@ __global__ void __launch_bounds__(256) k_front_fused(const FactorRec* __restrict
     amax = block_max_abs(amax, red);  // includes __syncthreads
     const T thr = (T)tol_rel * amax > T(0) ? (T)tol_rel * amax : tiny_pivot<T>();
 
-    // ---- partial LU on the fully assembled pivots (Table 2 compute_front)
+    // ---- partial LU on the fully assembled pivots (Table 2 compute_front), the Schur block deferred:
+    //      per pivot p the division T1 runs along the whole pivot row, the multiply-subtract T2/T3 only
+    //      on the pivot columns (all rows below p) and on the pivot rows' right part (R); the
+    //      contribution block then takes all k pivots in one register-tiled update below
+    const int nthr = blockDim.x;
     for (int p = 0; p < k; p++) {
         T piv = checked_pivot(F[p + p * ldm], thr, threadIdx.x == 0, f, p, st);
         // T1: divide the pivot row right of the pivot
-        for (int j = p + 1 + threadIdx.x; j < m; j += blockDim.x) {
+        for (int j = p + 1 + threadIdx.x; j < m; j += nthr) {
             T u = F[p + j * ldm] / piv;
             F[p + j * ldm] = u;
             urow[j] = u;
         }
         if (threadIdx.x == 0) F[p + p * ldm] = piv;
         __syncthreads();
-        // T2/T3: trailing block update
-        for (int j = p + 1 + warp; j < m; j += nwarp) {
+        // T2/T3 on the pivot columns p < j < k: one thread per row i > p
+        for (int i = p + 1 + threadIdx.x; i < m; i += nthr) {
+            const T lip = F[i + p * ldm];
+            for (int j = p + 1; j < k; j++) F[i + j * ldm] -= lip * urow[j];
+        }
+        // T2/T3 on R: rows p < i < k, columns j >= k (lanes down a column)
+        for (int j = k + warp; j < m; j += nwarp) {
             const T u = urow[j];
-            for (int i = p + 1 + lane; i < m; i += 32) F[i + j * ldm] -= F[i + p * ldm] * u;
+            for (int i = p + 1 + lane; i < k; i += 32) F[i + j * ldm] -= F[i + p * ldm] * u;
         }
         __syncthreads();
     }
 
-    // ---- write P (m x k), R (k x nc), S (nc x nc)
+    // ---- write P (m x k), R (k x nc)
     T* P = fac + fr.P_off;
     for (int j = warp; j < k; j += nwarp)
         for (int i = lane; i < m; i += 32) P[i + (int64_t)j * m] = F[i + j * ldm];
     T* R = fac + fr.R_off;
     for (int j = k + warp; j < m; j += nwarp)
         for (int i = lane; i < k; i += 32) R[i + (int64_t)(j - k) * k] = F[i + j * ldm];
-    T* S = cbs + fr.S_off;
-    for (int j = k + warp; j < m; j += nwarp)
-        for (int i = k + lane; i < m; i += 32) S[(i - k) + (int64_t)(j - k) * nc] = F[i + j * ldm];
+    // ---- S = F22 - L21 U12 straight to the contribution-block arena.  Threads form a 16 x (nthr/16)
+    //      grid; each holds 4 x 4 outputs strided by 16 rows / nthr/16 columns (so a warp's shared reads
+    //      of L21 hit 16 consecutive rows and those of U12 two columns), the k-deep sum in registers.
+    if (nc > 0) {
+        T* S = cbs + fr.S_off;
+        const int tr = threadIdx.x & 15, tcn = nthr >> 4, tc = threadIdx.x >> 4;
+        for (int j0 = 0; j0 < nc; j0 += 4 * tcn)
+            for (int i0 = 0; i0 < nc; i0 += 64) {
+                T acc[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; a++)
+#pragma unroll
+                    for (int b = 0; b < 4; b++) acc[a][b] = T(0);
+                int ri[4], cj[4];
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    ri[a] = min(i0 + tr + 16 * a, nc - 1);
+                    cj[a] = min(j0 + tc + tcn * a, nc - 1);
+                }
+                for (int l = 0; l < k; l++) {
+                    T la[4], ub[4];
+#pragma unroll
+                    for (int a = 0; a < 4; a++) {
+                        la[a] = F[(k + ri[a]) + l * ldm];
+                        ub[a] = F[l + (k + cj[a]) * ldm];
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; a++)
+#pragma unroll
+                        for (int b = 0; b < 4; b++) acc[a][b] += la[a] * ub[b];
+                }
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    const int j = j0 + tc + tcn * b;
+                    if (j >= nc) continue;
+#pragma unroll
+                    for (int a = 0; a < 4; a++) {
+                        const int i = i0 + tr + 16 * a;
+                        if (i < nc) S[i + (int64_t)j * nc] = F[(k + i) + (k + j) * ldm] - acc[a][b];
+                    }
+                }
+            }
+    }
 }
 
 // ---------------------------------------------------------------------------
