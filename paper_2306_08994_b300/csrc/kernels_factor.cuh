@@ -531,22 +531,56 @@ __global__ void __launch_bounds__(256) k_sym_mirror(const FrontDev* __restrict__
     }
 }
 
+// Owners of row q and of column q of the pivot block publish them (and row q
+// of L_D^-1, column q of U_D^-1) for elimination step q (k_panel_diag_blk).
+template <typename C, int RPT, bool INV>
+__device__ __forceinline__ void pivot_strip_publish(const C (&Ft)[RPT][RPT], const C (&Xt)[INV ? RPT : 1][INV ? RPT : 1],
+                                                    const C (&Yt)[INV ? RPT : 1][INV ? RPT : 1], int q, int ti, int tj,
+                                                    C* colF, C* rowF, C* rowX, C* colY) {
+    // the tile row / column is picked by a chain of selects (an indexed register
+    // read would put the tiles in local memory)
+    const int i0 = ti * RPT, j0 = tj * RPT, rq = q % RPT;
+    if (ti == q / RPT) {
+#pragma unroll
+        for (int c = 0; c < RPT; c++) {
+            C f = Ft[0][c], x = INV ? Xt[0][INV ? c : 0] : C(0);
+#pragma unroll
+            for (int r = 1; r < RPT; r++) {
+                f = r == rq ? Ft[r][c] : f;
+                if constexpr (INV) x = r == rq ? Xt[r][c] : x;
+            }
+            rowF[j0 + c] = f;
+            if constexpr (INV) rowX[j0 + c] = x;
+        }
+    }
+    if (tj == q / RPT) {
+#pragma unroll
+        for (int r = 0; r < RPT; r++) {
+            C f = Ft[r][0], y = INV ? Yt[INV ? r : 0][0] : C(0);
+#pragma unroll
+            for (int c = 1; c < RPT; c++) {
+                f = c == rq ? Ft[r][c] : f;
+                if constexpr (INV) y = c == rq ? Yt[r][c] : y;
+            }
+            colF[i0 + r] = f;
+            if constexpr (INV) colY[i0 + r] = y;
+        }
+    }
+}
+
 // Pivot block of a large front (NB x NB at pivot kb, padded with the
 // identity beyond w): partial LU in place (L with its diagonal, unit U) and
 // the explicit inverses L_D^-1 (on and below the diagonal) and U_D^-1 (strict
 // upper part) into the front's panel slot, for the panel products
 // L21 = A21 U_D^-1 and U12 = L_D^-1 A12 that follow.
-// Worked in 16 x 16 sub-blocks (NB/16 of them along the diagonal), 256
-// threads.  For each diagonal sub-block kk:
-//   (1) one warp factors it in registers (lane = row r and half h of the 16
-//       columns; pivot value, pivot column entry and pivot row broadcast by
-//       shuffles), with the static pivot check;
-//   (2) the sub-panels beside it are finished by triangular solves, one
-//       thread per row (L: X U_kk = A) or per column (U: L_kk Y = A);
-//   (3) the trailing sub-blocks take the rank-16 update.
-// Three block barriers per sub-block.  The inverses then come column by
-// column, one thread per column of L_D^-1 (L_D x = e_c) and of U_D^-1
-// (U_D y = e_c), each column in registers.
+// 256 threads, each holding a fixed (NB/16) x (NB/16) tile of the block, of
+// L_D^-1 and of U_D^-1 in registers for the whole kernel; one right-looking
+// elimination step per pivot with one block barrier, the pivot column and row
+// passed through a small double-buffered strip of shared memory.  The
+// inverses are updated in the same steps from the same column and row, so
+// the block costs w barrier-separated steps of a few shared loads and
+// 3 (NB/16)^2 FMAs per thread, in a short rolled loop (the whole kernel stays
+// small enough for the instruction cache; the block is latency-bound).
 // C is the arithmetic of the block (T by default).  With T = float and
 // C = double the block is factored and inverted in FP64 from the FP32 front
 // and rounded once on the way out: the FP64 pivot blocks of the root
@@ -561,7 +595,6 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
     constexpr bool kWide = sizeof(C) != sizeof(T);  // D and Z in dynamic shared memory
     __shared__ C Dst[kWide ? 1 : NB][NB + 1];
     __shared__ C Zst[kWide ? 1 : NB][NB + 1];
-    __shared__ C rdiag[NB];
     const DiagTask t = tasks[blockIdx.x];
     const FrontDev fr = fronts[t.front];
     const int m = fr.m, kb = t.kb, w = t.w;
@@ -604,15 +637,18 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
     if (pre > 0) stage(0);
     cp_async_wait_all();
     __syncthreads();
-    if (pre > 0) {
-        // the block's share of the pending update, pre pivots deep, NB at a time
-        constexpr int RPT = NB / 16;  // RPT x RPT outputs per thread
-        const int ti = tid >> 4, tj = tid & 15;
+    // Thread (ti, tj) owns the RPT x RPT tile at rows i0.., columns j0.. of the block for the rest of
+    // the kernel: first the pending lookahead update, then the LU and the inverses, all in registers.
+    constexpr int RPT = NB / 16;
+    const int ti = tid >> 4, tj = tid & 15, i0 = ti * RPT, j0 = tj * RPT;
+    C Ft[RPT][RPT];
+    {
         C acc[RPT][RPT];
 #pragma unroll
         for (int r = 0; r < RPT; r++)
 #pragma unroll
             for (int c = 0; c < RPT; c++) acc[r][c] = C(0);
+        // the block's share of the pending update, pre pivots deep, NB at a time
         for (int c0 = 0; c0 < pre; c0 += NB) {
             if (c0 > 0) {
                 __syncthreads();  // the previous slice is consumed
@@ -625,8 +661,8 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
                 C av[RPT], bv[RPT];
 #pragma unroll
                 for (int r = 0; r < RPT; r++) {
-                    av[r] = Z[ti * RPT + r][q];
-                    bv[r] = (C)Us[q * (NB + 1) + tj * RPT + r];
+                    av[r] = Z[i0 + r][q];
+                    bv[r] = (C)Us[q * (NB + 1) + j0 + r];
                 }
 #pragma unroll
                 for (int r = 0; r < RPT; r++)
@@ -637,136 +673,84 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
 #pragma unroll
         for (int r = 0; r < RPT; r++)
 #pragma unroll
-            for (int c = 0; c < RPT; c++) D[ti * RPT + r][tj * RPT + c] -= acc[r][c];
-        __syncthreads();
+            for (int c = 0; c < RPT; c++) Ft[r][c] = D[i0 + r][j0 + c] - acc[r][c];
     }
     const C amax = (C)__uint_as_float(famax[t.front]);
     const C thr = (C)tol_rel * amax > C(0) ? (C)tol_rel * amax : (C)tiny_pivot<T>();
 
-    for (int kk = 0; kk < NBB; kk++) {
-        const int o = 16 * kk;
-        // (1) diagonal sub-block: Table 2 tasks T1 (divide the pivot row), T2/T3 (update)
-        if (warp == 0) {
-            const int r = lane & 15, h = lane >> 4;
-            C a[8];
+    // Right-looking elimination, one block barrier per pivot p (Table 2 tasks on the block):
+    //   T4  the static pivot check on F[p, p],
+    //   T1  U[p, j] = F[p, j] / F[p, p] for j > p,
+    //   T2/T3  F[i, j] -= F[i, p] U[p, j] for i, j > p.
+    // The inverses ride along in the same sweep, from the same broadcast column and row:
+    //   X = L_D^-1 (L_D X = I, forward):   X[p, :] /= F[p, p];   X[i, :] -= F[i, p] X[p, :], i > p
+    //   Y = U_D^-1 (Y U_D = I, by columns): Y[:, j] -= Y[:, p] U[p, j], j > p
+    // Pivot p reads column p and row p of F (and row p of X, column p of Y) as they stand after
+    // step p - 1; their owners publish them into a double-buffered strip at the end of step p - 1.
+    __shared__ __align__(16) C colF[2][NB], rowF[2][NB], rowX[2][NB], colY[2][NB];
+    C Xt[INV ? RPT : 1][INV ? RPT : 1], Yt[INV ? RPT : 1][INV ? RPT : 1];
+    if constexpr (INV) {
 #pragma unroll
-            for (int e = 0; e < 8; e++) a[e] = D[o + r][o + 8 * h + e];
+        for (int r = 0; r < RPT; r++)
 #pragma unroll
-            for (int p = 0; p < 16; p++) {
-                const C pv = __shfl_sync(0xffffffffu, a[p & 7], p + 16 * (p >> 3));
-                C piv = pv;
-                if (o + p < w) piv = checked_pivot(pv, thr, lane == 0, t.front, kb + o + p, st);
-                const C rinv = C(1) / piv;
-                const C lr = __shfl_sync(0xffffffffu, a[p & 7], r + 16 * (p >> 3));
-#pragma unroll
-                for (int e = 0; e < 8; e++) {
-                    const int j = 8 * h + e;
-                    const C uj = __shfl_sync(0xffffffffu, a[e], p + 16 * h) * rinv;
-                    if (r > p && j > p) a[e] -= lr * uj;
-                    else if (r == p && j > p) a[e] = uj;
-                    else if (r == p && j == p) a[e] = piv;
-                }
-                if (lane == 0) rdiag[o + p] = rinv;
-            }
-#pragma unroll
-            for (int e = 0; e < 8; e++) D[o + r][o + 8 * h + e] = a[e];
-        }
-        __syncthreads();
-        const int R = NB - o - 16;  // rows (columns) of the sub-panels below (right of) the block
-        if (R > 0) {
-            // (2) L sub-panel rows: x U_kk = a (unit upper);  U sub-panel columns: L_kk y = a
-            if (tid < R) {
-                const int i = o + 16 + tid;
-                C x[16];
-#pragma unroll
-                for (int c = 0; c < 16; c++) x[c] = D[i][o + c];
-#pragma unroll
-                for (int c = 1; c < 16; c++)
-#pragma unroll
-                    for (int q = 0; q < c; q++) x[c] -= x[q] * D[o + q][o + c];
-#pragma unroll
-                for (int c = 0; c < 16; c++) D[i][o + c] = x[c];
-            } else if (tid >= 128 && tid < 128 + R) {
-                const int j = o + 16 + (tid - 128);
-                C y[16];
-#pragma unroll
-                for (int q = 0; q < 16; q++) y[q] = D[o + q][j];
-#pragma unroll
-                for (int rr = 0; rr < 16; rr++) {
-#pragma unroll
-                    for (int q = 0; q < rr; q++) y[rr] -= D[o + rr][o + q] * y[q];
-                    y[rr] *= rdiag[o + rr];
-                }
-#pragma unroll
-                for (int q = 0; q < 16; q++) D[o + q][j] = y[q];
-            }
-            __syncthreads();
-            // (3) trailing sub-blocks: A_ij -= L_i,kk U_kk,j
-            const int nb = R / 16, tr = tid >> 4, tc = tid & 15;
-            C acc[3][3];
-#pragma unroll
-            for (int aa = 0; aa < 3; aa++)
-#pragma unroll
-                for (int bb = 0; bb < 3; bb++) acc[aa][bb] = C(0);
-#pragma unroll
-            for (int q = 0; q < 16; q++) {
-                C lv[3], uv[3];
-#pragma unroll
-                for (int aa = 0; aa < 3; aa++) {
-                    lv[aa] = aa < nb ? D[o + 16 + tr + 16 * aa][o + q] : C(0);
-                    uv[aa] = aa < nb ? D[o + q][o + 16 + tc + 16 * aa] : C(0);
-                }
-#pragma unroll
-                for (int aa = 0; aa < 3; aa++)
-#pragma unroll
-                    for (int bb = 0; bb < 3; bb++) acc[aa][bb] += lv[aa] * uv[bb];
-            }
-#pragma unroll
-            for (int aa = 0; aa < 3; aa++)
-#pragma unroll
-                for (int bb = 0; bb < 3; bb++)
-                    if (aa < nb && bb < nb) D[o + 16 + tr + 16 * aa][o + 16 + tc + 16 * bb] -= acc[aa][bb];
-            __syncthreads();
-        }
+            for (int c = 0; c < RPT; c++) Xt[r][c] = Yt[r][c] = (i0 + r == j0 + c) ? C(1) : C(0);
     }
-    // factored block back to P (coalesced)
+    pivot_strip_publish<C, RPT, INV>(Ft, Xt, Yt, 0, ti, tj, colF[0], rowF[0], rowX[0], colY[0]);
+    __syncthreads();
+#pragma unroll 1
+    for (int p = 0; p < w; p++) {
+        const int b = p & 1;
+        const C piv = checked_pivot(colF[b][p], thr, tid == 0, t.front, kb + p, st);
+        const C rinv = C(1) / piv;
+        C lc[RPT], ur[RPT];
+#pragma unroll
+        for (int r = 0; r < RPT; r++) lc[r] = colF[b][i0 + r];
+#pragma unroll
+        for (int c = 0; c < RPT; c++) ur[c] = rowF[b][j0 + c] * rinv;
+#pragma unroll
+        for (int r = 0; r < RPT; r++)
+#pragma unroll
+            for (int c = 0; c < RPT; c++) {
+                const int i = i0 + r, j = j0 + c;
+                if (i > p) {
+                    if (j > p) Ft[r][c] -= lc[r] * ur[c];
+                } else if (i == p) {
+                    if (j > p) Ft[r][c] = ur[c];
+                    else if (j == p) Ft[r][c] = piv;
+                }
+            }
+        if constexpr (INV) {
+            C xr[RPT], yc[RPT];
+#pragma unroll
+            for (int c = 0; c < RPT; c++) xr[c] = rowX[b][j0 + c] * rinv;
+#pragma unroll
+            for (int r = 0; r < RPT; r++) yc[r] = colY[b][i0 + r];
+#pragma unroll
+            for (int r = 0; r < RPT; r++)
+#pragma unroll
+                for (int c = 0; c < RPT; c++) {
+                    const int i = i0 + r, j = j0 + c;
+                    if (i > p) Xt[r][c] -= lc[r] * xr[c];
+                    else if (i == p) Xt[r][c] = xr[c];
+                    if (j > p) Yt[r][c] -= yc[r] * ur[c];
+                }
+        }
+        if (p + 1 < w)
+            pivot_strip_publish<C, RPT, INV>(Ft, Xt, Yt, p + 1, ti, tj, colF[b ^ 1], rowF[b ^ 1], rowX[b ^ 1], colY[b ^ 1]);
+        __syncthreads();
+    }
+    // factored block back to P and the inverses to the panel slot, through shared memory (coalesced)
+#pragma unroll
+    for (int r = 0; r < RPT; r++)
+#pragma unroll
+        for (int c = 0; c < RPT; c++) {
+            D[i0 + r][j0 + c] = Ft[r][c];
+            if constexpr (INV) Z[i0 + r][j0 + c] = (i0 + r >= j0 + c) ? Xt[r][c] : Yt[r][c];
+        }
+    __syncthreads();
     for (int j = warp; j < w; j += 8)
         for (int i = lane; i < w; i += 32) P[(kb + i) + (int64_t)(kb + j) * m] = (T)D[i][j];
     if constexpr (!INV) return;  // the panel is finished by triangular solves (k_panel_trsm)
-
-    // ---- inverses, one thread per column: threads 0..NB-1 column c of L_D^-1 (forward),
-    //      threads NB..2NB-1 column c of U_D^-1 (backward, unit diagonal).  Right-looking: once
-    //      entry r is final it is applied to all later entries, so every step is NB-r independent
-    //      FMAs on a column held in registers (the D reads are warp-wide broadcasts).
-    if (tid < 2 * NB) {
-        const int c = tid % NB;
-        C a[NB];
-#pragma unroll
-        for (int r = 0; r < NB; r++) a[r] = r == c ? C(1) : C(0);
-        if (tid < NB) {
-#pragma unroll
-            for (int r = 0; r < NB; r++) {
-                const C xr = a[r] * rdiag[r];
-                a[r] = xr;
-#pragma unroll
-                for (int r2 = r + 1; r2 < NB; r2++) a[r2] -= D[r2][r] * xr;
-            }
-#pragma unroll
-            for (int r = 0; r < NB; r++)
-                if (r >= c) Z[r][c] = a[r];
-        } else {
-#pragma unroll
-            for (int r = NB - 1; r > 0; r--) {
-                const C yr = a[r];
-#pragma unroll
-                for (int r2 = 0; r2 < r; r2++) a[r2] -= D[r2][r] * yr;
-            }
-#pragma unroll
-            for (int r = 0; r < NB; r++)
-                if (r < c) Z[r][c] = a[r];
-        }
-    }
-    __syncthreads();
     T* Zg = slots + t.slot;
     for (int j = warp; j < w; j += 8)
         for (int i = lane; i < w; i += 32) Zg[i + j * 64] = (T)Z[i][j];
