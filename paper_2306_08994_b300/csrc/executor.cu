@@ -45,6 +45,7 @@ struct Launch {
     int threads = 0;  // fused: threads per CTA
     int stream = 0;   // 0: the caller's stream; 1: the side stream (pivot-block inverses); 2: the lookahead stream
     int wide = 0;     // K_PDIAG of FP32 fronts: factor the pivot blocks in FP64 (root separator classes)
+    int kmax = 0;     // fused: largest pivot count of the launch's fronts (picks the blocked form)
 };
 
 // Solve plan of one class: fronts split by size (see kernels_solve.cuh).
@@ -106,6 +107,7 @@ int upload(T** p, const std::vector<T>& v) {
     return MF_OK;
 }
 
+constexpr int kFusedBlockedMaxK = 32;  // fused fronts: blocked partial LU when every front has k <= this
 constexpr int kPanelNB64 = 32;  // panel width (pivot block of a step), FP64
 constexpr int kPanelNB32 = 64;  // FP32
 
@@ -289,6 +291,8 @@ struct mf_factors {
     int64_t pk_size = 0;
     float* d_pk2 = nullptr;      // the same for the side stream (pivot-block inverses)
     int64_t pk2_size = 0;
+    cudaStream_t s1 = nullptr;   // main factorization stream at the highest priority (with s2 / s3)
+    cudaEvent_t s1_in = nullptr, s1_out = nullptr;
     cudaStream_t s2 = nullptr;   // side stream: pivot-block inverses overlap the later classes
     std::vector<cudaEvent_t> fork_ev;
     cudaEvent_t join_ev = nullptr;
@@ -392,6 +396,9 @@ static void free_factors(mf_factors* f) {
     for (cudaEvent_t e : f->fork_ev)
         if (e) cudaEventDestroy(e);
     if (f->join_ev) cudaEventDestroy(f->join_ev);
+    if (f->s1) cudaStreamDestroy(f->s1);
+    if (f->s1_in) cudaEventDestroy(f->s1_in);
+    if (f->s1_out) cudaEventDestroy(f->s1_out);
     if (f->s2) cudaStreamDestroy(f->s2);
     if (f->s3) cudaStreamDestroy(f->s3);
     for (cudaEvent_t e : f->sync_ev)
@@ -440,7 +447,7 @@ static int run_graph(mf_factors* F, int kind, const void* p0, const void* p1, co
         return rc != MF_OK ? rc : MF_ECUDA;
     }
     cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, graph, 0);
+    e = cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -490,6 +497,14 @@ static int build_plan(mf_factors* F) {
     std::vector<InvTask> invt;
     std::vector<AsmTile> asmt;
     std::vector<DiagTask> pan;
+    // fronts whose 64 x 64 pivot-block inverses the pivot-block kernel also writes into Q
+    std::vector<char> q_from_pdiag(a->n_front, 0);
+    auto diag_q = [&](int32_t f) -> int64_t {
+        const FrontDev& fr = a->fronts[f];
+        if (!F->pinv || F->nb != 64 || fr.q_off < 0) return -1;
+        q_from_pdiag[f] = 1;
+        return fr.q_off;
+    };
     std::vector<GemmTile> gem;
     std::vector<TcTile> gtc;
     std::vector<TcPack> tcp;
@@ -873,6 +888,7 @@ static int build_plan(mf_factors* F) {
                 int th = F->opt.fused_threads[bi];
                 if (th <= 0) th = hi <= 64 ? 128 : 256;
                 push({K_FUSED, c, (int)L.size(), hi, (int64_t)flist.size(), bi, th}, FAM_FUSED, by, fl);
+                for (int32_t fi : L) F->plan.back().kmax = std::max(F->plan.back().kmax, a->fronts[fi].k);
                 flist.insert(flist.end(), L.begin(), L.end());
                 fwoff.resize(flist.size(), -1);
             }
@@ -960,7 +976,7 @@ static int build_plan(mf_factors* F) {
                     const FrontDev& fr = a->fronts[big[bi]];
                     if (kb >= fr.k) continue;
                     const int w = std::min(nb, fr.k - kb);
-                    pan.push_back({big[bi], kb, w, 0, (int64_t)bi * 64 * 64});
+                    pan.push_back({big[bi], kb, w, 0, (int64_t)bi * 64 * 64, diag_q(big[bi])});
                     pb += 3.0 * T * w * w;
                     pf += 2.0 * w * w * w;
                 }
@@ -1024,7 +1040,7 @@ static int build_plan(mf_factors* F) {
                     const FrontDev& fr = a->fronts[big[bi]];
                     if (kb + nb >= fr.k) continue;
                     const int w = std::min(nb, fr.k - kb - nb);
-                    pan.push_back({big[bi], kb + nb, w, pre, (int64_t)bi * 64 * 64});
+                    pan.push_back({big[bi], kb + nb, w, pre, (int64_t)bi * 64 * 64, diag_q(big[bi])});
                     pb += T * (3.0 * w * w + 2.0 * w * pre);
                     pf += 2.0 * w * w * w + 2.0 * w * w * pre;
                 }
@@ -1136,6 +1152,7 @@ static int build_plan(mf_factors* F) {
             double by = 0, fl = 0;
             for (int32_t f : ivf) {
                 const FrontDev& fr = a->fronts[f];
+                if (q_from_pdiag[f]) continue;  // written by the pivot-block kernel
                 for (int kb = 0; kb < fr.k; kb += 64) {
                     int w = std::min(64, fr.k - kb);
                     invt.push_back({f, kb, w, 0, fr.q_off});
@@ -1143,7 +1160,7 @@ static int build_plan(mf_factors* F) {
                     fl += 2.0 * w * w * w / 3.0;
                 }
             }
-            push({K_INVDIAG, cls, (int)(invt.size() - off), 0, off}, FAM_INV, by, fl);
+            if (invt.size() > (size_t)off) push({K_INVDIAG, cls, (int)(invt.size() - off), 0, off}, FAM_INV, by, fl);
             for (int S = 64; S < maxk; S *= 2) {
                 int64_t scr = 0;
                 int64_t g1 = (int64_t)gem.size();
@@ -1347,7 +1364,8 @@ static int set_smem_limits() {
     CUDA_TRY(cudaGetDevice(&dev));
     int maxsm = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    CUDA_TRY(cudaFuncSetAttribute(k_front_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_front_fused<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_front_fused<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_fwd_cta<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_fwd_cta<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_bwd_cta<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
@@ -1521,8 +1539,24 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     TRY(dev_alloc((char**)&F->d_pnl, (size_t)F->pnl_size * F->tsize));
     if (F->pk_size > 0) TRY(dev_alloc((char**)&F->d_pk, (size_t)F->pk_size * sizeof(float)));
     if (F->pk2_size > 0) TRY(dev_alloc((char**)&F->d_pk2, (size_t)F->pk2_size * sizeof(float)));
+    // Stream priorities: the chain of the main stream (and the lookahead pivot blocks beside it) is
+    // the critical path; the side stream's inverses fill the SMs it leaves idle, so their CTAs must
+    // not hold SMs that the next pivot block or panel product is waiting for.
+    int prio_lo = 0, prio_hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) {
+        free_factors(F);
+        return MF_ECUDA;
+    }
+    if (F->n_forks > 0 || F->n_sync > 0) {
+        if (cudaStreamCreateWithPriority(&F->s1, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+            cudaEventCreateWithFlags(&F->s1_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&F->s1_out, cudaEventDisableTiming) != cudaSuccess) {
+            free_factors(F);
+            return MF_ECUDA;
+        }
+    }
     if (F->n_forks > 0) {
-        if (cudaStreamCreateWithFlags(&F->s2, cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaStreamCreateWithPriority(&F->s2, cudaStreamNonBlocking, prio_lo) != cudaSuccess) {
             free_factors(F);
             return MF_ECUDA;
         }
@@ -1538,7 +1572,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
         }
     }
     if (F->n_sync > 0) {
-        if (cudaStreamCreateWithFlags(&F->s3, cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaStreamCreateWithPriority(&F->s3, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
             free_factors(F);
             return MF_ECUDA;
         }
@@ -1611,7 +1645,12 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
     k_init_status<<<1, 1, 0, s>>>(F->d_status);
     CUDA_TRY(cudaMemsetAsync(F->d_famax, 0, sizeof(unsigned int) * a->n_front, s));
     prof_end(F, s, slot);
-    const cudaStream_t s_main = s;
+    const cudaStream_t s_caller = s;
+    if (F->s1) {  // the plan runs on the high-priority stream, joined back at the end
+        CUDA_TRY(cudaEventRecord(F->s1_in, s_caller));
+        CUDA_TRY(cudaStreamWaitEvent(F->s1, F->s1_in, 0));
+    }
+    const cudaStream_t s_main = F->s1 ? F->s1 : s_caller;
     for (size_t li = 0; li < F->plan.size(); li++) {
         const Launch& L = F->plan[li];
         if (L.kind == K_FORK) {  // the side stream continues after everything issued so far
@@ -1640,8 +1679,12 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
             case K_FUSED: {
                 int ldm = L.maxm | 1;
                 size_t sm = fused_smem<T>(L.maxm);
-                k_front_fused<T><<<L.count, L.threads, sm, s>>>(F->d_frec + L.off, F->d_maps, d_values, a->npe,
-                                                              fac, cb, L.maxm, ldm, F->tol_rel, F->d_status);
+#define FUSED_LAUNCH(BLK)                                                                                          \
+    k_front_fused<T, BLK><<<L.count, L.threads, sm, s>>>(F->d_frec + L.off, F->d_maps, d_values, a->npe, fac, cb, \
+                                                         L.maxm, ldm, F->tol_rel, F->sym ? 1 : 0, F->d_status)
+                if (L.kmax <= kFusedBlockedMaxK) FUSED_LAUNCH(true);
+                else FUSED_LAUNCH(false);
+#undef FUSED_LAUNCH
                 break;
             }
             case K_GRP: {
@@ -1671,19 +1714,19 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
                     if (L.wide) {
                         if (F->pinv)
                             k_panel_diag_blk<T, NB, double, true><<<L.count, 256, panel_diag_dyn_smem<T, NB, double>(), s>>>(
-                                F->d_fronts, dt, fac, (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
+                                F->d_fronts, dt, fac, (T*)F->d_pnl, (T*)F->d_inv, F->d_famax, F->tol_rel, F->d_status);
                         else
                             k_panel_diag_blk<T, NB, double, false><<<L.count, 256, panel_diag_dyn_smem<T, NB, double>(), s>>>(
-                                F->d_fronts, dt, fac, (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
+                                F->d_fronts, dt, fac, (T*)F->d_pnl, (T*)F->d_inv, F->d_famax, F->tol_rel, F->d_status);
                         break;
                     }
                 }
                 if (F->pinv)
                     k_panel_diag_blk<T, NB, T, true><<<L.count, 256, panel_diag_dyn_smem<T, NB>(), s>>>(
-                        F->d_fronts, dt, fac, (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
+                        F->d_fronts, dt, fac, (T*)F->d_pnl, (T*)F->d_inv, F->d_famax, F->tol_rel, F->d_status);
                 else
                     k_panel_diag_blk<T, NB, T, false><<<L.count, 256, panel_diag_dyn_smem<T, NB>(), s>>>(
-                        F->d_fronts, dt, fac, (T*)F->d_pnl, F->d_famax, F->tol_rel, F->d_status);
+                        F->d_fronts, dt, fac, (T*)F->d_pnl, (T*)F->d_inv, F->d_famax, F->tol_rel, F->d_status);
                 break;
             }
             case K_TCD:
@@ -1762,6 +1805,10 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
         }
         prof_end(F, s, slot);
         CUDA_TRY(cudaGetLastError());
+    }
+    if (F->s1) {
+        CUDA_TRY(cudaEventRecord(F->s1_out, s_main));
+        CUDA_TRY(cudaStreamWaitEvent(s_caller, F->s1_out, 0));
     }
     return MF_OK;
 }

@@ -76,19 +76,29 @@ struct FactorRec {
 // ---------------------------------------------------------------------------
 // Fused small front: one CTA per front, the whole front in shared memory.
 // Extend-add (or the element matrix at a leaf), partial LU on the k pivots
-// with the division (T1), multiplication (T2) and subtraction (T3) tasks of
-// Sec. 3 / Table 2 on the pivot rows and columns, then P and R written out
-// and the Schur complement S = F22 - L21 U12 formed from registers straight
-// into the contribution-block arena.
+// (Sec. 3 / Table 2 tasks), P and R written out, and the Schur complement
+// S = F22 - L21 U12 formed straight into the contribution-block arena.
+// BLK (fronts with few pivots, k <= 32 for every front of the launch),
+// blocked form:
+//   (1) one warp factors the k x k pivot block: per pivot the T4 static
+//       check, T1 division of the pivot row, T2/T3 on the rows below;
+//   (2) one thread per row of L21 solves x U11 = a (U11 unit upper) and,
+//       for unsymmetric fronts, one thread per column of U12 solves
+//       L11 y = a; for symmetric fronts U12 = D^-1 L21^T (D = diag L11);
+//   (3) S from a 4 x 4 register tile per thread on a grid sized to the
+//       contribution block (ceil(nc/4)^2 tiles).
+// Three block barriers after the assembly, whatever k is.  !BLK (fronts
+// with more pivots): right-looking, one pivot at a time over the whole
+// block (two barriers per pivot), S deferred to the same tiled product.
 // Dynamic shared memory: ldm*maxm T + maxm T + 2*maxm int32 + 32 floats.
-template <typename T>
+template <typename T, bool BLK>
 __global__ void __launch_bounds__(256) k_front_fused(const FactorRec* __restrict__ recs,
                                                      const int32_t* __restrict__ maps, const double* __restrict__ values,
                                                      int npe, T* __restrict__ fac, T* __restrict__ cbs, int maxm, int ldm,
-                                                     double tol_rel, DevStatus* st) {
+                                                     double tol_rel, int sym, DevStatus* st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* F = reinterpret_cast<T*>(smem_raw);
-    T* urow = F + (size_t)ldm * maxm;
+    T* urow = F + (size_t)ldm * maxm;  // BLK: reciprocals of the pivots; otherwise the scaled pivot row
     int32_t* imap = reinterpret_cast<int32_t*>(urow + maxm);
     float* red = reinterpret_cast<float*>(imap + 2 * maxm);
 
@@ -96,107 +106,144 @@ __global__ void __launch_bounds__(256) k_front_fused(const FactorRec* __restrict
     const int32_t f = fr.front;
     const int m = fr.m, k = fr.k, nc = m - k;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int nthr = blockDim.x;
 
     const int nmap = fr.nchild > 0 ? fr.nchild * m : m;
-    for (int i = threadIdx.x; i < nmap; i += blockDim.x) imap[i] = maps[fr.map_off + i];
+    for (int i = threadIdx.x; i < nmap; i += nthr) imap[i] = maps[fr.map_off + i];
     __syncthreads();
 
-    // ---- assembly: per warp 4 columns x 2 rows per lane in flight (loads first, then stores)
+    // ---- assembly: entries in column-major order over the whole block, 8 per thread in flight
+    //      (all loads of a round before its stores); (i, j) stepped by nthr without divisions
     T amax = T(0);
-    if (fr.nchild == 0) {
+    {
+        const int mm = m * m, di = nthr % m, dj = nthr / m;
+        const bool leaf = fr.nchild == 0, two = fr.nchild > 1;
         const double* K = values + (int64_t)fr.elem * npe * npe;
-        for (int jb = warp; jb < m; jb += 4 * nwarp)
-            for (int ib = lane; ib < m; ib += 64) {
-                double v[4][2];
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-#pragma unroll
-                    for (int q = 0; q < 2; q++) {
-                        const int j = jb + u * nwarp, i = ib + 32 * q;
-                        v[u][q] = (j < m && i < m) ? K[imap[i] + imap[j] * npe] : 0.0;
-                    }
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-#pragma unroll
-                    for (int q = 0; q < 2; q++) {
-                        const int j = jb + u * nwarp, i = ib + 32 * q;
-                        if (j < m && i < m) {
-                            const T t = (T)v[u][q];
-                            F[i + j * ldm] = t;
-                            amax = max(amax, (T)fabs(t));
-                        }
-                    }
-            }
-    } else {
-        const int n0 = fr.cn[0];
-        const T* S0 = cbs + fr.cS[0];
-        const bool two = fr.nchild > 1;
+        const T* S0 = leaf ? nullptr : cbs + fr.cS[0];
         const T* S1 = two ? cbs + fr.cS[1] : nullptr;
-        const int n1 = two ? fr.cn[1] : 0;
-        for (int jb = warp; jb < m; jb += 4 * nwarp)
-            for (int ib = lane; ib < m; ib += 64) {
-                T v[4][2];
+        const int n0 = leaf ? 0 : fr.cn[0], n1 = two ? fr.cn[1] : 0;
+        int i = threadIdx.x % m, j = threadIdx.x / m;
+        for (int e0 = threadIdx.x; e0 < mm; e0 += 8 * nthr) {
+            T v[8];
+            int ii[8], jj[8];
 #pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int j = jb + u * nwarp;
-                    const int j0 = j < m ? imap[j] : -1;
-                    const int j1 = (two && j < m) ? imap[m + j] : -1;
-#pragma unroll
-                    for (int q = 0; q < 2; q++) {
-                        const int i = ib + 32 * q;
-                        T x = T(0);
-                        if (i < m) {
-                            const int i0 = imap[i];
-                            if (i0 >= 0 && j0 >= 0) x += S0[i0 + (int64_t)j0 * n0];
-                            if (j1 >= 0) {
-                                const int i1 = imap[m + i];
-                                if (i1 >= 0) x += S1[i1 + (int64_t)j1 * n1];
-                            }
+            for (int u = 0; u < 8; u++) {
+                ii[u] = i;
+                jj[u] = j;
+                T x = T(0);
+                if (e0 + u * nthr < mm) {
+                    if (leaf) {
+                        x = (T)K[imap[i] + imap[j] * npe];
+                    } else {
+                        const int i0 = imap[i], j0 = imap[j];
+                        if (i0 >= 0 && j0 >= 0) x = S0[i0 + j0 * n0];
+                        if (two) {
+                            const int i1 = imap[m + i], j1 = imap[m + j];
+                            if (i1 >= 0 && j1 >= 0) x += S1[i1 + j1 * n1];
                         }
-                        v[u][q] = x;
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-#pragma unroll
-                    for (int q = 0; q < 2; q++) {
-                        const int j = jb + u * nwarp, i = ib + 32 * q;
-                        if (j < m && i < m) {
-                            F[i + j * ldm] = v[u][q];
-                            amax = max(amax, (T)fabs(v[u][q]));
-                        }
-                    }
+                v[u] = x;
+                i += di;
+                j += dj;
+                if (i >= m) {
+                    i -= m;
+                    j++;
+                }
             }
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (e0 + u * nthr < mm) {
+                    F[ii[u] + jj[u] * ldm] = v[u];
+                    amax = max(amax, (T)fabs(v[u]));
+                }
+        }
     }
     amax = block_max_abs(amax, red);  // includes __syncthreads
     const T thr = (T)tol_rel * amax > T(0) ? (T)tol_rel * amax : tiny_pivot<T>();
 
-    // ---- partial LU on the fully assembled pivots (Table 2 compute_front), the Schur block deferred:
-    //      per pivot p the division T1 runs along the whole pivot row, the multiply-subtract T2/T3 only
-    //      on the pivot columns (all rows below p) and on the pivot rows' right part (R); the
-    //      contribution block then takes all k pivots in one register-tiled update below
-    const int nthr = blockDim.x;
-    for (int p = 0; p < k; p++) {
-        T piv = checked_pivot(F[p + p * ldm], thr, threadIdx.x == 0, f, p, st);
-        // T1: divide the pivot row right of the pivot
-        for (int j = p + 1 + threadIdx.x; j < m; j += nthr) {
-            T u = F[p + j * ldm] / piv;
-            F[p + j * ldm] = u;
-            urow[j] = u;
-        }
-        if (threadIdx.x == 0) F[p + p * ldm] = piv;
-        __syncthreads();
-        // T2/T3 on the pivot columns p < j < k: one thread per row i > p
-        for (int i = p + 1 + threadIdx.x; i < m; i += nthr) {
-            const T lip = F[i + p * ldm];
-            for (int j = p + 1; j < k; j++) F[i + j * ldm] -= lip * urow[j];
-        }
-        // T2/T3 on R: rows p < i < k, columns j >= k (lanes down a column)
-        for (int j = k + warp; j < m; j += nwarp) {
-            const T u = urow[j];
-            for (int i = p + 1 + lane; i < k; i += 32) F[i + j * ldm] -= F[i + p * ldm] * u;
+    if constexpr (BLK) {
+        T* rd = urow;
+        // ---- (1) pivot block, one warp: per pivot the static check (T4), the division of the pivot
+        //      row (T1, one lane per entry) and the update of the rows below (T2/T3, one lane per row)
+        if (warp == 0) {
+            for (int p = 0; p < k; p++) {
+                const T piv = checked_pivot(F[p + p * ldm], thr, lane == 0, f, p, st);
+                const T rinv = T(1) / piv;
+                __syncwarp();
+                if (lane == 0) {
+                    F[p + p * ldm] = piv;
+                    rd[p] = rinv;
+                }
+                for (int c = p + 1 + lane; c < k; c += 32) F[p + c * ldm] *= rinv;
+                __syncwarp();
+                for (int r = p + 1 + lane; r < k; r += 32) {
+                    const T l = F[r + p * ldm];
+                    for (int c = p + 1; c < k; c++) F[r + c * ldm] -= l * F[p + c * ldm];
+                }
+                __syncwarp();
+            }
         }
         __syncthreads();
+        // ---- (2) L21 by rows (x U11 = a), U12 by columns (L11 y = a) or from L21 (symmetric);
+        //      each solve in place in its own row / column, four partial sums per step
+        const int nsolve = sym ? nc : 2 * nc;
+        for (int t = threadIdx.x; t < nsolve; t += nthr) {
+            if (t < nc) {
+                const int i = k + t;
+                for (int c = 1; c < k; c++) {
+                    T s0 = F[i + c * ldm], s1 = T(0), s2 = T(0), s3 = T(0);
+                    int q = 0;
+                    for (; q + 4 <= c; q += 4) {
+                        s0 -= F[i + q * ldm] * F[q + c * ldm];
+                        s1 -= F[i + (q + 1) * ldm] * F[q + 1 + c * ldm];
+                        s2 -= F[i + (q + 2) * ldm] * F[q + 2 + c * ldm];
+                        s3 -= F[i + (q + 3) * ldm] * F[q + 3 + c * ldm];
+                    }
+                    for (; q < c; q++) s0 -= F[i + q * ldm] * F[q + c * ldm];
+                    F[i + c * ldm] = (s0 + s1) + (s2 + s3);
+                }
+                if (sym)
+                    for (int c = 0; c < k; c++) F[c + i * ldm] = F[i + c * ldm] * rd[c];
+            } else {
+                const int j = k + (t - nc);
+                for (int r = 0; r < k; r++) {
+                    T s0 = F[r + j * ldm], s1 = T(0), s2 = T(0), s3 = T(0);
+                    int q = 0;
+                    for (; q + 4 <= r; q += 4) {
+                        s0 -= F[r + q * ldm] * F[q + j * ldm];
+                        s1 -= F[r + (q + 1) * ldm] * F[q + 1 + j * ldm];
+                        s2 -= F[r + (q + 2) * ldm] * F[q + 2 + j * ldm];
+                        s3 -= F[r + (q + 3) * ldm] * F[q + 3 + j * ldm];
+                    }
+                    for (; q < r; q++) s0 -= F[r + q * ldm] * F[q + j * ldm];
+                    F[r + j * ldm] = ((s0 + s1) + (s2 + s3)) * rd[r];
+                }
+            }
+        }
+        __syncthreads();
+    } else {
+        // ---- right-looking partial LU, the Schur block deferred: per pivot the division T1 along
+        //      the whole pivot row, T2/T3 only on the pivot columns and on the pivot rows' right part
+        for (int p = 0; p < k; p++) {
+            T piv = checked_pivot(F[p + p * ldm], thr, threadIdx.x == 0, f, p, st);
+            for (int j = p + 1 + threadIdx.x; j < m; j += nthr) {
+                T u = F[p + j * ldm] / piv;
+                F[p + j * ldm] = u;
+                urow[j] = u;
+            }
+            if (threadIdx.x == 0) F[p + p * ldm] = piv;
+            __syncthreads();
+            for (int i = p + 1 + threadIdx.x; i < m; i += nthr) {
+                const T lip = F[i + p * ldm];
+                for (int j = p + 1; j < k; j++) F[i + j * ldm] -= lip * urow[j];
+            }
+            for (int j = k + warp; j < m; j += nwarp) {
+                const T u = urow[j];
+                for (int i = p + 1 + lane; i < k; i += 32) F[i + j * ldm] -= F[i + p * ldm] * u;
+            }
+            __syncthreads();
+        }
     }
 
     // ---- write P (m x k), R (k x nc)
@@ -206,48 +253,48 @@ __global__ void __launch_bounds__(256) k_front_fused(const FactorRec* __restrict
     T* R = fac + fr.R_off;
     for (int j = k + warp; j < m; j += nwarp)
         for (int i = lane; i < k; i += 32) R[i + (int64_t)(j - k) * k] = F[i + j * ldm];
-    // ---- S = F22 - L21 U12 straight to the contribution-block arena.  Threads form a 16 x (nthr/16)
-    //      grid; each holds 4 x 4 outputs strided by 16 rows / nthr/16 columns (so a warp's shared reads
-    //      of L21 hit 16 consecutive rows and those of U12 two columns), the k-deep sum in registers.
+    // ---- S = F22 - L21 U12 straight to the contribution-block arena: g = ceil(nc / 4) row and
+    //      column groups; thread tile (ti, tj) holds outputs (ti + g a, tj + g b), a, b < 4, so a
+    //      warp's shared reads of L21 run down consecutive rows and those of U12 are broadcasts
     if (nc > 0) {
         T* S = cbs + fr.S_off;
-        const int tr = threadIdx.x & 15, tcn = nthr >> 4, tc = threadIdx.x >> 4;
-        for (int j0 = 0; j0 < nc; j0 += 4 * tcn)
-            for (int i0 = 0; i0 < nc; i0 += 64) {
-                T acc[4][4];
+        const int g = (nc + 3) >> 2;
+        for (int t = threadIdx.x; t < g * g; t += nthr) {
+            const int ti = t % g, tj = t / g;
+            T acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int b = 0; b < 4; b++) acc[a][b] = T(0);
+            int ri[4], cj[4];
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                ri[a] = min(ti + g * a, nc - 1);
+                cj[a] = min(tj + g * a, nc - 1);
+            }
+            for (int l = 0; l < k; l++) {
+                T la[4], ub[4];
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    la[a] = F[(k + ri[a]) + l * ldm];
+                    ub[a] = F[l + (k + cj[a]) * ldm];
+                }
 #pragma unroll
                 for (int a = 0; a < 4; a++)
 #pragma unroll
-                    for (int b = 0; b < 4; b++) acc[a][b] = T(0);
-                int ri[4], cj[4];
+                    for (int b = 0; b < 4; b++) acc[a][b] += la[a] * ub[b];
+            }
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                const int j = tj + g * b;
+                if (j >= nc) continue;
 #pragma unroll
                 for (int a = 0; a < 4; a++) {
-                    ri[a] = min(i0 + tr + 16 * a, nc - 1);
-                    cj[a] = min(j0 + tc + tcn * a, nc - 1);
-                }
-                for (int l = 0; l < k; l++) {
-                    T la[4], ub[4];
-#pragma unroll
-                    for (int a = 0; a < 4; a++) {
-                        la[a] = F[(k + ri[a]) + l * ldm];
-                        ub[a] = F[l + (k + cj[a]) * ldm];
-                    }
-#pragma unroll
-                    for (int a = 0; a < 4; a++)
-#pragma unroll
-                        for (int b = 0; b < 4; b++) acc[a][b] += la[a] * ub[b];
-                }
-#pragma unroll
-                for (int b = 0; b < 4; b++) {
-                    const int j = j0 + tc + tcn * b;
-                    if (j >= nc) continue;
-#pragma unroll
-                    for (int a = 0; a < 4; a++) {
-                        const int i = i0 + tr + 16 * a;
-                        if (i < nc) S[i + (int64_t)j * nc] = F[(k + i) + (k + j) * ldm] - acc[a][b];
-                    }
+                    const int i = ti + g * a;
+                    if (i < nc) S[i + (int64_t)j * nc] = F[(k + i) + (k + j) * ldm] - acc[a][b];
                 }
             }
+        }
     }
 }
 
@@ -449,7 +496,8 @@ __global__ void __launch_bounds__(256) k_assemble_large(const FrontDev* __restri
 // so it can be factored while the rest of those updates runs.
 struct DiagTask {
     int32_t front, kb, w, pre;
-    int64_t slot;  // panel-slot offset (64 x 64, column-major, ld 64)
+    int64_t slot;   // panel-slot offset (64 x 64, column-major, ld 64)
+    int64_t q_off;  // >= 0: the inverses also go to the front's Q block in the inverse arena (ld k)
 };
 // dynamic shared memory of k_panel_diag_blk: the U block of the lookahead update (storage type T),
 // and with a wider compute type C also the working block D and the inverse block Z (C each)
@@ -588,7 +636,8 @@ __device__ __forceinline__ void pivot_strip_publish(const C (&Ft)[RPT][RPT], con
 template <typename T, int NB, typename C = T, bool INV = true>
 __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_diag_blk(const FrontDev* __restrict__ fronts,
                                                         const DiagTask* __restrict__ tasks, T* __restrict__ fac,
-                                                        T* __restrict__ slots, const unsigned int* __restrict__ famax,
+                                                        T* __restrict__ slots, T* __restrict__ inv,
+                                                        const unsigned int* __restrict__ famax,
                                                         double tol_rel, DevStatus* st) {
     constexpr int NBB = NB / 16;
     static_assert(NB % 16 == 0 && NBB <= 4, "NB must be 16, 32, 48 or 64");
@@ -702,25 +751,26 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
         const int b = p & 1;
         const C piv = checked_pivot(colF[b][p], thr, tid == 0, t.front, kb + p, st);
         const C rinv = C(1) / piv;
-        C lc[RPT], ur[RPT];
+        // masked column / row (zero outside i > p / j > p), so every update is a plain FMA on the
+        // whole tile and only the owners of row p take a short extra step
+        C lm[RPT], ur[RPT], um[RPT];
 #pragma unroll
-        for (int r = 0; r < RPT; r++) lc[r] = colF[b][i0 + r];
+        for (int r = 0; r < RPT; r++) {
+            const C l = colF[b][i0 + r];
+            lm[r] = i0 + r > p ? l : C(0);
+        }
 #pragma unroll
-        for (int c = 0; c < RPT; c++) ur[c] = rowF[b][j0 + c] * rinv;
+        for (int c = 0; c < RPT; c++) {
+            ur[c] = rowF[b][j0 + c] * rinv;
+            um[c] = j0 + c > p ? ur[c] : C(0);
+        }
 #pragma unroll
         for (int r = 0; r < RPT; r++)
 #pragma unroll
-            for (int c = 0; c < RPT; c++) {
-                const int i = i0 + r, j = j0 + c;
-                if (i > p) {
-                    if (j > p) Ft[r][c] -= lc[r] * ur[c];
-                } else if (i == p) {
-                    if (j > p) Ft[r][c] = ur[c];
-                    else if (j == p) Ft[r][c] = piv;
-                }
-            }
+            for (int c = 0; c < RPT; c++) Ft[r][c] -= lm[r] * um[c];
+        C xr[INV ? RPT : 1];
         if constexpr (INV) {
-            C xr[RPT], yc[RPT];
+            C yc[RPT];
 #pragma unroll
             for (int c = 0; c < RPT; c++) xr[c] = rowX[b][j0 + c] * rinv;
 #pragma unroll
@@ -729,10 +779,20 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
             for (int r = 0; r < RPT; r++)
 #pragma unroll
                 for (int c = 0; c < RPT; c++) {
-                    const int i = i0 + r, j = j0 + c;
-                    if (i > p) Xt[r][c] -= lc[r] * xr[c];
-                    else if (i == p) Xt[r][c] = xr[c];
-                    if (j > p) Yt[r][c] -= yc[r] * ur[c];
+                    Xt[r][c] -= lm[r] * xr[c];
+                    Yt[r][c] -= yc[r] * um[c];
+                }
+        }
+        if (ti == p / RPT) {  // row p: U right of the pivot (T1), the checked pivot, row p of L_D^-1
+            const int rp = p % RPT;
+#pragma unroll
+            for (int r = 0; r < RPT; r++)
+#pragma unroll
+                for (int c = 0; c < RPT; c++) {
+                    const bool own = r == rp;
+                    const int j = j0 + c;
+                    Ft[r][c] = own && j > p ? ur[c] : (own && j == p ? piv : Ft[r][c]);
+                    if constexpr (INV) Xt[r][c] = own ? xr[c] : Xt[r][c];
                 }
         }
         if (p + 1 < w)
@@ -754,6 +814,11 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
     T* Zg = slots + t.slot;
     for (int j = warp; j < w; j += 8)
         for (int i = lane; i < w; i += 32) Zg[i + j * 64] = (T)Z[i][j];
+    if (t.q_off >= 0) {  // the same block of the solve's pivot-block inverse Q (ld k)
+        T* Q = inv + t.q_off;
+        for (int j = warp; j < w; j += 8)
+            for (int i = lane; i < w; i += 32) Q[(kb + i) + (int64_t)(kb + j) * fr.k] = (T)Z[i][j];
+    }
 }
 
 // ---------------------------------------------------------------------------
