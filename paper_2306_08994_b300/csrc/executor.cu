@@ -279,7 +279,7 @@ struct mf_factors {
     void* d_scr = nullptr;
     void* d_ys = nullptr;
     int64_t scr_size = 1;
-    AsmTile* d_asm = nullptr;
+    AsmRec* d_asm = nullptr;
     DiagTask* d_panel = nullptr;
     void* d_pnl = nullptr;
     int64_t pnl_size = 64 * 64;
@@ -495,7 +495,7 @@ static int build_plan(mf_factors* F) {
     std::vector<TcTileD> gtcd;   // direct tensor-core tiles
     std::vector<RowBlock> rows;
     std::vector<InvTask> invt;
-    std::vector<AsmTile> asmt;
+    std::vector<AsmRec> asmt;
     std::vector<DiagTask> pan;
     // fronts whose 64 x 64 pivot-block inverses the pivot-block kernel also writes into Q
     std::vector<char> q_from_pdiag(a->n_front, 0);
@@ -905,8 +905,25 @@ static int build_plan(mf_factors* F) {
             for (int32_t f : big) {
                 const FrontDev& fr = a->fronts[f];
                 int m = fr.m;
+                AsmRec r{};
+                r.P_off = fr.P_off;
+                r.R_off = fr.R_off;
+                r.S_off = fr.S_off;
+                r.map_off = fr.map_off;
+                r.m = m;
+                r.k = fr.k;
+                r.front = f;
+                for (int q = 0; q < fr.nchild; q++) {
+                    const FrontDev& ch = a->fronts[fr.child[q]];
+                    r.cS[q] = ch.S_off;
+                    r.cn[q] = ch.m - ch.k;
+                }
                 for (int j0 = 0; j0 < m; j0 += 64)
-                    for (int i0 = 0; i0 < m; i0 += 64) asmt.push_back({f, i0, j0, 0});
+                    for (int i0 = 0; i0 < m; i0 += 64) {
+                        r.i0 = i0;
+                        r.j0 = j0;
+                        asmt.push_back(r);
+                    }
                 for (int q = 0; q < fr.nchild; q++) {
                     const FrontDev& ch = a->fronts[fr.child[q]];
                     by += T * (double)(ch.m - ch.k) * (ch.m - ch.k);
@@ -1705,7 +1722,7 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
                 break;
             }
             case K_ASM:
-                k_assemble_large<T><<<L.count, 256, 0, s>>>(F->d_fronts, F->d_asm + L.off, F->d_maps, fac, cb, F->d_famax);
+                k_assemble_large<T><<<L.count, 256, 0, s>>>(F->d_asm + L.off, F->d_maps, fac, cb, F->d_famax);
                 break;
             case K_PDIAG: {
                 constexpr int NB = sizeof(T) == 8 ? kPanelNB64 : kPanelNB32;

@@ -319,38 +319,30 @@ __global__ void __launch_bounds__(256) k_front_grp(const FactorRec* __restrict__
     const int m = active ? fr.m : 0, k = active ? fr.k : 0;
     const bool row = i < m;
     T a[G];
-    // ---- assembly
+    // ---- assembly: lane i loads its own row's maps; column j's maps are row j's, taken from
+    //      lane j by a shuffle (rows and columns of a front share one index set; every lane of
+    //      the warp takes part, so the shuffles stay outside the leaf / internal branches).
+    //      Children of a front with m <= G have contribution blocks of order <= G, so 32-bit
+    //      offsets suffice.
     T amax = T(0);
-    if (fr.nchild == 0) {
-        const int32_t* lm = maps + fr.map_off;
-        const double* K = values + (int64_t)fr.elem * npe * npe;
-        const int li = row ? lm[i] : 0;
-#pragma unroll
-        for (int j = 0; j < G; j++) {
-            T v = T(0);
-            if (row && j < m) v = (T)K[li + lm[j] * npe];
-            a[j] = v;
-            amax = max(amax, (T)fabs(v));
-        }
-    } else {
+    {
+        const bool leaf = fr.nchild == 0, two = fr.nchild > 1;
         const int32_t* m0 = maps + fr.map_off;
-        const int32_t* m1 = m0 + m;
-        const int n0 = fr.cn[0];
+        const int i0 = row ? m0[i] : -1;  // leaf: element-local node; internal: child-0 CB row
+        const int i1 = (row && two) ? m0[m + i] : -1;
+        const double* K = values + (int64_t)(leaf ? fr.elem : 0) * npe * npe;
         const T* S0 = cbs + fr.cS[0];
-        const bool two = fr.nchild > 1;
-        const T* S1 = two ? cbs + fr.cS[1] : nullptr;
-        const int n1 = two ? fr.cn[1] : 0;
-        const int i0 = row ? m0[i] : -1, i1 = (row && two) ? m1[i] : -1;
+        const T* S1 = cbs + (two ? fr.cS[1] : 0);
+        const int n0 = fr.cn[0], n1 = two ? fr.cn[1] : 0;
 #pragma unroll
         for (int j = 0; j < G; j++) {
+            const int j0 = __shfl_sync(0xffffffffu, i0, j, G), j1 = __shfl_sync(0xffffffffu, i1, j, G);
             T v = T(0);
-            if (j < m) {
-                const int j0 = m0[j];
-                if (i0 >= 0 && j0 >= 0) v += S0[i0 + (int64_t)j0 * n0];
-                if (i1 >= 0) {
-                    const int j1 = m1[j];
-                    if (j1 >= 0) v += S1[i1 + (int64_t)j1 * n1];
-                }
+            if (leaf) {
+                if (i0 >= 0 && j0 >= 0) v = (T)K[i0 + j0 * npe];
+            } else {
+                if (i0 >= 0 && j0 >= 0) v = S0[i0 + j0 * n0];
+                if (i1 >= 0 && j1 >= 0) v += S1[i1 + j1 * n1];
             }
             a[j] = v;
             amax = max(amax, (T)fabs(v));
@@ -389,10 +381,10 @@ __global__ void __launch_bounds__(256) k_front_grp(const FactorRec* __restrict__
         T* S = cbs + fr.S_off;
 #pragma unroll
         for (int j = 0; j < G; j++) {
-            if (j < k) P[i + (int64_t)j * m] = a[j];
+            if (j < k) P[i + j * m] = a[j];
             else if (j < m) {
-                if (i < k) R[i + (int64_t)(j - k) * k] = a[j];
-                else S[(i - k) + (int64_t)(j - k) * nc] = a[j];
+                if (i < k) R[i + (j - k) * k] = a[j];
+                else S[(i - k) + (j - k) * nc] = a[j];
             }
         }
     }
@@ -406,43 +398,50 @@ struct AsmTile {
     int32_t front, i0, j0, pad;
 };
 
+// One 64 x 64 tile of a large front's extend-add, with everything the tile
+// needs of the front and its children in the record itself, so the only
+// dependent loads are record -> row/column maps -> child entries.
+struct AsmRec {
+    int64_t P_off, R_off, S_off;  // the front's P, R (factor arena) and S (CB arena)
+    int64_t cS[2];                // children's contribution blocks (CB arena)
+    int64_t map_off;              // the front's child maps (nchild blocks of m int32)
+    int32_t m, k, cn[2];          // cn: children's contribution-block orders (0 = no child)
+    int32_t i0, j0, front, pad;
+};
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_assemble_large(const FrontDev* __restrict__ fronts, const AsmTile* __restrict__ tiles,
-                                                        const int32_t* __restrict__ maps, T* __restrict__ fac,
-                                                        T* __restrict__ cbs, unsigned int* __restrict__ famax) {
+__global__ void __launch_bounds__(256, 4) k_assemble_large(const AsmRec* __restrict__ recs, const int32_t* __restrict__ maps,
+                                                        T* __restrict__ fac, T* __restrict__ cbs,
+                                                        unsigned int* __restrict__ famax) {
     __shared__ float red[8];
-    const AsmTile t = tiles[blockIdx.x];
-    const FrontDev fr = fronts[t.front];
-    const int m = fr.m, k = fr.k, nc = m - k;
+    const AsmRec t = recs[blockIdx.x];
+    const int m = t.m, k = t.k, nc = m - k;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const FrontDev c0 = fronts[fr.child[0]];
-    const int n0 = c0.m - c0.k;
-    const T* S0 = cbs + c0.S_off;
-    const T* S1 = nullptr;
-    int n1 = 0;
-    const bool two = fr.nchild > 1;
-    if (two) {
-        const FrontDev c1 = fronts[fr.child[1]];
-        n1 = c1.m - c1.k;
-        S1 = cbs + c1.S_off;
-    }
-    const int32_t* map0 = maps + fr.map_off;
+    const int n0 = t.cn[0], n1 = t.cn[1];
+    const bool one = n0 > 0, two = n1 > 0;
+    const T* S0 = cbs + t.cS[0];
+    const T* S1 = cbs + t.cS[1];
+    const int32_t* map0 = maps + t.map_off;
     const int32_t* map1 = map0 + m;
+    // row maps of the thread's two rows and column maps of the warp's 8 columns, all issued
+    // before any child entry, then all 16 child entries before the stores; addresses are
+    // formed once per column (child column start, destination column start)
     int ri[2], r0[2], r1[2];
+#pragma unroll
     for (int q = 0; q < 2; q++) {
         ri[q] = t.i0 + lane + 32 * q;
-        r0[q] = ri[q] < m ? map0[ri[q]] : -1;
+        r0[q] = (one && ri[q] < m) ? map0[ri[q]] : -1;
         r1[q] = (two && ri[q] < m) ? map1[ri[q]] : -1;
     }
-    T amax = T(0);
-    // the warp's 8 columns: all column maps, then all child entries, then the stores, so the
-    // map -> entry load chains of the 8 columns overlap instead of running one after another
-    int cj0[8], cj1[8];
+    const T* c0[8];
+    const T* c1[8];
 #pragma unroll
     for (int u = 0; u < 8; u++) {
         const int j = t.j0 + warp + 8 * u;
-        cj0[u] = j < m ? map0[j] : -1;
-        cj1[u] = (two && j < m) ? map1[j] : -1;
+        const int a0 = (one && j < m) ? map0[j] : -1;
+        const int a1 = (two && j < m) ? map1[j] : -1;
+        c0[u] = a0 >= 0 ? S0 + (int64_t)a0 * n0 : nullptr;
+        c1[u] = a1 >= 0 ? S1 + (int64_t)a1 * n1 : nullptr;
     }
     T v[8][2];
 #pragma unroll
@@ -450,22 +449,24 @@ __global__ void __launch_bounds__(256) k_assemble_large(const FrontDev* __restri
 #pragma unroll
         for (int q = 0; q < 2; q++) {
             T x = T(0);
-            if (r0[q] >= 0 && cj0[u] >= 0) x += S0[r0[q] + (int64_t)cj0[u] * n0];
-            if (r1[q] >= 0 && cj1[u] >= 0) x += S1[r1[q] + (int64_t)cj1[u] * n1];
+            if (c0[u] != nullptr && r0[q] >= 0) x = c0[u][r0[q]];
+            if (c1[u] != nullptr && r1[q] >= 0) x += c1[u][r1[q]];
             v[u][q] = x;
         }
+    T amax = T(0);
 #pragma unroll
     for (int u = 0; u < 8; u++) {
         const int j = t.j0 + warp + 8 * u;
         if (j >= m) break;
+        // rows < k of column j go to P (j < k) or R, rows >= k to P or S
+        T* up = j < k ? fac + t.P_off + (int64_t)j * m : fac + t.R_off + (int64_t)(j - k) * k;
+        T* lo = j < k ? up : cbs + t.S_off + (int64_t)(j - k) * nc - k;
 #pragma unroll
         for (int q = 0; q < 2; q++) {
             const int i = ri[q];
             if (i >= m) continue;
             amax = max(amax, (T)fabs(v[u][q]));
-            if (j < k) fac[fr.P_off + i + (int64_t)j * m] = v[u][q];
-            else if (i < k) fac[fr.R_off + i + (int64_t)(j - k) * k] = v[u][q];
-            else cbs[fr.S_off + (i - k) + (int64_t)(j - k) * nc] = v[u][q];
+            (i < k ? up : lo)[i] = v[u][q];
         }
     }
     for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
