@@ -410,7 +410,7 @@ struct AsmRec {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_assemble_large(const AsmRec* __restrict__ recs, const int32_t* __restrict__ maps,
+__global__ void __launch_bounds__(256) k_assemble_large(const AsmRec* __restrict__ recs, const int32_t* __restrict__ maps,
                                                         T* __restrict__ fac, T* __restrict__ cbs,
                                                         unsigned int* __restrict__ famax) {
     __shared__ float red[8];
@@ -424,24 +424,19 @@ __global__ void __launch_bounds__(256, 4) k_assemble_large(const AsmRec* __restr
     const int32_t* map0 = maps + t.map_off;
     const int32_t* map1 = map0 + m;
     // row maps of the thread's two rows and column maps of the warp's 8 columns, all issued
-    // before any child entry, then all 16 child entries before the stores; addresses are
-    // formed once per column (child column start, destination column start)
-    int ri[2], r0[2], r1[2];
+    // before any child entry, then all 16 child entries before the stores
+    int ri[2], r0[2], r1[2], cj0[8], cj1[8];
 #pragma unroll
     for (int q = 0; q < 2; q++) {
         ri[q] = t.i0 + lane + 32 * q;
         r0[q] = (one && ri[q] < m) ? map0[ri[q]] : -1;
         r1[q] = (two && ri[q] < m) ? map1[ri[q]] : -1;
     }
-    const T* c0[8];
-    const T* c1[8];
 #pragma unroll
     for (int u = 0; u < 8; u++) {
         const int j = t.j0 + warp + 8 * u;
-        const int a0 = (one && j < m) ? map0[j] : -1;
-        const int a1 = (two && j < m) ? map1[j] : -1;
-        c0[u] = a0 >= 0 ? S0 + (int64_t)a0 * n0 : nullptr;
-        c1[u] = a1 >= 0 ? S1 + (int64_t)a1 * n1 : nullptr;
+        cj0[u] = (one && j < m) ? map0[j] : -1;
+        cj1[u] = (two && j < m) ? map1[j] : -1;
     }
     T v[8][2];
 #pragma unroll
@@ -449,8 +444,8 @@ __global__ void __launch_bounds__(256, 4) k_assemble_large(const AsmRec* __restr
 #pragma unroll
         for (int q = 0; q < 2; q++) {
             T x = T(0);
-            if (c0[u] != nullptr && r0[q] >= 0) x = c0[u][r0[q]];
-            if (c1[u] != nullptr && r1[q] >= 0) x += c1[u][r1[q]];
+            if (r0[q] >= 0 && cj0[u] >= 0) x += S0[r0[q] + (int64_t)cj0[u] * n0];
+            if (r1[q] >= 0 && cj1[u] >= 0) x += S1[r1[q] + (int64_t)cj1[u] * n1];
             v[u][q] = x;
         }
     T amax = T(0);
@@ -458,15 +453,14 @@ __global__ void __launch_bounds__(256, 4) k_assemble_large(const AsmRec* __restr
     for (int u = 0; u < 8; u++) {
         const int j = t.j0 + warp + 8 * u;
         if (j >= m) break;
-        // rows < k of column j go to P (j < k) or R, rows >= k to P or S
-        T* up = j < k ? fac + t.P_off + (int64_t)j * m : fac + t.R_off + (int64_t)(j - k) * k;
-        T* lo = j < k ? up : cbs + t.S_off + (int64_t)(j - k) * nc - k;
 #pragma unroll
         for (int q = 0; q < 2; q++) {
             const int i = ri[q];
             if (i >= m) continue;
             amax = max(amax, (T)fabs(v[u][q]));
-            (i < k ? up : lo)[i] = v[u][q];
+            if (j < k) fac[t.P_off + i + (int64_t)j * m] = v[u][q];
+            else if (i < k) fac[t.R_off + i + (int64_t)(j - k) * k] = v[u][q];
+            else cbs[t.S_off + (i - k) + (int64_t)(j - k) * nc] = v[u][q];
         }
     }
     for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
