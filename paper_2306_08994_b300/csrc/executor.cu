@@ -310,6 +310,12 @@ struct mf_factors {
     double* d_colabs = nullptr;  // column sums of |A| (||A^T||_inf of the adjoint refinement)
     // conjugate-gradient refinement: search direction p, s = -A p, a zero right-hand side, scalars
     double *d_cgp = nullptr, *d_cgs = nullptr, *d_zero = nullptr, *d_cg = nullptr;
+    // device-side CG loop (a while-conditional graph node): stop-test parameters (tol, iteration
+    // limit), the iteration counter, and the stream that captures the loop body
+    double* d_cgpar = nullptr;
+    int* d_cgit = nullptr;
+    cudaStream_t s_body = nullptr;
+    bool cg_loop_failed = false;  // the loop graph could not be built here: iterate from the host
     bool colabs_valid = false;
     const double* colabs_values = nullptr;
     int norm_blocks = 296;
@@ -359,6 +365,11 @@ struct mf_factors {
     double acc_bytes[MF_PROFILE_FAMILIES] = {};
     double acc_flops[MF_PROFILE_FAMILIES] = {};
     int64_t acc_launch[MF_PROFILE_FAMILIES] = {};
+    // work of one body pass of the device-side CG loop (recorded when its graph is captured), so
+    // the accounting can follow the number of passes each replay actually ran
+    double body_bytes[MF_PROFILE_FAMILIES] = {};
+    double body_flops[MF_PROFILE_FAMILIES] = {};
+    int64_t body_launch[MF_PROFILE_FAMILIES] = {};
 };
 
 enum Family { FAM_FUSED = 0, FAM_ASM = 1, FAM_PANEL = 2, FAM_TRAIL = 3, FAM_SCHUR = 4, FAM_FWD = 5, FAM_BWD = 6,
@@ -397,6 +408,7 @@ static void free_factors(mf_factors* f) {
         if (e) cudaEventDestroy(e);
     if (f->join_ev) cudaEventDestroy(f->join_ev);
     if (f->s1) cudaStreamDestroy(f->s1);
+    if (f->s_body) cudaStreamDestroy(f->s_body);
     if (f->s1_in) cudaEventDestroy(f->s1_in);
     if (f->s1_out) cudaEventDestroy(f->s1_out);
     if (f->s2) cudaStreamDestroy(f->s2);
@@ -406,7 +418,7 @@ static void free_factors(mf_factors* f) {
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_vsrc, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
-                    f->d_vec, f->d_flist, f->d_frec, f->d_fwoff, f->d_fws, f->d_fxs, f->d_pdiag, f->d_symt, f->d_trsm, f->d_gtcd, f->d_cgp, f->d_cgs, f->d_zero, f->d_cg, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
+                    f->d_vec, f->d_flist, f->d_frec, f->d_fwoff, f->d_fws, f->d_fxs, f->d_pdiag, f->d_symt, f->d_trsm, f->d_gtcd, f->d_cgp, f->d_cgs, f->d_zero, f->d_cg, f->d_cgpar, f->d_cgit, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
                     f->d_csr_dest, f->d_elemvals, f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms, f->d_colabs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1527,6 +1539,12 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
         TRY(dev_alloc(&F->d_cgs, nv));
         TRY(dev_alloc(&F->d_zero, nv));
         TRY(dev_alloc(&F->d_cg, (size_t)4 * F->max_nrhs));
+        TRY(dev_alloc(&F->d_cgpar, (size_t)2));
+        TRY(dev_alloc(&F->d_cgit, (size_t)1));
+        if (cudaStreamCreateWithFlags(&F->s_body, cudaStreamNonBlocking) != cudaSuccess) {
+            free_factors(F);
+            return MF_ECUDA;
+        }
         if (cudaMemset(F->d_zero, 0, nv * sizeof(double)) != cudaSuccess ||
             cudaMemset(F->d_cg, 0, 4 * F->max_nrhs * sizeof(double)) != cudaSuccess) {
             free_factors(F);
@@ -2267,7 +2285,7 @@ static int refine_impl(mf_factors* F, const double* d_values, const double* d_b,
             const double* q = &h[6 * r];
             double den = anorm * q[1] + q[2];
             double e = den > 0 ? q[0] / den : (q[0] > 0 ? INFINITY : 0.0);
-            eta = std::max(eta, e);
+            if (std::isnan(e) || e > eta) eta = e;  // a NaN norm is never taken for convergence
             rel = std::max(rel, q[4] > 0 ? std::sqrt(q[3] / q[4]) : std::sqrt(q[3]));
         }
         return MF_OK;
@@ -2314,6 +2332,97 @@ static int refine_impl(mf_factors* F, const double* d_values, const double* d_b,
             };
         };
         auto true_residual = [&](cudaStream_t st) -> int { return residual_norms(st); };
+        // With graph replay the CG iterations run in one graph: the restart step, the stop test on
+        // the device (k_cg_test), then a while-conditional node whose body is one CG step and the
+        // stop test again; the host reads the norms once per loop instead of once per iteration.
+        const bool device_loop = F->opt.use_graph && !F->prof && F->sweep_f.empty() && s != nullptr && !F->cg_loop_failed;
+        auto cg_loop = [&](cudaStream_t st) -> int {
+            int r2;
+            CUDA_TRY(cudaMemsetAsync(F->d_cgit, 0, sizeof(int), st));
+            if ((r2 = cg_step(true)(st))) return r2;
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t g = nullptr;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t nd = 0;
+            CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+            if (cs != cudaStreamCaptureStatusActive) return MF_EINVAL;
+            cudaGraphConditionalHandle h;
+            CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+            prof_begin(F, st, FAM_OTHER, 0.0, 0.0, 1);
+            k_cg_test<<<1, 32, 0, st>>>(F->d_norms, nrhs, F->d_cgpar, F->d_cgit, h);
+            CUDA_TRY(cudaGetLastError());
+            CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+            cudaGraphNodeParams cp{};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node;
+            CUDA_TRY(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+            CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+            CUDA_TRY(cudaStreamBeginCaptureToGraph(F->s_body, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeThreadLocal));
+            for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {
+                F->body_launch[q] = F->acc_launch[q];
+                F->body_bytes[q] = F->acc_bytes[q];
+                F->body_flops[q] = F->acc_flops[q];
+            }
+            r2 = cg_step(false)(F->s_body);
+            if (r2 == MF_OK) {
+                prof_begin(F, F->s_body, FAM_OTHER, 0.0, 0.0, 1);
+                k_cg_test<<<1, 32, 0, F->s_body>>>(F->d_norms, nrhs, F->d_cgpar, F->d_cgit, h);
+            }
+            for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {
+                F->body_launch[q] = F->acc_launch[q] - F->body_launch[q];
+                F->body_bytes[q] = F->acc_bytes[q] - F->body_bytes[q];
+                F->body_flops[q] = F->acc_flops[q] - F->body_flops[q];
+            }
+            cudaGraph_t body = nullptr;
+            const cudaError_t e1 = cudaGetLastError(), e2 = cudaStreamEndCapture(F->s_body, &body);
+            if (r2 != MF_OK) return r2;
+            if (e1 != cudaSuccess || e2 != cudaSuccess) return MF_ECUDA;
+            return MF_OK;
+        };
+        auto run_loop = [&]() -> int {  // graph kind 10; it counts the iterations run so far
+            int cnt = 0;
+            k_cg_params<<<1, 1, 0, s>>>(F->d_cgpar, tol, maxit - it);
+            CUDA_TRY(cudaGetLastError());
+            int r2;
+            if ((r2 = run_graph(F, 10, d_values, d_b, d_x, nrhs, s, cg_loop))) return r2;
+            CUDA_TRY(cudaMemcpyAsync(&cnt, F->d_cgit, sizeof(int), cudaMemcpyDeviceToHost, s));
+            if ((r2 = read_eta())) return r2;  // synchronises s
+            it += cnt;
+            // the graph's accounting holds one body pass; the replay ran cnt - 1 of them
+            for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {
+                F->acc_launch[q] += (int64_t)(cnt - 2) * F->body_launch[q];
+                F->acc_bytes[q] += (cnt - 2) * F->body_bytes[q];
+                F->acc_flops[q] += (cnt - 2) * F->body_flops[q];
+            }
+            return MF_OK;
+        };
+        bool loop_built = device_loop;
+        if (device_loop && (rc = run_loop())) {
+            // no loop graph was captured (nothing of it ran): keep to the host-driven iteration
+            (void)cudaGetLastError();
+            F->cg_loop_failed = true;
+            loop_built = false;
+            it = 0;
+        }
+        if (loop_built) {
+            for (;;) {
+                if (!std::isfinite(eta)) break;
+                if ((rc = run_graph(F, 9, d_values, d_b, d_x, nrhs, s, true_residual))) return rc;
+                if ((rc = read_eta())) return rc;
+                if (eta <= tol || it >= maxit || !std::isfinite(eta)) break;
+                if ((rc = run_loop())) return rc;  // the true residual drifted above tol: restart
+            }
+            if (info) {
+                info->iterations = it;
+                info->backward_error = eta;
+                info->rel_residual = rel;
+            }
+            return eta <= tol ? MF_OK : MF_ENOCONV;
+        }
         // graph kinds 7-9: CG restart step, CG step, true residual (forward system only)
         if ((rc = run_graph(F, 7, d_values, d_b, d_x, nrhs, s, cg_step(true)))) return rc;
         it = 1;

@@ -1229,6 +1229,31 @@ __global__ void k_cg_p(double* __restrict__ p, const double* __restrict__ z, con
     p[q] = fma(beta, p[q], z[q]);
 }
 
+// Stop test of the device-side CG loop, the host's test restated: eta = max over the right-hand
+// sides of |r| / (|A| |x| + |b|) from the norms block (a NaN stops the loop); continue while
+// eta > tol and fewer than the allowed iterations have run (par = {tol, iterations allowed}).
+__global__ void k_cg_test(const double* __restrict__ norms, int nrhs, const double* __restrict__ par,
+                          int* __restrict__ iter, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0) return;
+    const double anorm = norms[5];
+    double eta = 0.0;
+    for (int r = 0; r < nrhs; r++) {
+        const double* q = norms + 6 * r;
+        const double den = anorm * q[1] + q[2];
+        const double e = den > 0 ? q[0] / den : (q[0] > 0 ? INFINITY : 0.0);
+        if (isnan(e) || e > eta) eta = e;
+    }
+    const int it = *iter + 1;
+    *iter = it;
+    const bool go = eta > par[0] && isfinite(eta) && (double)it < par[1];
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void k_cg_params(double* __restrict__ par, double tol, int allowed) {
+    par[0] = tol;
+    par[1] = (double)allowed;
+}
+
 __global__ void k_cg_commit(double* __restrict__ cg, int nrhs) {
     const int r = threadIdx.x;
     if (r < nrhs) cg[4 * r] = cg[4 * r + 2];
