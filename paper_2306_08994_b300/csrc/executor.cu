@@ -315,7 +315,8 @@ struct mf_factors {
     double* d_cgpar = nullptr;
     int* d_cgit = nullptr;
     cudaStream_t s_body = nullptr;
-    bool cg_loop_failed = false;  // the loop graph could not be built here: iterate from the host
+    bool loop_failed = false;  // a loop graph could not be built here: iterate from the host
+    int loop_first_inc = 0;    // 1 when the loop graph's first step counts as an iteration (CG)
     bool colabs_valid = false;
     const double* colabs_values = nullptr;
     int norm_blocks = 296;
@@ -1534,17 +1535,17 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     TRY(dev_alloc(&F->d_colabs, (size_t)a->n_dof));
     TRY(dev_alloc(&F->d_part, (size_t)F->norm_blocks * 6 * F->max_nrhs));
     TRY(dev_alloc(&F->d_norms, (size_t)6 * F->max_nrhs));
+    TRY(dev_alloc(&F->d_cgpar, (size_t)2));
+    TRY(dev_alloc(&F->d_cgit, (size_t)1));
+    if (cudaStreamCreateWithFlags(&F->s_body, cudaStreamNonBlocking) != cudaSuccess) {
+        free_factors(F);
+        return MF_ECUDA;
+    }
     if (F->sym && F->opt.refine_cg) {
         TRY(dev_alloc(&F->d_cgp, nv));
         TRY(dev_alloc(&F->d_cgs, nv));
         TRY(dev_alloc(&F->d_zero, nv));
         TRY(dev_alloc(&F->d_cg, (size_t)4 * F->max_nrhs));
-        TRY(dev_alloc(&F->d_cgpar, (size_t)2));
-        TRY(dev_alloc(&F->d_cgit, (size_t)1));
-        if (cudaStreamCreateWithFlags(&F->s_body, cudaStreamNonBlocking) != cudaSuccess) {
-            free_factors(F);
-            return MF_ECUDA;
-        }
         if (cudaMemset(F->d_zero, 0, nv * sizeof(double)) != cudaSuccess ||
             cudaMemset(F->d_cg, 0, 4 * F->max_nrhs * sizeof(double)) != cudaSuccess) {
             free_factors(F);
@@ -2290,6 +2291,95 @@ static int refine_impl(mf_factors* F, const double* d_values, const double* d_b,
         }
         return MF_OK;
     };
+    // Device-side loops (graph replay only): the iterations run inside one graph, as a
+    // while-conditional node whose body is one iteration followed by the stop test computed on the
+    // device (k_cg_test, the host's test restated); the host reads the norms once per loop.
+    // capture_loop records, into the capture under way on st: the iteration counter reset, `first`,
+    // the stop test (counting `first` as an iteration when first_inc = 1), then the loop node with
+    // `body` + stop test captured into its body graph on the side stream s_body.
+    const bool device_loop = F->opt.use_graph && !F->prof && F->sweep_f.empty() && s != nullptr && !F->loop_failed;
+    auto capture_loop = [&](cudaStream_t st, auto&& first, auto&& body, int first_inc) -> int {
+        int r2;
+        CUDA_TRY(cudaMemsetAsync(F->d_cgit, 0, sizeof(int), st));
+        if ((r2 = first(st))) return r2;
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+        if (cs != cudaStreamCaptureStatusActive) return MF_EINVAL;
+        cudaGraphConditionalHandle h;
+        CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+        prof_begin(F, st, FAM_OTHER, 0.0, 0.0, 1);
+        k_cg_test<<<1, 32, 0, st>>>(F->d_norms, nrhs, F->d_cgpar, F->d_cgit, first_inc, h);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        CUDA_TRY(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+        CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        CUDA_TRY(cudaStreamBeginCaptureToGraph(F->s_body, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+        for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {
+            F->body_launch[q] = F->acc_launch[q];
+            F->body_bytes[q] = F->acc_bytes[q];
+            F->body_flops[q] = F->acc_flops[q];
+        }
+        r2 = body(F->s_body);
+        if (r2 == MF_OK) {
+            prof_begin(F, F->s_body, FAM_OTHER, 0.0, 0.0, 1);
+            k_cg_test<<<1, 32, 0, F->s_body>>>(F->d_norms, nrhs, F->d_cgpar, F->d_cgit, 1, h);
+        }
+        for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {
+            F->body_launch[q] = F->acc_launch[q] - F->body_launch[q];
+            F->body_bytes[q] = F->acc_bytes[q] - F->body_bytes[q];
+            F->body_flops[q] = F->acc_flops[q] - F->body_flops[q];
+        }
+        cudaGraph_t bg = nullptr;
+        const cudaError_t e1 = cudaGetLastError(), e2 = cudaStreamEndCapture(F->s_body, &bg);
+        if (r2 != MF_OK) return r2;
+        if (e1 != cudaSuccess || e2 != cudaSuccess) return MF_ECUDA;
+        return MF_OK;
+    };
+    // runs a loop graph (kind) and adds the iterations it ran to `it`
+    auto run_loop_graph = [&](int kind, auto&& enqueue_loop) -> int {
+        int cnt = 0;
+        k_cg_params<<<1, 1, 0, s>>>(F->d_cgpar, tol, maxit - it);
+        CUDA_TRY(cudaGetLastError());
+        int r2;
+        if ((r2 = run_graph(F, kind, d_values, d_b, d_x, nrhs, s, enqueue_loop))) return r2;
+        CUDA_TRY(cudaMemcpyAsync(&cnt, F->d_cgit, sizeof(int), cudaMemcpyDeviceToHost, s));
+        if ((r2 = read_eta())) return r2;  // synchronises s
+        it += cnt;
+        // the graph's accounting holds one body pass; the replay ran max(cnt - first_inc, 0) of them
+        const int extra = cnt - F->loop_first_inc - 1;
+        for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {
+            F->acc_launch[q] += (int64_t)extra * F->body_launch[q];
+            F->acc_bytes[q] += extra * F->body_bytes[q];
+            F->acc_flops[q] += extra * F->body_flops[q];
+        }
+        return MF_OK;
+    };
+    if (device_loop && !(F->sym && F->opt.refine_cg && !trans)) {
+        // stationary refinement: the first solve, then corrections until the stop test holds
+        F->loop_first_inc = 0;
+        auto st_loop = [&](cudaStream_t st) -> int { return capture_loop(st, start, step, 0); };
+        if ((rc = run_loop_graph(trans ? 12 : 11, st_loop)) == MF_OK) {
+            if (info) {
+                info->iterations = it;
+                info->backward_error = eta;
+                info->rel_residual = rel;
+            }
+            return eta <= tol ? MF_OK : MF_ENOCONV;
+        }
+        (void)cudaGetLastError();  // no loop graph was captured (nothing of it ran): host-driven loop
+        F->loop_failed = true;
+        it = 0;
+    }
     if ((rc = run_graph(F, kind0, d_values, d_b, d_x, nrhs, s, start))) return rc;
     if ((rc = read_eta())) return rc;
     if (F->sym && F->opt.refine_cg && !trans && maxit > 0 && eta > tol && std::isfinite(eta)) {
@@ -2332,79 +2422,18 @@ static int refine_impl(mf_factors* F, const double* d_values, const double* d_b,
             };
         };
         auto true_residual = [&](cudaStream_t st) -> int { return residual_norms(st); };
-        // With graph replay the CG iterations run in one graph: the restart step, the stop test on
-        // the device (k_cg_test), then a while-conditional node whose body is one CG step and the
-        // stop test again; the host reads the norms once per loop instead of once per iteration.
-        const bool device_loop = F->opt.use_graph && !F->prof && F->sweep_f.empty() && s != nullptr && !F->cg_loop_failed;
-        auto cg_loop = [&](cudaStream_t st) -> int {
-            int r2;
-            CUDA_TRY(cudaMemsetAsync(F->d_cgit, 0, sizeof(int), st));
-            if ((r2 = cg_step(true)(st))) return r2;
-            cudaStreamCaptureStatus cs;
-            cudaGraph_t g = nullptr;
-            const cudaGraphNode_t* deps = nullptr;
-            size_t nd = 0;
-            CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
-            if (cs != cudaStreamCaptureStatusActive) return MF_EINVAL;
-            cudaGraphConditionalHandle h;
-            CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
-            prof_begin(F, st, FAM_OTHER, 0.0, 0.0, 1);
-            k_cg_test<<<1, 32, 0, st>>>(F->d_norms, nrhs, F->d_cgpar, F->d_cgit, h);
-            CUDA_TRY(cudaGetLastError());
-            CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
-            cudaGraphNodeParams cp{};
-            cp.type = cudaGraphNodeTypeConditional;
-            cp.conditional.handle = h;
-            cp.conditional.type = cudaGraphCondTypeWhile;
-            cp.conditional.size = 1;
-            cudaGraphNode_t node;
-            CUDA_TRY(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
-            CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-            CUDA_TRY(cudaStreamBeginCaptureToGraph(F->s_body, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                                   cudaStreamCaptureModeThreadLocal));
-            for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {
-                F->body_launch[q] = F->acc_launch[q];
-                F->body_bytes[q] = F->acc_bytes[q];
-                F->body_flops[q] = F->acc_flops[q];
-            }
-            r2 = cg_step(false)(F->s_body);
-            if (r2 == MF_OK) {
-                prof_begin(F, F->s_body, FAM_OTHER, 0.0, 0.0, 1);
-                k_cg_test<<<1, 32, 0, F->s_body>>>(F->d_norms, nrhs, F->d_cgpar, F->d_cgit, h);
-            }
-            for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {
-                F->body_launch[q] = F->acc_launch[q] - F->body_launch[q];
-                F->body_bytes[q] = F->acc_bytes[q] - F->body_bytes[q];
-                F->body_flops[q] = F->acc_flops[q] - F->body_flops[q];
-            }
-            cudaGraph_t body = nullptr;
-            const cudaError_t e1 = cudaGetLastError(), e2 = cudaStreamEndCapture(F->s_body, &body);
-            if (r2 != MF_OK) return r2;
-            if (e1 != cudaSuccess || e2 != cudaSuccess) return MF_ECUDA;
-            return MF_OK;
-        };
-        auto run_loop = [&]() -> int {  // graph kind 10; it counts the iterations run so far
-            int cnt = 0;
-            k_cg_params<<<1, 1, 0, s>>>(F->d_cgpar, tol, maxit - it);
-            CUDA_TRY(cudaGetLastError());
-            int r2;
-            if ((r2 = run_graph(F, 10, d_values, d_b, d_x, nrhs, s, cg_loop))) return r2;
-            CUDA_TRY(cudaMemcpyAsync(&cnt, F->d_cgit, sizeof(int), cudaMemcpyDeviceToHost, s));
-            if ((r2 = read_eta())) return r2;  // synchronises s
-            it += cnt;
-            // the graph's accounting holds one body pass; the replay ran cnt - 1 of them
-            for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {
-                F->acc_launch[q] += (int64_t)(cnt - 2) * F->body_launch[q];
-                F->acc_bytes[q] += (cnt - 2) * F->body_bytes[q];
-                F->acc_flops[q] += (cnt - 2) * F->body_flops[q];
-            }
-            return MF_OK;
+        // With graph replay the CG iterations run in one loop graph: the restart step and its stop
+        // test, then the loop node whose body is one CG step and the stop test.
+        auto cg_loop = [&](cudaStream_t st) -> int { return capture_loop(st, cg_step(true), cg_step(false), 1); };
+        auto run_loop = [&]() -> int {
+            F->loop_first_inc = 1;
+            return run_loop_graph(10, cg_loop);
         };
         bool loop_built = device_loop;
         if (device_loop && (rc = run_loop())) {
             // no loop graph was captured (nothing of it ran): keep to the host-driven iteration
             (void)cudaGetLastError();
-            F->cg_loop_failed = true;
+            F->loop_failed = true;
             loop_built = false;
             it = 0;
         }

@@ -1229,11 +1229,12 @@ __global__ void k_cg_p(double* __restrict__ p, const double* __restrict__ z, con
     p[q] = fma(beta, p[q], z[q]);
 }
 
-// Stop test of the device-side CG loop, the host's test restated: eta = max over the right-hand
-// sides of |r| / (|A| |x| + |b|) from the norms block (a NaN stops the loop); continue while
-// eta > tol and fewer than the allowed iterations have run (par = {tol, iterations allowed}).
+// Stop test of the device-side refinement loops, the host's test restated: eta = max over the
+// right-hand sides of |r| / (|A| |x| + |b|) from the norms block (a NaN stops the loop); the
+// iteration counter grows by inc (the step just taken); continue while eta > tol and fewer than
+// the allowed iterations have run (par = {tol, iterations allowed}).
 __global__ void k_cg_test(const double* __restrict__ norms, int nrhs, const double* __restrict__ par,
-                          int* __restrict__ iter, cudaGraphConditionalHandle h) {
+                          int* __restrict__ iter, int inc, cudaGraphConditionalHandle h) {
     if (threadIdx.x != 0) return;
     const double anorm = norms[5];
     double eta = 0.0;
@@ -1243,7 +1244,7 @@ __global__ void k_cg_test(const double* __restrict__ norms, int nrhs, const doub
         const double e = den > 0 ? q[0] / den : (q[0] > 0 ? INFINITY : 0.0);
         if (isnan(e) || e > eta) eta = e;
     }
-    const int it = *iter + 1;
+    const int it = *iter + inc;
     *iter = it;
     const bool go = eta > par[0] && isfinite(eta) && (double)it < par[1];
     cudaGraphSetConditional(h, go ? 1u : 0u);

@@ -705,23 +705,27 @@ def test_conjugate_gradient_refinement(case, prec):
 
 @pytest.mark.parametrize("prec", ["f32", "tf32"])
 @pytest.mark.parametrize("maxit", [30, 1])
-def test_device_side_cg_loop_matches_host_loop(prec, maxit):
-    """With graph replay on a created stream the CG iterations run inside one graph (a
-    while-conditional node whose body is one CG step and the stop test computed on the device);
-    on the default stream (no graphs) the host drives the same steps.  Iteration count, backward
-    error, the iterate itself (bit for bit: the same kernels in the same order) and the per-family
-    launch accounting (plus one stop-test kernel per iteration) agree, on a converging run and on one stopped by the iteration limit; a
-    second call replays the cached loop graph with the same result."""
+@pytest.mark.parametrize("method", ["cg", "stationary", "adjoint"])
+def test_device_side_refinement_loop_matches_host_loop(prec, maxit, method):
+    """With graph replay on a created stream the refinement iterations run inside one graph (a
+    while-conditional node whose body is one iteration and the stop test computed on the device):
+    CG, stationary refinement, and stationary refinement of the adjoint system.  On the default
+    stream (no graphs) the host drives the same steps.  Iteration count, backward error, the
+    iterate itself (bit for bit: the same kernels in the same order) and the per-family launch
+    accounting (plus one stop-test kernel per loop test) agree, on a converging run and on one
+    stopped by the iteration limit; a second call replays the cached loop graph."""
     mk, opt = SYM_CASES["q3_24_super_panel"]
     pr = mk()
     extra = {"tc_min_cb": 16} if prec == "tf32" else {}
-    a, f, vals = _setup(pr, prec, symmetric=1, refine_cg=1, use_graph=1, **opt, **extra)
+    a, f, vals = _setup(pr, prec, symmetric=1, refine_cg=1 if method != "stationary" else 0, use_graph=1, **opt,
+                        **extra)
     f.factor(vals)
     torch.cuda.synchronize()
+    adj = method == "adjoint"
     b = torch.tensor(np.ascontiguousarray(pr.b.T), device=DEV)
     x_h = torch.empty_like(b)
     f.profile_read()
-    i_h = f.refine_solve(vals, b, x_h, tol=1e-12, maxit=maxit)
+    i_h = f.refine_solve(vals, b, x_h, tol=1e-12, maxit=maxit, adjoint=adj)
     torch.cuda.synchronize()
     l_h = {k: v["launches"] for k, v in f.profile_read().items()}
     st = torch.cuda.Stream()
@@ -729,15 +733,17 @@ def test_device_side_cg_loop_matches_host_loop(prec, maxit):
     for rep in range(2):
         x_d = torch.empty_like(b)
         with torch.cuda.stream(st):
-            i_d = f.refine_solve(vals, b, x_d, tol=1e-12, maxit=maxit, stream=st)
+            i_d = f.refine_solve(vals, b, x_d, tol=1e-12, maxit=maxit, stream=st, adjoint=adj)
         st.synchronize()
         outs.append((i_d, x_d, {k: v["launches"] for k, v in f.profile_read().items()}))
     for i_d, x_d, l_d in outs:
         assert i_d["rc"] == i_h["rc"] and i_d["iterations"] == i_h["iterations"], (i_d, i_h)
         assert i_d["backward_error"] == i_h["backward_error"], (i_d, i_h)
         assert torch.equal(x_d, x_h)
-        # the device loop adds one stop-test kernel per iteration, counted with the "other" family
-        l_d = dict(l_d, other=l_d["other"] - i_d["iterations"])
+        # stop tests on the device: one per iteration, plus the one after the first solve for the
+        # stationary loop (counted with the "other" family)
+        tests = i_d["iterations"] + (0 if method == "cg" else 1)
+        l_d = dict(l_d, other=l_d["other"] - tests)
         assert l_d == l_h, (l_d, l_h)
     if maxit == 1:
         assert i_h["iterations"] == 1
