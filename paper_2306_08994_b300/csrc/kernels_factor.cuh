@@ -722,16 +722,19 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
     const C amax = (C)__uint_as_float(famax[t.front]);
     const C thr = (C)tol_rel * amax > C(0) ? (C)tol_rel * amax : (C)tiny_pivot<T>();
 
-    // Right-looking elimination, one block barrier per pivot p (Table 2 tasks on the block):
-    //   T4  the static pivot check on F[p, p],
-    //   T1  U[p, j] = F[p, j] / F[p, p] for j > p,
-    //   T2/T3  F[i, j] -= F[i, p] U[p, j] for i, j > p.
-    // The inverses ride along in the same sweep, from the same broadcast column and row:
-    //   X = L_D^-1 (L_D X = I, forward):   X[p, :] /= F[p, p];   X[i, :] -= F[i, p] X[p, :], i > p
-    //   Y = U_D^-1 (Y U_D = I, by columns): Y[:, j] -= Y[:, p] U[p, j], j > p
-    // Pivot p reads column p and row p of F (and row p of X, column p of Y) as they stand after
-    // step p - 1; their owners publish them into a double-buffered strip at the end of step p - 1.
-    __shared__ __align__(16) C colF[2][NB], rowF[2][NB], rowX[2][NB], colY[2][NB];
+    // Right-looking elimination in steps of BP = RPT pivots, one block barrier per step (Table 2
+    // tasks on the block): every thread factors the BP x BP diagonal block of the step itself
+    // (T4 static check, T1 division of the pivot row, T2/T3 inside the block; all threads compute
+    // the same values), solves its own rows of L (x U_bb = a) and columns of U (L_bb y = a)
+    // against it, and applies the rank-BP update to its tile:  F[i, j] -= L[i, blk] U[blk, j].
+    // The inverses ride along, from the same strips:
+    //   X = L_D^-1:  rows blk final as L_bb^-1 (rows blk as they stand), X[i, :] -= L[i, blk] X[blk, :]
+    //   Y = U_D^-1:  columns blk final as (columns blk as they stand) U_bb^-1, Y[:, j] -= Y[:, blk] U[blk, j]
+    // Step s reads the columns and rows p0 = s BP .. p0 + BP - 1 of F (and rows of X, columns of Y)
+    // as they stand after step s - 1, published by their owners (the threads whose tile holds them:
+    // BP = RPT, so one tile column / row of threads) into a double-buffered strip.
+    constexpr int BP = RPT;
+    __shared__ __align__(16) C colF[2][BP][NB], rowF[2][BP][NB], rowX[2][BP][NB], colY[2][BP][NB];
     C Xt[INV ? RPT : 1][INV ? RPT : 1], Yt[INV ? RPT : 1][INV ? RPT : 1];
     if constexpr (INV) {
 #pragma unroll
@@ -739,59 +742,142 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
 #pragma unroll
             for (int c = 0; c < RPT; c++) Xt[r][c] = Yt[r][c] = (i0 + r == j0 + c) ? C(1) : C(0);
     }
-    pivot_strip_publish<C, RPT, INV>(Ft, Xt, Yt, 0, ti, tj, colF[0], rowF[0], rowX[0], colY[0]);
+    auto publish = [&](int blk, int buf) {
+        if (tj == blk) {
+#pragma unroll
+            for (int c = 0; c < BP; c++)
+#pragma unroll
+                for (int r = 0; r < RPT; r++) {
+                    colF[buf][c][i0 + r] = Ft[r][c];
+                    if constexpr (INV) colY[buf][c][i0 + r] = Yt[r][c];
+                }
+        }
+        if (ti == blk) {
+#pragma unroll
+            for (int q = 0; q < BP; q++)
+#pragma unroll
+                for (int c = 0; c < RPT; c++) {
+                    rowF[buf][q][j0 + c] = Ft[q][c];
+                    if constexpr (INV) rowX[buf][q][j0 + c] = Xt[q][c];
+                }
+        }
+    };
+    publish(0, 0);
     __syncthreads();
+    const int nsteps = (w + BP - 1) / BP;
 #pragma unroll 1
-    for (int p = 0; p < w; p++) {
-        const int b = p & 1;
-        const C piv = checked_pivot(colF[b][p], thr, tid == 0, t.front, kb + p, st);
-        const C rinv = C(1) / piv;
-        // masked column / row (zero outside i > p / j > p), so every update is a plain FMA on the
-        // whole tile and only the owners of row p take a short extra step
-        C lm[RPT], ur[RPT], um[RPT];
+    for (int sb = 0; sb < nsteps; sb++) {
+        const int bb = sb & 1, p0 = sb * BP;
+        // (a) the diagonal block (identity padding beyond w: its pivots are 1 and not checked)
+        C d[BP][BP], rv[BP];
+#pragma unroll
+        for (int a = 0; a < BP; a++)
+#pragma unroll
+            for (int c = 0; c < BP; c++) d[a][c] = colF[bb][c][p0 + a];
+#pragma unroll
+        for (int q = 0; q < BP; q++) {
+            if (p0 + q < w) d[q][q] = checked_pivot(d[q][q], thr, tid == 0, t.front, kb + p0 + q, st);
+            rv[q] = C(1) / d[q][q];
+#pragma unroll
+            for (int c = q + 1; c < BP; c++) d[q][c] *= rv[q];
+#pragma unroll
+            for (int a = q + 1; a < BP; a++)
+#pragma unroll
+                for (int c = q + 1; c < BP; c++) d[a][c] -= d[a][q] * d[q][c];
+        }
+        // (b) L of my rows below the block, U of my columns right of it (zero elsewhere)
+        const bool rows_below = i0 >= p0 + BP, cols_right = j0 >= p0 + BP;
+        C lm[RPT][BP], um[RPT][BP];
 #pragma unroll
         for (int r = 0; r < RPT; r++) {
-            const C l = colF[b][i0 + r];
-            lm[r] = i0 + r > p ? l : C(0);
+#pragma unroll
+            for (int c = 0; c < BP; c++) {
+                C x = colF[bb][c][i0 + r];
+#pragma unroll
+                for (int q = 0; q < c; q++) x -= lm[r][q] * d[q][c];
+                lm[r][c] = x;
+            }
+#pragma unroll
+            for (int c = 0; c < BP; c++) lm[r][c] = rows_below ? lm[r][c] : C(0);
         }
 #pragma unroll
         for (int c = 0; c < RPT; c++) {
-            ur[c] = rowF[b][j0 + c] * rinv;
-            um[c] = j0 + c > p ? ur[c] : C(0);
+#pragma unroll
+            for (int q = 0; q < BP; q++) {
+                C y = rowF[bb][q][j0 + c];
+#pragma unroll
+                for (int t2 = 0; t2 < q; t2++) y -= d[q][t2] * um[c][t2];
+                um[c][q] = y * rv[q];
+            }
+#pragma unroll
+            for (int q = 0; q < BP; q++) um[c][q] = cols_right ? um[c][q] : C(0);
         }
+        // (c) rank-BP update of my tile, then the final values of the block's rows and columns
 #pragma unroll
         for (int r = 0; r < RPT; r++)
 #pragma unroll
-            for (int c = 0; c < RPT; c++) Ft[r][c] -= lm[r] * um[c];
-        C xr[INV ? RPT : 1];
+            for (int c = 0; c < RPT; c++) {
+                C v = Ft[r][c];
+#pragma unroll
+                for (int q = 0; q < BP; q++) v -= lm[r][q] * um[c][q];
+                Ft[r][c] = v;
+            }
+        if (ti == sb) {  // my rows are the block's rows: U right of the block, the block itself
+#pragma unroll
+            for (int r = 0; r < RPT; r++)
+#pragma unroll
+                for (int c = 0; c < RPT; c++) {
+                    if (cols_right) Ft[r][c] = um[c][r];
+                    else if (tj == sb) Ft[r][c] = d[r][c];
+                }
+        }
+        if (tj == sb && rows_below) {  // my columns are the block's columns: L below the block
+#pragma unroll
+            for (int r = 0; r < RPT; r++)
+#pragma unroll
+                for (int c = 0; c < RPT; c++) Ft[r][c] = lm[r][c];
+        }
         if constexpr (INV) {
-            C yc[RPT];
+            // X: the block's rows through L_bb^-1, then the rows below
 #pragma unroll
-            for (int c = 0; c < RPT; c++) xr[c] = rowX[b][j0 + c] * rinv;
+            for (int c = 0; c < RPT; c++) {
+                C xf[BP];
 #pragma unroll
-            for (int r = 0; r < RPT; r++) yc[r] = colY[b][i0 + r];
+                for (int q = 0; q < BP; q++) {
+                    C x = rowX[bb][q][j0 + c];
 #pragma unroll
-            for (int r = 0; r < RPT; r++)
+                    for (int t2 = 0; t2 < q; t2++) x -= d[q][t2] * xf[t2];
+                    xf[q] = x * rv[q];
+                }
+#pragma unroll
+                for (int r = 0; r < RPT; r++) {
+                    C v = Xt[r][c];
+#pragma unroll
+                    for (int q = 0; q < BP; q++) v -= lm[r][q] * xf[q];
+                    Xt[r][c] = ti == sb ? xf[r] : v;
+                }
+            }
+            // Y: the block's columns through U_bb^-1, then the columns to the right
+#pragma unroll
+            for (int r = 0; r < RPT; r++) {
+                C yf[BP];
+#pragma unroll
+                for (int q = 0; q < BP; q++) {
+                    C y = colY[bb][q][i0 + r];
+#pragma unroll
+                    for (int t2 = 0; t2 < q; t2++) y -= yf[t2] * d[t2][q];
+                    yf[q] = y;
+                }
 #pragma unroll
                 for (int c = 0; c < RPT; c++) {
-                    Xt[r][c] -= lm[r] * xr[c];
-                    Yt[r][c] -= yc[r] * um[c];
-                }
-        }
-        if (ti == p / RPT) {  // row p: U right of the pivot (T1), the checked pivot, row p of L_D^-1
-            const int rp = p % RPT;
+                    C v = Yt[r][c];
 #pragma unroll
-            for (int r = 0; r < RPT; r++)
-#pragma unroll
-                for (int c = 0; c < RPT; c++) {
-                    const bool own = r == rp;
-                    const int j = j0 + c;
-                    Ft[r][c] = own && j > p ? ur[c] : (own && j == p ? piv : Ft[r][c]);
-                    if constexpr (INV) Xt[r][c] = own ? xr[c] : Xt[r][c];
+                    for (int q = 0; q < BP; q++) v -= yf[q] * um[c][q];
+                    Yt[r][c] = tj == sb ? yf[c] : v;
                 }
+            }
         }
-        if (p + 1 < w)
-            pivot_strip_publish<C, RPT, INV>(Ft, Xt, Yt, p + 1, ti, tj, colF[b ^ 1], rowF[b ^ 1], rowX[b ^ 1], colY[b ^ 1]);
+        if (sb + 1 < nsteps) publish(sb + 1, bb ^ 1);
         __syncthreads();
     }
     // factored block back to P and the inverses to the panel slot, through shared memory (coalesced)
