@@ -262,6 +262,7 @@ struct mf_factors {
     int foata_cls = 0;
     bool sym = false;                 // symmetric factors and solves (option symmetric)
     int64_t* d_pdiag = nullptr;       // symmetric solves: factor-arena offset of each dof's pivot
+    double* d_pdv = nullptr;          // the same pivots gathered per dof at the end of each factorization
     AsmTile* d_symt = nullptr;        // tiles of the symmetric-mode R copies and S mirrors
     TrsmTask* d_trsm = nullptr;       // triangular-solve panel tasks
     TcTileD* d_gtcd = nullptr;        // tensor-core tiles that split their own operands
@@ -294,6 +295,9 @@ struct mf_factors {
     cudaStream_t s1 = nullptr;   // main factorization stream at the highest priority (with s2 / s3)
     cudaEvent_t s1_in = nullptr, s1_out = nullptr;
     cudaStream_t s2 = nullptr;   // side stream: pivot-block inverses overlap the later classes
+    cudaStream_t sfan[3] = {};   // the independent kernels of one substitution class run side by side
+    cudaEvent_t fan_in = nullptr, fan_out[3] = {};
+    bool fan_off = false;        // set while a conditional-node body is captured (single stream there)
     std::vector<cudaEvent_t> fork_ev;
     cudaEvent_t join_ev = nullptr;
     int n_forks = 0;
@@ -413,13 +417,18 @@ static void free_factors(mf_factors* f) {
     if (f->s1_in) cudaEventDestroy(f->s1_in);
     if (f->s1_out) cudaEventDestroy(f->s1_out);
     if (f->s2) cudaStreamDestroy(f->s2);
+    for (int j = 0; j < 3; j++) {
+        if (f->sfan[j]) cudaStreamDestroy(f->sfan[j]);
+        if (f->fan_out[j]) cudaEventDestroy(f->fan_out[j]);
+    }
+    if (f->fan_in) cudaEventDestroy(f->fan_in);
     if (f->s3) cudaStreamDestroy(f->s3);
     for (cudaEvent_t e : f->sync_ev)
         if (e) cudaEventDestroy(e);
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_vsrc, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
-                    f->d_vec, f->d_flist, f->d_frec, f->d_fwoff, f->d_fws, f->d_fxs, f->d_pdiag, f->d_symt, f->d_trsm, f->d_gtcd, f->d_cgp, f->d_cgs, f->d_zero, f->d_cg, f->d_cgpar, f->d_cgit, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
+                    f->d_vec, f->d_flist, f->d_frec, f->d_fwoff, f->d_fws, f->d_fxs, f->d_pdiag, f->d_pdv, f->d_symt, f->d_trsm, f->d_gtcd, f->d_cgp, f->d_cgs, f->d_zero, f->d_cg, f->d_cgpar, f->d_cgit, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
                     f->d_csr_dest, f->d_elemvals, f->d_r, f->d_d, f->d_Y, f->d_rowabs, f->d_part, f->d_norms, f->d_colabs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1503,6 +1512,7 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
             for (int p = 0; p < fr.k; p++) pd[a->dofs[fr.dof_off + p]] = fr.P_off + p + (int64_t)p * fr.m;
         }
         TRY(upload(&F->d_pdiag, pd));
+        TRY(dev_alloc(&F->d_pdv, (size_t)a->n_dof));
     }
     if (a->csr_n > 0) {
         TRY(upload(&F->d_csr_dest, a->csr_dest));
@@ -1583,6 +1593,16 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
         free_factors(F);
         return MF_ECUDA;
     }
+    if (cudaEventCreateWithFlags(&F->fan_in, cudaEventDisableTiming) != cudaSuccess) {
+        free_factors(F);
+        return MF_ECUDA;
+    }
+    for (int j = 0; j < 3; j++)
+        if (cudaStreamCreateWithPriority(&F->sfan[j], cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+            cudaEventCreateWithFlags(&F->fan_out[j], cudaEventDisableTiming) != cudaSuccess) {
+            free_factors(F);
+            return MF_ECUDA;
+        }
     if (F->n_forks > 0 || F->n_sync > 0) {
         if (cudaStreamCreateWithPriority(&F->s1, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
             cudaEventCreateWithFlags(&F->s1_in, cudaEventDisableTiming) != cudaSuccess ||
@@ -1842,6 +1862,13 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
         prof_end(F, s, slot);
         CUDA_TRY(cudaGetLastError());
     }
+    if (F->sym) {  // the pivots in dof order, read by the D scaling of every symmetric solve
+        const int64_t n = a->n_dof;
+        int slot2 = prof_begin(F, s_main, FAM_OTHER, (8.0 + F->tsize + 8.0) * n, 0.0);
+        k_gather_pivots<T><<<(unsigned)((n + 255) / 256), 256, 0, s_main>>>(F->d_pdiag, fac, F->d_pdv, n);
+        prof_end(F, s_main, slot2);
+        CUDA_TRY(cudaGetLastError());
+    }
     if (F->s1) {
         CUDA_TRY(cudaEventRecord(F->s1_out, s_main));
         CUDA_TRY(cudaStreamWaitEvent(s_caller, F->s1_out, 0));
@@ -1900,6 +1927,47 @@ static int launch_sweep(mf_factors* F, const SweepArgs<T>& args, size_t smem, in
         if (nrhs == 1) KER<SOLVE_UNPAREN TARGS, 1><<<SOLVE_UNPAREN CFG>>>(SOLVE_UNPAREN ARGS);  \
         else KER<SOLVE_UNPAREN TARGS, kRhsChunk><<<SOLVE_UNPAREN CFG>>>(SOLVE_UNPAREN ARGS);    \
     } while (0)
+
+// The kernels of one substitution class cover disjoint fronts, so they need
+// not wait for one another: the first runs on the class's stream, the others
+// on side streams that start after everything issued before the class and are
+// joined back before the class ends (graph branches under capture).
+struct Fan {
+    static constexpr int kWays = 3;
+    mf_factors* F;
+    cudaStream_t s;
+    bool on;
+    int n = 0;
+    bool used[kWays] = {};
+    cudaError_t err = cudaSuccess;
+    Fan(mf_factors* f, cudaStream_t st, int units) : F(f), s(st), on(units > 1 && !f->fan_off) {
+        if (on) err = cudaEventRecord(F->fan_in, s);
+        if (err != cudaSuccess) on = false;
+    }
+    cudaStream_t next() {
+        const int i = n++;
+        if (!on || i == 0) return s;
+        const int j = (i - 1) % kWays;
+        if (!used[j]) {
+            cudaError_t e = cudaStreamWaitEvent(F->sfan[j], F->fan_in, 0);
+            if (e != cudaSuccess) {
+                if (err == cudaSuccess) err = e;
+                return s;
+            }
+            used[j] = true;
+        }
+        return F->sfan[j];
+    }
+    cudaError_t join() {
+        for (int j = 0; j < kWays; j++) {
+            if (!used[j]) continue;
+            cudaError_t e = cudaEventRecord(F->fan_out[j], F->sfan[j]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, F->fan_out[j], 0);
+            if (e != cudaSuccess && err == cudaSuccess) err = e;
+        }
+        return err;
+    }
+};
 
 template <typename T>
 static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStream_t s, bool trans_b, bool scale_d) {
@@ -1974,10 +2042,10 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
     }
 #define INV_LAUNCH(TR, PH, CNT, OFF)                                                                               \
     if ((PH == PH_BWD1 ? C.maxnc_inv : C.maxk_inv) > 512)                                                          \
-        k_inv_gemv<T, TR, PH, 32><<<dim3(CNT, nrhs), 1024, (32 * 32 + C.maxin_inv) * sizeof(T), s>>>(            \
+        k_inv_gemv<T, TR, PH, 32><<<dim3(CNT, nrhs), 1024, (32 * 32 + C.maxin_inv) * sizeof(T), ls>>>(            \
             fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_vsrc, vec, vs, ys, yss, d_x, n);                      \
     else                                                                                                           \
-        k_inv_gemv<T, TR, PH, 8><<<dim3(CNT, nrhs), 256, (8 * 32 + C.maxin_inv) * sizeof(T), s>>>(               \
+        k_inv_gemv<T, TR, PH, 8><<<dim3(CNT, nrhs), 256, (8 * 32 + C.maxin_inv) * sizeof(T), ls>>>(               \
             fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_vsrc, vec, vs, ys, yss, d_x, n)
     for (int c = 0; c < c_top; c++) {
         const ClassList& C = F->classes_f[c];
@@ -1985,11 +2053,12 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         for (int q = 0; q < kLgLists; q++) nk += C.n_lg[q] > 0;
         int slot = prof_begin(F, s, FAM_FWD, F->fwd_bytes[c] * nrhs, F->fwd_flops[c] * nrhs, nk, -1, MF_TRACE_FWD_CLASS,
                               c, a->cls_ptr[c + 1] - a->cls_ptr[c]);
+        Fan fan(F, s, nk - (C.n_piv > 0));
 #define GRP_FWD(Q, GS)                                                                                             \
         if (C.n_grp[Q]) {                                                                                          \
             dim3 g((C.n_grp[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)));                                             \
-            if (!trans) SOLVE_NR(k_fwd_grp, (T, false, GS), (g, 256, 0, s), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
-            else SOLVE_NR(k_fwd_grp, (T, true, GS), (g, 256, 0, s), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+            if (!trans) SOLVE_NR(k_fwd_grp, (T, false, GS), (g, 256, 0, fan.next()), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+            else SOLVE_NR(k_fwd_grp, (T, true, GS), (g, 256, 0, fan.next()), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
         }
         GRP_FWD(0, 4)
         GRP_FWD(1, 8)
@@ -1998,8 +2067,8 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
 #define LG_FWD(Q, GS, RS, KMS)                                                                                      \
         if (C.n_lg[Q]) {                                                                                           \
             dim3 g((C.n_lg[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)));                                              \
-            if (!trans) SOLVE_NR(k_fwd_lg, (T, false, GS, RS, KMS), (g, 256, 0, s), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
-            else SOLVE_NR(k_fwd_lg, (T, true, GS, RS, KMS), (g, 256, 0, s), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+            if (!trans) SOLVE_NR(k_fwd_lg, (T, false, GS, RS, KMS), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+            else SOLVE_NR(k_fwd_lg, (T, true, GS, RS, KMS), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
         }
         LG_FWD(0, 4, 1, 4)
         LG_FWD(1, 8, 1, 4)
@@ -2019,22 +2088,24 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
 #undef LG_FWD
         if (C.n_grp[3]) {  // 16 < m <= 32: the one-front-per-warp kernel is faster forward
             dim3 g((C.n_grp[3] + 7) / 8);
-            if (!trans) SOLVE_NR(k_fwd_warp, (T, false), (g, 256, 0, s), (fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
-            else SOLVE_NR(k_fwd_warp, (T, true), (g, 256, 0, s), (fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
+            if (!trans) SOLVE_NR(k_fwd_warp, (T, false), (g, 256, 0, fan.next()), (fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
+            else SOLVE_NR(k_fwd_warp, (T, true), (g, 256, 0, fan.next()), (fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
         }
         if (C.n_small) {
             dim3 g((C.n_small + 7) / 8);
-            if (!trans) SOLVE_NR(k_fwd_warp, (T, false), (g, 256, 0, s), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
-            else SOLVE_NR(k_fwd_warp, (T, true), (g, 256, 0, s), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
+            if (!trans) SOLVE_NR(k_fwd_warp, (T, false), (g, 256, 0, fan.next()), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
+            else SOLVE_NR(k_fwd_warp, (T, true), (g, 256, 0, fan.next()), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
         }
         if (C.n_cta) {
             dim3 g(C.n_cta);
             const int ldw = C.maxm_cta;
+            const cudaStream_t ls = fan.next();
             size_t sm = dgs + (size_t)kRhsChunk * ldw * sizeof(T);
-            if (!trans) k_fwd_cta<T, false><<<g, 256, sm, s>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, ldw);
-            else k_fwd_cta<T, true><<<g, 256, sm, s>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, ldw);
+            if (!trans) k_fwd_cta<T, false><<<g, 256, sm, ls>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, ldw);
+            else k_fwd_cta<T, true><<<g, 256, sm, ls>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, ldw);
         }
         if (C.n_piv) {
+            const cudaStream_t ls = fan.next();
             if (!trans) {
                 INV_LAUNCH(false, PH_FWD1, C.n_piv, C.off_piv);
                 INV_LAUNCH(false, PH_FWD2, C.n_all, C.off_all);
@@ -2043,6 +2114,7 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
                 INV_LAUNCH(true, PH_FWD2, C.n_all, C.off_all);
             }
         }
+        CUDA_TRY(fan.join());
         prof_end(F, s, slot);
         CUDA_TRY(cudaGetLastError());
     }
@@ -2051,8 +2123,8 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         if (rc != MF_OK) return rc;
     }
     if (scale_d) {
-        int slot = prof_begin(F, s, FAM_OTHER, (16.0 + 8.0 + F->tsize) * n * nrhs, 1.0 * n * nrhs);
-        k_scale_pivots<T><<<(unsigned)((n * nrhs + 255) / 256), 256, 0, s>>>(F->d_pdiag, fac, d_x, n, nrhs);
+        int slot = prof_begin(F, s, FAM_OTHER, (16.0 + 8.0) * n * nrhs, 1.0 * n * nrhs);
+        k_scale_pivots<<<(unsigned)((n * nrhs + 255) / 256), 256, 0, s>>>(F->d_pdv, d_x, n, nrhs);
         prof_end(F, s, slot);
         CUDA_TRY(cudaGetLastError());
     }
@@ -2068,11 +2140,12 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         for (int q = 0; q < kLgLists; q++) nk += C.n_lg[q] > 0;
         int slot = prof_begin(F, s, FAM_BWD, F->bwd_bytes[c] * nrhs, F->bwd_flops[c] * nrhs, nk, -1, MF_TRACE_BWD_CLASS,
                               c, a->cls_ptr[c + 1] - a->cls_ptr[c]);
+        Fan fan(F, s, nk - (C.n_piv > 0));
 #define GRP_BWD(Q, GS)                                                                                             \
         if (C.n_grp[Q]) {                                                                                          \
             dim3 g((C.n_grp[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)));                                             \
-            if (!trans) SOLVE_NR(k_bwd_grp, (T, false, GS), (g, 256, 0, s), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, d_x, n, nrhs)); \
-            else SOLVE_NR(k_bwd_grp, (T, true, GS), (g, 256, 0, s), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, d_x, n, nrhs)); \
+            if (!trans) SOLVE_NR(k_bwd_grp, (T, false, GS), (g, 256, 0, fan.next()), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, d_x, n, nrhs)); \
+            else SOLVE_NR(k_bwd_grp, (T, true, GS), (g, 256, 0, fan.next()), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, d_x, n, nrhs)); \
         }
         GRP_BWD(0, 4)
         GRP_BWD(1, 8)
@@ -2082,8 +2155,8 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
 #define LG_BWD(Q, GS, RS, KMS)                                                                                      \
         if (C.n_lg[Q]) {                                                                                           \
             dim3 g((C.n_lg[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)));                                              \
-            if (!trans) SOLVE_NR(k_bwd_lg, (T, false, GS, RS, KMS), (g, 256, 0, s), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
-            else SOLVE_NR(k_bwd_lg, (T, true, GS, RS, KMS), (g, 256, 0, s), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
+            if (!trans) SOLVE_NR(k_bwd_lg, (T, false, GS, RS, KMS), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
+            else SOLVE_NR(k_bwd_lg, (T, true, GS, RS, KMS), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
         }
         LG_BWD(0, 4, 1, 4)
         LG_BWD(1, 8, 1, 4)
@@ -2102,6 +2175,7 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         LG_BWD(14, 32, 3, 16)
 #undef LG_BWD
         if (C.n_piv) {
+            const cudaStream_t ls = fan.next();
             if (!trans) {
                 INV_LAUNCH(false, PH_BWD1, C.n_piv, C.off_piv);
                 INV_LAUNCH(false, PH_BWD2, C.n_piv, C.off_piv);
@@ -2113,15 +2187,17 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         if (C.n_cta) {
             dim3 g(C.n_cta);
             const int ldw = C.maxm_cta;
+            const cudaStream_t ls = fan.next();
             size_t sm = dgs + (size_t)(8 * 64 * kRhsChunk + kRhsChunk * ldw) * sizeof(T);
-            if (!trans) k_bwd_cta<T, false><<<g, 256, sm, s>>>(fr, L + C.off_cta, 0, fac, F->d_dofs, d_x, n, nrhs, ldw);
-            else k_bwd_cta<T, true><<<g, 256, sm, s>>>(fr, L + C.off_cta, 0, fac, F->d_dofs, d_x, n, nrhs, ldw);
+            if (!trans) k_bwd_cta<T, false><<<g, 256, sm, ls>>>(fr, L + C.off_cta, 0, fac, F->d_dofs, d_x, n, nrhs, ldw);
+            else k_bwd_cta<T, true><<<g, 256, sm, ls>>>(fr, L + C.off_cta, 0, fac, F->d_dofs, d_x, n, nrhs, ldw);
         }
         if (C.n_small) {
             dim3 g((C.n_small + 7) / 8);
-            if (!trans) SOLVE_NR(k_bwd_warp, (T, false), (g, 256, 0, s), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, d_x, n, nrhs));
-            else SOLVE_NR(k_bwd_warp, (T, true), (g, 256, 0, s), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, d_x, n, nrhs));
+            if (!trans) SOLVE_NR(k_bwd_warp, (T, false), (g, 256, 0, fan.next()), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, d_x, n, nrhs));
+            else SOLVE_NR(k_bwd_warp, (T, true), (g, 256, 0, fan.next()), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, d_x, n, nrhs));
         }
+        CUDA_TRY(fan.join());
         prof_end(F, s, slot);
         CUDA_TRY(cudaGetLastError());
     }
@@ -2329,7 +2405,9 @@ static int refine_impl(mf_factors* F, const double* d_values, const double* d_b,
             F->body_bytes[q] = F->acc_bytes[q];
             F->body_flops[q] = F->acc_flops[q];
         }
+        F->fan_off = true;  // the body graph of a conditional node is captured on one stream
         r2 = body(F->s_body);
+        F->fan_off = false;
         if (r2 == MF_OK) {
             prof_begin(F, F->s_body, FAM_OTHER, 0.0, 0.0, 1);
             k_cg_test<<<1, 32, 0, F->s_body>>>(F->d_norms, nrhs, F->d_cgpar, F->d_cgit, 1, h);

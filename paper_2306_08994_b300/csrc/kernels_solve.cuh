@@ -648,7 +648,40 @@ __device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fron
             for (int rr = 0; rr < nr; rr++) v[rr * ldw + i] = (T)__ldcg(x + (int64_t)(rb + rr) * n_dof + d);
         }
         __syncthreads();
-        if (!cb_done) {
+        if (!cb_done && TRANS) {
+            // L^T: pivot row i is column i of L below the pivot block, contiguous in P: one warp per
+            // pivot row, lanes along the column (coalesced), a shuffle tree per row
+            for (int i = warp; i < k; i += 8) {
+                const T* col = P + (int64_t)i * m;
+                T acc[kRhsChunk];
+#pragma unroll
+                for (int rr = 0; rr < kRhsChunk; rr++) acc[rr] = T(0);
+                int j = k + lane;
+                for (; j + 96 < m; j += 128) {
+                    T c[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) c[u] = col[j + 32 * u];
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+#pragma unroll
+                        for (int rr = 0; rr < kRhsChunk; rr++)
+                            if (rr < nr) acc[rr] += c[u] * v[rr * ldw + j + 32 * u];
+                }
+                for (; j < m; j += 32) {
+                    const T c = col[j];
+#pragma unroll
+                    for (int rr = 0; rr < kRhsChunk; rr++)
+                        if (rr < nr) acc[rr] += c * v[rr * ldw + j];
+                }
+#pragma unroll
+                for (int rr = 0; rr < kRhsChunk; rr++) {
+                    T sum = acc[rr];
+                    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                    if (lane == 0 && rr < nr) v[rr * ldw + i] -= sum;
+                }
+            }
+            __syncthreads();
+        } else if (!cb_done) {
             // pivot rows (lane, lane + 32; k < 64) minus their CB part; the 8 warps split the columns
             const int i0 = lane, i1 = lane + 32;
             T a0[kRhsChunk], a1[kRhsChunk];
@@ -684,9 +717,12 @@ __device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fron
             const int pb = max(0, pe - 32), wb = pe - pb;
             {
                 T t[4];
+                // row pb+i, unknown pb+j; the index that runs along memory is the fast one across the
+                // lanes (i for U, j for L^T, whose coefficient of j in row i is L[j][i])
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
-                    const int idx = threadIdx.x + 256 * q, i = idx & 31, j = idx >> 5;  // row pb+i, unknown pb+j
+                    const int idx = threadIdx.x + 256 * q;
+                    const int i = TRANS ? idx >> 5 : idx & 31, j = TRANS ? idx & 31 : idx >> 5;
                     t[q] = T(0);
                     if (i < wb && j < wb) t[q] = (i < j) ? bcoef<T, TRANS>(P, R, m, k, pb + i, pb + j)
                                                          : (i == j ? bdiag<T, TRANS>(P, m, pb + j) : T(0));
@@ -694,7 +730,8 @@ __device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fron
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     const int idx = threadIdx.x + 256 * q;
-                    Dg[(idx & 31) * 33 + (idx >> 5)] = t[q];
+                    const int i = TRANS ? idx >> 5 : idx & 31, j = TRANS ? idx & 31 : idx >> 5;
+                    Dg[i * 33 + j] = t[q];
                 }
             }
             __syncthreads();
@@ -709,7 +746,18 @@ __device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fron
                 if (lane < wb) vr[pb + lane] = val;
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < pb; i += blockDim.x) {
+            if (TRANS) {  // rows above the block: warp per row, lane = unknown (contiguous in L's column)
+                for (int i = warp; i < pb; i += 8) {
+                    const T cf = lane < wb ? bcoef<T, TRANS>(P, R, m, k, i, pb + lane) : T(0);
+#pragma unroll
+                    for (int rr = 0; rr < kRhsChunk; rr++) {
+                        T sum = rr < nr ? cf * v[rr * ldw + pb + min(lane, wb - 1)] : T(0);
+                        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                        if (lane == 0 && rr < nr) v[rr * ldw + i] -= sum;
+                    }
+                }
+            }
+            for (int i = threadIdx.x; i < pb && !TRANS; i += blockDim.x) {
                 T acc[kRhsChunk];
 #pragma unroll
                 for (int rr = 0; rr < kRhsChunk; rr++) acc[rr] = T(0);
@@ -1263,12 +1311,19 @@ __global__ void k_cg_commit(double* __restrict__ cg, int nrhs) {
 // Symmetric factors (A = L D^-1 L^T, D = diag(L)): between the forward sweep
 // with L and the backward sweep with L^T the pivot values are multiplied by
 // their pivots, z = D y.  diag_off[d]: factor-arena offset of dof d's pivot.
+// Symmetric solves, z = D y between the two sweeps.  The pivots are gathered
+// into dof order once per factorization (k_gather_pivots), so the scaling of
+// every solve reads them contiguously.
 template <typename T>
-__global__ void k_scale_pivots(const int64_t* __restrict__ diag_off, const T* __restrict__ fac, double* __restrict__ x,
-                               int64_t n, int nrhs) {
+__global__ void k_gather_pivots(const int64_t* __restrict__ diag_off, const T* __restrict__ fac, double* __restrict__ pdv,
+                                int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) pdv[i] = (double)fac[diag_off[i]];
+}
+__global__ void k_scale_pivots(const double* __restrict__ pdv, double* __restrict__ x, int64_t n, int nrhs) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * nrhs) return;
-    x[i] *= (double)fac[diag_off[i % n]];
+    x[i] *= pdv[nrhs == 1 ? i : i % n];
 }
 
 __global__ void k_axpy(double* __restrict__ x, const double* __restrict__ d, int64_t n) {
