@@ -1647,11 +1647,14 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
         if (F->prec == MF_F64) {
             e = cudaFuncSetAttribute(k_panel_diag_blk<double, kPanelNB64, double, true>, kA, s64);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_diag_blk<double, kPanelNB64, double, false>, kA, s64);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_diag_blk<double, kPanelNB64, double, true, true>, kA, s64);
         } else {
             e = cudaFuncSetAttribute(k_panel_diag_blk<float, kPanelNB32, float, true>, kA, s32);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_diag_blk<float, kPanelNB32, float, false>, kA, s32);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel_diag_blk<float, kPanelNB32, float, true, true>, kA, s32);
             e2 = cudaFuncSetAttribute(k_panel_diag_blk<float, kPanelNB32, double, true>, kA, sw);
             if (e2 == cudaSuccess) e2 = cudaFuncSetAttribute(k_panel_diag_blk<float, kPanelNB32, double, false>, kA, sw);
+            if (e2 == cudaSuccess) e2 = cudaFuncSetAttribute(k_panel_diag_blk<float, kPanelNB32, double, true, true>, kA, sw);
         }
         if (e != cudaSuccess || e2 != cudaSuccess) {
             (void)cudaGetLastError();
@@ -1768,7 +1771,10 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
                 const DiagTask* dt = F->d_panel + L.off;
                 if constexpr (sizeof(T) == 4) {
                     if (L.wide) {
-                        if (F->pinv)
+                        if (F->pinv && F->sym)
+                            k_panel_diag_blk<T, NB, double, true, true><<<L.count, 256, panel_diag_dyn_smem<T, NB, double>(), s>>>(
+                                F->d_fronts, dt, fac, (T*)F->d_pnl, (T*)F->d_inv, F->d_famax, F->tol_rel, F->d_status);
+                        else if (F->pinv)
                             k_panel_diag_blk<T, NB, double, true><<<L.count, 256, panel_diag_dyn_smem<T, NB, double>(), s>>>(
                                 F->d_fronts, dt, fac, (T*)F->d_pnl, (T*)F->d_inv, F->d_famax, F->tol_rel, F->d_status);
                         else
@@ -1777,7 +1783,10 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
                         break;
                     }
                 }
-                if (F->pinv)
+                if (F->pinv && F->sym)
+                    k_panel_diag_blk<T, NB, T, true, true><<<L.count, 256, panel_diag_dyn_smem<T, NB>(), s>>>(
+                        F->d_fronts, dt, fac, (T*)F->d_pnl, (T*)F->d_inv, F->d_famax, F->tol_rel, F->d_status);
+                else if (F->pinv)
                     k_panel_diag_blk<T, NB, T, true><<<L.count, 256, panel_diag_dyn_smem<T, NB>(), s>>>(
                         F->d_fronts, dt, fac, (T*)F->d_pnl, (T*)F->d_inv, F->d_famax, F->tol_rel, F->d_status);
                 else

@@ -627,8 +627,10 @@ __device__ __forceinline__ void pivot_strip_publish(const C (&Ft)[RPT][RPT], con
 // C is the arithmetic of the block (T by default).  With T = float and
 // C = double the block is factored and inverted in FP64 from the FP32 front
 // and rounded once on the way out: the FP64 pivot blocks of the root
-// separator fronts on the FP32-front path.
-template <typename T, int NB, typename C = T, bool INV = true>
+// separator fronts on the FP32-front path.  SYMB (symmetric fronts): for a
+// symmetric block U_D = diag(L_D)^-1 L_D^T, so U_D^-1 = L_D^-T diag(L_D) is
+// formed from L_D^-1 at the end instead of being carried through the steps.
+template <typename T, int NB, typename C = T, bool INV = true, bool SYMB = false>
 __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_diag_blk(const FrontDev* __restrict__ fronts,
                                                         const DiagTask* __restrict__ tasks, T* __restrict__ fac,
                                                         T* __restrict__ slots, T* __restrict__ inv,
@@ -749,7 +751,7 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
 #pragma unroll
                 for (int r = 0; r < RPT; r++) {
                     colF[buf][c][i0 + r] = Ft[r][c];
-                    if constexpr (INV) colY[buf][c][i0 + r] = Yt[r][c];
+                    if constexpr (INV && !SYMB) colY[buf][c][i0 + r] = Yt[r][c];
                 }
         }
         if (ti == blk) {
@@ -859,7 +861,7 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
             }
             // Y: the block's columns through U_bb^-1, then the columns to the right
 #pragma unroll
-            for (int r = 0; r < RPT; r++) {
+            for (int r = 0; r < RPT && !SYMB; r++) {
                 C yf[BP];
 #pragma unroll
                 for (int q = 0; q < BP; q++) {
@@ -886,9 +888,14 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
 #pragma unroll
         for (int c = 0; c < RPT; c++) {
             D[i0 + r][j0 + c] = Ft[r][c];
-            if constexpr (INV) Z[i0 + r][j0 + c] = (i0 + r >= j0 + c) ? Xt[r][c] : Yt[r][c];
+            if constexpr (INV) Z[i0 + r][j0 + c] = (i0 + r >= j0 + c) ? Xt[r][c] : (SYMB ? C(0) : Yt[r][c]);
         }
     __syncthreads();
+    if constexpr (INV && SYMB) {  // U_D^-1[i, j] = L_D^-1[j, i] L_D[j, j] above the diagonal
+        for (int j = warp; j < NB; j += 8)
+            for (int i = lane; i < j; i += 32) Z[i][j] = Z[j][i] * D[j][j];
+        __syncthreads();
+    }
     for (int j = warp; j < w; j += 8)
         for (int i = lane; i < w; i += 32) P[(kb + i) + (int64_t)(kb + j) * m] = (T)D[i][j];
     if constexpr (!INV) return;  // the panel is finished by triangular solves (k_panel_trsm)
