@@ -425,6 +425,8 @@ FP32_CASES = {
     "q3_16_hetero": (lambda: F.diffusion_2d(16, 3, seed=41), {"small_front_max": 48}),
     "q3_24_large_path": (lambda: F.diffusion_2d(24, 3, seed=42), {"small_front_max": 16, "super_panel": 64}),
     "q1_3d_8": (lambda: F.diffusion_3d_q1(8, seed=43), {"small_front_max": 24}),
+    # larger fronts: contribution blocks of up to 361 rows, pivot blocks of up to 289
+    "q3_96_large_fronts": (lambda: F.diffusion_2d(96, 3, seed=44), {"small_front_max": 16, "super_panel": 64}),
 }
 
 
@@ -449,7 +451,24 @@ def test_fp32_family_factors_match_oracle_front_by_front(case, prec):
     f.factor(vals)
     st = f.status()
     assert st["rc"] == 0 and st["n_perturbed"] == 0
-    s = _oracle(pr)
+    _check_fp32_family_factors(f, _oracle(pr), prec, case)
+
+
+@pytest.mark.parametrize("case", ["q3_96_large_fronts", "q3_24_large_path"])
+def test_symmetric_mode_fp32_factors_match_oracle_front_by_front(case):
+    """Option symmetric with FP32 fronts and SIMT products (the Schur updates only on and below
+    the diagonal, then mirrored): the exported L and U against the
+    oracle's FP64 LU factors front by front, within the FP32 bound of the general test above."""
+    mk, opt = FP32_CASES[case]
+    pr = mk()
+    a, f, vals = _setup(pr, "f32", symmetric=1, **opt)
+    f.factor(vals)
+    st = f.status()
+    assert st["rc"] == 0 and st["n_perturbed"] == 0
+    _check_fp32_family_factors(f, _oracle(pr), "f32", case)
+
+
+def _check_fp32_family_factors(f, s, prec, case):
     ksub = np.asarray(s.k, dtype=np.int64).copy()
     for v in range(s.n_front):  # postorder: children before parents
         if s.parent[v] >= 0:
