@@ -319,6 +319,7 @@ struct mf_factors {
     double* d_cgpar = nullptr;
     int* d_cgit = nullptr;
     cudaStream_t s_body = nullptr;
+    cudaStream_t s_aux = nullptr;   // captures the solves that loop bodies take as child-graph nodes
     bool loop_failed = false;  // a loop graph could not be built here: iterate from the host
     int loop_first_inc = 0;    // 1 when the loop graph's first step counts as an iteration (CG)
     bool colabs_valid = false;
@@ -375,6 +376,16 @@ struct mf_factors {
     double body_bytes[MF_PROFILE_FAMILIES] = {};
     double body_flops[MF_PROFILE_FAMILIES] = {};
     int64_t body_launch[MF_PROFILE_FAMILIES] = {};
+    // solves of F->d_d captured on their own (class kernels side by side) before a loop graph is
+    // captured, entered into the loop body as one child-graph node, with their launch accounting
+    struct BodySolve {
+        int nrhs;
+        bool trans;
+        cudaGraph_t graph;
+        double bytes[MF_PROFILE_FAMILIES], flops[MF_PROFILE_FAMILIES];
+        int64_t launches[MF_PROFILE_FAMILIES];
+    };
+    std::vector<BodySolve> body_solves;
 };
 
 enum Family { FAM_FUSED = 0, FAM_ASM = 1, FAM_PANEL = 2, FAM_TRAIL = 3, FAM_SCHUR = 4, FAM_FWD = 5, FAM_BWD = 6,
@@ -414,6 +425,7 @@ static void free_factors(mf_factors* f) {
     if (f->join_ev) cudaEventDestroy(f->join_ev);
     if (f->s1) cudaStreamDestroy(f->s1);
     if (f->s_body) cudaStreamDestroy(f->s_body);
+    if (f->s_aux) cudaStreamDestroy(f->s_aux);
     if (f->s1_in) cudaEventDestroy(f->s1_in);
     if (f->s1_out) cudaEventDestroy(f->s1_out);
     if (f->s2) cudaStreamDestroy(f->s2);
@@ -426,6 +438,7 @@ static void free_factors(mf_factors* f) {
     for (cudaEvent_t e : f->sync_ev)
         if (e) cudaEventDestroy(e);
     for (auto& g : f->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto& b : f->body_solves) cudaGraphDestroy(b.graph);
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     void* ptrs[] = {f->d_fronts, f->d_dofs, f->d_maps, f->d_vsrc, f->d_en, f->d_node_ptr, f->d_node_inc, f->d_fac, f->d_cb,
                     f->d_vec, f->d_flist, f->d_frec, f->d_fwoff, f->d_fws, f->d_fxs, f->d_pdiag, f->d_pdv, f->d_symt, f->d_trsm, f->d_gtcd, f->d_cgp, f->d_cgs, f->d_zero, f->d_cg, f->d_cgpar, f->d_cgit, f->d_slist, f->d_srec, f->d_rows, f->d_invt, f->d_inv, f->d_scr, f->d_ys, f->d_asm, f->d_panel, f->d_pnl, f->d_gemm, f->d_gtc, f->d_tcpack, f->d_tcjob, f->d_pk, f->d_pk2, f->d_sweep_f, f->d_sweep_b, f->d_bar, f->d_sub_tasks, f->d_sub_ecb, f->d_sub_euv, f->d_subs_tasks, f->d_subs_euv, f->d_famax, f->d_status,
@@ -1547,7 +1560,8 @@ extern "C" int mf_factors_create(const mf_analysis* a, const mf_options* opt, mf
     TRY(dev_alloc(&F->d_norms, (size_t)6 * F->max_nrhs));
     TRY(dev_alloc(&F->d_cgpar, (size_t)2));
     TRY(dev_alloc(&F->d_cgit, (size_t)1));
-    if (cudaStreamCreateWithFlags(&F->s_body, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&F->s_body, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&F->s_aux, cudaStreamNonBlocking) != cudaSuccess) {
         free_factors(F);
         return MF_ECUDA;
     }
@@ -2229,10 +2243,71 @@ static int solve_common(mf_factors* F, double* d_rhs, int nrhs, bool trans, mf_s
     if (!F->factored) return MF_EINVAL;
     if (nrhs > F->max_nrhs) return MF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
+    if (F->fan_off && d_rhs == F->d_d) {
+        // s is capturing the body graph of a conditional node: a solve captured beforehand on its
+        // own (prepare_body_solve) enters it as one child-graph node, its class kernels side by side
+        for (const auto& b : F->body_solves) {
+            if (b.nrhs != nrhs || b.trans != trans) continue;
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t g = nullptr;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t nd = 0;
+            cudaGraphNode_t node = nullptr;
+            CUDA_TRY(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+            if (cs != cudaStreamCaptureStatusActive) return MF_EINVAL;
+            CUDA_TRY(cudaGraphAddChildGraphNode(&node, g, deps, nd, b.graph));
+            CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+            for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {
+                F->acc_launch[q] += b.launches[q];
+                F->acc_bytes[q] += b.bytes[q];
+                F->acc_flops[q] += b.flops[q];
+            }
+            return MF_OK;
+        }
+    }
     // symmetric factors: A = A^T = L D^-1 L^T, the same sweeps for the solve and the adjoint solve
     const bool tf = F->sym ? false : trans, tb = F->sym ? true : trans;
     return F->prec == MF_F64 ? run_solve<double>(F, d_rhs, nrhs, tf, s, tb, F->sym)
                              : run_solve<float>(F, d_rhs, nrhs, tf, s, tb, F->sym);
+}
+
+// Capture (not run) the solve of F->d_d on the auxiliary stream, for the loop bodies; nothing is
+// enqueued and the launch accounting is left as it was.  Without it the bodies solve on one stream.
+static void prepare_body_solve(mf_factors* F, int nrhs, bool trans) {
+    for (const auto& b : F->body_solves)
+        if (b.nrhs == nrhs && b.trans == trans) return;
+    mf_factors::BodySolve b{};
+    b.nrhs = nrhs;
+    b.trans = trans;
+    double by[MF_PROFILE_FAMILIES], fl[MF_PROFILE_FAMILIES];
+    int64_t ln[MF_PROFILE_FAMILIES];
+    for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {
+        by[q] = F->acc_bytes[q];
+        fl[q] = F->acc_flops[q];
+        ln[q] = F->acc_launch[q];
+    }
+    if (cudaStreamBeginCapture(F->s_aux, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    const int rc = solve_common(F, F->d_d, nrhs, trans, (mf_stream_t)F->s_aux);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(F->s_aux, &g);
+    for (int q = 0; q < MF_PROFILE_FAMILIES; q++) {
+        b.bytes[q] = F->acc_bytes[q] - by[q];
+        b.flops[q] = F->acc_flops[q] - fl[q];
+        b.launches[q] = F->acc_launch[q] - ln[q];
+        F->acc_bytes[q] = by[q];
+        F->acc_flops[q] = fl[q];
+        F->acc_launch[q] = ln[q];
+    }
+    if (rc != MF_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        (void)cudaGetLastError();
+        return;
+    }
+    b.graph = g;
+    F->body_solves.push_back(b);
 }
 
 extern "C" int mf_solve(mf_factors* F, double* d_rhs, int nrhs, mf_stream_t stream) {
@@ -2454,6 +2529,7 @@ static int refine_impl(mf_factors* F, const double* d_values, const double* d_b,
     if (device_loop && !(F->sym && F->opt.refine_cg && !trans)) {
         // stationary refinement: the first solve, then corrections until the stop test holds
         F->loop_first_inc = 0;
+        prepare_body_solve(F, nrhs, trans);
         auto st_loop = [&](cudaStream_t st) -> int { return capture_loop(st, start, step, 0); };
         if ((rc = run_loop_graph(trans ? 12 : 11, st_loop)) == MF_OK) {
             if (info) {
@@ -2514,6 +2590,7 @@ static int refine_impl(mf_factors* F, const double* d_values, const double* d_b,
         auto cg_loop = [&](cudaStream_t st) -> int { return capture_loop(st, cg_step(true), cg_step(false), 1); };
         auto run_loop = [&]() -> int {
             F->loop_first_inc = 1;
+            prepare_body_solve(F, nrhs, false);
             return run_loop_graph(10, cg_loop);
         };
         bool loop_built = device_loop;
