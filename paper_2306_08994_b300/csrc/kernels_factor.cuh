@@ -896,17 +896,33 @@ __global__ void __launch_bounds__(256, sizeof(C) == sizeof(T) ? 2 : 1) k_panel_d
             for (int i = lane; i < j; i += 32) Z[i][j] = Z[j][i] * D[j][j];
         __syncthreads();
     }
-    for (int j = warp; j < w; j += 8)
-        for (int i = lane; i < w; i += 32) P[(kb + i) + (int64_t)(kb + j) * m] = (T)D[i][j];
-    if constexpr (!INV) return;  // the panel is finished by triangular solves (k_panel_trsm)
+    // one pass writes the block to P and (INV) its inverses to the panel slot and Q (ld k): every
+    // element of a thread (column warp + 8u, rows lane + 32v) is read from shared memory first, then
+    // the stores follow
+    constexpr int UJ = NB / 8, VI = (NB + 31) / 32;
+    T pv[UJ][VI], zv[UJ][VI];
+#pragma unroll
+    for (int u = 0; u < UJ; u++)
+#pragma unroll
+        for (int v = 0; v < VI; v++) {
+            const int j = warp + 8 * u, i = lane + 32 * v;
+            pv[u][v] = i < NB ? (T)D[i][j] : T(0);
+            if constexpr (INV) zv[u][v] = i < NB ? (T)Z[i][j] : T(0);
+        }
     T* Zg = slots + t.slot;
-    for (int j = warp; j < w; j += 8)
-        for (int i = lane; i < w; i += 32) Zg[i + j * 64] = (T)Z[i][j];
-    if (t.q_off >= 0) {  // the same block of the solve's pivot-block inverse Q (ld k)
-        T* Q = inv + t.q_off;
-        for (int j = warp; j < w; j += 8)
-            for (int i = lane; i < w; i += 32) Q[(kb + i) + (int64_t)(kb + j) * fr.k] = (T)Z[i][j];
-    }
+    T* Q = inv + (t.q_off >= 0 ? t.q_off : 0);  // the same block of the solve's pivot-block inverse
+#pragma unroll
+    for (int u = 0; u < UJ; u++)
+#pragma unroll
+        for (int v = 0; v < VI; v++) {
+            const int j = warp + 8 * u, i = lane + 32 * v;
+            if (i >= w || j >= w) continue;
+            P[(kb + i) + (int64_t)(kb + j) * m] = pv[u][v];
+            if constexpr (INV) {  // INV = false: the panel is finished by triangular solves (k_panel_trsm)
+                Zg[i + j * 64] = zv[u][v];
+                if (t.q_off >= 0) Q[(kb + i) + (int64_t)(kb + j) * fr.k] = zv[u][v];
+            }
+        }
 }
 
 // ---------------------------------------------------------------------------
