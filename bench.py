@@ -99,7 +99,7 @@ FP32_SIMT_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x 2 f
 # `bench.py --trace-once`).  The roofline's `traffic` is this ratio times the algorithmic bytes per launch of
 # the timed workload, i.e. the capture scaled by the units a launch processes.  Valid while the kernel is
 # unchanged.
-MEASURED_TRAFFIC_RATIO = {"gemm": 0.748, "panel_diag": 0.714, "fused_grp": 0.658, "gemm_tc": 1.202, "tc_pack": 0.308}
+MEASURED_TRAFFIC_RATIO = {"gemm": 0.748, "panel_diag": 0.615, "fused_grp": 0.658, "gemm_tc": 1.202, "tc_pack": 0.308}
 FP64_DFMA_TFLOPS = 1.201  # measured DFMA throughput of this B300 (register-resident FMA loop, all SMs)
 
 
