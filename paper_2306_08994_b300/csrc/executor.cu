@@ -557,6 +557,13 @@ static int build_plan(mf_factors* F) {
     int cur_stream = 0;  // stream the launches being planned go to
     // FP32-family fronts in the top root_f64 classes factor their pivot blocks in FP64
     auto wide_pdiag = [&](int c) { return F->prec != MF_F64 && F->opt.root_f64 > 0 && c >= a->n_cls - F->opt.root_f64; };
+    // symmetric fronts: the front's parent is assembled by the large-front kernel, which reads the
+    // children's contribution blocks from their lower triangles only
+    auto cb_read_lower = [&](int32_t f) {
+        const int32_t pa = a->parent[f];
+        return pa >= 0 && a->fronts[pa].m > F->small_max && a->fronts[pa].cls >= F->sub.h &&
+               a->fronts[pa].cls >= F->foata_cls;
+    };
     auto push = [&](Launch L, int fam, double bytes, double flops) {
         L.stream = cur_stream;
         F->plan.push_back(L);
@@ -953,17 +960,24 @@ static int build_plan(mf_factors* F) {
                     r.cS[q] = ch.S_off;
                     r.cn[q] = ch.m - ch.k;
                 }
+                // symmetric fronts: no tile whose entries all lie in R (overwritten by the transposing
+                // copy of U12) or, when the parent reads only the lower triangle of this front's
+                // contribution block, strictly above its diagonal
+                const bool lower_cb = F->sym && cb_read_lower(f);
                 for (int j0 = 0; j0 < m; j0 += 64)
                     for (int i0 = 0; i0 < m; i0 += 64) {
+                        if (F->sym && j0 >= fr.k && i0 + 63 < j0 && (lower_cb || i0 + 64 <= fr.k)) continue;
                         r.i0 = i0;
                         r.j0 = j0;
                         asmt.push_back(r);
                     }
                 for (int q = 0; q < fr.nchild; q++) {
                     const FrontDev& ch = a->fronts[fr.child[q]];
-                    by += T * (double)(ch.m - ch.k) * (ch.m - ch.k);
+                    const double n = ch.m - ch.k;
+                    by += T * (F->sym ? n * (n + 1) / 2 : n * n);
                 }
-                by += T * (double)m * m;
+                const double nc = m - fr.k;
+                by += T * (F->sym ? (double)m * fr.k + (lower_cb ? nc * (nc + 1) / 2 : nc * nc) : (double)m * m);
             }
             push({K_ASM, c, (int)(asmt.size() - off), 0, off}, FAM_ASM, by, 0.0);
         }
@@ -1173,6 +1187,7 @@ static int build_plan(mf_factors* F) {
                 const FrontDev& fr = a->fronts[f];
                 const int nc = fr.m - fr.k;
                 if (nc <= 1 || fr.k <= 0) continue;
+                if (cb_read_lower(f)) continue;  // its parent reads only the lower triangle
                 const bool on_tc = use_tc(nc, nc, fr.k);
                 for (int j0 = 0; j0 < nc; j0 += 64)
                     for (int i0 = j0 + 64; i0 < nc; i0 += 64) {
@@ -1778,7 +1793,8 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
                 break;
             }
             case K_ASM:
-                k_assemble_large<T><<<L.count, 256, 0, s>>>(F->d_asm + L.off, F->d_maps, fac, cb, F->d_famax);
+                if (F->sym) k_assemble_large<T, true><<<L.count, 256, 0, s>>>(F->d_asm + L.off, F->d_maps, fac, cb, F->d_famax);
+                else k_assemble_large<T><<<L.count, 256, 0, s>>>(F->d_asm + L.off, F->d_maps, fac, cb, F->d_famax);
                 break;
             case K_PDIAG: {
                 constexpr int NB = sizeof(T) == 8 ? kPanelNB64 : kPanelNB32;

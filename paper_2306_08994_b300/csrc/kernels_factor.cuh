@@ -409,7 +409,11 @@ struct AsmRec {
     int32_t i0, j0, front, pad;
 };
 
-template <typename T>
+// SYM (symmetric fronts): the children's contribution blocks are read from their lower
+// triangles only (entry (a, b) of a child is taken at (max, min)), so the strictly upper part of
+// a child's block is never needed; the plan leaves out the tiles this front's own R and strictly
+// upper contribution block (overwritten later by the transposing copy of U12 and never read).
+template <typename T, bool SYM = false>
 __global__ void __launch_bounds__(256) k_assemble_large(const AsmRec* __restrict__ recs, const int32_t* __restrict__ maps,
                                                         T* __restrict__ fac, T* __restrict__ cbs,
                                                         unsigned int* __restrict__ famax) {
@@ -444,8 +448,14 @@ __global__ void __launch_bounds__(256) k_assemble_large(const AsmRec* __restrict
 #pragma unroll
         for (int q = 0; q < 2; q++) {
             T x = T(0);
-            if (r0[q] >= 0 && cj0[u] >= 0) x += S0[r0[q] + (int64_t)cj0[u] * n0];
-            if (r1[q] >= 0 && cj1[u] >= 0) x += S1[r1[q] + (int64_t)cj1[u] * n1];
+            if (r0[q] >= 0 && cj0[u] >= 0) {
+                const int a0 = SYM ? max(r0[q], cj0[u]) : r0[q], b0 = SYM ? min(r0[q], cj0[u]) : cj0[u];
+                x += S0[a0 + (int64_t)b0 * n0];
+            }
+            if (r1[q] >= 0 && cj1[u] >= 0) {
+                const int a1 = SYM ? max(r1[q], cj1[u]) : r1[q], b1 = SYM ? min(r1[q], cj1[u]) : cj1[u];
+                x += S1[a1 + (int64_t)b1 * n1];
+            }
             v[u][q] = x;
         }
     T amax = T(0);
