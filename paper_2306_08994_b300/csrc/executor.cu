@@ -597,8 +597,11 @@ static int build_plan(mf_factors* F) {
     std::vector<TcC> tcc;
     int64_t tc_hi = 0;
     size_t tc_p0 = 0;
+    // a product of depth K < 128 (the trailing update of one 64-pivot super-panel) streams C once for
+    // few MMAs per output: it stays on the SIMT tiles unless the threshold on M, N is set below 128
     auto use_tc = [&](int M, int N, int K) {
-        return (F->prec == MF_TF32 || F->prec == MF_TF32_BF16) && std::min(M, N) >= F->tc_min && K >= 16;
+        return (F->prec == MF_TF32 || F->prec == MF_TF32_BF16) && std::min(M, N) >= F->tc_min && K >= 16 &&
+               K >= std::min(128, F->tc_min);
     };
     // per product mode (tc::Mode): packing bytes, product bytes and flops of the pending products
     double tc_pbm[3] = {0, 0, 0}, tc_gbm[3] = {0, 0, 0}, tc_gfm[3] = {0, 0, 0};
