@@ -2425,7 +2425,7 @@ static int refine_impl(mf_factors* F, const double* d_values, const double* d_b,
         dim3 gp(F->norm_blocks, nrhs);
         int sl = prof_begin(F, st, FAM_RESID, 24.0 * n * nrhs, 5.0 * n * nrhs, 2);
         k_norms_partial<<<gp, 256, 0, st>>>(F->d_r, d_x, d_b, anorm_rows, n, F->d_part);
-        k_norms_final<<<nrhs, 32, 0, st>>>(F->d_part, F->norm_blocks, F->d_norms);
+        k_norms_final<<<nrhs, 256, 0, st>>>(F->d_part, F->norm_blocks, F->d_norms);
         prof_end(F, st, sl);
         CUDA_TRY(cudaGetLastError());
         return MF_OK;
@@ -2581,7 +2581,7 @@ static int refine_impl(mf_factors* F, const double* d_values, const double* d_b,
                 if ((r2 = solve_common(F, F->d_d, nrhs, false, (mf_stream_t)st))) return r2;
                 sl = prof_begin(F, st, FAM_OTHER, 16.0 * n * nrhs, 2.0 * n * nrhs, 2);
                 k_dot_partial<<<dim3(nb, nrhs), 256, 0, st>>>(F->d_r, F->d_d, n, F->d_part);
-                k_dot_final<<<nrhs, 32, 0, st>>>(F->d_part, nb, F->d_cg, first ? 0 : 2);
+                k_dot_final<<<nrhs, 256, 0, st>>>(F->d_part, nb, F->d_cg, first ? 0 : 2);
                 prof_end(F, st, sl);
                 sl = prof_begin(F, st, FAM_OTHER, 24.0 * n * nrhs, 2.0 * n * nrhs, first ? 1 : 2);
                 k_cg_p<<<gv, 256, 0, st>>>(F->d_cgp, F->d_d, F->d_cg, n, first ? 1 : 0);
@@ -2591,13 +2591,13 @@ static int refine_impl(mf_factors* F, const double* d_values, const double* d_b,
                 if ((r2 = residual_into(F, d_values, F->d_cgp, F->d_zero, F->d_cgs, nrhs, st, false))) return r2;
                 sl = prof_begin(F, st, FAM_OTHER, 48.0 * n * nrhs, 6.0 * n * nrhs, 3);
                 k_dot_partial<<<dim3(nb, nrhs), 256, 0, st>>>(F->d_cgp, F->d_cgs, n, F->d_part);
-                k_dot_final<<<nrhs, 32, 0, st>>>(F->d_part, nb, F->d_cg, 1);
+                k_dot_final<<<nrhs, 256, 0, st>>>(F->d_part, nb, F->d_cg, 1);
                 k_cg_xr<<<gv, 256, 0, st>>>(d_x, F->d_r, F->d_cgp, F->d_cgs, F->d_cg, n);
                 prof_end(F, st, sl);
                 CUDA_TRY(cudaGetLastError());
                 sl = prof_begin(F, st, FAM_RESID, 24.0 * n * nrhs, 5.0 * n * nrhs, 2);
                 k_norms_partial<<<dim3(nb, nrhs), 256, 0, st>>>(F->d_r, d_x, d_b, anorm_rows, n, F->d_part);
-                k_norms_final<<<nrhs, 32, 0, st>>>(F->d_part, nb, F->d_norms);
+                k_norms_final<<<nrhs, 256, 0, st>>>(F->d_part, nb, F->d_norms);
                 prof_end(F, st, sl);
                 CUDA_TRY(cudaGetLastError());
                 return MF_OK;

@@ -1120,96 +1120,126 @@ __global__ void k_gather_residual(const int64_t* __restrict__ node_ptr, const in
     out[d + (int64_t)r * n_dof] = mode == 0 ? b[d + (int64_t)r * n_dof] - acc : acc;
 }
 
-// max that keeps a NaN once it has seen one (fmax would drop it)
-__device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
+// The maxima of |r|, |x|, |b| and of the row sums are taken on the bit patterns: with the sign
+// bit cleared, IEEE doubles order like unsigned integers, and a NaN (exponent all ones, mantissa
+// nonzero) lies above every number, so the maximum keeps it (an FP64 max would drop it, and FP64
+// compares would run on the GPU's small FP64 pipe).
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ double bits_double(unsigned long long u) { return __longlong_as_double((long long)u); }
 
 // Per right-hand side norms: out[r*6 + {0..5}] = ||r||_inf, ||x||_inf, ||b||_inf,
 // ||r||_2^2, ||b||_2^2, ||Arow||_inf (the last one only for r == 0, from rowabs).
-// Two stages for a deterministic sum: block partials, then one block.
-__global__ void k_norms_partial(const double* __restrict__ rv, const double* __restrict__ xv, const double* __restrict__ bv,
-                                const double* __restrict__ rowabs, int64_t n, double* __restrict__ part) {
+// Two stages for a deterministic sum: block partials, then one block.  Each thread loads all of
+// its elements (kNormsPer per array, strided by the grid) before it reduces them.
+constexpr int kNormsPer = 8;
+__global__ void __launch_bounds__(256) k_norms_partial(const double* __restrict__ rv, const double* __restrict__ xv,
+                                                       const double* __restrict__ bv, const double* __restrict__ rowabs,
+                                                       int64_t n, double* __restrict__ part) {
     const int r = blockIdx.y;
     const double* rr = rv + (int64_t)r * n;
     const double* xx = xv + (int64_t)r * n;
     const double* bb = bv + (int64_t)r * n;
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
+    unsigned long long m0 = 0, m1 = 0, m2 = 0, m5 = 0;
+    double a3 = 0, a4 = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    auto take = [&](int64_t i) {
-        const double ri = rr[i], xi = xx[i], bi = bb[i];
-        a0 = nanmax(a0, fabs(ri));
-        a1 = nanmax(a1, fabs(xi));
-        a2 = nanmax(a2, fabs(bi));
-        a3 += ri * ri;
-        a4 += bi * bi;
-        if (rowabs) a5 = nanmax(a5, rowabs[i]);
-    };
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (; i + 3 * stride < n; i += 4 * stride) {  // four elements' loads in flight per thread
-        double rq[4], xq[4], bq[4], aq[4];
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += kNormsPer * stride) {
+        double rq[kNormsPer], xq[kNormsPer], bq[kNormsPer], aq[kNormsPer];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            rq[u] = rr[i + u * stride];
-            xq[u] = xx[i + u * stride];
-            bq[u] = bb[i + u * stride];
-            aq[u] = rowabs ? rowabs[i + u * stride] : 0.0;
+        for (int u = 0; u < kNormsPer; u++) {
+            const int64_t i = base + u * stride;
+            const bool ok = i < n;
+            rq[u] = ok ? rr[i] : 0.0;
+            xq[u] = ok ? xx[i] : 0.0;
+            bq[u] = ok ? bb[i] : 0.0;
+            aq[u] = (ok && rowabs) ? rowabs[i] : 0.0;
         }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            a0 = nanmax(a0, fabs(rq[u]));
-            a1 = nanmax(a1, fabs(xq[u]));
-            a2 = nanmax(a2, fabs(bq[u]));
-            a3 += rq[u] * rq[u];
-            a4 += bq[u] * bq[u];
-            a5 = nanmax(a5, aq[u]);
+        for (int u = 0; u < kNormsPer; u++) {
+            m0 = max(m0, abs_bits(rq[u]));
+            m1 = max(m1, abs_bits(xq[u]));
+            m2 = max(m2, abs_bits(bq[u]));
+            m5 = max(m5, abs_bits(aq[u]));
+            a3 = fma(rq[u], rq[u], a3);
+            a4 = fma(bq[u], bq[u], a4);
         }
     }
-    for (; i < n; i += stride) take(i);
-    __shared__ double sh[6][32];
+    __shared__ unsigned long long shm[4][8];
+    __shared__ double shs[2][8];
     for (int o = 16; o > 0; o >>= 1) {
-        a0 = nanmax(a0, __shfl_xor_sync(0xffffffffu, a0, o));
-        a1 = nanmax(a1, __shfl_xor_sync(0xffffffffu, a1, o));
-        a2 = nanmax(a2, __shfl_xor_sync(0xffffffffu, a2, o));
+        m0 = max(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        m1 = max(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = max(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+        m5 = max(m5, __shfl_xor_sync(0xffffffffu, m5, o));
         a3 += __shfl_xor_sync(0xffffffffu, a3, o);
         a4 += __shfl_xor_sync(0xffffffffu, a4, o);
-        a5 = nanmax(a5, __shfl_xor_sync(0xffffffffu, a5, o));
     }
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) {
-        sh[0][w] = a0; sh[1][w] = a1; sh[2][w] = a2; sh[3][w] = a3; sh[4][w] = a4; sh[5][w] = a5;
+        shm[0][w] = m0; shm[1][w] = m1; shm[2][w] = m2; shm[3][w] = m5;
+        shs[0][w] = a3; shs[1][w] = a4;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double o0 = 0, o1 = 0, o2 = 0, o3 = 0, o4 = 0, o5 = 0;
+        unsigned long long o0 = 0, o1 = 0, o2 = 0, o5 = 0;
+        double o3 = 0, o4 = 0;
         for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
-            o0 = nanmax(o0, sh[0][i]); o1 = nanmax(o1, sh[1][i]); o2 = nanmax(o2, sh[2][i]);
-            o3 += sh[3][i]; o4 += sh[4][i]; o5 = nanmax(o5, sh[5][i]);
+            o0 = max(o0, shm[0][i]); o1 = max(o1, shm[1][i]); o2 = max(o2, shm[2][i]); o5 = max(o5, shm[3][i]);
+            o3 += shs[0][i]; o4 += shs[1][i];
         }
-        double* p = part + ((int64_t)r * gridDim.x + blockIdx.x) * 6;
-        p[0] = o0; p[1] = o1; p[2] = o2; p[3] = o3; p[4] = o4; p[5] = o5;
+        double* q = part + ((int64_t)r * gridDim.x + blockIdx.x) * 6;
+        q[0] = bits_double(o0); q[1] = bits_double(o1); q[2] = bits_double(o2);
+        q[3] = o3; q[4] = o4; q[5] = bits_double(o5);
     }
 }
 
-__global__ void k_norms_final(const double* __restrict__ part, int nblk, double* __restrict__ out) {
-    // one warp per right-hand side; fixed strided order, then a fixed shuffle tree
-    const int r = blockIdx.x, lane = threadIdx.x & 31;
-    if (threadIdx.x >= 32) return;
-    double o0 = 0, o1 = 0, o2 = 0, o3 = 0, o4 = 0, o5 = 0;
-    for (int i = lane; i < nblk; i += 32) {
-        const double* p = part + ((int64_t)r * nblk + i) * 6;
-        o0 = nanmax(o0, p[0]); o1 = nanmax(o1, p[1]); o2 = nanmax(o2, p[2]);
-        o3 += p[3]; o4 += p[4]; o5 = nanmax(o5, p[5]);
+// one block of 256 threads per right-hand side: every partial of a thread loaded first, then a
+// fixed-order reduction (strided per thread, a shuffle tree per warp, the warps in order)
+__global__ void __launch_bounds__(256) k_norms_final(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+    const int r = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long m0 = 0, m1 = 0, m2 = 0, m5 = 0;
+    double o3 = 0, o4 = 0;
+    for (int i0 = threadIdx.x; i0 < nblk; i0 += 4 * blockDim.x) {
+        double v[4][6];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int i = i0 + u * blockDim.x;
+#pragma unroll
+            for (int c = 0; c < 6; c++) v[u][c] = i < nblk ? part[((int64_t)r * nblk + i) * 6 + c] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            m0 = max(m0, abs_bits(v[u][0])); m1 = max(m1, abs_bits(v[u][1])); m2 = max(m2, abs_bits(v[u][2]));
+            m5 = max(m5, abs_bits(v[u][5]));
+            o3 += v[u][3]; o4 += v[u][4];
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
-        o0 = nanmax(o0, __shfl_xor_sync(0xffffffffu, o0, o));
-        o1 = nanmax(o1, __shfl_xor_sync(0xffffffffu, o1, o));
-        o2 = nanmax(o2, __shfl_xor_sync(0xffffffffu, o2, o));
+        m0 = max(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        m1 = max(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = max(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+        m5 = max(m5, __shfl_xor_sync(0xffffffffu, m5, o));
         o3 += __shfl_xor_sync(0xffffffffu, o3, o);
         o4 += __shfl_xor_sync(0xffffffffu, o4, o);
-        o5 = nanmax(o5, __shfl_xor_sync(0xffffffffu, o5, o));
     }
+    __shared__ unsigned long long shm[4][8];
+    __shared__ double shs[2][8];
     if (lane == 0) {
+        shm[0][w] = m0; shm[1][w] = m1; shm[2][w] = m2; shm[3][w] = m5;
+        shs[0][w] = o3; shs[1][w] = o4;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t0 = 0, t1 = 0, t2 = 0, t5 = 0;
+        double t3 = 0, t4 = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+            t0 = max(t0, shm[0][i]); t1 = max(t1, shm[1][i]); t2 = max(t2, shm[2][i]); t5 = max(t5, shm[3][i]);
+            t3 += shs[0][i]; t4 += shs[1][i];
+        }
         double* q = out + r * 6;
-        q[0] = o0; q[1] = o1; q[2] = o2; q[3] = o3; q[4] = o4; q[5] = o5;
+        q[0] = bits_double(t0); q[1] = bits_double(t1); q[2] = bits_double(t2);
+        q[3] = t3; q[4] = t4; q[5] = bits_double(t5);
     }
 }
 
@@ -1238,30 +1268,47 @@ __global__ void k_dot_partial(const double* __restrict__ a, const double* __rest
     }
 }
 
-// cg[4 r + slot] = sum of the partial sums of right-hand side r
-__global__ void k_dot_final(const double* __restrict__ part, int nblk, double* __restrict__ cg, int slot) {
-    const int r = blockIdx.x, lane = threadIdx.x & 31;
-    if (threadIdx.x >= 32) return;
+// cg[4 r + slot] = sum of the partial sums of right-hand side r (one block, all loads first, fixed
+// order).  With it the coefficient the next vector kernel needs, formed once: slot 2 (rho of the
+// next step) gives beta = rho_next / rho, slot 1 (p^T s, s = -A p) gives alpha = -rho / p^T s;
+// either goes to cg[4 r + 3].
+__global__ void __launch_bounds__(256) k_dot_final(const double* __restrict__ part, int nblk, double* __restrict__ cg, int slot) {
+    const int r = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double t = 0.0;
-    for (int i = lane; i < nblk; i += 32) t += part[(int64_t)r * nblk + i];
+    for (int i0 = threadIdx.x; i0 < nblk; i0 += 4 * blockDim.x) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = i0 + u * (int)blockDim.x < nblk ? part[(int64_t)r * nblk + i0 + u * blockDim.x] : 0.0;
+        t += (v[0] + v[1]) + (v[2] + v[3]);
+    }
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) cg[4 * r + slot] = t;
+    __shared__ double sh[8];
+    if (lane == 0) sh[w] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += sh[i];
+        double* c = cg + 4 * r;
+        c[slot] = s;
+        if (slot == 2) c[3] = c[0] != 0.0 ? s / c[0] : 0.0;
+        if (slot == 1) c[3] = s != 0.0 ? -c[0] / s : 0.0;
+    }
 }
 
-// x += alpha p, r += alpha s with s = -A p and alpha = rho / (p^T A p) = -rho / (p^T s)
+// x += alpha p, r += alpha s with s = -A p and alpha = rho / (p^T A p) = -rho / (p^T s) (cg[4 r + 3])
 __global__ void k_cg_xr(double* __restrict__ x, double* __restrict__ rv, const double* __restrict__ p,
                         const double* __restrict__ sv, const double* __restrict__ cg, int64_t n) {
     const int r = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double den = cg[4 * r + 1];
-    const double alpha = den != 0.0 ? -cg[4 * r] / den : 0.0;
+    const double alpha = cg[4 * r + 3];
     const int64_t q = (int64_t)r * n + i;
     x[q] = fma(alpha, p[q], x[q]);
     rv[q] = fma(alpha, sv[q], rv[q]);
 }
 
-// p = z + beta p with beta = rho_next / rho (first: p = z); then rho := rho_next (k_cg_commit)
+// p = z + beta p with beta = rho_next / rho (cg[4 r + 3]; first: p = z); then rho := rho_next
+// (k_cg_commit)
 __global__ void k_cg_p(double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ cg, int64_t n,
                        int first) {
     const int r = blockIdx.y;
@@ -1272,9 +1319,7 @@ __global__ void k_cg_p(double* __restrict__ p, const double* __restrict__ z, con
         p[q] = z[q];
         return;
     }
-    const double rho = cg[4 * r];
-    const double beta = rho != 0.0 ? cg[4 * r + 2] / rho : 0.0;
-    p[q] = fma(beta, p[q], z[q]);
+    p[q] = fma(cg[4 * r + 3], p[q], z[q]);
 }
 
 // Stop test of the device-side refinement loops, the host's test restated: eta = max over the
