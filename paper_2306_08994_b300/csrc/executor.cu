@@ -52,8 +52,8 @@ struct Launch {
 // Lane-group substitution kernels for small fronts with few pivots: (lanes per front G, rows per
 // lane R, pivot bound KM) of each list, chosen by m (G R >= m) and k (k <= KM).
 constexpr int kLgLists = 15;
-constexpr int kLgG[kLgLists] = {4, 8, 8, 16, 16, 16, 32, 32, 32, 32, 32, 32, 32, 32, 32};
-constexpr int kLgR[kLgLists] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 3, 3, 3};
+constexpr int kLgG[kLgLists] = {4, 4, 4, 4, 4, 4, 8, 8, 8, 16, 16, 16, 32, 32, 32};
+constexpr int kLgR[kLgLists] = {1, 2, 2, 4, 4, 4, 4, 4, 4, 4, 4, 4, 3, 3, 3};
 constexpr int kLgKM[kLgLists] = {4, 4, 8, 4, 8, 16, 4, 8, 16, 4, 8, 16, 4, 8, 16};
 static int lg_list_of(int m, int k) {
     const int base = m <= 4 ? 0 : m <= 8 ? 1 : m <= 16 ? 3 : m <= 32 ? 6 : m <= 64 ? 9 : m <= 96 ? 12 : -1;
@@ -725,6 +725,18 @@ static int build_plan(mf_factors* F) {
                 if (subtree_try(a, h, F->tsize, budget, F->subs, false)) break;
         if (F->subs.tasks.empty() || F->subs.h < 2) F->subs = SubtreePlan{};
     }
+    // first class of the persistent sweeps: the narrow top of the tree, where launch latency
+    // dominates; the wide bottom classes keep their own launches (full occupancy for their many
+    // small fronts) and their lane-group lists
+    {
+        int c0 = a->n_cls;
+        if (F->use_sweep) {
+            if (F->opt.sweep_kernel > 0) c0 = std::max(0, a->n_cls - F->opt.sweep_kernel);
+            else
+                while (c0 > 0 && a->cls_ptr[c0] - a->cls_ptr[c0 - 1] <= kSweepMaxFronts) c0--;
+        }
+        F->sweep_c0 = std::max(c0, F->subs.h);
+    }
     // zero update vectors: no pivots in the front's whole subtree (fronts are class-ordered, so
     // children come first)
     std::vector<char> zvec(a->n_front, 0);
@@ -757,7 +769,7 @@ static int build_plan(mf_factors* F) {
                 if (solved_by_subtree) break;
                 const FrontDev& fr = a->fronts[f];
                 if (forward ? zvec[f] : fr.k == 0) continue;
-                const int li = F->use_sweep ? -1 : lg_list_of(fr.m, fr.k);
+                const int li = c >= F->sweep_c0 ? -1 : lg_list_of(fr.m, fr.k);  // the sweep has no lane-group phase
                 if (li >= 0 && fr.q_off < 0) lg[li].push_back(f);
                 else if (fr.q_off >= 0) iv.push_back(f);
                 else if (fr.m <= 4) gp[0].push_back(f);
@@ -1327,15 +1339,6 @@ static int build_plan(mf_factors* F) {
         };
         const size_t TS = F->tsize;
         F->sweep_smem_f = F->sweep_smem_b = 16;
-        // the sweep takes the narrow top of the tree, where launch latency dominates; the wide bottom
-        // classes keep their own launches (full occupancy for their many small fronts)
-        int c0 = a->n_cls;
-        if (F->use_sweep) {
-            if (F->opt.sweep_kernel > 0) c0 = std::max(0, a->n_cls - F->opt.sweep_kernel);
-            else
-                while (c0 > 0 && a->cls_ptr[c0] - a->cls_ptr[c0 - 1] <= kSweepMaxFronts) c0--;
-        }
-        F->sweep_c0 = std::max(c0, F->subs.h);
         for (int c = F->sweep_c0; c < a->n_cls; c++) {
             const ClassList& C = F->classes_f[c];
             size_t st = F->sweep_f.size();
@@ -1436,10 +1439,14 @@ static int set_smem_limits() {
     CUDA_TRY(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     CUDA_TRY(cudaFuncSetAttribute(k_front_fused<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_front_fused<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_fwd_cta<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_fwd_cta<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_bwd_cta<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
-    CUDA_TRY(cudaFuncSetAttribute(k_bwd_cta<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_fwd_cta<T, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_fwd_cta<T, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_bwd_cta<T, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_bwd_cta<T, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_fwd_cta<T, false, kRhsChunk>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_fwd_cta<T, true, kRhsChunk>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_bwd_cta<T, false, kRhsChunk>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    CUDA_TRY(cudaFuncSetAttribute(k_bwd_cta<T, true, kRhsChunk>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_inv_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_subtree_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
     CUDA_TRY(cudaFuncSetAttribute(k_schur_tc<tc::kTf32x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
@@ -1961,13 +1968,38 @@ static int launch_sweep(mf_factors* F, const SweepArgs<T>& args, size_t smem, in
     return MF_OK;
 }
 
+// Substitution kernels are launched with programmatic stream serialization:
+// a kernel may be scheduled while the previous kernel of its stream drains,
+// loads its factor coefficients, and waits (griddepcontrol.wait) for that
+// kernel's results before touching the right-hand sides (kernels_solve.cuh).
+template <typename A>
+struct NoDeduce {
+    using type = A;
+};
+template <typename... KArgs>
+static cudaError_t launch_dep(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              typename NoDeduce<KArgs>::type... args) {  // converted to the kernel's parameter types
+    void* argv[] = {(void*)&args...};
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, (const void*)kern, argv);
+}
+
 // Launch a solve kernel templated on the right-hand-side chunk NR: 1 for a
 // single right-hand side, kRhsChunk otherwise.
 #define SOLVE_UNPAREN(...) __VA_ARGS__
-#define SOLVE_NR(KER, TARGS, CFG, ARGS)                                                        \
-    do {                                                                                       \
-        if (nrhs == 1) KER<SOLVE_UNPAREN TARGS, 1><<<SOLVE_UNPAREN CFG>>>(SOLVE_UNPAREN ARGS);  \
-        else KER<SOLVE_UNPAREN TARGS, kRhsChunk><<<SOLVE_UNPAREN CFG>>>(SOLVE_UNPAREN ARGS);    \
+#define SOLVE_NR(KER, TARGS, CFG, ARGS)                                                                      \
+    do {                                                                                                     \
+        if (nrhs == 1) CUDA_TRY(launch_dep(KER<SOLVE_UNPAREN TARGS, 1>, SOLVE_UNPAREN CFG, SOLVE_UNPAREN ARGS)); \
+        else CUDA_TRY(launch_dep(KER<SOLVE_UNPAREN TARGS, kRhsChunk>, SOLVE_UNPAREN CFG, SOLVE_UNPAREN ARGS));   \
     } while (0)
 
 // The kernels of one substitution class cover disjoint fronts, so they need
@@ -2084,11 +2116,11 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
     }
 #define INV_LAUNCH(TR, PH, CNT, OFF)                                                                               \
     if ((PH == PH_BWD1 ? C.maxnc_inv : C.maxk_inv) > 512)                                                          \
-        k_inv_gemv<T, TR, PH, 32><<<dim3(CNT, nrhs), 1024, (32 * 32 + C.maxin_inv) * sizeof(T), ls>>>(            \
-            fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_vsrc, vec, vs, ys, yss, d_x, n);                      \
+        CUDA_TRY(launch_dep(k_inv_gemv<T, TR, PH, 32>, dim3(CNT, nrhs), dim3(1024), (32 * 32 + C.maxin_inv) * sizeof(T), \
+                            ls, fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_vsrc, vec, vs, ys, yss, d_x, n));    \
     else                                                                                                           \
-        k_inv_gemv<T, TR, PH, 8><<<dim3(CNT, nrhs), 256, (8 * 32 + C.maxin_inv) * sizeof(T), ls>>>(               \
-            fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_vsrc, vec, vs, ys, yss, d_x, n)
+        CUDA_TRY(launch_dep(k_inv_gemv<T, TR, PH, 8>, dim3(CNT, nrhs), dim3(256), (8 * 32 + C.maxin_inv) * sizeof(T), \
+                            ls, fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_vsrc, vec, vs, ys, yss, d_x, n))
     for (int c = 0; c < c_top; c++) {
         const ClassList& C = F->classes_f[c];
         int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0) + (C.n_grp[0] > 0) + (C.n_grp[1] > 0) + (C.n_grp[2] > 0) + (C.n_grp[3] > 0);
@@ -2106,27 +2138,27 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         GRP_FWD(1, 8)
         GRP_FWD(2, 16)
 #undef GRP_FWD
-#define LG_FWD(Q, GS, RS, KMS)                                                                                      \
+#define LG_FWD(Q)                                                                                      \
         if (C.n_lg[Q]) {                                                                                           \
-            dim3 g((C.n_lg[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)));                                              \
-            if (!trans) SOLVE_NR(k_fwd_lg, (T, false, GS, RS, KMS), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
-            else SOLVE_NR(k_fwd_lg, (T, true, GS, RS, KMS), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+            dim3 g((C.n_lg[Q] + 8 * (32 / kLgG[Q]) - 1) / (8 * (32 / kLgG[Q])));                                              \
+            if (!trans) SOLVE_NR(k_fwd_lg, (T, false, kLgG[Q], kLgR[Q], kLgKM[Q]), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+            else SOLVE_NR(k_fwd_lg, (T, true, kLgG[Q], kLgR[Q], kLgKM[Q]), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
         }
-        LG_FWD(0, 4, 1, 4)
-        LG_FWD(1, 8, 1, 4)
-        LG_FWD(2, 8, 1, 8)
-        LG_FWD(3, 16, 1, 4)
-        LG_FWD(4, 16, 1, 8)
-        LG_FWD(5, 16, 1, 16)
-        LG_FWD(6, 32, 1, 4)
-        LG_FWD(7, 32, 1, 8)
-        LG_FWD(8, 32, 1, 16)
-        LG_FWD(9, 32, 2, 4)
-        LG_FWD(10, 32, 2, 8)
-        LG_FWD(11, 32, 2, 16)
-        LG_FWD(12, 32, 3, 4)
-        LG_FWD(13, 32, 3, 8)
-        LG_FWD(14, 32, 3, 16)
+        LG_FWD(0)
+        LG_FWD(1)
+        LG_FWD(2)
+        LG_FWD(3)
+        LG_FWD(4)
+        LG_FWD(5)
+        LG_FWD(6)
+        LG_FWD(7)
+        LG_FWD(8)
+        LG_FWD(9)
+        LG_FWD(10)
+        LG_FWD(11)
+        LG_FWD(12)
+        LG_FWD(13)
+        LG_FWD(14)
 #undef LG_FWD
         if (C.n_grp[3]) {  // 16 < m <= 32: the one-front-per-warp kernel is faster forward
             dim3 g((C.n_grp[3] + 7) / 8);
@@ -2143,8 +2175,8 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
             const int ldw = C.maxm_cta;
             const cudaStream_t ls = fan.next();
             size_t sm = dgs + (size_t)kRhsChunk * ldw * sizeof(T);
-            if (!trans) k_fwd_cta<T, false><<<g, 256, sm, ls>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, ldw);
-            else k_fwd_cta<T, true><<<g, 256, sm, ls>>>(fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, ldw);
+            if (!trans) SOLVE_NR(k_fwd_cta, (T, false), (g, 256, sm, ls), (fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, ldw));
+            else SOLVE_NR(k_fwd_cta, (T, true), (g, 256, sm, ls), (fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, ldw));
         }
         if (C.n_piv) {
             const cudaStream_t ls = fan.next();
@@ -2166,7 +2198,7 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
     }
     if (scale_d) {
         int slot = prof_begin(F, s, FAM_OTHER, (16.0 + 8.0) * n * nrhs, 1.0 * n * nrhs);
-        k_scale_pivots<<<(unsigned)((n * nrhs + 255) / 256), 256, 0, s>>>(F->d_pdv, d_x, n, nrhs);
+        CUDA_TRY(launch_dep(k_scale_pivots, dim3((unsigned)((n * nrhs + 255) / 256)), dim3(256), 0, s, F->d_pdv, d_x, n, nrhs));
         prof_end(F, s, slot);
         CUDA_TRY(cudaGetLastError());
     }
@@ -2194,27 +2226,27 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         GRP_BWD(2, 16)
         GRP_BWD(3, 32)
 #undef GRP_BWD
-#define LG_BWD(Q, GS, RS, KMS)                                                                                      \
+#define LG_BWD(Q)                                                                                      \
         if (C.n_lg[Q]) {                                                                                           \
-            dim3 g((C.n_lg[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)));                                              \
-            if (!trans) SOLVE_NR(k_bwd_lg, (T, false, GS, RS, KMS), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
-            else SOLVE_NR(k_bwd_lg, (T, true, GS, RS, KMS), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
+            dim3 g((C.n_lg[Q] + 8 * (32 / kLgG[Q]) - 1) / (8 * (32 / kLgG[Q])));                                              \
+            if (!trans) SOLVE_NR(k_bwd_lg, (T, false, kLgG[Q], kLgR[Q], kLgKM[Q]), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
+            else SOLVE_NR(k_bwd_lg, (T, true, kLgG[Q], kLgR[Q], kLgKM[Q]), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
         }
-        LG_BWD(0, 4, 1, 4)
-        LG_BWD(1, 8, 1, 4)
-        LG_BWD(2, 8, 1, 8)
-        LG_BWD(3, 16, 1, 4)
-        LG_BWD(4, 16, 1, 8)
-        LG_BWD(5, 16, 1, 16)
-        LG_BWD(6, 32, 1, 4)
-        LG_BWD(7, 32, 1, 8)
-        LG_BWD(8, 32, 1, 16)
-        LG_BWD(9, 32, 2, 4)
-        LG_BWD(10, 32, 2, 8)
-        LG_BWD(11, 32, 2, 16)
-        LG_BWD(12, 32, 3, 4)
-        LG_BWD(13, 32, 3, 8)
-        LG_BWD(14, 32, 3, 16)
+        LG_BWD(0)
+        LG_BWD(1)
+        LG_BWD(2)
+        LG_BWD(3)
+        LG_BWD(4)
+        LG_BWD(5)
+        LG_BWD(6)
+        LG_BWD(7)
+        LG_BWD(8)
+        LG_BWD(9)
+        LG_BWD(10)
+        LG_BWD(11)
+        LG_BWD(12)
+        LG_BWD(13)
+        LG_BWD(14)
 #undef LG_BWD
         if (C.n_piv) {
             const cudaStream_t ls = fan.next();
@@ -2231,8 +2263,8 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
             const int ldw = C.maxm_cta;
             const cudaStream_t ls = fan.next();
             size_t sm = dgs + (size_t)(8 * 64 * kRhsChunk + kRhsChunk * ldw) * sizeof(T);
-            if (!trans) k_bwd_cta<T, false><<<g, 256, sm, ls>>>(fr, L + C.off_cta, 0, fac, F->d_dofs, d_x, n, nrhs, ldw);
-            else k_bwd_cta<T, true><<<g, 256, sm, ls>>>(fr, L + C.off_cta, 0, fac, F->d_dofs, d_x, n, nrhs, ldw);
+            if (!trans) SOLVE_NR(k_bwd_cta, (T, false), (g, 256, sm, ls), (fr, L + C.off_cta, 0, fac, F->d_dofs, d_x, n, nrhs, ldw));
+            else SOLVE_NR(k_bwd_cta, (T, true), (g, 256, sm, ls), (fr, L + C.off_cta, 0, fac, F->d_dofs, d_x, n, nrhs, ldw));
         }
         if (C.n_small) {
             dim3 g((C.n_small + 7) / 8);

@@ -87,6 +87,18 @@ __device__ __forceinline__ T gather_rhs(const FR& fr, const int32_t* __restrict_
 // fewest registers) or kRhsChunk.
 constexpr int kRhsChunk = 4;
 
+// Programmatic dependent launch.  The substitution kernels are launched so that
+// they may start while the previous kernel of their stream is finishing: each
+// one first loads what no earlier kernel of the solve writes (factor
+// coefficients, dof lists, gather sources), then waits for its predecessor grid
+// to complete and flush (griddepcontrol.wait; a no-op without a programmatic
+// dependency) before it reads right-hand sides, update vectors or pivot
+// values.  Every thread that reads or writes those waits first, so a grid that
+// completes implies its predecessor completed.  launch_dependents lets the
+// next kernel's CTAs be scheduled once every CTA of this grid has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // y = w / d for one right-hand side, w * (1/d) for several (one reciprocal
 // per pivot shared by the chunk).
 template <typename T, int NR>
@@ -115,6 +127,7 @@ __device__ __forceinline__ void k_fwd_warp_body(const FrontDev* __restrict__ fro
     const int i0 = lane, i1 = lane + 32;
     const RhsSrc s0 = i0 < m ? rhs_src<SolveRec>(fr, fd, vsrc, i0) : RhsSrc{-1, -1, -1};
     const RhsSrc s1 = i1 < m ? rhs_src<SolveRec>(fr, fd, vsrc, i1) : RhsSrc{-1, -1, -1};
+    pdl_wait();
     for (int rb = 0; rb < nrhs; rb += NR) {
         const int nr = min(NR, nrhs - rb);
         T w0[NR], w1[NR];
@@ -175,6 +188,7 @@ __global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_fwd_warp(const FrontDe
                                                   int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                   const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
                                                   double* __restrict__ x, int64_t n_dof, int nrhs) {
+    pdl_trigger();
     k_fwd_warp_body<T, TRANS, NR>(fronts, list, count, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, blockIdx.x);
 }
 
@@ -192,6 +206,7 @@ __device__ __forceinline__ void k_bwd_warp_body(const FrontDev* __restrict__ fro
     const T* R = fac + fr.R_off;
     const int i0 = lane, i1 = lane + 32;
     const int d0 = i0 < m ? fd[i0] : 0, d1 = i1 < m ? fd[i1] : 0;
+    pdl_wait();
     for (int rb = 0; rb < nrhs; rb += NR) {
         const int nr = min(NR, nrhs - rb);
         // all unknowns of the front: pivots hold y, CB holds the final x
@@ -244,6 +259,7 @@ template <typename T, bool TRANS, int NR>
 __global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_bwd_warp(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                   int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                   double* __restrict__ x, int64_t n_dof, int nrhs) {
+    pdl_trigger();
     k_bwd_warp_body<T, TRANS, NR>(fronts, list, count, fac, dofs, x, n_dof, nrhs, blockIdx.x);
 }
 
@@ -285,6 +301,7 @@ __device__ __forceinline__ void k_fwd_lg_body(const SolveRec* __restrict__ list,
 #pragma unroll
     for (int p = 0; p < KM; p++) dg[p] = p < k ? fdiag<T, TRANS>(P, m, p) : T(1);
     const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)k);  // warp-uniform pivot count
+    pdl_wait();
     for (int rb = 0; rb < nrhs; rb += NR) {
         const int nr = min(NR, nrhs - rb);
         T w[R][NR];
@@ -328,6 +345,7 @@ __global__ void __launch_bounds__(256) k_fwd_lg(const SolveRec* __restrict__ lis
                                                 const int32_t* __restrict__ dofs, const int64_t* __restrict__ vsrc,
                                                 T* __restrict__ vecs, int64_t vec_size, double* __restrict__ x,
                                                 int64_t n_dof, int nrhs) {
+    pdl_trigger();
     k_fwd_lg_body<T, TRANS, G, R, KM, NR>(list, count, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, blockIdx.x);
 }
 
@@ -363,6 +381,7 @@ __device__ __forceinline__ void k_bwd_lg_body(const SolveRec* __restrict__ list,
 #pragma unroll
     for (int p = 0; p < KM; p++) dg[p] = p < k ? bdiag<T, TRANS>(P, m, p) : T(1);
     const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)k);
+    pdl_wait();
     for (int rb = 0; rb < nrhs; rb += NR) {
         const int nr = min(NR, nrhs - rb);
         T v[R][NR];
@@ -403,6 +422,7 @@ template <typename T, bool TRANS, int G, int R, int KM, int NR>
 __global__ void __launch_bounds__(256) k_bwd_lg(const SolveRec* __restrict__ list, int count, const T* __restrict__ fac,
                                                 const int32_t* __restrict__ dofs, double* __restrict__ x, int64_t n_dof,
                                                 int nrhs) {
+    pdl_trigger();
     k_bwd_lg_body<T, TRANS, G, R, KM, NR>(list, count, fac, dofs, x, n_dof, nrhs, blockIdx.x);
 }
 
@@ -436,6 +456,7 @@ __device__ __forceinline__ void k_fwd_grp_body(const FrontDev* __restrict__ fron
     }
     const RhsSrc src = (active && i < m) ? rhs_src<SolveRec>(fr, fd, vsrc, i) : RhsSrc{-1, -1, -1};
     const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)k);  // warp-uniform pivot count
+    pdl_wait();
     for (int rb = 0; rb < nrhs; rb += NR) {
         const int nr = min(NR, nrhs - rb);
         T w[NR];
@@ -471,6 +492,7 @@ __global__ void __launch_bounds__(256) k_fwd_grp(const FrontDev* __restrict__ fr
                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs) {
+    pdl_trigger();
     k_fwd_grp_body<T, TRANS, G, NR>(fronts, list, count, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, blockIdx.x);
 }
 
@@ -500,6 +522,7 @@ __device__ __forceinline__ void k_bwd_grp_body(const FrontDev* __restrict__ fron
     }
     const int di = (active && i < m) ? fd[i] : 0;
     const int mmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);  // warp-uniform front size
+    pdl_wait();
     for (int rb = 0; rb < nrhs; rb += NR) {
         const int nr = min(NR, nrhs - rb);
         T v[NR];
@@ -530,6 +553,7 @@ template <typename T, bool TRANS, int G, int NR>
 __global__ void __launch_bounds__(256) k_bwd_grp(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs) {
+    pdl_trigger();
     k_bwd_grp_body<T, TRANS, G, NR>(fronts, list, count, fac, dofs, x, n_dof, nrhs, blockIdx.x);
 }
 
@@ -538,7 +562,7 @@ __global__ void __launch_bounds__(256) k_bwd_grp(const FrontDev* __restrict__ fr
 // shared memory by all threads, solved by one warp per right-hand side, then
 // applied to the later rows, including the contribution-block rows (update
 // vector).  Shared memory: 32 x 33 T + kRhsChunk x ldw T (ldw >= m).
-template <typename T, bool TRANS>
+template <typename T, bool TRANS, int NR = kRhsChunk>
 __device__ __forceinline__ void k_fwd_cta_body(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int rows_all, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
@@ -553,8 +577,9 @@ __device__ __forceinline__ void k_fwd_cta_body(const FrontDev* __restrict__ fron
     const T* P = fac + fr.P_off;
     const T* R = fac + fr.R_off;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int rb = 0; rb < nrhs; rb += kRhsChunk) {
-        const int nr = min(kRhsChunk, nrhs - rb);
+    pdl_wait();
+    for (int rb = 0; rb < nrhs; rb += NR) {
+        const int nr = min(NR, nrhs - rb);
         for (int i = threadIdx.x; i < mr; i += blockDim.x) {
             const RhsSrc src = rhs_src<SolveRec>(fr, fd, vsrc, i);
             for (int rr = 0; rr < nr; rr++)
@@ -589,19 +614,28 @@ __device__ __forceinline__ void k_fwd_cta_body(const FrontDev* __restrict__ fron
                 if (lane < wb) wr[pb + lane] = val;
             }
             __syncthreads();
+            // rows below the block: 16 coefficients of a row are loaded before their products (two
+            // memory round trips per row of a 32-wide block)
             for (int i = pb + wb + threadIdx.x; i < mr; i += blockDim.x) {
-                T acc[kRhsChunk];
+                T acc[NR];
 #pragma unroll
-                for (int rr = 0; rr < kRhsChunk; rr++) acc[rr] = T(0);
-#pragma unroll 4
-                for (int p = 0; p < wb; p++) {
-                    const T cf = fcoef<T, TRANS>(P, R, m, k, i, pb + p);
+                for (int rr = 0; rr < NR; rr++) acc[rr] = T(0);
+                for (int p0 = 0; p0 < wb; p0 += 16) {
+                    // unconditional loads (columns past the block repeat its last one, weighted 0)
+                    T cf[16];
 #pragma unroll
-                    for (int rr = 0; rr < kRhsChunk; rr++)
-                        if (rr < nr) acc[rr] += cf * w[rr * ldw + pb + p];
+                    for (int p = 0; p < 16; p++) cf[p] = fcoef<T, TRANS>(P, R, m, k, i, pb + min(p0 + p, wb - 1));
+#pragma unroll
+                    for (int p = 0; p < 16; p++) {
+                        const int c = min(p0 + p, wb - 1);
+                        const T on = p0 + p < wb ? T(1) : T(0);
+#pragma unroll
+                        for (int rr = 0; rr < NR; rr++)
+                            if (rr < nr) acc[rr] += (on * cf[p]) * w[rr * ldw + pb + c];
+                    }
                 }
 #pragma unroll
-                for (int rr = 0; rr < kRhsChunk; rr++)
+                for (int rr = 0; rr < NR; rr++)
                     if (rr < nr) w[rr * ldw + i] -= acc[rr];
             }
             __syncthreads();
@@ -614,19 +648,20 @@ __device__ __forceinline__ void k_fwd_cta_body(const FrontDev* __restrict__ fron
         __syncthreads();
     }
 }
-template <typename T, bool TRANS>
+template <typename T, bool TRANS, int NR>
 __global__ void __launch_bounds__(256) k_fwd_cta(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int rows_all, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int ldw) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
-    k_fwd_cta_body<T, TRANS>(fronts, list, rows_all, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, ldw, blockIdx.x, smem_dyn);
+    pdl_trigger();
+    k_fwd_cta_body<T, TRANS, NR>(fronts, list, rows_all, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, ldw, blockIdx.x, smem_dyn);
 }
 
 // Backward, one CTA per mid-size front: the CB part of the pivot rows first,
 // then the unit (or, transposed, L11^T) triangle in 32-wide blocks.
 // Shared memory: 32 x 33 T + 8 x 64 x kRhsChunk T + kRhsChunk x ldw T.
-template <typename T, bool TRANS>
+template <typename T, bool TRANS, int NR = kRhsChunk>
 __device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int cb_done, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int ldw, int vb, unsigned char* smem_raw) {
@@ -641,8 +676,9 @@ __device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fron
     const T* R = fac + fr.R_off;
     const int mv = cb_done ? k : m;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int rb = 0; rb < nrhs; rb += kRhsChunk) {
-        const int nr = min(kRhsChunk, nrhs - rb);
+    pdl_wait();
+    for (int rb = 0; rb < nrhs; rb += NR) {
+        const int nr = min(NR, nrhs - rb);
         for (int i = threadIdx.x; i < mv; i += blockDim.x) {
             const int d = fd[i];
             for (int rr = 0; rr < nr; rr++) v[rr * ldw + i] = (T)__ldcg(x + (int64_t)(rb + rr) * n_dof + d);
@@ -653,28 +689,34 @@ __device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fron
             // pivot row, lanes along the column (coalesced), a shuffle tree per row
             for (int i = warp; i < k; i += 8) {
                 const T* col = P + (int64_t)i * m;
-                T acc[kRhsChunk];
+                T acc[NR];
 #pragma unroll
-                for (int rr = 0; rr < kRhsChunk; rr++) acc[rr] = T(0);
+                for (int rr = 0; rr < NR; rr++) acc[rr] = T(0);
                 int j = k + lane;
-                for (; j + 96 < m; j += 128) {
-                    T c[4];
+                for (; j + 32 * 11 < m; j += 32 * 12) {  // 12 loads in flight per lane
+                    T c[12];
 #pragma unroll
-                    for (int u = 0; u < 4; u++) c[u] = col[j + 32 * u];
+                    for (int u = 0; u < 12; u++) c[u] = col[j + 32 * u];
 #pragma unroll
-                    for (int u = 0; u < 4; u++)
+                    for (int u = 0; u < 12; u++)
 #pragma unroll
-                        for (int rr = 0; rr < kRhsChunk; rr++)
+                        for (int rr = 0; rr < NR; rr++)
                             if (rr < nr) acc[rr] += c[u] * v[rr * ldw + j + 32 * u];
                 }
-                for (; j < m; j += 32) {
-                    const T c = col[j];
+                {  // the remaining < 12 column chunks, guarded, all loads first
+                    T c[12];
 #pragma unroll
-                    for (int rr = 0; rr < kRhsChunk; rr++)
-                        if (rr < nr) acc[rr] += c * v[rr * ldw + j];
+                    for (int u = 0; u < 12; u++) c[u] = j + 32 * u < m ? col[j + 32 * u] : T(0);
+#pragma unroll
+                    for (int u = 0; u < 12; u++)
+                        if (j + 32 * u < m) {
+#pragma unroll
+                            for (int rr = 0; rr < NR; rr++)
+                                if (rr < nr) acc[rr] += c[u] * v[rr * ldw + j + 32 * u];
+                        }
                 }
 #pragma unroll
-                for (int rr = 0; rr < kRhsChunk; rr++) {
+                for (int rr = 0; rr < NR; rr++) {
                     T sum = acc[rr];
                     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
                     if (lane == 0 && rr < nr) v[rr * ldw + i] -= sum;
@@ -684,14 +726,15 @@ __device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fron
         } else if (!cb_done) {
             // pivot rows (lane, lane + 32; k < 64) minus their CB part; the 8 warps split the columns
             const int i0 = lane, i1 = lane + 32;
-            T a0[kRhsChunk], a1[kRhsChunk];
+            T a0[NR], a1[NR];
 #pragma unroll
-            for (int rr = 0; rr < kRhsChunk; rr++) a0[rr] = a1[rr] = T(0);
+            for (int rr = 0; rr < NR; rr++) a0[rr] = a1[rr] = T(0);
+#pragma unroll 8
             for (int j = k + warp; j < m; j += 8) {
                 const T c0 = i0 < k ? bcoef<T, TRANS>(P, R, m, k, i0, j) : T(0);
                 const T c1 = i1 < k ? bcoef<T, TRANS>(P, R, m, k, i1, j) : T(0);
 #pragma unroll
-                for (int rr = 0; rr < kRhsChunk; rr++) {
+                for (int rr = 0; rr < NR; rr++) {
                     if (rr < nr) {
                         const T xj = v[rr * ldw + j];
                         a0[rr] += c0 * xj;
@@ -700,7 +743,7 @@ __device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fron
                 }
             }
 #pragma unroll
-            for (int rr = 0; rr < kRhsChunk; rr++) {
+            for (int rr = 0; rr < NR; rr++) {
                 red[(rr * 8 + warp) * 64 + i0] = a0[rr];
                 red[(rr * 8 + warp) * 64 + i1] = a1[rr];
             }
@@ -750,7 +793,7 @@ __device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fron
                 for (int i = warp; i < pb; i += 8) {
                     const T cf = lane < wb ? bcoef<T, TRANS>(P, R, m, k, i, pb + lane) : T(0);
 #pragma unroll
-                    for (int rr = 0; rr < kRhsChunk; rr++) {
+                    for (int rr = 0; rr < NR; rr++) {
                         T sum = rr < nr ? cf * v[rr * ldw + pb + min(lane, wb - 1)] : T(0);
                         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
                         if (lane == 0 && rr < nr) v[rr * ldw + i] -= sum;
@@ -758,18 +801,18 @@ __device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fron
                 }
             }
             for (int i = threadIdx.x; i < pb && !TRANS; i += blockDim.x) {
-                T acc[kRhsChunk];
+                T acc[NR];
 #pragma unroll
-                for (int rr = 0; rr < kRhsChunk; rr++) acc[rr] = T(0);
+                for (int rr = 0; rr < NR; rr++) acc[rr] = T(0);
 #pragma unroll 4
                 for (int j = 0; j < wb; j++) {
                     const T cf = bcoef<T, TRANS>(P, R, m, k, i, pb + j);
 #pragma unroll
-                    for (int rr = 0; rr < kRhsChunk; rr++)
+                    for (int rr = 0; rr < NR; rr++)
                         if (rr < nr) acc[rr] += cf * v[rr * ldw + pb + j];
                 }
 #pragma unroll
-                for (int rr = 0; rr < kRhsChunk; rr++)
+                for (int rr = 0; rr < NR; rr++)
                     if (rr < nr) v[rr * ldw + i] -= acc[rr];
             }
             __syncthreads();
@@ -781,12 +824,13 @@ __device__ __forceinline__ void k_bwd_cta_body(const FrontDev* __restrict__ fron
         __syncthreads();
     }
 }
-template <typename T, bool TRANS>
+template <typename T, bool TRANS, int NR>
 __global__ void __launch_bounds__(256) k_bwd_cta(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int cb_done, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int ldw) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
-    k_bwd_cta_body<T, TRANS>(fronts, list, cb_done, fac, dofs, x, n_dof, nrhs, ldw, blockIdx.x, smem_dyn);
+    pdl_trigger();
+    k_bwd_cta_body<T, TRANS, NR>(fronts, list, cb_done, fac, dofs, x, n_dof, nrhs, ldw, blockIdx.x, smem_dyn);
 }
 
 // ---------------------------------------------------------------------------
@@ -836,10 +880,53 @@ __device__ __forceinline__ void k_inv_gemv_body(const FrontDev* __restrict__ fro
     const T* R = fac + fr.R_off;
     const T* Q = inv + (fr.q_off >= 0 ? fr.q_off : 0);
     if (PH == PH_FWD2 && t.r0 < k) {
+        pdl_wait();
         for (int i = t.r0 + threadIdx.x; i < t.r1; i += blockDim.x) xr[fd[i]] = (double)__ldcg(yr + i);
         return;
     }
     const int nin = (PH == PH_BWD1) ? m - k : k;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // column range of row i
+    auto lo = [&](int i) { return PH == PH_BWD2 ? i : 0; };
+    auto hi = [&](int i) { return PH == PH_FWD1 ? i + 1 : nin; };
+    // The first chunk of each row's coefficients is loaded before the wait for the previous
+    // kernel; the operand of the row's final update (its right-hand-side entry, or the dof it is
+    // written to) before the inputs are staged.
+    constexpr int RW = TRANS ? (32 + NW - 1) / NW : 1;  // rows per warp (TRANS) / per lane (!TRANS)
+    constexpr int PC = 8;                              // coefficients per row issued early
+    T pre[RW][PC];
+    T rhs[RW];
+    int xi[RW];
+    // !TRANS: full columns for every row of the block: FWD1 [0, r0); BWD2 [r1, k); else [0, nin)
+    const int f0 = PH == PH_BWD2 ? t.r1 : 0;
+    const int f1 = PH == PH_FWD1 ? t.r0 : nin;
+#pragma unroll
+    for (int q = 0; q < RW; q++) {
+        const int i = TRANS ? t.r0 + warp + NW * q : t.r0 + lane;
+        const bool valid = i < t.r1;
+        rhs[q] = T(0);
+        xi[q] = 0;
+#pragma unroll
+        for (int u = 0; u < PC; u++) {
+            if (!TRANS) {
+                const int j = f0 + warp + NW * u;
+                pre[q][u] = (valid && j < f1) ? inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j) : T(0);
+            } else {
+                const int j = (valid ? lo(i) : 0) + lane + 32 * u;
+                pre[q][u] = (valid && j < hi(i)) ? inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j) : T(0);
+            }
+        }
+    }
+    pdl_wait();
+#pragma unroll
+    for (int q = 0; q < RW; q++) {
+        const int i = TRANS ? t.r0 + warp + NW * q : t.r0 + lane;
+        if (i < t.r1 && (TRANS ? lane == 0 : warp == 0)) {
+            if (PH == PH_FWD2) rhs[q] = gather_rhs<T, FrontDev>(fr, fd, vsrc, vr, xr, i);
+            else if (PH == PH_BWD1) rhs[q] = (T)__ldcg(xr + fd[i]);
+            else if (PH == PH_BWD2) xi[q] = fd[i];
+        }
+    }
     for (int j = threadIdx.x; j < nin; j += blockDim.x) {
         T v;
         if (PH == PH_FWD1) v = gather_rhs<T, FrontDev>(fr, fd, vsrc, vr, xr, j);
@@ -848,29 +935,27 @@ __device__ __forceinline__ void k_inv_gemv_body(const FrontDev* __restrict__ fro
         vin[j] = v;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // column range of row i
-    auto lo = [&](int i) { return PH == PH_BWD2 ? i : 0; };
-    auto hi = [&](int i) { return PH == PH_FWD1 ? i + 1 : nin; };
-    auto finish = [&](int i, T acc) {
+    auto finish = [&](int i, int q, T acc) {
         if (PH == PH_FWD1) yr[i] = acc;
-        else if (PH == PH_FWD2) vr[fr.vec_off + (i - k)] = gather_rhs<T, FrontDev>(fr, fd, vsrc, vr, xr, i) - acc;
-        else if (PH == PH_BWD1) yr[i] = (T)__ldcg(xr + fd[i]) - acc;
-        else xr[fd[i]] = (double)acc;
+        else if (PH == PH_FWD2) vr[fr.vec_off + (i - k)] = rhs[q] - acc;
+        else if (PH == PH_BWD1) yr[i] = rhs[q] - acc;
+        else xr[xi[q]] = (double)acc;
     };
     if (!TRANS) {
         // lane = row, the NW warps split the columns; the rectangle part of the
         // column range needs no per-element test, only the triangle edge does
         const int i = t.r0 + lane;
         const bool valid = i < t.r1;
-        // full columns for every row of the block: FWD1 [0, r0); BWD2 [r1, k); else [0, nin)
-        const int f0 = PH == PH_BWD2 ? t.r1 : 0;
-        const int f1 = PH == PH_FWD1 ? t.r0 : nin;
         T acc[8];
 #pragma unroll
         for (int u = 0; u < 8; u++) acc[u] = T(0);
         if (valid) {
-            int j = f0 + warp;
+#pragma unroll
+            for (int u = 0; u < PC; u++) {
+                const int j = f0 + warp + NW * u;
+                if (j < f1) acc[u] += pre[0][u] * vin[j];
+            }
+            int j = f0 + warp + NW * PC;
             for (; j + 7 * NW < f1; j += 8 * NW) {
 #pragma unroll
                 for (int u = 0; u < 8; u++) acc[u] += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j + NW * u) * vin[j + NW * u];
@@ -887,15 +972,23 @@ __device__ __forceinline__ void k_inv_gemv_body(const FrontDev* __restrict__ fro
         if (warp == 0 && valid) {
             T sum = T(0);
             for (int w = 0; w < NW; w++) sum += red[w * 32 + lane];
-            finish(i, sum);
+            finish(i, 0, sum);
         }
     } else {
-        for (int i = t.r0 + warp; i < t.r1; i += NW) {  // one row per warp
+#pragma unroll
+        for (int q = 0; q < RW; q++) {  // one row per warp at a time
+            const int i = t.r0 + warp + NW * q;
+            if (i >= t.r1) break;
             T acc[8];
 #pragma unroll
             for (int u = 0; u < 8; u++) acc[u] = T(0);
             const int jl = lo(i), jh = hi(i);
-            int j = jl + lane;
+#pragma unroll
+            for (int u = 0; u < PC; u++) {
+                const int j = jl + lane + 32 * u;
+                if (j < jh) acc[u] += pre[q][u] * vin[j];
+            }
+            int j = jl + lane + 32 * PC;
             for (; j + 224 < jh; j += 256) {
 #pragma unroll
                 for (int u = 0; u < 8; u++) acc[u] += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j + 32 * u) * vin[j + 32 * u];
@@ -903,7 +996,7 @@ __device__ __forceinline__ void k_inv_gemv_body(const FrontDev* __restrict__ fro
             for (; j < jh; j += 32) acc[0] += inv_coef<T, TRANS, PH>(P, R, Q, m, k, i, j) * vin[j];
             T sum = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            if (lane == 0) finish(i, sum);
+            if (lane == 0) finish(i, q, sum);
         }
     }
 }
@@ -914,6 +1007,7 @@ __global__ void __launch_bounds__(NW * 32) k_inv_gemv(const FrontDev* __restrict
                                                   T* __restrict__ vecs, int64_t vec_size, T* __restrict__ ys,
                                                   int64_t ys_size, double* __restrict__ x, int64_t n_dof) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
+    pdl_trigger();
     k_inv_gemv_body<T, TRANS, PH, NW>(fronts, tasks, fac, inv, dofs, vsrc, vecs, vec_size, ys, ys_size, x, n_dof, blockIdx.x, smem_dyn, blockIdx.y);
 }
 
@@ -1031,10 +1125,10 @@ __global__ void __launch_bounds__(256) k_solve_sweep(SweepArgs<T> a) {
                     break;
                 case SW_CTA:
                     if (FWD)
-                        k_fwd_cta_body<T, TRANS>(a.fronts, L, 1, a.fac, a.dofs, a.vsrc, a.vecs, a.vec_size, a.x, a.n_dof, a.nrhs,
+                        k_fwd_cta_body<T, TRANS, NR>(a.fronts, L, 1, a.fac, a.dofs, a.vsrc, a.vecs, a.vec_size, a.x, a.n_dof, a.nrhs,
                                                  P.ldw, vb, smem_dyn);
                     else
-                        k_bwd_cta_body<T, TRANS>(a.fronts, L, 0, a.fac, a.dofs, a.x, a.n_dof, a.nrhs, P.ldw, vb, smem_dyn);
+                        k_bwd_cta_body<T, TRANS, NR>(a.fronts, L, 0, a.fac, a.dofs, a.x, a.n_dof, a.nrhs, P.ldw, vb, smem_dyn);
                     break;
                 case SW_INV1:
                     for (int r = 0; r < a.nrhs; r++)
@@ -1366,6 +1460,8 @@ __global__ void k_gather_pivots(const int64_t* __restrict__ diag_off, const T* _
     if (i < n) pdv[i] = (double)fac[diag_off[i]];
 }
 __global__ void k_scale_pivots(const double* __restrict__ pdv, double* __restrict__ x, int64_t n, int nrhs) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * nrhs) return;
     x[i] *= pdv[nrhs == 1 ? i : i % n];
