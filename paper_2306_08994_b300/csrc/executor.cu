@@ -85,6 +85,32 @@ constexpr int kSweepMaxFronts = 2048;  // classes with at most this many fronts 
         }                                    \
     } while (0)
 
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// while the previous kernel of its stream drains; it reads launch-invariant
+// data first and waits (griddepcontrol.wait) for that kernel's results before
+// touching anything an earlier kernel writes (pdl_wait in kernels_factor.cuh).
+// Only kernels that call pdl_wait are launched this way.
+template <typename A>
+struct NoDeduce {
+    using type = A;
+};
+template <typename... KArgs>
+static cudaError_t launch_dep(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              typename NoDeduce<KArgs>::type... args) {  // converted to the kernel's parameter types
+    void* argv[] = {(void*)&args...};
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, (const void*)kern, argv);
+}
+
 template <typename T>
 int dev_alloc(T** p, size_t n) {
     *p = nullptr;
@@ -1968,30 +1994,6 @@ static int launch_sweep(mf_factors* F, const SweepArgs<T>& args, size_t smem, in
     return MF_OK;
 }
 
-// Substitution kernels are launched with programmatic stream serialization:
-// a kernel may be scheduled while the previous kernel of its stream drains,
-// loads its factor coefficients, and waits (griddepcontrol.wait) for that
-// kernel's results before touching the right-hand sides (kernels_solve.cuh).
-template <typename A>
-struct NoDeduce {
-    using type = A;
-};
-template <typename... KArgs>
-static cudaError_t launch_dep(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                              typename NoDeduce<KArgs>::type... args) {  // converted to the kernel's parameter types
-    void* argv[] = {(void*)&args...};
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, (const void*)kern, argv);
-}
 
 // Launch a solve kernel templated on the right-hand-side chunk NR: 1 for a
 // single right-hand side, kRhsChunk otherwise.

@@ -9,6 +9,18 @@
 
 #include "mf_internal.h"
 
+// Programmatic dependent launch (used by the substitution kernels).  A kernel
+// launched with programmatic stream serialization may be scheduled while the
+// previous kernel of its stream is still running.  It reads only
+// launch-invariant data (task records, index maps, factor coefficients) before
+// pdl_wait, which returns once the predecessor grid has completed and its
+// memory is visible (a no-op for an ordinary launch); every thread that reads
+// or writes data of earlier kernels calls it first, so a completed grid implies
+// a completed predecessor.  pdl_trigger lets the next kernel's CTAs be
+// scheduled once every CTA of this grid has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 struct DevStatus {
     unsigned long long n_perturbed;
     unsigned long long first;  // (front << 32) | pivot of the first small pivot (min)

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 
+#include "kernels_factor.cuh"
 #include "mf_internal.h"
 
 // ---------------------------------------------------------------------------
@@ -87,17 +88,10 @@ __device__ __forceinline__ T gather_rhs(const FR& fr, const int32_t* __restrict_
 // fewest registers) or kRhsChunk.
 constexpr int kRhsChunk = 4;
 
-// Programmatic dependent launch.  The substitution kernels are launched so that
-// they may start while the previous kernel of their stream is finishing: each
-// one first loads what no earlier kernel of the solve writes (factor
-// coefficients, dof lists, gather sources), then waits for its predecessor grid
-// to complete and flush (griddepcontrol.wait; a no-op without a programmatic
-// dependency) before it reads right-hand sides, update vectors or pivot
-// values.  Every thread that reads or writes those waits first, so a grid that
-// completes implies its predecessor completed.  launch_dependents lets the
-// next kernel's CTAs be scheduled once every CTA of this grid has started.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// Substitution kernels use programmatic dependent launch (pdl_wait / pdl_trigger,
+// kernels_factor.cuh): each loads what no earlier kernel of the solve writes (factor
+// coefficients, dof lists, gather sources) before its pdl_wait, and right-hand sides,
+// update vectors and pivot values only after it.
 
 // y = w / d for one right-hand side, w * (1/d) for several (one reciprocal
 // per pivot shared by the chunk).
