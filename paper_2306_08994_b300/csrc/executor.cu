@@ -947,12 +947,19 @@ static int build_plan(mf_factors* F) {
             if (lo >= F->small_max) break;
             const int hi = std::min(G, F->small_max);
             std::vector<int32_t> L;
+            int mx = 0;
             for (int32_t f : all)
-                if (a->fronts[f].m > lo && a->fronts[f].m <= hi) L.push_back(f);
+                if (a->fronts[f].m > lo && a->fronts[f].m <= hi) {
+                    L.push_back(f);
+                    mx = std::max(mx, a->fronts[f].m);
+                }
             if (!L.empty()) {
                 double by, fl;
                 small_bytes(L, by, fl);
-                push({K_GRP, c, (int)L.size(), G, (int64_t)flist.size()}, FAM_FUSED, by, fl);
+                // the launch's widest front bounds the kernel's column loops: 24 for a 32-lane launch
+                // whose fronts all have m <= 24
+                const int mj = G == 32 && mx <= 24 ? 24 : G;
+                push({K_GRP, c, (int)L.size(), mj, (int64_t)flist.size()}, FAM_FUSED, by, fl);
                 flist.insert(flist.end(), L.begin(), L.end());
                 fwoff.resize(flist.size(), -1);
             }
@@ -1812,18 +1819,20 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
                 break;
             }
             case K_GRP: {
-                const unsigned per = 8 * (32 / L.maxm);  // fronts per 256-thread CTA
+                const int G = L.maxm <= 4 ? 4 : L.maxm <= 8 ? 8 : L.maxm <= 16 ? 16 : 32;  // L.maxm: widest front
+                const unsigned per = 8 * (32 / G);                                          // fronts per 256-thread CTA
                 const unsigned g = (unsigned)((L.count + per - 1) / per);
-#define GRP_CASE(GS)                                                                                             \
-    case GS:                                                                                                     \
-        k_front_grp<T, GS><<<g, 256, 0, s>>>(F->d_frec + L.off, L.count, F->d_maps, d_values, a->npe,               \
-                                             fac, cb, F->tol_rel, F->d_status);                                  \
+#define GRP_CASE(GS, MJS)                                                                                        \
+    case MJS:                                                                                                    \
+        k_front_grp<T, GS, MJS><<<g, 256, 0, s>>>(F->d_frec + L.off, L.count, F->d_maps, d_values, a->npe,          \
+                                                  fac, cb, F->tol_rel, F->d_status);                             \
         break;
                 switch (L.maxm) {
-                    GRP_CASE(4)
-                    GRP_CASE(8)
-                    GRP_CASE(16)
-                    GRP_CASE(32)
+                    GRP_CASE(4, 4)
+                    GRP_CASE(8, 8)
+                    GRP_CASE(16, 16)
+                    GRP_CASE(32, 24)
+                    GRP_CASE(32, 32)
                 }
 #undef GRP_CASE
                 break;

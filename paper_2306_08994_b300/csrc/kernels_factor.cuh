@@ -311,13 +311,13 @@ __global__ void __launch_bounds__(256) k_front_fused(const FactorRec* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// Tiny fronts (m <= G, G in {4, 8, 16, 32}): a group of G lanes per front,
+// Tiny fronts (m <= MJ <= G, G in {4, 8, 16, 32}): a group of G lanes per front,
 // 32/G fronts per warp, no shared memory.  Lane i holds row i of F in
 // registers; the pivot row, the pivot and the pivot-column entry travel by
 // width-G shuffles.  Same tasks as k_front_fused: assembly (element matrix
 // at a leaf, extend-add of the children's blocks otherwise), static pivot
 // check, T1 division of the pivot row, T2/T3 update, then P, R, S written.
-template <typename T, int G>
+template <typename T, int G, int MJ = G>
 __global__ void __launch_bounds__(256) k_front_grp(const FactorRec* __restrict__ recs, int count, const int32_t* __restrict__ maps,
                                                    const double* __restrict__ values, int npe, T* __restrict__ fac,
                                                    T* __restrict__ cbs, double tol_rel, DevStatus* st) {
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(256) k_front_grp(const FactorRec* __restrict__
     const int32_t f = active ? fr.front : -1;
     const int m = active ? fr.m : 0, k = active ? fr.k : 0;
     const bool row = i < m;
-    T a[G];
+    T a[MJ];  // MJ <= G: the widest front of the launch
     // ---- assembly: lane i loads its own row's maps; column j's maps are row j's, taken from
     //      lane j by a shuffle (rows and columns of a front share one index set; every lane of
     //      the warp takes part, so the shuffles stay outside the leaf / internal branches).
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(256) k_front_grp(const FactorRec* __restrict__
         const T* S1 = cbs + (two ? fr.cS[1] : 0);
         const int n0 = fr.cn[0], n1 = two ? fr.cn[1] : 0;
 #pragma unroll
-        for (int j = 0; j < G; j++) {
+        for (int j = 0; j < MJ; j++) {
             const int j0 = __shfl_sync(0xffffffffu, i0, j, G), j1 = __shfl_sync(0xffffffffu, i1, j, G);
             T v = T(0);
             if (leaf) {
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(256) k_front_grp(const FactorRec* __restrict__
     // ---- partial LU (Table 2): all lanes shuffle, each group applies its own pivots
     const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)k);
 #pragma unroll
-    for (int p = 0; p < G; p++) {
+    for (int p = 0; p < MJ; p++) {
         if (p < kmax) {
             const T pv = __shfl_sync(0xffffffffu, a[p], p, G);
             const bool mine = p < k;
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(256) k_front_grp(const FactorRec* __restrict__
             const T rinv = T(1) / piv;
             const T lp = a[p];
 #pragma unroll
-            for (int j = p + 1; j < G; j++) {
+            for (int j = p + 1; j < MJ; j++) {
                 const T uj = __shfl_sync(0xffffffffu, a[j], p, G) * rinv;
                 if (mine) {
                     if (i > p) a[j] -= lp * uj;
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(256) k_front_grp(const FactorRec* __restrict__
         T* R = fac + fr.R_off;
         T* S = cbs + fr.S_off;
 #pragma unroll
-        for (int j = 0; j < G; j++) {
+        for (int j = 0; j < MJ; j++) {
             if (j < k) P[i + j * m] = a[j];
             else if (j < m) {
                 if (i < k) R[i + (j - k) * k] = a[j];
