@@ -54,6 +54,10 @@ struct Launch {
 constexpr int kLgLists = 15;
 constexpr int kLgG[kLgLists] = {4, 4, 4, 4, 4, 4, 8, 8, 8, 16, 16, 16, 32, 32, 32};
 constexpr int kLgR[kLgLists] = {1, 2, 2, 4, 4, 4, 4, 4, 4, 4, 4, 4, 3, 3, 3};
+// several right-hand sides per launch (each lane carries R x kRhsChunk values): one row per lane
+// up to 32 rows, so the same lists run at full occupancy
+constexpr int kLgGm[kLgLists] = {4, 8, 8, 16, 16, 16, 32, 32, 32, 32, 32, 32, 32, 32, 32};
+constexpr int kLgRm[kLgLists] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 3, 3, 3};
 constexpr int kLgKM[kLgLists] = {4, 4, 8, 4, 8, 16, 4, 8, 16, 4, 8, 16, 4, 8, 16};
 static int lg_list_of(int m, int k) {
     const int base = m <= 4 ? 0 : m <= 8 ? 1 : m <= 16 ? 3 : m <= 32 ? 6 : m <= 64 ? 9 : m <= 96 ? 12 : -1;
@@ -2149,11 +2153,18 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         GRP_FWD(1, 8)
         GRP_FWD(2, 16)
 #undef GRP_FWD
-#define LG_FWD(Q)                                                                                      \
-        if (C.n_lg[Q]) {                                                                                           \
-            dim3 g((C.n_lg[Q] + 8 * (32 / kLgG[Q]) - 1) / (8 * (32 / kLgG[Q])));                                              \
-            if (!trans) SOLVE_NR(k_fwd_lg, (T, false, kLgG[Q], kLgR[Q], kLgKM[Q]), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
-            else SOLVE_NR(k_fwd_lg, (T, true, kLgG[Q], kLgR[Q], kLgKM[Q]), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+#define LG_FWD(Q)                                                                                           \
+        if (C.n_lg[Q]) {                                                                                    \
+            const int gq = nrhs == 1 ? kLgG[Q] : kLgGm[Q];                                                  \
+            const dim3 g((C.n_lg[Q] + 8 * (32 / gq) - 1) / (8 * (32 / gq)));                               \
+            const cudaStream_t ls = fan.next();                                                             \
+            if (nrhs == 1) {                                                                                \
+                if (!trans) CUDA_TRY(launch_dep(k_fwd_lg<T, false, kLgG[Q], kLgR[Q], kLgKM[Q], 1>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+                else CUDA_TRY(launch_dep(k_fwd_lg<T, true, kLgG[Q], kLgR[Q], kLgKM[Q], 1>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+            } else {                                                                                        \
+                if (!trans) CUDA_TRY(launch_dep(k_fwd_lg<T, false, kLgGm[Q], kLgRm[Q], kLgKM[Q], kRhsChunk>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+                else CUDA_TRY(launch_dep(k_fwd_lg<T, true, kLgGm[Q], kLgRm[Q], kLgKM[Q], kRhsChunk>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+            }                                                                                               \
         }
         LG_FWD(0)
         LG_FWD(1)
@@ -2237,11 +2248,18 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         GRP_BWD(2, 16)
         GRP_BWD(3, 32)
 #undef GRP_BWD
-#define LG_BWD(Q)                                                                                      \
-        if (C.n_lg[Q]) {                                                                                           \
-            dim3 g((C.n_lg[Q] + 8 * (32 / kLgG[Q]) - 1) / (8 * (32 / kLgG[Q])));                                              \
-            if (!trans) SOLVE_NR(k_bwd_lg, (T, false, kLgG[Q], kLgR[Q], kLgKM[Q]), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
-            else SOLVE_NR(k_bwd_lg, (T, true, kLgG[Q], kLgR[Q], kLgKM[Q]), (g, 256, 0, fan.next()), (L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
+#define LG_BWD(Q)                                                                                           \
+        if (C.n_lg[Q]) {                                                                                    \
+            const int gq = nrhs == 1 ? kLgG[Q] : kLgGm[Q];                                                  \
+            const dim3 g((C.n_lg[Q] + 8 * (32 / gq) - 1) / (8 * (32 / gq)));                               \
+            const cudaStream_t ls = fan.next();                                                             \
+            if (nrhs == 1) {                                                                                \
+                if (!trans) CUDA_TRY(launch_dep(k_bwd_lg<T, false, kLgG[Q], kLgR[Q], kLgKM[Q], 1>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
+                else CUDA_TRY(launch_dep(k_bwd_lg<T, true, kLgG[Q], kLgR[Q], kLgKM[Q], 1>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
+            } else {                                                                                        \
+                if (!trans) CUDA_TRY(launch_dep(k_bwd_lg<T, false, kLgGm[Q], kLgRm[Q], kLgKM[Q], kRhsChunk>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
+                else CUDA_TRY(launch_dep(k_bwd_lg<T, true, kLgGm[Q], kLgRm[Q], kLgKM[Q], kRhsChunk>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, d_x, n, nrhs)); \
+            }                                                                                               \
         }
         LG_BWD(0)
         LG_BWD(1)

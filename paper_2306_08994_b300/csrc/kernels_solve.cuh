@@ -608,24 +608,30 @@ __device__ __forceinline__ void k_fwd_cta_body(const FrontDev* __restrict__ fron
                 if (lane < wb) wr[pb + lane] = val;
             }
             __syncthreads();
-            // rows below the block: 16 coefficients of a row are loaded before their products (two
-            // memory round trips per row of a 32-wide block)
             for (int i = pb + wb + threadIdx.x; i < mr; i += blockDim.x) {
                 T acc[NR];
 #pragma unroll
                 for (int rr = 0; rr < NR; rr++) acc[rr] = T(0);
-                for (int p0 = 0; p0 < wb; p0 += 16) {
-                    // unconditional loads (columns past the block repeat its last one, weighted 0)
-                    T cf[16];
+                if constexpr (NR == 1) {
+                    // one right-hand side: 16 coefficients of the row loaded before their products
+                    // (unconditional loads; columns past the block repeat its last one, weighted 0)
+                    for (int p0 = 0; p0 < wb; p0 += 16) {
+                        T cf[16];
 #pragma unroll
-                    for (int p = 0; p < 16; p++) cf[p] = fcoef<T, TRANS>(P, R, m, k, i, pb + min(p0 + p, wb - 1));
+                        for (int p = 0; p < 16; p++) cf[p] = fcoef<T, TRANS>(P, R, m, k, i, pb + min(p0 + p, wb - 1));
 #pragma unroll
-                    for (int p = 0; p < 16; p++) {
-                        const int c = min(p0 + p, wb - 1);
-                        const T on = p0 + p < wb ? T(1) : T(0);
+                        for (int p = 0; p < 16; p++) {
+                            const T on = p0 + p < wb ? T(1) : T(0);
+                            acc[0] += (on * cf[p]) * w[pb + min(p0 + p, wb - 1)];
+                        }
+                    }
+                } else {
+#pragma unroll 4
+                    for (int p = 0; p < wb; p++) {
+                        const T cf = fcoef<T, TRANS>(P, R, m, k, i, pb + p);
 #pragma unroll
                         for (int rr = 0; rr < NR; rr++)
-                            if (rr < nr) acc[rr] += (on * cf[p]) * w[rr * ldw + pb + c];
+                            if (rr < nr) acc[rr] += cf * w[rr * ldw + pb + p];
                     }
                 }
 #pragma unroll
@@ -887,7 +893,7 @@ __device__ __forceinline__ void k_inv_gemv_body(const FrontDev* __restrict__ fro
     // kernel; the operand of the row's final update (its right-hand-side entry, or the dof it is
     // written to) before the inputs are staged.
     constexpr int RW = TRANS ? (32 + NW - 1) / NW : 1;  // rows per warp (TRANS) / per lane (!TRANS)
-    constexpr int PC = 8;                              // coefficients per row issued early
+    constexpr int PC = 8;  // coefficients per row issued early (before the wait for the previous kernel)
     T pre[RW][PC];
     T rhs[RW];
     int xi[RW];
