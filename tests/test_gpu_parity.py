@@ -306,6 +306,31 @@ def test_batched_meshes_with_four_rhs():
             off += n
 
 
+@pytest.mark.parametrize("sym", [0, 1])
+@pytest.mark.parametrize("case", ["q3_24", "q1_3d_8"])
+def test_one_and_four_rhs_substitutions_agree(case, sym):
+    """One FP32 factorization, then unrefined solves with one right-hand side (lane groups of
+    4-16 lanes with up to 4 rows per lane, row loads batched in the CTA kernels) and with four
+    (one row per lane, per-coefficient loops): the scaled copies of b give the scaled solution up
+    to FP32 rounding, and the single solve has an FP32-level backward error (host double-double
+    residual, Sec. 2.1 eq. Linear_system)."""
+    pr = {"q3_24": lambda: F.diffusion_2d(24, 3, seed=91), "q1_3d_8": lambda: F.diffusion_3d_q1(8, seed=92)}[case]()
+    a, f, vals = _setup(pr, "f32", symmetric=sym)
+    f.factor(vals)
+    b = pr.b[:, 0]
+    y1 = torch.tensor(b, device=DEV)
+    f.solve(y1)
+    scales = [1.0, 2.0, -1.0, 0.5]
+    y4 = torch.tensor(np.stack([s_ * b for s_ in scales]), device=DEV)
+    f.solve(y4)
+    y1 = y1.cpu().numpy()
+    y4 = y4.cpu().numpy()
+    top = np.abs(y1).max()
+    for c, s_ in enumerate(scales):
+        assert np.abs(y4[c] / s_ - y1).max() <= 1e-4 * top, (c, np.abs(y4[c] / s_ - y1).max() / top)
+    assert _backward_error_host(pr, y1, b) <= 1e-5
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_graph_replay_equals_direct_launches(prec):
     """use_graph: factor, solve and refinement replayed from captured CUDA graphs on a
