@@ -2132,10 +2132,15 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
 #define INV_LAUNCH(TR, PH, CNT, OFF)                                                                               \
     if ((PH == PH_BWD1 ? C.maxnc_inv : C.maxk_inv) > 512)                                                          \
         CUDA_TRY(launch_dep(k_inv_gemv<T, TR, PH, 32>, dim3(CNT, nrhs), dim3(1024), (32 * 32 + C.maxin_inv) * sizeof(T), \
-                            ls, fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_vsrc, vec, vs, ys, yss, d_x, n));    \
+                            ls, fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_vsrc, vec, vs, ys, yss, d_x, n,     \
+                            PH == PH_FWD2 ? fold : 0));                                                        \
     else                                                                                                           \
         CUDA_TRY(launch_dep(k_inv_gemv<T, TR, PH, 8>, dim3(CNT, nrhs), dim3(256), (8 * 32 + C.maxin_inv) * sizeof(T), \
-                            ls, fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_vsrc, vec, vs, ys, yss, d_x, n))
+                            ls, fr, F->d_rows + (OFF), fac, inv, F->d_dofs, F->d_vsrc, vec, vs, ys, yss, d_x, n,     \
+                            PH == PH_FWD2 ? fold : 0))
+    // the D scaling of symmetric solves goes into the forward kernels' pivot-row stores when every
+    // class runs as per-class launches (the subtree and persistent sweeps keep the separate pass)
+    const int fold = (scale_d && !trans && F->subs.h < 2 && c_top == a->n_cls) ? 1 : 0;
     for (int c = 0; c < c_top; c++) {
         const ClassList& C = F->classes_f[c];
         int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0) + (C.n_grp[0] > 0) + (C.n_grp[1] > 0) + (C.n_grp[2] > 0) + (C.n_grp[3] > 0);
@@ -2146,8 +2151,8 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
 #define GRP_FWD(Q, GS)                                                                                             \
         if (C.n_grp[Q]) {                                                                                          \
             dim3 g((C.n_grp[Q] + 8 * (32 / GS) - 1) / (8 * (32 / GS)));                                             \
-            if (!trans) SOLVE_NR(k_fwd_grp, (T, false, GS), (g, 256, 0, fan.next()), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
-            else SOLVE_NR(k_fwd_grp, (T, true, GS), (g, 256, 0, fan.next()), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+            if (!trans) SOLVE_NR(k_fwd_grp, (T, false, GS), (g, 256, 0, fan.next()), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, fold)); \
+            else SOLVE_NR(k_fwd_grp, (T, true, GS), (g, 256, 0, fan.next()), (fr, L + C.off_grp[Q], C.n_grp[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, fold)); \
         }
         GRP_FWD(0, 4)
         GRP_FWD(1, 8)
@@ -2159,11 +2164,11 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
             const dim3 g((C.n_lg[Q] + 8 * (32 / gq) - 1) / (8 * (32 / gq)));                               \
             const cudaStream_t ls = fan.next();                                                             \
             if (nrhs == 1) {                                                                                \
-                if (!trans) CUDA_TRY(launch_dep(k_fwd_lg<T, false, kLgG[Q], kLgR[Q], kLgKM[Q], 1>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
-                else CUDA_TRY(launch_dep(k_fwd_lg<T, true, kLgG[Q], kLgR[Q], kLgKM[Q], 1>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+                if (!trans) CUDA_TRY(launch_dep(k_fwd_lg<T, false, kLgG[Q], kLgR[Q], kLgKM[Q], 1>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, fold)); \
+                else CUDA_TRY(launch_dep(k_fwd_lg<T, true, kLgG[Q], kLgR[Q], kLgKM[Q], 1>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, fold)); \
             } else {                                                                                        \
-                if (!trans) CUDA_TRY(launch_dep(k_fwd_lg<T, false, kLgGm[Q], kLgRm[Q], kLgKM[Q], kRhsChunk>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
-                else CUDA_TRY(launch_dep(k_fwd_lg<T, true, kLgGm[Q], kLgRm[Q], kLgKM[Q], kRhsChunk>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs)); \
+                if (!trans) CUDA_TRY(launch_dep(k_fwd_lg<T, false, kLgGm[Q], kLgRm[Q], kLgKM[Q], kRhsChunk>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, fold)); \
+                else CUDA_TRY(launch_dep(k_fwd_lg<T, true, kLgGm[Q], kLgRm[Q], kLgKM[Q], kRhsChunk>, g, dim3(256), 0, ls, L + C.off_lg[Q], C.n_lg[Q], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, fold)); \
             }                                                                                               \
         }
         LG_FWD(0)
@@ -2184,21 +2189,21 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
 #undef LG_FWD
         if (C.n_grp[3]) {  // 16 < m <= 32: the one-front-per-warp kernel is faster forward
             dim3 g((C.n_grp[3] + 7) / 8);
-            if (!trans) SOLVE_NR(k_fwd_warp, (T, false), (g, 256, 0, fan.next()), (fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
-            else SOLVE_NR(k_fwd_warp, (T, true), (g, 256, 0, fan.next()), (fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
+            if (!trans) SOLVE_NR(k_fwd_warp, (T, false), (g, 256, 0, fan.next()), (fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, fold));
+            else SOLVE_NR(k_fwd_warp, (T, true), (g, 256, 0, fan.next()), (fr, L + C.off_grp[3], C.n_grp[3], fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, fold));
         }
         if (C.n_small) {
             dim3 g((C.n_small + 7) / 8);
-            if (!trans) SOLVE_NR(k_fwd_warp, (T, false), (g, 256, 0, fan.next()), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
-            else SOLVE_NR(k_fwd_warp, (T, true), (g, 256, 0, fan.next()), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs));
+            if (!trans) SOLVE_NR(k_fwd_warp, (T, false), (g, 256, 0, fan.next()), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, fold));
+            else SOLVE_NR(k_fwd_warp, (T, true), (g, 256, 0, fan.next()), (fr, L + C.off_small, C.n_small, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, fold));
         }
         if (C.n_cta) {
             dim3 g(C.n_cta);
             const int ldw = C.maxm_cta;
             const cudaStream_t ls = fan.next();
             size_t sm = dgs + (size_t)kRhsChunk * ldw * sizeof(T);
-            if (!trans) SOLVE_NR(k_fwd_cta, (T, false), (g, 256, sm, ls), (fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, ldw));
-            else SOLVE_NR(k_fwd_cta, (T, true), (g, 256, sm, ls), (fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, ldw));
+            if (!trans) SOLVE_NR(k_fwd_cta, (T, false), (g, 256, sm, ls), (fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, ldw, fold));
+            else SOLVE_NR(k_fwd_cta, (T, true), (g, 256, sm, ls), (fr, L + C.off_cta, 1, fac, F->d_dofs, F->d_vsrc, vec, vs, d_x, n, nrhs, ldw, fold));
         }
         if (C.n_piv) {
             const cudaStream_t ls = fan.next();
@@ -2218,7 +2223,7 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
         int rc = run_sweeps(true);
         if (rc != MF_OK) return rc;
     }
-    if (scale_d) {
+    if (scale_d && !fold) {
         int slot = prof_begin(F, s, FAM_OTHER, (16.0 + 8.0) * n * nrhs, 1.0 * n * nrhs);
         CUDA_TRY(launch_dep(k_scale_pivots, dim3((unsigned)((n * nrhs + 255) / 256)), dim3(256), 0, s, F->d_pdv, d_x, n, nrhs));
         prof_end(F, s, slot);

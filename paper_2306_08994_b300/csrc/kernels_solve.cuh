@@ -93,6 +93,15 @@ constexpr int kRhsChunk = 4;
 // coefficients, dof lists, gather sources) before its pdl_wait, and right-hand sides,
 // update vectors and pivot values only after it.
 
+// Symmetric solves scale the forward result by D before the backward sweep
+// (z = D y).  With scale set, a forward kernel stores the pivot rows as
+// y_p d_p (the pivot read from the factor, the product formed in FP64: the
+// same value the separate scaling pass computes), so that pass is skipped.
+template <typename T>
+__device__ __forceinline__ double pivot_out(T y, const T* P, int m, int row, int scale) {
+    return scale ? (double)y * (double)P[row + (int64_t)row * m] : (double)y;
+}
+
 // y = w / d for one right-hand side, w * (1/d) for several (one reciprocal
 // per pivot shared by the chunk).
 template <typename T, int NR>
@@ -109,7 +118,7 @@ template <typename T, bool TRANS, int NR>
 __device__ __forceinline__ void k_fwd_warp_body(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                   int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                   const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
-                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int vb) {
+                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int vb, int scale = 0) {
     const int wid = vb * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (wid >= count) return;
@@ -167,11 +176,11 @@ __device__ __forceinline__ void k_fwd_warp_body(const FrontDev* __restrict__ fro
             double* xr = x + (int64_t)(rb + rr) * n_dof;
             T* vr = vecs + (int64_t)(rb + rr) * vec_size;
             if (i0 < m) {
-                if (i0 < k) xr[fd[i0]] = (double)w0[rr];
+                if (i0 < k) xr[fd[i0]] = pivot_out(w0[rr], P, m, i0, scale);
                 else vr[fr.vec_off + (i0 - k)] = w0[rr];
             }
             if (i1 < m) {
-                if (i1 < k) xr[fd[i1]] = (double)w1[rr];
+                if (i1 < k) xr[fd[i1]] = pivot_out(w1[rr], P, m, i1, scale);
                 else vr[fr.vec_off + (i1 - k)] = w1[rr];
             }
         }
@@ -181,9 +190,9 @@ template <typename T, bool TRANS, int NR>
 __global__ void __launch_bounds__(256, NR == 1 ? 4 : 2) k_fwd_warp(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                   int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                   const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
-                                                  double* __restrict__ x, int64_t n_dof, int nrhs) {
+                                                  double* __restrict__ x, int64_t n_dof, int nrhs, int scale) {
     pdl_trigger();
-    k_fwd_warp_body<T, TRANS, NR>(fronts, list, count, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, blockIdx.x);
+    k_fwd_warp_body<T, TRANS, NR>(fronts, list, count, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, blockIdx.x, scale);
 }
 
 template <typename T, bool TRANS, int NR>
@@ -271,7 +280,7 @@ template <typename T, bool TRANS, int G, int R, int KM, int NR>
 __device__ __forceinline__ void k_fwd_lg_body(const SolveRec* __restrict__ list, int count, const T* __restrict__ fac,
                                               const int32_t* __restrict__ dofs, const int64_t* __restrict__ vsrc,
                                               T* __restrict__ vecs, int64_t vec_size, double* __restrict__ x,
-                                              int64_t n_dof, int nrhs, int vb) {
+                                              int64_t n_dof, int nrhs, int vb, int scale = 0) {
     static_assert(KM <= G * R, "pivot bound beyond the rows of a group");
     const int lane = threadIdx.x & 31;
     const int fidx = (vb * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
@@ -328,7 +337,7 @@ __device__ __forceinline__ void k_fwd_lg_body(const SolveRec* __restrict__ list,
 #pragma unroll
             for (int rr = 0; rr < NR; rr++) {
                 if (rr >= nr) break;
-                if (row < k) x[(int64_t)(rb + rr) * n_dof + src[q].xi] = (double)w[q][rr];
+                if (row < k) x[(int64_t)(rb + rr) * n_dof + src[q].xi] = pivot_out(w[q][rr], P, m, row, scale);
                 else vecs[(int64_t)(rb + rr) * vec_size + fr.vec_off + (row - k)] = w[q][rr];
             }
         }
@@ -338,9 +347,9 @@ template <typename T, bool TRANS, int G, int R, int KM, int NR>
 __global__ void __launch_bounds__(256) k_fwd_lg(const SolveRec* __restrict__ list, int count, const T* __restrict__ fac,
                                                 const int32_t* __restrict__ dofs, const int64_t* __restrict__ vsrc,
                                                 T* __restrict__ vecs, int64_t vec_size, double* __restrict__ x,
-                                                int64_t n_dof, int nrhs) {
+                                                int64_t n_dof, int nrhs, int scale) {
     pdl_trigger();
-    k_fwd_lg_body<T, TRANS, G, R, KM, NR>(list, count, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, blockIdx.x);
+    k_fwd_lg_body<T, TRANS, G, R, KM, NR>(list, count, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, blockIdx.x, scale);
 }
 
 // Backward (U x = y on the front's pivot rows; rows >= k already hold their
@@ -427,7 +436,7 @@ template <typename T, bool TRANS, int G, int NR>
 __device__ __forceinline__ void k_fwd_grp_body(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
-                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int vb) {
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int vb, int scale = 0) {
     const int lane = threadIdx.x & 31;
     const int fidx = (vb * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / G) + lane / G;
     const bool active = fidx < count;
@@ -475,7 +484,7 @@ __device__ __forceinline__ void k_fwd_grp_body(const FrontDev* __restrict__ fron
 #pragma unroll
             for (int rr = 0; rr < NR; rr++) {
                 if (rr >= nr) break;
-                if (i < k) x[(int64_t)(rb + rr) * n_dof + src.xi] = (double)w[rr];
+                if (i < k) x[(int64_t)(rb + rr) * n_dof + src.xi] = pivot_out(w[rr], P, m, i, scale);
                 else vecs[(int64_t)(rb + rr) * vec_size + fr.vec_off + (i - k)] = w[rr];
             }
         }
@@ -485,9 +494,9 @@ template <typename T, bool TRANS, int G, int NR>
 __global__ void __launch_bounds__(256) k_fwd_grp(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int count, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
-                                                 double* __restrict__ x, int64_t n_dof, int nrhs) {
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int scale) {
     pdl_trigger();
-    k_fwd_grp_body<T, TRANS, G, NR>(fronts, list, count, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, blockIdx.x);
+    k_fwd_grp_body<T, TRANS, G, NR>(fronts, list, count, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, blockIdx.x, scale);
 }
 
 template <typename T, bool TRANS, int G, int NR>
@@ -560,7 +569,8 @@ template <typename T, bool TRANS, int NR = kRhsChunk>
 __device__ __forceinline__ void k_fwd_cta_body(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int rows_all, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
-                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int ldw, int vb, unsigned char* smem_raw) {
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int ldw, int vb, unsigned char* smem_raw,
+                                                 int scale = 0) {
     __syncthreads();  // in a persistent sweep the previous body of this CTA may still be reading shared memory
     T* Dg = reinterpret_cast<T*>(smem_raw);  // 32 x 33
     T* w = Dg + 32 * 33;                     // kRhsChunk x ldw
@@ -642,7 +652,7 @@ __device__ __forceinline__ void k_fwd_cta_body(const FrontDev* __restrict__ fron
         }
         for (int i = threadIdx.x; i < mr; i += blockDim.x)
             for (int rr = 0; rr < nr; rr++) {
-                if (i < k) x[(int64_t)(rb + rr) * n_dof + fd[i]] = (double)w[rr * ldw + i];
+                if (i < k) x[(int64_t)(rb + rr) * n_dof + fd[i]] = pivot_out(w[rr * ldw + i], P, m, i, scale);
                 else vecs[(int64_t)(rb + rr) * vec_size + fr.vec_off + (i - k)] = w[rr * ldw + i];
             }
         __syncthreads();
@@ -652,10 +662,11 @@ template <typename T, bool TRANS, int NR>
 __global__ void __launch_bounds__(256) k_fwd_cta(const FrontDev* __restrict__ fronts, const SolveRec* __restrict__ list,
                                                  int rows_all, const T* __restrict__ fac, const int32_t* __restrict__ dofs,
                                                  const int64_t* __restrict__ vsrc, T* __restrict__ vecs, int64_t vec_size,
-                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int ldw) {
+                                                 double* __restrict__ x, int64_t n_dof, int nrhs, int ldw, int scale) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     pdl_trigger();
-    k_fwd_cta_body<T, TRANS, NR>(fronts, list, rows_all, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, ldw, blockIdx.x, smem_dyn);
+    k_fwd_cta_body<T, TRANS, NR>(fronts, list, rows_all, fac, dofs, vsrc, vecs, vec_size, x, n_dof, nrhs, ldw, blockIdx.x, smem_dyn,
+                                 scale);
 }
 
 // Backward, one CTA per mid-size front: the CB part of the pivot rows first,
@@ -864,7 +875,8 @@ __device__ __forceinline__ void k_inv_gemv_body(const FrontDev* __restrict__ fro
                                                   const T* __restrict__ fac, const T* __restrict__ inv,
                                                   const int32_t* __restrict__ dofs, const int64_t* __restrict__ vsrc,
                                                   T* __restrict__ vecs, int64_t vec_size, T* __restrict__ ys,
-                                                  int64_t ys_size, double* __restrict__ x, int64_t n_dof, int vb, unsigned char* smem_raw, int rr) {
+                                                  int64_t ys_size, double* __restrict__ x, int64_t n_dof, int vb, unsigned char* smem_raw, int rr,
+                                                  int scale = 0) {
     __syncthreads();  // in a persistent sweep the previous body of this CTA may still be reading shared memory
     T* red = reinterpret_cast<T*>(smem_raw);  // NW x 32
     T* vin = red + NW * 32;
@@ -881,7 +893,7 @@ __device__ __forceinline__ void k_inv_gemv_body(const FrontDev* __restrict__ fro
     const T* Q = inv + (fr.q_off >= 0 ? fr.q_off : 0);
     if (PH == PH_FWD2 && t.r0 < k) {
         pdl_wait();
-        for (int i = t.r0 + threadIdx.x; i < t.r1; i += blockDim.x) xr[fd[i]] = (double)__ldcg(yr + i);
+        for (int i = t.r0 + threadIdx.x; i < t.r1; i += blockDim.x) xr[fd[i]] = pivot_out(__ldcg(yr + i), P, m, i, scale);
         return;
     }
     const int nin = (PH == PH_BWD1) ? m - k : k;
@@ -1005,10 +1017,11 @@ __global__ void __launch_bounds__(NW * 32) k_inv_gemv(const FrontDev* __restrict
                                                   const T* __restrict__ fac, const T* __restrict__ inv,
                                                   const int32_t* __restrict__ dofs, const int64_t* __restrict__ vsrc,
                                                   T* __restrict__ vecs, int64_t vec_size, T* __restrict__ ys,
-                                                  int64_t ys_size, double* __restrict__ x, int64_t n_dof) {
+                                                  int64_t ys_size, double* __restrict__ x, int64_t n_dof, int scale) {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     pdl_trigger();
-    k_inv_gemv_body<T, TRANS, PH, NW>(fronts, tasks, fac, inv, dofs, vsrc, vecs, vec_size, ys, ys_size, x, n_dof, blockIdx.x, smem_dyn, blockIdx.y);
+    k_inv_gemv_body<T, TRANS, PH, NW>(fronts, tasks, fac, inv, dofs, vsrc, vecs, vec_size, ys, ys_size, x, n_dof, blockIdx.x, smem_dyn, blockIdx.y,
+                                      scale);
 }
 
 // ---------------------------------------------------------------------------
