@@ -422,6 +422,10 @@ enum Family { FAM_FUSED = 0, FAM_ASM = 1, FAM_PANEL = 2, FAM_TRAIL = 3, FAM_SCHU
               FAM_RESID = 7, FAM_OTHER = 8, FAM_INV = 9 };
 
 // Bracket one launch: returns a slot index (or -1 when profiling is off).
+// Symmetric solves with per-class launches only (no subtree or persistent sweep planned) take the
+// D scaling inside the forward kernels; the factorization then skips gathering the pivots.
+static bool scaling_folded(const mf_factors* F) { return F->sym && !F->use_sweep && F->subs.h < 2; }
+
 static int prof_begin(mf_factors* F, cudaStream_t s, int fam, double bytes, double flops, int kernels = 1,
                       int tag = -1, int kind = MF_TRACE_OTHER, int cls = -1, int tasks = 0) {
     F->acc_launch[fam] += kernels;
@@ -1950,7 +1954,7 @@ static int run_factor(mf_factors* F, const double* d_values, cudaStream_t s) {
         prof_end(F, s, slot);
         CUDA_TRY(cudaGetLastError());
     }
-    if (F->sym) {  // the pivots in dof order, read by the D scaling of every symmetric solve
+    if (F->sym && !scaling_folded(F)) {  // the pivots in dof order, read by the separate D scaling pass
         const int64_t n = a->n_dof;
         int slot2 = prof_begin(F, s_main, FAM_OTHER, (8.0 + F->tsize + 8.0) * n, 0.0);
         k_gather_pivots<T><<<(unsigned)((n + 255) / 256), 256, 0, s_main>>>(F->d_pdiag, fac, F->d_pdv, n);
@@ -2140,7 +2144,7 @@ static int run_solve(mf_factors* F, double* d_x, int nrhs, bool trans, cudaStrea
                             PH == PH_FWD2 ? fold : 0))
     // the D scaling of symmetric solves goes into the forward kernels' pivot-row stores when every
     // class runs as per-class launches (the subtree and persistent sweeps keep the separate pass)
-    const int fold = (scale_d && !trans && F->subs.h < 2 && c_top == a->n_cls) ? 1 : 0;
+    const int fold = (scale_d && !trans && F->subs.h < 2 && c_top == a->n_cls) ? 1 : 0;  // always when scaling_folded(F)
     for (int c = 0; c < c_top; c++) {
         const ClassList& C = F->classes_f[c];
         int nk = (C.n_small > 0) + (C.n_cta > 0) + 2 * (C.n_piv > 0) + (C.n_grp[0] > 0) + (C.n_grp[1] > 0) + (C.n_grp[2] > 0) + (C.n_grp[3] > 0);
